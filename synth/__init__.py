@@ -1,0 +1,16 @@
+"""Seeded synthetic inputs for the TL-FEA hot path.
+
+This package builds meshes (structured hexahedral grids split into T4/T10
+tetrahedra, or kept as H8 bricks), nodal displacement and velocity fields, and
+material tables. It contains no finite-element arithmetic: no shape functions,
+no quadrature, no stress. Both the CPU oracle (``oracle/``) and the CUDA path
+consume what it produces, so it must stay free of the method itself.
+"""
+
+from .mesh import (  # noqa: F401
+    T4, T10, H8, NODES_PER_ELEM, Mesh, box_mesh, concat_meshes,
+)
+from .workloads import (  # noqa: F401
+    block_t10_svk, cantilever_beam, batch_bodies, diff_block, newton_beams,
+    small_beam, lame_from_young,
+)
