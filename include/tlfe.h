@@ -1,0 +1,224 @@
+/*
+ * tlfe.h - C ABI of the GB300 (sm_103a) Total Lagrangian finite-element hot path.
+ *
+ * The operations follow "A Total Lagrangian Finite Element Framework for
+ * Multibody Dynamics: Part I - Formulation" (Zhou, Arivoli, Negrut):
+ *   - deformation gradient F = sum_i x_i h_i^T                 (Sec. 2.1, Eq. expression-F)
+ *   - H = Hp (U Hp)^{-1}, J_p = det(U Hp), quadrature          (Sec. 6)
+ *   - first Piola-Kirchhoff stress P(F, Fdot): St. Venant-Kirchhoff,
+ *     compressible neo-Hookean (Mooney-Rivlin with mu01 = 0),
+ *     Kelvin-Voigt damping                                      (Sec. 3.2, App. C)
+ *   - internal force f_i = int P h_i dV_r                       (Sec. 4.3, Eq. internal_force_universal)
+ *   - tangent K_ij = d f_i / d e_j                              (App. C, Eqs. svk_tangent, mr_tangent)
+ *   - backward-Euler residual and Newton matrix                 (Sec. 7, Eq. residual; Sec. 2.2 Newton matrix)
+ *
+ * Conventions shared by every call
+ *   - Node arrays are [n_nodes][3] row-major (x, y, z of node k at 3k..3k+2).
+ *   - Displacements: the state is passed as u = x - X_ref (and its rate
+ *     udot = xdot); the nodal unknowns of the paper are x = X_ref + u.
+ *   - Element arrays follow the global element numbering: blocks in the order
+ *     given at creation, elements of a block in their given order.
+ *   - Precision: a mesh created with TLFE_FP32 takes and returns float arrays
+ *     in every state/force call (element math in FP32); TLFE_FP64 takes double.
+ *     The Newton step state is always double.
+ *   - Pointers named *_dev are CUDA device pointers, *_host host pointers.
+ *     The caller owns every pointer it passes; the library never frees them and
+ *     keeps none of them after the call returns (create copies what it needs).
+ *   - Every call taking a stream (a cudaStream_t passed as void*, NULL = the
+ *     legacy default stream) only enqueues work on it and returns; results are
+ *     valid once the stream has reached that point. Calls do not synchronise
+ *     unless stated.
+ *   - Conditions found on the device (an inverted quadrature point, a
+ *     non-finite value) are latched in the mesh's status word and returned by
+ *     the next tlfe_sync (or by calls documented as synchronising).
+ *   - No call aborts, traps or exits; errors are returned as tlfe_status and a
+ *     thread-local message is available from tlfe_last_error().
+ *   - A mesh handle may be used from one host thread at a time.
+ */
+#ifndef TLFE_H
+#define TLFE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TLFE_OK = 0,
+    TLFE_E_INVALID = 1,       /* bad argument, out-of-range connectivity, bad sizes */
+    TLFE_E_OOM = 2,           /* device allocation failed */
+    TLFE_E_CUDA = 3,          /* a CUDA runtime call failed */
+    TLFE_E_INVERTED = 4,      /* J_p <= 0 at creation, or J <= 0 (neo-Hookean) on the device */
+    TLFE_E_NOT_CONVERGED = 5, /* Newton did not reach the tolerance within max_newton */
+    TLFE_E_TIMEOUT = 6,       /* a bounded device-side wait ran out */
+    TLFE_E_UNSUPPORTED = 7,   /* valid request this build does not implement */
+    TLFE_E_NONFINITE = 8      /* NaN / Inf met on the device */
+} tlfe_status;
+
+enum { TLFE_T4 = 0, TLFE_T10 = 1, TLFE_H8 = 2 };   /* element types (App. A; T4/H8 textbook) */
+enum { TLFE_SVK = 0, TLFE_NEOHOOKE = 1 };           /* elastic laws (Sec. 3.2) */
+enum { TLFE_FP64 = 0, TLFE_FP32 = 1 };              /* element arithmetic */
+enum { TLFE_SCATTER_ATOMIC = 0, TLFE_SCATTER_COLOR = 1 };
+
+/* One type-homogeneous element block.
+ *   type  : TLFE_T4 (4 nodes), TLFE_T10 (10 nodes, App. A.1 node order),
+ *           TLFE_H8 (8 nodes, tensor order i + 2j + 4k on {-1,1}^3)
+ *   n_qp  : quadrature points per element: T4 1; T10 4 or 5; H8 8
+ *   conn  : host [n_elem][nodes] 0-based global node ids (copied)
+ *   body  : host [n_elem] body id in [0, n_bodies), or NULL for body 0 */
+typedef struct {
+    int32_t type;
+    int32_t n_elem;
+    int32_t n_qp;
+    const int32_t *conn;
+    const int32_t *body;
+} tlfe_block;
+
+/* Material of one body. model = TLFE_SVK or TLFE_NEOHOOKE with Lame (mu,
+ * lambda); the neo-Hookean law is the paper's Mooney-Rivlin form with mu01 = 0,
+ * mu10 = mu / 2 and bulk modulus k = lambda + 2 mu / 3. mu_v, lambda_v >= 0 are
+ * the Kelvin-Voigt dissipation constants (Sec. 3.2.3; 0 = undamped). rho is
+ * the reference density (used by the mass matrix and the body force). */
+typedef struct {
+    int32_t model;
+    double mu, lambda, mu_v, lambda_v, rho;
+} tlfe_material;
+
+typedef struct {
+    int32_t n_nodes;
+    const double *X_ref;            /* host [n_nodes][3] reference coordinates */
+    int32_t n_blocks;
+    const tlfe_block *blocks;       /* host [n_blocks] */
+    int32_t n_bodies;
+    const tlfe_material *body_mat;  /* host [n_bodies] */
+    const double *elem_mu_lambda;   /* host [n_elem_total][2] per-element (mu, lambda), or NULL */
+    int32_t precision;              /* TLFE_FP32 or TLFE_FP64 */
+    int32_t scatter;                /* TLFE_SCATTER_ATOMIC (fast, order not fixed) or
+                                       TLFE_SCATTER_COLOR (deterministic colour passes) */
+    uint64_t color_seed;            /* priority seed of the conflict colouring */
+} tlfe_mesh_desc;
+
+typedef struct tlfe_mesh tlfe_mesh;
+
+/* Build a mesh handle on the current CUDA device: validates connectivity and
+ * sizes, uploads them, and runs the reference precompute of Section 6 on the
+ * device (H_q = Hp(xi_q) (U Hp(xi_q))^{-1} and w_q J_p, in FP64, stored in the
+ * mesh precision). With TLFE_SCATTER_COLOR it also colours the elements
+ * (Jones-Plassmann with priority splitmix64(e xor color_seed); equal to the
+ * sequential greedy colouring in descending priority). Synchronises `stream`.
+ * Returns TLFE_E_INVERTED if any J_p <= 0, TLFE_E_INVALID on bad input. */
+tlfe_status tlfe_create_mesh(const tlfe_mesh_desc *desc, void *stream, tlfe_mesh **out);
+
+/* Release every device array of the handle. Synchronises the device. */
+tlfe_status tlfe_destroy_mesh(tlfe_mesh *mesh);
+
+typedef struct {
+    int32_t n_nodes, n_elem, n_blocks, n_colors, precision, scatter;
+    int64_t n_qp;
+    int64_t stream_bytes_force;   /* algorithmic bytes of one tlfe_internal_force (see design notes) */
+    int64_t stream_bytes_matvec;  /* algorithmic bytes of one tlfe_tangent_matvec */
+    int64_t stream_bytes_vjp;     /* algorithmic bytes of one tlfe_vjp (all outputs) */
+    int64_t device_bytes;         /* device memory held by the handle */
+} tlfe_mesh_info;
+
+tlfe_status tlfe_get_mesh_info(const tlfe_mesh *mesh, tlfe_mesh_info *info);
+
+/* Colour of every element in global element order (host [n_elem]); -1 when
+ * the mesh was not coloured. Synchronises. */
+tlfe_status tlfe_get_colors(const tlfe_mesh *mesh, int32_t *colors_host);
+
+/* Wait for `stream`, read and clear the device status word.
+ * n_inverted (nullable) receives the number of quadrature points that met
+ * J <= 0 since the last sync. Returns TLFE_E_INVERTED / TLFE_E_NONFINITE when
+ * such events were latched, else TLFE_OK. */
+tlfe_status tlfe_sync(tlfe_mesh *mesh, void *stream, int64_t *n_inverted);
+
+/* Internal force (Sec. 4.3, Eq. internal_force_universal):
+ *   f_i = sum_e sum_q w_q J_p P(F_q, Fdot_q) h_{i,q},
+ * F = I + sum_i u_i h_i^T, Fdot = sum_i udot_i h_i^T, P = P^e + F S^v.
+ * u_dev, udot_dev: device [n_nodes][3] (udot may be NULL: no viscous stress).
+ * f_dev: device [n_nodes][3], overwritten. f_int is the restoring force
+ * (+dPi/dx). */
+tlfe_status tlfe_internal_force(tlfe_mesh *mesh, const void *u_dev, const void *udot_dev,
+                                void *f_dev, void *stream);
+
+/* Same operation on HOST arrays (pageable or pinned): copies u (and udot) to
+ * device buffers held by the handle, evaluates, and copies f back, all on
+ * `stream`. Synchronises `stream` before returning. */
+tlfe_status tlfe_internal_force_host(tlfe_mesh *mesh, const void *u_host, const void *udot_host,
+                                     void *f_host, void *stream);
+
+/* Matrix-free operator product (App. C; Newton matrix of Sec. 2.2 / Sec. 7):
+ *   y = a_M M v + a_K K_t(u, udot) v + a_C C(u) v
+ * M: consistent mass m_ij = rho int s_i s_j dV (Sec. 4.1), K_t = d f_int / d x
+ * (elastic and viscous), C = d f_int / d xdot (Kelvin-Voigt). All dtype arrays
+ * are device [n_nodes][3]; udot may be NULL; y_dev is overwritten.
+ * a_M != 0 needs affine elements (straight-edged tetrahedra, parallelepiped
+ * bricks): TLFE_E_UNSUPPORTED otherwise. */
+tlfe_status tlfe_tangent_matvec(tlfe_mesh *mesh, const void *u_dev, const void *udot_dev,
+                                const void *v_dev, double a_M, double a_K, double a_C,
+                                void *y_dev, void *stream);
+
+/* Diagonal of a_M M + a_K K^e + a_C C (the Jacobi preconditioner of the
+ * Newton/CG step; K^e is the elastic, symmetric part of K_t).
+ * d_dev: device [n_nodes][3], overwritten. */
+tlfe_status tlfe_jacobi_diag(tlfe_mesh *mesh, const void *u_dev, const void *udot_dev,
+                             double a_M, double a_K, double a_C, void *d_dev, void *stream);
+
+/* Vector-Jacobian products of f_int against a cotangent r:
+ *   g_u = K_t^T r,   g_udot = C^T r,
+ *   g_mu_lambda[e] = (r . d f / d mu_e, r . d f / d lambda_e)
+ * cot_dev, g_u_dev, g_udot_dev: device [n_nodes][3] in the mesh dtype;
+ * g_mu_lambda_dev: device double [n_elem][2]. Any output may be NULL (not
+ * computed); non-NULL outputs are overwritten. */
+tlfe_status tlfe_vjp(tlfe_mesh *mesh, const void *u_dev, const void *udot_dev, const void *cot_dev,
+                     void *g_u_dev, void *g_udot_dev, double *g_mu_lambda_dev, void *stream);
+
+/* Backward-Euler step (Sec. 7, Eqs. step_map_velocity_level and residual,
+ * without constraints): find v with
+ *   g(v) = M/h (v - v_n) + f_int(u_n + h v, v) - f_ff = 0,
+ * f_ff_i = rho v_i b0 (Eq. virtual_work_force_field_uniform), by inexact
+ * Newton: each iteration solves (M/h + h K^e + C) dv = -g by Jacobi-PCG with
+ * per-body scalars (all bodies advance together, each stops on its own), and
+ * stops when ||g_b|| <= newton_rtol ||g_b(v_n)|| for every body b. The residual,
+ * the CG vectors, dots and updates are FP64; the operator products run in the
+ * mesh precision. Nodes with fixed_dev[k] = 1 are clamped (v = 0).
+ * The whole step is one CUDA graph with conditional WHILE nodes (built on the
+ * first call, replayed afterwards). */
+typedef struct {
+    double h;
+    double gravity[3];
+    double newton_rtol;
+    double cg_rtol;
+    int32_t max_newton;
+    int32_t max_cg;
+    const uint8_t *fixed_dev;  /* device [n_nodes], or NULL */
+    int32_t use_graph;         /* 1 = CUDA graph with conditional nodes, 0 = host-driven loop */
+} tlfe_step_params;
+
+typedef struct {
+    int32_t newton_iters;      /* max over bodies */
+    int32_t cg_iters;          /* total CG iterations run by the step */
+    int32_t status;            /* tlfe_status of the step */
+    int32_t n_bodies_converged;
+    double rel_residual;       /* max over bodies of ||g_b|| / ||g_b(v_n)|| */
+} tlfe_step_report;
+
+/* u_n_dev, v_n_dev, v_out_dev: device double [n_nodes][3]. report_host is
+ * written before return. Synchronises `stream`. */
+tlfe_status tlfe_newton_step(tlfe_mesh *mesh, const double *u_n_dev, const double *v_n_dev,
+                             const tlfe_step_params *params, double *v_out_dev,
+                             tlfe_step_report *report_host, void *stream);
+
+/* Thread-local text of the last error (never NULL). */
+const char *tlfe_last_error(void);
+
+/* Library version string. */
+const char *tlfe_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TLFE_H */

@@ -73,6 +73,7 @@ def lib():
                 "orc_operator_apply": [i32, i32, i32, P, i32, P, P, P, P, f64, f64, f64, i32,
                                        i32, P, P],
                 "orc_element_matrices": [i32, i32, P, P, P, P, P, P, P, P],
+                "orc_element_matrices_sym": [i32, i32, P, P, P, P, P, P, P, P],
                 "orc_vjp": [i32, i32, i32, P, i32, P, P, P, P, P, P, P, P],
                 "orc_lumped_row_sums": [i32, i32, P, i32, P, P, P],
                 "orc_gravity": [i32, i32, P, i32, P, P, P, P],
@@ -171,6 +172,26 @@ def element_matrices(etype, nq, conn_e, X, u, udot, mat):
                                       _p(_f64(udot)), _p(mat), _p(Ke), _p(Ce), _p(Me)),
            "element_matrices")
     return Ke, Ce, Me
+
+
+def jacobi_diag(wl, a_M=0.0, a_K=1.0, a_C=0.0, u=None, udot="state"):
+    """diag(a_M M + a_K K^e + a_C C) from the closed-form element matrices
+    (K^e: elastic part, the viscous stiffness left out)."""
+    u = _f64(wl.u if u is None else u)
+    udot = _f64(wl.udot if isinstance(udot, str) else udot)
+    X = _f64(wl.X)
+    d = np.zeros_like(X)
+    for bi, blk in enumerate(wl.blocks):
+        m = block_materials(wl, bi)
+        n3 = 3 * NPE[blk.etype]
+        Ke, Ce, Me = (np.zeros((n3, n3)) for _ in range(3))
+        for e in range(blk.n_elem):
+            ce = np.ascontiguousarray(blk.conn[e], dtype=np.int32)
+            _check(lib().orc_element_matrices_sym(blk.etype, blk.nq, _p(ce), _p(X), _p(u), _p(udot),
+                                                  _p(m[e:e + 1]), _p(Ke), _p(Ce), _p(Me)), "element_matrices")
+            dg = a_M * np.diag(Me) + a_K * np.diag(Ke) + a_C * np.diag(Ce)
+            np.add.at(d, ce, dg.reshape(-1, 3))
+    return d
 
 
 def splitmix64(x):

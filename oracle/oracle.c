@@ -755,6 +755,13 @@ int orc_element_matrices(int type, int nq, const int32_t *conn_e, const double *
     return element_matrices_sel(type, nq, conn_e, X, u, udot, m, 0, Ke, Ce, Me);
 }
 
+int orc_element_matrices_sym(int type, int nq, const int32_t *conn_e, const double *X,
+                             const double *u, const double *udot, const orc_material *m,
+                             double *Ke, double *Ce, double *Me)
+{
+    return element_matrices_sel(type, nq, conn_e, X, u, udot, m, 1, Ke, Ce, Me);
+}
+
 int orc_operator_apply(int type, int nq, int n_elem, const int32_t *conn, int n_nodes,
                        const double *X, const double *u, const double *udot,
                        const orc_material *mat, double a_M, double a_K, double a_C,

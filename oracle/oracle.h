@@ -74,6 +74,11 @@ int orc_element_matrices(int type, int nq, const int32_t *conn_e, const double *
                          const double *u, const double *udot, const orc_material *m,
                          double *Ke, double *Ce, double *Me);
 
+/* same, with the viscous stiffness K^v left out of Ke (symmetric part) */
+int orc_element_matrices_sym(int type, int nq, const int32_t *conn_e, const double *X,
+                             const double *u, const double *udot, const orc_material *m,
+                             double *Ke, double *Ce, double *Me);
+
 /* ---- adjoint: g_u = K_t^T r, g_udot = C^T r, g_theta = d(f.r)/d(mu, lam) */
 int orc_vjp(int type, int nq, int n_elem, const int32_t *conn, int n_nodes,
             const double *X, const double *u, const double *udot,

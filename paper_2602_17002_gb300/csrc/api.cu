@@ -1,0 +1,621 @@
+// C ABI of libtlfe: mesh creation (validation, tile layout, reference
+// precompute, colouring), the element operations, status handling.
+// The Newton/CG step lives in newton.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "tlfe_elem.cuh"
+#include "tlfe_internal.h"
+#include "tlfe_mesh.h"
+
+using namespace tlfe;
+
+namespace tlfe {
+
+static thread_local std::string g_err = "";
+
+tlfe_status fail(tlfe_status st, const std::string &msg)
+{
+    g_err = msg;
+    return st;
+}
+
+tlfe_status cuda_fail(cudaError_t e, const char *where)
+{
+    g_err = std::string(where) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? TLFE_E_OOM : TLFE_E_CUDA;
+}
+
+void *dalloc(tlfe_mesh *m, size_t bytes, cudaError_t *err)
+{
+    void *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        *err = e;
+        return nullptr;
+    }
+    m->allocs.push_back(p);
+    m->device_bytes += (int64_t)bytes;
+    return p;
+}
+
+}  // namespace tlfe
+
+#define CK(call)                                                      \
+    do {                                                              \
+        cudaError_t e_ = (call);                                      \
+        if (e_ != cudaSuccess) return tlfe::cuda_fail(e_, #call);     \
+    } while (0)
+
+#define CKA(ptr, bytes, m)                                            \
+    do {                                                              \
+        cudaError_t e_ = cudaSuccess;                                 \
+        (ptr) = decltype(ptr)(tlfe::dalloc((m), (bytes), &e_));       \
+        if (!(ptr)) return tlfe::cuda_fail(e_, "cudaMalloc " #ptr);   \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// mesh creation
+// ---------------------------------------------------------------------------
+
+static bool valid_nq(int et, int nq)
+{
+    return (et == ET_T4 && nq == 1) || (et == ET_T10 && (nq == 4 || nq == 5)) || (et == ET_H8 && nq == 8);
+}
+
+static tlfe_status validate(const tlfe_mesh_desc *d)
+{
+    if (!d) return fail(TLFE_E_INVALID, "desc is NULL");
+    if (d->n_nodes <= 0 || !d->X_ref) return fail(TLFE_E_INVALID, "n_nodes must be > 0 and X_ref non-NULL");
+    if (d->n_blocks <= 0 || !d->blocks) return fail(TLFE_E_INVALID, "n_blocks must be > 0 and blocks non-NULL");
+    if (d->n_bodies <= 0 || !d->body_mat) return fail(TLFE_E_INVALID, "n_bodies must be > 0 and body_mat non-NULL");
+    if (d->precision != TLFE_FP32 && d->precision != TLFE_FP64) return fail(TLFE_E_INVALID, "bad precision");
+    if (d->scatter != TLFE_SCATTER_ATOMIC && d->scatter != TLFE_SCATTER_COLOR)
+        return fail(TLFE_E_INVALID, "bad scatter mode");
+    for (int k = 0; k < 3 * d->n_nodes; ++k)
+        if (!std::isfinite(d->X_ref[k])) return fail(TLFE_E_INVALID, "X_ref holds a non-finite value");
+    for (int b = 0; b < d->n_bodies; ++b) {
+        const tlfe_material &m = d->body_mat[b];
+        if (m.model != TLFE_SVK && m.model != TLFE_NEOHOOKE) return fail(TLFE_E_INVALID, "bad material model");
+        if (!std::isfinite(m.mu) || !std::isfinite(m.lambda) || !std::isfinite(m.mu_v) ||
+            !std::isfinite(m.lambda_v) || !std::isfinite(m.rho) || m.mu_v < 0 || m.lambda_v < 0 || m.rho < 0)
+            return fail(TLFE_E_INVALID, "bad material parameters");
+    }
+    int64_t ne = 0;
+    for (int bi = 0; bi < d->n_blocks; ++bi) {
+        const tlfe_block &b = d->blocks[bi];
+        if (b.type < 0 || b.type > 2) return fail(TLFE_E_INVALID, "bad element type");
+        if (!valid_nq(b.type, b.n_qp)) return fail(TLFE_E_UNSUPPORTED, "unsupported quadrature size for the element type");
+        if (b.n_elem < 0 || (b.n_elem > 0 && !b.conn)) return fail(TLFE_E_INVALID, "bad block element count / conn");
+        const int npe = nodes_per_elem(b.type);
+        for (int64_t k = 0; k < (int64_t)b.n_elem * npe; ++k)
+            if (b.conn[k] < 0 || b.conn[k] >= d->n_nodes)
+                return fail(TLFE_E_INVALID, "connectivity entry out of range in block " + std::to_string(bi));
+        if (b.body)
+            for (int k = 0; k < b.n_elem; ++k)
+                if (b.body[k] < 0 || b.body[k] >= d->n_bodies)
+                    return fail(TLFE_E_INVALID, "body id out of range in block " + std::to_string(bi));
+        ne += b.n_elem;
+    }
+    if (ne <= 0 || ne > (int64_t)INT32_MAX / 2) return fail(TLFE_E_INVALID, "total element count out of range");
+    if (d->elem_mu_lambda)
+        for (int64_t k = 0; k < 2 * ne; ++k)
+            if (!std::isfinite(d->elem_mu_lambda[k])) return fail(TLFE_E_INVALID, "elem_mu_lambda non-finite");
+    return TLFE_OK;
+}
+
+// greedy-equivalent Jones-Plassmann colouring of one block on the device
+static tlfe_status color_block(tlfe_mesh *m, const tlfe_block &b, uint64_t seed, std::vector<int32_t> &col,
+                               cudaStream_t s)
+{
+    const int npe = nodes_per_elem(b.type);
+    const int n = b.n_elem;
+    // node -> incident elements (CSR) of this block
+    std::vector<int32_t> off(m->n_nodes + 1, 0), inc((size_t)n * npe);
+    for (int64_t k = 0; k < (int64_t)n * npe; ++k) off[b.conn[k] + 1]++;
+    for (int k = 0; k < m->n_nodes; ++k) off[k + 1] += off[k];
+    std::vector<int32_t> fill(m->n_nodes, 0);
+    for (int e = 0; e < n; ++e)
+        for (int i = 0; i < npe; ++i) {
+            const int nd = b.conn[(int64_t)e * npe + i];
+            inc[off[nd] + fill[nd]++] = e;
+        }
+    int32_t *d_conn, *d_off, *d_inc, *d_col;
+    int *d_cnt;
+    size_t bytes = sizeof(int32_t) * ((size_t)n * npe * 2 + m->n_nodes + 1 + n) + 2 * sizeof(int);
+    char *buf = nullptr;
+    CK(cudaMalloc(&buf, bytes));
+    d_conn = (int32_t *)buf;
+    d_inc = d_conn + (size_t)n * npe;
+    d_off = d_inc + (size_t)n * npe;
+    d_col = d_off + m->n_nodes + 1;
+    d_cnt = (int *)(d_col + n);
+    tlfe_status st = TLFE_OK;
+    int h_cnt[2] = {n, 0};
+    cudaError_t e = cudaMemcpyAsync(d_conn, b.conn, sizeof(int32_t) * n * npe, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_inc, inc.data(), sizeof(int32_t) * n * npe, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_off, off.data(), sizeof(int32_t) * (m->n_nodes + 1), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_col, 0xff, sizeof(int32_t) * n, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_cnt, h_cnt, sizeof(h_cnt), cudaMemcpyHostToDevice, s);
+    // each round colours at least the highest-priority uncoloured element, so
+    // n rounds always suffice; in practice a few dozen do
+    for (int round = 0; e == cudaSuccess && round <= n; ++round) {
+        e = launch_color_round(n, npe, d_conn, d_off, d_inc, nullptr, seed, 0, d_col, d_cnt, d_cnt + 1, s);
+        if (e != cudaSuccess) break;
+        e = cudaMemcpyAsync(h_cnt, d_cnt, sizeof(h_cnt), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess || h_cnt[0] == 0 || h_cnt[1]) break;
+    }
+    if (e != cudaSuccess) st = cuda_fail(e, "colouring");
+    else if (h_cnt[1]) st = fail(TLFE_E_UNSUPPORTED, "more than 256 colours needed");
+    else if (h_cnt[0] != 0) st = fail(TLFE_E_CUDA, "colouring did not finish");
+    if (st == TLFE_OK) {
+        col.resize(n);
+        e = cudaMemcpy(col.data(), d_col, sizeof(int32_t) * n, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) st = cuda_fail(e, "colour download");
+    }
+    cudaFree(buf);
+    return st;
+}
+
+template <typename R> static Mat<R> to_mat(const tlfe_material &s)
+{
+    Mat<R> m;
+    m.model = s.model;
+    m.mu = R(s.mu);
+    m.lam = R(s.lambda);
+    m.mu_v = R(s.mu_v);
+    m.lam_v = R(s.lambda_v);
+    m.rho = R(s.rho);
+    return m;
+}
+
+static tlfe_status build_block(tlfe_mesh *m, const tlfe_mesh_desc *d, int bi, int elem_base, cudaStream_t s)
+{
+    const tlfe_block &b = d->blocks[bi];
+    BlockStore &B = m->blocks[bi];
+    B.et = b.type;
+    B.nq = b.n_qp;
+    B.npe = nodes_per_elem(b.type);
+    B.n_elem = b.n_elem;
+    B.elem_base = elem_base;
+    const int npe = B.npe;
+
+    // element order inside the layout: identity, or grouped by colour
+    std::vector<int32_t> order(b.n_elem);
+    std::iota(order.begin(), order.end(), 0);
+    std::vector<int> color_of;
+    B.n_colors = 0;
+    if (d->scatter == TLFE_SCATTER_COLOR && b.n_elem > 0) {
+        std::vector<int32_t> col;
+        tlfe_status st = color_block(m, b, d->color_seed, col, s);
+        if (st != TLFE_OK) return st;
+        B.colors = col;
+        B.n_colors = *std::max_element(col.begin(), col.end()) + 1;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return col[a] < col[c]; });
+    }
+    // tiles: in colour mode every colour starts a new tile
+    std::vector<int32_t> eid;
+    B.color_tile_off.assign(1, 0);
+    if (d->scatter == TLFE_SCATTER_COLOR) {
+        size_t k = 0;
+        for (int c = 0; c < B.n_colors; ++c) {
+            size_t k0 = k;
+            while (k < order.size() && B.colors[order[k]] == c) ++k;
+            for (size_t j = k0; j < k; ++j) eid.push_back(elem_base + order[j]);
+            while (eid.size() % TILE) eid.push_back(-1);
+            B.color_tile_off.push_back((int)(eid.size() / TILE));
+        }
+    } else {
+        for (size_t j = 0; j < order.size(); ++j) eid.push_back(elem_base + order[j]);
+        while (eid.size() % TILE) eid.push_back(-1);
+        B.color_tile_off.push_back((int)(eid.size() / TILE));
+    }
+    B.n_tiles = (int)(eid.size() / TILE);
+
+    // per tile: sorted unique node list and (element, node) -> list index
+    std::vector<int32_t> toff(B.n_tiles + 1, 0), tnodes;
+    std::vector<uint16_t> lidx((size_t)B.n_tiles * npe * TILE, 0);
+    tnodes.reserve((size_t)B.n_tiles * npe * 12);
+    std::vector<int32_t> tmp;
+    B.umax = 1;
+    for (int t = 0; t < B.n_tiles; ++t) {
+        tmp.clear();
+        for (int l = 0; l < TILE; ++l) {
+            const int e = eid[(size_t)t * TILE + l];
+            if (e < 0) continue;
+            for (int i = 0; i < npe; ++i) tmp.push_back(b.conn[(int64_t)(e - elem_base) * npe + i]);
+        }
+        std::sort(tmp.begin(), tmp.end());
+        tmp.erase(std::unique(tmp.begin(), tmp.end()), tmp.end());
+        for (int l = 0; l < TILE; ++l) {
+            const int e = eid[(size_t)t * TILE + l];
+            if (e < 0) continue;
+            for (int i = 0; i < npe; ++i) {
+                const int nd = b.conn[(int64_t)(e - elem_base) * npe + i];
+                const int pos = (int)(std::lower_bound(tmp.begin(), tmp.end(), nd) - tmp.begin());
+                lidx[((size_t)t * npe + i) * TILE + l] = (uint16_t)pos;
+            }
+        }
+        tnodes.insert(tnodes.end(), tmp.begin(), tmp.end());
+        toff[t + 1] = (int32_t)tnodes.size();
+        B.umax = std::max(B.umax, (int)tmp.size());
+    }
+    B.n_unique = (int64_t)tnodes.size();
+
+    // materials: uniform when all elements of the block share one body
+    const bool have_body = b.body != nullptr && b.n_elem > 0;
+    const int body0 = have_body ? b.body[0] : 0;
+    bool uniform = true;
+    if (have_body)
+        for (int k = 0; k < b.n_elem; ++k)
+            if (b.body[k] != body0) uniform = false;
+    B.uniform_body = uniform ? body0 : -1;
+    B.visc = false;
+    for (int k = 0; k < b.n_elem; ++k) {
+        const tlfe_material &mm = d->body_mat[have_body ? b.body[k] : 0];
+        if (mm.mu_v != 0.0 || mm.lambda_v != 0.0) B.visc = true;
+        if (uniform) break;
+    }
+    const size_t rs = m->precision == TLFE_FP32 ? 4 : 8;
+    const size_t nslot = (size_t)B.n_tiles * TILE;
+    CKA(B.d_eid, sizeof(int32_t) * nslot, m);
+    CKA(B.d_toff, sizeof(int32_t) * (B.n_tiles + 1), m);
+    CKA(B.d_tnodes, sizeof(int32_t) * tnodes.size(), m);
+    CKA(B.d_lidx, sizeof(uint16_t) * lidx.size(), m);
+    CKA(B.d_H, rs * nslot * B.nq * npe * 3, m);
+    CKA(B.d_wJ, rs * nslot * B.nq, m);
+    CKA(B.d_evol, rs * nslot, m);
+    CK(cudaMemcpyAsync(B.d_eid, eid.data(), sizeof(int32_t) * nslot, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(B.d_toff, toff.data(), sizeof(int32_t) * toff.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(B.d_tnodes, tnodes.data(), sizeof(int32_t) * tnodes.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(B.d_lidx, lidx.data(), sizeof(uint16_t) * lidx.size(), cudaMemcpyHostToDevice, s));
+    B.d_emat = nullptr;
+    if (!uniform) {
+        std::vector<int32_t> em(nslot, 0);
+        for (size_t k = 0; k < nslot; ++k)
+            if (eid[k] >= 0) em[k] = b.body[eid[k] - elem_base];
+        CKA(B.d_emat, sizeof(int32_t) * nslot, m);
+        CK(cudaMemcpyAsync(B.d_emat, em.data(), sizeof(int32_t) * nslot, cudaMemcpyHostToDevice, s));
+    }
+    B.d_elam = nullptr;
+    if (d->elem_mu_lambda) {
+        CKA(B.d_elam, rs * nslot * 2, m);
+        std::vector<double> el(nslot * 2, 0.0);
+        for (int t = 0; t < B.n_tiles; ++t)
+            for (int l = 0; l < TILE; ++l) {
+                const int e = eid[(size_t)t * TILE + l];
+                if (e < 0) continue;
+                el[((size_t)t * 2 + 0) * TILE + l] = d->elem_mu_lambda[(size_t)e * 2 + 0];
+                el[((size_t)t * 2 + 1) * TILE + l] = d->elem_mu_lambda[(size_t)e * 2 + 1];
+            }
+        if (m->precision == TLFE_FP32) {
+            std::vector<float> ef(el.begin(), el.end());
+            CK(cudaMemcpy(B.d_elam, ef.data(), 4 * ef.size(), cudaMemcpyHostToDevice));
+        } else {
+            CK(cudaMemcpy(B.d_elam, el.data(), 8 * el.size(), cudaMemcpyHostToDevice));
+        }
+    }
+    // reference precompute (Sec. 6) on the device
+    int32_t *d_conn = nullptr;
+    int *d_aff = nullptr;
+    CK(cudaMalloc(&d_conn, sizeof(int32_t) * std::max<size_t>(1, (size_t)b.n_elem * npe)));
+    CK(cudaMalloc(&d_aff, sizeof(int)));
+    const int one = 1;
+    cudaError_t e = cudaMemcpyAsync(d_conn, b.conn, sizeof(int32_t) * b.n_elem * npe, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_aff, &one, sizeof(int), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = launch_precompute(B.et, B.nq, m->precision, B.n_tiles, B.d_eid, d_conn, elem_base, m->d_X, B.d_H,
+                              B.d_wJ, B.d_evol, d_aff, m->d_status, s);
+    int aff = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&aff, d_aff, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d_conn);
+    cudaFree(d_aff);
+    if (e != cudaSuccess) return cuda_fail(e, "reference precompute");
+    B.affine = aff != 0;
+    return TLFE_OK;
+}
+
+extern "C" tlfe_status tlfe_create_mesh(const tlfe_mesh_desc *desc, void *stream, tlfe_mesh **out)
+{
+    if (!out) return fail(TLFE_E_INVALID, "out is NULL");
+    *out = nullptr;
+    tlfe_status st = validate(desc);
+    if (st != TLFE_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    tlfe_mesh *m = new tlfe_mesh();
+    CK(cudaGetDevice(&m->device));
+    CK(cudaDeviceGetAttribute(&m->n_sm, cudaDevAttrMultiProcessorCount, m->device));
+    m->precision = desc->precision;
+    m->scatter = desc->scatter;
+    m->n_nodes = desc->n_nodes;
+    m->n_bodies = desc->n_bodies;
+    m->h_mats.assign(desc->body_mat, desc->body_mat + desc->n_bodies);
+    m->blocks.resize(desc->n_blocks);
+    auto bail = [&](tlfe_status e) {
+        tlfe_destroy_mesh(m);
+        return e;
+    };
+#define CKM(call)                                                            \
+    do {                                                                     \
+        cudaError_t e_ = (call);                                             \
+        if (e_ != cudaSuccess) return bail(tlfe::cuda_fail(e_, #call));      \
+    } while (0)
+    cudaError_t ae = cudaSuccess;
+    m->d_status = (int *)dalloc(m, sizeof(int) * ST_COUNT, &ae);
+    m->d_X = (double *)dalloc(m, sizeof(double) * 3 * m->n_nodes, &ae);
+    m->d_mats_f = (Mat<float> *)dalloc(m, sizeof(Mat<float>) * m->n_bodies, &ae);
+    m->d_mats_d = (Mat<double> *)dalloc(m, sizeof(Mat<double>) * m->n_bodies, &ae);
+    if (ae != cudaSuccess) return bail(cuda_fail(ae, "cudaMalloc"));
+    CKM(cudaMemsetAsync(m->d_status, 0, sizeof(int) * ST_COUNT, s));
+    CKM(cudaMemcpyAsync(m->d_X, desc->X_ref, sizeof(double) * 3 * m->n_nodes, cudaMemcpyHostToDevice, s));
+    {
+        std::vector<Mat<float>> mf;
+        std::vector<Mat<double>> md;
+        for (auto &mm : m->h_mats) {
+            mf.push_back(to_mat<float>(mm));
+            md.push_back(to_mat<double>(mm));
+        }
+        CKM(cudaMemcpy(m->d_mats_f, mf.data(), sizeof(Mat<float>) * mf.size(), cudaMemcpyHostToDevice));
+        CKM(cudaMemcpy(m->d_mats_d, md.data(), sizeof(Mat<double>) * md.size(), cudaMemcpyHostToDevice));
+    }
+    int base = 0;
+    for (int bi = 0; bi < desc->n_blocks; ++bi) {
+        st = build_block(m, desc, bi, base, s);
+        if (st != TLFE_OK) return bail(st);
+        base += desc->blocks[bi].n_elem;
+        m->n_qp += (int64_t)desc->blocks[bi].n_elem * desc->blocks[bi].n_qp;
+    }
+    m->n_elem = base;
+    int h_status[ST_COUNT];
+    CKM(cudaMemcpy(h_status, m->d_status, sizeof(h_status), cudaMemcpyDeviceToHost));
+    if (h_status[ST_INVERTED] > 0)
+        return bail(fail(TLFE_E_INVERTED, std::to_string(h_status[ST_INVERTED]) +
+                                              " element(s) with J_p <= 0 in the reference configuration"));
+    CKM(cudaMemsetAsync(m->d_status, 0, sizeof(int) * ST_COUNT, s));
+    CKM(cudaStreamSynchronize(s));
+#undef CKM
+    *out = m;
+    return TLFE_OK;
+}
+
+extern "C" tlfe_status tlfe_destroy_mesh(tlfe_mesh *m)
+{
+    if (!m) return TLFE_OK;
+    cudaDeviceSynchronize();
+    destroy_newton(m);
+    if (m->graph_exec) cudaGraphExecDestroy(m->graph_exec);
+    for (void *p : m->allocs) cudaFree(p);
+    delete m;
+    return TLFE_OK;
+}
+
+extern "C" tlfe_status tlfe_get_mesh_info(const tlfe_mesh *m, tlfe_mesh_info *info)
+{
+    if (!m || !info) return fail(TLFE_E_INVALID, "NULL argument");
+    info->n_nodes = m->n_nodes;
+    info->n_elem = m->n_elem;
+    info->n_blocks = (int)m->blocks.size();
+    info->precision = m->precision;
+    info->scatter = m->scatter;
+    info->n_qp = m->n_qp;
+    int nc = 0;
+    for (auto &B : m->blocks) nc = std::max(nc, B.n_colors);
+    info->n_colors = m->scatter == TLFE_SCATTER_COLOR ? nc : 0;
+    const int64_t rs = m->precision == TLFE_FP32 ? 4 : 8;
+    int64_t eb = 0;  // element-side bytes: H, wJ, local indices, tile node lists, material arrays
+    for (auto &B : m->blocks) {
+        eb += (int64_t)B.n_elem * (B.nq * B.npe * 3 * rs + B.nq * rs + B.npe * 2);
+        eb += B.n_unique * 4;
+        if (B.d_emat) eb += (int64_t)B.n_elem * 4;
+        if (B.d_elam) eb += (int64_t)B.n_elem * 2 * rs;
+    }
+    const int64_t nb = (int64_t)m->n_nodes * 3 * rs;
+    bool visc = false;
+    for (auto &B : m->blocks) visc = visc || B.visc;
+    info->stream_bytes_force = eb + nb * (visc ? 3 : 2);          // u (+udot) read, f written
+    info->stream_bytes_matvec = eb + nb * (visc ? 4 : 3);         // + v read
+    info->stream_bytes_vjp = eb + nb * (visc ? 5 : 3) + (int64_t)m->n_elem * 16;  // u, udot, r; g_u, g_udot; g_theta
+    info->device_bytes = m->device_bytes;
+    return TLFE_OK;
+}
+
+extern "C" tlfe_status tlfe_get_colors(const tlfe_mesh *m, int32_t *colors)
+{
+    if (!m || !colors) return fail(TLFE_E_INVALID, "NULL argument");
+    for (auto &B : m->blocks)
+        for (int k = 0; k < B.n_elem; ++k) colors[B.elem_base + k] = B.colors.empty() ? -1 : B.colors[k];
+    return TLFE_OK;
+}
+
+extern "C" tlfe_status tlfe_sync(tlfe_mesh *m, void *stream, int64_t *n_inverted)
+{
+    if (!m) return fail(TLFE_E_INVALID, "mesh is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    int h[ST_COUNT];
+    CK(cudaMemcpyAsync(h, m->d_status, sizeof(h), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemsetAsync(m->d_status, 0, sizeof(h), s));
+    CK(cudaStreamSynchronize(s));
+    if (n_inverted) *n_inverted = h[ST_INVERTED];
+    if (h[ST_TIMEOUT]) return fail(TLFE_E_TIMEOUT, "a bounded device wait ran out");
+    if (h[ST_NONFINITE]) return fail(TLFE_E_NONFINITE, "non-finite value met on the device");
+    if (h[ST_INVERTED]) return fail(TLFE_E_INVERTED, std::to_string(h[ST_INVERTED]) + " quadrature point(s) with J <= 0");
+    return TLFE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// element operations
+// ---------------------------------------------------------------------------
+
+namespace tlfe {
+
+template <typename R> static const Mat<R> *mats_of(const tlfe_mesh *m);
+template <> const Mat<float> *mats_of<float>(const tlfe_mesh *m) { return m->d_mats_f; }
+template <> const Mat<double> *mats_of<double>(const tlfe_mesh *m) { return m->d_mats_d; }
+
+template <int OP, typename R>
+static tlfe_status run_block_op(tlfe_mesh *m, const BlockStore &B, KParams<R> p, cudaStream_t s)
+{
+    p.umax = B.umax;
+    p.tnode_off = B.d_toff;
+    p.tnodes = B.d_tnodes;
+    p.lidx = B.d_lidx;
+    p.eid = B.d_eid;
+    p.H = (const R *)B.d_H;
+    p.wJ = (const R *)B.d_wJ;
+    p.emat = B.d_emat;
+    p.elam = (const R *)B.d_elam;
+    p.evol = (const R *)B.d_evol;
+    p.mats = B.d_emat ? mats_of<R>(m) : nullptr;
+    p.mat0 = to_mat<R>(m->h_mats[B.uniform_body >= 0 ? B.uniform_body : 0]);
+    p.visc = (B.visc && p.ud) ? 1 : 0;
+    p.status = m->d_status;
+    const size_t smem = (size_t)4 * B.umax * op_nf(OP) * sizeof(R);
+    int occ = m->occupancy(OP, B.et, B.nq, sizeof(R), smem, [&]() { return occupancy_op<OP, R>(B.et, B.nq, smem); });
+    if (occ <= 0) return fail(TLFE_E_UNSUPPORTED, "element kernel does not fit on the device (shared memory)");
+    const int n_passes = (int)B.color_tile_off.size() - 1;
+    for (int c = 0; c < n_passes; ++c) {
+        p.tile_begin = B.color_tile_off[c];
+        p.tile_end = B.color_tile_off[c + 1];
+        const int tiles = p.tile_end - p.tile_begin;
+        if (tiles <= 0) continue;
+        p.rmw_scatter = m->scatter == TLFE_SCATTER_COLOR ? 1 : 0;
+        const int need = (tiles + 3) / 4;
+        const int grid = std::max(1, std::min(need, occ * m->n_sm));
+        cudaError_t e = launch_op<OP, R>(B.et, B.nq, p, grid, s);
+        if (e != cudaSuccess) return cuda_fail(e, "element kernel launch");
+    }
+    return TLFE_OK;
+}
+
+template <int OP, typename R>
+tlfe_status run_op(tlfe_mesh *m, const void *u, const void *ud, const void *v, void *out0, void *out1,
+                   double *gth, double aM, double aK, double aC, int sym_only, cudaStream_t s)
+{
+    KParams<R> p;
+    memset(&p, 0, sizeof(p));
+    p.u = (const R *)u;
+    p.ud = (const R *)ud;
+    p.v = (const R *)v;
+    p.out0 = (R *)out0;
+    p.out1 = (R *)out1;
+    p.gth = gth;
+    p.aM = R(aM);
+    p.aK = R(aK);
+    p.aC = R(aC);
+    p.sym_only = sym_only;
+    const size_t nb = sizeof(R) * 3 * (size_t)m->n_nodes;
+    if (out0) CK(cudaMemsetAsync(out0, 0, nb, s));
+    if (out1) CK(cudaMemsetAsync(out1, 0, nb, s));
+    for (const BlockStore &B : m->blocks) {
+        if (B.n_elem == 0) continue;
+        tlfe_status st = run_block_op<OP, R>(m, B, p, s);
+        if (st != TLFE_OK) return st;
+    }
+    return TLFE_OK;
+}
+
+template tlfe_status run_op<OP_FORCE, float>(tlfe_mesh *, const void *, const void *, const void *, void *, void *, double *, double, double, double, int, cudaStream_t);
+template tlfe_status run_op<OP_FORCE, double>(tlfe_mesh *, const void *, const void *, const void *, void *, void *, double *, double, double, double, int, cudaStream_t);
+template tlfe_status run_op<OP_MATVEC, float>(tlfe_mesh *, const void *, const void *, const void *, void *, void *, double *, double, double, double, int, cudaStream_t);
+template tlfe_status run_op<OP_MATVEC, double>(tlfe_mesh *, const void *, const void *, const void *, void *, void *, double *, double, double, double, int, cudaStream_t);
+template tlfe_status run_op<OP_DIAG, float>(tlfe_mesh *, const void *, const void *, const void *, void *, void *, double *, double, double, double, int, cudaStream_t);
+template tlfe_status run_op<OP_DIAG, double>(tlfe_mesh *, const void *, const void *, const void *, void *, void *, double *, double, double, double, int, cudaStream_t);
+
+}  // namespace tlfe
+
+static tlfe_status check_mesh_args(tlfe_mesh *m, std::initializer_list<const void *> req)
+{
+    if (!m) return fail(TLFE_E_INVALID, "mesh is NULL");
+    for (const void *p : req)
+        if (!p) return fail(TLFE_E_INVALID, "required array pointer is NULL");
+    return TLFE_OK;
+}
+
+static bool all_affine(const tlfe_mesh *m)
+{
+    for (auto &B : m->blocks)
+        if (B.n_elem > 0 && !B.affine) return false;
+    return true;
+}
+
+extern "C" tlfe_status tlfe_internal_force(tlfe_mesh *m, const void *u, const void *ud, void *f, void *stream)
+{
+    tlfe_status st = check_mesh_args(m, {u, f});
+    if (st != TLFE_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    return m->precision == TLFE_FP32
+               ? run_op<OP_FORCE, float>(m, u, ud, nullptr, f, nullptr, nullptr, 0, 1, 0, 0, s)
+               : run_op<OP_FORCE, double>(m, u, ud, nullptr, f, nullptr, nullptr, 0, 1, 0, 0, s);
+}
+
+extern "C" tlfe_status tlfe_internal_force_host(tlfe_mesh *m, const void *u_h, const void *ud_h, void *f_h,
+                                                void *stream)
+{
+    tlfe_status st = check_mesh_args(m, {u_h, f_h});
+    if (st != TLFE_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t nb = (size_t)3 * m->n_nodes * (m->precision == TLFE_FP32 ? 4 : 8);
+    if (!m->d_stage) CKA(m->d_stage, 3 * nb, m);
+    char *du = (char *)m->d_stage, *dud = du + nb, *df = du + 2 * nb;
+    CK(cudaMemcpyAsync(du, u_h, nb, cudaMemcpyHostToDevice, s));
+    if (ud_h) CK(cudaMemcpyAsync(dud, ud_h, nb, cudaMemcpyHostToDevice, s));
+    st = tlfe_internal_force(m, du, ud_h ? dud : nullptr, df, stream);
+    if (st != TLFE_OK) return st;
+    CK(cudaMemcpyAsync(f_h, df, nb, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return TLFE_OK;
+}
+
+extern "C" tlfe_status tlfe_tangent_matvec(tlfe_mesh *m, const void *u, const void *ud, const void *v, double aM,
+                                           double aK, double aC, void *y, void *stream)
+{
+    tlfe_status st = check_mesh_args(m, {u, v, y});
+    if (st != TLFE_OK) return st;
+    if (!std::isfinite(aM) || !std::isfinite(aK) || !std::isfinite(aC)) return fail(TLFE_E_INVALID, "non-finite coefficient");
+    if (aM != 0.0 && !all_affine(m)) return fail(TLFE_E_UNSUPPORTED, "consistent mass needs affine elements");
+    cudaStream_t s = (cudaStream_t)stream;
+    return m->precision == TLFE_FP32
+               ? run_op<OP_MATVEC, float>(m, u, ud, v, y, nullptr, nullptr, aM, aK, aC, 0, s)
+               : run_op<OP_MATVEC, double>(m, u, ud, v, y, nullptr, nullptr, aM, aK, aC, 0, s);
+}
+
+extern "C" tlfe_status tlfe_jacobi_diag(tlfe_mesh *m, const void *u, const void *ud, double aM, double aK, double aC,
+                                        void *d, void *stream)
+{
+    tlfe_status st = check_mesh_args(m, {u, d});
+    if (st != TLFE_OK) return st;
+    if (aM != 0.0 && !all_affine(m)) return fail(TLFE_E_UNSUPPORTED, "consistent mass needs affine elements");
+    cudaStream_t s = (cudaStream_t)stream;
+    return m->precision == TLFE_FP32
+               ? run_op<OP_DIAG, float>(m, u, ud, nullptr, d, nullptr, nullptr, aM, aK, aC, 1, s)
+               : run_op<OP_DIAG, double>(m, u, ud, nullptr, d, nullptr, nullptr, aM, aK, aC, 1, s);
+}
+
+extern "C" tlfe_status tlfe_vjp(tlfe_mesh *m, const void *u, const void *ud, const void *cot, void *g_u, void *g_ud,
+                                double *g_th, void *stream)
+{
+    tlfe_status st = check_mesh_args(m, {u, cot});
+    if (st != TLFE_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t nb = (size_t)3 * m->n_nodes * (m->precision == TLFE_FP32 ? 4 : 8);
+    if ((!g_u || !g_ud) && !m->d_scratch_vjp) CKA(m->d_scratch_vjp, 2 * nb, m);
+    void *o0 = g_u ? g_u : m->d_scratch_vjp;
+    void *o1 = g_ud ? g_ud : (char *)m->d_scratch_vjp + nb;
+    return m->precision == TLFE_FP32
+               ? run_op<OP_VJP, float>(m, u, ud, cot, o0, o1, g_th, 0, 1, 0, 0, s)
+               : run_op<OP_VJP, double>(m, u, ud, cot, o0, o1, g_th, 0, 1, 0, 0, s);
+}
+
+extern "C" const char *tlfe_last_error(void) { return tlfe::g_err.c_str(); }
+
+extern "C" const char *tlfe_version(void) { return "tlfe 0.1 (sm_103a)"; }

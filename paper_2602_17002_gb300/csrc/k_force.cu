@@ -1,0 +1,9 @@
+// Instantiations of the element kernel for OP_FORCE.
+#include "k_elem.cuh"
+
+namespace tlfe {
+template cudaError_t launch_op<OP_FORCE, float>(int, int, const KParams<float> &, int, cudaStream_t);
+template cudaError_t launch_op<OP_FORCE, double>(int, int, const KParams<double> &, int, cudaStream_t);
+template int occupancy_op<OP_FORCE, float>(int, int, size_t);
+template int occupancy_op<OP_FORCE, double>(int, int, size_t);
+}  // namespace tlfe

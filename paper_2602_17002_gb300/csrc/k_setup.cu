@@ -1,0 +1,189 @@
+// Mesh set-up kernels: the reference precompute of Section 6 and one round
+// of the Jones-Plassmann conflict colouring.
+#include "tlfe_elem.cuh"
+#include "tlfe_internal.h"
+
+namespace tlfe {
+
+// One thread per (tile, lane): for each quadrature point,
+//   Jp = U Hp(xi_q)  (U = [X_1 .. X_n]),  h_i^T = dS_i/dxi Jp^{-1},
+//   wJ = w_q det(Jp)                               (Sec. 6, H = Hp (U Hp)^{-1}, J_p)
+// in FP64, stored in the AoSoA layout [tile][q][node][dim][lane] in the mesh
+// precision. Also records the element volume sum_q wJ and whether the element
+// is affine (straight edges / parallelepiped), which the consistent-mass
+// shortcut m_ij = rho V Mhat_ij needs.
+template <typename R>
+__global__ void k_precompute(int et, int nq, int npe, int n_tiles, const int32_t *__restrict__ eid,
+                             const int32_t *__restrict__ conn, int elem_base,
+                             const double *__restrict__ X, R *__restrict__ H, R *__restrict__ wJ,
+                             R *__restrict__ evol, int *affine_flag, int *status)
+{
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)n_tiles * 32) return;
+    const int64_t t = idx >> 5;
+    const int lane = (int)(idx & 31);
+    const int e = eid[idx];
+    if (e < 0) {
+        for (int q = 0; q < nq; ++q) {
+            for (int k = 0; k < npe * 3; ++k) H[((t * nq + q) * npe * 3 + k) * 32 + lane] = R(0);
+            wJ[(t * nq + q) * 32 + lane] = R(0);
+        }
+        evol[idx] = R(0);
+        return;
+    }
+    const int64_t el = (int64_t)e - elem_base;
+    double Xe[10][3];
+    for (int i = 0; i < npe; ++i) {
+        const int64_t n = conn[el * npe + i];
+        for (int a = 0; a < 3; ++a) Xe[i][a] = X[n * 3 + a];
+    }
+    double vol = 0.0, jmin = 1e300, jmax = -1e300;
+    int inverted = 0;
+    for (int q = 0; q < nq; ++q) {
+        double xi[3], w, g[30];
+        quad_point(et, nq, q, xi, w);
+        parent_grad(et, xi, g);
+        double J[9];
+        for (int a = 0; a < 3; ++a)
+            for (int k = 0; k < 3; ++k) {
+                double s = 0.0;
+                for (int i = 0; i < npe; ++i) s += Xe[i][a] * g[i * 3 + k];
+                J[a * 3 + k] = s;
+            }
+        const double c00 = J[4] * J[8] - J[5] * J[7];
+        const double c01 = J[5] * J[6] - J[3] * J[8];
+        const double c02 = J[3] * J[7] - J[4] * J[6];
+        const double det = J[0] * c00 + J[1] * c01 + J[2] * c02;
+        jmin = fmin(jmin, det);
+        jmax = fmax(jmax, det);
+        double Ji[9];  // Jp^{-1} = cof(Jp)^T / det
+        Ji[0] = c00 / det;
+        Ji[3] = c01 / det;
+        Ji[6] = c02 / det;
+        Ji[1] = (J[2] * J[7] - J[1] * J[8]) / det;
+        Ji[4] = (J[0] * J[8] - J[2] * J[6]) / det;
+        Ji[7] = (J[1] * J[6] - J[0] * J[7]) / det;
+        Ji[2] = (J[1] * J[5] - J[2] * J[4]) / det;
+        Ji[5] = (J[2] * J[3] - J[0] * J[5]) / det;
+        Ji[8] = (J[0] * J[4] - J[1] * J[3]) / det;
+        const bool ok = det > 0.0;
+        if (!ok) inverted = 1;
+        for (int i = 0; i < npe; ++i)
+            for (int c = 0; c < 3; ++c) {
+                double s = 0.0;
+                for (int k = 0; k < 3; ++k) s += g[i * 3 + k] * Ji[k * 3 + c];
+                H[((t * nq + q) * npe * 3 + i * 3 + c) * 32 + lane] = ok ? R(s) : R(0);
+            }
+        const double wj = ok ? w * det : 0.0;
+        wJ[(t * nq + q) * 32 + lane] = R(wj);
+        vol += wj;
+    }
+    evol[idx] = R(vol);
+    if (inverted) atomicAdd(status + ST_INVERTED, 1);
+    // affine test: mid-edge nodes at edge midpoints (T10), parallelepiped (H8)
+    bool affine = true;
+    double ext = 0.0;
+    for (int i = 1; i < npe; ++i)
+        for (int a = 0; a < 3; ++a) ext = fmax(ext, fabs(Xe[i][a] - Xe[0][a]));
+    const double tol = 1e-10 * ext;
+    if (et == ET_T10) {
+        for (int m = 0; m < 6; ++m) {
+            int a, b;
+            t10_edge(m, a, b);
+            for (int d = 0; d < 3; ++d)
+                if (fabs(Xe[4 + m][d] - 0.5 * (Xe[a][d] + Xe[b][d])) > tol) affine = false;
+        }
+    } else if (et == ET_H8) {
+        for (int n = 0; n < 8; ++n)
+            for (int d = 0; d < 3; ++d) {
+                const double p = Xe[0][d] + ((n & 1) ? Xe[1][d] - Xe[0][d] : 0.0) +
+                                 ((n & 2) ? Xe[2][d] - Xe[0][d] : 0.0) + ((n & 4) ? Xe[4][d] - Xe[0][d] : 0.0);
+                if (fabs(Xe[n][d] - p) > tol) affine = false;
+            }
+    }
+    (void)jmin;
+    (void)jmax;
+    if (!affine) atomicAnd(affine_flag, 0);
+}
+
+cudaError_t launch_precompute(int et, int nq, int precision, int n_tiles, const int32_t *eid,
+                              const int32_t *conn_elem, int elem_base, const double *X, void *H,
+                              void *wJ, void *evol, int *affine_flag, int *status, cudaStream_t s)
+{
+    const int npe = nodes_per_elem(et);
+    const int64_t n = (int64_t)n_tiles * 32;
+    const int tpb = 128;
+    const unsigned grid = (unsigned)((n + tpb - 1) / tpb);
+    if (grid == 0) return cudaSuccess;
+    if (precision == TLFE_FP32)
+        k_precompute<float><<<grid, tpb, 0, s>>>(et, nq, npe, n_tiles, eid, conn_elem, elem_base, X,
+                                                 (float *)H, (float *)wJ, (float *)evol, affine_flag, status);
+    else
+        k_precompute<double><<<grid, tpb, 0, s>>>(et, nq, npe, n_tiles, eid, conn_elem, elem_base, X,
+                                                  (double *)H, (double *)wJ, (double *)evol, affine_flag,
+                                                  status);
+    return cudaGetLastError();
+}
+
+// splitmix64 finaliser (Steele, Lea and Flood 2014) applied to x + golden gamma
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x)
+{
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// One Jones-Plassmann round over the elements of one block. An uncoloured
+// element whose uncoloured conflicting neighbours (sharing a node) all have
+// lower priority takes the smallest colour not held by its coloured
+// neighbours. Coloured neighbours are exactly the higher-priority ones, so the
+// result equals greedy colouring in descending priority, whatever the order in
+// which elements of one round finish.
+__global__ void k_color_round(int n_elem, int npe, const int32_t *__restrict__ conn,
+                              const int32_t *__restrict__ inc_off, const int32_t *__restrict__ inc,
+                              uint64_t seed, int32_t *color, int *n_left, int *overflow)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_elem) return;
+    volatile int32_t *vc = color;
+    if (vc[e] >= 0) return;
+    const uint64_t pe = splitmix64((uint64_t)e ^ seed);
+    uint32_t used[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int i = 0; i < npe; ++i) {
+        const int nd = conn[(int64_t)e * npe + i];
+        for (int k = inc_off[nd]; k < inc_off[nd + 1]; ++k) {
+            const int o = inc[k];
+            if (o == e) continue;
+            const int c = vc[o];
+            if (c < 0) {
+                if (splitmix64((uint64_t)o ^ seed) > pe) return;
+            } else if (c < 256) {
+                used[c >> 5] |= 1u << (c & 31);
+            } else {
+                atomicExch(overflow, 1);
+            }
+        }
+    }
+    int c = 0;
+    while (c < 256 && (used[c >> 5] >> (c & 31)) & 1u) ++c;
+    if (c >= 256) {
+        atomicExch(overflow, 1);
+        c = 255;
+    }
+    vc[e] = c;
+    atomicSub(n_left, 1);
+}
+
+cudaError_t launch_color_round(int n_elem, int npe, const int32_t *conn, const int32_t *inc_off,
+                               const int32_t *inc, const int32_t *, uint64_t seed, int, int32_t *color,
+                               int *n_left, int *overflow, cudaStream_t s)
+{
+    const int tpb = 256;
+    const int grid = (n_elem + tpb - 1) / tpb;
+    if (grid == 0) return cudaSuccess;
+    k_color_round<<<grid, tpb, 0, s>>>(n_elem, npe, conn, inc_off, inc, seed, color, n_left, overflow);
+    return cudaGetLastError();
+}
+
+}  // namespace tlfe

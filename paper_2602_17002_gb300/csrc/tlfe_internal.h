@@ -1,0 +1,73 @@
+// Internal structures shared by the translation units of libtlfe.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/tlfe.h"
+#include "tlfe_math.cuh"
+
+namespace tlfe {
+
+enum { OP_FORCE = 0, OP_MATVEC = 1, OP_VJP = 2, OP_DIAG = 3 };
+enum { ST_INVERTED = 0, ST_NONFINITE = 1, ST_TIMEOUT = 2, ST_COUNT = 4 };
+
+constexpr int TILE = 32;  // elements per tile = lanes of one warp
+
+// values per node held in a warp's shared-memory patch: inputs (u, udot
+// [, v or cotangent]) then outputs (one array, two for the adjoint)
+__host__ __device__ constexpr int op_in_fields(int op) { return (op == OP_MATVEC || op == OP_VJP) ? 9 : 6; }
+__host__ __device__ constexpr int op_nf(int op) { return op_in_fields(op) + (op == OP_VJP ? 6 : 3); }
+
+// Everything an element kernel needs about one block and one call.
+template <typename R> struct KParams {
+    // block layout (AoSoA tiles of 32 elements, see create_mesh)
+    int tile_begin, tile_end;
+    int umax;                   // max unique nodes of a tile (shared-memory patch size)
+    const int32_t *tnode_off;   // [n_tiles + 1] offsets into tnodes
+    const int32_t *tnodes;      // sorted unique global node ids of each tile
+    const uint16_t *lidx;       // [n_tiles][npe][32] index of (elem, node) into the tile's list
+    const int32_t *eid;         // [n_tiles][32] global element id, -1 for padding lanes
+    const R *H;                 // [n_tiles][nq][npe][3][32]
+    const R *wJ;                // [n_tiles][nq][32]
+    const int32_t *emat;        // [n_tiles][32] material index, or nullptr (uniform mat0)
+    const R *elam;              // [n_tiles][2][32] per-element (mu, lam), or nullptr
+    const R *evol;              // [n_tiles][32] element volume (affine mass)
+    // materials
+    Mat<R> mat0;
+    const Mat<R> *mats;
+    // state and outputs ([n_nodes][3] arrays)
+    const R *u, *ud, *v;
+    R *out0, *out1;
+    double *gth;                // [n_elem][2] (VJP parameter gradient)
+    R aM, aK, aC;
+    int sym_only;
+    int rmw_scatter;            // 1: plain read-add-write (colour passes), 0: atomics
+    int visc;                   // udot given and material damped somewhere in the block
+    int *status;                // [ST_COUNT]
+};
+
+// element-kernel launcher for one op and precision, dispatching on (element
+// type, nq); grid = number of CTAs (4 warps each, grid-striding over tiles).
+// Defined in k_elem.cuh and instantiated in k_force.cu / k_matvec.cu /
+// k_vjp.cu / k_diag.cu.
+template <int OP, typename R>
+cudaError_t launch_op(int et, int nq, const KParams<R> &p, int grid, cudaStream_t s);
+
+// CTAs per SM the kernel of (op, et, nq, precision) can keep resident with
+// `smem` bytes of dynamic shared memory each
+template <int OP, typename R> int occupancy_op(int et, int nq, size_t smem);
+
+// set-up kernels
+cudaError_t launch_precompute(int et, int nq, int precision, int n_tiles, const int32_t *eid,
+                              const int32_t *conn_elem, int elem_base, const double *X, void *H,
+                              void *wJ, void *evol, int *affine_flag, int *status, cudaStream_t s);
+cudaError_t launch_color_round(int n_elem, int npe, const int32_t *conn, const int32_t *inc_off,
+                               const int32_t *inc, const int32_t *elem_local_to_block,
+                               uint64_t seed, int elem_base, int32_t *color, int *n_left,
+                               int *overflow, cudaStream_t s);
+
+}  // namespace tlfe

@@ -1,0 +1,76 @@
+// Host-side mesh handle of libtlfe.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <functional>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "tlfe_internal.h"
+
+namespace tlfe {
+
+struct NewtonState;  // newton.cu
+
+// One element block as stored on the device.
+struct BlockStore {
+    int et = 0, nq = 0, npe = 0, n_elem = 0, elem_base = 0, n_tiles = 0, umax = 0;
+    int n_colors = 0;
+    bool affine = false;
+    bool visc = false;
+    int uniform_body = 0;            // body id when every element shares it, else -1
+    int64_t n_unique = 0;            // sum over tiles of the unique node count
+    std::vector<int> color_tile_off; // tile range of each pass ([0, n_tiles] in atomic mode)
+    std::vector<int32_t> colors;     // colour of each block element (colour mode)
+    int32_t *d_eid = nullptr, *d_toff = nullptr, *d_tnodes = nullptr, *d_emat = nullptr;
+    uint16_t *d_lidx = nullptr;
+    void *d_H = nullptr, *d_wJ = nullptr, *d_evol = nullptr, *d_elam = nullptr;
+};
+
+}  // namespace tlfe
+
+struct tlfe_mesh {
+    int device = 0, n_sm = 0;
+    int precision = TLFE_FP32, scatter = TLFE_SCATTER_ATOMIC;
+    int n_nodes = 0, n_elem = 0, n_bodies = 0;
+    int64_t n_qp = 0;
+    int64_t device_bytes = 0;
+    std::vector<tlfe::BlockStore> blocks;
+    std::vector<tlfe_material> h_mats;
+    tlfe::Mat<float> *d_mats_f = nullptr;
+    tlfe::Mat<double> *d_mats_d = nullptr;
+    int *d_status = nullptr;
+    double *d_X = nullptr;
+    void *d_stage = nullptr;        // staging buffers of tlfe_internal_force_host
+    void *d_scratch_vjp = nullptr;  // stand-in outputs of tlfe_vjp
+    cudaGraphExec_t graph_exec = nullptr;
+    tlfe::NewtonState *newton = nullptr;
+    std::vector<void *> allocs;
+    std::map<std::tuple<int, int, int, int, size_t>, int> occ_cache;
+
+    int occupancy(int op, int et, int nq, int rsize, size_t smem, const std::function<int()> &query)
+    {
+        auto key = std::make_tuple(op, et, nq, rsize, smem);
+        auto it = occ_cache.find(key);
+        if (it != occ_cache.end()) return it->second;
+        const int v = query();
+        occ_cache[key] = v;
+        return v;
+    }
+};
+
+namespace tlfe {
+
+tlfe_status fail(tlfe_status st, const std::string &msg);
+tlfe_status cuda_fail(cudaError_t e, const char *where);
+void *dalloc(tlfe_mesh *m, size_t bytes, cudaError_t *err);
+void destroy_newton(tlfe_mesh *m);
+
+template <int OP, typename R>
+tlfe_status run_op(tlfe_mesh *m, const void *u, const void *ud, const void *v, void *out0, void *out1,
+                   double *gth, double aM, double aK, double aC, int sym_only, cudaStream_t s);
+
+}  // namespace tlfe

@@ -1,0 +1,340 @@
+"""Python binding of libtlfe (ctypes): argument marshalling only.
+
+Every computation happens in the CUDA library; this module checks tensor
+shapes/dtypes/devices, passes raw device pointers and the current CUDA stream,
+and turns non-zero status codes into exceptions. The function names mirror the
+C ABI in include/tlfe.h.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libtlfe.so")
+
+T4, T10, H8 = 0, 1, 2
+SVK, NEOHOOKE = 0, 1
+FP64, FP32 = 0, 1
+SCATTER_ATOMIC, SCATTER_COLOR = 0, 1
+
+STATUS = {0: "TLFE_OK", 1: "TLFE_E_INVALID", 2: "TLFE_E_OOM", 3: "TLFE_E_CUDA", 4: "TLFE_E_INVERTED",
+          5: "TLFE_E_NOT_CONVERGED", 6: "TLFE_E_TIMEOUT", 7: "TLFE_E_UNSUPPORTED", 8: "TLFE_E_NONFINITE"}
+
+
+class TLFEError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class tlfe_block(C.Structure):
+    _fields_ = [("type", C.c_int32), ("n_elem", C.c_int32), ("n_qp", C.c_int32),
+                ("conn", C.c_void_p), ("body", C.c_void_p)]
+
+
+class tlfe_material(C.Structure):
+    _fields_ = [("model", C.c_int32), ("mu", C.c_double), ("lambda_", C.c_double),
+                ("mu_v", C.c_double), ("lambda_v", C.c_double), ("rho", C.c_double)]
+
+
+class tlfe_mesh_desc(C.Structure):
+    _fields_ = [("n_nodes", C.c_int32), ("X_ref", C.c_void_p), ("n_blocks", C.c_int32),
+                ("blocks", C.c_void_p), ("n_bodies", C.c_int32), ("body_mat", C.c_void_p),
+                ("elem_mu_lambda", C.c_void_p), ("precision", C.c_int32), ("scatter", C.c_int32),
+                ("color_seed", C.c_uint64)]
+
+
+class tlfe_mesh_info(C.Structure):
+    _fields_ = [("n_nodes", C.c_int32), ("n_elem", C.c_int32), ("n_blocks", C.c_int32),
+                ("n_colors", C.c_int32), ("precision", C.c_int32), ("scatter", C.c_int32),
+                ("n_qp", C.c_int64), ("stream_bytes_force", C.c_int64),
+                ("stream_bytes_matvec", C.c_int64), ("stream_bytes_vjp", C.c_int64),
+                ("device_bytes", C.c_int64)]
+
+
+class tlfe_step_params(C.Structure):
+    _fields_ = [("h", C.c_double), ("gravity", C.c_double * 3), ("newton_rtol", C.c_double),
+                ("cg_rtol", C.c_double), ("max_newton", C.c_int32), ("max_cg", C.c_int32),
+                ("fixed_dev", C.c_void_p), ("use_graph", C.c_int32)]
+
+
+class tlfe_step_report(C.Structure):
+    _fields_ = [("newton_iters", C.c_int32), ("cg_iters", C.c_int32), ("status", C.c_int32),
+                ("n_bodies_converged", C.c_int32), ("rel_residual", C.c_double)]
+
+
+_lib = None
+
+EXPORTS = ["tlfe_create_mesh", "tlfe_destroy_mesh", "tlfe_get_mesh_info", "tlfe_get_colors", "tlfe_sync",
+           "tlfe_internal_force", "tlfe_internal_force_host", "tlfe_tangent_matvec", "tlfe_jacobi_diag",
+           "tlfe_vjp", "tlfe_newton_step", "tlfe_last_error", "tlfe_version"]
+
+
+def load(path: str = LIB_PATH) -> C.CDLL:
+    """Load libtlfe.so. Raises if it is missing: there is no fallback."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libtlfe.so not built at {path}; run __graft_entry__.build() "
+                          "(the TL-FEA path has no CPU fallback)")
+    L = C.CDLL(path)
+    P, I, D = C.c_void_p, C.c_int32, C.c_double
+    sig = {
+        "tlfe_create_mesh": [C.POINTER(tlfe_mesh_desc), P, C.POINTER(P)],
+        "tlfe_destroy_mesh": [P],
+        "tlfe_get_mesh_info": [P, C.POINTER(tlfe_mesh_info)],
+        "tlfe_get_colors": [P, P],
+        "tlfe_sync": [P, P, C.POINTER(C.c_int64)],
+        "tlfe_internal_force": [P, P, P, P, P],
+        "tlfe_internal_force_host": [P, P, P, P, P],
+        "tlfe_tangent_matvec": [P, P, P, P, D, D, D, P, P],
+        "tlfe_jacobi_diag": [P, P, P, D, D, D, P, P],
+        "tlfe_vjp": [P, P, P, P, P, P, P, P],
+        "tlfe_newton_step": [P, P, P, C.POINTER(tlfe_step_params), P, C.POINTER(tlfe_step_report), P],
+    }
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = C.c_int
+    L.tlfe_last_error.restype = C.c_char_p
+    L.tlfe_last_error.argtypes = []
+    L.tlfe_version.restype = C.c_char_p
+    L.tlfe_version.argtypes = []
+    _lib = L
+    return L
+
+
+def _check(code: int):
+    if code != 0:
+        raise TLFEError(code, load().tlfe_last_error().decode())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return C.c_void_p(t)
+    return C.c_void_p(t.data_ptr())
+
+
+class Mesh:
+    """Owner of a tlfe_mesh handle (see include/tlfe.h for the operations)."""
+
+    def __init__(self, X: np.ndarray, blocks: Sequence[tuple], materials: Sequence[tuple],
+                 elem_mu_lambda: Optional[np.ndarray] = None, precision: int = FP32,
+                 scatter: int = SCATTER_ATOMIC, color_seed: int = 0, stream=None):
+        """X: (n_nodes, 3) float64 reference coordinates.
+        blocks: (etype, n_qp, conn (n_elem, npe) int32, body (n_elem,) int32 or None).
+        materials: per body (model, mu, lam, mu_v, lam_v, rho)."""
+        L = load()
+        self._keep = []
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        assert X.ndim == 2 and X.shape[1] == 3
+        cb = (tlfe_block * len(blocks))()
+        for k, (et, nq, conn, body) in enumerate(blocks):
+            conn = np.ascontiguousarray(conn, dtype=np.int32)
+            body = None if body is None else np.ascontiguousarray(body, dtype=np.int32)
+            self._keep += [conn, body]
+            cb[k] = tlfe_block(int(et), int(conn.shape[0]), int(nq), conn.ctypes.data,
+                               None if body is None else body.ctypes.data)
+        cm = (tlfe_material * len(materials))()
+        for k, mt in enumerate(materials):
+            cm[k] = tlfe_material(int(mt[0]), *[float(x) for x in mt[1:6]])
+        eml = None
+        if elem_mu_lambda is not None:
+            eml = np.ascontiguousarray(elem_mu_lambda, dtype=np.float64)
+            self._keep.append(eml)
+        desc = tlfe_mesh_desc(X.shape[0], X.ctypes.data, len(blocks), C.addressof(cb), len(materials),
+                              C.addressof(cm), None if eml is None else eml.ctypes.data,
+                              int(precision), int(scatter), C.c_uint64(color_seed))
+        h = C.c_void_p()
+        _check(L.tlfe_create_mesh(C.byref(desc), _stream(stream), C.byref(h)))
+        self._h = h
+        self.precision = precision
+        self.n_nodes = X.shape[0]
+        self.info = self.get_info()
+        self._keep = None
+
+    @classmethod
+    def from_workload(cls, wl, precision=FP32, scatter=SCATTER_ATOMIC, color_seed=0, stream=None):
+        blocks = [(b.etype, b.nq, b.conn, b.body) for b in wl.blocks]
+        mats = [(int(wl.model[k]), *wl.params[k]) for k in range(wl.n_bodies)]
+        return cls(wl.X, blocks, mats, wl.elem_mu_lambda, precision, scatter, color_seed, stream)
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def torch_dtype(self):
+        import torch
+        return torch.float32 if self.precision == FP32 else torch.float64
+
+    def get_info(self) -> dict:
+        info = tlfe_mesh_info()
+        _check(load().tlfe_get_mesh_info(self._h, C.byref(info)))
+        return {k: getattr(info, k) for k, _ in tlfe_mesh_info._fields_}
+
+    def colors(self) -> np.ndarray:
+        out = np.zeros(self.info["n_elem"], np.int32)
+        _check(load().tlfe_get_colors(self._h, out.ctypes.data))
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().tlfe_destroy_mesh(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- checks
+    def _node_array(self, t, name, dtype=None):
+        import torch
+        if t is None:
+            return None
+        dt = dtype or self.torch_dtype
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dt and t.is_contiguous()
+                and tuple(t.shape) == (self.n_nodes, 3)):
+            raise TLFEError(1, f"{name} must be a contiguous CUDA {dt} tensor of shape ({self.n_nodes}, 3)")
+        return t
+
+    def _new(self, dtype=None):
+        import torch
+        return torch.empty((self.n_nodes, 3), dtype=dtype or self.torch_dtype, device="cuda")
+
+    # ---- operations (outputs are allocated when not given)
+    def sync(self, stream=None) -> int:
+        n = C.c_int64(0)
+        _check(load().tlfe_sync(self._h, _stream(stream), C.byref(n)))
+        return n.value
+
+    def internal_force(self, u, udot=None, out=None, stream=None):
+        self._node_array(u, "u")
+        self._node_array(udot, "udot")
+        out = self._new() if out is None else self._node_array(out, "out")
+        _check(load().tlfe_internal_force(self._h, _ptr(u), _ptr(udot), _ptr(out), _stream(stream)))
+        return out
+
+    def internal_force_host(self, u: np.ndarray, udot: Optional[np.ndarray], out: np.ndarray, stream=None):
+        """Host-buffer call: u, udot, out are contiguous numpy arrays (n_nodes, 3)."""
+        dt = np.float32 if self.precision == FP32 else np.float64
+        for a in (u, udot, out):
+            if a is not None and (a.dtype != dt or not a.flags.c_contiguous or a.shape != (self.n_nodes, 3)):
+                raise TLFEError(1, "host arrays must be contiguous (n_nodes, 3) of the mesh dtype")
+        _check(load().tlfe_internal_force_host(self._h, u.ctypes.data, None if udot is None else udot.ctypes.data,
+                                               out.ctypes.data, _stream(stream)))
+        return out
+
+    def internal_force_host_ptr(self, u_ptr: int, udot_ptr: Optional[int], out_ptr: int, stream=None):
+        _check(load().tlfe_internal_force_host(self._h, C.c_void_p(u_ptr),
+                                               None if udot_ptr is None else C.c_void_p(udot_ptr),
+                                               C.c_void_p(out_ptr), _stream(stream)))
+
+    def tangent_matvec(self, u, udot, v, a_M=0.0, a_K=1.0, a_C=0.0, out=None, stream=None):
+        self._node_array(u, "u")
+        self._node_array(udot, "udot")
+        self._node_array(v, "v")
+        out = self._new() if out is None else self._node_array(out, "out")
+        _check(load().tlfe_tangent_matvec(self._h, _ptr(u), _ptr(udot), _ptr(v), float(a_M), float(a_K),
+                                          float(a_C), _ptr(out), _stream(stream)))
+        return out
+
+    def jacobi_diag(self, u, udot=None, a_M=0.0, a_K=1.0, a_C=0.0, out=None, stream=None):
+        self._node_array(u, "u")
+        self._node_array(udot, "udot")
+        out = self._new() if out is None else self._node_array(out, "out")
+        _check(load().tlfe_jacobi_diag(self._h, _ptr(u), _ptr(udot), float(a_M), float(a_K), float(a_C),
+                                       _ptr(out), _stream(stream)))
+        return out
+
+    def vjp(self, u, udot, cot, want_u=True, want_udot=True, want_theta=True, stream=None):
+        import torch
+        self._node_array(u, "u")
+        self._node_array(udot, "udot")
+        self._node_array(cot, "cot")
+        gu = self._new() if want_u else None
+        gud = self._new() if want_udot else None
+        gth = torch.empty((self.info["n_elem"], 2), dtype=torch.float64, device="cuda") if want_theta else None
+        _check(load().tlfe_vjp(self._h, _ptr(u), _ptr(udot), _ptr(cot), _ptr(gu), _ptr(gud), _ptr(gth),
+                               _stream(stream)))
+        return gu, gud, gth
+
+    def newton_step(self, u_n, v_n, h, gravity=(0.0, 0.0, -9.81), fixed=None, newton_rtol=1e-8, cg_rtol=1e-4,
+                    max_newton=20, max_cg=1000, use_graph=True, v_out=None, stream=None):
+        import torch
+        self._node_array(u_n, "u_n", torch.float64)
+        self._node_array(v_n, "v_n", torch.float64)
+        v_out = self._new(torch.float64) if v_out is None else v_out
+        if fixed is not None and not (fixed.is_cuda and fixed.dtype == torch.uint8 and fixed.numel() == self.n_nodes):
+            raise TLFEError(1, "fixed must be a CUDA uint8 tensor with one entry per node")
+        p = tlfe_step_params(float(h), (C.c_double * 3)(*[float(g) for g in gravity]), float(newton_rtol),
+                             float(cg_rtol), int(max_newton), int(max_cg), _ptr(fixed), int(bool(use_graph)))
+        rep = tlfe_step_report()
+        code = load().tlfe_newton_step(self._h, _ptr(u_n), _ptr(v_n), C.byref(p), _ptr(v_out), C.byref(rep),
+                                       _stream(stream))
+        report = {k: getattr(rep, k) for k, _ in tlfe_step_report._fields_}
+        if code not in (0, 5):
+            _check(code)
+        report["code"] = code
+        return v_out, report
+
+
+# ---- C-ABI-named module functions -------------------------------------------
+
+def tlfe_create_mesh(*args, **kw) -> Mesh:
+    return Mesh(*args, **kw)
+
+
+def tlfe_destroy_mesh(mesh: Mesh):
+    mesh.close()
+
+
+def tlfe_internal_force(mesh: Mesh, u, udot, f, stream=None):
+    return mesh.internal_force(u, udot, out=f, stream=stream)
+
+
+def tlfe_internal_force_host(mesh: Mesh, u, udot, f, stream=None):
+    return mesh.internal_force_host(u, udot, f, stream=stream)
+
+
+def tlfe_tangent_matvec(mesh: Mesh, u, udot, v, a_M, a_K, a_C, y, stream=None):
+    return mesh.tangent_matvec(u, udot, v, a_M, a_K, a_C, out=y, stream=stream)
+
+
+def tlfe_jacobi_diag(mesh: Mesh, u, udot, a_M, a_K, a_C, d, stream=None):
+    return mesh.jacobi_diag(u, udot, a_M, a_K, a_C, out=d, stream=stream)
+
+
+def tlfe_vjp(mesh: Mesh, u, udot, cot, stream=None):
+    return mesh.vjp(u, udot, cot, stream=stream)
+
+
+def tlfe_newton_step(mesh: Mesh, u_n, v_n, h, **kw):
+    return mesh.newton_step(u_n, v_n, h, **kw)
+
+
+def tlfe_sync(mesh: Mesh, stream=None):
+    return mesh.sync(stream)
+
+
+def tlfe_version() -> str:
+    return load().tlfe_version().decode()

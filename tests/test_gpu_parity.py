@@ -1,0 +1,170 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU FP64 oracle.
+
+Tolerances (relative, max-norm, normalised by the oracle's max |value|):
+FP64 mode 1e-12, FP32 mode 2e-5; connectivity-derived integers (colours)
+bit-exact.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from synth.workloads import Block, Workload
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-12, 1: 2e-5}  # keyed by precision: FP64 = 0, FP32 = 1
+
+
+def T():
+    from paper_2602_17002_gb300 import tlfe
+    return tlfe
+
+
+def dev(a, dt):
+    return None if a is None else torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dt)
+
+
+def relerr(got, ref):
+    got = got.double().cpu().numpy() if hasattr(got, "cpu") else got
+    den = np.abs(ref).max()
+    return np.abs(got - ref).max() / (den if den > 0 else 1.0)
+
+
+def run_all(wl, prec, scatter=0, aM=0.0, aK=1.0, aC=0.0, diag=True):
+    tl = T()
+    mesh = tl.Mesh.from_workload(wl, precision=prec, scatter=scatter)
+    dt = mesh.torch_dtype
+    u, ud, v = dev(wl.u, dt), dev(wl.udot, dt), dev(wl.v, dt)
+    out = {"f": mesh.internal_force(u, ud), "y": mesh.tangent_matvec(u, ud, v, aM, aK, aC)}
+    out["gu"], out["gud"], out["gth"] = mesh.vjp(u, ud, v)
+    if diag:
+        out["d"] = mesh.jacobi_diag(u, ud, aM, aK, aC)
+    mesh.sync()
+    torch.cuda.synchronize()
+    return mesh, out
+
+
+def check_all(wl, out, prec, aM=0.0, aK=1.0, aC=0.0, diag=True):
+    tol = TOL[prec]
+    f_ref, _ = oracle.internal_force(wl)
+    assert relerr(out["f"], f_ref) <= tol
+    y_ref = oracle.operator_apply(wl, wl.v, a_M=aM, a_K=aK, a_C=aC)
+    assert relerr(out["y"], y_ref) <= tol
+    gu, gud, gth = oracle.vjp(wl, wl.v)
+    assert relerr(out["gu"], gu) <= tol
+    if wl.udot is not None and np.abs(gud).max() > 0:
+        assert relerr(out["gud"], gud) <= tol
+    assert relerr(out["gth"], gth) <= tol
+    if diag:
+        d_ref = oracle.jacobi_diag(wl, a_M=aM, a_K=aK, a_C=aC)
+        assert relerr(out["d"], d_ref) <= tol
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_block_t10_svk(prec):
+    wl = synth.block_t10_svk()
+    _, out = run_all(wl, prec)
+    check_all(wl, out, prec)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_small_beam_nh_kv_full_operator(prec):
+    wl = synth.small_beam(cells=(10, 2, 2))
+    h = 1e-3
+    _, out = run_all(wl, prec, aM=1.0 / h, aK=h, aC=1.0)
+    check_all(wl, out, prec, aM=1.0 / h, aK=h, aC=1.0)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_mixed_batch_t4_t10_h8(prec):
+    wl = synth.batch_bodies(n_bodies=9, seed=7, ne_range=(40, 400))
+    assert len(wl.blocks) >= 2
+    _, out = run_all(wl, prec)
+    check_all(wl, out, prec)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_per_element_parameters_and_damping(prec):
+    wl = synth.diff_block(cells=3)
+    _, out = run_all(wl, prec, aK=1.0, aC=2.0)
+    check_all(wl, out, prec, aK=1.0, aC=2.0)
+
+
+@pytest.mark.parametrize("n_elem", [1, 31, 33, 65])
+def test_ragged_tiles(n_elem):
+    base = synth.small_beam(cells=(6, 2, 2))
+    blk = base.blocks[0]
+    wl = Workload("ragged", base.X, [Block(blk.etype, blk.nq, blk.conn[:n_elem], blk.body[:n_elem])],
+                  base.model, base.params, u=base.u, udot=base.udot, v=base.v)
+    for prec in (0, 1):
+        _, out = run_all(wl, prec)
+        check_all(wl, out, prec)
+
+
+def test_empty_block_in_multiblock_mesh():
+    base = synth.small_beam(cells=(4, 1, 1))
+    blk = base.blocks[0]
+    wl = Workload("empty", base.X, [Block(blk.etype, blk.nq, blk.conn, blk.body),
+                                    Block(synth.T4, 1, np.zeros((0, 4), np.int32), np.zeros(0, np.int32))],
+                  base.model, base.params, u=base.u, udot=base.udot, v=base.v)
+    _, out = run_all(wl, 0)
+    check_all(wl, out, 0)
+
+
+def test_colour_scatter_matches_oracle_greedy_and_is_deterministic():
+    wl = synth.small_beam(cells=(12, 3, 3))
+    seed = 0xC0FFEE
+    tl = T()
+    mesh = tl.Mesh.from_workload(wl, precision=tl.FP32, scatter=tl.SCATTER_COLOR, color_seed=seed)
+    col = mesh.colors()
+    ref, nc = oracle.color_greedy(wl.blocks[0].conn, wl.n_nodes, seed)
+    assert np.array_equal(col, ref)
+    assert mesh.info["n_colors"] == nc
+    dt = mesh.torch_dtype
+    u, ud = dev(wl.u, dt), dev(wl.udot, dt)
+    f1 = mesh.internal_force(u, ud).cpu().numpy()
+    f2 = mesh.internal_force(u, ud).cpu().numpy()
+    assert np.array_equal(f1.view(np.uint32), f2.view(np.uint32))
+    f_ref, _ = oracle.internal_force(wl)
+    assert relerr(f1, f_ref) <= 2e-5
+
+
+def test_inverted_points_are_counted():
+    wl = synth.small_beam(cells=(4, 1, 1), damping=0.0)
+    # squash the beam through itself along x: J < 0 everywhere
+    u = wl.X * np.array([-2.0, 0.0, 0.0])
+    wl.u = u
+    _, bad = oracle.internal_force(wl)
+    assert bad > 0
+    tl = T()
+    mesh = tl.Mesh.from_workload(wl, precision=tl.FP64)
+    mesh.internal_force(dev(u, torch.float64), None)
+    with pytest.raises(tl.TLFEError) as ei:
+        mesh.sync()
+    assert ei.value.code == 4
+    assert mesh.sync() == 0  # cleared
+
+
+def test_inverted_reference_rejected():
+    tl = T()
+    m = synth.box_mesh(synth.T4, (1, 1, 1), (1, 1, 1))
+    conn = m.conn.copy()
+    conn[0, [1, 2]] = conn[0, [2, 1]]
+    with pytest.raises(tl.TLFEError) as ei:
+        tl.Mesh(m.X, [(synth.T4, 1, conn, None)], [(0, 1e6, 1e6, 0, 0, 1e3)])
+    assert ei.value.code == 4
+
+
+def test_host_buffer_call_matches_device_call():
+    wl = synth.small_beam(cells=(8, 2, 2))
+    tl = T()
+    mesh = tl.Mesh.from_workload(wl, precision=tl.FP32)
+    u = np.ascontiguousarray(wl.u, np.float32)
+    ud = np.ascontiguousarray(wl.udot, np.float32)
+    f_h = np.zeros_like(u)
+    mesh.internal_force_host(u, ud, f_h)
+    f_d = mesh.internal_force(dev(u, torch.float32), dev(ud, torch.float32)).cpu().numpy()
+    assert np.array_equal(f_h, f_d) or relerr(f_h, f_d) < 1e-6
