@@ -221,9 +221,13 @@ static tlfe_status build_block(tlfe_mesh *m, const tlfe_mesh_desc *d, int bi, in
     }
     B.n_tiles = (int)(eid.size() / TILE);
 
-    // per tile: sorted unique node list and (element, node) -> list index
+    // per tile: sorted unique node list, (element, node) -> list index, and
+    // the inverse map (unique node -> its slots i*32 + lane, with offsets)
     std::vector<int32_t> toff(B.n_tiles + 1, 0), tnodes;
     std::vector<uint16_t> lidx((size_t)B.n_tiles * npe * TILE, 0);
+    std::vector<uint16_t> nsl((size_t)B.n_tiles * npe * TILE, 0xFFFF), soff;
+    soff.reserve((size_t)B.n_tiles * (npe * 12 + 1));
+    std::vector<int> cnt;
     tnodes.reserve((size_t)B.n_tiles * npe * 12);
     std::vector<int32_t> tmp;
     B.umax = 1;
@@ -245,11 +249,48 @@ static tlfe_status build_block(tlfe_mesh *m, const tlfe_mesh_desc *d, int bi, in
                 lidx[((size_t)t * npe + i) * TILE + l] = (uint16_t)pos;
             }
         }
+        const int U = (int)tmp.size();
+        cnt.assign(U + 1, 0);
+        for (int l = 0; l < TILE; ++l)
+            if (eid[(size_t)t * TILE + l] >= 0)
+                for (int i = 0; i < npe; ++i) cnt[lidx[((size_t)t * npe + i) * TILE + l] + 1]++;
+        for (int k = 0; k < U; ++k) cnt[k + 1] += cnt[k];
+        for (int k = 0; k <= U; ++k) soff.push_back((uint16_t)cnt[k]);
+        for (int i = 0; i < npe; ++i)
+            for (int l = 0; l < TILE; ++l)
+                if (eid[(size_t)t * TILE + l] >= 0) {
+                    const int k = lidx[((size_t)t * npe + i) * TILE + l];
+                    nsl[(size_t)t * npe * TILE + cnt[k]++] = (uint16_t)(i * TILE + l);
+                }
         tnodes.insert(tnodes.end(), tmp.begin(), tmp.end());
         toff[t + 1] = (int32_t)tnodes.size();
-        B.umax = std::max(B.umax, (int)tmp.size());
+        B.umax = std::max(B.umax, U);
     }
     B.n_unique = (int64_t)tnodes.size();
+
+    // one fixed-size metadata record per tile, fetched by one bulk copy:
+    //   [U, 0, 0, 0 | eid[32] | node ids[umaxp] | lidx[npe][32] | nsl[npe*32] | soff[soffp]]
+    const int umaxp = (B.umax + 3) / 4 * 4;
+    const int soffp = (B.umax + 1 + 7) / 8 * 8;
+    B.meta_bytes = 16 + 4 * TILE + 4 * umaxp + 2 * 2 * npe * TILE + 2 * soffp;
+    B.meta_umaxp = umaxp;
+    std::vector<unsigned char> meta((size_t)B.n_tiles * B.meta_bytes, 0);
+    {
+        size_t so = 0;
+        for (int t = 0; t < B.n_tiles; ++t) {
+            unsigned char *r = meta.data() + (size_t)t * B.meta_bytes;
+            const int U = toff[t + 1] - toff[t];
+            int32_t *hdr = (int32_t *)r;
+            hdr[0] = U;
+            memcpy(r + 16, eid.data() + (size_t)t * TILE, 4 * TILE);
+            memcpy(r + 16 + 4 * TILE, tnodes.data() + toff[t], 4 * (size_t)U);
+            unsigned char *q = r + 16 + 4 * TILE + 4 * umaxp;
+            memcpy(q, lidx.data() + (size_t)t * npe * TILE, 2 * (size_t)npe * TILE);
+            memcpy(q + 2 * npe * TILE, nsl.data() + (size_t)t * npe * TILE, 2 * (size_t)npe * TILE);
+            memcpy(q + 4 * npe * TILE, soff.data() + so, 2 * (size_t)(U + 1));
+            so += U + 1;
+        }
+    }
 
     // materials: uniform when all elements of the block share one body
     const bool have_body = b.body != nullptr && b.n_elem > 0;
@@ -271,13 +312,16 @@ static tlfe_status build_block(tlfe_mesh *m, const tlfe_mesh_desc *d, int bi, in
     CKA(B.d_toff, sizeof(int32_t) * (B.n_tiles + 1), m);
     CKA(B.d_tnodes, sizeof(int32_t) * tnodes.size(), m);
     CKA(B.d_lidx, sizeof(uint16_t) * lidx.size(), m);
-    CKA(B.d_H, rs * nslot * B.nq * npe * 3, m);
-    CKA(B.d_wJ, rs * nslot * B.nq, m);
+    CKA(B.d_meta, meta.size(), m);
+    CKA(B.d_slab, rs * nslot * B.nq * (npe * 3 + 1), m);
     CKA(B.d_evol, rs * nslot, m);
     CK(cudaMemcpyAsync(B.d_eid, eid.data(), sizeof(int32_t) * nslot, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(B.d_toff, toff.data(), sizeof(int32_t) * toff.size(), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(B.d_tnodes, tnodes.data(), sizeof(int32_t) * tnodes.size(), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(B.d_lidx, lidx.data(), sizeof(uint16_t) * lidx.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(B.d_meta, meta.data(), meta.size(), cudaMemcpyHostToDevice, s));
+    // the host vectors are released below, before the copies have run: wait
+    CK(cudaStreamSynchronize(s));
     B.d_emat = nullptr;
     if (!uniform) {
         std::vector<int32_t> em(nslot, 0);
@@ -313,8 +357,8 @@ static tlfe_status build_block(tlfe_mesh *m, const tlfe_mesh_desc *d, int bi, in
     cudaError_t e = cudaMemcpyAsync(d_conn, b.conn, sizeof(int32_t) * b.n_elem * npe, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_aff, &one, sizeof(int), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
-        e = launch_precompute(B.et, B.nq, m->precision, B.n_tiles, B.d_eid, d_conn, elem_base, m->d_X, B.d_H,
-                              B.d_wJ, B.d_evol, d_aff, m->d_status, s);
+        e = launch_precompute(B.et, B.nq, m->precision, B.n_tiles, B.d_eid, d_conn, elem_base, m->d_X, B.d_slab,
+                              B.d_evol, d_aff, m->d_status, s);
     int aff = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&aff, d_aff, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -414,8 +458,8 @@ extern "C" tlfe_status tlfe_get_mesh_info(const tlfe_mesh *m, tlfe_mesh_info *in
     const int64_t rs = m->precision == TLFE_FP32 ? 4 : 8;
     int64_t eb = 0;  // element-side bytes: H, wJ, local indices, tile node lists, material arrays
     for (auto &B : m->blocks) {
-        eb += (int64_t)B.n_elem * (B.nq * B.npe * 3 * rs + B.nq * rs + B.npe * 2);
-        eb += B.n_unique * 4;
+        eb += (int64_t)B.n_elem * (B.nq * B.npe * 3 * rs + B.nq * rs);  // slab: h_i and w J_p
+        eb += (int64_t)B.n_tiles * B.meta_bytes;                        // per-tile metadata records
         if (B.d_emat) eb += (int64_t)B.n_elem * 4;
         if (B.d_elam) eb += (int64_t)B.n_elem * 2 * rs;
     }
@@ -469,9 +513,11 @@ static tlfe_status run_block_op(tlfe_mesh *m, const BlockStore &B, KParams<R> p,
     p.tnode_off = B.d_toff;
     p.tnodes = B.d_tnodes;
     p.lidx = B.d_lidx;
+    p.meta = B.d_meta;
+    p.meta_bytes = B.meta_bytes;
+    p.umaxp = B.meta_umaxp;
     p.eid = B.d_eid;
-    p.H = (const R *)B.d_H;
-    p.wJ = (const R *)B.d_wJ;
+    p.slab = (const R *)B.d_slab;
     p.emat = B.d_emat;
     p.elam = (const R *)B.d_elam;
     p.evol = (const R *)B.d_evol;
@@ -479,9 +525,18 @@ static tlfe_status run_block_op(tlfe_mesh *m, const BlockStore &B, KParams<R> p,
     p.mat0 = to_mat<R>(m->h_mats[B.uniform_body >= 0 ? B.uniform_body : 0]);
     p.visc = (B.visc && p.ud) ? 1 : 0;
     p.status = m->d_status;
-    const size_t smem = (size_t)4 * B.umax * op_nf(OP) * sizeof(R);
-    int occ = m->occupancy(OP, B.et, B.nq, sizeof(R), smem, [&]() { return occupancy_op<OP, R>(B.et, B.nq, smem); });
-    if (occ <= 0) return fail(TLFE_E_UNSUPPORTED, "element kernel does not fit on the device (shared memory)");
+    std::string why;
+    const int occ = m->occupancy(OP, B.et, B.nq, sizeof(R), (size_t)B.umax, [&]() {
+        int wbest = 0;
+        const int v = occupancy_op<OP, R>(B.et, B.nq, B.umax, B.meta_bytes, &wbest, &why);
+        m->occ_wpb[std::make_tuple(OP, B.et, B.nq, (int)sizeof(R), (size_t)B.umax)] = wbest;
+        return v;
+    });
+    const int wpb = m->occ_wpb[std::make_tuple(OP, B.et, B.nq, (int)sizeof(R), (size_t)B.umax)];
+    if (occ <= 0) {
+        m->occ_cache.erase(std::make_tuple(OP, B.et, B.nq, (int)sizeof(R), (size_t)B.umax));
+        return fail(TLFE_E_UNSUPPORTED, "element kernel cannot be made resident: " + why);
+    }
     const int n_passes = (int)B.color_tile_off.size() - 1;
     for (int c = 0; c < n_passes; ++c) {
         p.tile_begin = B.color_tile_off[c];
@@ -489,9 +544,10 @@ static tlfe_status run_block_op(tlfe_mesh *m, const BlockStore &B, KParams<R> p,
         const int tiles = p.tile_end - p.tile_begin;
         if (tiles <= 0) continue;
         p.rmw_scatter = m->scatter == TLFE_SCATTER_COLOR ? 1 : 0;
-        const int need = (tiles + 3) / 4;
-        const int grid = std::max(1, std::min(need, occ * m->n_sm));
-        cudaError_t e = launch_op<OP, R>(B.et, B.nq, p, grid, s);
+        // one warp per tile at a time, persistent over the resident warps
+        const int warps = std::min(tiles, std::max(1, occ / wpb) * wpb * m->n_sm);
+        const int grid = std::max(1, (warps + wpb - 1) / wpb);
+        cudaError_t e = launch_op<OP, R>(B.et, B.nq, p, grid, wpb, s);
         if (e != cudaSuccess) return cuda_fail(e, "element kernel launch");
     }
     return TLFE_OK;

@@ -1,272 +1,476 @@
-// Element kernels of the TL-FEA hot path (force, operator product, adjoint,
-// Jacobi diagonal), templated on element type, quadrature size, arithmetic
-// type and operation.
+// Element kernels of the TL-FEA hot path (internal force, operator product,
+// adjoint, Jacobi diagonal), templated on element type, quadrature size,
+// arithmetic type and operation.
 //
-// Work decomposition: one warp owns a tile of 32 elements (one element per
-// lane) at a time, grid-striding over tiles. Per tile:
-//   1. the warp gathers the nodal values of the tile's unique nodes (a sorted
-//      list built at mesh creation) into a shared-memory patch: consecutive
-//      lanes read consecutive node ids, so the gather is close to coalesced;
-//   2. each lane reads its element's node values from the patch through the
-//      precomputed local indices, streams its H and wJ slices (AoSoA layout,
-//      one 128-byte line per warp load, evict-first), and evaluates
-//      F = I + sum u_i h_i^T, the stress (or its directional derivative /
-//      adjoint) and the element vector sum_q wJ_q (.) h_i per quadrature point
-//      in registers;
-//   3. element vectors are summed into the patch with shared-memory atomics
-//      and the patch is added to the global array with one atomic per unique
-//      node and component (or a plain read-add-write in colour passes, where no
-//      two elements of a launch share a node).
+// Work decomposition: one thread per element, one warp per tile of 32
+// elements, warps independent of each other (persistent, grid-striding over
+// tiles). Per warp:
+//   - the reference data of one quadrature point of one tile (h_i rows and
+//     w_q J_p, a contiguous "slice" of the slab [tile][q][3 npe + 1][32]) is
+//     streamed by cp.async.bulk into a ring of NSLICE shared-memory slots,
+//     issued NSLICE slices ahead by lane 0 and completed on one mbarrier per
+//     slot;
+//   - the nodal values of the tile's unique nodes (a sorted list built at mesh
+//     creation) are gathered into a shared-memory patch with consecutive lanes
+//     on consecutive node ids; each lane then reads its element's nodes from
+//     the patch through precomputed local indices;
+//   - each lane evaluates F = I + sum_i u_i h_i^T per quadrature point and the
+//     stress, its directional derivative, its adjoint or the diagonal moduli,
+//     accumulating its element vector sum_q w_q J_p (.) h_iq in registers;
+//   - element vectors are summed into an output patch with shared-memory
+//     atomics, and the patch is added to the global array with one atomic per
+//     unique node and component (a plain read-add-write in colour passes,
+//     where no two elements of a launch share a node).
+// Every mbarrier wait is bounded; on timeout the kernel latches ST_TIMEOUT in
+// the status word, drains its own copies (again bounded) and returns.
 #pragma once
+
+#include <string>
 
 #include "tlfe_elem.cuh"
 #include "tlfe_internal.h"
 
 namespace tlfe {
 
-template <typename R> __device__ __forceinline__ R ld_stream(const R *p) { return __ldcs(p); }
+// ---------------------------------------------------------------------------
+// PTX helpers: mbarrier, bulk async copy, cp.async
+// ---------------------------------------------------------------------------
 
-template <typename R> __device__ __forceinline__ void atomic_add_global(R *p, R v) { atomicAdd(p, v); }
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bulk copy global -> shared, completion counted in bytes on `bar`
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+template <int BYTES> __device__ __forceinline__ void cp_async(void *dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_u32(dst)), "l"(src), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+constexpr long long MBAR_SPIN_LIMIT = 1ll << 20;  // try_wait rounds before giving up
+
+// ---------------------------------------------------------------------------
+// per-op sizes
+// ---------------------------------------------------------------------------
 
 template <int OP> struct OpFields {
-    static constexpr int IN = op_in_fields(OP);
-    static constexpr int NF = op_nf(OP);
+    static constexpr int IN = op_in_fields(OP);   // input values per node (u, udot [, v])
+    static constexpr int OUT = op_nf(OP) - IN;    // output values per node
+    static constexpr int NFI = IN / 3;            // input vector fields per node
+    static constexpr int NFO = OUT / 3;           // output vector fields per node
+    static constexpr int REC = 4 * NFI;           // patch record (values) of one node: 16-byte aligned vectors
+    static constexpr int RECO = 4 * NFO;
 };
 
+constexpr int NSLICE = 2;  // ring depth per warp (quadrature-point slices)
+
+template <int ET, typename R> struct Slice {
+    static constexpr int NPE = Elem<ET>::NPE;
+    static constexpr int ROWS = NPE * 3 + 1;
+    static constexpr uint32_t BYTES = ROWS * 32 * sizeof(R);  // multiple of 128
+};
+
+// shared memory of one warp: slice ring, two metadata buffers, and a work area
+// holding first the node patch [umax][REC] and later the element-vector slots
+// [NFO][npe * 32][3]; rounded up to 128 bytes so that every bulk-copy
+// destination stays 16-byte aligned
+template <int ET, typename R, int OP>
+__host__ __device__ constexpr size_t warp_region_bytes(int umax, int meta_bytes)
+{
+    const size_t patch = (size_t)umax * OpFields<OP>::REC * sizeof(R);
+    const size_t slots = (size_t)OpFields<OP>::NFO * Elem<ET>::NPE * 32 * 3 * sizeof(R);
+    return ((size_t)NSLICE * Slice<ET, R>::BYTES + 2 * (size_t)meta_bytes + (patch > slots ? patch : slots) + 127) /
+           128 * 128;
+}
+
+// dynamic shared memory of one CTA with `wpb` warps (mbarriers, then the warp regions)
+template <int ET, typename R, int OP>
+__host__ __device__ constexpr size_t elem_smem_bytes(int umax, int meta_bytes, int wpb)
+{
+    return 128 + (size_t)wpb * warp_region_bytes<ET, R, OP>(umax, meta_bytes);
+}
+
+// 3-vectors in 16-byte-aligned shared records
+__device__ __forceinline__ void ld3(const float *p, float &x, float &y, float &z)
+{
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    x = v.x;
+    y = v.y;
+    z = v.z;
+}
+__device__ __forceinline__ void ld3(const double *p, double &x, double &y, double &z)
+{
+    const double2 v = *reinterpret_cast<const double2 *>(p);
+    x = v.x;
+    y = v.y;
+    z = p[2];
+}
+__device__ __forceinline__ void st3(float *p, float x, float y, float z)
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(x, y, z, 0.f);
+}
+__device__ __forceinline__ void st3(double *p, double x, double y, double z)
+{
+    *reinterpret_cast<double2 *>(p) = make_double2(x, y);
+    p[2] = z;
+    p[3] = 0.0;
+}
+
+// bounded wait on an mbarrier phase; returns false when the limit ran out
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+{
+    long long spins = 0;
+    while (!mbar_try_wait(bar, parity))
+        if (++spins > MBAR_SPIN_LIMIT) return false;
+    return true;
+}
+
 template <int ET, int NQ, typename R, int OP>
-__global__ void __launch_bounds__(128) k_elem(const KParams<R> p)
+__global__ void __launch_bounds__(128, sizeof(R) == 4 ? (OP == OP_FORCE ? 4 : 3) : 1) k_elem(const KParams<R> p)
 {
     constexpr int NPE = Elem<ET>::NPE;
-    constexpr int NF = OpFields<OP>::NF;
-    constexpr int IN = OpFields<OP>::IN;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int REC = OpFields<OP>::REC;
+    constexpr int NFO = OpFields<OP>::NFO;
+    constexpr bool HAS_V = OpFields<OP>::NFI == 3;
+    using SL = Slice<ET, R>;
+    constexpr int ROWS = SL::ROWS;
+
+    extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
     const int umax = p.umax;
-    R *sw = reinterpret_cast<R *>(smem_raw) + (size_t)wib * umax * NF;
-    R *sU = sw;
-    R *sUd = sw + 3 * umax;
-    R *sV = sw + 6 * umax;
-    R *sO0 = sw + IN * umax;
-    R *sO1 = sO0 + 3 * umax;
+    const int MB = p.meta_bytes;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem) + wib * (NSLICE + 2);  // [wpb][NSLICE + 2] (<= 128 B)
+    uint64_t *mbar = bar + NSLICE;
+    unsigned char *wbase = smem + 128 + (size_t)wib * warp_region_bytes<ET, R, OP>(umax, MB);
+    unsigned char *ring = wbase;
+    unsigned char *mbuf = wbase + NSLICE * SL::BYTES;          // [2][MB]
+    R *work = reinterpret_cast<R *>(mbuf + 2 * (size_t)MB);     // patch [umax][REC], later slots
+
+    const int gw = blockIdx.x * wpb + wib;
+    const int W = gridDim.x * wpb;
+    const int t0 = p.tile_begin + gw;
+    const int n_my = t0 < p.tile_end ? (p.tile_end - t0 + W - 1) / W : 0;
+    const int n_slices = n_my * NQ;
     const bool need_ud = p.visc != 0;
 
-    for (int t = p.tile_begin + blockIdx.x * wpb + wib; t < p.tile_end; t += gridDim.x * wpb) {
-        const int nb = p.tnode_off[t];
-        const int U = p.tnode_off[t + 1] - nb;
-        // ---- 1. gather the tile's nodal values into the patch
-        for (int k = lane; k < U; k += 32) {
-            const int64_t n = p.tnodes[nb + k];
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                sU[3 * k + d] = __ldg(p.u + 3 * n + d);
-                if (need_ud) sUd[3 * k + d] = __ldg(p.ud + 3 * n + d);
-                if (OP == OP_MATVEC || OP == OP_VJP) sV[3 * k + d] = __ldg(p.v + 3 * n + d);
-                sO0[3 * k + d] = R(0);
-                if (OP == OP_VJP) sO1[3 * k + d] = R(0);
-            }
-        }
-        __syncwarp();
+    if (lane == 0) {
+        for (int b = 0; b < NSLICE + 2; ++b) mbar_init(bar + b, 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
 
-        // ---- 2. element computation, one element per lane
-        const int e = p.eid[t * 32 + lane];
-        const bool valid = e >= 0;
+    auto issue = [&](int j) {  // slab slice j of this warp into ring slot j % NSLICE
+        const int t = t0 + (j / NQ) * W;
+        const int q = j % NQ;
+        const int b = j % NSLICE;
+        mbar_arrive_expect_tx(bar + b, SL::BYTES);
+        bulk_g2s(ring + (size_t)b * SL::BYTES, p.slab + ((size_t)t * NQ + q) * ROWS * 32, SL::BYTES, bar + b);
+    };
+    auto issue_meta = [&](int k) {  // metadata of the warp's k-th tile into buffer k & 1
+        const int t = t0 + k * W;
+        mbar_arrive_expect_tx(mbar + (k & 1), (uint32_t)MB);
+        bulk_g2s(mbuf + (size_t)(k & 1) * MB, p.meta + (size_t)t * MB, (uint32_t)MB, mbar + (k & 1));
+    };
+    if (lane == 0) {
+        if (n_my > 0) issue_meta(0);
+        for (int j = 0; j < NSLICE && j < n_slices; ++j) issue(j);
+    }
+
+    bool timed_out = false;
+    for (int k = 0; k < n_my; ++k) {
+        const int t = t0 + k * W;
+        // ---- metadata of this tile (prefetched one tile ahead)
+        if (!mbar_wait_bounded(mbar + (k & 1), (uint32_t)((k >> 1) & 1))) timed_out = true;
+        if (__any_sync(0xffffffffu, timed_out)) {
+            timed_out = true;
+            break;
+        }
+        if (lane == 0 && k + 1 < n_my) issue_meta(k + 1);
+        const unsigned char *M = mbuf + (size_t)(k & 1) * MB;
+        const int U = *reinterpret_cast<const int32_t *>(M);
+        const int e = reinterpret_cast<const int32_t *>(M + 16)[lane];
+        const int32_t *nodes = reinterpret_cast<const int32_t *>(M + 16 + 128);
+        const uint16_t *mlidx = reinterpret_cast<const uint16_t *>(M + 16 + 128 + 4 * p.umaxp);
+        const uint16_t *nsl = mlidx + NPE * 32;
+        const uint16_t *soff = nsl + NPE * 32;
+
+        // ---- gather the tile's nodal inputs into the patch (one record per unique node)
+        for (int kk = lane; kk < U; kk += 32) {
+            const int64_t n = nodes[kk];
+            R *rec = work + (size_t)kk * REC;
+            st3(rec, __ldg(p.u + 3 * n), __ldg(p.u + 3 * n + 1), __ldg(p.u + 3 * n + 2));
+            if (need_ud) st3(rec + 4, __ldg(p.ud + 3 * n), __ldg(p.ud + 3 * n + 1), __ldg(p.ud + 3 * n + 2));
+            if (HAS_V) st3(rec + 8, __ldg(p.v + 3 * n), __ldg(p.v + 3 * n + 1), __ldg(p.v + 3 * n + 2));
+        }
         int li[NPE];
 #pragma unroll
-        for (int i = 0; i < NPE; ++i) li[i] = p.lidx[((size_t)t * NPE + i) * 32 + lane];
+        for (int i = 0; i < NPE; ++i) li[i] = mlidx[i * 32 + lane];
+        const bool valid = e >= 0;
         Mat<R> m = p.mat0;
-        if (p.mats) m = p.mats[p.emat[t * 32 + lane]];
+        if (p.mats) m = p.mats[p.emat[(size_t)t * 32 + lane]];
         if (p.elam) {
-            m.mu = p.elam[(size_t)(t * 2 + 0) * 32 + lane];
-            m.lam = p.elam[(size_t)(t * 2 + 1) * 32 + lane];
+            m.mu = p.elam[((size_t)t * 2 + 0) * 32 + lane];
+            m.lam = p.elam[((size_t)t * 2 + 1) * 32 + lane];
         }
         const bool visc = need_ud && (m.mu_v != R(0) || m.lam_v != R(0));
+        __syncwarp();
 
-        R ue[NPE][3], ve[NPE][3], acc0[NPE][3], acc1[NPE][3];
+        R acc0[NPE][3], acc1[NPE][3];
 #pragma unroll
         for (int i = 0; i < NPE; ++i)
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                ue[i][d] = sU[3 * li[i] + d];
-                if (OP == OP_MATVEC || OP == OP_VJP) ve[i][d] = sV[3 * li[i] + d];
                 acc0[i][d] = R(0);
                 if (OP == OP_VJP) acc1[i][d] = R(0);
             }
-        R gmu_acc = R(0), glam_acc = R(0), vol = R(0);
+        R gmu_acc = R(0), glam_acc = R(0);
         int bad = 0;
 
 #pragma unroll 1
         for (int q = 0; q < NQ; ++q) {
-            R h[NPE][3];
-            const R *Hq = p.H + ((size_t)t * NQ + q) * NPE * 3 * 32 + lane;
-#pragma unroll
-            for (int i = 0; i < NPE; ++i)
-#pragma unroll
-                for (int d = 0; d < 3; ++d) h[i][d] = ld_stream(Hq + (i * 3 + d) * 32);
-            const R w = ld_stream(p.wJ + ((size_t)t * NQ + q) * 32 + lane);
-            vol += w;
+            const int j = k * NQ + q;
+            const int b = j % NSLICE;
+            if (!mbar_wait_bounded(bar + b, (uint32_t)((j / NSLICE) & 1))) timed_out = true;
+            if (__any_sync(0xffffffffu, timed_out)) {
+                timed_out = true;
+                break;
+            }
+            const R *sl = reinterpret_cast<const R *>(ring + (size_t)b * SL::BYTES) + lane;
+            const R w = sl[NPE * 3 * 32];
 
-            QP<R> s;
+            // kinematics: G = sum u_i h_i^T, Fd = sum udot_i h_i^T, D = sum v_i h_i^T
+            QP<R> s1;
+            R D[9];
 #pragma unroll
-            for (int a = 0; a < 3; ++a)
+            for (int k2 = 0; k2 < 9; ++k2) {
+                s1.G[k2] = R(0);
+                s1.Fd[k2] = R(0);
+                D[k2] = R(0);
+            }
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    R g = R(0);
+            for (int i = 0; i < NPE; ++i) {
+                const R h0 = sl[(i * 3 + 0) * 32], h1 = sl[(i * 3 + 1) * 32], h2 = sl[(i * 3 + 2) * 32];
+                const R *rec = work + li[i] * REC;
+                R x[3];
+                ld3(rec, x[0], x[1], x[2]);
 #pragma unroll
-                    for (int i = 0; i < NPE; ++i) g += ue[i][a] * h[i][c];
-                    s.G[a * 3 + c] = g;
+                for (int a = 0; a < 3; ++a) {
+                    s1.G[a * 3 + 0] += x[a] * h0;
+                    s1.G[a * 3 + 1] += x[a] * h1;
+                    s1.G[a * 3 + 2] += x[a] * h2;
                 }
-            if (visc) {
+                if (visc) {
+                    ld3(rec + 4, x[0], x[1], x[2]);
 #pragma unroll
-                for (int a = 0; a < 3; ++a)
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        R g = R(0);
-#pragma unroll
-                        for (int i = 0; i < NPE; ++i) g += sUd[3 * li[i] + a] * h[i][c];
-                        s.Fd[a * 3 + c] = g;
+                    for (int a = 0; a < 3; ++a) {
+                        s1.Fd[a * 3 + 0] += x[a] * h0;
+                        s1.Fd[a * 3 + 1] += x[a] * h1;
+                        s1.Fd[a * 3 + 2] += x[a] * h2;
                     }
-            } else {
+                }
+                if (HAS_V) {
+                    ld3(rec + 8, x[0], x[1], x[2]);
 #pragma unroll
-                for (int k = 0; k < 9; ++k) s.Fd[k] = R(0);
+                    for (int a = 0; a < 3; ++a) {
+                        D[a * 3 + 0] += x[a] * h0;
+                        D[a * 3 + 1] += x[a] * h1;
+                        D[a * 3 + 2] += x[a] * h2;
+                    }
+                }
             }
             R P[9];
-            stress<R>(m, s, visc, P);
-            bad += s.ok ? 0 : 1;
+            stress<R>(m, s1, visc, P);
+            bad += (valid && !s1.ok) ? 1 : 0;
 
-            if (OP == OP_FORCE) {
-#pragma unroll
-                for (int k = 0; k < 9; ++k) P[k] *= w;
-#pragma unroll
-                for (int i = 0; i < NPE; ++i)
-#pragma unroll
-                    for (int a = 0; a < 3; ++a)
-                        acc0[i][a] += P[a * 3] * h[i][0] + P[a * 3 + 1] * h[i][1] + P[a * 3 + 2] * h[i][2];
-            } else if (OP == OP_MATVEC || OP == OP_VJP) {
-                R D[9];
-#pragma unroll
-                for (int a = 0; a < 3; ++a)
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        R g = R(0);
-#pragma unroll
-                        for (int i = 0; i < NPE; ++i) g += ve[i][a] * h[i][c];
-                        D[a * 3 + c] = g;
-                    }
-                if (OP == OP_MATVEC) {
-                    R dP[9];
-                    dstress<R>(m, s, visc, D, p.aK, p.aC, p.sym_only != 0, dP);
-#pragma unroll
-                    for (int k = 0; k < 9; ++k) dP[k] *= w;
-#pragma unroll
-                    for (int i = 0; i < NPE; ++i)
-#pragma unroll
-                        for (int a = 0; a < 3; ++a)
-                            acc0[i][a] += dP[a * 3] * h[i][0] + dP[a * 3 + 1] * h[i][1] + dP[a * 3 + 2] * h[i][2];
-                } else {
-                    R gF[9], gFd[9], gmu, glam;
-                    astress<R>(m, s, visc, D, gF, gFd, gmu, glam);
-                    gmu_acc += w * gmu;
-                    glam_acc += w * glam;
-#pragma unroll
-                    for (int k = 0; k < 9; ++k) {
-                        gF[k] *= w;
-                        gFd[k] *= w;
-                    }
-#pragma unroll
-                    for (int i = 0; i < NPE; ++i)
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) {
-                            acc0[i][a] += gF[a * 3] * h[i][0] + gF[a * 3 + 1] * h[i][1] + gF[a * 3 + 2] * h[i][2];
-                            acc1[i][a] += gFd[a * 3] * h[i][0] + gFd[a * 3 + 1] * h[i][1] + gFd[a * 3 + 2] * h[i][2];
-                        }
-                }
-            } else {  // OP_DIAG: diagonal of the symmetric operator a_K K^e + a_C C
+            if (OP == OP_DIAG) {
+                // diagonal of a_K K^e + a_C C: A_d[c][b] = dP_{d b} / dF_{d c}
 #pragma unroll
                 for (int d = 0; d < 3; ++d) {
-                    R A[3][3];  // A[c][b] = dP_{d b} / dF_{d c}
+                    R A[9];
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
                         R E[9], dP[9];
 #pragma unroll
-                        for (int k = 0; k < 9; ++k) E[k] = (k == d * 3 + c) ? R(1) : R(0);
-                        dstress<R>(m, s, visc, E, p.aK, p.aC, true, dP);
+                        for (int k2 = 0; k2 < 9; ++k2) E[k2] = (k2 == d * 3 + c) ? R(1) : R(0);
+                        dstress<R>(m, s1, visc, E, p.aK, p.aC, true, dP);
 #pragma unroll
-                        for (int b = 0; b < 3; ++b) A[c][b] = dP[d * 3 + b];
+                        for (int b2 = 0; b2 < 3; ++b2) A[c * 3 + b2] = w * dP[d * 3 + b2];
                     }
 #pragma unroll
                     for (int i = 0; i < NPE; ++i) {
-                        R t2 = R(0);
+                        const R h0 = sl[(i * 3 + 0) * 32], h1 = sl[(i * 3 + 1) * 32], h2 = sl[(i * 3 + 2) * 32];
+                        acc0[i][d] += h0 * (A[0] * h0 + A[1] * h1 + A[2] * h2) +
+                                      h1 * (A[3] * h0 + A[4] * h1 + A[5] * h2) +
+                                      h2 * (A[6] * h0 + A[7] * h1 + A[8] * h2);
+                    }
+                }
+            } else {
+                R T0[9], T1[9];  // element-vector operators of this point, scaled by w
+                if (OP == OP_FORCE) {
 #pragma unroll
-                        for (int c = 0; c < 3; ++c)
-                            t2 += h[i][c] * (A[c][0] * h[i][0] + A[c][1] * h[i][1] + A[c][2] * h[i][2]);
-                        acc0[i][d] += w * t2;
+                    for (int k2 = 0; k2 < 9; ++k2) T0[k2] = w * P[k2];
+                } else if (OP == OP_MATVEC) {
+                    dstress<R>(m, s1, visc, D, p.aK, p.aC, p.sym_only != 0, T0);
+#pragma unroll
+                    for (int k2 = 0; k2 < 9; ++k2) T0[k2] *= w;
+                } else {
+                    R gmu, glam;
+                    astress<R>(m, s1, visc, D, T0, T1, gmu, glam);
+                    gmu_acc += w * gmu;
+                    glam_acc += w * glam;
+#pragma unroll
+                    for (int k2 = 0; k2 < 9; ++k2) {
+                        T0[k2] *= w;
+                        T1[k2] *= w;
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < NPE; ++i) {
+                    const R h0 = sl[(i * 3 + 0) * 32], h1 = sl[(i * 3 + 1) * 32], h2 = sl[(i * 3 + 2) * 32];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        acc0[i][a] += T0[a * 3] * h0 + T0[a * 3 + 1] * h1 + T0[a * 3 + 2] * h2;
+                        if (OP == OP_VJP) acc1[i][a] += T1[a * 3] * h0 + T1[a * 3 + 1] * h1 + T1[a * 3 + 2] * h2;
                     }
                 }
             }
+            // slot b is no longer read: hand it to the slice NSLICE ahead
+            __syncwarp();
+            if (lane == 0 && j + NSLICE < n_slices) {
+                fence_proxy_async();
+                issue(j + NSLICE);
+            }
         }
+        if (timed_out) break;
 
         // consistent mass of affine elements: m_ij = rho V Mhat_ij (Sec. 4.1)
         if ((OP == OP_MATVEC || OP == OP_DIAG) && p.aM != R(0)) {
-            const R c = p.aM * m.rho * p.evol[t * 32 + lane];
+            const R c = p.aM * m.rho * p.evol[(size_t)t * 32 + lane];
+            if (OP == OP_MATVEC) {
 #pragma unroll
-            for (int i = 0; i < NPE; ++i) {
-                if (OP == OP_MATVEC) {
-                    R sx = R(0), sy = R(0), sz = R(0);
+                for (int jn = 0; jn < NPE; ++jn) {
+                    R x[3];
+                    ld3(work + li[jn] * REC + 8, x[0], x[1], x[2]);
 #pragma unroll
-                    for (int j = 0; j < NPE; ++j) {
-                        const R mh = R(mass_hat(ET, i, j));
-                        sx += mh * ve[j][0];
-                        sy += mh * ve[j][1];
-                        sz += mh * ve[j][2];
+                    for (int i = 0; i < NPE; ++i) {
+                        const R mh = c * R(mass_hat(ET, i, jn));
+                        acc0[i][0] += mh * x[0];
+                        acc0[i][1] += mh * x[1];
+                        acc0[i][2] += mh * x[2];
                     }
-                    acc0[i][0] += c * sx;
-                    acc0[i][1] += c * sy;
-                    acc0[i][2] += c * sz;
-                } else {
-                    const R mh = R(mass_hat(ET, i, i));
-                    acc0[i][0] += c * mh;
-                    acc0[i][1] += c * mh;
-                    acc0[i][2] += c * mh;
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < NPE; ++i) {
+                    const R mh = c * R(mass_hat(ET, i, i));
+                    acc0[i][0] += mh;
+                    acc0[i][1] += mh;
+                    acc0[i][2] += mh;
                 }
             }
         }
-        (void)vol;
+        if (OP == OP_VJP && valid && p.gth) {
+            p.gth[(size_t)e * 2 + 0] = double(gmu_acc);
+            p.gth[(size_t)e * 2 + 1] = double(glam_acc);
+        }
+        const int nbad = __reduce_add_sync(0xffffffffu, bad);
+        if (lane == 0 && nbad) atomicAdd(p.status + ST_INVERTED, nbad);
 
+        // ---- element vectors into slots [field][i * 32 + lane][3] (the patch is dead now)
+        __syncwarp();
         if (valid) {
 #pragma unroll
             for (int i = 0; i < NPE; ++i)
 #pragma unroll
                 for (int d = 0; d < 3; ++d) {
-                    atomicAdd(sO0 + 3 * li[i] + d, acc0[i][d]);
-                    if (OP == OP_VJP) atomicAdd(sO1 + 3 * li[i] + d, acc1[i][d]);
+                    work[(i * 32 + lane) * 3 + d] = acc0[i][d];
+                    if (NFO == 2) work[(NPE * 32 + i * 32 + lane) * 3 + d] = acc1[i][d];
                 }
-            if (OP == OP_VJP && p.gth) {
-                p.gth[(size_t)e * 2 + 0] = double(gmu_acc);
-                p.gth[(size_t)e * 2 + 1] = double(glam_acc);
-            }
-        }
-        if (!valid) bad = 0;
-        const int nbad = __reduce_add_sync(0xffffffffu, bad);
-        if (lane == 0 && nbad) atomicAdd(p.status + ST_INVERTED, nbad);
-        __syncwarp();
-
-        // ---- 3. add the patch into the global arrays
-        for (int k = lane; k < U; k += 32) {
-            const int64_t n = p.tnodes[nb + k];
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                if (p.rmw_scatter) {
-                    p.out0[3 * n + d] += sO0[3 * k + d];
-                    if (OP == OP_VJP && p.out1) p.out1[3 * n + d] += sO1[3 * k + d];
-                } else {
-                    atomic_add_global(p.out0 + 3 * n + d, sO0[3 * k + d]);
-                    if (OP == OP_VJP && p.out1) atomic_add_global(p.out1 + 3 * n + d, sO1[3 * k + d]);
-                }
-            }
         }
         __syncwarp();
+        // ---- one lane per unique node sums its slots and adds them to the global arrays
+        for (int kk = lane; kk < U; kk += 32) {
+            const int64_t n = nodes[kk];
+            const int s0 = soff[kk], s1e = soff[kk + 1];
+            R a0 = R(0), a1 = R(0), a2 = R(0), b0 = R(0), b1 = R(0), b2 = R(0);
+            for (int sidx = s0; sidx < s1e; ++sidx) {
+                const int sl2 = nsl[sidx];
+                a0 += work[sl2 * 3 + 0];
+                a1 += work[sl2 * 3 + 1];
+                a2 += work[sl2 * 3 + 2];
+                if (NFO == 2) {
+                    b0 += work[(NPE * 32 + sl2) * 3 + 0];
+                    b1 += work[(NPE * 32 + sl2) * 3 + 1];
+                    b2 += work[(NPE * 32 + sl2) * 3 + 2];
+                }
+            }
+            if (p.rmw_scatter) {
+                p.out0[3 * n] += a0;
+                p.out0[3 * n + 1] += a1;
+                p.out0[3 * n + 2] += a2;
+                if (NFO == 2) {
+                    p.out1[3 * n] += b0;
+                    p.out1[3 * n + 1] += b1;
+                    p.out1[3 * n + 2] += b2;
+                }
+            } else {
+                atomicAdd(p.out0 + 3 * n, a0);
+                atomicAdd(p.out0 + 3 * n + 1, a1);
+                atomicAdd(p.out0 + 3 * n + 2, a2);
+                if (NFO == 2) {
+                    atomicAdd(p.out1 + 3 * n, b0);
+                    atomicAdd(p.out1 + 3 * n + 1, b1);
+                    atomicAdd(p.out1 + 3 * n + 2, b2);
+                }
+            }
+        }
+        __syncwarp();
+    }
+    if (timed_out) {
+        // a copy never landed: record it and wait (bounded) for this warp's
+        // outstanding copies before leaving
+        if (lane == 0) atomicAdd(p.status + ST_TIMEOUT, 1);
+        for (int b = 0; b < NSLICE + 2; ++b) {
+            long long spins = 0;
+            while (!mbar_try_wait(bar + b, 0) && !mbar_try_wait(bar + b, 1) && ++spins < MBAR_SPIN_LIMIT) {
+            }
+        }
     }
 }
 
@@ -279,34 +483,55 @@ template <int OP, typename R> static void (*kernel_for(int et, int nq))(const KP
     return nullptr;
 }
 
-template <int OP, typename R> size_t smem_bytes(const KParams<R> &p)
+
+template <int OP, typename R> size_t smem_for(int et, int umax, int meta_bytes, int wpb)
 {
-    return (size_t)4 * p.umax * OpFields<OP>::NF * sizeof(R);
+    if (et == ET_T4) return elem_smem_bytes<ET_T4, R, OP>(umax, meta_bytes, wpb);
+    if (et == ET_T10) return elem_smem_bytes<ET_T10, R, OP>(umax, meta_bytes, wpb);
+    if (et == ET_H8) return elem_smem_bytes<ET_H8, R, OP>(umax, meta_bytes, wpb);
+    return 0;
 }
 
-template <int OP, typename R> int occupancy_op(int et, int nq, size_t smem)
+// resident warps per SM for the best CTA size among 4, 2 and 1 warps
+template <int OP, typename R> int occupancy_op(int et, int nq, int umax, int meta_bytes, int *wpb_out, std::string *why)
 {
     void (*kern)(const KParams<R>) = kernel_for<OP, R>(et, nq);
-    if (!kern) return 0;
-    if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    *wpb_out = 0;
+    if (!kern) {
+        *why = "no kernel for this element type and quadrature size";
         return 0;
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, 128, smem) != cudaSuccess) return 0;
-    return nb;
+    }
+    int best = 0;
+    for (int wpb : {4, 2, 1}) {
+        const size_t smem = smem_for<OP, R>(et, umax, meta_bytes, wpb);
+        if (smem > 227 * 1024) continue;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int nb = 0;
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, 32 * wpb, smem);
+        if (e != cudaSuccess) {
+            *why = std::string("occupancy query failed: ") + cudaGetErrorString(e);
+            return 0;
+        }
+        if (nb * wpb > best) {
+            best = nb * wpb;
+            *wpb_out = wpb;
+        }
+    }
+    if (best == 0)
+        *why = "shared memory per warp too large (patch of " + std::to_string(umax) + " nodes, metadata " +
+               std::to_string(meta_bytes) + " B)";
+    return best;
 }
 
 template <int OP, typename R>
-cudaError_t launch_op(int et, int nq, const KParams<R> &p, int grid, cudaStream_t s)
+cudaError_t launch_op(int et, int nq, const KParams<R> &p, int grid, int wpb, cudaStream_t s)
 {
     void (*kern)(const KParams<R>) = kernel_for<OP, R>(et, nq);
     if (!kern) return cudaErrorInvalidValue;
-    const size_t smem = smem_bytes<OP, R>(p);
-    if (smem > 48 * 1024) {
-        cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (err != cudaSuccess) return err;
-    }
-    kern<<<grid, 128, smem, s>>>(p);
+    const size_t smem = smem_for<OP, R>(et, p.umax, p.meta_bytes, wpb);
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    kern<<<grid, 32 * wpb, smem, s>>>(p);
     return cudaGetLastError();
 }
 

@@ -2,8 +2,8 @@
 #include "k_elem.cuh"
 
 namespace tlfe {
-template cudaError_t launch_op<OP_FORCE, float>(int, int, const KParams<float> &, int, cudaStream_t);
-template cudaError_t launch_op<OP_FORCE, double>(int, int, const KParams<double> &, int, cudaStream_t);
-template int occupancy_op<OP_FORCE, float>(int, int, size_t);
-template int occupancy_op<OP_FORCE, double>(int, int, size_t);
+template cudaError_t launch_op<OP_FORCE, float>(int, int, const KParams<float> &, int, int, cudaStream_t);
+template cudaError_t launch_op<OP_FORCE, double>(int, int, const KParams<double> &, int, int, cudaStream_t);
+template int occupancy_op<OP_FORCE, float>(int, int, int, int, int *, std::string *);
+template int occupancy_op<OP_FORCE, double>(int, int, int, int, int *, std::string *);
 }  // namespace tlfe

@@ -8,14 +8,16 @@ namespace tlfe {
 // One thread per (tile, lane): for each quadrature point,
 //   Jp = U Hp(xi_q)  (U = [X_1 .. X_n]),  h_i^T = dS_i/dxi Jp^{-1},
 //   wJ = w_q det(Jp)                               (Sec. 6, H = Hp (U Hp)^{-1}, J_p)
-// in FP64, stored in the AoSoA layout [tile][q][node][dim][lane] in the mesh
-// precision. Also records the element volume sum_q wJ and whether the element
-// is affine (straight edges / parallelepiped), which the consistent-mass
-// shortcut m_ij = rho V Mhat_ij needs.
+// in FP64, stored in the mesh precision as the slab
+//   slab[tile][q][r][lane], r = 3 i + c for (h_i)_c and r = 3 npe for wJ,
+// so that one quadrature point of one tile is a contiguous slice. Also
+// records the element volume sum_q wJ and whether the element is affine
+// (straight edges / parallelepiped), which the consistent-mass shortcut
+// m_ij = rho V Mhat_ij needs.
 template <typename R>
 __global__ void k_precompute(int et, int nq, int npe, int n_tiles, const int32_t *__restrict__ eid,
                              const int32_t *__restrict__ conn, int elem_base,
-                             const double *__restrict__ X, R *__restrict__ H, R *__restrict__ wJ,
+                             const double *__restrict__ X, R *__restrict__ slab,
                              R *__restrict__ evol, int *affine_flag, int *status)
 {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -23,11 +25,10 @@ __global__ void k_precompute(int et, int nq, int npe, int n_tiles, const int32_t
     const int64_t t = idx >> 5;
     const int lane = (int)(idx & 31);
     const int e = eid[idx];
+    const int rows = npe * 3 + 1;
     if (e < 0) {
-        for (int q = 0; q < nq; ++q) {
-            for (int k = 0; k < npe * 3; ++k) H[((t * nq + q) * npe * 3 + k) * 32 + lane] = R(0);
-            wJ[(t * nq + q) * 32 + lane] = R(0);
-        }
+        for (int q = 0; q < nq; ++q)
+            for (int k = 0; k < rows; ++k) slab[((t * nq + q) * rows + k) * 32 + lane] = R(0);
         evol[idx] = R(0);
         return;
     }
@@ -72,10 +73,10 @@ __global__ void k_precompute(int et, int nq, int npe, int n_tiles, const int32_t
             for (int c = 0; c < 3; ++c) {
                 double s = 0.0;
                 for (int k = 0; k < 3; ++k) s += g[i * 3 + k] * Ji[k * 3 + c];
-                H[((t * nq + q) * npe * 3 + i * 3 + c) * 32 + lane] = ok ? R(s) : R(0);
+                slab[((t * nq + q) * rows + i * 3 + c) * 32 + lane] = ok ? R(s) : R(0);
             }
         const double wj = ok ? w * det : 0.0;
-        wJ[(t * nq + q) * 32 + lane] = R(wj);
+        slab[((t * nq + q) * rows + npe * 3) * 32 + lane] = R(wj);
         vol += wj;
     }
     evol[idx] = R(vol);
@@ -107,8 +108,8 @@ __global__ void k_precompute(int et, int nq, int npe, int n_tiles, const int32_t
 }
 
 cudaError_t launch_precompute(int et, int nq, int precision, int n_tiles, const int32_t *eid,
-                              const int32_t *conn_elem, int elem_base, const double *X, void *H,
-                              void *wJ, void *evol, int *affine_flag, int *status, cudaStream_t s)
+                              const int32_t *conn_elem, int elem_base, const double *X, void *slab,
+                              void *evol, int *affine_flag, int *status, cudaStream_t s)
 {
     const int npe = nodes_per_elem(et);
     const int64_t n = (int64_t)n_tiles * 32;
@@ -117,11 +118,10 @@ cudaError_t launch_precompute(int et, int nq, int precision, int n_tiles, const 
     if (grid == 0) return cudaSuccess;
     if (precision == TLFE_FP32)
         k_precompute<float><<<grid, tpb, 0, s>>>(et, nq, npe, n_tiles, eid, conn_elem, elem_base, X,
-                                                 (float *)H, (float *)wJ, (float *)evol, affine_flag, status);
+                                                 (float *)slab, (float *)evol, affine_flag, status);
     else
         k_precompute<double><<<grid, tpb, 0, s>>>(et, nq, npe, n_tiles, eid, conn_elem, elem_base, X,
-                                                  (double *)H, (double *)wJ, (double *)evol, affine_flag,
-                                                  status);
+                                                  (double *)slab, (double *)evol, affine_flag, status);
     return cudaGetLastError();
 }
 

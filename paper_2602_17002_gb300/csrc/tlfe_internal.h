@@ -5,9 +5,11 @@
 #include <stdint.h>
 
 #include <string>
+
+#include <string>
 #include <vector>
 
-#include "../../include/tlfe.h"
+#include "tlfe.h"
 #include "tlfe_math.cuh"
 
 namespace tlfe {
@@ -30,9 +32,14 @@ template <typename R> struct KParams {
     const int32_t *tnode_off;   // [n_tiles + 1] offsets into tnodes
     const int32_t *tnodes;      // sorted unique global node ids of each tile
     const uint16_t *lidx;       // [n_tiles][npe][32] index of (elem, node) into the tile's list
+    // per-tile metadata records of meta_bytes each (16-byte multiple):
+    //   int32 U, 3 x pad | int32 eid[32] | int32 node id[umaxp] | u16 lidx[npe][32] |
+    //   u16 slot list[npe * 32] (slots i * 32 + lane of each unique node, by node) |
+    //   u16 slot offsets[U + 1] (padded)
+    const unsigned char *meta;
+    int meta_bytes, umaxp;
     const int32_t *eid;         // [n_tiles][32] global element id, -1 for padding lanes
-    const R *H;                 // [n_tiles][nq][npe][3][32]
-    const R *wJ;                // [n_tiles][nq][32]
+    const R *slab;              // [n_tiles][nq][3 npe + 1][32]: h_i components, then w_q J_p
     const int32_t *emat;        // [n_tiles][32] material index, or nullptr (uniform mat0)
     const R *elam;              // [n_tiles][2][32] per-element (mu, lam), or nullptr
     const R *evol;              // [n_tiles][32] element volume (affine mass)
@@ -55,16 +62,18 @@ template <typename R> struct KParams {
 // Defined in k_elem.cuh and instantiated in k_force.cu / k_matvec.cu /
 // k_vjp.cu / k_diag.cu.
 template <int OP, typename R>
-cudaError_t launch_op(int et, int nq, const KParams<R> &p, int grid, cudaStream_t s);
+cudaError_t launch_op(int et, int nq, const KParams<R> &p, int grid, int wpb, cudaStream_t s);
 
-// CTAs per SM the kernel of (op, et, nq, precision) can keep resident with
-// `smem` bytes of dynamic shared memory each
-template <int OP, typename R> int occupancy_op(int et, int nq, size_t smem);
+// warps per SM the kernel of (op, et, nq, precision) can keep resident for a
+// block whose tiles hold at most `umax` unique nodes
+// (CTA sizes of 1, 2 and 4 warps are tried; *wpb receives the best one)
+template <int OP, typename R>
+int occupancy_op(int et, int nq, int umax, int meta_bytes, int *wpb, std::string *why);
 
 // set-up kernels
 cudaError_t launch_precompute(int et, int nq, int precision, int n_tiles, const int32_t *eid,
-                              const int32_t *conn_elem, int elem_base, const double *X, void *H,
-                              void *wJ, void *evol, int *affine_flag, int *status, cudaStream_t s);
+                              const int32_t *conn_elem, int elem_base, const double *X, void *slab,
+                              void *evol, int *affine_flag, int *status, cudaStream_t s);
 cudaError_t launch_color_round(int n_elem, int npe, const int32_t *conn, const int32_t *inc_off,
                                const int32_t *inc, const int32_t *elem_local_to_block,
                                uint64_t seed, int elem_base, int32_t *color, int *n_left,

@@ -121,7 +121,7 @@ template <typename R> struct QP {
     R Sv[9];   // viscous 2nd PK stress
     R Cf[9];   // NH: cof(F)
     R dev[9];  // NH: dev(b - I)
-    R Jm1, J, Jm53;
+    R Jm1, J, Jm53, rJ;  // J - 1, J, J^{-5/3}, 1/J
     bool ok;
 };
 
@@ -178,7 +178,8 @@ __device__ __forceinline__ void stress(const Mat<R> &m, QP<R> &q, bool visc, R P
         return;
     }
     // neo-Hookean: mu10 = mu/2, k = lam + 2 mu / 3
-    const R kb = m.lam + R(2) * m.mu / R(3);
+    const R third = R(1.0 / 3.0);
+    const R kb = m.lam + R(2) * third * m.mu;
     const R I2 = G[0] * G[4] + G[4] * G[8] + G[0] * G[8] - G[1] * G[3] - G[5] * G[7] - G[2] * G[6];
     const R dG = G[0] * (G[4] * G[8] - G[5] * G[7]) - G[1] * (G[3] * G[8] - G[5] * G[6]) +
                  G[2] * (G[3] * G[7] - G[4] * G[6]);
@@ -193,7 +194,9 @@ __device__ __forceinline__ void stress(const Mat<R> &m, QP<R> &q, bool visc, R P
     }
     const R r = rcbrt_<R>(q.J);
     const R r2 = r * r;
-    q.Jm53 = r2 * r2 * r;
+    const R r3 = r2 * r;  // 1/J
+    q.Jm53 = r3 * r2;
+    q.rJ = r3;
     // b - I = G + G^T + G G^T
     R bt = R(0);
 #pragma unroll
@@ -205,7 +208,7 @@ __device__ __forceinline__ void stress(const Mat<R> &m, QP<R> &q, bool visc, R P
             q.dev[a * 3 + b] = s;
             q.dev[b * 3 + a] = s;
         }
-    bt = tr3(q.dev) / R(3);
+    bt = tr3(q.dev) * third;
     q.dev[0] -= bt;
     q.dev[4] -= bt;
     q.dev[8] -= bt;
@@ -244,7 +247,8 @@ __device__ __forceinline__ void dstress(const Mat<R> &m, const QP<R> &q, bool vi
             mm3_acc(dF, q.S, dP);
             mm3_acc(q.F, dS, dP);
         } else if (q.ok) {
-            const R kb = m.lam + R(2) * m.mu / R(3);
+            const R third = R(1.0 / 3.0);
+            const R kb = m.lam + R(2) * third * m.mu;
             // dJ = cof(F) : dF
             R dJ = R(0);
 #pragma unroll
@@ -262,11 +266,11 @@ __device__ __forceinline__ void dstress(const Mat<R> &m, const QP<R> &q, bool vi
                     db[a * 3 + b] = s;
                     db[b * 3 + a] = s;
                 }
-            const R dbt = tr3(db) / R(3);
+            const R dbt = tr3(db) * third;
             db[0] -= dbt;
             db[4] -= dbt;
             db[8] -= dbt;
-            const R dJm53 = R(-5) / R(3) * q.Jm53 * dJ / q.J;
+            const R dJm53 = R(-5.0 / 3.0) * q.Jm53 * dJ * q.rJ;
             R dA[9];
 #pragma unroll
             for (int k = 0; k < 9; ++k) dA[k] = m.mu * (dJm53 * q.dev[k] + q.Jm53 * db[k]);
@@ -279,8 +283,7 @@ __device__ __forceinline__ void dstress(const Mat<R> &m, const QP<R> &q, bool vi
             mm3_acc(q.S, dC, dP);
         }
         if (visc && !sym_only) {
-            if (m.model == MODEL_NH) mm3_acc(dF, q.Sv, dP);  // SVK's q.S already excludes Sv: add below
-            else mm3_acc(dF, q.Sv, dP);
+            mm3_acc(dF, q.Sv, dP);  // q.S holds the elastic part only, for both laws
             // F dS^v with dEdot = sym(Fd^T dF)
             R dE[9], dS[9];
             symAtB(q.Fd, dF, dE);
@@ -363,9 +366,9 @@ __device__ __forceinline__ void astress(const Mat<R> &m, const QP<R> &q, bool vi
         R Bm[9];
 #pragma unroll
         for (int k = 0; k < 9; ++k) Bm[k] = q.Jm53 * q.dev[k];
-        Bm[0] += R(2) / R(3) * q.Jm1;
-        Bm[4] += R(2) / R(3) * q.Jm1;
-        Bm[8] += R(2) / R(3) * q.Jm1;
+        Bm[0] += R(2.0 / 3.0) * q.Jm1;
+        Bm[4] += R(2.0 / 3.0) * q.Jm1;
+        Bm[8] += R(2.0 / 3.0) * q.Jm1;
         R Pm[9];
         mm3(Bm, q.Cf, Pm);
 #pragma unroll

@@ -27,7 +27,9 @@ struct BlockStore {
     std::vector<int32_t> colors;     // colour of each block element (colour mode)
     int32_t *d_eid = nullptr, *d_toff = nullptr, *d_tnodes = nullptr, *d_emat = nullptr;
     uint16_t *d_lidx = nullptr;
-    void *d_H = nullptr, *d_wJ = nullptr, *d_evol = nullptr, *d_elam = nullptr;
+    unsigned char *d_meta = nullptr;  // per-tile metadata records
+    int meta_bytes = 0, meta_umaxp = 0;
+    void *d_slab = nullptr, *d_evol = nullptr, *d_elam = nullptr;
 };
 
 }  // namespace tlfe
@@ -49,7 +51,8 @@ struct tlfe_mesh {
     cudaGraphExec_t graph_exec = nullptr;
     tlfe::NewtonState *newton = nullptr;
     std::vector<void *> allocs;
-    std::map<std::tuple<int, int, int, int, size_t>, int> occ_cache;
+    std::map<std::tuple<int, int, int, int, size_t>, int> occ_cache;  // resident warps per SM
+    std::map<std::tuple<int, int, int, int, size_t>, int> occ_wpb;    // warps per CTA chosen
 
     int occupancy(int op, int et, int nq, int rsize, size_t smem, const std::function<int()> &query)
     {
