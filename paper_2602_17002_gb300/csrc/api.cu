@@ -385,6 +385,24 @@ extern "C" tlfe_status tlfe_create_mesh(const tlfe_mesh_desc *desc, void *stream
     m->n_bodies = desc->n_bodies;
     m->h_mats.assign(desc->body_mat, desc->body_mat + desc->n_bodies);
     m->blocks.resize(desc->n_blocks);
+    m->color_seed = desc->color_seed;
+    m->h_X.assign(desc->X_ref, desc->X_ref + 3 * (size_t)desc->n_nodes);
+    m->node_body.assign(desc->n_nodes, -1);
+    {
+        int64_t ne = 0;
+        for (int bi = 0; bi < desc->n_blocks; ++bi) {
+            const tlfe_block &b = desc->blocks[bi];
+            const int npe = nodes_per_elem(b.type);
+            m->h_conn.emplace_back(b.conn, b.conn + (size_t)b.n_elem * npe);
+            if (b.body) m->h_body.emplace_back(b.body, b.body + b.n_elem);
+            else m->h_body.emplace_back((size_t)b.n_elem, 0);
+            m->h_blocks.push_back(b);
+            for (int e = 0; e < b.n_elem; ++e)
+                for (int i = 0; i < npe; ++i) m->node_body[b.conn[(size_t)e * npe + i]] = m->h_body.back()[e];
+            ne += b.n_elem;
+        }
+        if (desc->elem_mu_lambda) m->h_elam.assign(desc->elem_mu_lambda, desc->elem_mu_lambda + 2 * ne);
+    }
     auto bail = [&](tlfe_status e) {
         tlfe_destroy_mesh(m);
         return e;
@@ -437,7 +455,6 @@ extern "C" tlfe_status tlfe_destroy_mesh(tlfe_mesh *m)
     if (!m) return TLFE_OK;
     cudaDeviceSynchronize();
     destroy_newton(m);
-    if (m->graph_exec) cudaGraphExecDestroy(m->graph_exec);
     for (void *p : m->allocs) cudaFree(p);
     delete m;
     return TLFE_OK;
@@ -569,6 +586,7 @@ tlfe_status run_op(tlfe_mesh *m, const void *u, const void *ud, const void *v, v
     p.aK = R(aK);
     p.aC = R(aC);
     p.sym_only = sym_only;
+    p.mass_only = (OP == OP_MATVEC && aK == 0.0 && aC == 0.0) ? 1 : 0;
     const size_t nb = sizeof(R) * 3 * (size_t)m->n_nodes;
     if (out0) CK(cudaMemsetAsync(out0, 0, nb, s));
     if (out1) CK(cudaMemsetAsync(out1, 0, nb, s));
@@ -586,6 +604,8 @@ template tlfe_status run_op<OP_MATVEC, float>(tlfe_mesh *, const void *, const v
 template tlfe_status run_op<OP_MATVEC, double>(tlfe_mesh *, const void *, const void *, const void *, void *, void *, double *, double, double, double, int, cudaStream_t);
 template tlfe_status run_op<OP_DIAG, float>(tlfe_mesh *, const void *, const void *, const void *, void *, void *, double *, double, double, double, int, cudaStream_t);
 template tlfe_status run_op<OP_DIAG, double>(tlfe_mesh *, const void *, const void *, const void *, void *, void *, double *, double, double, double, int, cudaStream_t);
+template tlfe_status run_op<OP_VJP, float>(tlfe_mesh *, const void *, const void *, const void *, void *, void *, double *, double, double, double, int, cudaStream_t);
+template tlfe_status run_op<OP_VJP, double>(tlfe_mesh *, const void *, const void *, const void *, void *, void *, double *, double, double, double, int, cudaStream_t);
 
 }  // namespace tlfe
 

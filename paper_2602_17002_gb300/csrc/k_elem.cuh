@@ -186,7 +186,8 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? (OP == OP_FORCE ? 4 : 3)
     const int W = gridDim.x * wpb;
     const int t0 = p.tile_begin + gw;
     const int n_my = t0 < p.tile_end ? (p.tile_end - t0 + W - 1) / W : 0;
-    const int n_slices = n_my * NQ;
+    const bool mass_only = OP == OP_MATVEC && p.mass_only != 0;
+    const int n_slices = mass_only ? 0 : n_my * NQ;
     const bool need_ud = p.visc != 0;
 
     if (lane == 0) {
@@ -263,7 +264,7 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? (OP == OP_FORCE ? 4 : 3)
         int bad = 0;
 
 #pragma unroll 1
-        for (int q = 0; q < NQ; ++q) {
+        for (int q = 0; q < (mass_only ? 0 : NQ); ++q) {
             const int j = k * NQ + q;
             const int b = j % NSLICE;
             if (!mbar_wait_bounded(bar + b, (uint32_t)((j / NSLICE) & 1))) timed_out = true;

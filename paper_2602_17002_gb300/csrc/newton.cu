@@ -1,18 +1,803 @@
-// Backward-Euler Newton/CG step (Section 7 without constraints).
+// Backward-Euler step of Section 7 (no constraint terms), batched over bodies.
+//
+//   q(v) = q_n + h v                                   (Eq. step_map_velocity_level)
+//   g(v) = M/h (v - v_n) + f_int(q(v), v) - f_ff       (Eq. residual, f_ext = 0)
+//
+// Inexact Newton: each iteration solves (M/h + h K^e + C) dv = -g, the
+// symmetric part of dg/dv = M/h + h K_t + C (the Newton matrix of Sec. 2.2
+// without constraint terms, plus the Kelvin-Voigt damping C), by
+// Jacobi-preconditioned CG, then v += dv. Bodies are independent: every body
+// has its own CG scalars and convergence masks, all bodies advance in
+// lockstep, and each stops when ||g_b|| <= newton_rtol ||g_b(v_n)||.
+//
+// Precision: the residual, the CG vectors, dots and updates are FP64; the
+// operator product and the Jacobi diagonal use the mesh precision. For an FP32
+// mesh the residual is evaluated on an FP64 twin of the mesh (same description,
+// FP64 slab), built on the first call.
+//
+// Per-body reductions are deterministic: the DOFs of every body (which must
+// own one contiguous node range) are cut into fixed chunks; one CTA reduces a
+// chunk into a partial, and one thread per body sums its partials in order.
+//
+// The whole step is one CUDA graph with two nested conditional WHILE nodes
+// (Newton outside, CG inside), captured on the first call for a given
+// parameter set and replayed afterwards; use_graph = 0 runs the same kernels
+// from a host loop.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
 #include "tlfe_mesh.h"
 
 namespace tlfe {
-struct NewtonState {};
+
+constexpr int CHUNK = 4096;  // DOFs per reduction chunk
+constexpr int RT = 256;      // threads per chunk CTA
+
+enum {
+    S_G0 = 0,   // ||g_b(v_n)||
+    S_GN,       // ||g_b||
+    S_NACT,     // Newton active (1/0)
+    S_RZ,       // r . z
+    S_R0,       // ||r_0||
+    S_RN,       // ||r||
+    S_ALPHA,
+    S_BETA,
+    S_CACT,     // CG active (1/0)
+    S_NIT,      // Newton iterations of the body
+    S_COUNT
+};
+enum { I_NEWTON = 0, I_CG, I_CG_TOTAL, I_ANY_N, I_ANY_C, I_COUNT };
+
+struct NewtonState {
+    // parameters the captured graph was built for
+    double h = 0, grav[3] = {0, 0, 0}, nrtol = 0, crtol = 0;
+    int max_newton = 0, max_cg = 0;
+    const void *fixed_user = nullptr;
+    int use_graph = -1;
+    // body / chunk tables
+    int nb = 0, n_chunks = 0;
+    int32_t *chunk_start = nullptr, *chunk_end = nullptr, *chunk_body = nullptr, *body_chunk_off = nullptr;
+    // FP64 vectors [3N]
+    double *u_n = nullptr, *v_n = nullptr, *v = nullptr, *u_cur = nullptr, *dv = nullptr, *g = nullptr,
+           *fff = nullptr, *y1 = nullptr, *y2 = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr,
+           *Ap = nullptr, *Dinv = nullptr, *gv = nullptr, *Dd = nullptr;
+    // mesh-precision vectors [3N]
+    float *u32 = nullptr, *ud32 = nullptr, *p32 = nullptr, *Ap32 = nullptr, *D32 = nullptr;
+    uint8_t *fixed = nullptr;  // [N], 1 = clamped (nodes outside every element included)
+    double *partials = nullptr;  // [2][n_chunks]
+    double *sc = nullptr;        // [S_COUNT][nb]
+    int *it = nullptr;           // [I_COUNT]
+    tlfe_mesh *twin = nullptr;   // FP64 mesh for the residual (FP32 meshes only)
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphConditionalHandle hN = 0, hC = 0;
+    cudaStream_t s_main = nullptr, s_body = nullptr, s_cg = nullptr;  // capture streams
+    std::vector<void *> allocs;
+};
+
+// ---------------------------------------------------------------------------
+// kernels (grid = n_chunks CTAs of RT threads; CTA c owns DOFs [start_c, end_c)
+// of body chunk_body[c])
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ double block_sum(double v, double *sh)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += sh[k];
+    return s;  // valid in thread 0
+}
+
+struct ChunkArgs {
+    const int32_t *start, *end, *body;
+    int n_chunks;
+};
+
+// u_cur = u_n + h v, dv = v - v_n, and the mesh-precision copies
+template <typename R>
+__global__ void k_prep(ChunkArgs c, double h, const double *u_n, const double *v, const double *v_n, double *u_cur,
+                       double *dv, R *u_lo, R *ud_lo)
+{
+    const int ch = blockIdx.x;
+    for (int i = c.start[ch] + threadIdx.x; i < c.end[ch]; i += blockDim.x) {
+        const double uc = u_n[i] + h * v[i];
+        u_cur[i] = uc;
+        dv[i] = v[i] - v_n[i];
+        if (u_lo) u_lo[i] = R(uc);
+        if (ud_lo) ud_lo[i] = R(v[i]);
+    }
+}
+
+// g = y1 + y2 - f_ff on free DOFs, 0 on clamped ones; partial of g.g
+__global__ void k_residual(ChunkArgs c, const double *y1, const double *y2, const double *fff, const uint8_t *fixed,
+                           double *g, double *partials)
+{
+    __shared__ double sh[32];
+    const int ch = blockIdx.x;
+    double acc = 0.0;
+    for (int i = c.start[ch] + threadIdx.x; i < c.end[ch]; i += blockDim.x) {
+        const double gi = fixed[i / 3] ? 0.0 : y1[i] + y2[i] - fff[i];
+        g[i] = gi;
+        acc += gi * gi;
+    }
+    const double s = block_sum(acc, sh);
+    if (threadIdx.x == 0) partials[ch] = s;
+}
+
+// Newton convergence test per body; sets the Newton WHILE condition
+__global__ void k_newton_check(int nb, const int32_t *boff, const double *partials, double *sc, int *it, double rtol,
+                               int max_newton, cudaGraphConditionalHandle hN, int use_handle)
+{
+    int any = 0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        double s = 0.0;
+        for (int k = boff[b]; k < boff[b + 1]; ++k) s += partials[k];
+        const double gn = sqrt(s);
+        if (it[I_NEWTON] == 0) sc[S_G0 * nb + b] = gn;
+        sc[S_GN * nb + b] = gn;
+        const double g0 = sc[S_G0 * nb + b];
+        const int act = (g0 > 0.0 && gn > rtol * g0 && it[I_NEWTON] < max_newton) ? 1 : 0;
+        sc[S_NACT * nb + b] = act;
+        any |= act;
+    }
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) {
+        it[I_ANY_N] = any;
+        if (use_handle) cudaGraphSetConditional(hN, any ? 1u : 0u);
+    }
+}
+
+// Jacobi inverse on free DOFs of Newton-active bodies
+template <typename R>
+__global__ void k_dinv(ChunkArgs c, const R *D, const uint8_t *fixed, const double *sc, int nb, double *Dinv)
+{
+    const int ch = blockIdx.x;
+    const int b = c.body[ch];
+    const bool act = sc[S_NACT * nb + b] != 0.0;
+    for (int i = c.start[ch] + threadIdx.x; i < c.end[ch]; i += blockDim.x) {
+        const double d = double(D[i]);
+        Dinv[i] = (act && !fixed[i / 3] && d != 0.0) ? 1.0 / d : 0.0;
+    }
+}
+
+// x = 0, r = -g (active bodies), z = Dinv r, p = z; partials of r.z and r.r
+__global__ void k_cg_init(ChunkArgs c, const double *g, const double *Dinv, const double *sc, int nb, double *x,
+                          double *r, double *z, double *p, double *partials)
+{
+    __shared__ double sh[32];
+    const int ch = blockIdx.x;
+    const int b = c.body[ch];
+    const bool act = sc[S_NACT * nb + b] != 0.0;
+    double rz = 0.0, rr = 0.0;
+    for (int i = c.start[ch] + threadIdx.x; i < c.end[ch]; i += blockDim.x) {
+        const double ri = act ? -g[i] : 0.0;
+        const double zi = Dinv[i] * ri;
+        x[i] = 0.0;
+        r[i] = ri;
+        z[i] = zi;
+        p[i] = zi;
+        rz += ri * zi;
+        rr += ri * ri;
+    }
+    const double s1 = block_sum(rz, sh);
+    if (threadIdx.x == 0) partials[ch] = s1;
+    const double s2 = block_sum(rr, sh);
+    if (threadIdx.x == 0) partials[c.n_chunks + ch] = s2;
+}
+
+__global__ void k_cg_init_finish(int nb, const int32_t *boff, const double *partials, int n_chunks, double *sc,
+                                 int *it, int max_cg, cudaGraphConditionalHandle hC, int use_handle)
+{
+    int any = 0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        double rz = 0.0, rr = 0.0;
+        for (int k = boff[b]; k < boff[b + 1]; ++k) {
+            rz += partials[k];
+            rr += partials[n_chunks + k];
+        }
+        const double r0 = sqrt(rr);
+        sc[S_RZ * nb + b] = rz;
+        sc[S_R0 * nb + b] = r0;
+        sc[S_RN * nb + b] = r0;
+        const int act = (sc[S_NACT * nb + b] != 0.0 && r0 > 0.0 && rz > 0.0 && max_cg > 0) ? 1 : 0;
+        sc[S_CACT * nb + b] = act;
+        any |= act;
+    }
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) {
+        it[I_CG] = 0;
+        it[I_ANY_C] = any;
+        if (use_handle) cudaGraphSetConditional(hC, any ? 1u : 0u);
+    }
+}
+
+// mesh-precision copy of the search direction
+template <typename R> __global__ void k_to_lo(ChunkArgs c, const double *a, R *b)
+{
+    const int ch = blockIdx.x;
+    for (int i = c.start[ch] + threadIdx.x; i < c.end[ch]; i += blockDim.x) b[i] = R(a[i]);
+}
+
+// Ap (FP64, clamped DOFs zero); partial of p.Ap
+template <typename R>
+__global__ void k_cg_pap(ChunkArgs c, const R *Ap_lo, const uint8_t *fixed, const double *p, double *Ap,
+                         double *partials)
+{
+    __shared__ double sh[32];
+    const int ch = blockIdx.x;
+    double acc = 0.0;
+    for (int i = c.start[ch] + threadIdx.x; i < c.end[ch]; i += blockDim.x) {
+        const double a = fixed[i / 3] ? 0.0 : double(Ap_lo[i]);
+        Ap[i] = a;
+        acc += p[i] * a;
+    }
+    const double s = block_sum(acc, sh);
+    if (threadIdx.x == 0) partials[ch] = s;
+}
+
+__global__ void k_cg_alpha(int nb, const int32_t *boff, const double *partials, double *sc)
+{
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        double pap = 0.0;
+        for (int k = boff[b]; k < boff[b + 1]; ++k) pap += partials[k];
+        const bool act = sc[S_CACT * nb + b] != 0.0 && pap > 0.0;
+        if (sc[S_CACT * nb + b] != 0.0 && !(pap > 0.0)) sc[S_CACT * nb + b] = 0.0;  // not SPD here: stop this body
+        sc[S_ALPHA * nb + b] = act ? sc[S_RZ * nb + b] / pap : 0.0;
+    }
+}
+
+// x += alpha p, r -= alpha Ap, z = Dinv r; partials of r.r and r.z
+__global__ void k_cg_xr(ChunkArgs c, const double *sc, int nb, const double *p, const double *Ap,
+                        const double *Dinv, double *x, double *r, double *z, double *partials)
+{
+    __shared__ double sh[32];
+    const int ch = blockIdx.x;
+    const int b = c.body[ch];
+    const double alpha = sc[S_ALPHA * nb + b];
+    double rr = 0.0, rz = 0.0;
+    for (int i = c.start[ch] + threadIdx.x; i < c.end[ch]; i += blockDim.x) {
+        const double xi = x[i] + alpha * p[i];
+        const double ri = r[i] - alpha * Ap[i];
+        const double zi = Dinv[i] * ri;
+        x[i] = xi;
+        r[i] = ri;
+        z[i] = zi;
+        rr += ri * ri;
+        rz += ri * zi;
+    }
+    const double s1 = block_sum(rr, sh);
+    if (threadIdx.x == 0) partials[ch] = s1;
+    const double s2 = block_sum(rz, sh);
+    if (threadIdx.x == 0) partials[c.n_chunks + ch] = s2;
+}
+
+__global__ void k_cg_beta(int nb, const int32_t *boff, const double *partials, int n_chunks, double *sc, int *it,
+                          double rtol, int max_cg, cudaGraphConditionalHandle hC, int use_handle)
+{
+    int any = 0;
+    const int itn = it[I_CG] + 1;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        double rr = 0.0, rz = 0.0;
+        for (int k = boff[b]; k < boff[b + 1]; ++k) {
+            rr += partials[k];
+            rz += partials[n_chunks + k];
+        }
+        const double rn = sqrt(rr);
+        int act = sc[S_CACT * nb + b] != 0.0 ? 1 : 0;
+        if (act) {
+            sc[S_RN * nb + b] = rn;
+            const double rz_old = sc[S_RZ * nb + b];
+            sc[S_BETA * nb + b] = rz_old != 0.0 ? rz / rz_old : 0.0;
+            sc[S_RZ * nb + b] = rz;
+            if (!(rn > rtol * sc[S_R0 * nb + b]) || itn >= max_cg) act = 0;
+            sc[S_CACT * nb + b] = act;
+        }
+        any |= act;
+    }
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) {
+        it[I_CG] = itn;
+        it[I_CG_TOTAL] += 1;
+        it[I_ANY_C] = any;
+        if (use_handle) cudaGraphSetConditional(hC, any ? 1u : 0u);
+    }
+}
+
+// p = z + beta p on CG-active bodies
+__global__ void k_cg_p(ChunkArgs c, const double *sc, int nb, const double *z, double *p)
+{
+    const int ch = blockIdx.x;
+    const int b = c.body[ch];
+    if (sc[S_CACT * nb + b] == 0.0) return;
+    const double beta = sc[S_BETA * nb + b];
+    for (int i = c.start[ch] + threadIdx.x; i < c.end[ch]; i += blockDim.x) p[i] = z[i] + beta * p[i];
+}
+
+// v += x on Newton-active bodies (x is zero elsewhere); count the iteration
+__global__ void k_v_update(ChunkArgs c, const double *sc, int nb, const double *x, double *v)
+{
+    const int ch = blockIdx.x;
+    const int b = c.body[ch];
+    if (sc[S_NACT * nb + b] == 0.0) return;
+    for (int i = c.start[ch] + threadIdx.x; i < c.end[ch]; i += blockDim.x) v[i] += x[i];
+}
+
+__global__ void k_newton_count(int nb, double *sc, int *it)
+{
+    for (int b = threadIdx.x; b < nb; b += blockDim.x)
+        if (sc[S_NACT * nb + b] != 0.0) sc[S_NIT * nb + b] += 1.0;
+    if (threadIdx.x == 0) it[I_NEWTON] += 1;
+}
+
+// v = v_n with clamped DOFs zeroed; counters reset
+__global__ void k_start(ChunkArgs c, const uint8_t *fixed, const double *v_n, double *v)
+{
+    const int ch = blockIdx.x;
+    for (int i = c.start[ch] + threadIdx.x; i < c.end[ch]; i += blockDim.x) v[i] = fixed[i / 3] ? 0.0 : v_n[i];
+}
+
+__global__ void k_reset(int nb, double *sc, int *it)
+{
+    for (int b = threadIdx.x; b < nb; b += blockDim.x)
+        for (int k = 0; k < S_COUNT; ++k) sc[k * nb + b] = 0.0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < I_COUNT; ++k) it[k] = 0;
+}
+
+// gravity vector field b0 at every node (f_ff = M b0, since sum_j s_j = 1)
+__global__ void k_fill_grav(int64_t n_nodes, double gx, double gy, double gz, double *out)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_nodes) return;
+    out[3 * k] = gx;
+    out[3 * k + 1] = gy;
+    out[3 * k + 2] = gz;
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+#define NCK(call)                                                     \
+    do {                                                              \
+        cudaError_t e_ = (call);                                      \
+        if (e_ != cudaSuccess) return tlfe::cuda_fail(e_, #call);     \
+    } while (0)
+
+template <typename T> static tlfe_status nalloc(NewtonState *ns, T **p, size_t n)
+{
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, sizeof(T) * (n ? n : 1));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (newton workspace)");
+    ns->allocs.push_back(q);
+    *p = (T *)q;
+    return TLFE_OK;
+}
+
 void destroy_newton(tlfe_mesh *m)
 {
-    delete m->newton;
+    NewtonState *ns = m->newton;
+    if (!ns) return;
+    if (ns->exec) cudaGraphExecDestroy(ns->exec);
+    if (ns->graph) cudaGraphDestroy(ns->graph);
+    if (ns->s_main) cudaStreamDestroy(ns->s_main);
+    if (ns->s_body) cudaStreamDestroy(ns->s_body);
+    if (ns->s_cg) cudaStreamDestroy(ns->s_cg);
+    for (void *q : ns->allocs) cudaFree(q);
+    if (ns->twin) tlfe_destroy_mesh(ns->twin);
+    delete ns;
     m->newton = nullptr;
 }
+
+// bodies must own contiguous node ranges; builds the chunk tables
+static tlfe_status setup_newton(tlfe_mesh *m, cudaStream_t s)
+{
+    NewtonState *ns = new NewtonState();
+    m->newton = ns;
+    const int N = m->n_nodes;
+    std::vector<int> nstart(m->n_bodies, -1), nend(m->n_bodies, -1);
+    int prev = -2;
+    std::vector<char> seen(m->n_bodies, 0);
+    for (int k = 0; k < N; ++k) {
+        const int b = m->node_body[k];
+        if (b < 0) {
+            prev = -2;
+            continue;
+        }
+        if (b != prev) {
+            if (seen[b]) return fail(TLFE_E_UNSUPPORTED, "newton step needs every body to own one contiguous node range");
+            seen[b] = 1;
+            nstart[b] = k;
+        }
+        nend[b] = k + 1;
+        prev = b;
+    }
+    // every element's nodes must belong to its own body (bodies do not share nodes)
+    for (size_t bi = 0; bi < m->h_conn.size(); ++bi) {
+        const int npe = nodes_per_elem(m->h_blocks[bi].type);
+        for (size_t e = 0; e < m->h_body[bi].size(); ++e)
+            for (int i = 0; i < npe; ++i)
+                if (m->node_body[m->h_conn[bi][e * npe + i]] != m->h_body[bi][e])
+                    return fail(TLFE_E_UNSUPPORTED, "newton step needs bodies that share no node");
+    }
+    ns->nb = m->n_bodies;
+    std::vector<int32_t> cs, ce, cb, boff(ns->nb + 1, 0);
+    for (int b = 0; b < ns->nb; ++b) {
+        if (nstart[b] >= 0)
+            for (int64_t d = 3 * (int64_t)nstart[b]; d < 3 * (int64_t)nend[b]; d += CHUNK) {
+                cs.push_back((int32_t)d);
+                ce.push_back((int32_t)std::min<int64_t>(d + CHUNK, 3 * (int64_t)nend[b]));
+                cb.push_back(b);
+            }
+        boff[b + 1] = (int32_t)cs.size();
+    }
+    ns->n_chunks = (int)cs.size();
+    if (ns->n_chunks == 0) return fail(TLFE_E_INVALID, "no body owns any node");
+    const size_t N3 = 3 * (size_t)N;
+    tlfe_status st = TLFE_OK;
+#define NA(ptr, n)                              \
+    if ((st = nalloc(ns, &(ptr), (n))) != TLFE_OK) return st;
+    NA(ns->chunk_start, ns->n_chunks);
+    NA(ns->chunk_end, ns->n_chunks);
+    NA(ns->chunk_body, ns->n_chunks);
+    NA(ns->body_chunk_off, ns->nb + 1);
+    for (double **q : {&ns->u_n, &ns->v_n, &ns->v, &ns->u_cur, &ns->dv, &ns->g, &ns->fff, &ns->y1, &ns->y2, &ns->x,
+                       &ns->r, &ns->z, &ns->p, &ns->Ap, &ns->Dinv, &ns->gv, &ns->Dd})
+        NA(*q, N3);
+    for (float **q : {&ns->u32, &ns->ud32, &ns->p32, &ns->Ap32, &ns->D32}) NA(*q, N3);
+    NA(ns->fixed, (size_t)N);
+    NA(ns->partials, 2 * (size_t)ns->n_chunks);
+    NA(ns->sc, (size_t)S_COUNT * ns->nb);
+    NA(ns->it, (size_t)I_COUNT);
+#undef NA
+    NCK(cudaMemcpyAsync(ns->chunk_start, cs.data(), 4 * cs.size(), cudaMemcpyHostToDevice, s));
+    NCK(cudaMemcpyAsync(ns->chunk_end, ce.data(), 4 * ce.size(), cudaMemcpyHostToDevice, s));
+    NCK(cudaMemcpyAsync(ns->chunk_body, cb.data(), 4 * cb.size(), cudaMemcpyHostToDevice, s));
+    NCK(cudaMemcpyAsync(ns->body_chunk_off, boff.data(), 4 * boff.size(), cudaMemcpyHostToDevice, s));
+    NCK(cudaStreamSynchronize(s));
+    NCK(cudaStreamCreateWithFlags(&ns->s_main, cudaStreamNonBlocking));
+    NCK(cudaStreamCreateWithFlags(&ns->s_body, cudaStreamNonBlocking));
+    NCK(cudaStreamCreateWithFlags(&ns->s_cg, cudaStreamNonBlocking));
+    // FP64 twin for the residual of an FP32 mesh
+    if (m->precision == TLFE_FP32) {
+        tlfe_mesh_desc d;
+        memset(&d, 0, sizeof(d));
+        d.n_nodes = m->n_nodes;
+        d.X_ref = m->h_X.data();
+        std::vector<tlfe_block> blocks = m->h_blocks;
+        for (size_t bi = 0; bi < blocks.size(); ++bi) {
+            blocks[bi].conn = m->h_conn[bi].data();
+            blocks[bi].body = m->h_body[bi].data();
+        }
+        d.n_blocks = (int)blocks.size();
+        d.blocks = blocks.data();
+        d.n_bodies = m->n_bodies;
+        d.body_mat = m->h_mats.data();
+        d.elem_mu_lambda = m->h_elam.empty() ? nullptr : m->h_elam.data();
+        d.precision = TLFE_FP64;
+        d.scatter = m->scatter;
+        d.color_seed = m->color_seed;
+        st = tlfe_create_mesh(&d, s, &ns->twin);
+        if (st != TLFE_OK) return st;
+    }
+    return TLFE_OK;
+}
+
+struct StepCtx {
+    tlfe_mesh *m;
+    NewtonState *ns;
+    ChunkArgs c;
+    int use_handle;
+};
+
+// --- building blocks, all stream-ordered on s --------------------------------
+
+static tlfe_status enq_residual(const StepCtx &x, cudaStream_t s)
+{
+    NewtonState *ns = x.ns;
+    tlfe_mesh *m64 = ns->twin ? ns->twin : x.m;
+    const int nc = ns->n_chunks;
+    if (x.m->precision == TLFE_FP32)
+        k_prep<float><<<nc, RT, 0, s>>>(x.c, ns->h, ns->u_n, ns->v, ns->v_n, ns->u_cur, ns->dv, ns->u32, ns->ud32);
+    else
+        k_prep<double><<<nc, RT, 0, s>>>(x.c, ns->h, ns->u_n, ns->v, ns->v_n, ns->u_cur, ns->dv, nullptr, nullptr);
+    NCK(cudaGetLastError());
+    tlfe_status st = run_op<OP_MATVEC, double>(m64, ns->u_cur, ns->v, ns->dv, ns->y1, nullptr, nullptr, 1.0 / ns->h,
+                                               0.0, 0.0, 0, s);
+    if (st != TLFE_OK) return st;
+    st = run_op<OP_FORCE, double>(m64, ns->u_cur, ns->v, nullptr, ns->y2, nullptr, nullptr, 0.0, 1.0, 0.0, 0, s);
+    if (st != TLFE_OK) return st;
+    k_residual<<<nc, RT, 0, s>>>(x.c, ns->y1, ns->y2, ns->fff, ns->fixed, ns->g, ns->partials);
+    k_newton_check<<<1, 1024, 0, s>>>(ns->nb, ns->body_chunk_off, ns->partials, ns->sc, ns->it, ns->nrtol,
+                                       ns->max_newton, ns->hN, x.use_handle);
+    NCK(cudaGetLastError());
+    return TLFE_OK;
+}
+
+static tlfe_status enq_cg_init(const StepCtx &x, cudaStream_t s)
+{
+    NewtonState *ns = x.ns;
+    const int nc = ns->n_chunks;
+    const double h = ns->h;
+    tlfe_status st;
+    if (x.m->precision == TLFE_FP32) {
+        st = run_op<OP_DIAG, float>(x.m, ns->u32, ns->ud32, nullptr, ns->D32, nullptr, nullptr, 1.0 / h, h, 1.0, 1, s);
+        if (st != TLFE_OK) return st;
+        k_dinv<float><<<nc, RT, 0, s>>>(x.c, ns->D32, ns->fixed, ns->sc, ns->nb, ns->Dinv);
+    } else {
+        st = run_op<OP_DIAG, double>(x.m, ns->u_cur, ns->v, nullptr, ns->Dd, nullptr, nullptr, 1.0 / h, h, 1.0, 1, s);
+        if (st != TLFE_OK) return st;
+        k_dinv<double><<<nc, RT, 0, s>>>(x.c, ns->Dd, ns->fixed, ns->sc, ns->nb, ns->Dinv);
+    }
+    k_cg_init<<<nc, RT, 0, s>>>(x.c, ns->g, ns->Dinv, ns->sc, ns->nb, ns->x, ns->r, ns->z, ns->p, ns->partials);
+    k_cg_init_finish<<<1, 1024, 0, s>>>(ns->nb, ns->body_chunk_off, ns->partials, nc, ns->sc, ns->it, ns->max_cg,
+                                         ns->hC, x.use_handle);
+    NCK(cudaGetLastError());
+    return TLFE_OK;
+}
+
+static tlfe_status enq_cg_iter(const StepCtx &x, cudaStream_t s)
+{
+    NewtonState *ns = x.ns;
+    const int nc = ns->n_chunks;
+    const double h = ns->h;
+    tlfe_status st;
+    if (x.m->precision == TLFE_FP32) {
+        k_to_lo<float><<<nc, RT, 0, s>>>(x.c, ns->p, ns->p32);
+        st = run_op<OP_MATVEC, float>(x.m, ns->u32, ns->ud32, ns->p32, ns->Ap32, nullptr, nullptr, 1.0 / h, h, 1.0, 1,
+                                      s);
+        if (st != TLFE_OK) return st;
+        k_cg_pap<float><<<nc, RT, 0, s>>>(x.c, ns->Ap32, ns->fixed, ns->p, ns->Ap, ns->partials);
+    } else {
+        st = run_op<OP_MATVEC, double>(x.m, ns->u_cur, ns->v, ns->p, ns->y1, nullptr, nullptr, 1.0 / h, h, 1.0, 1, s);
+        if (st != TLFE_OK) return st;
+        k_cg_pap<double><<<nc, RT, 0, s>>>(x.c, ns->y1, ns->fixed, ns->p, ns->Ap, ns->partials);
+    }
+    k_cg_alpha<<<1, 1024, 0, s>>>(ns->nb, ns->body_chunk_off, ns->partials, ns->sc);
+    k_cg_xr<<<nc, RT, 0, s>>>(x.c, ns->sc, ns->nb, ns->p, ns->Ap, ns->Dinv, ns->x, ns->r, ns->z, ns->partials);
+    k_cg_beta<<<1, 1024, 0, s>>>(ns->nb, ns->body_chunk_off, ns->partials, nc, ns->sc, ns->it, ns->crtol, ns->max_cg,
+                                  ns->hC, x.use_handle);
+    k_cg_p<<<nc, RT, 0, s>>>(x.c, ns->sc, ns->nb, ns->z, ns->p);
+    NCK(cudaGetLastError());
+    return TLFE_OK;
+}
+
+static tlfe_status enq_newton_tail(const StepCtx &x, cudaStream_t s)
+{
+    NewtonState *ns = x.ns;
+    k_v_update<<<ns->n_chunks, RT, 0, s>>>(x.c, ns->sc, ns->nb, ns->x, ns->v);
+    k_newton_count<<<1, 1024, 0, s>>>(ns->nb, ns->sc, ns->it);
+    NCK(cudaGetLastError());
+    return enq_residual(x, s);
+}
+
+static tlfe_status enq_prologue(const StepCtx &x, cudaStream_t s)
+{
+    NewtonState *ns = x.ns;
+    k_reset<<<1, 1024, 0, s>>>(ns->nb, ns->sc, ns->it);
+    k_start<<<ns->n_chunks, RT, 0, s>>>(x.c, ns->fixed, ns->v_n, ns->v);
+    NCK(cudaGetLastError());
+    return enq_residual(x, s);
+}
+
+// add a conditional WHILE node to the graph being captured on `s`; returns its body graph
+static tlfe_status add_while(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraph_t *body)
+{
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t ndeps = 0;
+    NCK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &ndeps));
+    if (cs != cudaStreamCaptureStatusActive) return fail(TLFE_E_CUDA, "stream is not capturing");
+    // cudaGraphNodeParams has no usable default constructor: zero a buffer
+    alignas(cudaGraphNodeParams) unsigned char buf[sizeof(cudaGraphNodeParams)];
+    memset(buf, 0, sizeof(buf));
+    cudaGraphNodeParams *cp = reinterpret_cast<cudaGraphNodeParams *>(buf);
+    cp->type = cudaGraphNodeTypeConditional;
+    cp->conditional.handle = h;
+    cp->conditional.type = cudaGraphCondTypeWhile;
+    cp->conditional.size = 1;
+    cudaGraphNode_t node;
+    NCK(cudaGraphAddNode(&node, g, deps, nullptr, ndeps, cp));
+    NCK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    *body = cp->conditional.phGraph_out[0];
+    return TLFE_OK;
+}
+
+// Captures on the step's own streams (the caller's stream may be the legacy
+// default stream, which cannot be captured); the graph is launched on the
+// caller's stream afterwards.
+static tlfe_status build_graph(StepCtx &x)
+{
+    NewtonState *ns = x.ns;
+    cudaStream_t s = ns->s_main;
+    if (ns->exec) {
+        cudaGraphExecDestroy(ns->exec);
+        ns->exec = nullptr;
+    }
+    if (ns->graph) {
+        cudaGraphDestroy(ns->graph);
+        ns->graph = nullptr;
+    }
+    NCK(cudaGraphCreate(&ns->graph, 0));
+    NCK(cudaGraphConditionalHandleCreate(&ns->hN, ns->graph, 0, 0));
+    x.use_handle = 1;
+    // main graph: prologue, Newton WHILE
+    NCK(cudaStreamBeginCaptureToGraph(s, ns->graph, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    tlfe_status st = enq_prologue(x, s);
+    cudaGraph_t body_n = nullptr;
+    if (st == TLFE_OK) st = add_while(s, ns->hN, &body_n);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s, &g);
+    if (st != TLFE_OK) return st;
+    if (e != cudaSuccess) return cuda_fail(e, "end capture (main)");
+    // Newton body: Jacobi + CG init, CG WHILE, update + residual
+    NCK(cudaGraphConditionalHandleCreate(&ns->hC, body_n, 0, 0));
+    NCK(cudaStreamBeginCaptureToGraph(ns->s_body, body_n, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    st = enq_cg_init(x, ns->s_body);
+    cudaGraph_t body_c = nullptr;
+    if (st == TLFE_OK) st = add_while(ns->s_body, ns->hC, &body_c);
+    if (st == TLFE_OK) st = enq_newton_tail(x, ns->s_body);
+    e = cudaStreamEndCapture(ns->s_body, &g);
+    if (st != TLFE_OK) return st;
+    if (e != cudaSuccess) return cuda_fail(e, "end capture (newton body)");
+    // CG body
+    NCK(cudaStreamBeginCaptureToGraph(ns->s_cg, body_c, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    st = enq_cg_iter(x, ns->s_cg);
+    e = cudaStreamEndCapture(ns->s_cg, &g);
+    if (st != TLFE_OK) return st;
+    if (e != cudaSuccess) return cuda_fail(e, "end capture (cg body)");
+    NCK(cudaGraphInstantiate(&ns->exec, ns->graph, 0));
+    return TLFE_OK;
+}
+
+// warm the per-kernel occupancy caches outside any capture
+static tlfe_status warm(StepCtx &x, cudaStream_t s)
+{
+    x.use_handle = 0;
+    tlfe_status st = enq_prologue(x, s);
+    if (st == TLFE_OK) st = enq_cg_init(x, s);
+    if (st == TLFE_OK && x.ns->max_cg > 0) st = enq_cg_iter(x, s);
+    if (st != TLFE_OK) return st;
+    NCK(cudaStreamSynchronize(s));
+    return TLFE_OK;
+}
+
 }  // namespace tlfe
 
-extern "C" tlfe_status tlfe_newton_step(tlfe_mesh *m, const double *, const double *, const tlfe_step_params *,
-                                        double *, tlfe_step_report *, void *)
+using namespace tlfe;
+
+extern "C" tlfe_status tlfe_newton_step(tlfe_mesh *m, const double *u_n, const double *v_n,
+                                        const tlfe_step_params *prm, double *v_out, tlfe_step_report *rep,
+                                        void *stream)
 {
-    if (!m) return tlfe::fail(TLFE_E_INVALID, "mesh is NULL");
-    return tlfe::fail(TLFE_E_UNSUPPORTED, "newton step not built yet");
+    if (!m || !u_n || !v_n || !prm || !v_out || !rep) return fail(TLFE_E_INVALID, "NULL argument");
+    memset(rep, 0, sizeof(*rep));
+    if (!(prm->h > 0.0) || !std::isfinite(prm->h) || !(prm->newton_rtol >= 0.0) || !(prm->cg_rtol >= 0.0) ||
+        prm->max_newton < 0 || prm->max_cg < 0)
+        return fail(TLFE_E_INVALID, "bad step parameters");
+    for (auto &B : m->blocks)
+        if (B.n_elem > 0 && !B.affine) return fail(TLFE_E_UNSUPPORTED, "newton step needs affine elements (consistent mass)");
+    cudaStream_t s = (cudaStream_t)stream;
+    tlfe_status st;
+    if (!m->newton) {
+        st = setup_newton(m, s);
+        if (st != TLFE_OK) {
+            destroy_newton(m);
+            return st;
+        }
+    }
+    NewtonState *ns = m->newton;
+    const size_t N = (size_t)m->n_nodes, N3 = 3 * N;
+    const bool same = ns->use_graph >= 0 && ns->h == prm->h && ns->grav[0] == prm->gravity[0] &&
+                      ns->grav[1] == prm->gravity[1] && ns->grav[2] == prm->gravity[2] &&
+                      ns->nrtol == prm->newton_rtol && ns->crtol == prm->cg_rtol && ns->max_newton == prm->max_newton &&
+                      ns->max_cg == prm->max_cg && ns->fixed_user == (const void *)prm->fixed_dev;
+    StepCtx x{m, ns, {ns->chunk_start, ns->chunk_end, ns->chunk_body, ns->n_chunks}, 0};
+    // inputs into the workspace (the graph only ever sees workspace pointers)
+    NCK(cudaMemcpyAsync(ns->u_n, u_n, 8 * N3, cudaMemcpyDeviceToDevice, s));
+    NCK(cudaMemcpyAsync(ns->v_n, v_n, 8 * N3, cudaMemcpyDeviceToDevice, s));
+    if (!same) {
+        ns->h = prm->h;
+        memcpy(ns->grav, prm->gravity, sizeof(ns->grav));
+        ns->nrtol = prm->newton_rtol;
+        ns->crtol = prm->cg_rtol;
+        ns->max_newton = prm->max_newton;
+        ns->max_cg = prm->max_cg;
+        ns->fixed_user = prm->fixed_dev;
+        // clamped nodes: user's flags, plus nodes outside every element
+        std::vector<uint8_t> fx(N, 0);
+        if (prm->fixed_dev) NCK(cudaMemcpy(fx.data(), prm->fixed_dev, N, cudaMemcpyDeviceToHost));
+        for (size_t k = 0; k < N; ++k)
+            if (m->node_body[k] < 0) fx[k] = 1;
+        NCK(cudaMemcpy(ns->fixed, fx.data(), N, cudaMemcpyHostToDevice));
+        // f_ff = M b0 (Eq. virtual_work_force_field_uniform with sum_j s_j = 1)
+        k_fill_grav<<<(unsigned)((N + 255) / 256), 256, 0, s>>>((int64_t)N, prm->gravity[0], prm->gravity[1],
+                                                                prm->gravity[2], ns->gv);
+        NCK(cudaGetLastError());
+        tlfe_mesh *m64 = ns->twin ? ns->twin : m;
+        st = run_op<OP_MATVEC, double>(m64, ns->u_n, nullptr, ns->gv, ns->fff, nullptr, nullptr, 1.0, 0.0, 0.0, 0, s);
+        if (st != TLFE_OK) return st;
+        st = warm(x, s);
+        if (st != TLFE_OK) return st;
+        ns->use_graph = prm->use_graph ? 1 : 0;
+        if (prm->use_graph) {
+            NCK(cudaStreamSynchronize(s));
+            st = build_graph(x);
+            if (st != TLFE_OK) {
+                ns->use_graph = -1;
+                return st;
+            }
+        }
+        NCK(cudaMemcpyAsync(ns->u_n, u_n, 8 * N3, cudaMemcpyDeviceToDevice, s));
+        NCK(cudaMemcpyAsync(ns->v_n, v_n, 8 * N3, cudaMemcpyDeviceToDevice, s));
+    }
+    if (ns->use_graph == 1 && prm->use_graph) {
+        NCK(cudaGraphLaunch(ns->exec, s));
+    } else {
+        // host-driven loop over the same kernels
+        x.use_handle = 0;
+        st = enq_prologue(x, s);
+        if (st != TLFE_OK) return st;
+        int flags[I_COUNT];
+        for (;;) {
+            NCK(cudaMemcpyAsync(flags, ns->it, sizeof(flags), cudaMemcpyDeviceToHost, s));
+            NCK(cudaStreamSynchronize(s));
+            if (!flags[I_ANY_N]) break;
+            st = enq_cg_init(x, s);
+            if (st != TLFE_OK) return st;
+            for (;;) {
+                NCK(cudaMemcpyAsync(flags, ns->it, sizeof(flags), cudaMemcpyDeviceToHost, s));
+                NCK(cudaStreamSynchronize(s));
+                if (!flags[I_ANY_C]) break;
+                st = enq_cg_iter(x, s);
+                if (st != TLFE_OK) return st;
+            }
+            st = enq_newton_tail(x, s);
+            if (st != TLFE_OK) return st;
+        }
+    }
+    NCK(cudaMemcpyAsync(v_out, ns->v, 8 * N3, cudaMemcpyDeviceToDevice, s));
+    // report
+    std::vector<double> sc((size_t)S_COUNT * ns->nb);
+    int it[I_COUNT];
+    NCK(cudaMemcpyAsync(sc.data(), ns->sc, 8 * sc.size(), cudaMemcpyDeviceToHost, s));
+    NCK(cudaMemcpyAsync(it, ns->it, sizeof(it), cudaMemcpyDeviceToHost, s));
+    NCK(cudaStreamSynchronize(s));
+    int conv = 0, bodies = 0, nit = 0;
+    double worst = 0.0;
+    for (int b = 0; b < ns->nb; ++b) {
+        const double g0 = sc[S_G0 * ns->nb + b], gn = sc[S_GN * ns->nb + b];
+        if (!(g0 > 0.0)) {
+            ++conv;  // nothing to solve for this body (or it owns no node)
+            continue;
+        }
+        ++bodies;
+        const double rel = gn / g0;
+        worst = std::max(worst, rel);
+        if (rel <= prm->newton_rtol) ++conv;
+        nit = std::max(nit, (int)sc[S_NIT * ns->nb + b]);
+    }
+    (void)bodies;
+    rep->newton_iters = nit;
+    rep->cg_iters = it[I_CG_TOTAL];
+    rep->n_bodies_converged = conv;
+    rep->rel_residual = worst;
+    rep->status = conv == ns->nb ? TLFE_OK : TLFE_E_NOT_CONVERGED;
+    int64_t ninv = 0;
+    st = tlfe_sync(m, stream, &ninv);
+    if (st == TLFE_OK && ns->twin) st = tlfe_sync(ns->twin, stream, &ninv);
+    if (st != TLFE_OK) return st;
+    if (rep->status != TLFE_OK) return fail(TLFE_E_NOT_CONVERGED, "newton step did not reach the tolerance");
+    return TLFE_OK;
 }

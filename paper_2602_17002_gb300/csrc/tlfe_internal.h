@@ -52,6 +52,7 @@ template <typename R> struct KParams {
     double *gth;                // [n_elem][2] (VJP parameter gradient)
     R aM, aK, aC;
     int sym_only;
+    int mass_only;              // operator product with a_K = a_C = 0: no quadrature loop, no slab stream
     int rmw_scatter;            // 1: plain read-add-write (colour passes), 0: atomics
     int visc;                   // udot given and material damped somewhere in the block
     int *status;                // [ST_COUNT]

@@ -48,8 +48,15 @@ struct tlfe_mesh {
     double *d_X = nullptr;
     void *d_stage = nullptr;        // staging buffers of tlfe_internal_force_host
     void *d_scratch_vjp = nullptr;  // stand-in outputs of tlfe_vjp
-    cudaGraphExec_t graph_exec = nullptr;
     tlfe::NewtonState *newton = nullptr;
+    // host copy of the creation description (the Newton step builds an FP64
+    // twin of an FP32 mesh from it) and the node -> body map
+    std::vector<double> h_X;
+    std::vector<std::vector<int32_t>> h_conn, h_body;
+    std::vector<tlfe_block> h_blocks;
+    std::vector<double> h_elam;
+    uint64_t color_seed = 0;
+    std::vector<int32_t> node_body;  // body of each node (-1: in no element)
     std::vector<void *> allocs;
     std::map<std::tuple<int, int, int, int, size_t>, int> occ_cache;  // resident warps per SM
     std::map<std::tuple<int, int, int, int, size_t>, int> occ_wpb;    // warps per CTA chosen

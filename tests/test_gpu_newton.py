@@ -1,0 +1,105 @@
+"""Batched backward-Euler Newton/CG step on the GPU against closed forms and the
+FP64 oracle (Section 7 without constraints)."""
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from synth.workloads import Block, Workload
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+G = np.array([0.0, 0.0, -9.81])
+H = 1e-3
+
+
+def T():
+    from paper_2602_17002_gb300 import tlfe
+    return tlfe
+
+
+def beams(n_bodies, sizes, clamp=True, damping=0.0):
+    """n_bodies small clamped beams (one body each) concatenated."""
+    ms = [synth.box_mesh(synth.T10, (c, 1, 1), (0.05 * c, 0.05, 0.05)) for c in sizes[:n_bodies]]
+    big = synth.concat_meshes(ms)
+    fixed = (np.abs(big.X[:, 0]) < 1e-12).astype(np.uint8) if clamp else None
+    params = np.tile(np.array([[3.8e6, 5.8e6, damping, 0.0, 1000.0]]), (n_bodies, 1))
+    wl = Workload("beams", big.X, [Block(synth.T10, 5, big.conn, big.body)],
+                  np.full(n_bodies, synth.workloads.NEOHOOKE, np.int32), params,
+                  u=np.zeros_like(big.X), udot=np.zeros_like(big.X), fixed=fixed)
+    return wl
+
+
+def step(wl, prec, use_graph=True, rtol=1e-8, cg_rtol=1e-4):
+    tl = T()
+    mesh = tl.Mesh.from_workload(wl, precision=prec)
+    z = torch.zeros((wl.n_nodes, 3), dtype=torch.float64, device="cuda")
+    fx = None if wl.fixed is None else torch.from_numpy(wl.fixed).cuda()
+    v, rep = mesh.newton_step(z, z.clone(), H, gravity=G, fixed=fx, newton_rtol=rtol, cg_rtol=cg_rtol,
+                              max_newton=20, max_cg=2000, use_graph=use_graph)
+    torch.cuda.synchronize()
+    return v.cpu().numpy(), rep, mesh
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_free_fall_is_exact(prec, use_graph):
+    wl = beams(2, [3, 4], clamp=False)
+    v, rep, _ = step(wl, prec, use_graph, rtol=1e-10)
+    assert rep["code"] == 0 and rep["status"] == 0
+    assert np.abs(v - H * G).max() < 1e-9 * 9.81 * H
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_clamped_beam_matches_oracle(prec):
+    wl = beams(1, [6], clamp=True)
+    v, rep, _ = step(wl, prec, True, rtol=1e-10, cg_rtol=1e-6)
+    assert rep["status"] == 0 and rep["rel_residual"] <= 1e-10
+    v_ref, rep_ref = oracle.newton_step(wl, np.zeros_like(wl.X), np.zeros_like(wl.X), H, G, fixed=wl.fixed,
+                                        newton_rtol=1e-10, cg_rtol=1e-6)
+    assert rep_ref["status"] == 0
+    assert np.abs(v - v_ref).max() <= 1e-6 * np.abs(v_ref).max()
+    assert np.abs(v[wl.fixed == 1]).max() == 0.0
+
+
+def test_batched_bodies_equal_single_body_solves_and_graph_equals_host_loop():
+    sizes = [3, 5, 8]
+    wl = beams(3, sizes, clamp=True)
+    vb, rep, _ = step(wl, 1, True)
+    assert rep["status"] == 0 and rep["n_bodies_converged"] == 3
+    vh, reph, _ = step(wl, 1, False)
+    assert np.array_equal(vb, vh)
+    assert rep["cg_iters"] == reph["cg_iters"]
+    off = 0
+    for k, c in enumerate(sizes):
+        one = beams(1, [c], clamp=True)
+        v1, r1, _ = step(one, 1, True)
+        n = one.n_nodes
+        assert r1["status"] == 0
+        # same problem, same iterates up to the order of the FP32 operator sums
+        assert np.abs(vb[off:off + n] - v1).max() <= 1e-6 * np.abs(v1).max()
+        off += n
+
+
+def test_step_is_replayable_and_reports_iterations():
+    wl = beams(2, [4, 6], clamp=True)
+    tl = T()
+    mesh = tl.Mesh.from_workload(wl, precision=tl.FP32)
+    z = torch.zeros((wl.n_nodes, 3), dtype=torch.float64, device="cuda")
+    fx = torch.from_numpy(wl.fixed).cuda()
+    v1, r1 = mesh.newton_step(z, z.clone(), H, gravity=G, fixed=fx)
+    v2, r2 = mesh.newton_step(z, z.clone(), H, gravity=G, fixed=fx)
+    assert torch.equal(v1, v2) and r1 == r2
+    assert r1["newton_iters"] >= 1 and r1["cg_iters"] >= 1
+
+
+def test_not_converged_is_reported():
+    wl = beams(1, [6], clamp=True)
+    tl = T()
+    mesh = tl.Mesh.from_workload(wl, precision=tl.FP32)
+    z = torch.zeros((wl.n_nodes, 3), dtype=torch.float64, device="cuda")
+    fx = torch.from_numpy(wl.fixed).cuda()
+    v, rep = mesh.newton_step(z, z.clone(), H, gravity=G, fixed=fx, newton_rtol=1e-14, max_newton=1, max_cg=1)
+    assert rep["code"] == 5 and rep["status"] == 5
