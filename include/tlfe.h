@@ -212,6 +212,16 @@ tlfe_status tlfe_newton_step(tlfe_mesh *mesh, const double *u_n_dev, const doubl
                              const tlfe_step_params *params, double *v_out_dev,
                              tlfe_step_report *report_host, void *stream);
 
+/* Per-body Euclidean norms of a node array (the deterministic FP64 reduction
+ * the Newton step uses for its residual and CG tests, Sec. 7):
+ *   out_dev[b] = sqrt(sum over the nodes k of body b of |x_k|^2)
+ * x_dev: device double [n_nodes][3]; out_dev: device double [n_bodies].
+ * Every body must own one contiguous node range and share no node with another
+ * body (TLFE_E_UNSUPPORTED otherwise). The first call (or the first Newton
+ * step) allocates the reduction workspace of the handle. Stream-ordered; the
+ * result does not depend on the launch configuration. */
+tlfe_status tlfe_body_norms(tlfe_mesh *mesh, const double *x_dev, double *out_dev, void *stream);
+
 /* Thread-local text of the last error (never NULL). */
 const char *tlfe_last_error(void);
 

@@ -673,9 +673,48 @@ static tlfe_status warm(StepCtx &x, cudaStream_t s)
     return TLFE_OK;
 }
 
+// partial of x.x per chunk
+__global__ void k_sq_partials(ChunkArgs c, const double *x, double *partials)
+{
+    __shared__ double sh[32];
+    const int ch = blockIdx.x;
+    double acc = 0.0;
+    for (int i = c.start[ch] + threadIdx.x; i < c.end[ch]; i += blockDim.x) acc += x[i] * x[i];
+    const double s = block_sum(acc, sh);
+    if (threadIdx.x == 0) partials[ch] = s;
+}
+
+__global__ void k_body_norms(int nb, const int32_t *boff, const double *partials, double *out)
+{
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        double s = 0.0;
+        for (int k = boff[b]; k < boff[b + 1]; ++k) s += partials[k];
+        out[b] = sqrt(s);
+    }
+}
+
 }  // namespace tlfe
 
 using namespace tlfe;
+
+extern "C" tlfe_status tlfe_body_norms(tlfe_mesh *m, const double *x, double *out, void *stream)
+{
+    if (!m || !x || !out) return fail(TLFE_E_INVALID, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!m->newton) {
+        tlfe_status st = setup_newton(m, s);
+        if (st != TLFE_OK) {
+            destroy_newton(m);
+            return st;
+        }
+    }
+    NewtonState *ns = m->newton;
+    ChunkArgs c{ns->chunk_start, ns->chunk_end, ns->chunk_body, ns->n_chunks};
+    k_sq_partials<<<ns->n_chunks, RT, 0, s>>>(c, x, ns->partials);
+    k_body_norms<<<1, 1024, 0, s>>>(ns->nb, ns->body_chunk_off, ns->partials, out);
+    NCK(cudaGetLastError());
+    return TLFE_OK;
+}
 
 extern "C" tlfe_status tlfe_newton_step(tlfe_mesh *m, const double *u_n, const double *v_n,
                                         const tlfe_step_params *prm, double *v_out, tlfe_step_report *rep,

@@ -72,7 +72,7 @@ _lib = None
 
 EXPORTS = ["tlfe_create_mesh", "tlfe_destroy_mesh", "tlfe_get_mesh_info", "tlfe_get_colors", "tlfe_sync",
            "tlfe_internal_force", "tlfe_internal_force_host", "tlfe_tangent_matvec", "tlfe_jacobi_diag",
-           "tlfe_vjp", "tlfe_newton_step", "tlfe_last_error", "tlfe_version"]
+           "tlfe_vjp", "tlfe_newton_step", "tlfe_body_norms", "tlfe_last_error", "tlfe_version"]
 
 
 def load(path: str = LIB_PATH) -> C.CDLL:
@@ -97,6 +97,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "tlfe_jacobi_diag": [P, P, P, D, D, D, P, P],
         "tlfe_vjp": [P, P, P, P, P, P, P, P],
         "tlfe_newton_step": [P, P, P, C.POINTER(tlfe_step_params), P, C.POINTER(tlfe_step_report), P],
+        "tlfe_body_norms": [P, P, P, P],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -167,6 +168,7 @@ class Mesh:
         self._h = h
         self.precision = precision
         self.n_nodes = X.shape[0]
+        self._n_bodies = len(materials)
         self.info = self.get_info()
         self._keep = None
 
@@ -278,6 +280,14 @@ class Mesh:
                                _stream(stream)))
         return gu, gud, gth
 
+    def body_norms(self, x, out=None, stream=None):
+        """Per-body 2-norms of a (n_nodes, 3) float64 CUDA tensor."""
+        import torch
+        self._node_array(x, "x", torch.float64)
+        out = torch.empty(self._n_bodies, dtype=torch.float64, device="cuda") if out is None else out
+        _check(load().tlfe_body_norms(self._h, _ptr(x), _ptr(out), _stream(stream)))
+        return out
+
     def newton_step(self, u_n, v_n, h, gravity=(0.0, 0.0, -9.81), fixed=None, newton_rtol=1e-8, cg_rtol=1e-4,
                     max_newton=20, max_cg=1000, use_graph=True, v_out=None, stream=None):
         import torch
@@ -330,6 +340,10 @@ def tlfe_vjp(mesh: Mesh, u, udot, cot, stream=None):
 
 def tlfe_newton_step(mesh: Mesh, u_n, v_n, h, **kw):
     return mesh.newton_step(u_n, v_n, h, **kw)
+
+
+def tlfe_body_norms(mesh: Mesh, x, out=None, stream=None):
+    return mesh.body_norms(x, out=out, stream=stream)
 
 
 def tlfe_sync(mesh: Mesh, stream=None):

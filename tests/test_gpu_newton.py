@@ -103,3 +103,18 @@ def test_not_converged_is_reported():
     fx = torch.from_numpy(wl.fixed).cuda()
     v, rep = mesh.newton_step(z, z.clone(), H, gravity=G, fixed=fx, newton_rtol=1e-14, max_newton=1, max_cg=1)
     assert rep["code"] == 5 and rep["status"] == 5
+
+
+def test_body_norms_match_numpy():
+    wl = beams(3, [3, 5, 4], clamp=False)
+    tl = T()
+    mesh = tl.Mesh.from_workload(wl, precision=tl.FP32)
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal(wl.X.shape)
+    out = mesh.body_norms(torch.from_numpy(x).cuda()).cpu().numpy()
+    body = np.zeros(wl.n_nodes, int)
+    for blk in wl.blocks:
+        for e in range(blk.n_elem):
+            body[blk.conn[e]] = blk.body[e]
+    ref = np.array([np.linalg.norm(x[body == b]) for b in range(3)])
+    assert np.abs(out - ref).max() <= 1e-12 * ref.max()
