@@ -222,6 +222,25 @@ tlfe_status tlfe_newton_step(tlfe_mesh *mesh, const double *u_n_dev, const doubl
  * result does not depend on the launch configuration. */
 tlfe_status tlfe_body_norms(tlfe_mesh *mesh, const double *x_dev, double *out_dev, void *stream);
 
+/* Euclidean norm of a device vector, for callers that cannot allocate device
+ * memory: a process that has reserved its whole device budget up front (a
+ * real-time or embedded control loop, a host application that hands out all
+ * GPU memory from its own pool) or code that must not call cudaMalloc on its
+ * hot path because it synchronises the device and can fail at run time. The
+ * paper has no counterpart; this is the same deterministic chunked FP64
+ * reduction as tlfe_body_norms, without a mesh handle or workspace.
+ *   *out_dev = sqrt(sum_k x_dev[k]^2),  k < n
+ * x_dev: device double [n]; out_dev: device double [1]. n must be at most
+ * 4096 * 4096 = 16,777,216 (TLFE_E_INVALID beyond, with a message naming the
+ * limit): the partial sums live in a fixed 32 KiB array in device memory that
+ * every GPU loading the library holds until the process exits.
+ * Allocates nothing (no cudaMalloc, cudaFree or allocating library routine).
+ * The first call on a device looks up that array's device address, once per
+ * device, so make that first call before any stream capture. All calls share
+ * the array: calls that overlap on the GPU (different streams, or devices
+ * sharing nothing but this library) race; order them on one stream. */
+tlfe_status tlfe_norm_noalloc(const double *x_dev, int64_t n, double *out_dev, void *stream);
+
 /* Thread-local text of the last error (never NULL). */
 const char *tlfe_last_error(void);
 

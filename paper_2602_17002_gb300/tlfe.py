@@ -72,7 +72,7 @@ _lib = None
 
 EXPORTS = ["tlfe_create_mesh", "tlfe_destroy_mesh", "tlfe_get_mesh_info", "tlfe_get_colors", "tlfe_sync",
            "tlfe_internal_force", "tlfe_internal_force_host", "tlfe_tangent_matvec", "tlfe_jacobi_diag",
-           "tlfe_vjp", "tlfe_newton_step", "tlfe_body_norms", "tlfe_last_error", "tlfe_version"]
+           "tlfe_vjp", "tlfe_newton_step", "tlfe_body_norms", "tlfe_norm_noalloc", "tlfe_last_error", "tlfe_version"]
 
 
 def load(path: str = LIB_PATH) -> C.CDLL:
@@ -98,6 +98,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "tlfe_vjp": [P, P, P, P, P, P, P, P],
         "tlfe_newton_step": [P, P, P, C.POINTER(tlfe_step_params), P, C.POINTER(tlfe_step_report), P],
         "tlfe_body_norms": [P, P, P, P],
+        "tlfe_norm_noalloc": [P, C.c_int64, P, P],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -344,6 +345,18 @@ def tlfe_newton_step(mesh: Mesh, u_n, v_n, h, **kw):
 
 def tlfe_body_norms(mesh: Mesh, x, out=None, stream=None):
     return mesh.body_norms(x, out=out, stream=stream)
+
+
+def tlfe_norm_noalloc(x, out, stream=None):
+    """2-norm of the contiguous float64 CUDA tensor x into out (float64, 1 value);
+    allocates nothing on the device."""
+    import torch
+    if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float64 and x.is_contiguous()):
+        raise TLFEError(1, "x must be a contiguous CUDA float64 tensor")
+    if not (isinstance(out, torch.Tensor) and out.is_cuda and out.dtype == torch.float64 and out.numel() >= 1):
+        raise TLFEError(1, "out must be a CUDA float64 tensor with at least one element")
+    _check(load().tlfe_norm_noalloc(_ptr(x), C.c_int64(x.numel()), _ptr(out), _stream(stream)))
+    return out
 
 
 def tlfe_sync(mesh: Mesh, stream=None):

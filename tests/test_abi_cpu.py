@@ -71,8 +71,12 @@ def test_validation_errors_need_no_gpu(lib):
     assert lib.tlfe_create_mesh(C.byref(d), None, C.byref(h)) == 1
 
 
-def test_null_handles_are_rejected(lib):
+def test_null_handles_and_oversized_noalloc_are_rejected(lib):
     assert lib.tlfe_internal_force(None, None, None, None, None) == 1
     assert lib.tlfe_vjp(None, None, None, None, None, None, None, None) == 1
     assert lib.tlfe_sync(None, None, None) == 1
     assert lib.tlfe_destroy_mesh(None) == 0
+    one = C.c_double(0.0)
+    assert lib.tlfe_norm_noalloc(C.byref(one), C.c_int64(4096 * 4096 + 1), C.byref(one), None) == 1
+    assert "exceeds the maximum" in lib.tlfe_last_error().decode()
+    assert lib.tlfe_norm_noalloc(None, C.c_int64(-1), C.byref(one), None) == 1
