@@ -18,9 +18,14 @@
  *     udot = xdot); the nodal unknowns of the paper are x = X_ref + u.
  *   - Element arrays follow the global element numbering: blocks in the order
  *     given at creation, elements of a block in their given order.
- *   - Precision: a mesh created with TLFE_FP32 takes and returns float arrays
- *     in every state/force call (element math in FP32); TLFE_FP64 takes double.
- *     The Newton step state is always double.
+ *   - Precision: the displacement u is always double (FP64), in both
+ *     precisions. A mesh created with TLFE_FP32 does its element math in FP32
+ *     and takes and returns float for every other node array (udot, v, the
+ *     cotangent, forces and products); TLFE_FP64 uses double throughout. FP32
+ *     kernels split u into an FP32 pair (hi, lo) and form element-relative
+ *     differences u_i - u_0 in FP32, so large rigid motions do not cost the
+ *     strain its accuracy (F depends on u only through those differences,
+ *     because sum_i h_i = 0). The Newton step state is always double.
  *   - Pointers named *_dev are CUDA device pointers, *_host host pointers.
  *     The caller owns every pointer it passes; the library never frees them and
  *     keeps none of them after the call returns (create copies what it needs).
@@ -138,13 +143,14 @@ tlfe_status tlfe_sync(tlfe_mesh *mesh, void *stream, int64_t *n_inverted);
 /* Internal force (Sec. 4.3, Eq. internal_force_universal):
  *   f_i = sum_e sum_q w_q J_p P(F_q, Fdot_q) h_{i,q},
  * F = I + sum_i u_i h_i^T, Fdot = sum_i udot_i h_i^T, P = P^e + F S^v.
- * u_dev, udot_dev: device [n_nodes][3] (udot may be NULL: no viscous stress).
- * f_dev: device [n_nodes][3], overwritten. f_int is the restoring force
- * (+dPi/dx). */
+ * u_dev: device double [n_nodes][3]; udot_dev: device [n_nodes][3] in the
+ * mesh dtype, or NULL (no viscous stress). f_dev: device [n_nodes][3] in the
+ * mesh dtype, overwritten. f_int is the restoring force (+dPi/dx). */
 tlfe_status tlfe_internal_force(tlfe_mesh *mesh, const void *u_dev, const void *udot_dev,
                                 void *f_dev, void *stream);
 
-/* Same operation on HOST arrays (pageable or pinned): copies u (and udot) to
+/* Same operation on HOST arrays (pageable or pinned; u double, udot and f in
+ * the mesh dtype): copies u (and udot) to
  * device buffers held by the handle, evaluates, and copies f back, all on
  * `stream`. Synchronises `stream` before returning. */
 tlfe_status tlfe_internal_force_host(tlfe_mesh *mesh, const void *u_host, const void *udot_host,
@@ -153,8 +159,9 @@ tlfe_status tlfe_internal_force_host(tlfe_mesh *mesh, const void *u_host, const 
 /* Matrix-free operator product (App. C; Newton matrix of Sec. 2.2 / Sec. 7):
  *   y = a_M M v + a_K K_t(u, udot) v + a_C C(u) v
  * M: consistent mass m_ij = rho int s_i s_j dV (Sec. 4.1), K_t = d f_int / d x
- * (elastic and viscous), C = d f_int / d xdot (Kelvin-Voigt). All dtype arrays
- * are device [n_nodes][3]; udot may be NULL; y_dev is overwritten.
+ * (elastic and viscous), C = d f_int / d xdot (Kelvin-Voigt). u_dev is device
+ * double [n_nodes][3]; udot_dev, v_dev and y_dev are device [n_nodes][3] in the
+ * mesh dtype; udot may be NULL; y_dev is overwritten.
  * a_M != 0 needs affine elements (straight-edged tetrahedra, parallelepiped
  * bricks): TLFE_E_UNSUPPORTED otherwise. */
 tlfe_status tlfe_tangent_matvec(tlfe_mesh *mesh, const void *u_dev, const void *udot_dev,
@@ -167,10 +174,18 @@ tlfe_status tlfe_tangent_matvec(tlfe_mesh *mesh, const void *u_dev, const void *
 tlfe_status tlfe_jacobi_diag(tlfe_mesh *mesh, const void *u_dev, const void *udot_dev,
                              double a_M, double a_K, double a_C, void *d_dev, void *stream);
 
+/* Replace the per-element Lame parameters (mu_e, lambda_e) of every element
+ * (device double [n_elem][2], global element order); later calls use them in
+ * place of the body materials' (mu, lambda). The first call on a handle created
+ * without elem_mu_lambda allocates the per-element copy. Stream-ordered; the
+ * caller's array is not kept. */
+tlfe_status tlfe_set_elem_mu_lambda(tlfe_mesh *mesh, const double *mu_lambda_dev, void *stream);
+
 /* Vector-Jacobian products of f_int against a cotangent r:
  *   g_u = K_t^T r,   g_udot = C^T r,
  *   g_mu_lambda[e] = (r . d f / d mu_e, r . d f / d lambda_e)
- * cot_dev, g_u_dev, g_udot_dev: device [n_nodes][3] in the mesh dtype;
+ * u_dev: device double [n_nodes][3]; udot_dev, cot_dev, g_u_dev, g_udot_dev:
+ * device [n_nodes][3] in the mesh dtype;
  * g_mu_lambda_dev: device double [n_elem][2]. Any output may be NULL (not
  * computed); non-NULL outputs are overwritten. */
 tlfe_status tlfe_vjp(tlfe_mesh *mesh, const void *u_dev, const void *udot_dev, const void *cot_dev,

@@ -217,7 +217,7 @@ def block_materials(wl, bi):
     return m
 
 
-def internal_force(wl, u=None, udot="state", kin_form=1, mats=None):
+def internal_force(wl, u=None, udot="state", kin_form=2, mats=None):
     """Assembled f_int (Eq. internal_force_universal); returns (f, n_inverted)."""
     u = _f64(wl.u if u is None else u)
     udot = _f64(wl.udot if isinstance(udot, str) else udot)

@@ -302,13 +302,16 @@ int orc_exact_rule(int type, int order, double *pts, double *w)
 /* Section 6: reference precompute                                           */
 /* ------------------------------------------------------------------------ */
 
-/* dU/dxi = U Hp(xi) (3x3), with U = [u_1 .. u_n] the reference node matrix */
+/* dU/dxi = U Hp(xi) (3x3), with U = [u_1 .. u_n] the reference node matrix
+ * (Sec. 6). Evaluated as sum_{i>1} (u_i - u_1) (dS_i/dxi)^T, equal because the
+ * parent gradients sum to zero (sum_i s_i = 1, App. A); node coordinates far
+ * from the origin then cost no digits. */
 static void parent_jacobian(int n, const double *Xe, const double *Hp, double Jp[9])
 {
     for (int a = 0; a < 3; ++a)
         for (int k = 0; k < 3; ++k) {
             double s = 0.0;
-            for (int i = 0; i < n; ++i) s += Xe[i * 3 + a] * Hp[i * 3 + k];
+            for (int i = 1; i < n; ++i) s += (Xe[i * 3 + a] - Xe[a]) * Hp[i * 3 + k];
             Jp[a * 3 + k] = s;
         }
 }
@@ -468,7 +471,13 @@ int orc_strain_energy(const orc_material *m, const double F[9], double *psi)
 /* Section 2.1 / Eq. (expression-F): kinematics at one quadrature point       */
 /* ------------------------------------------------------------------------ */
 
-/* He: [n][3] = h_i; Xe, ue: [n][3]. */
+/* He: [n][3] = h_i; Xe, ue: [n][3].
+ * kin_form 0: F = sum_i x_i h_i^T, x = X + u (Eq. expression-F as printed);
+ * kin_form 1: F = I + sum_i u_i h_i^T (U H = I, Sec. 6);
+ * kin_form 2: F = I + sum_i (u_i - u_1) h_i^T (also sum_i h_i = 0, the
+ *             gradient of the partition of unity sum_i s_i = 1). The three are
+ *             equal in exact arithmetic; 2 rounds least when the element moves
+ *             far from its reference position. */
 static void deformation_gradient(int n, const double *He, const double *Xe, const double *ue,
                                  int kin_form, double F[9])
 {
@@ -478,8 +487,11 @@ static void deformation_gradient(int n, const double *He, const double *Xe, cons
             if (kin_form == 0) {
                 for (int i = 0; i < n; ++i) s += (Xe[i * 3 + a] + ue[i * 3 + a]) * He[i * 3 + c];
                 F[a * 3 + c] = s;
-            } else {
+            } else if (kin_form == 1) {
                 for (int i = 0; i < n; ++i) s += ue[i * 3 + a] * He[i * 3 + c];
+                F[a * 3 + c] = (a == c ? 1.0 : 0.0) + s;
+            } else {
+                for (int i = 1; i < n; ++i) s += (ue[i * 3 + a] - ue[a]) * He[i * 3 + c];
                 F[a * 3 + c] = (a == c ? 1.0 : 0.0) + s;
             }
         }
@@ -707,7 +719,7 @@ static int element_matrices_sel(int type, int nq, const int32_t *ce, const doubl
     int bad = 0;
     for (int q = 0; q < nq; ++q) {
         const double *He = g.H + q * n * 3;
-        deformation_gradient(n, He, Xe, ue, 1, F);
+        deformation_gradient(n, He, Xe, ue, 2, F);
         if (udot) rate_gradient(n, He, vde, Fd);
         else memset(Fd, 0, sizeof(Fd));
         const double wq = g.wJ[q];
@@ -896,7 +908,7 @@ int orc_vjp(int type, int nq, int n_elem, const int32_t *conn, int n_nodes,
             double gm = 0.0, gl = 0.0;
             for (int q = 0; q < nq; ++q) {
                 const double *He = g.H + q * n * 3;
-                deformation_gradient(n, He, Xe, ue, 1, F);
+                deformation_gradient(n, He, Xe, ue, 2, F);
                 if (stress_param_derivs(mat + e, F, dmu, dlam) < 0) return -1;
                 for (int i = 0; i < n; ++i) {
                     double a[3], b[3];
@@ -996,7 +1008,7 @@ static int residual(const step_ctx *c, const double *u_n, const double *v_n, con
                                 NULL, c->mat, 1.0 / h, 0.0, 0.0, 0, 1, dv, g);
     if (st < 0) return st;
     int st2 = orc_internal_force(c->type, c->nq, c->n_elem, c->conn, c->n_nodes, c->X, u_tmp, v,
-                                 c->mat, 1, g);
+                                 c->mat, 2, g);
     if (st2 < 0) return st2;
     project(c, g);
     return st + st2;

@@ -57,7 +57,9 @@ int orc_strain_energy(const orc_material *m, const double F[9], double *psi);
 
 /* ---- kinematics + internal force, Eq. (internal_force_universal) ------ */
 /* kin_form 0: F = sum_i x_i h_i^T with x = X + u (the paper's literal form)
- * kin_form 1: F = I + sum_i u_i h_i^T (same quantity, using U H = I).      */
+ * kin_form 1: F = I + sum_i u_i h_i^T (same quantity, using U H = I)
+ * kin_form 2: F = I + sum_i (u_i - u_1) h_i^T (same, using sum_i h_i = 0);
+ *             used by every other oracle routine.                          */
 int orc_internal_force(int type, int nq, int n_elem, const int32_t *conn, int n_nodes,
                        const double *X, const double *u, const double *udot,
                        const orc_material *mat, int kin_form, double *f);

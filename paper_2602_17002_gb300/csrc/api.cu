@@ -480,12 +480,13 @@ extern "C" tlfe_status tlfe_get_mesh_info(const tlfe_mesh *m, tlfe_mesh_info *in
         if (B.d_emat) eb += (int64_t)B.n_elem * 4;
         if (B.d_elam) eb += (int64_t)B.n_elem * 2 * rs;
     }
-    const int64_t nb = (int64_t)m->n_nodes * 3 * rs;
+    const int64_t nb = (int64_t)m->n_nodes * 3 * rs;    // one node array in the mesh precision
+    const int64_t nu = (int64_t)m->n_nodes * 3 * 8;     // the FP64 displacement
     bool visc = false;
     for (auto &B : m->blocks) visc = visc || B.visc;
-    info->stream_bytes_force = eb + nb * (visc ? 3 : 2);          // u (+udot) read, f written
-    info->stream_bytes_matvec = eb + nb * (visc ? 4 : 3);         // + v read
-    info->stream_bytes_vjp = eb + nb * (visc ? 5 : 3) + (int64_t)m->n_elem * 16;  // u, udot, r; g_u, g_udot; g_theta
+    info->stream_bytes_force = eb + nu + nb * (visc ? 2 : 1);           // u (+udot) read, f written
+    info->stream_bytes_matvec = eb + nu + nb * (visc ? 3 : 2);          // + v read
+    info->stream_bytes_vjp = eb + nu + nb * (visc ? 4 : 2) + (int64_t)m->n_elem * 16;  // u, udot, r; g_u, g_udot; g_theta
     info->device_bytes = m->device_bytes;
     return TLFE_OK;
 }
@@ -576,7 +577,7 @@ tlfe_status run_op(tlfe_mesh *m, const void *u, const void *ud, const void *v, v
 {
     KParams<R> p;
     memset(&p, 0, sizeof(p));
-    p.u = (const R *)u;
+    p.u = (const double *)u;
     p.ud = (const R *)ud;
     p.v = (const R *)v;
     p.out0 = (R *)out0;
@@ -641,9 +642,10 @@ extern "C" tlfe_status tlfe_internal_force_host(tlfe_mesh *m, const void *u_h, c
     if (st != TLFE_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     const size_t nb = (size_t)3 * m->n_nodes * (m->precision == TLFE_FP32 ? 4 : 8);
-    if (!m->d_stage) CKA(m->d_stage, 3 * nb, m);
-    char *du = (char *)m->d_stage, *dud = du + nb, *df = du + 2 * nb;
-    CK(cudaMemcpyAsync(du, u_h, nb, cudaMemcpyHostToDevice, s));
+    const size_t nu = (size_t)3 * m->n_nodes * 8;  // the displacement is FP64 in both precisions
+    if (!m->d_stage) CKA(m->d_stage, nu + 2 * nb, m);
+    char *du = (char *)m->d_stage, *dud = du + nu, *df = dud + nb;
+    CK(cudaMemcpyAsync(du, u_h, nu, cudaMemcpyHostToDevice, s));
     if (ud_h) CK(cudaMemcpyAsync(dud, ud_h, nb, cudaMemcpyHostToDevice, s));
     st = tlfe_internal_force(m, du, ud_h ? dud : nullptr, df, stream);
     if (st != TLFE_OK) return st;
@@ -690,6 +692,23 @@ extern "C" tlfe_status tlfe_vjp(tlfe_mesh *m, const void *u, const void *ud, con
     return m->precision == TLFE_FP32
                ? run_op<OP_VJP, float>(m, u, ud, cot, o0, o1, g_th, 0, 1, 0, 0, s)
                : run_op<OP_VJP, double>(m, u, ud, cot, o0, o1, g_th, 0, 1, 0, 0, s);
+}
+
+extern "C" tlfe_status tlfe_set_elem_mu_lambda(tlfe_mesh *m, const double *mu_lambda_dev, void *stream)
+{
+    tlfe_status st = check_mesh_args(m, {mu_lambda_dev});
+    if (st != TLFE_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t rs = m->precision == TLFE_FP32 ? 4 : 8;
+    for (auto &B : m->blocks) {
+        if (B.n_tiles == 0) continue;
+        if (!B.d_elam) CKA(B.d_elam, rs * (size_t)B.n_tiles * TILE * 2, m);
+        cudaError_t e = launch_set_elam(m->precision, B.n_tiles, B.d_eid, mu_lambda_dev, B.d_elam, s);
+        if (e != cudaSuccess) return cuda_fail(e, "tlfe_set_elem_mu_lambda");
+    }
+    // keep the FP64 twin used by the Newton step consistent
+    if (tlfe_mesh *tw = newton_twin(m)) return tlfe_set_elem_mu_lambda(tw, mu_lambda_dev, stream);
+    return TLFE_OK;
 }
 
 extern "C" const char *tlfe_last_error(void) { return tlfe::g_err.c_str(); }

@@ -92,8 +92,17 @@ template <int OP> struct OpFields {
     static constexpr int OUT = op_nf(OP) - IN;    // output values per node
     static constexpr int NFI = IN / 3;            // input vector fields per node
     static constexpr int NFO = OUT / 3;           // output vector fields per node
-    static constexpr int REC = 4 * NFI;           // patch record (values) of one node: 16-byte aligned vectors
-    static constexpr int RECO = 4 * NFO;
+};
+
+// Patch record of one node: 16-byte aligned 4-vectors of R. The displacement
+// arrives in FP64; FP32 kernels keep it as an unevaluated pair (hi, lo) with
+// hi = fl32(u), lo = fl32(u - hi), so that element-relative differences
+// u_i - u_0 are formed without the rounding of |u| (large rigid motions).
+template <int OP, typename R> struct Rec {
+    static constexpr int NU = sizeof(R) == 4 ? 2 : 1;          // vectors holding u
+    static constexpr int OFF_UD = 4 * NU;                       // udot
+    static constexpr int OFF_V = 4 * (NU + 1);                  // direction / cotangent
+    static constexpr int REC = 4 * (NU + OpFields<OP>::NFI - 1);
 };
 
 constexpr int NSLICE = 2;  // ring depth per warp (quadrature-point slices)
@@ -111,7 +120,7 @@ template <int ET, typename R> struct Slice {
 template <int ET, typename R, int OP>
 __host__ __device__ constexpr size_t warp_region_bytes(int umax, int meta_bytes)
 {
-    const size_t patch = (size_t)umax * OpFields<OP>::REC * sizeof(R);
+    const size_t patch = (size_t)umax * Rec<OP, R>::REC * sizeof(R);
     const size_t slots = (size_t)OpFields<OP>::NFO * Elem<ET>::NPE * 32 * 3 * sizeof(R);
     return ((size_t)NSLICE * Slice<ET, R>::BYTES + 2 * (size_t)meta_bytes + (patch > slots ? patch : slots) + 127) /
            128 * 128;
@@ -160,10 +169,12 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 }
 
 template <int ET, int NQ, typename R, int OP>
-__global__ void __launch_bounds__(128, sizeof(R) == 4 ? (OP == OP_FORCE ? 4 : 3) : 1) k_elem(const KParams<R> p)
+__global__ void __launch_bounds__(128, sizeof(R) == 4 ? 3 : 1) k_elem(const KParams<R> p)
 {
     constexpr int NPE = Elem<ET>::NPE;
-    constexpr int REC = OpFields<OP>::REC;
+    constexpr int REC = Rec<OP, R>::REC;
+    constexpr int OFF_UD = Rec<OP, R>::OFF_UD;
+    constexpr int OFF_V = Rec<OP, R>::OFF_V;
     constexpr int NFO = OpFields<OP>::NFO;
     constexpr bool HAS_V = OpFields<OP>::NFI == 3;
     using SL = Slice<ET, R>;
@@ -235,9 +246,16 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? (OP == OP_FORCE ? 4 : 3)
         for (int kk = lane; kk < U; kk += 32) {
             const int64_t n = nodes[kk];
             R *rec = work + (size_t)kk * REC;
-            st3(rec, __ldg(p.u + 3 * n), __ldg(p.u + 3 * n + 1), __ldg(p.u + 3 * n + 2));
-            if (need_ud) st3(rec + 4, __ldg(p.ud + 3 * n), __ldg(p.ud + 3 * n + 1), __ldg(p.ud + 3 * n + 2));
-            if (HAS_V) st3(rec + 8, __ldg(p.v + 3 * n), __ldg(p.v + 3 * n + 1), __ldg(p.v + 3 * n + 2));
+            const double ux = __ldg(p.u + 3 * n), uy = __ldg(p.u + 3 * n + 1), uz = __ldg(p.u + 3 * n + 2);
+            if (sizeof(R) == 4) {
+                const float hx = float(ux), hy = float(uy), hz = float(uz);
+                st3(rec, R(hx), R(hy), R(hz));
+                st3(rec + 4, R(float(ux - double(hx))), R(float(uy - double(hy))), R(float(uz - double(hz))));
+            } else {
+                st3(rec, R(ux), R(uy), R(uz));
+            }
+            if (need_ud) st3(rec + OFF_UD, __ldg(p.ud + 3 * n), __ldg(p.ud + 3 * n + 1), __ldg(p.ud + 3 * n + 2));
+            if (HAS_V) st3(rec + OFF_V, __ldg(p.v + 3 * n), __ldg(p.v + 3 * n + 1), __ldg(p.v + 3 * n + 2));
         }
         int li[NPE];
 #pragma unroll
@@ -252,6 +270,22 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? (OP == OP_FORCE ? 4 : 3)
         const bool visc = need_ud && (m.mu_v != R(0) || m.lam_v != R(0));
         __syncwarp();
 
+        // element-relative displacements d_i = u_i - u_0 (sum_i h_i = 0, so
+        // G = sum_i u_i h_i^T = sum_{i>0} d_i h_i^T, with rigid translation removed exactly)
+        R dd[NPE][3];
+        {
+            R h0v[3], l0v[3] = {R(0), R(0), R(0)};
+            ld3(work + li[0] * REC, h0v[0], h0v[1], h0v[2]);
+            if (sizeof(R) == 4) ld3(work + li[0] * REC + 4, l0v[0], l0v[1], l0v[2]);
+#pragma unroll
+            for (int i = 1; i < NPE; ++i) {
+                R hv[3], lv[3] = {R(0), R(0), R(0)};
+                ld3(work + li[i] * REC, hv[0], hv[1], hv[2]);
+                if (sizeof(R) == 4) ld3(work + li[i] * REC + 4, lv[0], lv[1], lv[2]);
+#pragma unroll
+                for (int a = 0; a < 3; ++a) dd[i][a] = (hv[a] - h0v[a]) + (lv[a] - l0v[a]);
+            }
+        }
         R acc0[NPE][3], acc1[NPE][3];
 #pragma unroll
         for (int i = 0; i < NPE; ++i)
@@ -275,7 +309,7 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? (OP == OP_FORCE ? 4 : 3)
             const R *sl = reinterpret_cast<const R *>(ring + (size_t)b * SL::BYTES) + lane;
             const R w = sl[NPE * 3 * 32];
 
-            // kinematics: G = sum u_i h_i^T, Fd = sum udot_i h_i^T, D = sum v_i h_i^T
+            // kinematics: G = sum d_i h_i^T, Fd = sum udot_i h_i^T, D = sum v_i h_i^T
             QP<R> s1;
             R D[9];
 #pragma unroll
@@ -289,15 +323,16 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? (OP == OP_FORCE ? 4 : 3)
                 const R h0 = sl[(i * 3 + 0) * 32], h1 = sl[(i * 3 + 1) * 32], h2 = sl[(i * 3 + 2) * 32];
                 const R *rec = work + li[i] * REC;
                 R x[3];
-                ld3(rec, x[0], x[1], x[2]);
+                if (i > 0) {
 #pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    s1.G[a * 3 + 0] += x[a] * h0;
-                    s1.G[a * 3 + 1] += x[a] * h1;
-                    s1.G[a * 3 + 2] += x[a] * h2;
+                    for (int a = 0; a < 3; ++a) {
+                        s1.G[a * 3 + 0] += dd[i][a] * h0;
+                        s1.G[a * 3 + 1] += dd[i][a] * h1;
+                        s1.G[a * 3 + 2] += dd[i][a] * h2;
+                    }
                 }
                 if (visc) {
-                    ld3(rec + 4, x[0], x[1], x[2]);
+                    ld3(rec + OFF_UD, x[0], x[1], x[2]);
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
                         s1.Fd[a * 3 + 0] += x[a] * h0;
@@ -306,7 +341,7 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? (OP == OP_FORCE ? 4 : 3)
                     }
                 }
                 if (HAS_V) {
-                    ld3(rec + 8, x[0], x[1], x[2]);
+                    ld3(rec + OFF_V, x[0], x[1], x[2]);
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
                         D[a * 3 + 0] += x[a] * h0;
@@ -387,7 +422,7 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? (OP == OP_FORCE ? 4 : 3)
 #pragma unroll
                 for (int jn = 0; jn < NPE; ++jn) {
                     R x[3];
-                    ld3(work + li[jn] * REC + 8, x[0], x[1], x[2]);
+                    ld3(work + li[jn] * REC + OFF_V, x[0], x[1], x[2]);
 #pragma unroll
                     for (int i = 0; i < NPE; ++i) {
                         const R mh = c * R(mass_hat(ET, i, jn));

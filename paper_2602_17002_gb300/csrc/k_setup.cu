@@ -44,11 +44,14 @@ __global__ void k_precompute(int et, int nq, int npe, int n_tiles, const int32_t
         double xi[3], w, g[30];
         quad_point(et, nq, q, xi, w);
         parent_grad(et, xi, g);
+        // Jp = sum_{i>0} (X_i - X_0) dS_i/dxi^T: equal to U Hp since the parent
+        // gradients sum to zero; relative coordinates keep the digits that
+        // large absolute coordinates would cancel away
         double J[9];
         for (int a = 0; a < 3; ++a)
             for (int k = 0; k < 3; ++k) {
                 double s = 0.0;
-                for (int i = 0; i < npe; ++i) s += Xe[i][a] * g[i * 3 + k];
+                for (int i = 1; i < npe; ++i) s += (Xe[i][a] - Xe[0][a]) * g[i * 3 + k];
                 J[a * 3 + k] = s;
             }
         const double c00 = J[4] * J[8] - J[5] * J[7];
@@ -122,6 +125,32 @@ cudaError_t launch_precompute(int et, int nq, int precision, int n_tiles, const 
     else
         k_precompute<double><<<grid, tpb, 0, s>>>(et, nq, npe, n_tiles, eid, conn_elem, elem_base, X,
                                                   (double *)slab, (double *)evol, affine_flag, status);
+    return cudaGetLastError();
+}
+
+// per-element (mu, lambda) from a device array in global element order into the
+// block's AoSoA copy [tile][2][32]
+template <typename R>
+__global__ void k_set_elam(int n_slots, const int32_t *__restrict__ eid, const double *__restrict__ src,
+                           R *__restrict__ elam)
+{
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n_slots) return;
+    const int t = idx >> 5, lane = idx & 31;
+    const int e = eid[idx];
+    elam[((size_t)t * 2 + 0) * 32 + lane] = e >= 0 ? R(src[(size_t)e * 2 + 0]) : R(0);
+    elam[((size_t)t * 2 + 1) * 32 + lane] = e >= 0 ? R(src[(size_t)e * 2 + 1]) : R(0);
+}
+
+cudaError_t launch_set_elam(int precision, int n_tiles, const int32_t *eid, const double *src, void *elam,
+                            cudaStream_t s)
+{
+    const int n = n_tiles * 32;
+    if (n == 0) return cudaSuccess;
+    if (precision == TLFE_FP32)
+        k_set_elam<float><<<(n + 255) / 256, 256, 0, s>>>(n, eid, src, (float *)elam);
+    else
+        k_set_elam<double><<<(n + 255) / 256, 256, 0, s>>>(n, eid, src, (double *)elam);
     return cudaGetLastError();
 }
 

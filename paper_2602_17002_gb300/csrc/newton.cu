@@ -66,7 +66,7 @@ struct NewtonState {
            *fff = nullptr, *y1 = nullptr, *y2 = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr,
            *Ap = nullptr, *Dinv = nullptr, *gv = nullptr, *Dd = nullptr;
     // mesh-precision vectors [3N]
-    float *u32 = nullptr, *ud32 = nullptr, *p32 = nullptr, *Ap32 = nullptr, *D32 = nullptr;
+    float *ud32 = nullptr, *p32 = nullptr, *Ap32 = nullptr, *D32 = nullptr;
     uint8_t *fixed = nullptr;  // [N], 1 = clamped (nodes outside every element included)
     double *partials = nullptr;  // [2][n_chunks]
     double *sc = nullptr;        // [S_COUNT][nb]
@@ -454,7 +454,7 @@ static tlfe_status setup_newton(tlfe_mesh *m, cudaStream_t s)
     for (double **q : {&ns->u_n, &ns->v_n, &ns->v, &ns->u_cur, &ns->dv, &ns->g, &ns->fff, &ns->y1, &ns->y2, &ns->x,
                        &ns->r, &ns->z, &ns->p, &ns->Ap, &ns->Dinv, &ns->gv, &ns->Dd})
         NA(*q, N3);
-    for (float **q : {&ns->u32, &ns->ud32, &ns->p32, &ns->Ap32, &ns->D32}) NA(*q, N3);
+    for (float **q : {&ns->ud32, &ns->p32, &ns->Ap32, &ns->D32}) NA(*q, N3);
     NA(ns->fixed, (size_t)N);
     NA(ns->partials, 2 * (size_t)ns->n_chunks);
     NA(ns->sc, (size_t)S_COUNT * ns->nb);
@@ -508,7 +508,7 @@ static tlfe_status enq_residual(const StepCtx &x, cudaStream_t s)
     tlfe_mesh *m64 = ns->twin ? ns->twin : x.m;
     const int nc = ns->n_chunks;
     if (x.m->precision == TLFE_FP32)
-        k_prep<float><<<nc, RT, 0, s>>>(x.c, ns->h, ns->u_n, ns->v, ns->v_n, ns->u_cur, ns->dv, ns->u32, ns->ud32);
+        k_prep<float><<<nc, RT, 0, s>>>(x.c, ns->h, ns->u_n, ns->v, ns->v_n, ns->u_cur, ns->dv, nullptr, ns->ud32);
     else
         k_prep<double><<<nc, RT, 0, s>>>(x.c, ns->h, ns->u_n, ns->v, ns->v_n, ns->u_cur, ns->dv, nullptr, nullptr);
     NCK(cudaGetLastError());
@@ -531,7 +531,7 @@ static tlfe_status enq_cg_init(const StepCtx &x, cudaStream_t s)
     const double h = ns->h;
     tlfe_status st;
     if (x.m->precision == TLFE_FP32) {
-        st = run_op<OP_DIAG, float>(x.m, ns->u32, ns->ud32, nullptr, ns->D32, nullptr, nullptr, 1.0 / h, h, 1.0, 1, s);
+        st = run_op<OP_DIAG, float>(x.m, ns->u_cur, ns->ud32, nullptr, ns->D32, nullptr, nullptr, 1.0 / h, h, 1.0, 1, s);
         if (st != TLFE_OK) return st;
         k_dinv<float><<<nc, RT, 0, s>>>(x.c, ns->D32, ns->fixed, ns->sc, ns->nb, ns->Dinv);
     } else {
@@ -554,8 +554,8 @@ static tlfe_status enq_cg_iter(const StepCtx &x, cudaStream_t s)
     tlfe_status st;
     if (x.m->precision == TLFE_FP32) {
         k_to_lo<float><<<nc, RT, 0, s>>>(x.c, ns->p, ns->p32);
-        st = run_op<OP_MATVEC, float>(x.m, ns->u32, ns->ud32, ns->p32, ns->Ap32, nullptr, nullptr, 1.0 / h, h, 1.0, 1,
-                                      s);
+        st = run_op<OP_MATVEC, float>(x.m, ns->u_cur, ns->ud32, ns->p32, ns->Ap32, nullptr, nullptr, 1.0 / h, h, 1.0,
+                                      1, s);
         if (st != TLFE_OK) return st;
         k_cg_pap<float><<<nc, RT, 0, s>>>(x.c, ns->Ap32, ns->fixed, ns->p, ns->Ap, ns->partials);
     } else {
@@ -696,6 +696,10 @@ __global__ void k_body_norms(int nb, const int32_t *boff, const double *partials
 }  // namespace tlfe
 
 using namespace tlfe;
+
+namespace tlfe {
+tlfe_mesh *newton_twin(tlfe_mesh *m) { return m->newton ? m->newton->twin : nullptr; }
+}  // namespace tlfe
 
 extern "C" tlfe_status tlfe_body_norms(tlfe_mesh *m, const double *x, double *out, void *stream)
 {

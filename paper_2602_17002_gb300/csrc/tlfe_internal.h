@@ -47,7 +47,8 @@ template <typename R> struct KParams {
     Mat<R> mat0;
     const Mat<R> *mats;
     // state and outputs ([n_nodes][3] arrays)
-    const R *u, *ud, *v;
+    const double *u;            // displacement, always FP64 (see Rec in k_elem.cuh)
+    const R *ud, *v;
     R *out0, *out1;
     double *gth;                // [n_elem][2] (VJP parameter gradient)
     R aM, aK, aC;
@@ -75,6 +76,8 @@ int occupancy_op(int et, int nq, int umax, int meta_bytes, int *wpb, std::string
 cudaError_t launch_precompute(int et, int nq, int precision, int n_tiles, const int32_t *eid,
                               const int32_t *conn_elem, int elem_base, const double *X, void *slab,
                               void *evol, int *affine_flag, int *status, cudaStream_t s);
+cudaError_t launch_set_elam(int precision, int n_tiles, const int32_t *eid, const double *src, void *elam,
+                            cudaStream_t s);
 cudaError_t launch_color_round(int n_elem, int npe, const int32_t *conn, const int32_t *inc_off,
                                const int32_t *inc, const int32_t *elem_local_to_block,
                                uint64_t seed, int elem_base, int32_t *color, int *n_left,

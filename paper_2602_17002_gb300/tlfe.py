@@ -72,7 +72,7 @@ _lib = None
 
 EXPORTS = ["tlfe_create_mesh", "tlfe_destroy_mesh", "tlfe_get_mesh_info", "tlfe_get_colors", "tlfe_sync",
            "tlfe_internal_force", "tlfe_internal_force_host", "tlfe_tangent_matvec", "tlfe_jacobi_diag",
-           "tlfe_vjp", "tlfe_newton_step", "tlfe_body_norms", "tlfe_norm_noalloc", "tlfe_last_error", "tlfe_version"]
+           "tlfe_vjp", "tlfe_set_elem_mu_lambda", "tlfe_newton_step", "tlfe_body_norms", "tlfe_norm_noalloc", "tlfe_last_error", "tlfe_version"]
 
 
 def load(path: str = LIB_PATH) -> C.CDLL:
@@ -98,6 +98,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "tlfe_vjp": [P, P, P, P, P, P, P, P],
         "tlfe_newton_step": [P, P, P, C.POINTER(tlfe_step_params), P, C.POINTER(tlfe_step_report), P],
         "tlfe_body_norms": [P, P, P, P],
+        "tlfe_set_elem_mu_lambda": [P, P, P],
         "tlfe_norm_noalloc": [P, C.c_int64, P, P],
     }
     for name, args in sig.items():
@@ -231,16 +232,22 @@ class Mesh:
         return n.value
 
     def internal_force(self, u, udot=None, out=None, stream=None):
-        self._node_array(u, "u")
+        """u: (n_nodes, 3) float64 displacement (FP64 in both precisions); udot
+        and the returned force are in the mesh dtype."""
+        import torch
+        self._node_array(u, "u", torch.float64)
         self._node_array(udot, "udot")
         out = self._new() if out is None else self._node_array(out, "out")
         _check(load().tlfe_internal_force(self._h, _ptr(u), _ptr(udot), _ptr(out), _stream(stream)))
         return out
 
     def internal_force_host(self, u: np.ndarray, udot: Optional[np.ndarray], out: np.ndarray, stream=None):
-        """Host-buffer call: u, udot, out are contiguous numpy arrays (n_nodes, 3)."""
+        """Host-buffer call: u (float64), udot and out (mesh dtype) are contiguous
+        numpy arrays of shape (n_nodes, 3)."""
         dt = np.float32 if self.precision == FP32 else np.float64
-        for a in (u, udot, out):
+        if u.dtype != np.float64 or not u.flags.c_contiguous or u.shape != (self.n_nodes, 3):
+            raise TLFEError(1, "u must be a contiguous float64 (n_nodes, 3) array")
+        for a in (udot, out):
             if a is not None and (a.dtype != dt or not a.flags.c_contiguous or a.shape != (self.n_nodes, 3)):
                 raise TLFEError(1, "host arrays must be contiguous (n_nodes, 3) of the mesh dtype")
         _check(load().tlfe_internal_force_host(self._h, u.ctypes.data, None if udot is None else udot.ctypes.data,
@@ -253,7 +260,8 @@ class Mesh:
                                                C.c_void_p(out_ptr), _stream(stream)))
 
     def tangent_matvec(self, u, udot, v, a_M=0.0, a_K=1.0, a_C=0.0, out=None, stream=None):
-        self._node_array(u, "u")
+        import torch
+        self._node_array(u, "u", torch.float64)
         self._node_array(udot, "udot")
         self._node_array(v, "v")
         out = self._new() if out is None else self._node_array(out, "out")
@@ -262,16 +270,25 @@ class Mesh:
         return out
 
     def jacobi_diag(self, u, udot=None, a_M=0.0, a_K=1.0, a_C=0.0, out=None, stream=None):
-        self._node_array(u, "u")
+        import torch
+        self._node_array(u, "u", torch.float64)
         self._node_array(udot, "udot")
         out = self._new() if out is None else self._node_array(out, "out")
         _check(load().tlfe_jacobi_diag(self._h, _ptr(u), _ptr(udot), float(a_M), float(a_K), float(a_C),
                                        _ptr(out), _stream(stream)))
         return out
 
+    def set_elem_mu_lambda(self, theta, stream=None):
+        """theta: contiguous CUDA float64 tensor (n_elem, 2) of per-element (mu, lambda)."""
+        import torch
+        if not (theta.is_cuda and theta.dtype == torch.float64 and theta.is_contiguous()
+                and tuple(theta.shape) == (self.info["n_elem"], 2)):
+            raise TLFEError(1, f"theta must be a contiguous CUDA float64 tensor ({self.info['n_elem']}, 2)")
+        _check(load().tlfe_set_elem_mu_lambda(self._h, _ptr(theta), _stream(stream)))
+
     def vjp(self, u, udot, cot, want_u=True, want_udot=True, want_theta=True, stream=None):
         import torch
-        self._node_array(u, "u")
+        self._node_array(u, "u", torch.float64)
         self._node_array(udot, "udot")
         self._node_array(cot, "cot")
         gu = self._new() if want_u else None
@@ -337,6 +354,10 @@ def tlfe_jacobi_diag(mesh: Mesh, u, udot, a_M, a_K, a_C, d, stream=None):
 
 def tlfe_vjp(mesh: Mesh, u, udot, cot, stream=None):
     return mesh.vjp(u, udot, cot, stream=stream)
+
+
+def tlfe_set_elem_mu_lambda(mesh: Mesh, theta, stream=None):
+    return mesh.set_elem_mu_lambda(theta, stream=stream)
 
 
 def tlfe_newton_step(mesh: Mesh, u_n, v_n, h, **kw):

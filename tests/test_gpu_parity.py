@@ -37,7 +37,7 @@ def run_all(wl, prec, scatter=0, aM=0.0, aK=1.0, aC=0.0, diag=True):
     tl = T()
     mesh = tl.Mesh.from_workload(wl, precision=prec, scatter=scatter)
     dt = mesh.torch_dtype
-    u, ud, v = dev(wl.u, dt), dev(wl.udot, dt), dev(wl.v, dt)
+    u, ud, v = dev(wl.u, torch.float64), dev(wl.udot, dt), dev(wl.v, dt)
     out = {"f": mesh.internal_force(u, ud), "y": mesh.tangent_matvec(u, ud, v, aM, aK, aC)}
     out["gu"], out["gud"], out["gth"] = mesh.vjp(u, ud, v)
     if diag:
@@ -124,7 +124,7 @@ def test_colour_scatter_matches_oracle_greedy_and_is_deterministic():
     assert np.array_equal(col, ref)
     assert mesh.info["n_colors"] == nc
     dt = mesh.torch_dtype
-    u, ud = dev(wl.u, dt), dev(wl.udot, dt)
+    u, ud = dev(wl.u, torch.float64), dev(wl.udot, dt)
     f1 = mesh.internal_force(u, ud).cpu().numpy()
     f2 = mesh.internal_force(u, ud).cpu().numpy()
     assert np.array_equal(f1.view(np.uint32), f2.view(np.uint32))
@@ -162,9 +162,44 @@ def test_host_buffer_call_matches_device_call():
     wl = synth.small_beam(cells=(8, 2, 2))
     tl = T()
     mesh = tl.Mesh.from_workload(wl, precision=tl.FP32)
-    u = np.ascontiguousarray(wl.u, np.float32)
+    u = np.ascontiguousarray(wl.u, np.float64)
     ud = np.ascontiguousarray(wl.udot, np.float32)
-    f_h = np.zeros_like(u)
+    f_h = np.zeros_like(ud)
     mesh.internal_force_host(u, ud, f_h)
-    f_d = mesh.internal_force(dev(u, torch.float32), dev(ud, torch.float32)).cpu().numpy()
+    f_d = mesh.internal_force(dev(u, torch.float64), dev(ud, torch.float32)).cpu().numpy()
     assert np.array_equal(f_h, f_d) or relerr(f_h, f_d) < 1e-6
+
+
+def _subset(wl, mask):
+    blk = wl.blocks[0]
+    return Workload("sub", wl.X, [Block(blk.etype, blk.nq, blk.conn[mask], blk.body[mask])], wl.model, wl.params,
+                    u=wl.u, udot=wl.udot, v=wl.v,
+                    elem_mu_lambda=None if wl.elem_mu_lambda is None else wl.elem_mu_lambda[mask])
+
+
+def test_beam_full_size_bench_configuration():
+    """The 480k-T10 beam the benchmark times, in its launch configuration:
+    force against the oracle everywhere; K v and the adjoint at sampled nodes
+    (a node's value depends only on the elements holding it)."""
+    wl = synth.cantilever_beam()
+    tl = T()
+    f_ref, bad = oracle.internal_force(wl)
+    assert bad == 0
+    for prec, tol in ((1, 2e-5), (0, 1e-12)):
+        mesh = tl.Mesh.from_workload(wl, precision=prec)
+        dt = mesh.torch_dtype
+        u, ud, v = dev(wl.u, torch.float64), dev(wl.udot, dt), dev(wl.v, dt)
+        f = mesh.internal_force(u, ud)
+        y = mesh.tangent_matvec(u, ud, v, 0.0, 1.0, 1.0)
+        gu, gud, gth = mesh.vjp(u, ud, v)
+        mesh.sync()
+        assert relerr(f, f_ref) <= tol
+        rng = np.random.default_rng(8)
+        ks = rng.choice(wl.n_nodes, 300, replace=False)
+        sub = _subset(wl, np.isin(wl.blocks[0].conn, ks).any(axis=1))
+        y_ref = oracle.operator_apply(sub, wl.v, a_K=1.0, a_C=1.0)
+        g_ref, gd_ref, _ = oracle.vjp(sub, wl.v)
+        assert relerr(y.double().cpu().numpy()[ks], y_ref[ks]) <= tol
+        assert relerr(gu.double().cpu().numpy()[ks], g_ref[ks]) <= tol
+        assert relerr(gud.double().cpu().numpy()[ks], gd_ref[ks]) <= tol
+        mesh.close()

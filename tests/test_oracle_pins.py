@@ -590,3 +590,19 @@ def test_greedy_colouring_valid_and_equal_to_brute_force():
     for c in range(nc):
         nodes = m.conn[col == c].ravel()
         assert len(nodes) == len(set(nodes.tolist()))
+
+
+def test_kinematic_forms_agree_and_rigid_translation_is_exact():
+    # Eq. expression-F with U H = I and sum_i h_i = 0: the three forms are equal
+    wl = synth.block_t10_svk()
+    f2, _ = oracle.internal_force(wl, kin_form=2)
+    for form in (0, 1):
+        f, _ = oracle.internal_force(wl, kin_form=form)
+        assert np.abs(f - f2).max() < 1e-12 * np.abs(f2).max()
+    # a rigid translation by a large offset: the element-relative form sees
+    # exactly zero strain, hence exactly zero force
+    wl.u = np.tile(np.array([123.456, -7.25, 0.3]), (wl.n_nodes, 1))
+    f2, _ = oracle.internal_force(wl, kin_form=2)
+    assert np.abs(f2).max() == 0.0
+    f1, _ = oracle.internal_force(wl, kin_form=1)
+    assert np.abs(f1).max() > 0.0          # the plain displacement form rounds
