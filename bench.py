@@ -1,19 +1,34 @@
 """Benchmark of the TL-FEA hot path on GB300.
 
-Workload: the 10 x 1 x 1 m cantilever beam, 200 x 20 x 20 cells split into
-480,000 Kuhn T10 tetrahedra (674,081 nodes), 5-point quadrature,
-compressible neo-Hookean (mu = 3.8e6, lambda = 5.8e6 Pa) with Kelvin-Voigt
-damping (mu_v = 1e3 Pa s), seeded bending field + 0.1 % noise, seeded
-velocities; FP32 element arithmetic.
+Default workload (--workload beam): the 10 x 1 x 1 m cantilever beam,
+200 x 20 x 20 cells split into 480,000 Kuhn T10 tetrahedra (674,081 nodes),
+5-point quadrature, compressible neo-Hookean (mu = 3.8e6, lambda = 5.8e6 Pa)
+with Kelvin-Voigt damping (mu_v = 1e3 Pa s), seeded bending field + 0.1 %
+noise, seeded velocities; FP32 element arithmetic, FP64 displacement state.
 
 One step = one pass of the element hot path over the beam:
   internal force f(u, udot)                       (tlfe_internal_force)
   full tangent product y = K_t v + C v            (tlfe_tangent_matvec)
   adjoint g_u, g_udot, g_(mu, lambda) of f . r    (tlfe_vjp)
 value = quadrature points processed through that pass per second (whole job).
+The same step is also timed with FP64 element arithmetic ("fp64_plain").
 
-L2 is flushed (a 512 MiB memset) before every timed step, outside the step's
-CUDA-event pair; ms_per_step is the mean of the per-step event times.
+Other workloads (one JSON line each):
+  --workload newton  64 clamped neo-Hookean beams (6.75 M T10) under gravity:
+                     one backward-Euler step, Newton to relative residual 1e-8
+                     with Jacobi-PCG; batched FP32 operator + FP64 residual in
+                     one CUDA graph, against the FP64 library one body at a time
+                     with a host-driven loop.
+  --workload batch   512 bodies of uneven size, mixed T4/T10/H8, SVK or
+                     neo-Hookean: force + K v of every body, replayed as one
+                     CUDA graph.
+  --workload diff    1 M-element T10 block with per-element (mu, lambda):
+                     loss 1/2 |f - f_target|^2, forward + adjoint through the
+                     torch.autograd.Function.
+
+L2: inputs and streamed element data are larger than L2 (129 MB) in every
+workload, and a 512 MiB memset flushes L2 before every timed step, outside
+the step's CUDA-event pair.
 
 --impl reference times the CPU FP64 oracle on a bounded sample of the same
 workload on the host cores (the reference arm of this build).
@@ -36,8 +51,22 @@ sys.path.insert(0, ROOT)
 
 METRIC = "quad-pt force evals/s & % HBM roofline; batched FP32 fwd+VJP vs plain FP64"
 UNIT = "quad-pt/s"
-WORKLOAD = "cantilever beam 10x1x1 m, 200x20x20 cells -> 480k T10 (674,081 nodes), Q=5, neo-Hookean + Kelvin-Voigt, FP32"
+WORKLOADS = {
+    "beam": "cantilever beam 10x1x1 m, 200x20x20 cells -> 480k T10 (674,081 nodes), Q=5, neo-Hookean + "
+            "Kelvin-Voigt, FP32",
+    "newton": "implicit step: 64 clamped neo-Hookean beams (5:1:1, N_e ~ logU[2e4, 3e5], 6.75 M T10, Q=5), "
+              "gravity, h = 1e-3 s, Newton rel. residual 1e-8, Jacobi-PCG rtol 1e-4",
+    "batch": "512 bodies, N_e ~ logU[1e3, 2e5], mixed T4 Q1 / T10 Q5 / H8 Q8, SVK or neo-Hookean, "
+             "E ~ logU[1e6, 1e9], FP32, graph-captured force + K v",
+    "diff": "1 m^3 block 55^3 cells -> 998,250 T10, Q=5, neo-Hookean per-element (mu, lambda) + Kelvin-Voigt, "
+            "loss 1/2 |f - f_target|^2, forward + VJP, FP32",
+}
+GRAVITY = (0.0, 0.0, -9.81)
 
+
+# ---------------------------------------------------------------------------
+# shared helpers
+# ---------------------------------------------------------------------------
 
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -127,25 +156,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_sample_oracle(wl, n_elem_sample):
-    """Time the oracle (force + closed-form tangent product + adjoint) on the
-    first n_elem_sample elements of the workload; returns (qp/s, seconds, threads)."""
-    import numpy as np
-    import oracle
-    from synth.workloads import Block, Workload
-    blk = wl.blocks[0]
-    sub = Workload("sample", wl.X, [Block(blk.etype, blk.nq, blk.conn[:n_elem_sample], blk.body[:n_elem_sample])],
-                   wl.model, wl.params, u=wl.u, udot=wl.udot, v=wl.v)
-    oracle.lib()
-    t0 = time.perf_counter()
-    oracle.internal_force(sub)
-    oracle.operator_apply(sub, wl.v, a_K=1.0, a_C=1.0)
-    oracle.vjp(sub, wl.v)
-    dt = time.perf_counter() - t0
-    return n_elem_sample * blk.nq / dt, dt, 1
-
-
-def dist_setup(n_gpus):
+def dist_setup():
     import torch
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -166,120 +177,209 @@ def barrier(world):
 
 
 def allmax(x, world):
+    """Max of a host scalar over all ranks (NCCL: through a CUDA tensor;
+    gloo: a CPU tensor)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
 
+def job_value(units_per_rank, world, step_ms_max):
+    """Whole-job throughput of weak-scaled replicas: every rank processes
+    units_per_rank per step; the job takes the slowest rank's time."""
+    return world * units_per_rank / (step_ms_max * 1e-3)
+
+
+def base_line(args, world, workload, value, unit, step_ms, dtype, higher=True, **config):
+    return {"metric": METRIC, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": higher, "scaling": "weak",
+            "vs_baseline": None, "dtype": dtype, "data": "synthetic (seeded)",
+            "config": dict({"workload": WORKLOADS[workload],
+                            "l2": "inputs > L2; 512 MiB memset flush before every timed step, outside its events",
+                            "parallelism": f"replicas x{world} (one independent problem per GPU)"}, **config)}
+
+
+def timed_steps(step, steps, flush, stream, n_ev=2):
+    """Run `steps` calls of step(ev) with an L2 flush before each; step records
+    its own events ev[0..n_ev-1]; returns the per-step event lists."""
+    import torch
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(n_ev)] for _ in range(steps)]
+    for k in range(steps):
+        flush.zero_()
+        step(evs[k])
+    torch.cuda.synchronize()
+    return evs
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle samples (the cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+
+def _sub_first(wl, n):
+    from synth.workloads import Block, Workload
+    blk = wl.blocks[0]
+    n = min(n, blk.n_elem)
+    return Workload("sample", wl.X, [Block(blk.etype, blk.nq, blk.conn[:n], blk.body[:n])], wl.model, wl.params,
+                    u=wl.u, udot=wl.udot, v=wl.v,
+                    elem_mu_lambda=None if wl.elem_mu_lambda is None else wl.elem_mu_lambda[:n])
+
+
+def cpu_sample(workload, wl, n_sample):
+    """Time the oracle on a bounded sample of the workload on one host core.
+    Returns (value in the workload's unit, seconds, threads, sample text)."""
+    import numpy as np
+    import oracle
+    oracle.lib()
+    if workload == "newton":
+        import synth
+        bodies = synth.split_bodies(wl)
+        b = min(bodies, key=lambda x: x.n_elem)
+        z = np.zeros_like(b.X)
+        t0 = time.perf_counter()
+        _, rep = oracle.newton_step(b, z, z, 1e-3, np.array(GRAVITY), fixed=b.fixed, newton_rtol=1e-8,
+                                    cg_rtol=1e-4, max_newton=20, max_cg=4000)
+        dt = time.perf_counter() - t0
+        # steps/s of the whole batch, extrapolated per element from the smallest body
+        val = 1.0 / (dt * wl.n_elem / b.n_elem)
+        return val, dt, 1, (f"oracle Newton step of the smallest body ({b.n_elem} T10), extrapolated per element "
+                            f"to {wl.n_elem}, {dt:.1f} s")
+    sub = _sub_first(wl, n_sample)
+    blk = sub.blocks[0]
+    t0 = time.perf_counter()
+    if workload == "beam":
+        oracle.internal_force(sub)
+        oracle.operator_apply(sub, wl.v, a_K=1.0, a_C=1.0)
+        oracle.vjp(sub, wl.v)
+        what = "force + closed-form K_t v + C v + adjoint"
+    elif workload == "batch":
+        oracle.internal_force(sub)
+        oracle.operator_apply(sub, wl.v, a_K=1.0)
+        what = "force + closed-form K v"
+    else:  # diff
+        oracle.internal_force(sub)
+        oracle.vjp(sub, wl.v)
+        what = "force + adjoint"
+    dt = time.perf_counter() - t0
+    return (blk.n_elem * blk.nq / dt, dt, 1,
+            f"first {blk.n_elem} of {wl.n_elem} elements ({'T4 T10 H8'.split()[blk.etype]} block), {what}, "
+            f"{dt:.1f} s")
+
+
+def build_workload(workload):
+    import synth
+    if workload == "beam":
+        return synth.cantilever_beam()
+    if workload == "newton":
+        return synth.newton_beams(64)
+    if workload == "batch":
+        return synth.batch_bodies(512)
+    return synth.diff_block()
+
+
+def diff_cotangent(wl):
+    import numpy as np
+    return np.random.default_rng(24).standard_normal(wl.X.shape)
+
+
 def run_reference(args):
-    """CPU oracle arm: rank 0 only; each step a bounded sample of the beam."""
+    """CPU oracle arm: rank 0 only; each step a bounded sample of the workload."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     import numpy as np
-    import synth
-    wl = synth.cantilever_beam()
-    n_s = args.ref_sample
-    for _ in range(max(0, args.warmup)):
-        cpu_sample_oracle(wl, max(64, n_s // 8))
-    ts = []
-    for _ in range(args.steps):
-        q, dt, thr = cpu_sample_oracle(wl, n_s)
+    wl = build_workload(args.workload)
+    if args.workload == "diff":
+        wl.v = diff_cotangent(wl)
+    if args.workload != "newton":
+        for _ in range(max(0, args.warmup)):
+            cpu_sample(args.workload, wl, max(64, args.ref_sample // 16))
+    ts, vals = [], []
+    steps = 1 if args.workload == "newton" else args.steps
+    what = ""
+    for _ in range(steps):
+        v, dt, thr, what = cpu_sample(args.workload, wl, args.ref_sample)
         ts.append(dt)
-    t = float(np.mean(ts))
-    value = n_s * 5 / t
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD + " (oracle: first %d elements per step)" % n_s},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"first {n_s} of 480,000 elements (force + closed-form K_t v + C v + adjoint)"},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        vals.append(v)
+    value = float(np.mean(vals))
+    unit = "steps/s" if args.workload == "newton" else UNIT
+    line = base_line(args, 1, args.workload, value, unit, float(np.mean(ts)) * 1e3, "f64")
+    line.update({"impl": "reference", "n_gpus": args.gpus,
+                 "cpu_baseline": {"value": value, "unit": unit, "cores": 1, "kind": "oracle", "sample": what},
+                 "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}})
+    line["config"]["parallelism"] = "host, 1 core"
     print(json.dumps(line), flush=True)
     return 0
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="tlfe", choices=["tlfe", "reference"])
-    ap.add_argument("--ref-sample", type=int, default=3000)
-    ap.add_argument("--cpu-sample", type=int, default=3000)
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    args = ap.parse_args()
-    if args.warmup < 3:
-        args.warmup = 3
-    if args.impl == "reference":
-        return run_reference(args)
+# ---------------------------------------------------------------------------
+# workload: beam (default)
+# ---------------------------------------------------------------------------
 
+def run_beam(args, rank, world):
     import numpy as np
     import torch
 
-    import synth
     from paper_2602_17002_gb300 import tlfe
-
-    rank, world, local = dist_setup(args.gpus)
-    wl = synth.cantilever_beam()
-    mesh = tlfe.Mesh.from_workload(wl, precision=tlfe.FP32)
-    info = mesh.info
-    dt = torch.float32
-    u = torch.from_numpy(wl.u).to("cuda", torch.float64)   # displacement state: FP64 in both precisions
-    ud = torch.from_numpy(wl.udot).to("cuda", dt)
-    v = torch.from_numpy(wl.v).to("cuda", dt)
-    f = torch.empty_like(ud)
-    y = torch.empty_like(ud)
-    gu = torch.empty_like(ud)
-    gud = torch.empty_like(ud)
-    gth = torch.empty((wl.n_elem, 2), dtype=torch.float64, device="cuda")
-    flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device="cuda")
+    wl = build_workload("beam")
     L = tlfe.load()
+    flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
     sp = tlfe._stream(stream)
-    h = mesh.handle
+    u = torch.from_numpy(wl.u).to("cuda", torch.float64)   # displacement state: FP64 in both precisions
 
-    def step(ev=None):
-        if ev:
-            ev[0].record(stream)
-        tlfe._check(L.tlfe_internal_force(h, tlfe._ptr(u), tlfe._ptr(ud), tlfe._ptr(f), sp))
-        if ev:
-            ev[1].record(stream)
-        tlfe._check(L.tlfe_tangent_matvec(h, tlfe._ptr(u), tlfe._ptr(ud), tlfe._ptr(v), 0.0, 1.0, 1.0,
-                                          tlfe._ptr(y), sp))
-        if ev:
-            ev[2].record(stream)
-        tlfe._check(L.tlfe_vjp(h, tlfe._ptr(u), tlfe._ptr(ud), tlfe._ptr(v), tlfe._ptr(gu), tlfe._ptr(gud),
-                               tlfe._ptr(gth), sp))
-        if ev:
-            ev[3].record(stream)
+    def make(prec):
+        mesh = tlfe.Mesh.from_workload(wl, precision=prec)
+        dt = mesh.torch_dtype
+        ud = torch.from_numpy(wl.udot).to("cuda", dt)
+        v = torch.from_numpy(wl.v).to("cuda", dt)
+        outs = [torch.empty_like(ud) for _ in range(4)]
+        gth = torch.empty((wl.n_elem, 2), dtype=torch.float64, device="cuda")
+        return mesh, ud, v, outs, gth
 
+    def make_step(mesh, u_, ud, v, outs, gth):
+        h = mesh.handle
+        f, y, gu, gud = outs
+
+        def step(ev=None):
+            if ev:
+                ev[0].record(stream)
+            tlfe._check(L.tlfe_internal_force(h, tlfe._ptr(u_), tlfe._ptr(ud), tlfe._ptr(f), sp))
+            if ev:
+                ev[1].record(stream)
+            tlfe._check(L.tlfe_tangent_matvec(h, tlfe._ptr(u_), tlfe._ptr(ud), tlfe._ptr(v), 0.0, 1.0, 1.0,
+                                              tlfe._ptr(y), sp))
+            if ev:
+                ev[2].record(stream)
+            tlfe._check(L.tlfe_vjp(h, tlfe._ptr(u_), tlfe._ptr(ud), tlfe._ptr(v), tlfe._ptr(gu), tlfe._ptr(gud),
+                                   tlfe._ptr(gth), sp))
+            if ev:
+                ev[3].record(stream)
+        return step
+
+    mesh, ud, v, outs, gth = make(tlfe.FP32)
+    info = mesh.info
+    step = make_step(mesh, u, ud, v, outs, gth)
     for _ in range(args.warmup):
         step()
     mesh.sync()
     torch.cuda.synchronize()
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
     barrier(world)
     torch.cuda.synchronize()
     with ClockSampler(torch.cuda.current_device()) as clk:
-        for k in range(args.steps):
-            flush.zero_()
-            step(evs[k])
-        torch.cuda.synchronize()
+        evs = timed_steps(step, args.steps, flush, stream, 4)
     barrier(world)
     st = mesh.sync()
     per = np.array([[evs[k][j].elapsed_time(evs[k][j + 1]) for j in range(3)] for k in range(args.steps)])
-    step_ms = float(per.sum(axis=1).mean())
-    step_ms_max = allmax(step_ms, world)
+    step_ms = allmax(float(per.sum(axis=1).mean()), world)
     kern_ms = per.mean(axis=0)
     units = wl.n_qp
-    value = world * units / (step_ms_max * 1e-3)
+    value = job_value(units, world, step_ms)
 
-    # roofline of the dominant kernel
     names = ["force", "matvec", "vjp"]
     bytes_alg = [info["stream_bytes_force"], info["stream_bytes_matvec"], info["stream_bytes_vjp"]]
     j = int(np.argmax(kern_ms))
@@ -290,22 +390,18 @@ def main():
             "algorithmic_bytes": bytes_alg[j]}
 
     # end to end through the public API with host buffers (pinned), copies timed
-    hu = u.cpu().pin_memory()
-    hud = ud.cpu().pin_memory()
-    hv = v.cpu().pin_memory()
-    hf, hy, hgu, hgud = (torch.empty(ud.shape, dtype=dt).pin_memory() for _ in range(4))
+    f, y, gu, gud = outs
+    hu, hud, hv = u.cpu().pin_memory(), ud.cpu().pin_memory(), v.cpu().pin_memory()
+    hf, hy, hgu, hgud = (torch.empty(ud.shape, dtype=ud.dtype).pin_memory() for _ in range(4))
     hgth = torch.empty(gth.shape, dtype=torch.float64).pin_memory()
     du, dud, dv = torch.empty_like(u), torch.empty_like(ud), torch.empty_like(ud)
+    e2e_inner = make_step(mesh, du, dud, dv, outs, gth)
 
     def e2e_step():
         du.copy_(hu, non_blocking=True)
         dud.copy_(hud, non_blocking=True)
         dv.copy_(hv, non_blocking=True)
-        tlfe._check(L.tlfe_internal_force(h, tlfe._ptr(du), tlfe._ptr(dud), tlfe._ptr(f), sp))
-        tlfe._check(L.tlfe_tangent_matvec(h, tlfe._ptr(du), tlfe._ptr(dud), tlfe._ptr(dv), 0.0, 1.0, 1.0,
-                                          tlfe._ptr(y), sp))
-        tlfe._check(L.tlfe_vjp(h, tlfe._ptr(du), tlfe._ptr(dud), tlfe._ptr(dv), tlfe._ptr(gu), tlfe._ptr(gud),
-                               tlfe._ptr(gth), sp))
+        e2e_inner()
         hf.copy_(f, non_blocking=True)
         hy.copy_(y, non_blocking=True)
         hgu.copy_(gu, non_blocking=True)
@@ -316,8 +412,7 @@ def main():
         e2e_step()
     torch.cuda.synchronize()
     barrier(world)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
         e2e_step()
@@ -325,32 +420,322 @@ def main():
     torch.cuda.synchronize()
     e2e_ms = allmax(e0.elapsed_time(e1) / args.steps, world)
     h2d = u.numel() * 8 + 2 * ud.numel() * 4
-    d2h = 4 * u.numel() * 4 + gth.numel() * 8
+    d2h = 4 * ud.numel() * 4 + gth.numel() * 8
+    mesh.close()
 
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": step_ms_max, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "step": "internal force + K_t v + C v + VJP (u, udot, mu, lambda)",
-                       "n_elem": wl.n_elem, "n_nodes": wl.n_nodes, "n_qp": units,
-                       "l2": "flushed (512 MiB memset) before every step, outside the timed events",
-                       "parallelism": f"replicas x{world} (one independent beam per GPU)"},
-            "kernels_ms": {n: float(t) for n, t in zip(names, kern_ms)},
-            "kernels_gbs": {n: b / (t * 1e-3) / 1e9 for n, b, t in zip(names, bytes_alg, kern_ms)},
-            "force_qps": units / (kern_ms[0] * 1e-3),
-            "roofline": roof,
-            "e2e": {"value": world * units / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
-            "gpu_launches": 3 * args.steps,
-            "clocks": clk.summary(),
-            "device_status": st}
+    # the same step with FP64 element arithmetic (the plain path)
+    m64, ud64, v64, outs64, gth64 = make(tlfe.FP64)
+    step64 = make_step(m64, u, ud64, v64, outs64, gth64)
+    for _ in range(args.warmup):
+        step64()
+    torch.cuda.synchronize()
+    evs64 = timed_steps(step64, max(3, args.steps // 4), flush, stream, 4)
+    per64 = np.array([[e[j].elapsed_time(e[j + 1]) for j in range(3)] for e in evs64])
+    ms64 = float(per64.sum(axis=1).mean())
+    st64 = m64.sync()
+    m64.close()
+
+    line = base_line(args, world, "beam", value, UNIT, step_ms, "f32",
+                     step="internal force + K_t v + C v + VJP (u, udot, mu, lambda)", n_elem=wl.n_elem,
+                     n_nodes=wl.n_nodes, n_qp=units)
+    line.update({
+        "kernels_ms": {n: float(t) for n, t in zip(names, kern_ms)},
+        "kernels_gbs": {n: b / (t * 1e-3) / 1e9 for n, b, t in zip(names, bytes_alg, kern_ms)},
+        "force_qps": units / (kern_ms[0] * 1e-3),
+        "roofline": roof,
+        "fp64_plain": {"ms_per_step": ms64, "kernels_ms": {n: float(t) for n, t in zip(names, per64.mean(axis=0))},
+                       "speedup_fp32_over_fp64": ms64 / step_ms, "device_status": st64},
+        "e2e": {"value": world * units / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+        "gpu_launches": 3 * args.steps,
+        "clocks": clk.summary(),
+        "device_status": st})
+    return line, wl
+
+
+# ---------------------------------------------------------------------------
+# workload: newton (batched graph-captured FP32 step vs plain FP64 per body)
+# ---------------------------------------------------------------------------
+
+def run_newton(args, rank, world):
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2602_17002_gb300 import tlfe
+    wl = build_workload("newton")
+    h = 1e-3
+    kw = dict(gravity=GRAVITY, newton_rtol=1e-8, cg_rtol=1e-4, max_newton=20, max_cg=4000)
+    flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    mesh = tlfe.Mesh.from_workload(wl, precision=tlfe.FP32)
+    z = torch.zeros((wl.n_nodes, 3), dtype=torch.float64, device="cuda")
+    fx = torch.from_numpy(wl.fixed).cuda()
+    v_out = torch.empty_like(z)
+    reps = []
+
+    def step(ev=None):
+        if ev:
+            ev[0].record(stream)
+        _, rep = mesh.newton_step(z, z, h, fixed=fx, use_graph=True, v_out=v_out, **kw)
+        if ev:
+            ev[1].record(stream)
+        reps.append(rep)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        evs = timed_steps(step, args.steps, flush, stream)
+    barrier(world)
+    ms = allmax(float(np.mean([e[0].elapsed_time(e[1]) for e in evs])), world)
+    rep = reps[-1]
+    v_b = v_out.cpu().numpy()
+
+    # e2e: state from pinned host memory, velocity back to the host
+    hz = z.cpu().pin_memory()
+    hv = torch.empty_like(hz).pin_memory()
+    du, dv = torch.empty_like(z), torch.empty_like(z)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        du.copy_(hz, non_blocking=True)
+        dv.copy_(hz, non_blocking=True)
+        mesh.newton_step(du, dv, h, fixed=fx, use_graph=True, v_out=v_out, **kw)
+        hv.copy_(v_out, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = allmax(e0.elapsed_time(e1) / args.steps, world)
+    mesh.close()
+
+    # plain path: the FP64 library, one body at a time, host-driven Newton/CG loop
+    bodies = synth.split_bodies(wl)
+    plain = []
+    for b in bodies:
+        mb = tlfe.Mesh.from_workload(b, precision=tlfe.FP64)
+        zb = torch.zeros((b.n_nodes, 3), dtype=torch.float64, device="cuda")
+        plain.append((mb, zb, torch.from_numpy(b.fixed).cuda(), torch.empty_like(zb)))
+
+    def plain_step():
+        out = []
+        for mb, zb, fb, vb in plain:
+            _, r = mb.newton_step(zb, zb, h, fixed=fb, use_graph=False, v_out=vb, **kw)
+            out.append(r)
+        return out
+
+    plain_step()                                   # warm-up (per-body kernels and workspaces)
+    torch.cuda.synchronize()
+    flush.zero_()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    p0.record(stream)
+    preps = plain_step()
+    p1.record(stream)
+    torch.cuda.synchronize()
+    ms_plain = p0.elapsed_time(p1)
+    wall_plain = (time.perf_counter() - t0) * 1e3
+    v_p = np.concatenate([vb.cpu().numpy() for _, _, _, vb in plain])
+    for mb, *_ in plain:
+        mb.close()
+    dv_rel = float(np.abs(v_b - v_p).max() / max(np.abs(v_p).max(), 1e-300))
+
+    line = base_line(args, world, "newton", world * 1e3 / ms, "steps/s", ms, "f32",
+                     n_bodies=wl.n_bodies, n_elem=wl.n_elem, n_nodes=wl.n_nodes,
+                     step="one backward-Euler step of all bodies from rest (h = 1e-3 s, gravity, x = 0 clamped)")
+    line.update({
+        "batched": {"ms_per_step": ms, "newton_iters": rep["newton_iters"], "cg_iters": rep["cg_iters"],
+                    "rel_residual": rep["rel_residual"], "bodies_converged": rep["n_bodies_converged"],
+                    "status": rep["status"], "precision": "FP32 element kernels, FP64 residual/dots/update",
+                    "graph": True},
+        "plain_fp64": {"ms_per_step": ms_plain, "host_wall_ms": wall_plain,
+                       "newton_iters_max": max(r["newton_iters"] for r in preps),
+                       "cg_iters_sum": int(sum(r["cg_iters"] for r in preps)),
+                       "rel_residual_max": max(r["rel_residual"] for r in preps),
+                       "bodies_converged": int(sum(r["status"] == 0 for r in preps)),
+                       "precision": "FP64 everywhere", "graph": False, "schedule": "one body at a time"},
+        "speedup_batched_over_plain": ms_plain / ms,
+        "max_rel_diff_v": dv_rel,
+        "e2e": {"value": world * 1e3 / e2e_ms, "unit": "steps/s", "h2d_bytes_per_step": 2 * z.numel() * 8,
+                "d2h_bytes_per_step": z.numel() * 8, "ms_per_step": e2e_ms},
+        "gpu_launches": None,
+        "gpu_launches_note": "graph replays; the kernel count follows the Newton/CG iteration counts",
+        "clocks": clk.summary()})
+    return line, wl
+
+
+# ---------------------------------------------------------------------------
+# workload: batch (512 uneven bodies, graph-captured force + K v)
+# ---------------------------------------------------------------------------
+
+def run_batch(args, rank, world):
+    import numpy as np
+    import torch
+
+    from paper_2602_17002_gb300 import tlfe
+    wl = build_workload("batch")
+    mesh = tlfe.Mesh.from_workload(wl, precision=tlfe.FP32)
+    info = mesh.info
+    u = torch.from_numpy(wl.u).to("cuda", torch.float64)
+    v = torch.from_numpy(wl.v).to("cuda", torch.float32)
+    f, y = torch.empty_like(v), torch.empty_like(v)
+    flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device="cuda")
+    side = torch.cuda.Stream()
+    L = tlfe.load()
+
+    def calls(s):
+        sp = tlfe._stream(s)
+        tlfe._check(L.tlfe_internal_force(mesh.handle, tlfe._ptr(u), None, tlfe._ptr(f), sp))
+        tlfe._check(L.tlfe_tangent_matvec(mesh.handle, tlfe._ptr(u), None, tlfe._ptr(v), 0.0, 1.0, 0.0,
+                                          tlfe._ptr(y), sp))
+
+    with torch.cuda.stream(side):
+        for _ in range(2):
+            calls(side)                      # occupancy and schedule caches filled before capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side):
+        calls(side)
+    stream = torch.cuda.current_stream()
+
+    def step(ev=None):
+        if ev:
+            ev[0].record(stream)
+        g.replay()
+        if ev:
+            ev[1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        evs = timed_steps(step, args.steps, flush, stream)
+    barrier(world)
+    st = mesh.sync()
+    ms = allmax(float(np.mean([e[0].elapsed_time(e[1]) for e in evs])), world)
+    units = wl.n_qp
+    peak, peak_kind = peaks()
+    b_alg = info["stream_bytes_force"] + info["stream_bytes_matvec"]
+    achieved = b_alg / (ms * 1e-3) / 1e9
+    # e2e: u and v from pinned host memory, f and K v back
+    hu, hv = u.cpu().pin_memory(), v.cpu().pin_memory()
+    hf, hy = torch.empty_like(hv).pin_memory(), torch.empty_like(hv).pin_memory()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        u.copy_(hu, non_blocking=True)
+        v.copy_(hv, non_blocking=True)
+        g.replay()
+        hf.copy_(f, non_blocking=True)
+        hy.copy_(y, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = allmax(e0.elapsed_time(e1) / args.steps, world)
+    types = {0: "T4", 1: "T10", 2: "H8"}
+    line = base_line(args, world, "batch", world * units / (ms * 1e-3), UNIT, ms, "f32",
+                     n_bodies=wl.n_bodies, n_elem=wl.n_elem, n_nodes=wl.n_nodes, n_qp=units,
+                     elements_by_type={types[b.etype]: b.n_elem for b in wl.blocks},
+                     step="internal force + K v over all bodies, one CUDA graph replay")
+    line.update({
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "force + matvec, all element blocks", "peak_source": peak_kind,
+                     "algorithmic_bytes": b_alg},
+        "e2e": {"value": world * units / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": u.numel() * 8 + v.numel() * 4, "d2h_bytes_per_step": 2 * v.numel() * 4},
+        "gpu_launches": 2 * len([b for b in wl.blocks if b.n_elem]) * args.steps,
+        "clocks": clk.summary(), "device_status": st})
+    mesh.close()
+    return line, wl
+
+
+# ---------------------------------------------------------------------------
+# workload: diff (forward + VJP through torch.autograd)
+# ---------------------------------------------------------------------------
+
+def run_diff(args, rank, world):
+    import numpy as np
+    import torch
+
+    from paper_2602_17002_gb300 import autograd, tlfe
+    wl = build_workload("diff")
+    mesh = tlfe.Mesh.from_workload(wl, precision=tlfe.FP32)
+    info = mesh.info
+    u = torch.from_numpy(wl.u).to("cuda", torch.float64).requires_grad_(True)
+    ud = torch.from_numpy(wl.udot).to("cuda", torch.float32).requires_grad_(True)
+    theta = torch.from_numpy(wl.elem_mu_lambda).to("cuda", torch.float64).requires_grad_(True)
+    # f_target from the perturbed parameter field, computed once by the library
+    with torch.no_grad():
+        f_t = autograd.internal_force(mesh, u, ud, torch.from_numpy(wl.extra["theta_target"]).cuda()).double()
+    flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    losses = []
+
+    def step(ev=None):
+        if ev:
+            ev[0].record(stream)
+        for t in (u, ud, theta):
+            t.grad = None
+        f = autograd.internal_force(mesh, u, ud, theta)
+        loss = 0.5 * ((f.double() - f_t) ** 2).sum()
+        loss.backward()
+        if ev:
+            ev[1].record(stream)
+        losses.append(loss.detach())
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        evs = timed_steps(step, args.steps, flush, stream)
+    barrier(world)
+    st = mesh.sync()
+    ms = allmax(float(np.mean([e[0].elapsed_time(e[1]) for e in evs])), world)
+    units = wl.n_qp
+    peak, peak_kind = peaks()
+    b_alg = info["stream_bytes_force"] + info["stream_bytes_vjp"]
+    achieved = b_alg / (ms * 1e-3) / 1e9
+    line = base_line(args, world, "diff", world * units / (ms * 1e-3), UNIT, ms, "f32",
+                     n_elem=wl.n_elem, n_nodes=wl.n_nodes, n_qp=units,
+                     step="autograd forward (tlfe_internal_force) + loss in torch + backward (tlfe_vjp)")
+    line.update({
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "force + vjp (+ torch loss)", "peak_source": peak_kind,
+                     "algorithmic_bytes": b_alg},
+        "loss": float(losses[-1].item()),
+        "e2e": None, "gpu_launches": 2 * args.steps, "clocks": clk.summary(), "device_status": st})
+    mesh.close()
+    return line, wl
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="tlfe", choices=["tlfe", "reference"])
+    ap.add_argument("--workload", default="beam", choices=sorted(WORKLOADS))
+    ap.add_argument("--ref-sample", type=int, default=10000, help="elements per reference-arm step")
+    ap.add_argument("--cpu-sample", type=int, default=40000, help="elements in the cpu_baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    rank, world, _ = dist_setup()
+    run = {"beam": run_beam, "newton": run_newton, "batch": run_batch, "diff": run_diff}[args.workload]
+    line, wl = run(args, rank, world)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        q, secs, thr = cpu_sample_oracle(wl, args.cpu_sample)
-        line["cpu_baseline"] = {"value": q, "unit": UNIT, "cores": thr, "kind": "oracle",
-                                "sample": f"first {args.cpu_sample} of {wl.n_elem} elements, force + closed-form "
-                                          f"K_t v + C v + adjoint, {secs:.1f} s"}
+        if args.workload == "diff":
+            wl.v = diff_cotangent(wl)
+        val, secs, thr, what = cpu_sample(args.workload, wl, args.cpu_sample)
+        line["cpu_baseline"] = {"value": val, "unit": line["unit"], "cores": thr, "kind": "oracle", "sample": what}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    mesh.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

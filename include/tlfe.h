@@ -66,6 +66,16 @@ enum { TLFE_T4 = 0, TLFE_T10 = 1, TLFE_H8 = 2 };   /* element types (App. A; T4/
 enum { TLFE_SVK = 0, TLFE_NEOHOOKE = 1 };           /* elastic laws (Sec. 3.2) */
 enum { TLFE_FP64 = 0, TLFE_FP32 = 1 };              /* element arithmetic */
 enum { TLFE_SCATTER_ATOMIC = 0, TLFE_SCATTER_COLOR = 1 };
+/* Where the element kernels take the reference gradients h_i from:
+ *   TLFE_PATH_AUTO   : affine blocks (every T4; straight-edged T10;
+ *                      parallelepiped H8) keep J^{-1} and det J per element and
+ *                      form h_i = J^{-T} dS_i/dxi(xi_q) at each point (Sec. 6,
+ *                      affine case); other blocks stream the precomputed h_i
+ *                      and w_q J_p of every point
+ *   TLFE_PATH_SLAB   : every block streams the per-point h_i and w_q J_p
+ *   TLFE_PATH_AFFINE : every block on the affine path; TLFE_E_UNSUPPORTED at
+ *                      creation when a block is not affine */
+enum { TLFE_PATH_AUTO = 0, TLFE_PATH_SLAB = 1, TLFE_PATH_AFFINE = 2 };
 
 /* One type-homogeneous element block.
  *   type  : TLFE_T4 (4 nodes), TLFE_T10 (10 nodes, App. A.1 node order),
@@ -103,14 +113,16 @@ typedef struct {
     int32_t scatter;                /* TLFE_SCATTER_ATOMIC (fast, order not fixed) or
                                        TLFE_SCATTER_COLOR (deterministic colour passes) */
     uint64_t color_seed;            /* priority seed of the conflict colouring */
+    int32_t element_path;           /* TLFE_PATH_AUTO, TLFE_PATH_SLAB or TLFE_PATH_AFFINE */
 } tlfe_mesh_desc;
 
 typedef struct tlfe_mesh tlfe_mesh;
 
 /* Build a mesh handle on the current CUDA device: validates connectivity and
  * sizes, uploads them, and runs the reference precompute of Section 6 on the
- * device (H_q = Hp(xi_q) (U Hp(xi_q))^{-1} and w_q J_p, in FP64, stored in the
- * mesh precision). With TLFE_SCATTER_COLOR it also colours the elements
+ * device in FP64, stored in the mesh precision: J^{-1} and det J per element
+ * on the affine path, H_q = Hp(xi_q) (U Hp(xi_q))^{-1} and w_q J_p per point
+ * on the slab path (see element_path). With TLFE_SCATTER_COLOR it also colours the elements
  * (Jones-Plassmann with priority splitmix64(e xor color_seed); equal to the
  * sequential greedy colouring in descending priority). Synchronises `stream`.
  * Returns TLFE_E_INVERTED if any J_p <= 0, TLFE_E_INVALID on bad input. */
@@ -126,6 +138,7 @@ typedef struct {
     int64_t stream_bytes_matvec;  /* algorithmic bytes of one tlfe_tangent_matvec */
     int64_t stream_bytes_vjp;     /* algorithmic bytes of one tlfe_vjp (all outputs) */
     int64_t device_bytes;         /* device memory held by the handle */
+    int32_t n_affine_blocks;      /* blocks whose kernels run on the affine path */
 } tlfe_mesh_info;
 
 tlfe_status tlfe_get_mesh_info(const tlfe_mesh *mesh, tlfe_mesh_info *info);

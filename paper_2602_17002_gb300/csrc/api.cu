@@ -80,6 +80,8 @@ static tlfe_status validate(const tlfe_mesh_desc *d)
     if (d->precision != TLFE_FP32 && d->precision != TLFE_FP64) return fail(TLFE_E_INVALID, "bad precision");
     if (d->scatter != TLFE_SCATTER_ATOMIC && d->scatter != TLFE_SCATTER_COLOR)
         return fail(TLFE_E_INVALID, "bad scatter mode");
+    if (d->element_path != TLFE_PATH_AUTO && d->element_path != TLFE_PATH_SLAB && d->element_path != TLFE_PATH_AFFINE)
+        return fail(TLFE_E_INVALID, "bad element path");
     for (int k = 0; k < 3 * d->n_nodes; ++k)
         if (!std::isfinite(d->X_ref[k])) return fail(TLFE_E_INVALID, "X_ref holds a non-finite value");
     for (int b = 0; b < d->n_bodies; ++b) {
@@ -313,7 +315,6 @@ static tlfe_status build_block(tlfe_mesh *m, const tlfe_mesh_desc *d, int bi, in
     CKA(B.d_tnodes, sizeof(int32_t) * tnodes.size(), m);
     CKA(B.d_lidx, sizeof(uint16_t) * lidx.size(), m);
     CKA(B.d_meta, meta.size(), m);
-    CKA(B.d_slab, rs * nslot * B.nq * (npe * 3 + 1), m);
     CKA(B.d_evol, rs * nslot, m);
     CK(cudaMemcpyAsync(B.d_eid, eid.data(), sizeof(int32_t) * nslot, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(B.d_toff, toff.data(), sizeof(int32_t) * toff.size(), cudaMemcpyHostToDevice, s));
@@ -348,24 +349,59 @@ static tlfe_status build_block(tlfe_mesh *m, const tlfe_mesh_desc *d, int bi, in
             CK(cudaMemcpy(B.d_elam, el.data(), 8 * el.size(), cudaMemcpyHostToDevice));
         }
     }
-    // reference precompute (Sec. 6) on the device
+    // reference precompute (Sec. 6) on the device: first J^{-1}, det J and the
+    // affine test per element; then, for blocks on the slab path, the
+    // per-point h_i and w_q J_p
     int32_t *d_conn = nullptr;
-    int *d_aff = nullptr;
+    int *d_aflag = nullptr;
     CK(cudaMalloc(&d_conn, sizeof(int32_t) * std::max<size_t>(1, (size_t)b.n_elem * npe)));
-    CK(cudaMalloc(&d_aff, sizeof(int)));
+    CK(cudaMalloc(&d_aflag, sizeof(int)));
     const int one = 1;
-    cudaError_t e = cudaMemcpyAsync(d_conn, b.conn, sizeof(int32_t) * b.n_elem * npe, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_aff, &one, sizeof(int), cudaMemcpyHostToDevice, s);
+    int aflag = 0;
+    cudaError_t e = cudaSuccess;
+    if (d->element_path != TLFE_PATH_SLAB) {
+        e = cudaMalloc(&B.d_aff, rs * nslot * AFF_ROWS);
+        if (e == cudaSuccess) {
+            m->allocs.push_back(B.d_aff);
+            m->device_bytes += (int64_t)(rs * nslot * AFF_ROWS);
+        }
+    }
     if (e == cudaSuccess)
-        e = launch_precompute(B.et, B.nq, m->precision, B.n_tiles, B.d_eid, d_conn, elem_base, m->d_X, B.d_slab,
-                              B.d_evol, d_aff, m->d_status, s);
-    int aff = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&aff, d_aff, sizeof(int), cudaMemcpyDeviceToHost, s);
+        e = cudaMemcpyAsync(d_conn, b.conn, sizeof(int32_t) * b.n_elem * npe, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_aflag, &one, sizeof(int), cudaMemcpyHostToDevice, s);
+    void *aff_out = B.d_aff;
+    if (e == cudaSuccess && !aff_out) {  // slab path only: the affine test still runs, into scratch
+        e = cudaMalloc(&aff_out, std::max<size_t>(16, rs * nslot * AFF_ROWS));
+    }
+    if (e == cudaSuccess)
+        e = launch_precompute_affine(B.et, m->precision, B.n_tiles, B.d_eid, d_conn, elem_base, m->d_X, aff_out,
+                                     B.d_evol, d_aflag, m->d_status, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&aflag, d_aflag, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (aff_out != B.d_aff) cudaFree(aff_out);
+    B.affine = aflag != 0 && b.n_elem > 0;
+    if (e == cudaSuccess && d->element_path == TLFE_PATH_AFFINE && !B.affine && b.n_elem > 0) {
+        cudaFree(d_conn);
+        cudaFree(d_aflag);
+        return fail(TLFE_E_UNSUPPORTED, "element_path = TLFE_PATH_AFFINE but block " + std::to_string(bi) +
+                                            " has non-affine elements");
+    }
+    B.use_affine = B.affine && d->element_path != TLFE_PATH_SLAB;
+    if (e == cudaSuccess && !B.use_affine) {
+        e = cudaMalloc(&B.d_slab, rs * nslot * B.nq * (npe * 3 + 1));
+        if (e == cudaSuccess) {
+            m->allocs.push_back(B.d_slab);
+            m->device_bytes += (int64_t)(rs * nslot * B.nq * (npe * 3 + 1));
+            e = cudaMemcpyAsync(d_aflag, &one, sizeof(int), cudaMemcpyHostToDevice, s);
+        }
+        if (e == cudaSuccess)
+            e = launch_precompute(B.et, B.nq, m->precision, B.n_tiles, B.d_eid, d_conn, elem_base, m->d_X,
+                                  B.d_slab, B.d_evol, d_aflag, m->d_status, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
     cudaFree(d_conn);
-    cudaFree(d_aff);
+    cudaFree(d_aflag);
     if (e != cudaSuccess) return cuda_fail(e, "reference precompute");
-    B.affine = aff != 0;
     return TLFE_OK;
 }
 
@@ -386,6 +422,7 @@ extern "C" tlfe_status tlfe_create_mesh(const tlfe_mesh_desc *desc, void *stream
     m->h_mats.assign(desc->body_mat, desc->body_mat + desc->n_bodies);
     m->blocks.resize(desc->n_blocks);
     m->color_seed = desc->color_seed;
+    m->element_path = desc->element_path;
     m->h_X.assign(desc->X_ref, desc->X_ref + 3 * (size_t)desc->n_nodes);
     m->node_body.assign(desc->n_nodes, -1);
     {
@@ -474,8 +511,14 @@ extern "C" tlfe_status tlfe_get_mesh_info(const tlfe_mesh *m, tlfe_mesh_info *in
     info->n_colors = m->scatter == TLFE_SCATTER_COLOR ? nc : 0;
     const int64_t rs = m->precision == TLFE_FP32 ? 4 : 8;
     int64_t eb = 0;  // element-side bytes: H, wJ, local indices, tile node lists, material arrays
+    int naff = 0;
     for (auto &B : m->blocks) {
-        eb += (int64_t)B.n_elem * (B.nq * B.npe * 3 * rs + B.nq * rs);  // slab: h_i and w J_p
+        if (B.use_affine) {
+            eb += (int64_t)B.n_elem * AFF_ROWS * rs;              // J^{-1} and det J
+            ++naff;
+        } else {
+            eb += (int64_t)B.n_elem * (B.nq * B.npe * 3 * rs + B.nq * rs);  // slab: h_i and w J_p
+        }
         eb += (int64_t)B.n_tiles * B.meta_bytes;                        // per-tile metadata records
         if (B.d_emat) eb += (int64_t)B.n_elem * 4;
         if (B.d_elam) eb += (int64_t)B.n_elem * 2 * rs;
@@ -488,6 +531,7 @@ extern "C" tlfe_status tlfe_get_mesh_info(const tlfe_mesh *m, tlfe_mesh_info *in
     info->stream_bytes_matvec = eb + nu + nb * (visc ? 3 : 2);          // + v read
     info->stream_bytes_vjp = eb + nu + nb * (visc ? 4 : 2) + (int64_t)m->n_elem * 16;  // u, udot, r; g_u, g_udot; g_theta
     info->device_bytes = m->device_bytes;
+    info->n_affine_blocks = naff;
     return TLFE_OK;
 }
 
@@ -536,6 +580,7 @@ static tlfe_status run_block_op(tlfe_mesh *m, const BlockStore &B, KParams<R> p,
     p.umaxp = B.meta_umaxp;
     p.eid = B.d_eid;
     p.slab = (const R *)B.d_slab;
+    p.aff = B.use_affine ? (const R *)B.d_aff : nullptr;
     p.emat = B.d_emat;
     p.elam = (const R *)B.d_elam;
     p.evol = (const R *)B.d_evol;
@@ -544,15 +589,17 @@ static tlfe_status run_block_op(tlfe_mesh *m, const BlockStore &B, KParams<R> p,
     p.visc = (B.visc && p.ud) ? 1 : 0;
     p.status = m->d_status;
     std::string why;
-    const int occ = m->occupancy(OP, B.et, B.nq, sizeof(R), (size_t)B.umax, [&]() {
+    // occupancy key: op, element type and path, quadrature size, precision, patch size
+    const int etk = B.et + (B.use_affine ? 16 : 0);
+    const int occ = m->occupancy(OP, etk, B.nq, sizeof(R), (size_t)B.umax, [&]() {
         int wbest = 0;
-        const int v = occupancy_op<OP, R>(B.et, B.nq, B.umax, B.meta_bytes, &wbest, &why);
-        m->occ_wpb[std::make_tuple(OP, B.et, B.nq, (int)sizeof(R), (size_t)B.umax)] = wbest;
+        const int v = occupancy_op<OP, R>(B.et, B.nq, B.use_affine, B.umax, B.meta_bytes, &wbest, &why);
+        m->occ_wpb[std::make_tuple(OP, etk, B.nq, (int)sizeof(R), (size_t)B.umax)] = wbest;
         return v;
     });
-    const int wpb = m->occ_wpb[std::make_tuple(OP, B.et, B.nq, (int)sizeof(R), (size_t)B.umax)];
+    const int wpb = m->occ_wpb[std::make_tuple(OP, etk, B.nq, (int)sizeof(R), (size_t)B.umax)];
     if (occ <= 0) {
-        m->occ_cache.erase(std::make_tuple(OP, B.et, B.nq, (int)sizeof(R), (size_t)B.umax));
+        m->occ_cache.erase(std::make_tuple(OP, etk, B.nq, (int)sizeof(R), (size_t)B.umax));
         return fail(TLFE_E_UNSUPPORTED, "element kernel cannot be made resident: " + why);
     }
     const int n_passes = (int)B.color_tile_off.size() - 1;

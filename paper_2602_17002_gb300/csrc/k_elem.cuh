@@ -17,10 +17,11 @@
 //   - each lane evaluates F = I + sum_i u_i h_i^T per quadrature point and the
 //     stress, its directional derivative, its adjoint or the diagonal moduli,
 //     accumulating its element vector sum_q w_q J_p (.) h_iq in registers;
-//   - element vectors are summed into an output patch with shared-memory
-//     atomics, and the patch is added to the global array with one atomic per
-//     unique node and component (a plain read-add-write in colour passes,
-//     where no two elements of a launch share a node).
+//   - element vectors go to conflict-free shared slots [i * 32 + lane]; one
+//     lane per unique node sums that node's slots (a node-to-slot list built
+//     at mesh creation) and adds the sum to the global array with one atomic
+//     per component (a plain read-add-write in colour passes, where no two
+//     elements of a launch share a node).
 // Every mbarrier wait is bounded; on timeout the kernel latches ST_TIMEOUT in
 // the status word, drains its own copies (again bounded) and returns.
 #pragma once
@@ -94,15 +95,20 @@ template <int OP> struct OpFields {
     static constexpr int NFO = OUT / 3;           // output vector fields per node
 };
 
-// Patch record of one node: 16-byte aligned 4-vectors of R. The displacement
-// arrives in FP64; FP32 kernels keep it as an unevaluated pair (hi, lo) with
-// hi = fl32(u), lo = fl32(u - hi), so that element-relative differences
-// u_i - u_0 are formed without the rounding of |u| (large rigid motions).
+// Patch record of one node: packed 3-vectors in a record padded to 16 bytes.
+//   FP32: [u_hi(3) u_lo(3) | udot(3) | v(3)]  -> 12 floats (48 B)
+//   FP64: [u(3) | udot(3) | v(3)]             -> 6 or 10 doubles
+// The displacement arrives in FP64; FP32 kernels keep it as an unevaluated
+// pair (hi, lo) with u = hi + lo to about 2^-46 |u|, so that element-relative
+// differences u_i - u_0 are formed without the rounding of |u| (large rigid
+// motions).
 template <int OP, typename R> struct Rec {
-    static constexpr int NU = sizeof(R) == 4 ? 2 : 1;          // vectors holding u
-    static constexpr int OFF_UD = 4 * NU;                       // udot
-    static constexpr int OFF_V = 4 * (NU + 1);                  // direction / cotangent
-    static constexpr int REC = 4 * (NU + OpFields<OP>::NFI - 1);
+    static constexpr int NU = sizeof(R) == 4 ? 2 : 1;          // 3-vectors holding u
+    static constexpr int OFF_UD = 3 * NU;                       // udot
+    static constexpr int OFF_V = 3 * NU + 3;                    // direction / cotangent
+    static constexpr int RAW = 3 * (NU + OpFields<OP>::NFI - 1);
+    static constexpr int ALIGN = 16 / (int)sizeof(R);
+    static constexpr int REC = (RAW + ALIGN - 1) / ALIGN * ALIGN;
 };
 
 constexpr int NSLICE = 2;  // ring depth per warp (quadrature-point slices)
@@ -113,50 +119,119 @@ template <int ET, typename R> struct Slice {
     static constexpr uint32_t BYTES = ROWS * 32 * sizeof(R);  // multiple of 128
 };
 
-// shared memory of one warp: slice ring, two metadata buffers, and a work area
-// holding first the node patch [umax][REC] and later the element-vector slots
-// [NFO][npe * 32][3]; rounded up to 128 bytes so that every bulk-copy
-// destination stays 16-byte aligned
-template <int ET, typename R, int OP>
+// per-element affine record of a tile: J^{-1} (row-major, 9 rows) and det J, [10][32]
+template <typename R> struct AffRec {
+    static constexpr int ROWS = AFF_ROWS;
+    static constexpr uint32_t BYTES = ROWS * 32 * sizeof(R);  // multiple of 16
+};
+
+// shared memory of one warp: slice ring (isoparametric path only), two
+// metadata buffers (each followed, on the affine path, by the tile's affine
+// record), and a work area holding first the node patch [umax][REC] and later
+// the element-vector slots [npe * 32][3] of one output field; rounded up to
+// 128 bytes so that every bulk-copy destination stays 16-byte aligned
+template <int ET, typename R, int OP, bool AFF>
 __host__ __device__ constexpr size_t warp_region_bytes(int umax, int meta_bytes)
 {
     const size_t patch = (size_t)umax * Rec<OP, R>::REC * sizeof(R);
-    const size_t slots = (size_t)OpFields<OP>::NFO * Elem<ET>::NPE * 32 * 3 * sizeof(R);
-    return ((size_t)NSLICE * Slice<ET, R>::BYTES + 2 * (size_t)meta_bytes + (patch > slots ? patch : slots) + 127) /
-           128 * 128;
+    const size_t slots = (size_t)Elem<ET>::NPE * 32 * 3 * sizeof(R);  // one output field at a time
+    const size_t ring = AFF ? 0 : (size_t)NSLICE * Slice<ET, R>::BYTES;
+    const size_t mrec = (size_t)meta_bytes + (AFF ? AffRec<R>::BYTES : 0);
+    return (ring + 2 * mrec + (patch > slots ? patch : slots) + 127) / 128 * 128;
 }
 
 // dynamic shared memory of one CTA with `wpb` warps (mbarriers, then the warp regions)
-template <int ET, typename R, int OP>
+template <int ET, typename R, int OP, bool AFF>
 __host__ __device__ constexpr size_t elem_smem_bytes(int umax, int meta_bytes, int wpb)
 {
-    return 128 + (size_t)wpb * warp_region_bytes<ET, R, OP>(umax, meta_bytes);
+    return 128 + (size_t)wpb * warp_region_bytes<ET, R, OP, AFF>(umax, meta_bytes);
 }
 
-// 3-vectors in 16-byte-aligned shared records
-__device__ __forceinline__ void ld3(const float *p, float &x, float &y, float &z)
+// 3-vectors at compile-time offsets of a 16-byte-aligned shared record, with
+// the widest aligned vector accesses the offset allows
+template <int OFF> __device__ __forceinline__ void ld3c(const float *r, float &x, float &y, float &z)
 {
-    const float4 v = *reinterpret_cast<const float4 *>(p);
-    x = v.x;
-    y = v.y;
-    z = v.z;
+    if constexpr (OFF % 4 == 0) {
+        const float4 v = *reinterpret_cast<const float4 *>(r + OFF);
+        x = v.x, y = v.y, z = v.z;
+    } else if constexpr (OFF % 4 == 2) {
+        const float2 v = *reinterpret_cast<const float2 *>(r + OFF);
+        x = v.x, y = v.y, z = r[OFF + 2];
+    } else {
+        const float2 v = *reinterpret_cast<const float2 *>(r + OFF + 1);
+        x = r[OFF], y = v.x, z = v.y;
+    }
 }
-__device__ __forceinline__ void ld3(const double *p, double &x, double &y, double &z)
+template <int OFF> __device__ __forceinline__ void ld3c(const double *r, double &x, double &y, double &z)
 {
-    const double2 v = *reinterpret_cast<const double2 *>(p);
-    x = v.x;
-    y = v.y;
-    z = p[2];
+    if constexpr (OFF % 2 == 0) {
+        const double2 v = *reinterpret_cast<const double2 *>(r + OFF);
+        x = v.x, y = v.y, z = r[OFF + 2];
+    } else {
+        const double2 v = *reinterpret_cast<const double2 *>(r + OFF + 1);
+        x = r[OFF], y = v.x, z = v.y;
+    }
 }
-__device__ __forceinline__ void st3(float *p, float x, float y, float z)
+template <int OFF> __device__ __forceinline__ void st3c(float *r, float x, float y, float z)
 {
-    *reinterpret_cast<float4 *>(p) = make_float4(x, y, z, 0.f);
+    if constexpr (OFF % 4 == 0) {
+        *reinterpret_cast<float4 *>(r + OFF) = make_float4(x, y, z, 0.f);
+    } else if constexpr (OFF % 4 == 2) {
+        *reinterpret_cast<float2 *>(r + OFF) = make_float2(x, y);
+        r[OFF + 2] = z;
+    } else {
+        r[OFF] = x;
+        *reinterpret_cast<float2 *>(r + OFF + 1) = make_float2(y, z);
+    }
 }
-__device__ __forceinline__ void st3(double *p, double x, double y, double z)
+template <int OFF> __device__ __forceinline__ void st3c(double *r, double x, double y, double z)
 {
-    *reinterpret_cast<double2 *>(p) = make_double2(x, y);
-    p[2] = z;
-    p[3] = 0.0;
+    if constexpr (OFF % 2 == 0) {
+        *reinterpret_cast<double2 *>(r + OFF) = make_double2(x, y);
+        r[OFF + 2] = z;
+    } else {
+        r[OFF] = x;
+        *reinterpret_cast<double2 *>(r + OFF + 1) = make_double2(y, z);
+    }
+}
+// FP32 u pair of a record: hi at 0..2, lo at 3..5 (one 16-byte and one 8-byte load)
+__device__ __forceinline__ void ld_u(const float *r, float h[3], float l[3])
+{
+    const float4 a = *reinterpret_cast<const float4 *>(r);
+    const float2 b = *reinterpret_cast<const float2 *>(r + 4);
+    h[0] = a.x, h[1] = a.y, h[2] = a.z, l[0] = a.w, l[1] = b.x, l[2] = b.y;
+}
+__device__ __forceinline__ void ld_u(const double *r, double h[3], double l[3])
+{
+    ld3c<0>(r, h[0], h[1], h[2]);
+    l[0] = l[1] = l[2] = 0.0;
+}
+
+// x = hi + lo to about 2^-46 |x| with hi, lo in FP32, by integer and FP32
+// operations only (the FP64 pipe of this GPU runs at a small fraction of the
+// FP32 rate): hi keeps the leading 24 significant bits of x (exact in FP32),
+// lo the next 23 bits scaled by 2^(e - 46). |x| < 2^-126 gives (+-0, +-0);
+// |x| >= 2^128, inf and NaN fall back to the plain FP32 rounding with lo = 0.
+__device__ __forceinline__ void split_f64(double x, float &hi, float &lo)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned hw = (unsigned)(b >> 32), lw = (unsigned)b;
+    const unsigned sign = hw & 0x80000000u;
+    const int e = (int)((hw >> 20) & 0x7FFu) - 1023;  // unbiased binary exponent
+    if (e < -126) {
+        hi = __uint_as_float(sign);
+        lo = __uint_as_float(sign);
+    } else if (e <= 127) {
+        const unsigned mhi = ((hw & 0xFFFFFu) << 3) | (lw >> 29);  // significand bits 51..29
+        hi = __uint_as_float(sign | ((unsigned)(e + 127) << 23) | mhi);
+        const unsigned r = (lw >> 6) & 0x7FFFFFu;                   // significand bits 28..6
+        const float rf = __uint_as_float(0x4B000000u | r) - 8388608.0f;  // = r exactly
+        const float sc = e >= -80 ? __uint_as_float((unsigned)(e + 81) << 23) : 0.0f;  // 2^(e - 46)
+        lo = __uint_as_float(sign | __float_as_uint(rf * sc));
+    } else {
+        hi = (float)x;
+        lo = 0.0f;
+    }
 }
 
 // bounded wait on an mbarrier phase; returns false when the limit ran out
@@ -168,7 +243,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return true;
 }
 
-template <int ET, int NQ, typename R, int OP>
+template <int ET, int NQ, typename R, int OP, bool AFF>
 __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 3 : 1) k_elem(const KParams<R> p)
 {
     constexpr int NPE = Elem<ET>::NPE;
@@ -177,8 +252,11 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 3 : 1) k_elem(const KPar
     constexpr int OFF_V = Rec<OP, R>::OFF_V;
     constexpr int NFO = OpFields<OP>::NFO;
     constexpr bool HAS_V = OpFields<OP>::NFI == 3;
+    constexpr bool DD_REG = OP == OP_FORCE || OP == OP_DIAG;
     using SL = Slice<ET, R>;
     constexpr int ROWS = SL::ROWS;
+    using PG = ParentGrad<ET, NQ, R>;
+    constexpr uint32_t AB = AFF ? AffRec<R>::BYTES : 0;
 
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31;
@@ -188,17 +266,18 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 3 : 1) k_elem(const KPar
     const int MB = p.meta_bytes;
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem) + wib * (NSLICE + 2);  // [wpb][NSLICE + 2] (<= 128 B)
     uint64_t *mbar = bar + NSLICE;
-    unsigned char *wbase = smem + 128 + (size_t)wib * warp_region_bytes<ET, R, OP>(umax, MB);
+    const size_t MRB = (size_t)MB + AB;                        // metadata (+ affine) record bytes
+    unsigned char *wbase = smem + 128 + (size_t)wib * warp_region_bytes<ET, R, OP, AFF>(umax, MB);
     unsigned char *ring = wbase;
-    unsigned char *mbuf = wbase + NSLICE * SL::BYTES;          // [2][MB]
-    R *work = reinterpret_cast<R *>(mbuf + 2 * (size_t)MB);     // patch [umax][REC], later slots
+    unsigned char *mbuf = wbase + (AFF ? 0 : NSLICE * SL::BYTES);  // [2][MB + AB]
+    R *work = reinterpret_cast<R *>(mbuf + 2 * MRB);           // patch [umax][REC], later slots
 
     const int gw = blockIdx.x * wpb + wib;
     const int W = gridDim.x * wpb;
     const int t0 = p.tile_begin + gw;
     const int n_my = t0 < p.tile_end ? (p.tile_end - t0 + W - 1) / W : 0;
     const bool mass_only = OP == OP_MATVEC && p.mass_only != 0;
-    const int n_slices = mass_only ? 0 : n_my * NQ;
+    const int n_slices = (mass_only || AFF) ? 0 : n_my * NQ;
     const bool need_ud = p.visc != 0;
 
     if (lane == 0) {
@@ -214,10 +293,12 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 3 : 1) k_elem(const KPar
         mbar_arrive_expect_tx(bar + b, SL::BYTES);
         bulk_g2s(ring + (size_t)b * SL::BYTES, p.slab + ((size_t)t * NQ + q) * ROWS * 32, SL::BYTES, bar + b);
     };
-    auto issue_meta = [&](int k) {  // metadata of the warp's k-th tile into buffer k & 1
+    auto issue_meta = [&](int k) {  // metadata (+ affine record) of the warp's k-th tile into buffer k & 1
         const int t = t0 + k * W;
-        mbar_arrive_expect_tx(mbar + (k & 1), (uint32_t)MB);
-        bulk_g2s(mbuf + (size_t)(k & 1) * MB, p.meta + (size_t)t * MB, (uint32_t)MB, mbar + (k & 1));
+        unsigned char *dst = mbuf + (size_t)(k & 1) * MRB;
+        mbar_arrive_expect_tx(mbar + (k & 1), (uint32_t)MRB);
+        bulk_g2s(dst, p.meta + (size_t)t * MB, (uint32_t)MB, mbar + (k & 1));
+        if constexpr (AFF) bulk_g2s(dst + MB, p.aff + (size_t)t * AffRec<R>::ROWS * 32, AB, mbar + (k & 1));
     };
     if (lane == 0) {
         if (n_my > 0) issue_meta(0);
@@ -234,7 +315,7 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 3 : 1) k_elem(const KPar
             break;
         }
         if (lane == 0 && k + 1 < n_my) issue_meta(k + 1);
-        const unsigned char *M = mbuf + (size_t)(k & 1) * MB;
+        const unsigned char *M = mbuf + (size_t)(k & 1) * MRB;
         const int U = *reinterpret_cast<const int32_t *>(M);
         const int e = reinterpret_cast<const int32_t *>(M + 16)[lane];
         const int32_t *nodes = reinterpret_cast<const int32_t *>(M + 16 + 128);
@@ -247,15 +328,18 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 3 : 1) k_elem(const KPar
             const int64_t n = nodes[kk];
             R *rec = work + (size_t)kk * REC;
             const double ux = __ldg(p.u + 3 * n), uy = __ldg(p.u + 3 * n + 1), uz = __ldg(p.u + 3 * n + 2);
-            if (sizeof(R) == 4) {
-                const float hx = float(ux), hy = float(uy), hz = float(uz);
-                st3(rec, R(hx), R(hy), R(hz));
-                st3(rec + 4, R(float(ux - double(hx))), R(float(uy - double(hy))), R(float(uz - double(hz))));
+            if constexpr (sizeof(R) == 4) {
+                float h[3], l[3];
+                split_f64(ux, h[0], l[0]);
+                split_f64(uy, h[1], l[1]);
+                split_f64(uz, h[2], l[2]);
+                *reinterpret_cast<float4 *>(rec) = make_float4(h[0], h[1], h[2], l[0]);
+                *reinterpret_cast<float2 *>(rec + 4) = make_float2(l[1], l[2]);
             } else {
-                st3(rec, R(ux), R(uy), R(uz));
+                st3c<0>(rec, R(ux), R(uy), R(uz));
             }
-            if (need_ud) st3(rec + OFF_UD, __ldg(p.ud + 3 * n), __ldg(p.ud + 3 * n + 1), __ldg(p.ud + 3 * n + 2));
-            if (HAS_V) st3(rec + OFF_V, __ldg(p.v + 3 * n), __ldg(p.v + 3 * n + 1), __ldg(p.v + 3 * n + 2));
+            if (need_ud) st3c<OFF_UD>(rec, __ldg(p.ud + 3 * n), __ldg(p.ud + 3 * n + 1), __ldg(p.ud + 3 * n + 2));
+            if (HAS_V) st3c<OFF_V>(rec, __ldg(p.v + 3 * n), __ldg(p.v + 3 * n + 1), __ldg(p.v + 3 * n + 2));
         }
         int li[NPE];
 #pragma unroll
@@ -268,20 +352,29 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 3 : 1) k_elem(const KPar
             m.lam = p.elam[((size_t)t * 2 + 1) * 32 + lane];
         }
         const bool visc = need_ud && (m.mu_v != R(0) || m.lam_v != R(0));
+        // affine path: J^{-1} and det J of this lane's element (Sec. 6, affine case)
+        R Ji[9], detJ = R(0);
+        if constexpr (AFF) {
+            const R *A = reinterpret_cast<const R *>(M + MB) + lane;
+#pragma unroll
+            for (int r = 0; r < 9; ++r) Ji[r] = A[r * 32];
+            detJ = A[9 * 32];
+        }
         __syncwarp();
 
         // element-relative displacements d_i = u_i - u_0 (sum_i h_i = 0, so
-        // G = sum_i u_i h_i^T = sum_{i>0} d_i h_i^T, with rigid translation removed exactly)
+        // G = sum_i u_i h_i^T = sum_{i>0} d_i h_i^T, with rigid translation
+        // removed exactly). Kept in registers by the force and diagonal
+        // kernels; the operator and adjoint kernels, which hold more
+        // accumulators, re-form them from the patch at every point.
+        R h0v[3], l0v[3];
+        ld_u(work + li[0] * REC, h0v, l0v);
         R dd[NPE][3];
-        {
-            R h0v[3], l0v[3] = {R(0), R(0), R(0)};
-            ld3(work + li[0] * REC, h0v[0], h0v[1], h0v[2]);
-            if (sizeof(R) == 4) ld3(work + li[0] * REC + 4, l0v[0], l0v[1], l0v[2]);
+        if constexpr (DD_REG) {
 #pragma unroll
             for (int i = 1; i < NPE; ++i) {
-                R hv[3], lv[3] = {R(0), R(0), R(0)};
-                ld3(work + li[i] * REC, hv[0], hv[1], hv[2]);
-                if (sizeof(R) == 4) ld3(work + li[i] * REC + 4, lv[0], lv[1], lv[2]);
+                R hv[3], lv[3];
+                ld_u(work + li[i] * REC, hv, lv);
 #pragma unroll
                 for (int a = 0; a < 3; ++a) dd[i][a] = (hv[a] - h0v[a]) + (lv[a] - l0v[a]);
             }
@@ -299,17 +392,31 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 3 : 1) k_elem(const KPar
 
 #pragma unroll 1
         for (int q = 0; q < (mass_only ? 0 : NQ); ++q) {
-            const int j = k * NQ + q;
-            const int b = j % NSLICE;
-            if (!mbar_wait_bounded(bar + b, (uint32_t)((j / NSLICE) & 1))) timed_out = true;
-            if (__any_sync(0xffffffffu, timed_out)) {
-                timed_out = true;
-                break;
+            // reference gradients of this point: the slab slice (isoparametric
+            // path), or the parent gradients g_i with h_i = J^{-T} g_i (affine path)
+            const R *sl = nullptr;
+            PG pg;
+            R w;
+            if constexpr (AFF) {
+                pg.at(q);
+                w = quad_weight<ET, NQ, R>(q) * detJ;
+            } else {
+                const int j = k * NQ + q;
+                const int b = j % NSLICE;
+                if (!mbar_wait_bounded(bar + b, (uint32_t)((j / NSLICE) & 1))) timed_out = true;
+                if (__any_sync(0xffffffffu, timed_out)) {
+                    timed_out = true;
+                    break;
+                }
+                sl = reinterpret_cast<const R *>(ring + (size_t)b * SL::BYTES) + lane;
+                w = sl[NPE * 3 * 32];
             }
-            const R *sl = reinterpret_cast<const R *>(ring + (size_t)b * SL::BYTES) + lane;
-            const R w = sl[NPE * 3 * 32];
+            // gradient entry k of node i; nz(i, k) = false where it vanishes identically
+            auto grad = [&](int i, int k2) -> R { return AFF ? pg.g(i, k2) : sl[(i * 3 + k2) * 32]; };
+            auto nz = [&](int i, int k2) -> bool { return !AFF || PG::nz(i, k2); };
 
             // kinematics: G = sum d_i h_i^T, Fd = sum udot_i h_i^T, D = sum v_i h_i^T
+            // (affine path: the same sums against g_i, then times J^{-1})
             QP<R> s1;
             R D[9];
 #pragma unroll
@@ -320,34 +427,55 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 3 : 1) k_elem(const KPar
             }
 #pragma unroll
             for (int i = 0; i < NPE; ++i) {
-                const R h0 = sl[(i * 3 + 0) * 32], h1 = sl[(i * 3 + 1) * 32], h2 = sl[(i * 3 + 2) * 32];
+                R hk[3];
+#pragma unroll
+                for (int k2 = 0; k2 < 3; ++k2) hk[k2] = nz(i, k2) ? grad(i, k2) : R(0);
                 const R *rec = work + li[i] * REC;
                 R x[3];
                 if (i > 0) {
+                    if constexpr (!DD_REG) {
+                        R hv[3], lv[3];
+                        ld_u(rec, hv, lv);
 #pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        s1.G[a * 3 + 0] += dd[i][a] * h0;
-                        s1.G[a * 3 + 1] += dd[i][a] * h1;
-                        s1.G[a * 3 + 2] += dd[i][a] * h2;
+                        for (int a = 0; a < 3; ++a) dd[i][a] = (hv[a] - h0v[a]) + (lv[a] - l0v[a]);
                     }
+#pragma unroll
+                    for (int a = 0; a < 3; ++a)
+#pragma unroll
+                        for (int k2 = 0; k2 < 3; ++k2)
+                            if (nz(i, k2)) s1.G[a * 3 + k2] += dd[i][a] * hk[k2];
                 }
                 if (visc) {
-                    ld3(rec + OFF_UD, x[0], x[1], x[2]);
+                    ld3c<OFF_UD>(rec, x[0], x[1], x[2]);
 #pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        s1.Fd[a * 3 + 0] += x[a] * h0;
-                        s1.Fd[a * 3 + 1] += x[a] * h1;
-                        s1.Fd[a * 3 + 2] += x[a] * h2;
-                    }
+                    for (int a = 0; a < 3; ++a)
+#pragma unroll
+                        for (int k2 = 0; k2 < 3; ++k2)
+                            if (nz(i, k2)) s1.Fd[a * 3 + k2] += x[a] * hk[k2];
                 }
                 if (HAS_V) {
-                    ld3(rec + OFF_V, x[0], x[1], x[2]);
+                    ld3c<OFF_V>(rec, x[0], x[1], x[2]);
 #pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        D[a * 3 + 0] += x[a] * h0;
-                        D[a * 3 + 1] += x[a] * h1;
-                        D[a * 3 + 2] += x[a] * h2;
-                    }
+                    for (int a = 0; a < 3; ++a)
+#pragma unroll
+                        for (int k2 = 0; k2 < 3; ++k2)
+                            if (nz(i, k2)) D[a * 3 + k2] += x[a] * hk[k2];
+                }
+            }
+            if constexpr (AFF) {
+                R T[9];
+                mm3(s1.G, Ji, T);
+#pragma unroll
+                for (int k2 = 0; k2 < 9; ++k2) s1.G[k2] = T[k2];
+                if (visc) {
+                    mm3(s1.Fd, Ji, T);
+#pragma unroll
+                    for (int k2 = 0; k2 < 9; ++k2) s1.Fd[k2] = T[k2];
+                }
+                if (HAS_V) {
+                    mm3(D, Ji, T);
+#pragma unroll
+                    for (int k2 = 0; k2 < 9; ++k2) D[k2] = T[k2];
                 }
             }
             R P[9];
@@ -370,7 +498,19 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 3 : 1) k_elem(const KPar
                     }
 #pragma unroll
                     for (int i = 0; i < NPE; ++i) {
-                        const R h0 = sl[(i * 3 + 0) * 32], h1 = sl[(i * 3 + 1) * 32], h2 = sl[(i * 3 + 2) * 32];
+                        R hh[3];
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            if constexpr (AFF) {  // h_i = J^{-T} g_i
+                                hh[c] = R(0);
+#pragma unroll
+                                for (int k2 = 0; k2 < 3; ++k2)
+                                    if (nz(i, k2)) hh[c] += grad(i, k2) * Ji[k2 * 3 + c];
+                            } else {
+                                hh[c] = grad(i, c);
+                            }
+                        }
+                        const R h0 = hh[0], h1 = hh[1], h2 = hh[2];
                         acc0[i][d] += h0 * (A[0] * h0 + A[1] * h1 + A[2] * h2) +
                                       h1 * (A[3] * h0 + A[4] * h1 + A[5] * h2) +
                                       h2 * (A[6] * h0 + A[7] * h1 + A[8] * h2);
@@ -396,21 +536,51 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 3 : 1) k_elem(const KPar
                         T1[k2] *= w;
                     }
                 }
+                if constexpr (AFF) {
+                    // T h_i = (T J^{-T}) g_i
+                    R T[9];
 #pragma unroll
-                for (int i = 0; i < NPE; ++i) {
-                    const R h0 = sl[(i * 3 + 0) * 32], h1 = sl[(i * 3 + 1) * 32], h2 = sl[(i * 3 + 2) * 32];
+                    for (int a = 0; a < 3; ++a)
 #pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        acc0[i][a] += T0[a * 3] * h0 + T0[a * 3 + 1] * h1 + T0[a * 3 + 2] * h2;
-                        if (OP == OP_VJP) acc1[i][a] += T1[a * 3] * h0 + T1[a * 3 + 1] * h1 + T1[a * 3 + 2] * h2;
+                        for (int k2 = 0; k2 < 3; ++k2)
+                            T[a * 3 + k2] = T0[a * 3] * Ji[k2 * 3] + T0[a * 3 + 1] * Ji[k2 * 3 + 1] +
+                                            T0[a * 3 + 2] * Ji[k2 * 3 + 2];
+#pragma unroll
+                    for (int k2 = 0; k2 < 9; ++k2) T0[k2] = T[k2];
+                    if (OP == OP_VJP) {
+#pragma unroll
+                        for (int a = 0; a < 3; ++a)
+#pragma unroll
+                            for (int k2 = 0; k2 < 3; ++k2)
+                                T[a * 3 + k2] = T1[a * 3] * Ji[k2 * 3] + T1[a * 3 + 1] * Ji[k2 * 3 + 1] +
+                                                T1[a * 3 + 2] * Ji[k2 * 3 + 2];
+#pragma unroll
+                        for (int k2 = 0; k2 < 9; ++k2) T1[k2] = T[k2];
                     }
                 }
+#pragma unroll
+                for (int i = 0; i < NPE; ++i) {
+                    R hk[3];
+#pragma unroll
+                    for (int k2 = 0; k2 < 3; ++k2) hk[k2] = nz(i, k2) ? grad(i, k2) : R(0);
+#pragma unroll
+                    for (int a = 0; a < 3; ++a)
+#pragma unroll
+                        for (int k2 = 0; k2 < 3; ++k2)
+                            if (nz(i, k2)) {
+                                acc0[i][a] += T0[a * 3 + k2] * hk[k2];
+                                if (OP == OP_VJP) acc1[i][a] += T1[a * 3 + k2] * hk[k2];
+                            }
+                }
             }
-            // slot b is no longer read: hand it to the slice NSLICE ahead
-            __syncwarp();
-            if (lane == 0 && j + NSLICE < n_slices) {
-                fence_proxy_async();
-                issue(j + NSLICE);
+            if constexpr (!AFF) {
+                // slot b is no longer read: hand it to the slice NSLICE ahead
+                const int j = k * NQ + q;
+                __syncwarp();
+                if (lane == 0 && j + NSLICE < n_slices) {
+                    fence_proxy_async();
+                    issue(j + NSLICE);
+                }
             }
         }
         if (timed_out) break;
@@ -422,7 +592,7 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 3 : 1) k_elem(const KPar
 #pragma unroll
                 for (int jn = 0; jn < NPE; ++jn) {
                     R x[3];
-                    ld3(work + li[jn] * REC + OFF_V, x[0], x[1], x[2]);
+                    ld3c<OFF_V>(work + li[jn] * REC, x[0], x[1], x[2]);
 #pragma unroll
                     for (int i = 0; i < NPE; ++i) {
                         const R mh = c * R(mass_hat(ET, i, jn));
@@ -448,51 +618,38 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 3 : 1) k_elem(const KPar
         const int nbad = __reduce_add_sync(0xffffffffu, bad);
         if (lane == 0 && nbad) atomicAdd(p.status + ST_INVERTED, nbad);
 
-        // ---- element vectors into slots [field][i * 32 + lane][3] (the patch is dead now)
-        __syncwarp();
-        if (valid) {
+        // ---- per output field: element vectors into slots [i * 32 + lane][3]
+        // (the patch is dead now), then one lane per unique node sums its
+        // slots and adds them to the global array
 #pragma unroll
-            for (int i = 0; i < NPE; ++i)
+        for (int fo = 0; fo < NFO; ++fo) {
+            R *out = fo == 0 ? p.out0 : p.out1;
+            __syncwarp();
+            if (valid) {
 #pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    work[(i * 32 + lane) * 3 + d] = acc0[i][d];
-                    if (NFO == 2) work[(NPE * 32 + i * 32 + lane) * 3 + d] = acc1[i][d];
-                }
-        }
-        __syncwarp();
-        // ---- one lane per unique node sums its slots and adds them to the global arrays
-        for (int kk = lane; kk < U; kk += 32) {
-            const int64_t n = nodes[kk];
-            const int s0 = soff[kk], s1e = soff[kk + 1];
-            R a0 = R(0), a1 = R(0), a2 = R(0), b0 = R(0), b1 = R(0), b2 = R(0);
-            for (int sidx = s0; sidx < s1e; ++sidx) {
-                const int sl2 = nsl[sidx];
-                a0 += work[sl2 * 3 + 0];
-                a1 += work[sl2 * 3 + 1];
-                a2 += work[sl2 * 3 + 2];
-                if (NFO == 2) {
-                    b0 += work[(NPE * 32 + sl2) * 3 + 0];
-                    b1 += work[(NPE * 32 + sl2) * 3 + 1];
-                    b2 += work[(NPE * 32 + sl2) * 3 + 2];
-                }
+                for (int i = 0; i < NPE; ++i)
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) work[(i * 32 + lane) * 3 + d] = fo == 0 ? acc0[i][d] : acc1[i][d];
             }
-            if (p.rmw_scatter) {
-                p.out0[3 * n] += a0;
-                p.out0[3 * n + 1] += a1;
-                p.out0[3 * n + 2] += a2;
-                if (NFO == 2) {
-                    p.out1[3 * n] += b0;
-                    p.out1[3 * n + 1] += b1;
-                    p.out1[3 * n + 2] += b2;
+            __syncwarp();
+            for (int kk = lane; kk < U; kk += 32) {
+                const int64_t n = nodes[kk];
+                const int s0 = soff[kk], s1e = soff[kk + 1];
+                R a0 = R(0), a1 = R(0), a2 = R(0);
+                for (int sidx = s0; sidx < s1e; ++sidx) {
+                    const int sl2 = nsl[sidx];
+                    a0 += work[sl2 * 3 + 0];
+                    a1 += work[sl2 * 3 + 1];
+                    a2 += work[sl2 * 3 + 2];
                 }
-            } else {
-                atomicAdd(p.out0 + 3 * n, a0);
-                atomicAdd(p.out0 + 3 * n + 1, a1);
-                atomicAdd(p.out0 + 3 * n + 2, a2);
-                if (NFO == 2) {
-                    atomicAdd(p.out1 + 3 * n, b0);
-                    atomicAdd(p.out1 + 3 * n + 1, b1);
-                    atomicAdd(p.out1 + 3 * n + 2, b2);
+                if (p.rmw_scatter) {
+                    out[3 * n] += a0;
+                    out[3 * n + 1] += a1;
+                    out[3 * n + 2] += a2;
+                } else {
+                    atomicAdd(out + 3 * n, a0);
+                    atomicAdd(out + 3 * n + 1, a1);
+                    atomicAdd(out + 3 * n + 2, a2);
                 }
             }
         }
@@ -510,28 +667,36 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 3 : 1) k_elem(const KPar
     }
 }
 
-template <int OP, typename R> static void (*kernel_for(int et, int nq))(const KParams<R>)
+template <int OP, typename R, bool AFF> static void (*kernel_for_(int et, int nq))(const KParams<R>)
 {
-    if (et == ET_T4 && nq == 1) return k_elem<ET_T4, 1, R, OP>;
-    if (et == ET_T10 && nq == 4) return k_elem<ET_T10, 4, R, OP>;
-    if (et == ET_T10 && nq == 5) return k_elem<ET_T10, 5, R, OP>;
-    if (et == ET_H8 && nq == 8) return k_elem<ET_H8, 8, R, OP>;
+    if (et == ET_T4 && nq == 1) return k_elem<ET_T4, 1, R, OP, AFF>;
+    if (et == ET_T10 && nq == 4) return k_elem<ET_T10, 4, R, OP, AFF>;
+    if (et == ET_T10 && nq == 5) return k_elem<ET_T10, 5, R, OP, AFF>;
+    if (et == ET_H8 && nq == 8) return k_elem<ET_H8, 8, R, OP, AFF>;
     return nullptr;
 }
-
-
-template <int OP, typename R> size_t smem_for(int et, int umax, int meta_bytes, int wpb)
+template <int OP, typename R> static void (*kernel_for(int et, int nq, bool aff))(const KParams<R>)
 {
-    if (et == ET_T4) return elem_smem_bytes<ET_T4, R, OP>(umax, meta_bytes, wpb);
-    if (et == ET_T10) return elem_smem_bytes<ET_T10, R, OP>(umax, meta_bytes, wpb);
-    if (et == ET_H8) return elem_smem_bytes<ET_H8, R, OP>(umax, meta_bytes, wpb);
+    return aff ? kernel_for_<OP, R, true>(et, nq) : kernel_for_<OP, R, false>(et, nq);
+}
+
+template <int OP, typename R, bool AFF> size_t smem_for_(int et, int umax, int meta_bytes, int wpb)
+{
+    if (et == ET_T4) return elem_smem_bytes<ET_T4, R, OP, AFF>(umax, meta_bytes, wpb);
+    if (et == ET_T10) return elem_smem_bytes<ET_T10, R, OP, AFF>(umax, meta_bytes, wpb);
+    if (et == ET_H8) return elem_smem_bytes<ET_H8, R, OP, AFF>(umax, meta_bytes, wpb);
     return 0;
+}
+template <int OP, typename R> size_t smem_for(int et, int umax, int meta_bytes, int wpb, bool aff)
+{
+    return aff ? smem_for_<OP, R, true>(et, umax, meta_bytes, wpb) : smem_for_<OP, R, false>(et, umax, meta_bytes, wpb);
 }
 
 // resident warps per SM for the best CTA size among 4, 2 and 1 warps
-template <int OP, typename R> int occupancy_op(int et, int nq, int umax, int meta_bytes, int *wpb_out, std::string *why)
+template <int OP, typename R>
+int occupancy_op(int et, int nq, bool aff, int umax, int meta_bytes, int *wpb_out, std::string *why)
 {
-    void (*kern)(const KParams<R>) = kernel_for<OP, R>(et, nq);
+    void (*kern)(const KParams<R>) = kernel_for<OP, R>(et, nq, aff);
     *wpb_out = 0;
     if (!kern) {
         *why = "no kernel for this element type and quadrature size";
@@ -539,7 +704,7 @@ template <int OP, typename R> int occupancy_op(int et, int nq, int umax, int met
     }
     int best = 0;
     for (int wpb : {4, 2, 1}) {
-        const size_t smem = smem_for<OP, R>(et, umax, meta_bytes, wpb);
+        const size_t smem = smem_for<OP, R>(et, umax, meta_bytes, wpb, aff);
         if (smem > 227 * 1024) continue;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         int nb = 0;
@@ -559,12 +724,14 @@ template <int OP, typename R> int occupancy_op(int et, int nq, int umax, int met
     return best;
 }
 
+// launch on the affine path when p.aff is set, else on the isoparametric (slab) path
 template <int OP, typename R>
 cudaError_t launch_op(int et, int nq, const KParams<R> &p, int grid, int wpb, cudaStream_t s)
 {
-    void (*kern)(const KParams<R>) = kernel_for<OP, R>(et, nq);
+    const bool aff = p.aff != nullptr;
+    void (*kern)(const KParams<R>) = kernel_for<OP, R>(et, nq, aff);
     if (!kern) return cudaErrorInvalidValue;
-    const size_t smem = smem_for<OP, R>(et, p.umax, p.meta_bytes, wpb);
+    const size_t smem = smem_for<OP, R>(et, p.umax, p.meta_bytes, wpb, aff);
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     kern<<<grid, 32 * wpb, smem, s>>>(p);

@@ -5,6 +5,63 @@
 
 namespace tlfe {
 
+// Affine element (Sec. 6, affine case): the map from the parent element is
+// u(xi) = A xi + b. Holds for every T4; for T10 when the mid-edge nodes sit at
+// their edge midpoints; for H8 when the brick is a parallelepiped. Tolerance
+// 1e-10 of the element extent.
+__device__ bool element_is_affine(int et, int npe, const double Xe[10][3])
+{
+    bool affine = true;
+    double ext = 0.0;
+    for (int i = 1; i < npe; ++i)
+        for (int a = 0; a < 3; ++a) ext = fmax(ext, fabs(Xe[i][a] - Xe[0][a]));
+    const double tol = 1e-10 * ext;
+    if (et == ET_T10) {
+        for (int m = 0; m < 6; ++m) {
+            int a, b;
+            t10_edge(m, a, b);
+            for (int d = 0; d < 3; ++d)
+                if (fabs(Xe[4 + m][d] - 0.5 * (Xe[a][d] + Xe[b][d])) > tol) affine = false;
+        }
+    } else if (et == ET_H8) {
+        for (int n = 0; n < 8; ++n)
+            for (int d = 0; d < 3; ++d) {
+                const double p = Xe[0][d] + ((n & 1) ? Xe[1][d] - Xe[0][d] : 0.0) +
+                                 ((n & 2) ? Xe[2][d] - Xe[0][d] : 0.0) + ((n & 4) ? Xe[4][d] - Xe[0][d] : 0.0);
+                if (fabs(Xe[n][d] - p) > tol) affine = false;
+            }
+    }
+    return affine;
+}
+
+// Jp = U Hp(xi) evaluated as sum_{i>0} (X_i - X_0) dS_i/dxi^T (the parent
+// gradients sum to zero); relative coordinates keep the digits that large
+// absolute coordinates would cancel away. Returns det Jp and Jp^{-1} = cof^T / det.
+__device__ double parent_jacobian_inv(int et, int npe, const double Xe[10][3], const double *g, double Ji[9])
+{
+    double J[9];
+    for (int a = 0; a < 3; ++a)
+        for (int k = 0; k < 3; ++k) {
+            double s = 0.0;
+            for (int i = 1; i < npe; ++i) s += (Xe[i][a] - Xe[0][a]) * g[i * 3 + k];
+            J[a * 3 + k] = s;
+        }
+    const double c00 = J[4] * J[8] - J[5] * J[7];
+    const double c01 = J[5] * J[6] - J[3] * J[8];
+    const double c02 = J[3] * J[7] - J[4] * J[6];
+    const double det = J[0] * c00 + J[1] * c01 + J[2] * c02;
+    Ji[0] = c00 / det;
+    Ji[3] = c01 / det;
+    Ji[6] = c02 / det;
+    Ji[1] = (J[2] * J[7] - J[1] * J[8]) / det;
+    Ji[4] = (J[0] * J[8] - J[2] * J[6]) / det;
+    Ji[7] = (J[1] * J[6] - J[0] * J[7]) / det;
+    Ji[2] = (J[1] * J[5] - J[2] * J[4]) / det;
+    Ji[5] = (J[2] * J[3] - J[0] * J[5]) / det;
+    Ji[8] = (J[0] * J[4] - J[1] * J[3]) / det;
+    return det;
+}
+
 // One thread per (tile, lane): for each quadrature point,
 //   Jp = U Hp(xi_q)  (U = [X_1 .. X_n]),  h_i^T = dS_i/dxi Jp^{-1},
 //   wJ = w_q det(Jp)                               (Sec. 6, H = Hp (U Hp)^{-1}, J_p)
@@ -44,32 +101,10 @@ __global__ void k_precompute(int et, int nq, int npe, int n_tiles, const int32_t
         double xi[3], w, g[30];
         quad_point(et, nq, q, xi, w);
         parent_grad(et, xi, g);
-        // Jp = sum_{i>0} (X_i - X_0) dS_i/dxi^T: equal to U Hp since the parent
-        // gradients sum to zero; relative coordinates keep the digits that
-        // large absolute coordinates would cancel away
-        double J[9];
-        for (int a = 0; a < 3; ++a)
-            for (int k = 0; k < 3; ++k) {
-                double s = 0.0;
-                for (int i = 1; i < npe; ++i) s += (Xe[i][a] - Xe[0][a]) * g[i * 3 + k];
-                J[a * 3 + k] = s;
-            }
-        const double c00 = J[4] * J[8] - J[5] * J[7];
-        const double c01 = J[5] * J[6] - J[3] * J[8];
-        const double c02 = J[3] * J[7] - J[4] * J[6];
-        const double det = J[0] * c00 + J[1] * c01 + J[2] * c02;
+        double Ji[9];
+        const double det = parent_jacobian_inv(et, npe, Xe, g, Ji);
         jmin = fmin(jmin, det);
         jmax = fmax(jmax, det);
-        double Ji[9];  // Jp^{-1} = cof(Jp)^T / det
-        Ji[0] = c00 / det;
-        Ji[3] = c01 / det;
-        Ji[6] = c02 / det;
-        Ji[1] = (J[2] * J[7] - J[1] * J[8]) / det;
-        Ji[4] = (J[0] * J[8] - J[2] * J[6]) / det;
-        Ji[7] = (J[1] * J[6] - J[0] * J[7]) / det;
-        Ji[2] = (J[1] * J[5] - J[2] * J[4]) / det;
-        Ji[5] = (J[2] * J[3] - J[0] * J[5]) / det;
-        Ji[8] = (J[0] * J[4] - J[1] * J[3]) / det;
         const bool ok = det > 0.0;
         if (!ok) inverted = 1;
         for (int i = 0; i < npe; ++i)
@@ -84,27 +119,7 @@ __global__ void k_precompute(int et, int nq, int npe, int n_tiles, const int32_t
     }
     evol[idx] = R(vol);
     if (inverted) atomicAdd(status + ST_INVERTED, 1);
-    // affine test: mid-edge nodes at edge midpoints (T10), parallelepiped (H8)
-    bool affine = true;
-    double ext = 0.0;
-    for (int i = 1; i < npe; ++i)
-        for (int a = 0; a < 3; ++a) ext = fmax(ext, fabs(Xe[i][a] - Xe[0][a]));
-    const double tol = 1e-10 * ext;
-    if (et == ET_T10) {
-        for (int m = 0; m < 6; ++m) {
-            int a, b;
-            t10_edge(m, a, b);
-            for (int d = 0; d < 3; ++d)
-                if (fabs(Xe[4 + m][d] - 0.5 * (Xe[a][d] + Xe[b][d])) > tol) affine = false;
-        }
-    } else if (et == ET_H8) {
-        for (int n = 0; n < 8; ++n)
-            for (int d = 0; d < 3; ++d) {
-                const double p = Xe[0][d] + ((n & 1) ? Xe[1][d] - Xe[0][d] : 0.0) +
-                                 ((n & 2) ? Xe[2][d] - Xe[0][d] : 0.0) + ((n & 4) ? Xe[4][d] - Xe[0][d] : 0.0);
-                if (fabs(Xe[n][d] - p) > tol) affine = false;
-            }
-    }
+    const bool affine = element_is_affine(et, npe, Xe);
     (void)jmin;
     (void)jmax;
     if (!affine) atomicAnd(affine_flag, 0);
@@ -125,6 +140,69 @@ cudaError_t launch_precompute(int et, int nq, int precision, int n_tiles, const 
     else
         k_precompute<double><<<grid, tpb, 0, s>>>(et, nq, npe, n_tiles, eid, conn_elem, elem_base, X,
                                                   (double *)slab, (double *)evol, affine_flag, status);
+    return cudaGetLastError();
+}
+
+// Affine path (Sec. 6, affine case): one thread per (tile, lane) writes
+//   aff[tile][r][lane], r = 0..8: J^{-1} (row-major), r = 9: det J
+// with J = du/dxi constant over the element (evaluated at the centroid, in
+// FP64, relative coordinates), the element volume det J * |parent| into evol,
+// and clears *affine_flag when an element of the block is not affine.
+// det J <= 0 counts as an inverted element.
+template <typename R>
+__global__ void k_precompute_affine(int et, int npe, int n_tiles, const int32_t *__restrict__ eid,
+                                    const int32_t *__restrict__ conn, int elem_base,
+                                    const double *__restrict__ X, R *__restrict__ aff, R *__restrict__ evol,
+                                    int *affine_flag, int *status)
+{
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)n_tiles * 32) return;
+    const int64_t t = idx >> 5;
+    const int lane = (int)(idx & 31);
+    const int e = eid[idx];
+    if (e < 0) {
+        for (int r = 0; r < 10; ++r) aff[(t * 10 + r) * 32 + lane] = R(0);
+        evol[idx] = R(0);
+        return;
+    }
+    const int64_t el = (int64_t)e - elem_base;
+    double Xe[10][3];
+    for (int i = 0; i < npe; ++i) {
+        const int64_t n = conn[el * npe + i];
+        for (int a = 0; a < 3; ++a) Xe[i][a] = X[n * 3 + a];
+    }
+    double xi[3], g[30];
+    if (et == ET_H8) {
+        xi[0] = xi[1] = xi[2] = 0.0;
+    } else {
+        xi[0] = xi[1] = xi[2] = 0.25;
+    }
+    parent_grad(et, xi, g);
+    double Ji[9];
+    const double det = parent_jacobian_inv(et, npe, Xe, g, Ji);
+    const bool ok = det > 0.0;
+    for (int r = 0; r < 9; ++r) aff[(t * 10 + r) * 32 + lane] = ok ? R(Ji[r]) : R(0);
+    aff[(t * 10 + 9) * 32 + lane] = ok ? R(det) : R(0);
+    evol[idx] = ok ? R(det * (et == ET_H8 ? 8.0 : 1.0 / 6.0)) : R(0);
+    if (!ok) atomicAdd(status + ST_INVERTED, 1);
+    if (!element_is_affine(et, npe, Xe)) atomicAnd(affine_flag, 0);
+}
+
+cudaError_t launch_precompute_affine(int et, int precision, int n_tiles, const int32_t *eid,
+                                     const int32_t *conn_elem, int elem_base, const double *X, void *aff,
+                                     void *evol, int *affine_flag, int *status, cudaStream_t s)
+{
+    const int npe = nodes_per_elem(et);
+    const int64_t n = (int64_t)n_tiles * 32;
+    const int tpb = 128;
+    const unsigned grid = (unsigned)((n + tpb - 1) / tpb);
+    if (grid == 0) return cudaSuccess;
+    if (precision == TLFE_FP32)
+        k_precompute_affine<float><<<grid, tpb, 0, s>>>(et, npe, n_tiles, eid, conn_elem, elem_base, X,
+                                                        (float *)aff, (float *)evol, affine_flag, status);
+    else
+        k_precompute_affine<double><<<grid, tpb, 0, s>>>(et, npe, n_tiles, eid, conn_elem, elem_base, X,
+                                                         (double *)aff, (double *)evol, affine_flag, status);
     return cudaGetLastError();
 }
 

@@ -487,6 +487,7 @@ static tlfe_status setup_newton(tlfe_mesh *m, cudaStream_t s)
         d.precision = TLFE_FP64;
         d.scatter = m->scatter;
         d.color_seed = m->color_seed;
+        d.element_path = m->element_path;
         st = tlfe_create_mesh(&d, s, &ns->twin);
         if (st != TLFE_OK) return st;
     }

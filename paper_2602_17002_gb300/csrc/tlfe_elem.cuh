@@ -149,4 +149,97 @@ __host__ __device__ inline double vol_hat(int et, int i)
     return s;
 }
 
+// ---------------------------------------------------------------------------
+// Affine elements (Sec. 6, affine case): with du/dxi = J constant, the
+// reference gradients are h_i = J^{-T} dS_i/dxi(xi_q) and the quadrature
+// weight is w_q det J. The element kernels then stream J^{-1} and det J per
+// element instead of h_i per point, and evaluate the parent gradients at each
+// point from the point's coordinates. ParentGrad<ET, NQ, R> gives the entry
+// g(i, k) = dS_i/dxi_k at the current point; nz(i, k) is false where the entry
+// vanishes identically, so that fully unrolled loops skip those terms.
+// ---------------------------------------------------------------------------
+
+// barycentric gradients dL_j/dxi_k of the tetrahedron: L1 -> (-1,-1,-1), L2..L4 -> unit vectors
+__host__ __device__ constexpr int tet_dL(int j, int k) { return j == 0 ? -1 : (k == j - 1 ? 1 : 0); }
+__host__ __device__ constexpr int t10_ea(int e) { return e == 0 ? 0 : (e == 1 ? 1 : (e == 2 ? 0 : (e == 3 ? 0 : (e == 4 ? 1 : 2)))); }
+__host__ __device__ constexpr int t10_eb(int e) { return e == 0 ? 1 : (e == 1 ? 2 : (e == 2 ? 2 : 3)); }
+
+template <int ET, int NQ, typename R> struct ParentGrad;
+
+// T4: constant gradients dS_i/dxi = dL_i/dxi
+template <int NQ, typename R> struct ParentGrad<ET_T4, NQ, R> {
+    __device__ __forceinline__ void at(int) {}
+    __host__ __device__ static constexpr bool nz(int i, int k) { return tet_dL(i, k) != 0; }
+    __device__ __forceinline__ R g(int i, int k) const { return tet_dL(i, k) > 0 ? R(1) : R(-1); }
+};
+
+// T10: corners L_i (2 L_i - 1) -> (4 L_i - 1) dL_i; edge (a, b): 4 L_a L_b -> 4 (L_b dL_a + L_a dL_b).
+// The point is held as L4 = 4 L.
+template <int NQ, typename R> struct ParentGrad<ET_T10, NQ, R> {
+    R L4[4];
+    __device__ __forceinline__ void at(int q)
+    {
+        if constexpr (NQ == 5) {  // centroid, then (1/2, 1/6, 1/6, 1/6) permutations
+#pragma unroll
+            for (int j = 0; j < 4; ++j) L4[j] = q == 0 ? R(1) : (j == q - 1 ? R(2) : R(2.0 / 3.0));
+        } else if constexpr (NQ == 4) {  // (a, b, b, b) permutations, a = (5 + 3 sqrt5)/20, b = (5 - sqrt5)/20
+            const R a4 = R(0.58541019662496845446 * 4.0), b4 = R(0.13819660112501051518 * 4.0);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) L4[j] = j == q ? a4 : b4;
+        } else {  // centroid
+#pragma unroll
+            for (int j = 0; j < 4; ++j) L4[j] = R(1);
+        }
+    }
+    __host__ __device__ static constexpr bool nz(int i, int k)
+    {
+        return i < 4 ? tet_dL(i, k) != 0 : (tet_dL(t10_ea(i - 4), k) != 0 || tet_dL(t10_eb(i - 4), k) != 0);
+    }
+    __device__ __forceinline__ R g(int i, int k) const
+    {
+        if (i < 4) {
+            const R c = L4[i] - R(1);
+            return tet_dL(i, k) > 0 ? c : -c;
+        }
+        const int a = t10_ea(i - 4), b = t10_eb(i - 4);
+        const int da = tet_dL(a, k), db = tet_dL(b, k);
+        const R ta = da > 0 ? L4[b] : -L4[b];  // 4 L_b dL_a
+        const R tb = db > 0 ? L4[a] : -L4[a];  // 4 L_a dL_b
+        if (da != 0 && db != 0) return ta + tb;
+        return da != 0 ? ta : tb;
+    }
+};
+
+// H8 (parallelepiped): dS_n/dxi_k = (s_k / 2) prod_{j != k} (1 + s_j xi_j) / 2 with
+// s_j = -1 / +1 from bit j of n; the point is held as the six factors (1 +- xi_j) / 2.
+template <int NQ, typename R> struct ParentGrad<ET_H8, NQ, R> {
+    R f[3][2];  // f[j][s] = (1 + (2s - 1) xi_j) / 2
+    __device__ __forceinline__ void at(int q)
+    {
+        const R gp = R(0.57735026918962576451);  // 1/sqrt(3)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const R x = NQ == 8 ? (((q >> j) & 1) ? gp : -gp) : R(0);
+            f[j][0] = R(0.5) * (R(1) - x);
+            f[j][1] = R(0.5) * (R(1) + x);
+        }
+    }
+    __host__ __device__ static constexpr bool nz(int, int) { return true; }
+    __device__ __forceinline__ R g(int n, int k) const
+    {
+        const int j1 = (k + 1) % 3, j2 = (k + 2) % 3;
+        const R p = R(0.5) * f[j1][(n >> j1) & 1] * f[j2][(n >> j2) & 1];
+        return ((n >> k) & 1) ? p : -p;
+    }
+};
+
+// quadrature weight w_q of point q (parent measure), matching quad_point
+template <int ET, int NQ, typename R> __device__ __forceinline__ R quad_weight(int q)
+{
+    if constexpr (ET == ET_H8) return NQ == 8 ? R(1) : R(8);
+    if constexpr (NQ == 5) return q == 0 ? R(-2.0 / 15.0) : R(3.0 / 40.0);
+    if constexpr (NQ == 4) return R(1.0 / 24.0);
+    return R(1.0 / 6.0);
+}
+
 }  // namespace tlfe

@@ -5,8 +5,6 @@
 #include <stdint.h>
 
 #include <string>
-
-#include <string>
 #include <vector>
 
 #include "tlfe.h"
@@ -17,7 +15,8 @@ namespace tlfe {
 enum { OP_FORCE = 0, OP_MATVEC = 1, OP_VJP = 2, OP_DIAG = 3 };
 enum { ST_INVERTED = 0, ST_NONFINITE = 1, ST_TIMEOUT = 2, ST_COUNT = 4 };
 
-constexpr int TILE = 32;  // elements per tile = lanes of one warp
+constexpr int TILE = 32;     // elements per tile = lanes of one warp
+constexpr int AFF_ROWS = 10;  // affine record rows per tile: J^{-1} (9, row-major), det J
 
 // values per node held in a warp's shared-memory patch: inputs (u, udot
 // [, v or cotangent]) then outputs (one array, two for the adjoint)
@@ -40,6 +39,7 @@ template <typename R> struct KParams {
     int meta_bytes, umaxp;
     const int32_t *eid;         // [n_tiles][32] global element id, -1 for padding lanes
     const R *slab;              // [n_tiles][nq][3 npe + 1][32]: h_i components, then w_q J_p
+    const R *aff;               // affine path: [n_tiles][10][32] J^{-1} (row-major) and det J; nullptr = slab path
     const int32_t *emat;        // [n_tiles][32] material index, or nullptr (uniform mat0)
     const R *elam;              // [n_tiles][2][32] per-element (mu, lam), or nullptr
     const R *evol;              // [n_tiles][32] element volume (affine mass)
@@ -60,22 +60,26 @@ template <typename R> struct KParams {
 };
 
 // element-kernel launcher for one op and precision, dispatching on (element
-// type, nq); grid = number of CTAs (4 warps each, grid-striding over tiles).
+// type, nq) and on the path (affine when p.aff is set, else the slab);
+// grid = number of CTAs of wpb warps each, grid-striding over tiles.
 // Defined in k_elem.cuh and instantiated in k_force.cu / k_matvec.cu /
 // k_vjp.cu / k_diag.cu.
 template <int OP, typename R>
 cudaError_t launch_op(int et, int nq, const KParams<R> &p, int grid, int wpb, cudaStream_t s);
 
-// warps per SM the kernel of (op, et, nq, precision) can keep resident for a
-// block whose tiles hold at most `umax` unique nodes
+// warps per SM the kernel of (op, et, nq, precision, path) can keep resident
+// for a block whose tiles hold at most `umax` unique nodes
 // (CTA sizes of 1, 2 and 4 warps are tried; *wpb receives the best one)
 template <int OP, typename R>
-int occupancy_op(int et, int nq, int umax, int meta_bytes, int *wpb, std::string *why);
+int occupancy_op(int et, int nq, bool aff, int umax, int meta_bytes, int *wpb, std::string *why);
 
 // set-up kernels
 cudaError_t launch_precompute(int et, int nq, int precision, int n_tiles, const int32_t *eid,
                               const int32_t *conn_elem, int elem_base, const double *X, void *slab,
                               void *evol, int *affine_flag, int *status, cudaStream_t s);
+cudaError_t launch_precompute_affine(int et, int precision, int n_tiles, const int32_t *eid,
+                                     const int32_t *conn_elem, int elem_base, const double *X, void *aff,
+                                     void *evol, int *affine_flag, int *status, cudaStream_t s);
 cudaError_t launch_set_elam(int precision, int n_tiles, const int32_t *eid, const double *src, void *elam,
                             cudaStream_t s);
 cudaError_t launch_color_round(int n_elem, int npe, const int32_t *conn, const int32_t *inc_off,

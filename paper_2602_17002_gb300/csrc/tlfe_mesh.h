@@ -19,7 +19,8 @@ struct NewtonState;  // newton.cu
 struct BlockStore {
     int et = 0, nq = 0, npe = 0, n_elem = 0, elem_base = 0, n_tiles = 0, umax = 0;
     int n_colors = 0;
-    bool affine = false;
+    bool affine = false;             // every element affine (Sec. 6, affine case)
+    bool use_affine = false;         // kernels run on the affine path (J^{-1}, det J per element)
     bool visc = false;
     int uniform_body = 0;            // body id when every element shares it, else -1
     int64_t n_unique = 0;            // sum over tiles of the unique node count
@@ -30,6 +31,7 @@ struct BlockStore {
     unsigned char *d_meta = nullptr;  // per-tile metadata records
     int meta_bytes = 0, meta_umaxp = 0;
     void *d_slab = nullptr, *d_evol = nullptr, *d_elam = nullptr;
+    void *d_aff = nullptr;           // [n_tiles][10][32] J^{-1}, det J (affine path)
 };
 
 }  // namespace tlfe
@@ -56,6 +58,7 @@ struct tlfe_mesh {
     std::vector<tlfe_block> h_blocks;
     std::vector<double> h_elam;
     uint64_t color_seed = 0;
+    int element_path = TLFE_PATH_AUTO;
     std::vector<int32_t> node_body;  // body of each node (-1: in no element)
     std::vector<void *> allocs;
     std::map<std::tuple<int, int, int, int, size_t>, int> occ_cache;  // resident warps per SM

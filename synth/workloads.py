@@ -244,3 +244,24 @@ def newton_beams(n_bodies: int = 64, seed: int = 5, ne_range=(2e4, 3e5),
         model=np.full(n_bodies, NEOHOOKE, np.int32), params=params,
         u=np.zeros_like(X), udot=np.zeros_like(X), v=None,
         fixed=np.concatenate(fixed))
+
+
+def split_bodies(wl: Workload) -> List[Workload]:
+    """One single-body workload per body of a one-block workload whose bodies
+    own contiguous node ranges (as newton_beams builds them); node ids are
+    renumbered from zero and per-node arrays sliced."""
+    assert len(wl.blocks) == 1
+    blk = wl.blocks[0]
+    out = []
+    for b in range(wl.n_bodies):
+        sel = blk.body == b
+        conn = blk.conn[sel]
+        lo, hi = int(conn.min()), int(conn.max()) + 1
+        sl = slice(lo, hi)
+        pick = lambda a: None if a is None else np.ascontiguousarray(a[sl])  # noqa: E731
+        out.append(Workload(
+            name=f"{wl.name}_body{b}", X=np.ascontiguousarray(wl.X[sl]),
+            blocks=[Block(blk.etype, blk.nq, (conn - lo).astype(np.int32), np.zeros(conn.shape[0], np.int32))],
+            model=wl.model[b:b + 1].copy(), params=wl.params[b:b + 1].copy(),
+            u=pick(wl.u), udot=pick(wl.udot), v=pick(wl.v), fixed=pick(wl.fixed)))
+    return out

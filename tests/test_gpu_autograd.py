@@ -14,41 +14,91 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-def test_loss_gradient_matches_finite_differences():
+def _fd_directions(wl, theta0, rng):
+    """(name, direction, FD step) for u, udot and the per-element parameters."""
+    return [("u", rng.standard_normal(wl.X.shape), 1e-7),
+            ("udot", rng.standard_normal(wl.X.shape), 1e-4),
+            ("theta", rng.standard_normal(theta0.shape) * theta0, 1e-6)]
+
+
+def _oracle_f(wl, base, name, step):
+    """FP64 oracle force with one of (u, udot, theta) moved by `step`."""
+    u0, ud0, th0 = base
+    wl.u, wl.udot, wl.elem_mu_lambda = u0.copy(), ud0.copy(), th0.copy()
+    if name == "u":
+        wl.u = u0 + step
+    elif name == "udot":
+        wl.udot = ud0 + step
+    else:
+        wl.elem_mu_lambda = th0 + step
+    f, _ = oracle.internal_force(wl)
+    wl.u, wl.udot, wl.elem_mu_lambda = u0, ud0, th0
+    return f
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_adjoint_matches_central_differences(prec):
+    """The hand-written adjoint (tlfe_vjp) for a fixed cotangent r against
+    central differences of the FP64 oracle's r . f along random directions of
+    u, udot and the per-element (mu, lambda): relative error <= 1e-4."""
+    from paper_2602_17002_gb300 import tlfe
+    wl = synth.diff_block(cells=3)
+    theta0 = wl.elem_mu_lambda.copy()
+    base = (wl.u.copy(), wl.udot.copy(), theta0)
+    rng = np.random.default_rng(3)
+    r = rng.standard_normal(wl.X.shape)
+    mesh = tlfe.Mesh.from_workload(wl, precision=prec)
+    dt = mesh.torch_dtype
+    gu, gud, gth = mesh.vjp(torch.tensor(wl.u, dtype=torch.float64, device="cuda"),
+                            torch.tensor(wl.udot, dtype=dt, device="cuda"), torch.tensor(r, dtype=dt, device="cuda"))
+    g = {"u": gu.double().cpu().numpy(), "udot": gud.double().cpu().numpy(), "theta": gth.cpu().numpy()}
+    for name, d, e in _fd_directions(wl, theta0, rng):
+        fd = (np.sum(r * _oracle_f(wl, base, name, e * d)) - np.sum(r * _oracle_f(wl, base, name, -e * d))) / (2 * e)
+        an = float(np.sum(g[name] * d))
+        assert abs(an - fd) <= 1e-4 * abs(fd), (name, an, fd)
+
+
+def test_loss_gradient_through_autograd():
+    """Loss 1/2 |f - f_target|^2 through torch.autograd (forward
+    tlfe_internal_force, backward tlfe_vjp). FP64 mesh: against central
+    differences of the oracle loss (1e-4). FP32 mesh: against the oracle's
+    gradient for the same cotangent f - f_target (1e-4); the cotangent then
+    carries the FP32 forward's rounding, which a random-direction difference
+    of this loss amplifies through the stiffness, so there the finite
+    differences measure the forward, not the adjoint."""
     from paper_2602_17002_gb300 import tlfe
     from paper_2602_17002_gb300.autograd import internal_force
     wl = synth.diff_block(cells=3)
     theta0 = wl.elem_mu_lambda.copy()
+    base = (wl.u.copy(), wl.udot.copy(), theta0)
     wl.elem_mu_lambda = wl.extra["theta_target"]
     f_target, _ = oracle.internal_force(wl)
     wl.elem_mu_lambda = theta0
-    mesh = tlfe.Mesh.from_workload(wl, precision=tlfe.FP32)
-    u = torch.tensor(wl.u, dtype=torch.float64, device="cuda", requires_grad=True)
-    ud = torch.tensor(wl.udot, dtype=torch.float32, device="cuda", requires_grad=True)
-    th = torch.tensor(theta0, dtype=torch.float64, device="cuda", requires_grad=True)
-    ft = torch.tensor(f_target, device="cuda")
-    f = internal_force(mesh, u, ud, th)
-    loss = 0.5 * ((f.double() - ft) ** 2).sum()     # FP64 reduction of the FP32 force
-    loss.backward()
-    gu, gud, gth = u.grad.double().cpu().numpy(), ud.grad.double().cpu().numpy(), th.grad.cpu().numpy()
-
-    def L(du=0.0, dud=0.0, dth=0.0):
-        wl.u, wl.udot, wl.elem_mu_lambda = wl_u + du, wl_ud + dud, theta0 + dth
-        f64, _ = oracle.internal_force(wl)
-        wl.u, wl.udot, wl.elem_mu_lambda = wl_u, wl_ud, theta0
-        return 0.5 * np.sum((f64 - f_target) ** 2)
-
-    wl_u, wl_ud = wl.u.copy(), wl.udot.copy()
-    rng = np.random.default_rng(3)
-    for name, g, scale in (("u", gu, 1e-7), ("udot", gud, 1e-4), ("theta", gth, 1e-6)):
-        for _ in range(2):
-            shape = theta0.shape if name == "theta" else wl.X.shape
-            d = rng.standard_normal(shape) * (theta0 if name == "theta" else 1.0)
-            e = scale
-            kw = {"u": "du", "udot": "dud", "theta": "dth"}[name]
-            fd = (L(**{kw: e * d}) - L(**{kw: -e * d})) / (2 * e)
-            an = float(np.sum(g * d))
-            assert abs(an - fd) <= 1e-4 * abs(fd), (name, an, fd)
+    for prec in (0, 1):
+        mesh = tlfe.Mesh.from_workload(wl, precision=prec)
+        u = torch.tensor(wl.u, dtype=torch.float64, device="cuda", requires_grad=True)
+        ud = torch.tensor(wl.udot, dtype=mesh.torch_dtype, device="cuda", requires_grad=True)
+        th = torch.tensor(theta0, dtype=torch.float64, device="cuda", requires_grad=True)
+        ft = torch.tensor(f_target, device="cuda")
+        f = internal_force(mesh, u, ud, th)
+        loss = 0.5 * ((f.double() - ft) ** 2).sum()     # FP64 reduction
+        loss.backward()
+        g = {"u": u.grad.double().cpu().numpy(), "udot": ud.grad.double().cpu().numpy(),
+             "theta": th.grad.cpu().numpy()}
+        rng = np.random.default_rng(3)
+        if prec == 0:
+            for name, d, e in _fd_directions(wl, theta0, rng):
+                lp = 0.5 * np.sum((_oracle_f(wl, base, name, e * d) - f_target) ** 2)
+                lm = 0.5 * np.sum((_oracle_f(wl, base, name, -e * d) - f_target) ** 2)
+                fd = (lp - lm) / (2 * e)
+                an = float(np.sum(g[name] * d))
+                assert abs(an - fd) <= 1e-4 * abs(fd), (name, an, fd)
+        else:
+            cot = f.detach().double().cpu().numpy() - f_target
+            ref = dict(zip(("u", "udot", "theta"), oracle.vjp(wl, cot)))
+            for name, d, _ in _fd_directions(wl, theta0, rng):
+                an, rf = float(np.sum(g[name] * d)), float(np.sum(ref[name] * d))
+                assert abs(an - rf) <= 1e-4 * abs(rf), (name, an, rf)
 
 
 def test_adjoint_at_full_size_on_sampled_outputs():

@@ -16,6 +16,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 TOL = {0: 1e-12, 1: 2e-5}  # keyed by precision: FP64 = 0, FP32 = 1
+PATHS = [0, 1]             # element path: auto (affine blocks on the affine path), slab
 
 
 def T():
@@ -33,9 +34,9 @@ def relerr(got, ref):
     return np.abs(got - ref).max() / (den if den > 0 else 1.0)
 
 
-def run_all(wl, prec, scatter=0, aM=0.0, aK=1.0, aC=0.0, diag=True):
+def run_all(wl, prec, scatter=0, aM=0.0, aK=1.0, aC=0.0, diag=True, path=0):
     tl = T()
-    mesh = tl.Mesh.from_workload(wl, precision=prec, scatter=scatter)
+    mesh = tl.Mesh.from_workload(wl, precision=prec, scatter=scatter, element_path=path)
     dt = mesh.torch_dtype
     u, ud, v = dev(wl.u, torch.float64), dev(wl.udot, dt), dev(wl.v, dt)
     out = {"f": mesh.internal_force(u, ud), "y": mesh.tangent_matvec(u, ud, v, aM, aK, aC)}
@@ -63,45 +64,85 @@ def check_all(wl, out, prec, aM=0.0, aK=1.0, aC=0.0, diag=True):
         assert relerr(out["d"], d_ref) <= tol
 
 
+@pytest.mark.parametrize("path", PATHS)
 @pytest.mark.parametrize("prec", [0, 1])
-def test_block_t10_svk(prec):
+def test_block_t10_svk(prec, path):
     wl = synth.block_t10_svk()
-    _, out = run_all(wl, prec)
+    mesh, out = run_all(wl, prec, path=path)
+    assert mesh.info["n_affine_blocks"] == (1 if path == 0 else 0)
     check_all(wl, out, prec)
 
 
+@pytest.mark.parametrize("path", PATHS)
 @pytest.mark.parametrize("prec", [0, 1])
-def test_small_beam_nh_kv_full_operator(prec):
+def test_small_beam_nh_kv_full_operator(prec, path):
     wl = synth.small_beam(cells=(10, 2, 2))
     h = 1e-3
-    _, out = run_all(wl, prec, aM=1.0 / h, aK=h, aC=1.0)
+    _, out = run_all(wl, prec, aM=1.0 / h, aK=h, aC=1.0, path=path)
     check_all(wl, out, prec, aM=1.0 / h, aK=h, aC=1.0)
 
 
+@pytest.mark.parametrize("path", PATHS)
 @pytest.mark.parametrize("prec", [0, 1])
-def test_mixed_batch_t4_t10_h8(prec):
+def test_mixed_batch_t4_t10_h8(prec, path):
     wl = synth.batch_bodies(n_bodies=9, seed=7, ne_range=(40, 400))
     assert len(wl.blocks) >= 2
-    _, out = run_all(wl, prec)
+    _, out = run_all(wl, prec, path=path)
     check_all(wl, out, prec)
 
 
+@pytest.mark.parametrize("path", PATHS)
 @pytest.mark.parametrize("prec", [0, 1])
-def test_per_element_parameters_and_damping(prec):
+def test_per_element_parameters_and_damping(prec, path):
     wl = synth.diff_block(cells=3)
-    _, out = run_all(wl, prec, aK=1.0, aC=2.0)
+    _, out = run_all(wl, prec, aK=1.0, aC=2.0, path=path)
     check_all(wl, out, prec, aK=1.0, aC=2.0)
 
 
+@pytest.mark.parametrize("path", PATHS)
 @pytest.mark.parametrize("n_elem", [1, 31, 33, 65])
-def test_ragged_tiles(n_elem):
+def test_ragged_tiles(n_elem, path):
     base = synth.small_beam(cells=(6, 2, 2))
     blk = base.blocks[0]
     wl = Workload("ragged", base.X, [Block(blk.etype, blk.nq, blk.conn[:n_elem], blk.body[:n_elem])],
                   base.model, base.params, u=base.u, udot=base.udot, v=base.v)
     for prec in (0, 1):
-        _, out = run_all(wl, prec)
+        _, out = run_all(wl, prec, path=path)
         check_all(wl, out, prec)
+
+
+def _curved(wl, amp, seed):
+    """Move every mid-edge T10 node (and, for H8, every node) off its straight
+    position: the elements become genuinely isoparametric (non-affine)."""
+    X = wl.X.copy()
+    rng = np.random.default_rng(seed)
+    for blk in wl.blocks:
+        if blk.etype == synth.T10:
+            mids = np.unique(blk.conn[:, 4:])
+            X[mids] += rng.uniform(-amp, amp, (mids.size, 3))
+        elif blk.etype == synth.H8:
+            nodes = np.unique(blk.conn)
+            X[nodes] += rng.uniform(-amp, amp, (nodes.size, 3))
+    return Workload(wl.name + "_curved", X, wl.blocks, wl.model, wl.params, u=wl.u, udot=wl.udot, v=wl.v,
+                    elem_mu_lambda=wl.elem_mu_lambda)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_curved_elements_use_the_slab_path(prec):
+    """Non-affine T10 (curved edges) and H8 (distorted bricks): the automatic
+    path streams per-point h_i, and results match the isoparametric oracle;
+    forcing the affine path on them is refused."""
+    base = synth.batch_bodies(n_bodies=6, seed=9, ne_range=(60, 300))
+    wl = _curved(base, 0.004, 5)           # cells of 0.05 m: up to 8 % of the edge
+    mesh, out = run_all(wl, prec, path=0)
+    n_t4 = sum(b.etype == synth.T4 for b in wl.blocks)
+    assert mesh.info["n_affine_blocks"] == n_t4    # only the T4 block stays affine
+    check_all(wl, out, prec)
+    if n_t4 < len(wl.blocks):
+        tl = T()
+        with pytest.raises(tl.TLFEError) as ei:
+            tl.Mesh.from_workload(wl, precision=prec, element_path=tl.PATH_AFFINE)
+        assert ei.value.code == 7
 
 
 def test_empty_block_in_multiblock_mesh():
@@ -185,8 +226,8 @@ def test_beam_full_size_bench_configuration():
     tl = T()
     f_ref, bad = oracle.internal_force(wl)
     assert bad == 0
-    for prec, tol in ((1, 2e-5), (0, 1e-12)):
-        mesh = tl.Mesh.from_workload(wl, precision=prec)
+    for prec, tol, path in ((1, 2e-5, 0), (1, 2e-5, 1), (0, 1e-12, 0)):
+        mesh = tl.Mesh.from_workload(wl, precision=prec, element_path=path)
         dt = mesh.torch_dtype
         u, ud, v = dev(wl.u, torch.float64), dev(wl.udot, dt), dev(wl.v, dt)
         f = mesh.internal_force(u, ud)
