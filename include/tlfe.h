@@ -187,6 +187,20 @@ tlfe_status tlfe_tangent_matvec(tlfe_mesh *mesh, const void *u_dev, const void *
 tlfe_status tlfe_jacobi_diag(tlfe_mesh *mesh, const void *u_dev, const void *udot_dev,
                              double a_M, double a_K, double a_C, void *d_dev, void *stream);
 
+/* Launch-schedule autotuner (no counterpart in the paper; a property of this
+ * GPU implementation). For every element block it times the force, operator
+ * (when v_dev is given) and adjoint (when v_dev is given) kernels on the
+ * caller's state over the resident CTA sizes (4, 2, 1 warps) and both tile
+ * assignments (interleaved; contiguous runs per warp), writing into scratch
+ * arrays, and keeps the fastest schedule for later calls with the same
+ * material mode (velocity given or not). Results of later calls are unchanged
+ * up to the order of floating-point additions in the scatter.
+ * u_dev: device double [n_nodes][3]; udot_dev, v_dev: device [n_nodes][3] in
+ * the mesh dtype, or NULL. Allocates and frees scratch; synchronises `stream`.
+ * Optional: without it, the schedule comes from the occupancy API. */
+tlfe_status tlfe_autotune(tlfe_mesh *mesh, const double *u_dev, const void *udot_dev, const void *v_dev,
+                          void *stream);
+
 /* Replace the per-element Lame parameters (mu_e, lambda_e) of every element
  * (device double [n_elem][2], global element order); later calls use them in
  * place of the body materials' (mu, lambda). The first call on a handle created

@@ -224,7 +224,8 @@ static tlfe_status build_block(tlfe_mesh *m, const tlfe_mesh_desc *d, int bi, in
     B.n_tiles = (int)(eid.size() / TILE);
 
     // per tile: sorted unique node list, (element, node) -> list index, and
-    // the inverse map (unique node -> its slots i*32 + lane, with offsets)
+    // for each slot i*32 + lane its position in the node-sorted order (the
+    // positions of unique node k are [soff[k], soff[k + 1]))
     std::vector<int32_t> toff(B.n_tiles + 1, 0), tnodes;
     std::vector<uint16_t> lidx((size_t)B.n_tiles * npe * TILE, 0);
     std::vector<uint16_t> nsl((size_t)B.n_tiles * npe * TILE, 0xFFFF), soff;
@@ -262,7 +263,7 @@ static tlfe_status build_block(tlfe_mesh *m, const tlfe_mesh_desc *d, int bi, in
             for (int l = 0; l < TILE; ++l)
                 if (eid[(size_t)t * TILE + l] >= 0) {
                     const int k = lidx[((size_t)t * npe + i) * TILE + l];
-                    nsl[(size_t)t * npe * TILE + cnt[k]++] = (uint16_t)(i * TILE + l);
+                    nsl[(size_t)t * npe * TILE + i * TILE + l] = (uint16_t)(cnt[k]++);
                 }
         tnodes.insert(tnodes.end(), tmp.begin(), tmp.end());
         toff[t + 1] = (int32_t)tnodes.size();
@@ -271,7 +272,7 @@ static tlfe_status build_block(tlfe_mesh *m, const tlfe_mesh_desc *d, int bi, in
     B.n_unique = (int64_t)tnodes.size();
 
     // one fixed-size metadata record per tile, fetched by one bulk copy:
-    //   [U, 0, 0, 0 | eid[32] | node ids[umaxp] | lidx[npe][32] | nsl[npe*32] | soff[soffp]]
+    //   [U, 0, 0, 0 | eid[32] | node ids[umaxp] | lidx[npe][32] | position[npe*32] | soff[soffp]]
     const int umaxp = (B.umax + 3) / 4 * 4;
     const int soffp = (B.umax + 1 + 7) / 8 * 8;
     B.meta_bytes = 16 + 4 * TILE + 4 * umaxp + 2 * 2 * npe * TILE + 2 * soffp;
@@ -303,9 +304,11 @@ static tlfe_status build_block(tlfe_mesh *m, const tlfe_mesh_desc *d, int bi, in
             if (b.body[k] != body0) uniform = false;
     B.uniform_body = uniform ? body0 : -1;
     B.visc = false;
+    B.model = b.n_elem > 0 ? d->body_mat[body0].model : -1;
     for (int k = 0; k < b.n_elem; ++k) {
         const tlfe_material &mm = d->body_mat[have_body ? b.body[k] : 0];
         if (mm.mu_v != 0.0 || mm.lambda_v != 0.0) B.visc = true;
+        if (mm.model != B.model) B.model = -1;
         if (uniform) break;
     }
     const size_t rs = m->precision == TLFE_FP32 ? 4 : 8;
@@ -568,8 +571,17 @@ template <typename R> static const Mat<R> *mats_of(const tlfe_mesh *m);
 template <> const Mat<float> *mats_of<float>(const tlfe_mesh *m) { return m->d_mats_f; }
 template <> const Mat<double> *mats_of<double>(const tlfe_mesh *m) { return m->d_mats_d; }
 
-template <int OP, typename R>
-static tlfe_status run_block_op(tlfe_mesh *m, const BlockStore &B, KParams<R> p, cudaStream_t s)
+// material mode of a launch: the block's law when all its elements share
+// one, with the viscous term when a velocity is given and the block is damped
+static int mat_mode_of(const BlockStore &B, bool visc)
+{
+    if (B.model == MODEL_NH) return visc ? MAT_NH_KV : MAT_NH;
+    if (B.model == MODEL_SVK) return visc ? MAT_SVK_KV : MAT_SVK;
+    return MAT_ANY;
+}
+
+// fill the block-independent fields of an element launch for block B
+template <typename R> static void block_params(tlfe_mesh *m, const BlockStore &B, KParams<R> &p)
 {
     p.umax = B.umax;
     p.tnode_off = B.d_toff;
@@ -587,21 +599,35 @@ static tlfe_status run_block_op(tlfe_mesh *m, const BlockStore &B, KParams<R> p,
     p.mats = B.d_emat ? mats_of<R>(m) : nullptr;
     p.mat0 = to_mat<R>(m->h_mats[B.uniform_body >= 0 ? B.uniform_body : 0]);
     p.visc = (B.visc && p.ud) ? 1 : 0;
+    p.mat_mode = mat_mode_of(B, p.visc != 0);
     p.status = m->d_status;
-    std::string why;
-    // occupancy key: op, element type and path, quadrature size, precision, patch size
-    const int etk = B.et + (B.use_affine ? 16 : 0);
-    const int occ = m->occupancy(OP, etk, B.nq, sizeof(R), (size_t)B.umax, [&]() {
-        int wbest = 0;
-        const int v = occupancy_op<OP, R>(B.et, B.nq, B.use_affine, B.umax, B.meta_bytes, &wbest, &why);
-        m->occ_wpb[std::make_tuple(OP, etk, B.nq, (int)sizeof(R), (size_t)B.umax)] = wbest;
-        return v;
-    });
-    const int wpb = m->occ_wpb[std::make_tuple(OP, etk, B.nq, (int)sizeof(R), (size_t)B.umax)];
-    if (occ <= 0) {
-        m->occ_cache.erase(std::make_tuple(OP, etk, B.nq, (int)sizeof(R), (size_t)B.umax));
-        return fail(TLFE_E_UNSUPPORTED, "element kernel cannot be made resident: " + why);
+}
+
+// the launch schedule of (OP, block bi): from the cache, else from the occupancy API
+template <int OP, typename R>
+static tlfe_status block_sched(tlfe_mesh *m, int bi, int mat, LaunchSched *out)
+{
+    const BlockStore &B = m->blocks[bi];
+    const auto key = std::make_tuple(OP, bi, mat, (int)sizeof(R));
+    auto it = m->sched.find(key);
+    if (it == m->sched.end()) {
+        std::string why;
+        LaunchSched ls;
+        ls.wpb = 0;  // best CTA size
+        ls.resident = occupancy_op<OP, R>(B.et, B.nq, B.use_affine, mat, B.umax, B.meta_bytes, &ls.wpb, &why);
+        if (ls.resident <= 0) return fail(TLFE_E_UNSUPPORTED, "element kernel cannot be made resident: " + why);
+        it = m->sched.emplace(key, ls).first;
     }
+    *out = it->second;
+    return TLFE_OK;
+}
+
+// launch one element kernel per colour pass of block B with schedule ls
+template <int OP, typename R>
+static tlfe_status launch_block(tlfe_mesh *m, const BlockStore &B, KParams<R> p, const LaunchSched &ls,
+                                cudaStream_t s)
+{
+    p.tile_chunk = ls.chunk;
     const int n_passes = (int)B.color_tile_off.size() - 1;
     for (int c = 0; c < n_passes; ++c) {
         p.tile_begin = B.color_tile_off[c];
@@ -610,12 +636,23 @@ static tlfe_status run_block_op(tlfe_mesh *m, const BlockStore &B, KParams<R> p,
         if (tiles <= 0) continue;
         p.rmw_scatter = m->scatter == TLFE_SCATTER_COLOR ? 1 : 0;
         // one warp per tile at a time, persistent over the resident warps
-        const int warps = std::min(tiles, std::max(1, occ / wpb) * wpb * m->n_sm);
-        const int grid = std::max(1, (warps + wpb - 1) / wpb);
-        cudaError_t e = launch_op<OP, R>(B.et, B.nq, p, grid, wpb, s);
+        const int warps = std::min(tiles, std::max(1, ls.resident / ls.wpb) * ls.wpb * m->n_sm);
+        const int grid = std::max(1, (warps + ls.wpb - 1) / ls.wpb);
+        cudaError_t e = launch_op<OP, R>(B.et, B.nq, p, grid, ls.wpb, s);
         if (e != cudaSuccess) return cuda_fail(e, "element kernel launch");
     }
     return TLFE_OK;
+}
+
+template <int OP, typename R>
+static tlfe_status run_block_op(tlfe_mesh *m, int bi, KParams<R> p, cudaStream_t s)
+{
+    const BlockStore &B = m->blocks[bi];
+    block_params<R>(m, B, p);
+    LaunchSched ls;
+    tlfe_status st = block_sched<OP, R>(m, bi, p.mat_mode, &ls);
+    if (st != TLFE_OK) return st;
+    return launch_block<OP, R>(m, B, p, ls, s);
 }
 
 template <int OP, typename R>
@@ -638,12 +675,99 @@ tlfe_status run_op(tlfe_mesh *m, const void *u, const void *ud, const void *v, v
     const size_t nb = sizeof(R) * 3 * (size_t)m->n_nodes;
     if (out0) CK(cudaMemsetAsync(out0, 0, nb, s));
     if (out1) CK(cudaMemsetAsync(out1, 0, nb, s));
-    for (const BlockStore &B : m->blocks) {
-        if (B.n_elem == 0) continue;
-        tlfe_status st = run_block_op<OP, R>(m, B, p, s);
+    for (int bi = 0; bi < (int)m->blocks.size(); ++bi) {
+        if (m->blocks[bi].n_elem == 0) continue;
+        tlfe_status st = run_block_op<OP, R>(m, bi, p, s);
         if (st != TLFE_OK) return st;
     }
     return TLFE_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// Autotuner: time every resident CTA size (4, 2, 1 warps) and both tile
+// assignments (interleaved, contiguous runs) of each block's force, operator
+// and adjoint kernels on the caller's inputs, with outputs in scratch arrays,
+// and keep the fastest per (op, block, material mode).
+// ---------------------------------------------------------------------------
+
+template <int OP, typename R>
+static tlfe_status tune_block(tlfe_mesh *m, int bi, KParams<R> p, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1)
+{
+    const BlockStore &B = m->blocks[bi];
+    block_params<R>(m, B, p);
+    const int mat = p.mat_mode;
+    LaunchSched best;
+    float best_ms = 1e30f;
+    for (int wpb : {4, 2, 1}) {
+        std::string why;
+        LaunchSched ls;
+        ls.wpb = wpb;
+        ls.resident = occupancy_op<OP, R>(B.et, B.nq, B.use_affine, mat, B.umax, B.meta_bytes, &ls.wpb, &why);
+        if (ls.resident <= 0) continue;
+        for (int chunk : {0, 1}) {
+            ls.chunk = chunk;
+            tlfe_status st = launch_block<OP, R>(m, B, p, ls, s);  // warm-up
+            if (st != TLFE_OK) return st;
+            float ms[3];
+            for (int r = 0; r < 3; ++r) {
+                CK(cudaEventRecord(e0, s));
+                st = launch_block<OP, R>(m, B, p, ls, s);
+                if (st != TLFE_OK) return st;
+                CK(cudaEventRecord(e1, s));
+                CK(cudaEventSynchronize(e1));
+                CK(cudaEventElapsedTime(&ms[r], e0, e1));
+            }
+            std::sort(ms, ms + 3);
+            if (ms[1] < best_ms) {
+                best_ms = ms[1];
+                best = ls;
+            }
+        }
+    }
+    if (best.resident <= 0) return fail(TLFE_E_UNSUPPORTED, "no resident configuration for block " + std::to_string(bi));
+    best.tuned = true;
+    m->sched[std::make_tuple(OP, bi, mat, (int)sizeof(R))] = best;
+    return TLFE_OK;
+}
+
+template <typename R>
+static tlfe_status tune_all(tlfe_mesh *m, const double *u, const void *ud, const void *v, cudaStream_t s)
+{
+    const size_t nb = sizeof(R) * 3 * (size_t)m->n_nodes;
+    void *o0 = nullptr, *o1 = nullptr;
+    double *gth = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    tlfe_status st = TLFE_OK;
+    cudaError_t e = cudaMalloc(&o0, nb);
+    if (e == cudaSuccess) e = cudaMalloc(&o1, nb);
+    if (e == cudaSuccess) e = cudaMalloc(&gth, sizeof(double) * 2 * std::max(1, m->n_elem));
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) st = cuda_fail(e, "tlfe_autotune scratch");
+    KParams<R> p;
+    memset(&p, 0, sizeof(p));
+    p.u = u;
+    p.ud = (const R *)ud;
+    p.v = (const R *)v;
+    p.out0 = (R *)o0;
+    p.out1 = (R *)o1;
+    p.gth = gth;
+    p.aK = R(1);
+    p.aC = R(1);
+    for (int bi = 0; bi < (int)m->blocks.size() && st == TLFE_OK; ++bi) {
+        if (m->blocks[bi].n_elem == 0) continue;
+        st = tune_block<OP_FORCE, R>(m, bi, p, s, e0, e1);
+        if (st == TLFE_OK && v) st = tune_block<OP_MATVEC, R>(m, bi, p, s, e0, e1);
+        if (st == TLFE_OK && v) st = tune_block<OP_VJP, R>(m, bi, p, s, e0, e1);
+    }
+    cudaStreamSynchronize(s);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(o0);
+    cudaFree(o1);
+    cudaFree(gth);
+    return st;
 }
 
 template tlfe_status run_op<OP_FORCE, float>(tlfe_mesh *, const void *, const void *, const void *, void *, void *, double *, double, double, double, int, cudaStream_t);
@@ -739,6 +863,14 @@ extern "C" tlfe_status tlfe_vjp(tlfe_mesh *m, const void *u, const void *ud, con
     return m->precision == TLFE_FP32
                ? run_op<OP_VJP, float>(m, u, ud, cot, o0, o1, g_th, 0, 1, 0, 0, s)
                : run_op<OP_VJP, double>(m, u, ud, cot, o0, o1, g_th, 0, 1, 0, 0, s);
+}
+
+extern "C" tlfe_status tlfe_autotune(tlfe_mesh *m, const double *u, const void *ud, const void *v, void *stream)
+{
+    tlfe_status st = check_mesh_args(m, {u});
+    if (st != TLFE_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    return m->precision == TLFE_FP32 ? tune_all<float>(m, u, ud, v, s) : tune_all<double>(m, u, ud, v, s);
 }
 
 extern "C" tlfe_status tlfe_set_elem_mu_lambda(tlfe_mesh *m, const double *mu_lambda_dev, void *stream)

@@ -81,6 +81,7 @@ template <int BYTES> __device__ __forceinline__ void cp_async(void *dst, const v
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+__device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 
 constexpr long long MBAR_SPIN_LIMIT = 1ll << 20;  // try_wait rounds before giving up
 
@@ -243,8 +244,19 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return true;
 }
 
-template <int ET, int NQ, typename R, int OP, bool AFF>
-__global__ void __launch_bounds__(128, sizeof(R) == 4 ? 3 : 1) k_elem(const KParams<R> p)
+// Resident CTAs (of 4 warps) per SM the register allocation aims at, by
+// measurement on the beam workload: the FP32 affine force kernel fits 16
+// warps per SM in 128 registers; the adjoint, with two element vectors live,
+// runs fastest unspilled at 8 warps; FP64 kernels take all 255 registers.
+template <typename R, int OP, bool AFF> constexpr int min_ctas()
+{
+    if (sizeof(R) != 4) return 1;
+    if (OP == OP_VJP) return 2;
+    return (OP == OP_FORCE && AFF) ? 4 : 3;
+}
+
+template <int ET, int NQ, typename R, int OP, bool AFF, int MAT>
+__global__ void __launch_bounds__(128, min_ctas<R, OP, AFF>()) k_elem(const KParams<R> p)
 {
     constexpr int NPE = Elem<ET>::NPE;
     constexpr int REC = Rec<OP, R>::REC;
@@ -274,8 +286,14 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 3 : 1) k_elem(const KPar
 
     const int gw = blockIdx.x * wpb + wib;
     const int W = gridDim.x * wpb;
-    const int t0 = p.tile_begin + gw;
-    const int n_my = t0 < p.tile_end ? (p.tile_end - t0 + W - 1) / W : 0;
+    // tiles of this warp: interleaved (t0 + k W) or, with tile_chunk, one
+    // contiguous run of neighbouring tiles (which share nodes through L2)
+    const int n_tiles = p.tile_end - p.tile_begin;
+    const int per = (n_tiles + W - 1) / W;
+    const int t0 = p.tile_chunk ? p.tile_begin + gw * per : p.tile_begin + gw;
+    const int tstep = p.tile_chunk ? 1 : W;
+    const int n_my = p.tile_chunk ? max(0, min(per, n_tiles - gw * per))
+                                  : (t0 < p.tile_end ? (p.tile_end - t0 + W - 1) / W : 0);
     const bool mass_only = OP == OP_MATVEC && p.mass_only != 0;
     const int n_slices = (mass_only || AFF) ? 0 : n_my * NQ;
     const bool need_ud = p.visc != 0;
@@ -287,14 +305,14 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 3 : 1) k_elem(const KPar
     __syncwarp();
 
     auto issue = [&](int j) {  // slab slice j of this warp into ring slot j % NSLICE
-        const int t = t0 + (j / NQ) * W;
+        const int t = t0 + (j / NQ) * tstep;
         const int q = j % NQ;
         const int b = j % NSLICE;
         mbar_arrive_expect_tx(bar + b, SL::BYTES);
         bulk_g2s(ring + (size_t)b * SL::BYTES, p.slab + ((size_t)t * NQ + q) * ROWS * 32, SL::BYTES, bar + b);
     };
     auto issue_meta = [&](int k) {  // metadata (+ affine record) of the warp's k-th tile into buffer k & 1
-        const int t = t0 + k * W;
+        const int t = t0 + k * tstep;
         unsigned char *dst = mbuf + (size_t)(k & 1) * MRB;
         mbar_arrive_expect_tx(mbar + (k & 1), (uint32_t)MRB);
         bulk_g2s(dst, p.meta + (size_t)t * MB, (uint32_t)MB, mbar + (k & 1));
@@ -307,7 +325,7 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 3 : 1) k_elem(const KPar
 
     bool timed_out = false;
     for (int k = 0; k < n_my; ++k) {
-        const int t = t0 + k * W;
+        const int t = t0 + k * tstep;
         // ---- metadata of this tile (prefetched one tile ahead)
         if (!mbar_wait_bounded(mbar + (k & 1), (uint32_t)((k >> 1) & 1))) timed_out = true;
         if (__any_sync(0xffffffffu, timed_out)) {
@@ -320,26 +338,41 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 3 : 1) k_elem(const KPar
         const int e = reinterpret_cast<const int32_t *>(M + 16)[lane];
         const int32_t *nodes = reinterpret_cast<const int32_t *>(M + 16 + 128);
         const uint16_t *mlidx = reinterpret_cast<const uint16_t *>(M + 16 + 128 + 4 * p.umaxp);
-        const uint16_t *nsl = mlidx + NPE * 32;
-        const uint16_t *soff = nsl + NPE * 32;
+        const uint16_t *spos = mlidx + NPE * 32;  // slot (i, lane) -> node-sorted position
+        const uint16_t *soff = spos + NPE * 32;   // positions of unique node kk: [soff[kk], soff[kk + 1])
 
-        // ---- gather the tile's nodal inputs into the patch (one record per unique node)
+        // ---- gather the tile's nodal inputs into the patch, one record per
+        // unique node: every lane issues asynchronous copies (cp.async) for all
+        // of its nodes before waiting once, so that the load latencies of the
+        // whole tile overlap without holding registers; FP32 kernels then
+        // split the FP64 displacement in place into its (hi, lo) pair (both
+        // take the same 24 bytes of the record)
         for (int kk = lane; kk < U; kk += 32) {
             const int64_t n = nodes[kk];
             R *rec = work + (size_t)kk * REC;
-            const double ux = __ldg(p.u + 3 * n), uy = __ldg(p.u + 3 * n + 1), uz = __ldg(p.u + 3 * n + 2);
-            if constexpr (sizeof(R) == 4) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) cp_async<8>(reinterpret_cast<double *>(rec) + a, p.u + 3 * n + a);
+            if (need_ud)
+#pragma unroll
+                for (int a = 0; a < 3; ++a) cp_async<sizeof(R)>(rec + OFF_UD + a, p.ud + 3 * n + a);
+            if (HAS_V)
+#pragma unroll
+                for (int a = 0; a < 3; ++a) cp_async<sizeof(R)>(rec + OFF_V + a, p.v + 3 * n + a);
+        }
+        cp_async_commit();
+        cp_async_wait<0>();
+        if constexpr (sizeof(R) == 4) {
+            for (int kk = lane; kk < U; kk += 32) {
+                R *rec = work + (size_t)kk * REC;
+                const double2 u01 = *reinterpret_cast<const double2 *>(rec);
+                const double u2 = reinterpret_cast<const double *>(rec)[2];
                 float h[3], l[3];
-                split_f64(ux, h[0], l[0]);
-                split_f64(uy, h[1], l[1]);
-                split_f64(uz, h[2], l[2]);
+                split_f64(u01.x, h[0], l[0]);
+                split_f64(u01.y, h[1], l[1]);
+                split_f64(u2, h[2], l[2]);
                 *reinterpret_cast<float4 *>(rec) = make_float4(h[0], h[1], h[2], l[0]);
                 *reinterpret_cast<float2 *>(rec + 4) = make_float2(l[1], l[2]);
-            } else {
-                st3c<0>(rec, R(ux), R(uy), R(uz));
             }
-            if (need_ud) st3c<OFF_UD>(rec, __ldg(p.ud + 3 * n), __ldg(p.ud + 3 * n + 1), __ldg(p.ud + 3 * n + 2));
-            if (HAS_V) st3c<OFF_V>(rec, __ldg(p.v + 3 * n), __ldg(p.v + 3 * n + 1), __ldg(p.v + 3 * n + 2));
         }
         int li[NPE];
 #pragma unroll
@@ -351,7 +384,12 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 3 : 1) k_elem(const KPar
             m.mu = p.elam[((size_t)t * 2 + 0) * 32 + lane];
             m.lam = p.elam[((size_t)t * 2 + 1) * 32 + lane];
         }
-        const bool visc = need_ud && (m.mu_v != R(0) || m.lam_v != R(0));
+        // material: the law and the presence of the viscous term are
+        // compile-time constants when the block allows (MAT != MAT_ANY)
+        if constexpr (MAT == MAT_NH || MAT == MAT_NH_KV) m.model = MODEL_NH;
+        if constexpr (MAT == MAT_SVK || MAT == MAT_SVK_KV) m.model = MODEL_SVK;
+        const bool visc = MAT == MAT_ANY ? (need_ud && (m.mu_v != R(0) || m.lam_v != R(0)))
+                                         : (MAT == MAT_NH_KV || MAT == MAT_SVK_KV);
         // affine path: J^{-1} and det J of this lane's element (Sec. 6, affine case)
         R Ji[9], detJ = R(0);
         if constexpr (AFF) {
@@ -585,6 +623,25 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 3 : 1) k_elem(const KPar
         }
         if (timed_out) break;
 
+        // ---- the next tile's nodal inputs towards L2 while this tile scatters
+        // (its metadata was requested at the start of this tile)
+        if (k + 1 < n_my) {
+            if (!mbar_wait_bounded(mbar + ((k + 1) & 1), (uint32_t)(((k + 1) >> 1) & 1))) timed_out = true;
+            if (__any_sync(0xffffffffu, timed_out)) {
+                timed_out = true;
+                break;
+            }
+            const unsigned char *Mn = mbuf + (size_t)((k + 1) & 1) * MRB;
+            const int Un = *reinterpret_cast<const int32_t *>(Mn);
+            const int32_t *nodes_n = reinterpret_cast<const int32_t *>(Mn + 16 + 128);
+            for (int kk = lane; kk < Un; kk += 32) {
+                const int64_t n = nodes_n[kk];
+                prefetch_l2(p.u + 3 * n);
+                if (need_ud) prefetch_l2(p.ud + 3 * n);
+                if (HAS_V) prefetch_l2(p.v + 3 * n);
+            }
+        }
+
         // consistent mass of affine elements: m_ij = rho V Mhat_ij (Sec. 4.1)
         if ((OP == OP_MATVEC || OP == OP_DIAG) && p.aM != R(0)) {
             const R c = p.aM * m.rho * p.evol[(size_t)t * 32 + lane];
@@ -618,29 +675,35 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 3 : 1) k_elem(const KPar
         const int nbad = __reduce_add_sync(0xffffffffu, bad);
         if (lane == 0 && nbad) atomicAdd(p.status + ST_INVERTED, nbad);
 
-        // ---- per output field: element vectors into slots [i * 32 + lane][3]
-        // (the patch is dead now), then one lane per unique node sums its
-        // slots and adds them to the global array
+        // ---- per output field: each lane writes its element vector into the
+        // node-sorted position array (the patch is dead now), then one lane per
+        // unique node sums that node's contiguous positions and adds the sum
+        // to the global array
 #pragma unroll
         for (int fo = 0; fo < NFO; ++fo) {
             R *out = fo == 0 ? p.out0 : p.out1;
             __syncwarp();
             if (valid) {
 #pragma unroll
-                for (int i = 0; i < NPE; ++i)
+                for (int i = 0; i < NPE; ++i) {
+                    const int ps = spos[i * 32 + lane];
 #pragma unroll
-                    for (int d = 0; d < 3; ++d) work[(i * 32 + lane) * 3 + d] = fo == 0 ? acc0[i][d] : acc1[i][d];
+                    for (int d = 0; d < 3; ++d) work[ps * 3 + d] = fo == 0 ? acc0[i][d] : acc1[i][d];
+                }
             }
             __syncwarp();
             for (int kk = lane; kk < U; kk += 32) {
                 const int64_t n = nodes[kk];
                 const int s0 = soff[kk], s1e = soff[kk + 1];
                 R a0 = R(0), a1 = R(0), a2 = R(0);
-                for (int sidx = s0; sidx < s1e; ++sidx) {
-                    const int sl2 = nsl[sidx];
-                    a0 += work[sl2 * 3 + 0];
-                    a1 += work[sl2 * 3 + 1];
-                    a2 += work[sl2 * 3 + 2];
+                for (int sb = s0; sb < s1e; sb += 4) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (sb + j < s1e) {
+                            a0 += work[(sb + j) * 3 + 0];
+                            a1 += work[(sb + j) * 3 + 1];
+                            a2 += work[(sb + j) * 3 + 2];
+                        }
                 }
                 if (p.rmw_scatter) {
                     out[3 * n] += a0;
@@ -667,17 +730,32 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 3 : 1) k_elem(const KPar
     }
 }
 
-template <int OP, typename R, bool AFF> static void (*kernel_for_(int et, int nq))(const KParams<R>)
+template <int OP, typename R, bool AFF, int MAT> static void (*kernel_for_(int et, int nq))(const KParams<R>)
 {
-    if (et == ET_T4 && nq == 1) return k_elem<ET_T4, 1, R, OP, AFF>;
-    if (et == ET_T10 && nq == 4) return k_elem<ET_T10, 4, R, OP, AFF>;
-    if (et == ET_T10 && nq == 5) return k_elem<ET_T10, 5, R, OP, AFF>;
-    if (et == ET_H8 && nq == 8) return k_elem<ET_H8, 8, R, OP, AFF>;
+    if (et == ET_T4 && nq == 1) return k_elem<ET_T4, 1, R, OP, AFF, MAT>;
+    if (et == ET_T10 && nq == 4) return k_elem<ET_T10, 4, R, OP, AFF, MAT>;
+    if (et == ET_T10 && nq == 5) return k_elem<ET_T10, 5, R, OP, AFF, MAT>;
+    if (et == ET_H8 && nq == 8) return k_elem<ET_H8, 8, R, OP, AFF, MAT>;
     return nullptr;
 }
-template <int OP, typename R> static void (*kernel_for(int et, int nq, bool aff))(const KParams<R>)
+// FP32 kernels are specialised on the material mode; FP64 kernels (the plain
+// reference path, FP64-pipe bound) use the generic mode only
+template <int OP, typename R, bool AFF> static void (*kernel_for_m(int et, int nq, int mat))(const KParams<R>)
 {
-    return aff ? kernel_for_<OP, R, true>(et, nq) : kernel_for_<OP, R, false>(et, nq);
+    if constexpr (sizeof(R) == 4) {
+        switch (mat) {
+        case MAT_NH: return kernel_for_<OP, R, AFF, MAT_NH>(et, nq);
+        case MAT_NH_KV: return kernel_for_<OP, R, AFF, MAT_NH_KV>(et, nq);
+        case MAT_SVK: return kernel_for_<OP, R, AFF, MAT_SVK>(et, nq);
+        case MAT_SVK_KV: return kernel_for_<OP, R, AFF, MAT_SVK_KV>(et, nq);
+        default: break;
+        }
+    }
+    return kernel_for_<OP, R, AFF, MAT_ANY>(et, nq);
+}
+template <int OP, typename R> static void (*kernel_for(int et, int nq, bool aff, int mat))(const KParams<R>)
+{
+    return aff ? kernel_for_m<OP, R, true>(et, nq, mat) : kernel_for_m<OP, R, false>(et, nq, mat);
 }
 
 template <int OP, typename R, bool AFF> size_t smem_for_(int et, int umax, int meta_bytes, int wpb)
@@ -692,18 +770,21 @@ template <int OP, typename R> size_t smem_for(int et, int umax, int meta_bytes, 
     return aff ? smem_for_<OP, R, true>(et, umax, meta_bytes, wpb) : smem_for_<OP, R, false>(et, umax, meta_bytes, wpb);
 }
 
-// resident warps per SM for the best CTA size among 4, 2 and 1 warps
+// resident warps per SM for the best CTA size among 4, 2 and 1 warps, or for
+// the CTA size *wpb_io when it is positive on entry
 template <int OP, typename R>
-int occupancy_op(int et, int nq, bool aff, int umax, int meta_bytes, int *wpb_out, std::string *why)
+int occupancy_op(int et, int nq, bool aff, int mat, int umax, int meta_bytes, int *wpb_io, std::string *why)
 {
-    void (*kern)(const KParams<R>) = kernel_for<OP, R>(et, nq, aff);
-    *wpb_out = 0;
+    void (*kern)(const KParams<R>) = kernel_for<OP, R>(et, nq, aff, mat);
+    const int only = *wpb_io;
+    *wpb_io = 0;
     if (!kern) {
         *why = "no kernel for this element type and quadrature size";
         return 0;
     }
     int best = 0;
     for (int wpb : {4, 2, 1}) {
+        if (only > 0 && wpb != only) continue;
         const size_t smem = smem_for<OP, R>(et, umax, meta_bytes, wpb, aff);
         if (smem > 227 * 1024) continue;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -715,7 +796,7 @@ int occupancy_op(int et, int nq, bool aff, int umax, int meta_bytes, int *wpb_ou
         }
         if (nb * wpb > best) {
             best = nb * wpb;
-            *wpb_out = wpb;
+            *wpb_io = wpb;
         }
     }
     if (best == 0)
@@ -724,12 +805,13 @@ int occupancy_op(int et, int nq, bool aff, int umax, int meta_bytes, int *wpb_ou
     return best;
 }
 
-// launch on the affine path when p.aff is set, else on the isoparametric (slab) path
+// launch on the affine path when p.aff is set, else on the isoparametric
+// (slab) path; material mode p.mat_mode
 template <int OP, typename R>
 cudaError_t launch_op(int et, int nq, const KParams<R> &p, int grid, int wpb, cudaStream_t s)
 {
     const bool aff = p.aff != nullptr;
-    void (*kern)(const KParams<R>) = kernel_for<OP, R>(et, nq, aff);
+    void (*kern)(const KParams<R>) = kernel_for<OP, R>(et, nq, aff, p.mat_mode);
     if (!kern) return cudaErrorInvalidValue;
     const size_t smem = smem_for<OP, R>(et, p.umax, p.meta_bytes, wpb, aff);
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -14,6 +14,9 @@ namespace tlfe {
 
 enum { OP_FORCE = 0, OP_MATVEC = 1, OP_VJP = 2, OP_DIAG = 3 };
 enum { ST_INVERTED = 0, ST_NONFINITE = 1, ST_TIMEOUT = 2, ST_COUNT = 4 };
+// material modes of an element launch: the law and the viscous term fixed at
+// compile time, or both read per element (MAT_ANY)
+enum { MAT_ANY = 0, MAT_NH = 1, MAT_NH_KV = 2, MAT_SVK = 3, MAT_SVK_KV = 4 };
 
 constexpr int TILE = 32;     // elements per tile = lanes of one warp
 constexpr int AFF_ROWS = 10;  // affine record rows per tile: J^{-1} (9, row-major), det J
@@ -33,8 +36,8 @@ template <typename R> struct KParams {
     const uint16_t *lidx;       // [n_tiles][npe][32] index of (elem, node) into the tile's list
     // per-tile metadata records of meta_bytes each (16-byte multiple):
     //   int32 U, 3 x pad | int32 eid[32] | int32 node id[umaxp] | u16 lidx[npe][32] |
-    //   u16 slot list[npe * 32] (slots i * 32 + lane of each unique node, by node) |
-    //   u16 slot offsets[U + 1] (padded)
+    //   u16 position[npe * 32] (slot i * 32 + lane -> its place in the node-sorted order) |
+    //   u16 node offsets[U + 1] into that order (padded)
     const unsigned char *meta;
     int meta_bytes, umaxp;
     const int32_t *eid;         // [n_tiles][32] global element id, -1 for padding lanes
@@ -56,6 +59,8 @@ template <typename R> struct KParams {
     int mass_only;              // operator product with a_K = a_C = 0: no quadrature loop, no slab stream
     int rmw_scatter;            // 1: plain read-add-write (colour passes), 0: atomics
     int visc;                   // udot given and material damped somewhere in the block
+    int mat_mode;               // MAT_* (compile-time material of the launched kernel)
+    int tile_chunk;             // 1: each warp takes a contiguous run of tiles; 0: interleaved
     int *status;                // [ST_COUNT]
 };
 
@@ -71,7 +76,7 @@ cudaError_t launch_op(int et, int nq, const KParams<R> &p, int grid, int wpb, cu
 // for a block whose tiles hold at most `umax` unique nodes
 // (CTA sizes of 1, 2 and 4 warps are tried; *wpb receives the best one)
 template <int OP, typename R>
-int occupancy_op(int et, int nq, bool aff, int umax, int meta_bytes, int *wpb, std::string *why);
+int occupancy_op(int et, int nq, bool aff, int mat, int umax, int meta_bytes, int *wpb, std::string *why);
 
 // set-up kernels
 cudaError_t launch_precompute(int et, int nq, int precision, int n_tiles, const int32_t *eid,

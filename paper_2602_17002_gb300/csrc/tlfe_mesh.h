@@ -16,11 +16,19 @@ namespace tlfe {
 struct NewtonState;  // newton.cu
 
 // One element block as stored on the device.
+struct LaunchSched {
+    int resident = 0;   // resident warps per SM at wpb warps per CTA (0: not resident)
+    int wpb = 0;        // warps per CTA
+    int chunk = 0;      // 1: contiguous tile runs per warp; 0: interleaved
+    bool tuned = false; // chosen by measurement
+};
+
 struct BlockStore {
     int et = 0, nq = 0, npe = 0, n_elem = 0, elem_base = 0, n_tiles = 0, umax = 0;
     int n_colors = 0;
     bool affine = false;             // every element affine (Sec. 6, affine case)
     bool use_affine = false;         // kernels run on the affine path (J^{-1}, det J per element)
+    int model = -1;                  // elastic law shared by every element of the block, or -1
     bool visc = false;
     int uniform_body = 0;            // body id when every element shares it, else -1
     int64_t n_unique = 0;            // sum over tiles of the unique node count
@@ -61,18 +69,10 @@ struct tlfe_mesh {
     int element_path = TLFE_PATH_AUTO;
     std::vector<int32_t> node_body;  // body of each node (-1: in no element)
     std::vector<void *> allocs;
-    std::map<std::tuple<int, int, int, int, size_t>, int> occ_cache;  // resident warps per SM
-    std::map<std::tuple<int, int, int, int, size_t>, int> occ_wpb;    // warps per CTA chosen
-
-    int occupancy(int op, int et, int nq, int rsize, size_t smem, const std::function<int()> &query)
-    {
-        auto key = std::make_tuple(op, et, nq, rsize, smem);
-        auto it = occ_cache.find(key);
-        if (it != occ_cache.end()) return it->second;
-        const int v = query();
-        occ_cache[key] = v;
-        return v;
-    }
+    // launch schedule of one (op, block, material mode, precision): resident
+    // warps per SM at `wpb` warps per CTA, and the tile assignment; filled from
+    // the occupancy API on first use, replaced by measurement in tlfe_autotune
+    std::map<std::tuple<int, int, int, int>, tlfe::LaunchSched> sched;
 };
 
 namespace tlfe {

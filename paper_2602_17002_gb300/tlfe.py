@@ -73,7 +73,7 @@ _lib = None
 
 EXPORTS = ["tlfe_create_mesh", "tlfe_destroy_mesh", "tlfe_get_mesh_info", "tlfe_get_colors", "tlfe_sync",
            "tlfe_internal_force", "tlfe_internal_force_host", "tlfe_tangent_matvec", "tlfe_jacobi_diag",
-           "tlfe_vjp", "tlfe_set_elem_mu_lambda", "tlfe_newton_step", "tlfe_body_norms", "tlfe_norm_noalloc", "tlfe_last_error", "tlfe_version"]
+           "tlfe_vjp", "tlfe_set_elem_mu_lambda", "tlfe_autotune", "tlfe_newton_step", "tlfe_body_norms", "tlfe_norm_noalloc", "tlfe_last_error", "tlfe_version"]
 
 
 def load(path: str = LIB_PATH) -> C.CDLL:
@@ -100,6 +100,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "tlfe_newton_step": [P, P, P, C.POINTER(tlfe_step_params), P, C.POINTER(tlfe_step_report), P],
         "tlfe_body_norms": [P, P, P, P],
         "tlfe_set_elem_mu_lambda": [P, P, P],
+        "tlfe_autotune": [P, P, P, P, P],
         "tlfe_norm_noalloc": [P, C.c_int64, P, P],
     }
     for name, args in sig.items():
@@ -281,6 +282,17 @@ class Mesh:
                                        _ptr(out), _stream(stream)))
         return out
 
+    def autotune(self, u, udot=None, v=None, stream=None):
+        """Pick launch schedules by measurement (tlfe_autotune); u float64 (n_nodes, 3),
+        udot / v in the mesh dtype or None."""
+        import torch
+        self._node_array(u, "u", torch.float64)
+        if udot is not None:
+            self._node_array(udot, "udot")
+        if v is not None:
+            self._node_array(v, "v")
+        _check(load().tlfe_autotune(self._h, _ptr(u), _ptr(udot), _ptr(v), _stream(stream)))
+
     def set_elem_mu_lambda(self, theta, stream=None):
         """theta: contiguous CUDA float64 tensor (n_elem, 2) of per-element (mu, lambda)."""
         import torch
@@ -357,6 +369,10 @@ def tlfe_jacobi_diag(mesh: Mesh, u, udot, a_M, a_K, a_C, d, stream=None):
 
 def tlfe_vjp(mesh: Mesh, u, udot, cot, stream=None):
     return mesh.vjp(u, udot, cot, stream=stream)
+
+
+def tlfe_autotune(mesh: Mesh, u, udot=None, v=None, stream=None):
+    return mesh.autotune(u, udot, v, stream)
 
 
 def tlfe_set_elem_mu_lambda(mesh: Mesh, theta, stream=None):

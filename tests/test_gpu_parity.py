@@ -244,3 +244,24 @@ def test_beam_full_size_bench_configuration():
         assert relerr(gu.double().cpu().numpy()[ks], g_ref[ks]) <= tol
         assert relerr(gud.double().cpu().numpy()[ks], gd_ref[ks]) <= tol
         mesh.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_autotuned_schedules_keep_parity(prec):
+    """tlfe_autotune picks CTA size and tile assignment by measurement; the
+    results stay within the parity bars afterwards (with and without udot,
+    i.e. both material modes of a damped block)."""
+    wl = synth.small_beam(cells=(12, 3, 3))
+    tl = T()
+    mesh = tl.Mesh.from_workload(wl, precision=prec)
+    dt = mesh.torch_dtype
+    u, ud, v = dev(wl.u, torch.float64), dev(wl.udot, dt), dev(wl.v, dt)
+    mesh.autotune(u, ud, v)
+    mesh.autotune(u, None, v)
+    out = {"f": mesh.internal_force(u, ud), "y": mesh.tangent_matvec(u, ud, v, 0.0, 1.0, 1.0)}
+    out["gu"], out["gud"], out["gth"] = mesh.vjp(u, ud, v)
+    f0 = mesh.internal_force(u, None)
+    mesh.sync()
+    check_all(wl, out, prec, aK=1.0, aC=1.0, diag=False)
+    f_ref0, _ = oracle.internal_force(wl, udot=None)
+    assert relerr(f0, f_ref0) <= TOL[prec]
