@@ -209,15 +209,18 @@ def base_line(args, world, workload, value, unit, step_ms, dtype, higher=True, *
                             "parallelism": f"replicas x{world} (one independent problem per GPU)"}, **config)}
 
 
-def timed_steps(step, steps, flush, stream, n_ev=2):
+def timed_steps(step, steps, flush, stream, n_ev=2, label="timed"):
     """Run `steps` calls of step(ev) with an L2 flush before each; step records
-    its own events ev[0..n_ev-1]; returns the per-step event lists."""
+    its own events ev[0..n_ev-1]; returns the per-step event lists. The steps
+    run inside the NVTX range `label` (profilers can select it)."""
     import torch
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(n_ev)] for _ in range(steps)]
+    torch.cuda.nvtx.range_push(label)
     for k in range(steps):
         flush.zero_()
         step(evs[k])
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     return evs
 
 
@@ -366,14 +369,14 @@ def run_beam(args, rank, world):
                 ev[3].record(stream)
         return step
 
-    def time_step(mesh, ud, v, outs, gth, steps):
+    def time_step(mesh, ud, v, outs, gth, steps, label):
         mesh.autotune(u, ud, v)
         step = make_step(mesh, u, ud, v, outs, gth)
         for _ in range(args.warmup):
             step()
         mesh.sync()
         torch.cuda.synchronize()
-        evs = timed_steps(step, steps, flush, stream, 4)
+        evs = timed_steps(step, steps, flush, stream, 4, label)
         return np.array([[e[j].elapsed_time(e[j + 1]) for j in range(3)] for e in evs])
 
     names = ["force", "matvec", "vjp"]
@@ -382,7 +385,7 @@ def run_beam(args, rank, world):
     # the isoparametric (slab) path on the same mesh: per-point h_i streamed
     ms_, ud_, v_, outs_, gth_ = make(tlfe.FP32, tlfe.PATH_SLAB)
     info_s = ms_.info
-    per_s = time_step(ms_, ud_, v_, outs_, gth_, max(3, args.steps // 2))
+    per_s = time_step(ms_, ud_, v_, outs_, gth_, max(3, args.steps // 2), "beam_slab_timed")
     ms_.close()
     ks = per_s.mean(axis=0)
     bytes_s = [info_s["stream_bytes_force"], info_s["stream_bytes_matvec"], info_s["stream_bytes_vjp"]]
@@ -391,7 +394,8 @@ def run_beam(args, rank, world):
     slab = {"kernels_ms": {n: float(t) for n, t in zip(names, ks)}, "ms_per_step": float(per_s.sum(axis=1).mean()),
             "kernels_gbs": {n: b / (t * 1e-3) / 1e9 for n, b, t in zip(names, bytes_s, ks)},
             "roofline": {"bound": "hbm", "achieved": ach_s, "peak": peak, "unit": "GB/s", "frac": ach_s / peak,
-                         "kernel": names[js], "peak_source": peak_kind, "algorithmic_bytes": bytes_s[js]}}
+                         "traffic": ncu_traffic("slab_" + names[js]), "kernel": names[js], "peak_source": peak_kind,
+                         "algorithmic_bytes": bytes_s[js]}}
 
     # the default (affine) path: the timed step, launch schedules autotuned first
     mesh, ud, v, outs, gth = make(tlfe.FP32)
@@ -405,7 +409,7 @@ def run_beam(args, rank, world):
     barrier(world)
     torch.cuda.synchronize()
     with ClockSampler(torch.cuda.current_device()) as clk:
-        evs = timed_steps(step, args.steps, flush, stream, 4)
+        evs = timed_steps(step, args.steps, flush, stream, 4, "beam_affine_timed")
     barrier(world)
     st = mesh.sync()
     per = np.array([[evs[k][j].elapsed_time(evs[k][j + 1]) for j in range(3)] for k in range(args.steps)])
@@ -463,7 +467,7 @@ def run_beam(args, rank, world):
 
     # the same step with FP64 element arithmetic (the plain path)
     m64, ud64, v64, outs64, gth64 = make(tlfe.FP64)
-    per64 = time_step(m64, ud64, v64, outs64, gth64, max(3, args.steps // 4))
+    per64 = time_step(m64, ud64, v64, outs64, gth64, max(3, args.steps // 4), "beam_fp64_timed")
     ms64 = float(per64.sum(axis=1).mean())
     st64 = m64.sync()
     m64.close()

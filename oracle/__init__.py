@@ -26,8 +26,8 @@ _lock = threading.Lock()
 _lib = None
 
 MAT_DTYPE = np.dtype([("model", np.int32), ("mu", np.float64), ("lam", np.float64),
-                      ("mu_v", np.float64), ("lam_v", np.float64), ("rho", np.float64)],
-                     align=True)
+                      ("mu_v", np.float64), ("lam_v", np.float64), ("rho", np.float64),
+                      ("mu01", np.float64)], align=True)
 NPE = {0: 4, 1: 10, 2: 8}
 
 
@@ -144,9 +144,11 @@ def precompute(etype, nq, conn, X):
     return H, wJ, bad
 
 
-def material(model, mu, lam, mu_v=0.0, lam_v=0.0, rho=1000.0):
+def material(model, mu, lam, mu_v=0.0, lam_v=0.0, rho=1000.0, mu01=0.0):
+    """Material record: model 0 SVK, 1 neo-Hookean, 2 Mooney-Rivlin (mu10 = mu/2 - mu01)."""
     m = np.zeros(1, MAT_DTYPE)
     m["model"], m["mu"], m["lam"], m["mu_v"], m["lam_v"], m["rho"] = model, mu, lam, mu_v, lam_v, rho
+    m["mu01"] = mu01
     return m
 
 
@@ -210,7 +212,9 @@ def block_materials(wl, bi):
     m = np.zeros(blk.n_elem, MAT_DTYPE)
     pb = wl.params[blk.body]
     m["model"] = wl.model[blk.body]
-    m["mu"], m["lam"], m["mu_v"], m["lam_v"], m["rho"] = pb.T
+    m["mu"], m["lam"], m["mu_v"], m["lam_v"], m["rho"] = pb.T[:5]
+    if pb.shape[1] > 5:                      # optional sixth column: Mooney-Rivlin mu01
+        m["mu01"] = pb[:, 5]
     if wl.elem_mu_lambda is not None:
         m["mu"] = wl.elem_mu_lambda[off:off + blk.n_elem, 0]
         m["lam"] = wl.elem_mu_lambda[off:off + blk.n_elem, 1]

@@ -390,10 +390,34 @@ static int has_viscous(const orc_material *m, const double *Fd)
     return Fd != NULL && (m->mu_v != 0.0 || m->lam_v != 0.0);
 }
 
+/* Mooney-Rivlin constants from the material record: the small-strain shear
+ * modulus 2 (mu10 + mu01) equals mu and the bulk modulus is k = lam + 2 mu / 3;
+ * neo-Hookean is the case mu01 = 0. */
+static void mr_constants(const orc_material *m, double *mu10, double *mu01, double *k)
+{
+    *mu01 = m->model == 2 ? m->mu01 : 0.0;
+    *mu10 = 0.5 * m->mu - *mu01;
+    *k = m->lam + 2.0 * m->mu / 3.0;
+}
+
+/* I1 = tr C and I2 = 1/2 (I1^2 - tr(C C)) of C = F^T F */
+static void invariants(const double F[9], double *I1, double *I2, double C[9])
+{
+    double Ft[9];
+    transpose3(F, Ft);
+    matmul3(Ft, F, C);
+    double trC2 = 0.0;
+    for (int a = 0; a < 9; ++a) trC2 += C[a] * C[a]; /* C symmetric: tr(C C) */
+    *I1 = C[0] + C[4] + C[8];
+    *I2 = 0.5 * (*I1 * *I1 - trC2);
+}
+
 /* P = P^e(F) + F S^v (Eq. total1PKstress). Elastic parts:
  *   SVK: P = lam (1/2 tr(F^T F) - 3/2) F + mu F F^T F - mu F  (App. C, expanded SVK P)
- *   NH : P = 2 mu10 J^{-2/3} (F - 1/3 I1 F^{-T}) + k (J - 1) J F^{-T}
- *        (App. C, Mooney-Rivlin P with mu01 = 0). */
+ *   MR : P = 2 mu10 J^{-2/3} (F - 1/3 I1 F^{-T})
+ *          + 2 mu01 J^{-4/3} (I1 F - F C - 2/3 I2 F^{-T})
+ *          + k (J - 1) J F^{-T}                      (App. C, Eq. mr_first_piola)
+ *   NH : the same with mu01 = 0. */
 int orc_stress(const orc_material *m, const double F[9], const double Fd[9], double P[9])
 {
     int status = 0;
@@ -406,21 +430,24 @@ int orc_stress(const orc_material *m, const double F[9], const double Fd[9], dou
         matmul3(FFt, F, FFtF);
         const double c = m->lam * (0.5 * trC - 1.5);
         for (int a = 0; a < 9; ++a) P[a] = c * F[a] + m->mu * FFtF[a] - m->mu * F[a];
-    } else if (m->model == 1) {
+    } else if (m->model == 1 || m->model == 2) {
         const double J = det3(F);
         if (!(J > 0.0)) {
             for (int a = 0; a < 9; ++a) P[a] = 0.0;
             return 1;
         }
-        const double mu10 = 0.5 * m->mu, k = m->lam + 2.0 * m->mu / 3.0;
-        double Fi[9], FiT[9];
+        double mu10, mu01, k;
+        mr_constants(m, &mu10, &mu01, &k);
+        double Fi[9], FiT[9], C[9], FC[9], I1, I2;
         inv3(F, J, Fi);
         transpose3(Fi, FiT);
-        double I1 = 0.0;
-        for (int a = 0; a < 9; ++a) I1 += F[a] * F[a];
+        invariants(F, &I1, &I2, C);
+        matmul3(F, C, FC);
         const double Jm23 = 1.0 / (cbrt(J) * cbrt(J));
+        const double Jm43 = Jm23 * Jm23;
         for (int a = 0; a < 9; ++a)
-            P[a] = 2.0 * mu10 * Jm23 * (F[a] - I1 / 3.0 * FiT[a]) + k * (J - 1.0) * J * FiT[a];
+            P[a] = 2.0 * mu10 * Jm23 * (F[a] - I1 / 3.0 * FiT[a]) +
+                   2.0 * mu01 * Jm43 * (I1 * F[a] - FC[a] - 2.0 / 3.0 * I2 * FiT[a]) + k * (J - 1.0) * J * FiT[a];
     } else {
         return -1;
     }
@@ -434,8 +461,8 @@ int orc_stress(const orc_material *m, const double F[9], const double Fd[9], dou
 }
 
 /* Strain-energy densities: SVK psi(E) = lam/2 (tr E)^2 + mu tr(E^2) (Eq.
- * svk_strain_energy); MR with mu01 = 0: psi = mu10 (J^{-2/3} I1 - 3) + k/2 (J-1)^2
- * (Eq. mr_strain_energy). */
+ * svk_strain_energy); MR: psi = mu10 (J^{-2/3} I1 - 3) + mu01 (J^{-4/3} I2 - 3)
+ * + k/2 (J-1)^2 (Eq. mr_strain_energy; neo-Hookean: mu01 = 0). */
 int orc_strain_energy(const orc_material *m, const double F[9], double *psi)
 {
     if (m->model == 0) {
@@ -452,16 +479,17 @@ int orc_strain_energy(const orc_material *m, const double F[9], double *psi)
         *psi = 0.5 * m->lam * tr * tr + m->mu * trE2;
         return 0;
     }
-    if (m->model == 1) {
+    if (m->model == 1 || m->model == 2) {
         const double J = det3(F);
         if (!(J > 0.0)) {
             *psi = NAN;
             return 1;
         }
-        double I1 = 0.0;
-        for (int a = 0; a < 9; ++a) I1 += F[a] * F[a];
-        const double mu10 = 0.5 * m->mu, k = m->lam + 2.0 * m->mu / 3.0;
-        *psi = mu10 * (I1 / (cbrt(J) * cbrt(J)) - 3.0) + 0.5 * k * (J - 1.0) * (J - 1.0);
+        double C[9], I1, I2, mu10, mu01, k;
+        invariants(F, &I1, &I2, C);
+        mr_constants(m, &mu10, &mu01, &k);
+        const double Jm23 = 1.0 / (cbrt(J) * cbrt(J));
+        *psi = mu10 * (I1 * Jm23 - 3.0) + mu01 * (I2 * Jm23 * Jm23 - 3.0) + 0.5 * k * (J - 1.0) * (J - 1.0);
         return 0;
     }
     return -1;
@@ -582,7 +610,8 @@ static void eye_add(double K[9], double c)
 
 /* Elastic block dP-contribution K_ij at one quadrature point (without wJ):
  *   SVK: Eq. (svk_tangent)
- *   NH : Eq. (mr_tangent) terms dt1 - dt2 + dt6 (mu01 = 0). */
+ *   MR : Eq. (mr_tangent), dt1 - dt2 + dt3 - dt4 - dt5 + dt6
+ *   NH : the same with mu01 = 0 (dt3 = dt4 = dt5 = 0). */
 static int elastic_block(const orc_material *m, const double F[9], const double *hi,
                          const double *hj, double K[9])
 {
@@ -606,15 +635,15 @@ static int elastic_block(const orc_material *m, const double F[9], const double 
         eye_add(K, -m->mu * hij);
         return 0;
     }
-    if (m->model == 1) {
+    if (m->model == 1 || m->model == 2) {
         const double J = det3(F);
         if (!(J > 0.0)) return 1;
-        const double mu10 = 0.5 * m->mu, k = m->lam + 2.0 * m->mu / 3.0;
-        double Fi[9], FiT[9];
+        double mu10, mu01, k;
+        mr_constants(m, &mu10, &mu01, &k);
+        double Fi[9], FiT[9], C[9], I1, I2;
         inv3(F, J, Fi);
         transpose3(Fi, FiT);
-        double I1 = 0.0;
-        for (int a = 0; a < 9; ++a) I1 += F[a] * F[a];
+        invariants(F, &I1, &I2, C);
         const double Jm23 = 1.0 / (cbrt(J) * cbrt(J));
         double Gi[3], Gj[3]; /* F^{-T} h_i, F^{-T} h_j */
         matvec3(FiT, hi, Gi);
@@ -632,6 +661,34 @@ static int elastic_block(const orc_material *m, const double F[9], const double 
         /* dt6 = k J [ (2J - 1)(F^{-T}h_i)(F^{-T}h_j)^T - (J - 1)(F^{-T}h_j)(F^{-T}h_i)^T ] */
         outer_add(K, k * J * (2.0 * J - 1.0), Gi, Gj);
         outer_add(K, -k * J * (J - 1.0), Gj, Gi);
+        if (mu01 != 0.0) {
+            const double Jm43 = Jm23 * Jm23;
+            double Ft[9], FFt[9], FFtFhi[3], Bj[3];
+            transpose3(F, Ft);
+            matmul3(F, Ft, FFt);
+            matvec3(FFt, Fhi, FFtFhi);
+            /* dt3 = 2 mu01 J^{-4/3} [ I1 (h_j.h_i) I + (F h_i)(2 F h_j)^T - 4/3 I1 (F h_i)(F^{-T} h_j)^T ] */
+            const double c3 = 2.0 * mu01 * Jm43;
+            eye_add(K, c3 * I1 * hij);
+            outer_add(K, c3 * 2.0, Fhi, Fhj);
+            outer_add(K, -c3 * 4.0 / 3.0 * I1, Fhi, Gj);
+            /* - dt4, dt4 = 2 mu01 J^{-4/3} [ (F h_j).(F h_i) I + (F h_j)(F h_i)^T + (h_j.h_i) F F^T
+             *               - 4/3 F F^T (F h_i)(F^{-T} h_j)^T ] */
+            eye_add(K, -c3 * dot3(Fhj, Fhi));
+            outer_add(K, -c3, Fhj, Fhi);
+            for (int a = 0; a < 9; ++a) K[a] -= c3 * hij * FFt[a];
+            outer_add(K, c3 * 4.0 / 3.0, FFtFhi, Gj);
+            /* - dt5, dt5 = 4 mu01/3 J^{-4/3} [ (F^{-T}h_i)( 2 (F h_j)^T (I1 I - F F^T) - 4/3 I2 (F^{-T}h_j)^T )
+             *               - I2 (F^{-T}h_j)(F^{-T}h_i)^T ] */
+            const double c5 = 4.0 * mu01 / 3.0 * Jm43;
+            for (int b = 0; b < 3; ++b) { /* B_j = (I1 I - F F^T)^T (F h_j) = (I1 I - F F^T)(F h_j) */
+                Bj[b] = I1 * Fhj[b];
+                for (int c = 0; c < 3; ++c) Bj[b] -= FFt[c * 3 + b] * Fhj[c];
+            }
+            outer_add(K, -c5 * 2.0, Gi, Bj);
+            outer_add(K, c5 * 4.0 / 3.0 * I2, Gi, Gj);
+            outer_add(K, c5 * I2, Gj, Gi);
+        }
         return 0;
     }
     return -1;
@@ -832,7 +889,8 @@ int orc_operator_apply(int type, int nq, int n_elem, const int32_t *conn, int n_
  *   SVK (P = lam trE F + 2 mu F E): dP/dlam = trE F, dP/dmu = 2 F E.
  *   NH  (P = mu J^{-2/3}(F - I1/3 F^{-T}) + (lam + 2mu/3)(J-1) J F^{-T}):
  *       dP/dmu  = J^{-2/3}(F - I1/3 F^{-T}) + 2/3 (J-1) J F^{-T},
- *       dP/dlam = (J-1) J F^{-T}. */
+ *       dP/dlam = (J-1) J F^{-T}.
+ *   MR  (mu10 = mu/2 - mu01, mu01 fixed): the same as NH. */
 static int stress_param_derivs(const orc_material *m, const double F[9], double dPdmu[9],
                                double dPdlam[9])
 {
@@ -853,7 +911,9 @@ static int stress_param_derivs(const orc_material *m, const double F[9], double 
         }
         return 0;
     }
-    if (m->model == 1) {
+    if (m->model == 1 || m->model == 2) {
+        /* MR: mu10 = mu/2 - mu01 with mu01 held fixed, so the mu01 term does not
+         * depend on (mu, lam) and the derivatives equal the neo-Hookean ones */
         const double J = det3(F);
         if (!(J > 0.0)) {
             memset(dPdmu, 0, sizeof(double) * 9);

@@ -34,10 +34,11 @@ extern "C" {
 #endif
 
 typedef struct {
-    int32_t model;      /* 0 SVK, 1 neo-Hookean */
-    double mu, lam;     /* Lame constants */
+    int32_t model;      /* 0 SVK, 1 neo-Hookean, 2 Mooney-Rivlin */
+    double mu, lam;     /* Lame constants (small-strain shear and Lame lambda) */
     double mu_v, lam_v; /* Kelvin-Voigt constants */
     double rho;         /* reference density */
+    double mu01;        /* Mooney-Rivlin mu01 (model 2); mu10 = mu/2 - mu01 */
 } orc_material;
 
 /* ---- parent elements (Appendix A) and quadrature (Section 6) ---------- */

@@ -187,11 +187,25 @@ def test_precompute_flags_inverted_elements():
 # ------------------------------------------------------------------------
 
 MU, LAM = 3.8e6, 5.8e6
+MU01 = 0.3 * MU / 2          # Mooney-Rivlin: mu10 = mu/2 - mu01 = 0.7 mu/2
 
 
-@pytest.mark.parametrize("model", [0, 1])
+def _mat(model):
+    """SVK (0), neo-Hookean (1) or Mooney-Rivlin (2) with the test constants."""
+    return oracle.material(model, MU, LAM, mu01=MU01 if model == 2 else 0.0)
+
+
+def mr_beam(cells=(4, 2, 2)):
+    """small_beam with a Mooney-Rivlin body (mu01 = 0.3 mu/2), no damping."""
+    wl = synth.small_beam(cells=cells, damping=0.0)
+    wl.model = np.full(wl.n_bodies, 2, np.int32)
+    wl.params = np.concatenate([wl.params, np.full((wl.n_bodies, 1), MU01)], axis=1)
+    return wl
+
+
+@pytest.mark.parametrize("model", [0, 1, 2])
 def test_stress_is_energy_gradient(model):
-    mat = oracle.material(model, MU, LAM)
+    mat = _mat(model)
     rng = np.random.default_rng(3)
     for _ in range(5):
         F = _rand_F(rng)
@@ -230,9 +244,37 @@ def test_neohooke_uniaxial_closed_form():
         assert abs(P[2, 2] - p22) < 1e-8 * (abs(p22) + 1)
 
 
-def test_neohooke_small_strain_limit_is_lame():
+def test_mooney_rivlin_uniaxial_closed_form():
+    # F = diag(l, 1, 1): J = l, I1 = l^2 + 2, I2 = 2 l^2 + 1; both isochoric
+    # terms reduce to (2 l^2 - 2) / (3 l) along x and (1 - l^2) / 3 across
+    mat = _mat(2)
+    mu10, k = MU / 2 - MU01, LAM + 2 * MU / 3
+    for l1 in (0.7, 1.0, 1.05, 1.6):
+        P, _ = oracle.stress(mat, np.diag([l1, 1.0, 1.0]))
+        a = 2 * mu10 * l1 ** (-2 / 3) + 2 * MU01 * l1 ** (-4 / 3)
+        p11 = a * (2 * l1 * l1 - 2) / (3 * l1) + k * (l1 - 1)
+        p22 = a * (1 - l1 * l1) / 3 + k * (l1 - 1) * l1
+        assert abs(P[0, 0] - p11) < 1e-8 * (abs(p11) + 1)
+        assert abs(P[1, 1] - p22) < 1e-8 * (abs(p22) + 1)
+        assert abs(P[2, 2] - p22) < 1e-8 * (abs(p22) + 1)
+        assert np.abs(P - np.diag(np.diag(P))).max() < 1e-9 * (abs(p11) + 1)
+
+
+def test_mooney_rivlin_with_zero_mu01_is_neohooke():
+    rng = np.random.default_rng(12)
+    mr0 = oracle.material(2, MU, LAM, mu01=0.0)
+    nh = _mat(1)
+    for _ in range(4):
+        F = _rand_F(rng)
+        assert np.array_equal(oracle.stress(mr0, F)[0], oracle.stress(nh, F)[0])
+        assert oracle.strain_energy(mr0, F) == oracle.strain_energy(nh, F)
+
+
+@pytest.mark.parametrize("model", [1, 2])
+def test_small_strain_limit_is_lame(model):
     # linearisation about F = I gives sigma = lam tr(eps) I + 2 mu eps
-    mat = oracle.material(1, MU, LAM)
+    # (Mooney-Rivlin: shear modulus 2 (mu10 + mu01) = mu)
+    mat = _mat(model)
     rng = np.random.default_rng(4)
     G = 1e-7 * rng.uniform(-1, 1, (3, 3))
     P, _ = oracle.stress(mat, np.eye(3) + G)
@@ -241,9 +283,9 @@ def test_neohooke_small_strain_limit_is_lame():
     assert np.abs(P - lin).max() < 1e-5 * np.abs(lin).max()
 
 
-@pytest.mark.parametrize("model", [0, 1])
+@pytest.mark.parametrize("model", [0, 1, 2])
 def test_objectivity_and_rigid_rotation(model):
-    mat = oracle.material(model, MU, LAM)
+    mat = _mat(model)
     rng = np.random.default_rng(5)
     R = _rotation(rng)
     P0, _ = oracle.stress(mat, np.eye(3))
@@ -385,10 +427,15 @@ def test_internal_force_t4_closed_form():
 # App. C: tangent blocks
 # ------------------------------------------------------------------------
 
-@pytest.mark.parametrize("builder", ["svk", "nh_kv"])
+@pytest.mark.parametrize("builder", ["svk", "nh_kv", "mr"])
 def test_tangent_matches_fd_and_symmetry(builder):
+    """Closed-form blocks (Eqs. svk_tangent, mr_tangent incl. dt3-dt5, derived
+    KV blocks) against central differences of the force, symmetry, rigid
+    translation and the transpose."""
     if builder == "svk":
         wl = synth.block_t10_svk(cells=2)
+    elif builder == "mr":
+        wl = mr_beam()
     else:
         wl = synth.small_beam(cells=(4, 2, 2))
     rng = np.random.default_rng(9)
