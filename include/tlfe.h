@@ -63,7 +63,7 @@ typedef enum {
 } tlfe_status;
 
 enum { TLFE_T4 = 0, TLFE_T10 = 1, TLFE_H8 = 2 };   /* element types (App. A; T4/H8 textbook) */
-enum { TLFE_SVK = 0, TLFE_NEOHOOKE = 1 };           /* elastic laws (Sec. 3.2) */
+enum { TLFE_SVK = 0, TLFE_NEOHOOKE = 1, TLFE_MOONEY_RIVLIN = 2 };  /* elastic laws (Sec. 3.2, App. C) */
 enum { TLFE_FP64 = 0, TLFE_FP32 = 1 };              /* element arithmetic */
 enum { TLFE_SCATTER_ATOMIC = 0, TLFE_SCATTER_COLOR = 1 };
 /* Where the element kernels take the reference gradients h_i from:
@@ -91,14 +91,18 @@ typedef struct {
     const int32_t *body;
 } tlfe_block;
 
-/* Material of one body. model = TLFE_SVK or TLFE_NEOHOOKE with Lame (mu,
- * lambda); the neo-Hookean law is the paper's Mooney-Rivlin form with mu01 = 0,
- * mu10 = mu / 2 and bulk modulus k = lambda + 2 mu / 3. mu_v, lambda_v >= 0 are
- * the Kelvin-Voigt dissipation constants (Sec. 3.2.3; 0 = undamped). rho is
- * the reference density (used by the mass matrix and the body force). */
+/* Material of one body. model = TLFE_SVK, TLFE_NEOHOOKE or TLFE_MOONEY_RIVLIN
+ * with Lame (mu, lambda). The Mooney-Rivlin law is the paper's (App. C, Eq.
+ * mr_first_piola) with mu10 = mu / 2 - mu01 and bulk modulus
+ * k = lambda + 2 mu / 3, so that its small-strain shear modulus
+ * 2 (mu10 + mu01) is mu; the neo-Hookean law is its mu01 = 0 case (mu01 is
+ * ignored for the other models). mu_v, lambda_v >= 0 are the Kelvin-Voigt
+ * dissipation constants (Sec. 3.2.3; 0 = undamped). rho is the reference
+ * density (used by the mass matrix and the body force). */
 typedef struct {
     int32_t model;
     double mu, lambda, mu_v, lambda_v, rho;
+    double mu01;
 } tlfe_material;
 
 typedef struct {

@@ -86,10 +86,13 @@ static tlfe_status validate(const tlfe_mesh_desc *d)
         if (!std::isfinite(d->X_ref[k])) return fail(TLFE_E_INVALID, "X_ref holds a non-finite value");
     for (int b = 0; b < d->n_bodies; ++b) {
         const tlfe_material &m = d->body_mat[b];
-        if (m.model != TLFE_SVK && m.model != TLFE_NEOHOOKE) return fail(TLFE_E_INVALID, "bad material model");
+        if (m.model != TLFE_SVK && m.model != TLFE_NEOHOOKE && m.model != TLFE_MOONEY_RIVLIN)
+            return fail(TLFE_E_INVALID, "bad material model");
         if (!std::isfinite(m.mu) || !std::isfinite(m.lambda) || !std::isfinite(m.mu_v) ||
             !std::isfinite(m.lambda_v) || !std::isfinite(m.rho) || m.mu_v < 0 || m.lambda_v < 0 || m.rho < 0)
             return fail(TLFE_E_INVALID, "bad material parameters");
+        if (m.model == TLFE_MOONEY_RIVLIN && !std::isfinite(m.mu01))
+            return fail(TLFE_E_INVALID, "bad Mooney-Rivlin mu01");
     }
     int64_t ne = 0;
     for (int bi = 0; bi < d->n_blocks; ++bi) {
@@ -177,6 +180,7 @@ template <typename R> static Mat<R> to_mat(const tlfe_material &s)
     m.mu_v = R(s.mu_v);
     m.lam_v = R(s.lambda_v);
     m.rho = R(s.rho);
+    m.mu01 = s.model == TLFE_MOONEY_RIVLIN ? R(s.mu01) : R(0);
     return m;
 }
 

@@ -8,11 +8,14 @@
 //   E     = (G + G^T + G^T G) / 2
 //   b - I = G + G^T + G G^T
 //   J - 1 = tr G + I2(G) + det G     (expansion of det(I + G))
-// The neo-Hookean stress of App. C (Mooney-Rivlin with mu01 = 0) is used in
-// the algebraically equal form
-//   P = [ mu J^{-5/3} dev(b - I) + k (J - 1) I ] cof(F),  cof(F) = J F^{-T},
-// which needs no division by J in the volumetric term and no cancellation of
-// the identity in the isochoric one.
+// The Mooney-Rivlin stress of App. C (Eq. mr_first_piola; neo-Hookean is
+// mu01 = 0) is used in the algebraically equal form
+//   P = [ 2 mu10 J^{-5/3} D + 2 mu01 J^{-7/3} dev(I1 b - b^2) + k (J - 1) I ] cof(F)
+// with cof(F) = J F^{-T}, D = dev(b - I) and, writing b = I + beta,
+//   dev(I1 b - b^2) = (1 + tr(beta)/3) D - dev(D D)
+// (I1 F - F C = (I1 b - b^2) F^{-T} and F = b F^{-T}), which needs no division
+// by J in the volumetric term and no cancellation of the identity in the
+// isochoric ones.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -21,7 +24,7 @@
 namespace tlfe {
 
 enum { ET_T4 = 0, ET_T10 = 1, ET_H8 = 2 };
-enum { MODEL_SVK = 0, MODEL_NH = 1 };
+enum { MODEL_SVK = 0, MODEL_NH = 1, MODEL_MR = 2 };
 
 template <int ET> struct Elem;
 template <> struct Elem<ET_T4> { static constexpr int NPE = 4; };
@@ -34,10 +37,11 @@ __host__ __device__ inline int nodes_per_elem(int et)
 }
 
 // Material record as the kernels see it (Lame constants, Kelvin-Voigt
-// constants, density) in the arithmetic type R.
+// constants, density, Mooney-Rivlin mu01 with mu10 = mu/2 - mu01; mu01 = 0
+// unless model == MODEL_MR) in the arithmetic type R.
 template <typename R> struct Mat {
     int model;
-    R mu, lam, mu_v, lam_v, rho;
+    R mu, lam, mu_v, lam_v, rho, mu01;
 };
 
 // ---------------------------------------------------------------------------
@@ -117,11 +121,12 @@ template <typename R> struct QP {
     R F[9];    // I + G
     R G[9];    // sum u_i h_i^T
     R Fd[9];   // sum udot_i h_i^T (valid when visc)
-    R S[9];    // SVK: elastic 2nd PK stress (plus viscous); NH: A = mu J^{-5/3} dev(b-I) + k (J-1) I
+    R S[9];    // SVK: elastic 2nd PK stress; MR / NH: A with P = A cof(F)
     R Sv[9];   // viscous 2nd PK stress
     R Cf[9];   // NH: cof(F)
-    R dev[9];  // NH: dev(b - I)
+    R dev[9];  // MR / NH: D = dev(b - I)
     R Jm1, J, Jm53, rJ;  // J - 1, J, J^{-5/3}, 1/J
+    R bt;      // MR: tr(b - I) / 3
     bool ok;
 };
 
@@ -209,11 +214,25 @@ __device__ __forceinline__ void stress(const Mat<R> &m, QP<R> &q, bool visc, R P
             q.dev[b * 3 + a] = s;
         }
     bt = tr3(q.dev) * third;
+    q.bt = bt;
     q.dev[0] -= bt;
     q.dev[4] -= bt;
     q.dev[8] -= bt;
+    const R c1 = (m.mu - R(2) * m.mu01) * q.Jm53;  // 2 mu10 J^{-5/3}
 #pragma unroll
-    for (int k = 0; k < 9; ++k) q.S[k] = m.mu * q.Jm53 * q.dev[k];
+    for (int k = 0; k < 9; ++k) q.S[k] = c1 * q.dev[k];
+    if (m.model == MODEL_MR) {
+        // + 2 mu01 J^{-7/3} [ (1 + tr(beta)/3) D - dev(D D) ]
+        const R c2 = R(2) * m.mu01 * q.Jm53 * q.Jm53 * q.J;
+        R DD[9];
+        mm3(q.dev, q.dev, DD);
+        const R t = tr3(DD) * third;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) q.S[k] += c2 * ((R(1) + bt) * q.dev[k] - DD[k]);
+        q.S[0] += c2 * t;
+        q.S[4] += c2 * t;
+        q.S[8] += c2 * t;
+    }
     q.S[0] += kb * q.Jm1;
     q.S[4] += kb * q.Jm1;
     q.S[8] += kb * q.Jm1;
@@ -271,9 +290,28 @@ __device__ __forceinline__ void dstress(const Mat<R> &m, const QP<R> &q, bool vi
             db[4] -= dbt;
             db[8] -= dbt;
             const R dJm53 = R(-5.0 / 3.0) * q.Jm53 * dJ * q.rJ;
+            const R mu2 = m.mu - R(2) * m.mu01;  // 2 mu10
             R dA[9];
 #pragma unroll
-            for (int k = 0; k < 9; ++k) dA[k] = m.mu * (dJm53 * q.dev[k] + q.Jm53 * db[k]);
+            for (int k = 0; k < 9; ++k) dA[k] = mu2 * (dJm53 * q.dev[k] + q.Jm53 * db[k]);
+            if (m.model == MODEL_MR) {
+                // d{ c2 [ (1 + bt) D - dev(D D) ] }, c2 = 2 mu01 J^{-7/3}
+                const R c2 = R(2) * m.mu01 * q.Jm53 * q.Jm53 * q.J;
+                const R dc2 = R(-7.0 / 3.0) * c2 * dJ * q.rJ;
+                R DD[9], dDD[9];
+                mm3(q.dev, q.dev, DD);
+                mm3(db, q.dev, dDD);
+                mm3_acc(q.dev, db, dDD);
+                const R t = tr3(DD) * third, dt = tr3(dDD) * third;
+#pragma unroll
+                for (int k = 0; k < 9; ++k)
+                    dA[k] += dc2 * ((R(1) + q.bt) * q.dev[k] - DD[k]) +
+                             c2 * (dbt * q.dev[k] + (R(1) + q.bt) * db[k] - dDD[k]);
+                const R iso = dc2 * t + c2 * dt;
+                dA[0] += iso;
+                dA[4] += iso;
+                dA[8] += iso;
+            }
             dA[0] += kb * dJ;
             dA[4] += kb * dJ;
             dA[8] += kb * dJ;
@@ -362,7 +400,8 @@ __device__ __forceinline__ void astress(const Mat<R> &m, const QP<R> &q, bool vi
             glam += t * q.F[k] * Gh[k];
         }
     } else if (q.ok) {
-        // P = [mu J^{-5/3} dev + (lam + 2mu/3)(J-1) I] cof
+        // P = [(mu - 2 mu01) J^{-5/3} D + 2 mu01 J^{-7/3} D2 + (lam + 2mu/3)(J-1) I] cof with
+        // mu01 held fixed: dP/dmu = [J^{-5/3} D + 2/3 (J-1) I] cof, dP/dlam = (J-1) cof
         R Bm[9];
 #pragma unroll
         for (int k = 0; k < 9; ++k) Bm[k] = q.Jm53 * q.dev[k];

@@ -18,7 +18,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libtlfe.so")
 
 T4, T10, H8 = 0, 1, 2
-SVK, NEOHOOKE = 0, 1
+SVK, NEOHOOKE, MOONEY_RIVLIN = 0, 1, 2
 FP64, FP32 = 0, 1
 SCATTER_ATOMIC, SCATTER_COLOR = 0, 1
 PATH_AUTO, PATH_SLAB, PATH_AFFINE = 0, 1, 2
@@ -40,7 +40,7 @@ class tlfe_block(C.Structure):
 
 class tlfe_material(C.Structure):
     _fields_ = [("model", C.c_int32), ("mu", C.c_double), ("lambda_", C.c_double),
-                ("mu_v", C.c_double), ("lambda_v", C.c_double), ("rho", C.c_double)]
+                ("mu_v", C.c_double), ("lambda_v", C.c_double), ("rho", C.c_double), ("mu01", C.c_double)]
 
 
 class tlfe_mesh_desc(C.Structure):
@@ -145,7 +145,7 @@ class Mesh:
                  scatter: int = SCATTER_ATOMIC, color_seed: int = 0, stream=None, element_path: int = PATH_AUTO):
         """X: (n_nodes, 3) float64 reference coordinates.
         blocks: (etype, n_qp, conn (n_elem, npe) int32, body (n_elem,) int32 or None).
-        materials: per body (model, mu, lam, mu_v, lam_v, rho).
+        materials: per body (model, mu, lam, mu_v, lam_v, rho[, mu01]).
         element_path: PATH_AUTO, PATH_SLAB or PATH_AFFINE (see include/tlfe.h)."""
         L = load()
         self._keep = []
@@ -160,7 +160,8 @@ class Mesh:
                                None if body is None else body.ctypes.data)
         cm = (tlfe_material * len(materials))()
         for k, mt in enumerate(materials):
-            cm[k] = tlfe_material(int(mt[0]), *[float(x) for x in mt[1:6]])
+            vals = [float(x) for x in mt[1:7]] + [0.0] * (7 - len(mt))
+            cm[k] = tlfe_material(int(mt[0]), *vals)
         eml = None
         if elem_mu_lambda is not None:
             eml = np.ascontiguousarray(elem_mu_lambda, dtype=np.float64)

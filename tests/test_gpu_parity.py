@@ -265,3 +265,27 @@ def test_autotuned_schedules_keep_parity(prec):
     check_all(wl, out, prec, aK=1.0, aC=1.0, diag=False)
     f_ref0, _ = oracle.internal_force(wl, udot=None)
     assert relerr(f0, f_ref0) <= TOL[prec]
+
+
+def _mooney_rivlin(wl, mu01_frac=0.3):
+    """The workload with every body switched to Mooney-Rivlin, mu01 = frac * mu/2."""
+    wl.model = np.full(wl.n_bodies, 2, np.int32)
+    wl.params = np.concatenate([wl.params, (mu01_frac * 0.5 * wl.params[:, :1])], axis=1)
+    return wl
+
+
+@pytest.mark.parametrize("path", PATHS)
+@pytest.mark.parametrize("prec", [0, 1])
+def test_mooney_rivlin_with_damping(prec, path):
+    """Full Mooney-Rivlin (App. C, mu01 != 0) with Kelvin-Voigt damping:
+    force, K_t v + C v, adjoint and diagonal against the oracle."""
+    wl = _mooney_rivlin(synth.small_beam(cells=(10, 2, 2)))
+    mesh, out = run_all(wl, prec, aK=1.0, aC=1.0, path=path)
+    check_all(wl, out, prec, aK=1.0, aC=1.0)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_mooney_rivlin_per_element_parameters(prec):
+    wl = _mooney_rivlin(synth.diff_block(cells=3), 0.2)
+    _, out = run_all(wl, prec)
+    check_all(wl, out, prec)
