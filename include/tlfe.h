@@ -191,7 +191,30 @@ tlfe_status tlfe_tangent_matvec(tlfe_mesh *mesh, const void *u_dev, const void *
 tlfe_status tlfe_jacobi_diag(tlfe_mesh *mesh, const void *u_dev, const void *udot_dev,
                              double a_M, double a_K, double a_C, void *d_dev, void *stream);
 
-/* Launch-schedule autotuner (no counterpart in the paper; a property of this
+/* External loads (Sec. 4), added into f_dev (device double [n_nodes][3],
+ * caller-owned; zero it first for a fresh load vector). Both calls are
+ * stream-ordered and use FP64 arithmetic with atomic accumulation.
+ *
+ * Pointwise forces (Eq. virtual_work_point_force_discrete): load k acts on
+ * global element elem_dev[k] at parent coordinates xi_dev[k][3] with force
+ * force_dev[k][3], and adds s_i(xi) force to each node i of the element.
+ *
+ * Surface tractions (Eq. virtual_work_traction_discrete): face k is local face
+ * face_dev[k] of global element elem_dev[k], loaded by the nominal traction
+ * t0_dev[k][3] (force per reference area, constant over the face); adds
+ * int s_i t0 dA0 to each node of the element by boundary quadrature on the
+ * reference configuration. Local faces: tetrahedra, face k is opposite corner
+ * k; bricks, face 2 d + s lies at parent coordinate xi_d = -1 (s = 0) or +1
+ * (s = 1). Rules: triangles 4 x 4 collapsed Gauss-Legendre, quadrilaterals
+ * 3 x 3 Gauss-Legendre, dA0 = |dX/da x dX/db| da db.
+ * Non-finite parent coordinates or a bad face id are counted in the status
+ * word (TLFE_E_NONFINITE at the next sync) and skipped. */
+tlfe_status tlfe_point_loads(tlfe_mesh *mesh, int32_t n, const int32_t *elem_dev, const double *xi_dev,
+                             const double *force_dev, double *f_dev, void *stream);
+tlfe_status tlfe_surface_traction(tlfe_mesh *mesh, int32_t n, const int32_t *elem_dev, const int32_t *face_dev,
+                                  const double *t0_dev, double *f_dev, void *stream);
+
+/* Launch-schedule autotuner/* Launch-schedule autotuner (no counterpart in the paper; a property of this
  * GPU implementation). For every element block it times the force, operator
  * (when v_dev is given) and adjoint (when v_dev is given) kernels on the
  * caller's state over the resident CTA sizes (4, 2, 1 warps) and both tile
@@ -224,8 +247,9 @@ tlfe_status tlfe_vjp(tlfe_mesh *mesh, const void *u_dev, const void *udot_dev, c
 
 /* Backward-Euler step (Sec. 7, Eqs. step_map_velocity_level and residual,
  * without constraints): find v with
- *   g(v) = M/h (v - v_n) + f_int(u_n + h v, v) - f_ff = 0,
- * f_ff_i = rho v_i b0 (Eq. virtual_work_force_field_uniform), by inexact
+ *   g(v) = M/h (v - v_n) + f_int(u_n + h v, v) - f_ff - f_ext = 0,
+ * f_ff_i = rho v_i b0 (Eq. virtual_work_force_field_uniform), f_ext the
+ * optional applied load (f_ext_dev; dead load over the step), by inexact
  * Newton: each iteration solves (M/h + h K^e + C) dv = -g by Jacobi-PCG with
  * per-body scalars (all bodies advance together, each stops on its own), and
  * stops when ||g_b|| <= newton_rtol ||g_b(v_n)|| for every body b. The residual,
@@ -242,6 +266,8 @@ typedef struct {
     int32_t max_cg;
     const uint8_t *fixed_dev;  /* device [n_nodes], or NULL */
     int32_t use_graph;         /* 1 = CUDA graph with conditional nodes, 0 = host-driven loop */
+    const double *f_ext_dev;   /* device double [n_nodes][3] applied load of the step (Sec. 4:
+                                  point loads, tractions), or NULL; read at every call */
 } tlfe_step_params;
 
 typedef struct {

@@ -318,3 +318,25 @@ def color_greedy(conn, n_nodes, seed):
     nc = _check(lib().orc_color_greedy(conn.shape[0], conn.shape[1], _p(conn), int(n_nodes),
                                        C.c_uint64(seed), _p(col)), "color")
     return col, nc
+
+
+def point_loads(wl, block, elem, xi, force):
+    """Assembled f_iP = s_i(xi_P) f_P (Sec. 4, pointwise loads) of loads at
+    parent points xi (k, 3) of block-local elements elem (k,)."""
+    blk = wl.blocks[block]
+    f = np.zeros((wl.n_nodes, 3))
+    _check(lib().orc_point_loads(blk.etype, len(elem), _p(blk.conn), _p(np.ascontiguousarray(elem, np.int32)),
+                                 _p(_f64(xi)), _p(_f64(force)), _p(f)), "point_loads")
+    return f
+
+
+def surface_traction(wl, block, elem, face, t0):
+    """Assembled f_i = int s_i t0 dA0 (Sec. 4, surface tractions) over faces
+    `face` of block-local elements `elem` with nominal tractions t0 (k, 3)."""
+    blk = wl.blocks[block]
+    f = np.zeros((wl.n_nodes, 3))
+    _check(lib().orc_surface_traction(blk.etype, len(elem), _p(blk.conn), _p(_f64(wl.X)),
+                                      _p(np.ascontiguousarray(elem, np.int32)),
+                                      _p(np.ascontiguousarray(face, np.int32)), _p(_f64(t0)), _p(f)),
+           "surface_traction")
+    return f

@@ -1026,6 +1026,139 @@ int orc_gravity(int type, int n_elem, const int32_t *conn, int n_nodes, const do
 }
 
 /* ------------------------------------------------------------------------ */
+/* Sec. 4 (Pointwise External Force Loads, Surface Traction Loads)           */
+/* ------------------------------------------------------------------------ */
+
+/* f_iP = s_i(xi_P) f_P (Eq. virtual_work_point_force_discrete), assembled:
+ * load k acts at parent point xi[k] of element elem[k] (0-based within this
+ * connectivity) with force[k]. Adds into f. */
+int orc_point_loads(int type, int n_loads, const int32_t *conn, const int32_t *elem, const double *xi,
+                    const double *force, double *f)
+{
+    const int n = orc_nodes_per_elem(type);
+    if (n < 0) return -1;
+    double s[10];
+    for (int k = 0; k < n_loads; ++k) {
+        if (orc_shape(type, xi + 3 * k, s)) return -1;
+        const int32_t *ce = conn + (size_t)elem[k] * n;
+        for (int i = 0; i < n; ++i)
+            for (int a = 0; a < 3; ++a) f[(size_t)ce[i] * 3 + a] += s[i] * force[3 * k + a];
+    }
+    return 0;
+}
+
+/* Face `face` of the parent element as a map (a, b) -> xi with its tangents
+ * dxi/da, dxi/db:
+ *   tetrahedra: face k lies opposite barycentric vertex k (L_k = 0); with the
+ *     other vertices p < q < r, L_p = 1 - a - b, L_q = a, L_r = b on the unit
+ *     triangle; xi = (L_2, L_3, L_4) in the 1-based numbering of App. A.1;
+ *   bricks: face 2 d + s is xi_d = (s ? +1 : -1); (a, b) are the other two
+ *     parent coordinates in increasing order, on [-1, 1]^2. */
+static int face_map(int type, int face, double a, double b, double xi[3], double ta[3], double tb[3])
+{
+    if (type == 0 || type == 1) {
+        if (face < 0 || face > 3) return -1;
+        int v[3], m = 0;
+        for (int j = 0; j < 4; ++j)
+            if (j != face) v[m++] = j;
+        double L[4] = {0, 0, 0, 0}, La[4] = {0, 0, 0, 0}, Lb[4] = {0, 0, 0, 0};
+        L[v[0]] = 1.0 - a - b;
+        L[v[1]] = a;
+        L[v[2]] = b;
+        La[v[0]] = -1.0;
+        La[v[1]] = 1.0;
+        Lb[v[0]] = -1.0;
+        Lb[v[2]] = 1.0;
+        for (int c = 0; c < 3; ++c) {
+            xi[c] = L[c + 1];
+            ta[c] = La[c + 1];
+            tb[c] = Lb[c + 1];
+        }
+        return 0;
+    }
+    if (type == 2) {
+        if (face < 0 || face > 5) return -1;
+        const int d = face / 2, sgn = face % 2;
+        const int d1 = d == 0 ? 1 : 0, d2 = d == 2 ? 1 : 2;
+        for (int c = 0; c < 3; ++c) ta[c] = tb[c] = 0.0;
+        xi[d] = sgn ? 1.0 : -1.0;
+        xi[d1] = a;
+        xi[d2] = b;
+        ta[d1] = 1.0;
+        tb[d2] = 1.0;
+        return 0;
+    }
+    return -1;
+}
+
+/* Face rule: tetrahedron faces 4 x 4 collapsed Gauss-Legendre on the unit
+ * triangle ((a, b) = (u, (1 - u) v), weight (1 - u)); brick faces 3 x 3
+ * Gauss-Legendre. Returns the number of points. */
+static int face_rule(int type, double *pa, double *pb, double *pw)
+{
+    double gx[4], gw[4];
+    if (type == 0 || type == 1) {
+        gauss_legendre(4, gx, gw);
+        int q = 0;
+        for (int i = 0; i < 4; ++i)
+            for (int j = 0; j < 4; ++j, ++q) {
+                const double u = 0.5 * (gx[i] + 1.0), v = 0.5 * (gx[j] + 1.0);
+                pa[q] = u;
+                pb[q] = (1.0 - u) * v;
+                pw[q] = 0.25 * gw[i] * gw[j] * (1.0 - u);
+            }
+        return 16;
+    }
+    gauss_legendre(3, gx, gw);
+    int q = 0;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j, ++q) {
+            pa[q] = gx[i];
+            pb[q] = gx[j];
+            pw[q] = gw[i] * gw[j];
+        }
+    return 9;
+}
+
+/* f_i^tr = int_{Gamma_t0} s_i t0 dA0 (Eq. virtual_work_traction_discrete) for a
+ * nominal traction t0 constant over each loaded face, by boundary quadrature
+ * on the reference configuration: dA0 = |dX/da x dX/db| da db with
+ * X(a, b) = sum_i X_i s_i(xi(a, b)). Face k is face fid[k] of element
+ * elem[k]; adds into f. */
+int orc_surface_traction(int type, int n_faces, const int32_t *conn, const double *X, const int32_t *elem,
+                         const int32_t *fid, const double *t0, double *f)
+{
+    const int n = orc_nodes_per_elem(type);
+    if (n < 0) return -1;
+    double pa[16], pb[16], pw[16], s[10], Hp[30];
+    const int nq = face_rule(type, pa, pb, pw);
+    for (int k = 0; k < n_faces; ++k) {
+        const int32_t *ce = conn + (size_t)elem[k] * n;
+        for (int q = 0; q < nq; ++q) {
+            double xi[3], ta[3], tb[3];
+            if (face_map(type, fid[k], pa[q], pb[q], xi, ta, tb)) return -1;
+            orc_shape(type, xi, s);
+            orc_shape_grad(type, xi, Hp);
+            double Xa[3] = {0, 0, 0}, Xb[3] = {0, 0, 0};
+            for (int i = 0; i < n; ++i)
+                for (int c = 0; c < 3; ++c) {
+                    const double xic = X[(size_t)ce[i] * 3 + c];
+                    for (int d = 0; d < 3; ++d) {
+                        Xa[c] += xic * Hp[i * 3 + d] * ta[d];
+                        Xb[c] += xic * Hp[i * 3 + d] * tb[d];
+                    }
+                }
+            const double nx = Xa[1] * Xb[2] - Xa[2] * Xb[1], ny = Xa[2] * Xb[0] - Xa[0] * Xb[2],
+                         nz = Xa[0] * Xb[1] - Xa[1] * Xb[0];
+            const double dA = sqrt(nx * nx + ny * ny + nz * nz) * pw[q];
+            for (int i = 0; i < n; ++i)
+                for (int a = 0; a < 3; ++a) f[(size_t)ce[i] * 3 + a] += s[i] * t0[3 * k + a] * dA;
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Section 7: backward-Euler step without constraints                        */
 /* ------------------------------------------------------------------------ */
 

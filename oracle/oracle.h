@@ -95,6 +95,12 @@ int orc_gravity(int type, int n_elem, const int32_t *conn, int n_nodes, const do
                 const orc_material *mat, const double g[3], double *f_ff);
 
 /* ---- backward-Euler Newton step, Section 7 without constraints --------- */
+/* ---- external loads (Sec. 4: pointwise loads, surface tractions) ------ */
+int orc_point_loads(int type, int n_loads, const int32_t *conn, const int32_t *elem, const double *xi,
+                    const double *force, double *f);
+int orc_surface_traction(int type, int n_faces, const int32_t *conn, const double *X, const int32_t *elem,
+                         const int32_t *fid, const double *t0, double *f);
+
 typedef struct {
     int32_t newton_iters, cg_iters, status;
     double rel_residual;

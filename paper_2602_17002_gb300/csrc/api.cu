@@ -359,9 +359,10 @@ static tlfe_status build_block(tlfe_mesh *m, const tlfe_mesh_desc *d, int bi, in
     // reference precompute (Sec. 6) on the device: first J^{-1}, det J and the
     // affine test per element; then, for blocks on the slab path, the
     // per-point h_i and w_q J_p
-    int32_t *d_conn = nullptr;
+    // the block connectivity stays on the device (external loads use it)
+    CKA(B.d_conn, sizeof(int32_t) * std::max<size_t>(1, (size_t)b.n_elem * npe), m);
+    int32_t *d_conn = B.d_conn;
     int *d_aflag = nullptr;
-    CK(cudaMalloc(&d_conn, sizeof(int32_t) * std::max<size_t>(1, (size_t)b.n_elem * npe)));
     CK(cudaMalloc(&d_aflag, sizeof(int)));
     const int one = 1;
     int aflag = 0;
@@ -388,7 +389,6 @@ static tlfe_status build_block(tlfe_mesh *m, const tlfe_mesh_desc *d, int bi, in
     if (aff_out != B.d_aff) cudaFree(aff_out);
     B.affine = aflag != 0 && b.n_elem > 0;
     if (e == cudaSuccess && d->element_path == TLFE_PATH_AFFINE && !B.affine && b.n_elem > 0) {
-        cudaFree(d_conn);
         cudaFree(d_aflag);
         return fail(TLFE_E_UNSUPPORTED, "element_path = TLFE_PATH_AFFINE but block " + std::to_string(bi) +
                                             " has non-affine elements");
@@ -406,7 +406,6 @@ static tlfe_status build_block(tlfe_mesh *m, const tlfe_mesh_desc *d, int bi, in
                                   B.d_slab, B.d_evol, d_aflag, m->d_status, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     }
-    cudaFree(d_conn);
     cudaFree(d_aflag);
     if (e != cudaSuccess) return cuda_fail(e, "reference precompute");
     return TLFE_OK;

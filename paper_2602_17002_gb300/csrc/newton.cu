@@ -63,7 +63,7 @@ struct NewtonState {
     int32_t *chunk_start = nullptr, *chunk_end = nullptr, *chunk_body = nullptr, *body_chunk_off = nullptr;
     // FP64 vectors [3N]
     double *u_n = nullptr, *v_n = nullptr, *v = nullptr, *u_cur = nullptr, *dv = nullptr, *g = nullptr,
-           *fff = nullptr, *y1 = nullptr, *y2 = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr,
+           *fff = nullptr, *fgrav = nullptr, *y1 = nullptr, *y2 = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr,
            *Ap = nullptr, *Dinv = nullptr, *gv = nullptr, *Dd = nullptr;
     // mesh-precision vectors [3N]
     float *ud32 = nullptr, *p32 = nullptr, *Ap32 = nullptr, *D32 = nullptr;
@@ -132,6 +132,13 @@ __global__ void k_residual(ChunkArgs c, const double *y1, const double *y2, cons
     }
     const double s = block_sum(acc, sh);
     if (threadIdx.x == 0) partials[ch] = s;
+}
+
+// c = a + b (FP64 node arrays)
+__global__ void k_add(int64_t n, const double *a, const double *b, double *c)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) c[i] = a[i] + b[i];
 }
 
 // Newton convergence test per body; sets the Newton WHILE condition
@@ -451,7 +458,7 @@ static tlfe_status setup_newton(tlfe_mesh *m, cudaStream_t s)
     NA(ns->chunk_end, ns->n_chunks);
     NA(ns->chunk_body, ns->n_chunks);
     NA(ns->body_chunk_off, ns->nb + 1);
-    for (double **q : {&ns->u_n, &ns->v_n, &ns->v, &ns->u_cur, &ns->dv, &ns->g, &ns->fff, &ns->y1, &ns->y2, &ns->x,
+    for (double **q : {&ns->u_n, &ns->v_n, &ns->v, &ns->u_cur, &ns->dv, &ns->g, &ns->fff, &ns->fgrav, &ns->y1, &ns->y2, &ns->x,
                        &ns->r, &ns->z, &ns->p, &ns->Ap, &ns->Dinv, &ns->gv, &ns->Dd})
         NA(*q, N3);
     for (float **q : {&ns->ud32, &ns->p32, &ns->Ap32, &ns->D32}) NA(*q, N3);
@@ -770,8 +777,9 @@ extern "C" tlfe_status tlfe_newton_step(tlfe_mesh *m, const double *u_n, const d
                                                                 prm->gravity[2], ns->gv);
         NCK(cudaGetLastError());
         tlfe_mesh *m64 = ns->twin ? ns->twin : m;
-        st = run_op<OP_MATVEC, double>(m64, ns->u_n, nullptr, ns->gv, ns->fff, nullptr, nullptr, 1.0, 0.0, 0.0, 0, s);
+        st = run_op<OP_MATVEC, double>(m64, ns->u_n, nullptr, ns->gv, ns->fgrav, nullptr, nullptr, 1.0, 0.0, 0.0, 0, s);
         if (st != TLFE_OK) return st;
+        NCK(cudaMemcpyAsync(ns->fff, ns->fgrav, 8 * N3, cudaMemcpyDeviceToDevice, s));
         st = warm(x, s);
         if (st != TLFE_OK) return st;
         ns->use_graph = prm->use_graph ? 1 : 0;
@@ -785,6 +793,13 @@ extern "C" tlfe_status tlfe_newton_step(tlfe_mesh *m, const double *u_n, const d
         }
         NCK(cudaMemcpyAsync(ns->u_n, u_n, 8 * N3, cudaMemcpyDeviceToDevice, s));
         NCK(cudaMemcpyAsync(ns->v_n, v_n, 8 * N3, cudaMemcpyDeviceToDevice, s));
+    }
+    // applied load of this step: f_ff + f_ext (Sec. 4), read by the residual
+    if (prm->f_ext_dev) {
+        k_add<<<(unsigned)((N3 + 255) / 256), 256, 0, s>>>((int64_t)N3, ns->fgrav, prm->f_ext_dev, ns->fff);
+        NCK(cudaGetLastError());
+    } else {
+        NCK(cudaMemcpyAsync(ns->fff, ns->fgrav, 8 * N3, cudaMemcpyDeviceToDevice, s));
     }
     if (ns->use_graph == 1 && prm->use_graph) {
         NCK(cudaGraphLaunch(ns->exec, s));

@@ -56,6 +56,31 @@ __host__ __device__ inline void parent_grad(int et, const double xi[3], double *
             }
 }
 
+// s_i(xi) in double: T4 barycentric; T10 corners L (2 L - 1), mid-edge nodes
+// 4 L_a L_b; H8 trilinear tensor products
+__host__ __device__ inline void shape_fn(int et, const double xi[3], double *sh)
+{
+    if (et == ET_T4 || et == ET_T10) {
+        const double L[4] = {1.0 - xi[0] - xi[1] - xi[2], xi[0], xi[1], xi[2]};
+        if (et == ET_T4) {
+            for (int k = 0; k < 4; ++k) sh[k] = L[k];
+            return;
+        }
+        for (int k = 0; k < 4; ++k) sh[k] = L[k] * (2.0 * L[k] - 1.0);
+        for (int e = 0; e < 6; ++e) {
+            int a, b;
+            t10_edge(e, a, b);
+            sh[4 + e] = 4.0 * L[a] * L[b];
+        }
+        return;
+    }
+    for (int n = 0; n < 8; ++n) {
+        double v = 1.0;
+        for (int d = 0; d < 3; ++d) v *= 0.5 * (1.0 + (((n >> d) & 1) ? xi[d] : -xi[d]));
+        sh[n] = v;
+    }
+}
+
 // Quadrature point q of the (et, nq) rule: parent coordinates and weight.
 // Tetrahedra (parent volume 1/6): 1-point centroid; 4-point degree-2 rule with
 // barycentric (a, b, b, b), a = (5 + 3 sqrt5)/20, b = (5 - sqrt5)/20, w = 1/24;

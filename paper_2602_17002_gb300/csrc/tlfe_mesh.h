@@ -40,6 +40,7 @@ struct BlockStore {
     int meta_bytes = 0, meta_umaxp = 0;
     void *d_slab = nullptr, *d_evol = nullptr, *d_elam = nullptr;
     void *d_aff = nullptr;           // [n_tiles][10][32] J^{-1}, det J (affine path)
+    int32_t *d_conn = nullptr;       // [n_elem][npe] global node ids (block element order)
 };
 
 }  // namespace tlfe

@@ -61,7 +61,7 @@ class tlfe_mesh_info(C.Structure):
 class tlfe_step_params(C.Structure):
     _fields_ = [("h", C.c_double), ("gravity", C.c_double * 3), ("newton_rtol", C.c_double),
                 ("cg_rtol", C.c_double), ("max_newton", C.c_int32), ("max_cg", C.c_int32),
-                ("fixed_dev", C.c_void_p), ("use_graph", C.c_int32)]
+                ("fixed_dev", C.c_void_p), ("use_graph", C.c_int32), ("f_ext_dev", C.c_void_p)]
 
 
 class tlfe_step_report(C.Structure):
@@ -73,7 +73,7 @@ _lib = None
 
 EXPORTS = ["tlfe_create_mesh", "tlfe_destroy_mesh", "tlfe_get_mesh_info", "tlfe_get_colors", "tlfe_sync",
            "tlfe_internal_force", "tlfe_internal_force_host", "tlfe_tangent_matvec", "tlfe_jacobi_diag",
-           "tlfe_vjp", "tlfe_set_elem_mu_lambda", "tlfe_autotune", "tlfe_newton_step", "tlfe_body_norms", "tlfe_norm_noalloc", "tlfe_last_error", "tlfe_version"]
+           "tlfe_vjp", "tlfe_set_elem_mu_lambda", "tlfe_autotune", "tlfe_point_loads", "tlfe_surface_traction", "tlfe_newton_step", "tlfe_body_norms", "tlfe_norm_noalloc", "tlfe_last_error", "tlfe_version"]
 
 
 def load(path: str = LIB_PATH) -> C.CDLL:
@@ -101,6 +101,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "tlfe_body_norms": [P, P, P, P],
         "tlfe_set_elem_mu_lambda": [P, P, P],
         "tlfe_autotune": [P, P, P, P, P],
+        "tlfe_point_loads": [P, I, P, P, P, P, P],
+        "tlfe_surface_traction": [P, I, P, P, P, P, P],
         "tlfe_norm_noalloc": [P, C.c_int64, P, P],
     }
     for name, args in sig.items():
@@ -322,16 +324,42 @@ class Mesh:
         _check(load().tlfe_body_norms(self._h, _ptr(x), _ptr(out), _stream(stream)))
         return out
 
+    def point_loads(self, elem, xi, force, out=None, stream=None):
+        """Add s_i(xi_k) force_k (Sec. 4, pointwise loads) into out (float64
+        (n_nodes, 3), zeros when None): elem (k,) int32 global element ids,
+        xi (k, 3) parent coordinates, force (k, 3), CUDA float64."""
+        import torch
+        out = self._new(torch.float64).zero_() if out is None else out
+        self._node_array(out, "out", torch.float64)
+        n = int(elem.numel())
+        _check(load().tlfe_point_loads(self._h, n, _ptr(elem), _ptr(xi), _ptr(force), _ptr(out), _stream(stream)))
+        return out
+
+    def surface_traction(self, elem, face, t0, out=None, stream=None):
+        """Add int s_i t0 dA0 (Sec. 4, surface tractions) into out: face k is
+        local face face[k] of global element elem[k] (both int32), t0 (k, 3)
+        nominal traction, CUDA float64."""
+        import torch
+        out = self._new(torch.float64).zero_() if out is None else out
+        self._node_array(out, "out", torch.float64)
+        n = int(elem.numel())
+        _check(load().tlfe_surface_traction(self._h, n, _ptr(elem), _ptr(face), _ptr(t0), _ptr(out),
+                                            _stream(stream)))
+        return out
+
     def newton_step(self, u_n, v_n, h, gravity=(0.0, 0.0, -9.81), fixed=None, newton_rtol=1e-8, cg_rtol=1e-4,
-                    max_newton=20, max_cg=1000, use_graph=True, v_out=None, stream=None):
+                    max_newton=20, max_cg=1000, use_graph=True, v_out=None, stream=None, f_ext=None):
         import torch
         self._node_array(u_n, "u_n", torch.float64)
         self._node_array(v_n, "v_n", torch.float64)
+        if f_ext is not None:
+            self._node_array(f_ext, "f_ext", torch.float64)
         v_out = self._new(torch.float64) if v_out is None else v_out
         if fixed is not None and not (fixed.is_cuda and fixed.dtype == torch.uint8 and fixed.numel() == self.n_nodes):
             raise TLFEError(1, "fixed must be a CUDA uint8 tensor with one entry per node")
         p = tlfe_step_params(float(h), (C.c_double * 3)(*[float(g) for g in gravity]), float(newton_rtol),
-                             float(cg_rtol), int(max_newton), int(max_cg), _ptr(fixed), int(bool(use_graph)))
+                             float(cg_rtol), int(max_newton), int(max_cg), _ptr(fixed), int(bool(use_graph)),
+                             _ptr(f_ext))
         rep = tlfe_step_report()
         code = load().tlfe_newton_step(self._h, _ptr(u_n), _ptr(v_n), C.byref(p), _ptr(v_out), C.byref(rep),
                                        _stream(stream))
@@ -374,6 +402,14 @@ def tlfe_vjp(mesh: Mesh, u, udot, cot, stream=None):
 
 def tlfe_autotune(mesh: Mesh, u, udot=None, v=None, stream=None):
     return mesh.autotune(u, udot, v, stream)
+
+
+def tlfe_point_loads(mesh: Mesh, elem, xi, force, f, stream=None):
+    return mesh.point_loads(elem, xi, force, f, stream)
+
+
+def tlfe_surface_traction(mesh: Mesh, elem, face, t0, f, stream=None):
+    return mesh.surface_traction(elem, face, t0, f, stream)
 
 
 def tlfe_set_elem_mu_lambda(mesh: Mesh, theta, stream=None):

@@ -154,3 +154,26 @@ def concat_meshes(meshes):
     assert all(m.etype == etype for m in meshes)
     return Mesh(np.concatenate(X), np.concatenate(conn).astype(np.int32), etype,
                 np.concatenate(body))
+
+
+def face_corners(etype: int, face: int):
+    """Local corner nodes of a parent face: tetrahedra, face k is opposite
+    vertex k (the other three corners in increasing order); bricks, face
+    2 d + s holds the corners whose bit d equals s."""
+    if etype in (T4, T10):
+        return [j for j in range(4) if j != face]
+    d, s = divmod(face, 2)
+    return [n for n in range(8) if ((n >> d) & 1) == s]
+
+
+def boundary_faces(etype: int, conn: np.ndarray):
+    """(element, local face) of every face that belongs to exactly one element."""
+    nf = 4 if etype in (T4, T10) else 6
+    seen = {}
+    for e in range(conn.shape[0]):
+        for f in range(nf):
+            key = tuple(sorted(int(conn[e, c]) for c in face_corners(etype, f)))
+            seen.setdefault(key, []).append((e, f))
+    faces = [v[0] for v in seen.values() if len(v) == 1]
+    faces.sort()
+    return np.array([e for e, _ in faces], np.int32), np.array([f for _, f in faces], np.int32)

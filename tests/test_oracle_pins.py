@@ -653,3 +653,80 @@ def test_kinematic_forms_agree_and_rigid_translation_is_exact():
     assert np.abs(f2).max() == 0.0
     f1, _ = oracle.internal_force(wl, kin_form=1)
     assert np.abs(f1).max() > 0.0          # the plain displacement form rounds
+
+
+# ------------------------------------------------------------------------
+# Sec. 4: pointwise loads and surface tractions
+# ------------------------------------------------------------------------
+
+def _outward_normals(etype, X, conn, elem, face):
+    """Unit outward normals and areas of flat boundary faces (geometry of the
+    corner nodes; the element's other corners lie on the inner side)."""
+    n_out, area = [], []
+    for e, f in zip(elem, face):
+        cs = synth.face_corners(etype, f)
+        P = X[conn[e, cs]]
+        if etype == H8:          # corners in bit order: (0, 1, 3, 2) walks the quad
+            P = P[[0, 1, 3, 2]]
+            nv = 0.5 * np.cross(P[2] - P[0], P[3] - P[1])
+        else:
+            nv = 0.5 * np.cross(P[1] - P[0], P[2] - P[0])
+        inner = X[conn[e, [c for c in range(4 if etype != H8 else 8) if c not in cs]]].mean(axis=0)
+        if np.dot(nv, inner - P[0]) > 0:
+            nv = -nv
+        a = np.linalg.norm(nv)
+        n_out.append(nv / a)
+        area.append(a)
+    return np.array(n_out), np.array(area)
+
+
+@pytest.mark.parametrize("etype,nq", [(T4, 1), (T10, 5), (H8, 8)])
+def test_traction_of_uniform_stress_balances_internal_force(etype, nq):
+    """A homogeneous deformation F = A is in equilibrium under the boundary
+    traction t0 = P(A) n0 (Sec. 4, the nominal traction induced by a stress):
+    the assembled traction load equals f_int at every node (interior nodes
+    carry neither). Also: each face's load sums to t0 times its area."""
+    m = synth.box_mesh(etype, (2, 2, 3), (1.0, 1.2, 1.5), origin=(0.3, -0.2, 0.1))
+    from synth.workloads import Block, Workload
+    rng = np.random.default_rng(31)
+    A = np.eye(3) + 0.1 * rng.uniform(-1, 1, (3, 3))
+    u = m.X @ (A - np.eye(3)).T
+    wl = Workload("uniform", m.X, [Block(etype, nq, m.conn, np.zeros(m.n_elem, np.int32))],
+                  np.array([1], np.int32), np.array([[MU, LAM, 0.0, 0.0, 1000.0]]), u=u, udot=None)
+    f_int, bad = oracle.internal_force(wl)
+    assert bad == 0
+    P, _ = oracle.stress(_mat(1), A)
+    elem, face = synth.boundary_faces(etype, m.conn)
+    nrm, area = _outward_normals(etype, m.X, m.conn, elem, face)
+    t0 = nrm @ P.T                                       # t0 = P n0 per face
+    f_tr = oracle.surface_traction(wl, 0, elem, face, t0)
+    assert np.abs(f_tr - f_int).max() < 1e-9 * np.abs(f_int).max()
+    for k in (0, len(elem) // 2, len(elem) - 1):
+        one = oracle.surface_traction(wl, 0, elem[k:k + 1], face[k:k + 1], t0[k:k + 1])
+        assert np.abs(one.sum(axis=0) - t0[k] * area[k]).max() < 1e-12 * np.abs(t0[k]).max() * area[k]
+
+
+@pytest.mark.parametrize("etype,nq", [(T4, 1), (T10, 5), (H8, 8)])
+def test_point_loads_partition_and_kronecker(etype, nq):
+    m = synth.box_mesh(etype, (2, 1, 1), (1.0, 1.0, 1.0))
+    from synth.workloads import Block, Workload
+    wl = Workload("pl", m.X, [Block(etype, nq, m.conn, np.zeros(m.n_elem, np.int32))],
+                  np.array([1], np.int32), np.array([[MU, LAM, 0.0, 0.0, 1000.0]]), u=np.zeros_like(m.X))
+    rng = np.random.default_rng(32)
+    k = 7
+    elem = rng.integers(0, m.n_elem, k).astype(np.int32)
+    if etype == H8:
+        xi = rng.uniform(-1, 1, (k, 3))
+    else:
+        L = rng.dirichlet(np.ones(4), k)
+        xi = L[:, 1:]
+    force = rng.standard_normal((k, 3))
+    f = oracle.point_loads(wl, 0, elem, xi, force)
+    assert np.abs(f.sum(axis=0) - force.sum(axis=0)).max() < 1e-12
+    # a load at a node of the parent element goes to that node only
+    node_xi = {T4: [0, 0, 0], T10: [0.5, 0, 0], H8: [1, -1, -1]}[etype]
+    node_id = {T4: 0, T10: 4, H8: 1}[etype]
+    f1 = oracle.point_loads(wl, 0, np.array([0], np.int32), np.array([node_xi], float), np.array([[1.0, 2.0, 3.0]]))
+    g = m.conn[0, node_id]
+    assert np.abs(f1[g] - [1.0, 2.0, 3.0]).max() < 1e-14
+    assert np.abs(np.delete(f1, g, axis=0)).max() < 1e-14
