@@ -80,6 +80,13 @@ def lib():
                 "orc_newton_step": [i32, i32, i32, P, i32, P, P, P, P, f64, P, P, f64, f64,
                                     i32, i32, P, P],
                 "orc_color_greedy": [i32, i32, P, i32, C.c_uint64, P],
+                "orc_point_loads": [i32, i32, P, P, P, P, P],
+                "orc_surface_traction": [i32, i32, P, P, P, P, P, P],
+                "orc_constraint_eval": [i32, i32, P, P, P, P, P],
+                "orc_constraint_jt": [i32, i32, P, P, P, P, P, P],
+                "orc_constraint_j": [i32, i32, P, P, P, P, P, P],
+                "orc_newton_step_alm": [i32, i32, i32, P, i32, P, P, P, P, f64, P, P, f64, f64, i32, i32,
+                                        i32, P, f64, f64, i32, P, P, P, P, P],
             }.items():
                 fn = getattr(L, name)
                 fn.argtypes = args
@@ -340,3 +347,72 @@ def surface_traction(wl, block, elem, face, t0):
                                       _p(np.ascontiguousarray(face, np.int32)), _p(_f64(t0)), _p(f)),
            "surface_traction")
     return f
+
+
+CON_DTYPE = np.dtype([("type", np.int32), ("elem", np.int32, (4,)), ("xi", np.float64, (4, 3)),
+                      ("d", np.float64, (3,)), ("f", np.float64)], align=True)
+CD, DIST, DP1, DP2 = 0, 1, 2, 3
+
+
+def constraints(items):
+    """Constraint records from dicts {type, elem: [..], xi: [[..], ..], d, f}
+    (points P, Q[, R, T]; elem < 0 marks a ground point at world coordinates xi)."""
+    c = np.zeros(len(items), CON_DTYPE)
+    for k, it in enumerate(items):
+        c[k]["type"] = it["type"]
+        el = list(it["elem"]) + [-1] * (4 - len(it["elem"]))
+        c[k]["elem"] = el
+        xi = np.zeros((4, 3))
+        xi[:len(it["xi"])] = it["xi"]
+        c[k]["xi"] = xi
+        c[k]["d"] = it.get("d", (0.0, 0.0, 0.0))
+        c[k]["f"] = it.get("f", 0.0)
+    return c
+
+
+def constraint_eval(wl, cons, u=None):
+    """c(q) of the constraint primitives (CD, DIST, DP1, DP2) at q = X + u."""
+    blk = wl.blocks[0]
+    out = np.zeros(len(cons))
+    _check(lib().orc_constraint_eval(blk.etype, len(cons), _p(cons), _p(blk.conn), _p(_f64(wl.X)),
+                                     _p(_f64(wl.u if u is None else u)), _p(out)), "constraint_eval")
+    return out
+
+
+def constraint_jt(wl, cons, w, u=None):
+    """C_q^T w as an (n_nodes, 3) array."""
+    blk = wl.blocks[0]
+    f = np.zeros((wl.n_nodes, 3))
+    _check(lib().orc_constraint_jt(blk.etype, len(cons), _p(cons), _p(blk.conn), _p(_f64(wl.X)),
+                                   _p(_f64(wl.u if u is None else u)), _p(_f64(w)), _p(f)), "constraint_jt")
+    return f
+
+
+def constraint_j(wl, cons, v, u=None):
+    """C_q v as an (n_cons,) array."""
+    blk = wl.blocks[0]
+    out = np.zeros(len(cons))
+    _check(lib().orc_constraint_j(blk.etype, len(cons), _p(cons), _p(blk.conn), _p(_f64(wl.X)),
+                                  _p(_f64(wl.u if u is None else u)), _p(_f64(v)), _p(out)), "constraint_j")
+    return out
+
+
+def newton_step_alm(wl, u_n, v_n, h, gravity, cons, rho, lam=None, fixed=None, newton_rtol=1e-8, cg_rtol=1e-4,
+                    max_newton=20, max_cg=2000, alm_tol=1e-10, max_outer=50):
+    """Augmented-Lagrangian backward-Euler step (Sec. 7): returns (v, lam, report)."""
+    assert len(wl.blocks) == 1
+    blk = wl.blocks[0]
+    m = block_materials(wl, 0)
+    v = np.zeros_like(_f64(wl.X))
+    lam = np.zeros(len(cons)) if lam is None else np.array(lam, dtype=np.float64)
+    rep = Report()
+    outer = C.c_int(0)
+    cn = C.c_double(0.0)
+    fx = None if fixed is None else np.ascontiguousarray(fixed, dtype=np.uint8)
+    _check(lib().orc_newton_step_alm(blk.etype, blk.nq, blk.n_elem, _p(blk.conn), wl.n_nodes, _p(_f64(wl.X)),
+                                     _p(m), _p(_f64(u_n)), _p(_f64(v_n)), C.c_double(h), _p(_f64(gravity)), _p(fx),
+                                     C.c_double(newton_rtol), C.c_double(cg_rtol), int(max_newton), int(max_cg),
+                                     len(cons), _p(cons), C.c_double(rho), C.c_double(alm_tol), int(max_outer),
+                                     _p(lam), _p(v), C.byref(rep), C.byref(outer), C.byref(cn)), "newton_step_alm")
+    return v, lam, {"newton_iters": rep.newton_iters, "cg_iters": rep.cg_iters, "status": rep.status,
+                    "rel_residual": rep.rel_residual, "outer_iters": outer.value, "c_norm": cn.value}

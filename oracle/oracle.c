@@ -1159,7 +1159,130 @@ int orc_surface_traction(int type, int n_faces, const int32_t *conn, const doubl
 }
 
 /* ------------------------------------------------------------------------ */
-/* Section 7: backward-Euler step without constraints                        */
+/* Bilateral constraints (Sec. 3.x primitives DP1, DP2, DIST, CD)            */
+/* ------------------------------------------------------------------------ */
+
+/* Position r of constraint point p: sum_i s_i(xi_p) (X_i + u_i) of element
+ * elem[p] (point evaluation through the shape functions); elem[p] < 0 is a
+ * fixed ground point at world coordinates xi_p. */
+static void con_point(int type, const orc_constraint *k, int p, const int32_t *conn, const double *X,
+                      const double *u, double r[3])
+{
+    if (k->elem[p] < 0) {
+        for (int a = 0; a < 3; ++a) r[a] = k->xi[p][a];
+        return;
+    }
+    const int n = orc_nodes_per_elem(type);
+    double s[10];
+    orc_shape(type, k->xi[p], s);
+    const int32_t *ce = conn + (size_t)k->elem[p] * n;
+    for (int a = 0; a < 3; ++a) {
+        double v = 0.0;
+        for (int i = 0; i < n; ++i) v += s[i] * (X[(size_t)ce[i] * 3 + a] + (u ? u[(size_t)ce[i] * 3 + a] : 0.0));
+        r[a] = v;
+    }
+}
+
+static int con_npoints(int ctype) { return (ctype == 2 || ctype == 3) ? 4 : 2; }
+
+/* c and dc/dr_p of one constraint:
+ *   CD  : c = d.(r_Q - r_P) - f;            dc/dr_P = -d, dc/dr_Q = +d
+ *   DIST: c = 1/2 (a.a - f^2), a = r_Q - r_P; dc/dr_P = -a, dc/dr_Q = +a
+ *   DP1, DP2: c = a.b - f, a = r_Q - r_P, b = r_T - r_R;
+ *         dc/dr_P = -b, dc/dr_Q = +b, dc/dr_R = -a, dc/dr_T = +a
+ * (Eqs. cd_constraint, dist_constraint, dp1_constraint, dp2_constraint and their blocks). */
+static int con_eval(int type, const orc_constraint *k, const int32_t *conn, const double *X, const double *u,
+                    double *c, double gp[4][3])
+{
+    double r[4][3];
+    const int np = con_npoints(k->type);
+    for (int p = 0; p < np; ++p) con_point(type, k, p, conn, X, u, r[p]);
+    double a[3], b[3];
+    for (int q = 0; q < 3; ++q) a[q] = r[1][q] - r[0][q];
+    memset(gp, 0, sizeof(double) * 12);
+    if (k->type == 0) {
+        *c = dot3(k->d, a) - k->f;
+        for (int q = 0; q < 3; ++q) {
+            gp[0][q] = -k->d[q];
+            gp[1][q] = k->d[q];
+        }
+    } else if (k->type == 1) {
+        *c = 0.5 * (dot3(a, a) - k->f * k->f);
+        for (int q = 0; q < 3; ++q) {
+            gp[0][q] = -a[q];
+            gp[1][q] = a[q];
+        }
+    } else if (k->type == 2 || k->type == 3) {
+        for (int q = 0; q < 3; ++q) b[q] = r[3][q] - r[2][q];
+        *c = dot3(a, b) - k->f;
+        for (int q = 0; q < 3; ++q) {
+            gp[0][q] = -b[q];
+            gp[1][q] = b[q];
+            gp[2][q] = -a[q];
+            gp[3][q] = a[q];
+        }
+    } else {
+        return -1;
+    }
+    return 0;
+}
+
+/* c(q) for every constraint, q = X + u */
+int orc_constraint_eval(int type, int n_cons, const orc_constraint *cons, const int32_t *conn, const double *X,
+                        const double *u, double *c)
+{
+    double gp[4][3];
+    for (int k = 0; k < n_cons; ++k)
+        if (con_eval(type, cons + k, conn, X, u, c + k, gp)) return -1;
+    return 0;
+}
+
+/* f += C_q^T w: for each constraint k and point p on an element, node i of
+ * that element receives w_k s_i(xi_p) dc_k/dr_p (the element blocks above,
+ * applied without forming C_q) */
+int orc_constraint_jt(int type, int n_cons, const orc_constraint *cons, const int32_t *conn, const double *X,
+                      const double *u, const double *w, double *f)
+{
+    const int n = orc_nodes_per_elem(type);
+    double gp[4][3], c, s[10];
+    for (int k = 0; k < n_cons; ++k) {
+        const orc_constraint *ck = cons + k;
+        if (con_eval(type, ck, conn, X, u, &c, gp)) return -1;
+        for (int p = 0; p < con_npoints(ck->type); ++p) {
+            if (ck->elem[p] < 0) continue;
+            orc_shape(type, ck->xi[p], s);
+            const int32_t *ce = conn + (size_t)ck->elem[p] * n;
+            for (int i = 0; i < n; ++i)
+                for (int a = 0; a < 3; ++a) f[(size_t)ce[i] * 3 + a] += w[k] * s[i] * gp[p][a];
+        }
+    }
+    return 0;
+}
+
+/* out = C_q v */
+int orc_constraint_j(int type, int n_cons, const orc_constraint *cons, const int32_t *conn, const double *X,
+                     const double *u, const double *v, double *out)
+{
+    const int n = orc_nodes_per_elem(type);
+    double gp[4][3], c, s[10];
+    for (int k = 0; k < n_cons; ++k) {
+        const orc_constraint *ck = cons + k;
+        if (con_eval(type, ck, conn, X, u, &c, gp)) return -1;
+        double acc = 0.0;
+        for (int p = 0; p < con_npoints(ck->type); ++p) {
+            if (ck->elem[p] < 0) continue;
+            orc_shape(type, ck->xi[p], s);
+            const int32_t *ce = conn + (size_t)ck->elem[p] * n;
+            for (int i = 0; i < n; ++i)
+                for (int a = 0; a < 3; ++a) acc += gp[p][a] * s[i] * v[(size_t)ce[i] * 3 + a];
+        }
+        out[k] = acc;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Section 7: backward-Euler step (augmented-Lagrangian constraints optional) */
 /* ------------------------------------------------------------------------ */
 
 typedef struct {
@@ -1169,6 +1292,13 @@ typedef struct {
     const orc_material *mat;
     const uint8_t *fixed;
     double *A; /* element matrices [n_elem][3n][3n] of M/h + h K^e + C */
+    /* augmented-Lagrangian constraints (Sec. 7): none when n_cons = 0 */
+    int n_cons;
+    const orc_constraint *cons;
+    const double *lam;
+    double rho, h;
+    const double *uq;  /* q(v) - X at which C_q is evaluated */
+    double *cw;        /* [n_cons] scratch */
 } step_ctx;
 
 static void project(const step_ctx *c, double *x)
@@ -1185,8 +1315,8 @@ static double norm2(const double *x, size_t N)
     return sqrt(s);
 }
 
-/* g(v) = 1/h M (v - v_n) + f_int(q(v), v) - f_ff with q(v) = q_n + h v
- * (Eqs. step_map_velocity_level and residual, no constraint term, f_ext = 0);
+/* g(v) = 1/h M (v - v_n) + f_int(q(v), v) - f_ff + h C_q^T (lam + rho c)
+ * with q(v) = q_n + h v (Eqs. step_map_velocity_level and residual, f_ext = 0);
  * clamped DOFs are projected out. */
 static int residual(const step_ctx *c, const double *u_n, const double *v_n, const double *v,
                     double h, const double *f_ff, double *u_tmp, double *dv, double *g)
@@ -1203,6 +1333,11 @@ static int residual(const step_ctx *c, const double *u_n, const double *v_n, con
     int st2 = orc_internal_force(c->type, c->nq, c->n_elem, c->conn, c->n_nodes, c->X, u_tmp, v,
                                  c->mat, 2, g);
     if (st2 < 0) return st2;
+    if (c->n_cons > 0) {
+        if (orc_constraint_eval(c->type, c->n_cons, c->cons, c->conn, c->X, u_tmp, c->cw)) return -1;
+        for (int k = 0; k < c->n_cons; ++k) c->cw[k] = h * (c->lam[k] + c->rho * c->cw[k]);
+        if (orc_constraint_jt(c->type, c->n_cons, c->cons, c->conn, c->X, u_tmp, c->cw, g)) return -1;
+    }
     project(c, g);
     return st + st2;
 }
@@ -1220,23 +1355,34 @@ static void apply_A(const step_ctx *c, const double *x, double *y)
             y[(size_t)ce[r / 3] * 3 + r % 3] += s;
         }
     }
+    if (c->n_cons > 0) {
+        /* Gauss-Newton constraint term h^2 rho C_q^T C_q (the curvature terms
+         * h^2 sum eta_k grad^2 c_k are left out, App. B.2) */
+        orc_constraint_j(c->type, c->n_cons, c->cons, c->conn, c->X, c->uq, x, c->cw);
+        for (int k = 0; k < c->n_cons; ++k) c->cw[k] *= c->h * c->h * c->rho;
+        orc_constraint_jt(c->type, c->n_cons, c->cons, c->conn, c->X, c->uq, c->cw, y);
+    }
     project(c, y);
 }
 
-/* Inexact Newton on g(v) = 0. Each iteration solves
- * (M/h + h K^e + C) dv = -g with Jacobi-preconditioned CG (the symmetric part
- * of dg/dv = M/h + h K_t + C), then v += dv. Stops when ||g|| <= rtol ||g(v_n)||. */
-int orc_newton_step(int type, int nq, int n_elem, const int32_t *conn, int n_nodes,
-                    const double *X, const orc_material *mat, const double *u_n,
-                    const double *v_n, double h, const double gravity[3],
-                    const uint8_t *fixed, double newton_rtol, double cg_rtol,
-                    int max_newton, int max_cg, double *v_out, orc_report *rep)
+/* Inexact Newton on g(v) = 0 at fixed multipliers. Each iteration solves
+ * (M/h + h K^e + C [+ h^2 rho C_q^T C_q]) dv = -g with Jacobi-preconditioned
+ * CG (the symmetric, Gauss-Newton part of dg/dv), then v += dv. Stops when
+ * ||g|| <= rtol g_ref, g_ref = ||g|| at the start (or *g_ref_io when it is
+ * positive on entry; it returns the reference used). v_out holds the start. */
+static int newton_core(int type, int nq, int n_elem, const int32_t *conn, int n_nodes, const double *X,
+                       const orc_material *mat, const double *u_n, const double *v_n, double h,
+                       const double gravity[3], const uint8_t *fixed, double newton_rtol, double cg_rtol,
+                       int max_newton, int max_cg, int n_cons, const orc_constraint *cons, const double *lam,
+                       double rho, double *g_ref_io, double *v_out, orc_report *rep)
 {
     const int n = orc_nodes_per_elem(type);
     if (n < 0 || h <= 0.0) return -1;
     const int NE = 3 * n;
     const size_t N = (size_t)n_nodes * 3;
-    step_ctx c = {type, nq, n_elem, n, n_nodes, conn, X, mat, fixed, NULL};
+    step_ctx c = {type, nq, n_elem, n, n_nodes, conn, X, mat, fixed, NULL, n_cons, cons, lam, rho, h, NULL, NULL};
+    double *cw = malloc(sizeof(double) * (n_cons > 0 ? n_cons : 1));
+    c.cw = cw;
     c.A = malloc(sizeof(double) * (size_t)n_elem * NE * NE);
     double *f_ff = calloc(N, sizeof(double)), *g = malloc(N * sizeof(double)),
            *ut = malloc(N * sizeof(double)), *dv = malloc(N * sizeof(double)),
@@ -1255,14 +1401,18 @@ int orc_newton_step(int type, int nq, int n_elem, const int32_t *conn, int n_nod
         goto done;
     }
     orc_gravity(type, n_elem, conn, n_nodes, X, mat, gravity, f_ff);
-    memcpy(v_out, v_n, N * sizeof(double));
     project(&c, v_out);
+    c.uq = ut;
     if (residual(&c, u_n, v_n, v_out, h, f_ff, ut, dv, g) < 0) {
         ret = -1;
         goto done;
     }
-    const double g0 = norm2(g, N);
-    double gn = g0;
+    double g0 = norm2(g, N);
+    if (g_ref_io) {
+        if (*g_ref_io > 0.0) g0 = *g_ref_io;
+        else *g_ref_io = g0;
+    }
+    double gn = norm2(g, N);
     int it = 0;
     while (g0 > 0.0 && gn > newton_rtol * g0 && it < max_newton) {
         /* assemble element matrices of the symmetric Newton operator at v */
@@ -1278,6 +1428,21 @@ int orc_newton_step(int type, int nq, int n_elem, const int32_t *conn, int n_nod
             double *Ae = c.A + (size_t)e * NE * NE;
             for (int k = 0; k < NE * NE; ++k) Ae[k] = Me[k] / h + h * Ke[k] + Ce[k];
             for (int q = 0; q < NE; ++q) D[(size_t)ce[q / 3] * 3 + q % 3] += Ae[(size_t)q * NE + q];
+        }
+        if (n_cons > 0) {
+            /* diagonal of h^2 rho C_q^T C_q: sum over constraint points of (s_i dc/dr_p)^2 */
+            double gp[4][3], cv, sh[10];
+            for (int k = 0; k < n_cons; ++k) {
+                con_eval(type, cons + k, conn, X, ut, &cv, gp);
+                for (int pp = 0; pp < con_npoints(cons[k].type); ++pp) {
+                    if (cons[k].elem[pp] < 0) continue;
+                    orc_shape(type, cons[k].xi[pp], sh);
+                    const int32_t *ce = conn + (size_t)cons[k].elem[pp] * n;
+                    for (int i = 0; i < n; ++i)
+                        for (int a = 0; a < 3; ++a)
+                            D[(size_t)ce[i] * 3 + a] += h * h * rho * sh[i] * sh[i] * gp[pp][a] * gp[pp][a];
+                }
+            }
         }
         /* Jacobi-PCG on A x = -g */
         for (size_t k = 0; k < N; ++k) {
@@ -1324,6 +1489,7 @@ int orc_newton_step(int type, int nq, int n_elem, const int32_t *conn, int n_nod
     rep->rel_residual = g0 > 0.0 ? gn / g0 : 0.0;
     rep->status = (g0 > 0.0 && gn > newton_rtol * g0) ? 5 : 0;
 done:
+    free(cw);
     free(c.A);
     free(f_ff);
     free(g);
@@ -1338,6 +1504,62 @@ done:
     free(Ke);
     free(Ce);
     free(Me);
+    return ret;
+}
+
+int orc_newton_step(int type, int nq, int n_elem, const int32_t *conn, int n_nodes,
+                    const double *X, const orc_material *mat, const double *u_n,
+                    const double *v_n, double h, const double gravity[3],
+                    const uint8_t *fixed, double newton_rtol, double cg_rtol,
+                    int max_newton, int max_cg, double *v_out, orc_report *rep)
+{
+    memcpy(v_out, v_n, (size_t)n_nodes * 3 * sizeof(double));
+    return newton_core(type, nq, n_elem, conn, n_nodes, X, mat, u_n, v_n, h, gravity, fixed, newton_rtol, cg_rtol,
+                       max_newton, max_cg, 0, NULL, NULL, 0.0, NULL, v_out, rep);
+}
+
+/* Augmented-Lagrangian step (Sec. 7, Eq. alm_multiplier_update): alternate the
+ * inner Newton solve of g(v, lam) = 0 with lam += rho c(q(v)) until
+ * ||c(q(v))||_2 <= alm_tol or max_outer updates; lam is updated in place.
+ * Reports the outer iterations and ||c||. */
+int orc_newton_step_alm(int type, int nq, int n_elem, const int32_t *conn, int n_nodes, const double *X,
+                        const orc_material *mat, const double *u_n, const double *v_n, double h,
+                        const double gravity[3], const uint8_t *fixed, double newton_rtol, double cg_rtol,
+                        int max_newton, int max_cg, int n_cons, const orc_constraint *cons, double rho,
+                        double alm_tol, int max_outer, double *lam, double *v_out, orc_report *rep,
+                        int *outer_iters, double *c_norm)
+{
+    const size_t N = (size_t)n_nodes * 3;
+    double *uq = malloc(N * sizeof(double)), *cv = malloc(sizeof(double) * (n_cons > 0 ? n_cons : 1));
+    if (!uq || !cv) {
+        free(uq);
+        free(cv);
+        return -2;
+    }
+    memcpy(v_out, v_n, N * sizeof(double));
+    int ret = 0, k = 0;
+    double g_ref = 0.0; /* inner solves stop relative to the first residual of the step */
+    orc_report r1;
+    rep->newton_iters = rep->cg_iters = 0;
+    for (;;) {
+        ret = newton_core(type, nq, n_elem, conn, n_nodes, X, mat, u_n, v_n, h, gravity, fixed, newton_rtol,
+                          cg_rtol, max_newton, max_cg, n_cons, cons, lam, rho, &g_ref, v_out, &r1);
+        if (ret < 0) break;
+        rep->newton_iters += r1.newton_iters;
+        rep->cg_iters += r1.cg_iters;
+        rep->status = r1.status;
+        rep->rel_residual = r1.rel_residual;
+        for (size_t q = 0; q < N; ++q) uq[q] = u_n[q] + h * v_out[q];
+        orc_constraint_eval(type, n_cons, cons, conn, X, uq, cv);
+        *c_norm = norm2(cv, (size_t)n_cons);
+        if (*c_norm <= alm_tol || k >= max_outer) break;
+        for (int j = 0; j < n_cons; ++j) lam[j] += rho * cv[j];
+        ++k;
+    }
+    *outer_iters = k;
+    if (ret >= 0 && *c_norm > alm_tol) rep->status = 5;
+    free(uq);
+    free(cv);
     return ret;
 }
 

@@ -106,6 +106,28 @@ typedef struct {
     double rel_residual;
 } orc_report;
 
+/* ---- bilateral constraints (Sec. 3 primitives) and the ALM step (Sec. 7) */
+typedef struct {
+    int32_t type;      /* 0 CD, 1 DIST, 2 DP1, 3 DP2 */
+    int32_t elem[4];   /* element of points P, Q, R, T (block-local); < 0: ground point */
+    double xi[4][3];   /* parent coordinates (ground points: world coordinates) */
+    double d[3];       /* CD axis */
+    double f;          /* prescribed value (DIST: the distance) */
+} orc_constraint;
+
+int orc_constraint_eval(int type, int n_cons, const orc_constraint *cons, const int32_t *conn, const double *X,
+                        const double *u, double *c);
+int orc_constraint_jt(int type, int n_cons, const orc_constraint *cons, const int32_t *conn, const double *X,
+                      const double *u, const double *w, double *f);
+int orc_constraint_j(int type, int n_cons, const orc_constraint *cons, const int32_t *conn, const double *X,
+                     const double *u, const double *v, double *out);
+int orc_newton_step_alm(int type, int nq, int n_elem, const int32_t *conn, int n_nodes, const double *X,
+                        const orc_material *mat, const double *u_n, const double *v_n, double h,
+                        const double gravity[3], const uint8_t *fixed, double newton_rtol, double cg_rtol,
+                        int max_newton, int max_cg, int n_cons, const orc_constraint *cons, double rho,
+                        double alm_tol, int max_outer, double *lam, double *v_out, orc_report *rep,
+                        int *outer_iters, double *c_norm);
+
 int orc_newton_step(int type, int nq, int n_elem, const int32_t *conn, int n_nodes,
                     const double *X, const orc_material *mat, const double *u_n,
                     const double *v_n, double h, const double gravity[3],

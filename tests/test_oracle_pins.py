@@ -730,3 +730,111 @@ def test_point_loads_partition_and_kronecker(etype, nq):
     g = m.conn[0, node_id]
     assert np.abs(f1[g] - [1.0, 2.0, 3.0]).max() < 1e-14
     assert np.abs(np.delete(f1, g, axis=0)).max() < 1e-14
+
+
+# ------------------------------------------------------------------------
+# Sec. 3 constraint primitives and the augmented-Lagrangian step (Sec. 7)
+# ------------------------------------------------------------------------
+
+def _two_beams():
+    """Two T10 beams (bodies 0 and 1) side by side, with seeded displacements."""
+    from synth.workloads import Block, Workload
+    m1 = synth.box_mesh(T10, (4, 1, 1), (0.2, 0.05, 0.05))
+    m2 = synth.box_mesh(T10, (4, 1, 1), (0.2, 0.05, 0.05), origin=(0.0, 0.1, 0.0))
+    m = synth.concat_meshes([m1, m2])
+    rng = np.random.default_rng(41)
+    u = 0.002 * rng.standard_normal(m.X.shape)
+    return Workload("two", m.X, [Block(T10, 5, m.conn, m.body)], np.array([1, 1], np.int32),
+                    np.array([[MU, LAM, 0.0, 0.0, 1000.0]] * 2), u=u, udot=None)
+
+
+def _random_constraints(wl, rng):
+    ne = wl.blocks[0].n_elem
+    half = ne // 2
+
+    def pt(body):
+        e = int(rng.integers(0, half)) + (half if body else 0)
+        return e, rng.dirichlet(np.ones(4))[1:]
+    items = []
+    for t in (oracle.CD, oracle.DIST, oracle.DP1, oracle.DP2):
+        np_ = 2 if t in (oracle.CD, oracle.DIST) else 4
+        bodies = [0, 1] if np_ == 2 else ([0, 0, 1, 1] if t == oracle.DP1 else [0, 0, 0, 1])
+        pts = [pt(b) for b in bodies]
+        items.append({"type": t, "elem": [p[0] for p in pts], "xi": [p[1] for p in pts],
+                      "d": (0.0, 1.0, 0.0), "f": 0.03})
+    # a ground point (clamp-like coordinate difference)
+    e, xi = pt(0)
+    items.append({"type": oracle.CD, "elem": [e, -1], "xi": [xi, [0.05, 0.02, 0.01]], "d": (1.0, 0.0, 0.0)})
+    return oracle.constraints(items)
+
+
+def test_constraint_jacobian_blocks_match_central_differences():
+    """C_q v (the element blocks of Eqs. cd_blocks, dist_blocks, dp1_block_P,
+    dp2_blocks) equals the central difference of c along v, and C_q^T is its
+    adjoint."""
+    wl = _two_beams()
+    rng = np.random.default_rng(42)
+    cons = _random_constraints(wl, rng)
+    v = rng.standard_normal(wl.X.shape)
+    w = rng.standard_normal(len(cons))
+    Jv = oracle.constraint_j(wl, cons, v)
+    h = 1e-6
+    fd = (oracle.constraint_eval(wl, cons, wl.u + h * v) - oracle.constraint_eval(wl, cons, wl.u - h * v)) / (2 * h)
+    assert np.abs(Jv - fd).max() < 1e-8 * np.abs(fd).max()
+    JTw = oracle.constraint_jt(wl, cons, w)
+    assert abs(np.sum(JTw * v) - np.sum(w * Jv)) < 1e-12 * abs(np.sum(w * Jv))
+
+
+def test_constraint_values_closed_form():
+    """c of each primitive at nodes, where point evaluation returns the node."""
+    from synth.workloads import Block, Workload
+    m = synth.box_mesh(T4, (1, 1, 1), (1.0, 1.0, 1.0))
+    u = np.zeros_like(m.X)
+    wl = Workload("c", m.X, [Block(T4, 1, m.conn, np.zeros(m.n_elem, np.int32))], np.array([1], np.int32),
+                  np.array([[MU, LAM, 0.0, 0.0, 1000.0]]), u=u)
+    c0 = m.conn[0]
+    X = m.X
+    node_xi = [[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]]   # T4 corners in parent coordinates
+    cons = oracle.constraints([
+        {"type": oracle.CD, "elem": [0, 0], "xi": [node_xi[0], node_xi[1]], "d": (1, 0, 0), "f": 0.25},
+        {"type": oracle.DIST, "elem": [0, 0], "xi": [node_xi[0], node_xi[2]], "f": 0.5},
+        {"type": oracle.DP1, "elem": [0, 0, 0, 0], "xi": node_xi, "f": 0.1},
+    ])
+    c = oracle.constraint_eval(wl, cons)
+    a01 = X[c0[1]] - X[c0[0]]
+    a02 = X[c0[2]] - X[c0[0]]
+    b23 = X[c0[3]] - X[c0[2]]
+    assert abs(c[0] - (a01[0] - 0.25)) < 1e-14
+    assert abs(c[1] - 0.5 * (a02 @ a02 - 0.25)) < 1e-14
+    assert abs(c[2] - (a01 @ b23 - 0.1)) < 1e-14
+
+
+def test_alm_clamp_by_coordinate_differences_reproduces_the_projected_clamp():
+    """Clamping the x = 0 face by three CD constraints per node to ground
+    points (Sec. 3 CD, Sec. 7 ALM with multiplier updates) converges to the
+    step with the clamped DOFs projected out."""
+    from synth.workloads import Block, Workload
+    m = synth.box_mesh(T10, (4, 1, 1), (0.2, 0.05, 0.05))
+    wl = Workload("b", m.X, [Block(T10, 5, m.conn, np.zeros(m.n_elem, np.int32))], np.array([1], np.int32),
+                  np.array([[MU, LAM, 0.0, 0.0, 1000.0]]), u=np.zeros_like(m.X))
+    fixed = (np.abs(m.X[:, 0]) < 1e-12).astype(np.uint8)
+    g = np.array([0.0, 0.0, -9.81])
+    z = np.zeros_like(m.X)
+    v_proj, rep = oracle.newton_step(wl, z, z, 1e-3, g, fixed=fixed, newton_rtol=1e-10, cg_rtol=1e-10)
+    assert rep["status"] == 0
+    # one element holding each clamped node, and that node's parent coordinates
+    nxi = _load_golden("t10_parent_nodes.txt")[:, 5:8]      # App. A.1 node table: parent (xi, eta, zeta)
+    items = []
+    for node in np.nonzero(fixed)[0]:
+        e, i = [(e, i) for e in range(m.n_elem) for i in range(10) if m.conn[e, i] == node][0]
+        for d in range(3):
+            dv = [0.0, 0.0, 0.0]
+            dv[d] = 1.0
+            items.append({"type": oracle.CD, "elem": [e, -1], "xi": [nxi[i], m.X[node]], "d": dv, "f": 0.0})
+    cons = oracle.constraints(items)
+    v, lam, r = oracle.newton_step_alm(wl, z, z, 1e-3, g, cons, rho=1e10, newton_rtol=1e-10, cg_rtol=1e-10,
+                                       alm_tol=1e-12, max_outer=20)
+    assert r["status"] == 0 and r["c_norm"] <= 1e-12
+    assert np.abs(v - v_proj).max() <= 1e-7 * np.abs(v_proj).max()
+    # the multipliers carry the support reactions: C_q^T lam h balances the load at the clamp
+    assert np.abs(lam).max() > 0
