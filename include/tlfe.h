@@ -214,7 +214,42 @@ tlfe_status tlfe_point_loads(tlfe_mesh *mesh, int32_t n, const int32_t *elem_dev
 tlfe_status tlfe_surface_traction(tlfe_mesh *mesh, int32_t n, const int32_t *elem_dev, const int32_t *face_dev,
                                   const double *t0_dev, double *f_dev, void *stream);
 
-/* Launch-schedule autotuner/* Launch-schedule autotuner (no counterpart in the paper; a property of this
+/* Bilateral constraint primitives (Sec. 3: DP1, DP2, DIST, CD), each a scalar
+ * position-level condition c(q) = 0 built from point evaluations
+ * r_X = sum_i s_i(xi_X) (X_i + u_i) of material points on elements:
+ *   TLFE_CON_CD  : c = d . (r_Q - r_P) - f          (Eq. cd_constraint)
+ *   TLFE_CON_DIST: c = 1/2 (|r_Q - r_P|^2 - f^2)    (Eq. dist_constraint)
+ *   TLFE_CON_DP1 : c = (r_Q - r_P) . (r_T - r_R) - f (Eq. dp1_constraint)
+ *   TLFE_CON_DP2 : the same expression with P, Q, R on one body and T on the
+ *                  other (Eq. dp2_constraint)
+ * Points P, Q (and R, T for DP1 / DP2): elem[k] is the global element and
+ * xi[k] the parent coordinates; elem[k] < 0 makes the point a fixed ground
+ * point at world coordinates xi[k]. d: CD axis; f: prescribed value f(t_{n+1})
+ * (DIST: the distance). */
+enum { TLFE_CON_CD = 0, TLFE_CON_DIST = 1, TLFE_CON_DP1 = 2, TLFE_CON_DP2 = 3 };
+typedef struct {
+    int32_t type;
+    int32_t elem[4];
+    double xi[4][3];
+    double d[3];
+    double f;
+} tlfe_constraint;
+
+/* c_dev[k] = c_k(X + u) for the n constraints cons_dev (device arrays; u_dev
+ * device double [n_nodes][3], c_dev device double [n]). Allocates and frees
+ * scratch; synchronises `stream`. Invalid elements or types: TLFE_E_INVALID. */
+tlfe_status tlfe_constraint_eval(tlfe_mesh *mesh, int32_t n, const tlfe_constraint *cons_dev, const double *u_dev,
+                                 double *c_dev, void *stream);
+/* f_dev += C_q^T w (C_q = dc/dq at X + u, applied through the element blocks
+ * of Sec. 3 without forming C_q); w_dev device double [n], f_dev device double
+ * [n_nodes][3]. */
+tlfe_status tlfe_constraint_jt(tlfe_mesh *mesh, int32_t n, const tlfe_constraint *cons_dev, const double *u_dev,
+                               const double *w_dev, double *f_dev, void *stream);
+/* out_dev[k] = (C_q v)_k; v_dev device double [n_nodes][3]. */
+tlfe_status tlfe_constraint_j(tlfe_mesh *mesh, int32_t n, const tlfe_constraint *cons_dev, const double *u_dev,
+                              const double *v_dev, double *out_dev, void *stream);
+
+/* Launch-schedule autotuner (no counterpart in the paper; a property of this
  * GPU implementation). For every element block it times the force, operator
  * (when v_dev is given) and adjoint (when v_dev is given) kernels on the
  * caller's state over the resident CTA sizes (4, 2, 1 warps) and both tile
@@ -245,9 +280,10 @@ tlfe_status tlfe_set_elem_mu_lambda(tlfe_mesh *mesh, const double *mu_lambda_dev
 tlfe_status tlfe_vjp(tlfe_mesh *mesh, const void *u_dev, const void *udot_dev, const void *cot_dev,
                      void *g_u_dev, void *g_udot_dev, double *g_mu_lambda_dev, void *stream);
 
-/* Backward-Euler step (Sec. 7, Eqs. step_map_velocity_level and residual,
- * without constraints): find v with
- *   g(v) = M/h (v - v_n) + f_int(u_n + h v, v) - f_ff - f_ext = 0,
+/* Backward-Euler step (Sec. 7, Eqs. step_map_velocity_level and residual):
+ * find v with
+ *   g(v) = M/h (v - v_n) + f_int(u_n + h v, v) - f_ff - f_ext
+ *          [+ h C_q^T (lambda + rho c)] = 0,
  * f_ff_i = rho v_i b0 (Eq. virtual_work_force_field_uniform), f_ext the
  * optional applied load (f_ext_dev; dead load over the step), by inexact
  * Newton: each iteration solves (M/h + h K^e + C) dv = -g by Jacobi-PCG with
@@ -256,7 +292,15 @@ tlfe_status tlfe_vjp(tlfe_mesh *mesh, const void *u_dev, const void *udot_dev, c
  * the CG vectors, dots and updates are FP64; the operator products run in the
  * mesh precision. Nodes with fixed_dev[k] = 1 are clamped (v = 0).
  * The whole step is one CUDA graph with conditional WHILE nodes (built on the
- * first call, replayed afterwards). */
+ * first call, replayed afterwards).
+ * With constraints (n_cons > 0) the step is the augmented-Lagrangian iteration
+ * of Sec. 7: Newton solves of g(v, lambda) = 0, whose CG matrix adds the
+ * Gauss-Newton term h^2 rho C_q^T C_q (the curvature terms of App. B.2 are left
+ * out), alternate with lambda += rho c(q(v)) (Eq. alm_multiplier_update) until
+ * ||c|| <= alm_tol or max_outer updates; the Newton solves after the first
+ * start from the previous v and stop relative to the step's first residual.
+ * Constraints may couple bodies: the whole mesh is then solved as one system
+ * (one convergence test). */
 typedef struct {
     double h;
     double gravity[3];
@@ -268,6 +312,13 @@ typedef struct {
     int32_t use_graph;         /* 1 = CUDA graph with conditional nodes, 0 = host-driven loop */
     const double *f_ext_dev;   /* device double [n_nodes][3] applied load of the step (Sec. 4:
                                   point loads, tractions), or NULL; read at every call */
+    /* augmented-Lagrangian constraints (Sec. 7); n_cons = 0 for none */
+    int32_t n_cons;
+    const tlfe_constraint *cons_dev;  /* device [n_cons] */
+    double rho;                /* penalty rho > 0 */
+    double alm_tol;            /* stop when ||c(q(v))||_2 <= alm_tol */
+    int32_t max_outer;         /* multiplier updates at most */
+    double *lambda_dev;        /* device double [n_cons], multipliers in/out */
 } tlfe_step_params;
 
 typedef struct {
@@ -276,6 +327,8 @@ typedef struct {
     int32_t status;            /* tlfe_status of the step */
     int32_t n_bodies_converged;
     double rel_residual;       /* max over bodies of ||g_b|| / ||g_b(v_n)|| */
+    int32_t outer_iters;       /* multiplier updates (constraints) */
+    double c_norm;             /* ||c(q(v))||_2 at return (constraints) */
 } tlfe_step_report;
 
 /* u_n_dev, v_n_dev, v_out_dev: device double [n_nodes][3]. report_host is

@@ -77,6 +77,17 @@ struct NewtonState {
     cudaGraphConditionalHandle hN = 0, hC = 0;
     cudaStream_t s_main = nullptr, s_body = nullptr, s_cg = nullptr;  // capture streams
     std::vector<void *> allocs;
+    // augmented-Lagrangian constraints (Sec. 7): one coupled system when present
+    int coupled = 0;             // 1: every body in one convergence group
+    int n_cons = 0, cap_cons = 0;
+    double rho = 0;
+    tlfe_constraint *cons = nullptr;               // [cap] copy of the caller's set
+    double *con_sh = nullptr, *con_gp = nullptr;   // [cap][4][CON_MAXN], [cap][4][3]
+    int32_t *con_nd = nullptr;                     // [cap][4][CON_MAXN]
+    double *con_c = nullptr, *con_w = nullptr, *lam = nullptr;  // [cap]
+    int *con_bad = nullptr;
+    int *alm = nullptr;          // [2]: keep the first residual norm as reference; start from the current v
+    double *g0keep = nullptr;    // [nb] residual norms of the first Newton solve of the step
 };
 
 // ---------------------------------------------------------------------------
@@ -142,15 +153,25 @@ __global__ void k_add(int64_t n, const double *a, const double *b, double *c)
 }
 
 // Newton convergence test per body; sets the Newton WHILE condition
+// (alm[0]: later solves of an augmented-Lagrangian step keep the first
+// solve's reference norm g0keep)
 __global__ void k_newton_check(int nb, const int32_t *boff, const double *partials, double *sc, int *it, double rtol,
-                               int max_newton, cudaGraphConditionalHandle hN, int use_handle)
+                               int max_newton, cudaGraphConditionalHandle hN, int use_handle, const int *alm,
+                               double *g0keep)
 {
     int any = 0;
     for (int b = threadIdx.x; b < nb; b += blockDim.x) {
         double s = 0.0;
         for (int k = boff[b]; k < boff[b + 1]; ++k) s += partials[k];
         const double gn = sqrt(s);
-        if (it[I_NEWTON] == 0) sc[S_G0 * nb + b] = gn;
+        if (it[I_NEWTON] == 0) {
+            if (alm[0]) {
+                sc[S_G0 * nb + b] = g0keep[b];
+            } else {
+                sc[S_G0 * nb + b] = gn;
+                g0keep[b] = gn;
+            }
+        }
         sc[S_GN * nb + b] = gn;
         const double g0 = sc[S_G0 * nb + b];
         const int act = (g0 > 0.0 && gn > rtol * g0 && it[I_NEWTON] < max_newton) ? 1 : 0;
@@ -347,8 +368,9 @@ __global__ void k_newton_count(int nb, double *sc, int *it)
 }
 
 // v = v_n with clamped DOFs zeroed; counters reset
-__global__ void k_start(ChunkArgs c, const uint8_t *fixed, const double *v_n, double *v)
+__global__ void k_start(ChunkArgs c, const uint8_t *fixed, const double *v_n, double *v, const int *alm)
 {
+    if (alm[1]) return;  // augmented-Lagrangian re-solve: start from the current v
     const int ch = blockIdx.x;
     for (int i = c.start[ch] + threadIdx.x; i < c.end[ch]; i += blockDim.x) v[i] = fixed[i / 3] ? 0.0 : v_n[i];
 }
@@ -407,10 +429,11 @@ void destroy_newton(tlfe_mesh *m)
 }
 
 // bodies must own contiguous node ranges; builds the chunk tables
-static tlfe_status setup_newton(tlfe_mesh *m, cudaStream_t s)
+static tlfe_status setup_newton(tlfe_mesh *m, cudaStream_t s, int coupled)
 {
     NewtonState *ns = new NewtonState();
     m->newton = ns;
+    ns->coupled = coupled;
     const int N = m->n_nodes;
     std::vector<int> nstart(m->n_bodies, -1), nend(m->n_bodies, -1);
     int prev = -2;
@@ -437,16 +460,19 @@ static tlfe_status setup_newton(tlfe_mesh *m, cudaStream_t s)
                 if (m->node_body[m->h_conn[bi][e * npe + i]] != m->h_body[bi][e])
                     return fail(TLFE_E_UNSUPPORTED, "newton step needs bodies that share no node");
     }
-    ns->nb = m->n_bodies;
+    // convergence groups: one per body, or a single group when constraints
+    // may couple bodies
+    ns->nb = coupled ? 1 : m->n_bodies;
     std::vector<int32_t> cs, ce, cb, boff(ns->nb + 1, 0);
-    for (int b = 0; b < ns->nb; ++b) {
+    for (int b = 0; b < m->n_bodies; ++b) {
+        const int grp = coupled ? 0 : b;
         if (nstart[b] >= 0)
             for (int64_t d = 3 * (int64_t)nstart[b]; d < 3 * (int64_t)nend[b]; d += CHUNK) {
                 cs.push_back((int32_t)d);
                 ce.push_back((int32_t)std::min<int64_t>(d + CHUNK, 3 * (int64_t)nend[b]));
-                cb.push_back(b);
+                cb.push_back(grp);
             }
-        boff[b + 1] = (int32_t)cs.size();
+        boff[grp + 1] = (int32_t)cs.size();
     }
     ns->n_chunks = (int)cs.size();
     if (ns->n_chunks == 0) return fail(TLFE_E_INVALID, "no body owns any node");
@@ -466,6 +492,9 @@ static tlfe_status setup_newton(tlfe_mesh *m, cudaStream_t s)
     NA(ns->partials, 2 * (size_t)ns->n_chunks);
     NA(ns->sc, (size_t)S_COUNT * ns->nb);
     NA(ns->it, (size_t)I_COUNT);
+    NA(ns->alm, 2);
+    NA(ns->g0keep, (size_t)ns->nb);
+    NA(ns->con_bad, 1);
 #undef NA
     NCK(cudaMemcpyAsync(ns->chunk_start, cs.data(), 4 * cs.size(), cudaMemcpyHostToDevice, s));
     NCK(cudaMemcpyAsync(ns->chunk_end, ce.data(), 4 * ce.size(), cudaMemcpyHostToDevice, s));
@@ -525,9 +554,15 @@ static tlfe_status enq_residual(const StepCtx &x, cudaStream_t s)
     if (st != TLFE_OK) return st;
     st = run_op<OP_FORCE, double>(m64, ns->u_cur, ns->v, nullptr, ns->y2, nullptr, nullptr, 0.0, 1.0, 0.0, 0, s);
     if (st != TLFE_OK) return st;
+    if (ns->n_cons > 0) {
+        // + h C_q^T (lambda + rho c) at q(v) (Eq. residual)
+        NCK(con_eval(ns->n_cons, ns->cons, ns->con_sh, ns->con_nd, x.m->d_X, ns->u_cur, ns->con_c, ns->con_gp, s));
+        NCK(con_weights(ns->n_cons, ns->lam, ns->con_c, ns->rho, ns->h, ns->con_w, s));
+        NCK(con_jt<double>(ns->n_cons, ns->con_sh, ns->con_nd, ns->con_gp, ns->con_w, 1.0, ns->y2, s));
+    }
     k_residual<<<nc, RT, 0, s>>>(x.c, ns->y1, ns->y2, ns->fff, ns->fixed, ns->g, ns->partials);
     k_newton_check<<<1, 1024, 0, s>>>(ns->nb, ns->body_chunk_off, ns->partials, ns->sc, ns->it, ns->nrtol,
-                                       ns->max_newton, ns->hN, x.use_handle);
+                                       ns->max_newton, ns->hN, x.use_handle, ns->alm, ns->g0keep);
     NCK(cudaGetLastError());
     return TLFE_OK;
 }
@@ -541,10 +576,14 @@ static tlfe_status enq_cg_init(const StepCtx &x, cudaStream_t s)
     if (x.m->precision == TLFE_FP32) {
         st = run_op<OP_DIAG, float>(x.m, ns->u_cur, ns->ud32, nullptr, ns->D32, nullptr, nullptr, 1.0 / h, h, 1.0, 1, s);
         if (st != TLFE_OK) return st;
+        if (ns->n_cons > 0)
+            NCK(con_diag<float>(ns->n_cons, ns->con_sh, ns->con_nd, ns->con_gp, h * h * ns->rho, ns->D32, s));
         k_dinv<float><<<nc, RT, 0, s>>>(x.c, ns->D32, ns->fixed, ns->sc, ns->nb, ns->Dinv);
     } else {
         st = run_op<OP_DIAG, double>(x.m, ns->u_cur, ns->v, nullptr, ns->Dd, nullptr, nullptr, 1.0 / h, h, 1.0, 1, s);
         if (st != TLFE_OK) return st;
+        if (ns->n_cons > 0)
+            NCK(con_diag<double>(ns->n_cons, ns->con_sh, ns->con_nd, ns->con_gp, h * h * ns->rho, ns->Dd, s));
         k_dinv<double><<<nc, RT, 0, s>>>(x.c, ns->Dd, ns->fixed, ns->sc, ns->nb, ns->Dinv);
     }
     k_cg_init<<<nc, RT, 0, s>>>(x.c, ns->g, ns->Dinv, ns->sc, ns->nb, ns->x, ns->r, ns->z, ns->p, ns->partials);
@@ -565,10 +604,18 @@ static tlfe_status enq_cg_iter(const StepCtx &x, cudaStream_t s)
         st = run_op<OP_MATVEC, float>(x.m, ns->u_cur, ns->ud32, ns->p32, ns->Ap32, nullptr, nullptr, 1.0 / h, h, 1.0,
                                       1, s);
         if (st != TLFE_OK) return st;
+        if (ns->n_cons > 0) {  // + h^2 rho C_q^T C_q p (Gauss-Newton)
+            NCK(con_j(ns->n_cons, ns->con_sh, ns->con_nd, ns->con_gp, ns->p, ns->con_w, s));
+            NCK(con_jt<float>(ns->n_cons, ns->con_sh, ns->con_nd, ns->con_gp, ns->con_w, h * h * ns->rho, ns->Ap32, s));
+        }
         k_cg_pap<float><<<nc, RT, 0, s>>>(x.c, ns->Ap32, ns->fixed, ns->p, ns->Ap, ns->partials);
     } else {
         st = run_op<OP_MATVEC, double>(x.m, ns->u_cur, ns->v, ns->p, ns->y1, nullptr, nullptr, 1.0 / h, h, 1.0, 1, s);
         if (st != TLFE_OK) return st;
+        if (ns->n_cons > 0) {
+            NCK(con_j(ns->n_cons, ns->con_sh, ns->con_nd, ns->con_gp, ns->p, ns->con_w, s));
+            NCK(con_jt<double>(ns->n_cons, ns->con_sh, ns->con_nd, ns->con_gp, ns->con_w, h * h * ns->rho, ns->y1, s));
+        }
         k_cg_pap<double><<<nc, RT, 0, s>>>(x.c, ns->y1, ns->fixed, ns->p, ns->Ap, ns->partials);
     }
     k_cg_alpha<<<1, 1024, 0, s>>>(ns->nb, ns->body_chunk_off, ns->partials, ns->sc);
@@ -593,7 +640,7 @@ static tlfe_status enq_prologue(const StepCtx &x, cudaStream_t s)
 {
     NewtonState *ns = x.ns;
     k_reset<<<1, 1024, 0, s>>>(ns->nb, ns->sc, ns->it);
-    k_start<<<ns->n_chunks, RT, 0, s>>>(x.c, ns->fixed, ns->v_n, ns->v);
+    k_start<<<ns->n_chunks, RT, 0, s>>>(x.c, ns->fixed, ns->v_n, ns->v, ns->alm);
     NCK(cudaGetLastError());
     return enq_residual(x, s);
 }
@@ -713,12 +760,15 @@ extern "C" tlfe_status tlfe_body_norms(tlfe_mesh *m, const double *x, double *ou
 {
     if (!m || !x || !out) return fail(TLFE_E_INVALID, "NULL argument");
     cudaStream_t s = (cudaStream_t)stream;
+    // per-body tables (a workspace built for a coupled, constrained step has one group)
+    if (m->newton && m->newton->coupled) destroy_newton(m);
     if (!m->newton) {
-        tlfe_status st = setup_newton(m, s);
+        tlfe_status st = setup_newton(m, s, 0);
         if (st != TLFE_OK) {
             destroy_newton(m);
             return st;
         }
+        NCK(cudaMemsetAsync(m->newton->alm, 0, 2 * sizeof(int), s));
     }
     NewtonState *ns = m->newton;
     ChunkArgs c{ns->chunk_start, ns->chunk_end, ns->chunk_body, ns->n_chunks};
@@ -728,79 +778,12 @@ extern "C" tlfe_status tlfe_body_norms(tlfe_mesh *m, const double *x, double *ou
     return TLFE_OK;
 }
 
-extern "C" tlfe_status tlfe_newton_step(tlfe_mesh *m, const double *u_n, const double *v_n,
-                                        const tlfe_step_params *prm, double *v_out, tlfe_step_report *rep,
-                                        void *stream)
+// One Newton solve of the step (graph replay or host-driven loop) and its
+// per-group residual report.
+static tlfe_status newton_solve(StepCtx &x, const tlfe_step_params *prm, tlfe_step_report *rep, cudaStream_t s)
 {
-    if (!m || !u_n || !v_n || !prm || !v_out || !rep) return fail(TLFE_E_INVALID, "NULL argument");
-    memset(rep, 0, sizeof(*rep));
-    if (!(prm->h > 0.0) || !std::isfinite(prm->h) || !(prm->newton_rtol >= 0.0) || !(prm->cg_rtol >= 0.0) ||
-        prm->max_newton < 0 || prm->max_cg < 0)
-        return fail(TLFE_E_INVALID, "bad step parameters");
-    for (auto &B : m->blocks)
-        if (B.n_elem > 0 && !B.affine) return fail(TLFE_E_UNSUPPORTED, "newton step needs affine elements (consistent mass)");
-    cudaStream_t s = (cudaStream_t)stream;
+    NewtonState *ns = x.ns;
     tlfe_status st;
-    if (!m->newton) {
-        st = setup_newton(m, s);
-        if (st != TLFE_OK) {
-            destroy_newton(m);
-            return st;
-        }
-    }
-    NewtonState *ns = m->newton;
-    const size_t N = (size_t)m->n_nodes, N3 = 3 * N;
-    const bool same = ns->use_graph >= 0 && ns->h == prm->h && ns->grav[0] == prm->gravity[0] &&
-                      ns->grav[1] == prm->gravity[1] && ns->grav[2] == prm->gravity[2] &&
-                      ns->nrtol == prm->newton_rtol && ns->crtol == prm->cg_rtol && ns->max_newton == prm->max_newton &&
-                      ns->max_cg == prm->max_cg && ns->fixed_user == (const void *)prm->fixed_dev;
-    StepCtx x{m, ns, {ns->chunk_start, ns->chunk_end, ns->chunk_body, ns->n_chunks}, 0};
-    // inputs into the workspace (the graph only ever sees workspace pointers)
-    NCK(cudaMemcpyAsync(ns->u_n, u_n, 8 * N3, cudaMemcpyDeviceToDevice, s));
-    NCK(cudaMemcpyAsync(ns->v_n, v_n, 8 * N3, cudaMemcpyDeviceToDevice, s));
-    if (!same) {
-        ns->h = prm->h;
-        memcpy(ns->grav, prm->gravity, sizeof(ns->grav));
-        ns->nrtol = prm->newton_rtol;
-        ns->crtol = prm->cg_rtol;
-        ns->max_newton = prm->max_newton;
-        ns->max_cg = prm->max_cg;
-        ns->fixed_user = prm->fixed_dev;
-        // clamped nodes: user's flags, plus nodes outside every element
-        std::vector<uint8_t> fx(N, 0);
-        if (prm->fixed_dev) NCK(cudaMemcpy(fx.data(), prm->fixed_dev, N, cudaMemcpyDeviceToHost));
-        for (size_t k = 0; k < N; ++k)
-            if (m->node_body[k] < 0) fx[k] = 1;
-        NCK(cudaMemcpy(ns->fixed, fx.data(), N, cudaMemcpyHostToDevice));
-        // f_ff = M b0 (Eq. virtual_work_force_field_uniform with sum_j s_j = 1)
-        k_fill_grav<<<(unsigned)((N + 255) / 256), 256, 0, s>>>((int64_t)N, prm->gravity[0], prm->gravity[1],
-                                                                prm->gravity[2], ns->gv);
-        NCK(cudaGetLastError());
-        tlfe_mesh *m64 = ns->twin ? ns->twin : m;
-        st = run_op<OP_MATVEC, double>(m64, ns->u_n, nullptr, ns->gv, ns->fgrav, nullptr, nullptr, 1.0, 0.0, 0.0, 0, s);
-        if (st != TLFE_OK) return st;
-        NCK(cudaMemcpyAsync(ns->fff, ns->fgrav, 8 * N3, cudaMemcpyDeviceToDevice, s));
-        st = warm(x, s);
-        if (st != TLFE_OK) return st;
-        ns->use_graph = prm->use_graph ? 1 : 0;
-        if (prm->use_graph) {
-            NCK(cudaStreamSynchronize(s));
-            st = build_graph(x);
-            if (st != TLFE_OK) {
-                ns->use_graph = -1;
-                return st;
-            }
-        }
-        NCK(cudaMemcpyAsync(ns->u_n, u_n, 8 * N3, cudaMemcpyDeviceToDevice, s));
-        NCK(cudaMemcpyAsync(ns->v_n, v_n, 8 * N3, cudaMemcpyDeviceToDevice, s));
-    }
-    // applied load of this step: f_ff + f_ext (Sec. 4), read by the residual
-    if (prm->f_ext_dev) {
-        k_add<<<(unsigned)((N3 + 255) / 256), 256, 0, s>>>((int64_t)N3, ns->fgrav, prm->f_ext_dev, ns->fff);
-        NCK(cudaGetLastError());
-    } else {
-        NCK(cudaMemcpyAsync(ns->fff, ns->fgrav, 8 * N3, cudaMemcpyDeviceToDevice, s));
-    }
     if (ns->use_graph == 1 && prm->use_graph) {
         NCK(cudaGraphLaunch(ns->exec, s));
     } else {
@@ -826,33 +809,181 @@ extern "C" tlfe_status tlfe_newton_step(tlfe_mesh *m, const double *u_n, const d
             if (st != TLFE_OK) return st;
         }
     }
-    NCK(cudaMemcpyAsync(v_out, ns->v, 8 * N3, cudaMemcpyDeviceToDevice, s));
-    // report
     std::vector<double> sc((size_t)S_COUNT * ns->nb);
     int it[I_COUNT];
     NCK(cudaMemcpyAsync(sc.data(), ns->sc, 8 * sc.size(), cudaMemcpyDeviceToHost, s));
     NCK(cudaMemcpyAsync(it, ns->it, sizeof(it), cudaMemcpyDeviceToHost, s));
     NCK(cudaStreamSynchronize(s));
-    int conv = 0, bodies = 0, nit = 0;
+    int conv = 0, nit = 0;
     double worst = 0.0;
     for (int b = 0; b < ns->nb; ++b) {
         const double g0 = sc[S_G0 * ns->nb + b], gn = sc[S_GN * ns->nb + b];
         if (!(g0 > 0.0)) {
-            ++conv;  // nothing to solve for this body (or it owns no node)
+            ++conv;  // nothing to solve for this group (or it owns no node)
             continue;
         }
-        ++bodies;
         const double rel = gn / g0;
         worst = std::max(worst, rel);
         if (rel <= prm->newton_rtol) ++conv;
         nit = std::max(nit, (int)sc[S_NIT * ns->nb + b]);
     }
-    (void)bodies;
-    rep->newton_iters = nit;
-    rep->cg_iters = it[I_CG_TOTAL];
+    rep->newton_iters += nit;
+    rep->cg_iters += it[I_CG_TOTAL];
     rep->n_bodies_converged = conv;
     rep->rel_residual = worst;
     rep->status = conv == ns->nb ? TLFE_OK : TLFE_E_NOT_CONVERGED;
+    return TLFE_OK;
+}
+
+// constraint workspace for n constraints (the graph captures its pointers)
+static tlfe_status ensure_constraints(NewtonState *ns, int n)
+{
+    if (n <= ns->cap_cons) return TLFE_OK;
+    tlfe_status st;
+    tlfe_constraint *c = nullptr;
+    cudaError_t e = cudaMalloc(&c, sizeof(tlfe_constraint) * (size_t)n);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (constraints)");
+    ns->allocs.push_back(c);
+    ns->cons = c;
+    if ((st = nalloc(ns, &ns->con_sh, (size_t)n * 4 * CON_MAXN)) != TLFE_OK) return st;
+    if ((st = nalloc(ns, &ns->con_nd, (size_t)n * 4 * CON_MAXN)) != TLFE_OK) return st;
+    if ((st = nalloc(ns, &ns->con_gp, (size_t)n * 12)) != TLFE_OK) return st;
+    if ((st = nalloc(ns, &ns->con_c, (size_t)n)) != TLFE_OK) return st;
+    if ((st = nalloc(ns, &ns->con_w, (size_t)n)) != TLFE_OK) return st;
+    if ((st = nalloc(ns, &ns->lam, (size_t)n)) != TLFE_OK) return st;
+    ns->cap_cons = n;
+    ns->use_graph = -1;  // buffers moved: the graph is rebuilt
+    return TLFE_OK;
+}
+
+extern "C" tlfe_status tlfe_newton_step(tlfe_mesh *m, const double *u_n, const double *v_n,
+                                        const tlfe_step_params *prm, double *v_out, tlfe_step_report *rep,
+                                        void *stream)
+{
+    if (!m || !u_n || !v_n || !prm || !v_out || !rep) return fail(TLFE_E_INVALID, "NULL argument");
+    memset(rep, 0, sizeof(*rep));
+    if (!(prm->h > 0.0) || !std::isfinite(prm->h) || !(prm->newton_rtol >= 0.0) || !(prm->cg_rtol >= 0.0) ||
+        prm->max_newton < 0 || prm->max_cg < 0)
+        return fail(TLFE_E_INVALID, "bad step parameters");
+    const int n_cons = prm->n_cons;
+    if (n_cons < 0 || (n_cons > 0 && (!prm->cons_dev || !prm->lambda_dev || !(prm->rho > 0.0) ||
+                                      !std::isfinite(prm->rho) || !(prm->alm_tol >= 0.0) || prm->max_outer < 0)))
+        return fail(TLFE_E_INVALID, "bad constraint parameters");
+    for (auto &B : m->blocks)
+        if (B.n_elem > 0 && !B.affine) return fail(TLFE_E_UNSUPPORTED, "newton step needs affine elements (consistent mass)");
+    cudaStream_t s = (cudaStream_t)stream;
+    tlfe_status st;
+    const int coupled = n_cons > 0 ? 1 : 0;
+    if (m->newton && m->newton->coupled != coupled) destroy_newton(m);
+    if (!m->newton) {
+        st = setup_newton(m, s, coupled);
+        if (st != TLFE_OK) {
+            destroy_newton(m);
+            return st;
+        }
+        NCK(cudaMemsetAsync(m->newton->alm, 0, 2 * sizeof(int), s));
+    }
+    NewtonState *ns = m->newton;
+    const size_t N = (size_t)m->n_nodes, N3 = 3 * N;
+    if (n_cons > 0) {
+        st = ensure_constraints(ns, n_cons);
+        if (st != TLFE_OK) return st;
+        const ConBlocks bt = con_blocks(m);
+        if (bt.n < 0) return fail(TLFE_E_UNSUPPORTED, "constraints support at most 16 element blocks");
+        int bad = 0;
+        NCK(cudaMemcpyAsync(ns->cons, prm->cons_dev, sizeof(tlfe_constraint) * (size_t)n_cons,
+                            cudaMemcpyDeviceToDevice, s));
+        NCK(cudaMemsetAsync(ns->con_bad, 0, sizeof(int), s));
+        NCK(con_prepare(bt, n_cons, ns->cons, ns->con_sh, ns->con_nd, ns->con_bad, s));
+        NCK(cudaMemcpyAsync(&bad, ns->con_bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+        NCK(cudaStreamSynchronize(s));
+        if (bad) return fail(TLFE_E_INVALID, "constraint with a bad type or an element outside the mesh");
+    }
+    const bool same = ns->use_graph >= 0 && ns->h == prm->h && ns->grav[0] == prm->gravity[0] &&
+                      ns->grav[1] == prm->gravity[1] && ns->grav[2] == prm->gravity[2] &&
+                      ns->nrtol == prm->newton_rtol && ns->crtol == prm->cg_rtol && ns->max_newton == prm->max_newton &&
+                      ns->max_cg == prm->max_cg && ns->fixed_user == (const void *)prm->fixed_dev &&
+                      ns->n_cons == n_cons && (n_cons == 0 || ns->rho == prm->rho);
+    StepCtx x{m, ns, {ns->chunk_start, ns->chunk_end, ns->chunk_body, ns->n_chunks}, 0};
+    if (!same) {
+        ns->h = prm->h;
+        memcpy(ns->grav, prm->gravity, sizeof(ns->grav));
+        ns->nrtol = prm->newton_rtol;
+        ns->crtol = prm->cg_rtol;
+        ns->max_newton = prm->max_newton;
+        ns->max_cg = prm->max_cg;
+        ns->fixed_user = prm->fixed_dev;
+        ns->n_cons = n_cons;
+        ns->rho = prm->rho;
+        // clamped nodes: user's flags, plus nodes outside every element
+        std::vector<uint8_t> fx(N, 0);
+        if (prm->fixed_dev) NCK(cudaMemcpy(fx.data(), prm->fixed_dev, N, cudaMemcpyDeviceToHost));
+        for (size_t k = 0; k < N; ++k)
+            if (m->node_body[k] < 0) fx[k] = 1;
+        NCK(cudaMemcpy(ns->fixed, fx.data(), N, cudaMemcpyHostToDevice));
+        // f_ff = M b0 (Eq. virtual_work_force_field_uniform with sum_j s_j = 1)
+        NCK(cudaMemcpyAsync(ns->u_n, u_n, 8 * N3, cudaMemcpyDeviceToDevice, s));
+        k_fill_grav<<<(unsigned)((N + 255) / 256), 256, 0, s>>>((int64_t)N, prm->gravity[0], prm->gravity[1],
+                                                                prm->gravity[2], ns->gv);
+        NCK(cudaGetLastError());
+        tlfe_mesh *m64 = ns->twin ? ns->twin : m;
+        st = run_op<OP_MATVEC, double>(m64, ns->u_n, nullptr, ns->gv, ns->fgrav, nullptr, nullptr, 1.0, 0.0, 0.0, 0, s);
+        if (st != TLFE_OK) return st;
+        NCK(cudaMemcpyAsync(ns->fff, ns->fgrav, 8 * N3, cudaMemcpyDeviceToDevice, s));
+        NCK(cudaMemcpyAsync(ns->v_n, v_n, 8 * N3, cudaMemcpyDeviceToDevice, s));
+        if (n_cons > 0)
+            NCK(cudaMemcpyAsync(ns->lam, prm->lambda_dev, sizeof(double) * (size_t)n_cons, cudaMemcpyDeviceToDevice, s));
+        NCK(cudaMemsetAsync(ns->alm, 0, 2 * sizeof(int), s));
+        st = warm(x, s);
+        if (st != TLFE_OK) return st;
+        ns->use_graph = prm->use_graph ? 1 : 0;
+        if (prm->use_graph) {
+            NCK(cudaStreamSynchronize(s));
+            st = build_graph(x);
+            if (st != TLFE_OK) {
+                ns->use_graph = -1;
+                return st;
+            }
+        }
+    }
+    // inputs into the workspace (the graph only ever sees workspace pointers)
+    NCK(cudaMemcpyAsync(ns->u_n, u_n, 8 * N3, cudaMemcpyDeviceToDevice, s));
+    NCK(cudaMemcpyAsync(ns->v_n, v_n, 8 * N3, cudaMemcpyDeviceToDevice, s));
+    if (n_cons > 0)
+        NCK(cudaMemcpyAsync(ns->lam, prm->lambda_dev, sizeof(double) * (size_t)n_cons, cudaMemcpyDeviceToDevice, s));
+    // applied load of this step: f_ff + f_ext (Sec. 4), read by the residual
+    if (prm->f_ext_dev) {
+        k_add<<<(unsigned)((N3 + 255) / 256), 256, 0, s>>>((int64_t)N3, ns->fgrav, prm->f_ext_dev, ns->fff);
+        NCK(cudaGetLastError());
+    } else {
+        NCK(cudaMemcpyAsync(ns->fff, ns->fgrav, 8 * N3, cudaMemcpyDeviceToDevice, s));
+    }
+    // the Newton solve; with constraints, the augmented-Lagrangian loop of
+    // Sec. 7 around it (later solves warm-start and keep the first reference)
+    static const int flags0[2] = {0, 0}, flags1[2] = {1, 1};
+    NCK(cudaMemcpyAsync(ns->alm, flags0, sizeof(flags0), cudaMemcpyHostToDevice, s));
+    std::vector<double> ch((size_t)std::max(0, n_cons));
+    for (int outer = 0;; ++outer) {
+        st = newton_solve(x, prm, rep, s);
+        if (st != TLFE_OK) return st;
+        if (n_cons == 0) break;
+        // c at the solution (the last residual evaluated it at q(v))
+        NCK(cudaMemcpyAsync(ch.data(), ns->con_c, sizeof(double) * (size_t)n_cons, cudaMemcpyDeviceToHost, s));
+        NCK(cudaStreamSynchronize(s));
+        double cn = 0.0;
+        for (double c : ch) cn += c * c;
+        rep->c_norm = std::sqrt(cn);
+        rep->outer_iters = outer;
+        if (rep->c_norm <= prm->alm_tol || outer >= prm->max_outer) break;
+        NCK(con_lam_update(n_cons, ns->lam, ns->con_c, ns->rho, s));  // Eq. alm_multiplier_update
+        NCK(cudaMemcpyAsync(ns->alm, flags1, sizeof(flags1), cudaMemcpyHostToDevice, s));
+    }
+    if (n_cons > 0) {
+        NCK(cudaMemcpyAsync(prm->lambda_dev, ns->lam, sizeof(double) * (size_t)n_cons, cudaMemcpyDeviceToDevice, s));
+        NCK(cudaMemcpyAsync(ns->alm, flags0, sizeof(flags0), cudaMemcpyHostToDevice, s));
+        if (rep->status == TLFE_OK && rep->c_norm > prm->alm_tol) rep->status = TLFE_E_NOT_CONVERGED;
+    }
+    NCK(cudaMemcpyAsync(v_out, ns->v, 8 * N3, cudaMemcpyDeviceToDevice, s));
     int64_t ninv = 0;
     st = tlfe_sync(m, stream, &ninv);
     if (st == TLFE_OK && ns->twin) st = tlfe_sync(ns->twin, stream, &ninv);

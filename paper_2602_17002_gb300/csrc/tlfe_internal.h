@@ -92,4 +92,26 @@ cudaError_t launch_color_round(int n_elem, int npe, const int32_t *conn, const i
                                uint64_t seed, int elem_base, int32_t *color, int *n_left,
                                int *overflow, cudaStream_t s);
 
+// ---- constraint primitives (constraints.cu) ----
+constexpr int CON_MAXN = 10;  // nodes of the largest element
+constexpr int CON_MAXB = 16;  // element blocks a constraint set can refer to
+struct ConBlocks {            // block table passed to the kernels by value
+    int n;
+    int et[CON_MAXB], base[CON_MAXB], ne[CON_MAXB];
+    const int32_t *conn[CON_MAXB];
+};
+cudaError_t con_prepare(const ConBlocks &bt, int n, const tlfe_constraint *cons, double *sh, int32_t *nd, int *bad,
+                        cudaStream_t s);
+cudaError_t con_eval(int n, const tlfe_constraint *cons, const double *sh, const int32_t *nd, const double *X,
+                     const double *u, double *c, double *gp, cudaStream_t s);
+template <typename R>
+cudaError_t con_jt(int n, const double *sh, const int32_t *nd, const double *gp, const double *w, double scale, R *f,
+                   cudaStream_t s);
+cudaError_t con_j(int n, const double *sh, const int32_t *nd, const double *gp, const double *v, double *out,
+                  cudaStream_t s);
+template <typename R>
+cudaError_t con_diag(int n, const double *sh, const int32_t *nd, const double *gp, double alpha, R *D, cudaStream_t s);
+cudaError_t con_weights(int n, const double *lam, const double *c, double rho, double h, double *w, cudaStream_t s);
+cudaError_t con_lam_update(int n, double *lam, const double *c, double rho, cudaStream_t s);
+
 }  // namespace tlfe

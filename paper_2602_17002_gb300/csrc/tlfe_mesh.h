@@ -83,6 +83,7 @@ tlfe_status cuda_fail(cudaError_t e, const char *where);
 void *dalloc(tlfe_mesh *m, size_t bytes, cudaError_t *err);
 void destroy_newton(tlfe_mesh *m);
 tlfe_mesh *newton_twin(tlfe_mesh *m);  // FP64 twin of an FP32 mesh built by the Newton step, or nullptr
+ConBlocks con_blocks(const tlfe_mesh *m);  // n = -1 when the mesh has more blocks than a constraint set supports
 
 template <int OP, typename R>
 tlfe_status run_op(tlfe_mesh *m, const void *u, const void *ud, const void *v, void *out0, void *out1,

@@ -61,19 +61,29 @@ class tlfe_mesh_info(C.Structure):
 class tlfe_step_params(C.Structure):
     _fields_ = [("h", C.c_double), ("gravity", C.c_double * 3), ("newton_rtol", C.c_double),
                 ("cg_rtol", C.c_double), ("max_newton", C.c_int32), ("max_cg", C.c_int32),
-                ("fixed_dev", C.c_void_p), ("use_graph", C.c_int32), ("f_ext_dev", C.c_void_p)]
+                ("fixed_dev", C.c_void_p), ("use_graph", C.c_int32), ("f_ext_dev", C.c_void_p),
+                ("n_cons", C.c_int32), ("cons_dev", C.c_void_p), ("rho", C.c_double), ("alm_tol", C.c_double),
+                ("max_outer", C.c_int32), ("lambda_dev", C.c_void_p)]
 
 
 class tlfe_step_report(C.Structure):
     _fields_ = [("newton_iters", C.c_int32), ("cg_iters", C.c_int32), ("status", C.c_int32),
-                ("n_bodies_converged", C.c_int32), ("rel_residual", C.c_double)]
+                ("n_bodies_converged", C.c_int32), ("rel_residual", C.c_double), ("outer_iters", C.c_int32),
+                ("c_norm", C.c_double)]
 
+
+# bilateral constraint records (tlfe_constraint): points P, Q[, R, T] as (global
+# element, parent coordinates); element < 0 = ground point at world coordinates
+CON_CD, CON_DIST, CON_DP1, CON_DP2 = 0, 1, 2, 3
+CON_DTYPE = np.dtype([("type", np.int32), ("elem", np.int32, (4,)), ("xi", np.float64, (4, 3)),
+                      ("d", np.float64, (3,)), ("f", np.float64)], align=True)
 
 _lib = None
 
 EXPORTS = ["tlfe_create_mesh", "tlfe_destroy_mesh", "tlfe_get_mesh_info", "tlfe_get_colors", "tlfe_sync",
            "tlfe_internal_force", "tlfe_internal_force_host", "tlfe_tangent_matvec", "tlfe_jacobi_diag",
-           "tlfe_vjp", "tlfe_set_elem_mu_lambda", "tlfe_autotune", "tlfe_point_loads", "tlfe_surface_traction", "tlfe_newton_step", "tlfe_body_norms", "tlfe_norm_noalloc", "tlfe_last_error", "tlfe_version"]
+           "tlfe_vjp", "tlfe_set_elem_mu_lambda", "tlfe_autotune", "tlfe_point_loads", "tlfe_surface_traction",
+           "tlfe_constraint_eval", "tlfe_constraint_jt", "tlfe_constraint_j", "tlfe_newton_step", "tlfe_body_norms", "tlfe_norm_noalloc", "tlfe_last_error", "tlfe_version"]
 
 
 def load(path: str = LIB_PATH) -> C.CDLL:
@@ -103,6 +113,9 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "tlfe_autotune": [P, P, P, P, P],
         "tlfe_point_loads": [P, I, P, P, P, P, P],
         "tlfe_surface_traction": [P, I, P, P, P, P, P],
+        "tlfe_constraint_eval": [P, I, P, P, P, P],
+        "tlfe_constraint_jt": [P, I, P, P, P, P, P],
+        "tlfe_constraint_j": [P, I, P, P, P, P, P],
         "tlfe_norm_noalloc": [P, C.c_int64, P, P],
     }
     for name, args in sig.items():
@@ -347,8 +360,46 @@ class Mesh:
                                             _stream(stream)))
         return out
 
+    def _cons(self, cons):
+        """(device bytes tensor, count) of a CON_DTYPE array (numpy, host)."""
+        import torch
+        arr = np.ascontiguousarray(cons, dtype=CON_DTYPE)
+        return torch.from_numpy(arr.view(np.uint8).copy()).cuda(), int(arr.shape[0])
+
+    def constraint_eval(self, cons, u, stream=None):
+        """c_k(X + u) of the constraint records (Sec. 3 primitives), float64 CUDA (n,)."""
+        import torch
+        self._node_array(u, "u", torch.float64)
+        dc, n = self._cons(cons)
+        out = torch.empty(n, dtype=torch.float64, device="cuda")
+        _check(load().tlfe_constraint_eval(self._h, n, _ptr(dc), _ptr(u), _ptr(out), _stream(stream)))
+        return out
+
+    def constraint_jt(self, cons, u, w, out=None, stream=None):
+        """out += C_q^T w (float64 (n_nodes, 3); zeros when None)."""
+        import torch
+        self._node_array(u, "u", torch.float64)
+        out = self._new(torch.float64).zero_() if out is None else out
+        dc, n = self._cons(cons)
+        _check(load().tlfe_constraint_jt(self._h, n, _ptr(dc), _ptr(u), _ptr(w), _ptr(out), _stream(stream)))
+        return out
+
+    def constraint_j(self, cons, u, v, stream=None):
+        """C_q v, float64 CUDA (n,)."""
+        import torch
+        self._node_array(u, "u", torch.float64)
+        self._node_array(v, "v", torch.float64)
+        dc, n = self._cons(cons)
+        out = torch.empty(n, dtype=torch.float64, device="cuda")
+        _check(load().tlfe_constraint_j(self._h, n, _ptr(dc), _ptr(u), _ptr(v), _ptr(out), _stream(stream)))
+        return out
+
     def newton_step(self, u_n, v_n, h, gravity=(0.0, 0.0, -9.81), fixed=None, newton_rtol=1e-8, cg_rtol=1e-4,
-                    max_newton=20, max_cg=1000, use_graph=True, v_out=None, stream=None, f_ext=None):
+                    max_newton=20, max_cg=1000, use_graph=True, v_out=None, stream=None, f_ext=None,
+                    constraints=None, rho=1.0, alm_tol=1e-10, max_outer=20, lam=None):
+        """Backward-Euler step (tlfe_newton_step). With constraints (a CON_DTYPE
+        array) it is the augmented-Lagrangian step; lam (float64 CUDA (n,),
+        zeros when None) carries the multipliers in and out."""
         import torch
         self._node_array(u_n, "u_n", torch.float64)
         self._node_array(v_n, "v_n", torch.float64)
@@ -357,13 +408,19 @@ class Mesh:
         v_out = self._new(torch.float64) if v_out is None else v_out
         if fixed is not None and not (fixed.is_cuda and fixed.dtype == torch.uint8 and fixed.numel() == self.n_nodes):
             raise TLFEError(1, "fixed must be a CUDA uint8 tensor with one entry per node")
+        dc, n_cons = (None, 0) if constraints is None else self._cons(constraints)
+        if n_cons and lam is None:
+            lam = torch.zeros(n_cons, dtype=torch.float64, device="cuda")
         p = tlfe_step_params(float(h), (C.c_double * 3)(*[float(g) for g in gravity]), float(newton_rtol),
                              float(cg_rtol), int(max_newton), int(max_cg), _ptr(fixed), int(bool(use_graph)),
-                             _ptr(f_ext))
+                             _ptr(f_ext), n_cons, _ptr(dc), float(rho), float(alm_tol), int(max_outer),
+                             _ptr(lam if n_cons else None))
         rep = tlfe_step_report()
         code = load().tlfe_newton_step(self._h, _ptr(u_n), _ptr(v_n), C.byref(p), _ptr(v_out), C.byref(rep),
                                        _stream(stream))
         report = {k: getattr(rep, k) for k, _ in tlfe_step_report._fields_}
+        if n_cons:
+            report["lam"] = lam
         if code not in (0, 5):
             _check(code)
         report["code"] = code
@@ -410,6 +467,18 @@ def tlfe_point_loads(mesh: Mesh, elem, xi, force, f, stream=None):
 
 def tlfe_surface_traction(mesh: Mesh, elem, face, t0, f, stream=None):
     return mesh.surface_traction(elem, face, t0, f, stream)
+
+
+def tlfe_constraint_eval(mesh: Mesh, cons, u, stream=None):
+    return mesh.constraint_eval(cons, u, stream)
+
+
+def tlfe_constraint_jt(mesh: Mesh, cons, u, w, f, stream=None):
+    return mesh.constraint_jt(cons, u, w, f, stream)
+
+
+def tlfe_constraint_j(mesh: Mesh, cons, u, v, stream=None):
+    return mesh.constraint_j(cons, u, v, stream)
 
 
 def tlfe_set_elem_mu_lambda(mesh: Mesh, theta, stream=None):
