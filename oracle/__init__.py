@@ -28,7 +28,7 @@ _lib = None
 MAT_DTYPE = np.dtype([("model", np.int32), ("mu", np.float64), ("lam", np.float64),
                       ("mu_v", np.float64), ("lam_v", np.float64), ("rho", np.float64),
                       ("mu01", np.float64)], align=True)
-NPE = {0: 4, 1: 10, 2: 8}
+NPE = {0: 4, 1: 10, 2: 8, 3: 27}
 
 
 class Report(C.Structure):

@@ -93,9 +93,18 @@ int orc_nodes_per_elem(int type)
     case 0: return 4;
     case 1: return 10;
     case 2: return 8;
+    case 3: return 27;
     default: return -1;
     }
 }
+
+#define ORC_MAXN 27 /* nodes of the largest element (Q27) */
+#define ORC_MAXQ 27 /* points of the largest volume rule (3x3x3 Gauss) */
+
+/* 1-D quadratic Lagrange polynomials of the Q27 element on nodes -1, 0, 1
+ * (App., "1D Lagrange Polynomials"): L0 = s(s-1)/2, L1 = 1 - s^2, L2 = s(s+1)/2 */
+static double quad1(int a, double t) { return a == 0 ? 0.5 * t * (t - 1.0) : (a == 1 ? 1.0 - t * t : 0.5 * t * (t + 1.0)); }
+static double dquad1(int a, double t) { return a == 0 ? t - 0.5 : (a == 1 ? -2.0 * t : t + 0.5); }
 
 /* 1-D linear Lagrange factors on [-1, 1] used by the H8 tensor product */
 static double lin1(int i, double t) { return i == 0 ? 0.5 * (1.0 - t) : 0.5 * (1.0 + t); }
@@ -132,6 +141,14 @@ int orc_shape(int type, const double xi[3], double *s)
             for (int j = 0; j < 2; ++j)
                 for (int i = 0; i < 2; ++i)
                     s[i + 2 * j + 4 * k] = lin1(i, x) * lin1(j, y) * lin1(k, z);
+        return 0;
+    }
+    if (type == 3) {
+        /* Q27: tensor products L_i(xi) L_j(eta) L_k(zeta), node i + 3 j + 9 k
+         * at parent coordinates (i - 1, j - 1, k - 1) (App., Q27 node table) */
+        for (int k = 0; k < 3; ++k)
+            for (int j = 0; j < 3; ++j)
+                for (int i = 0; i < 3; ++i) s[i + 3 * j + 9 * k] = quad1(i, x) * quad1(j, y) * quad1(k, z);
         return 0;
     }
     return -1;
@@ -171,6 +188,17 @@ int orc_shape_grad(int type, const double xi[3], double *Hp)
                     Hp[n * 3 + 0] = dlin1(i) * lin1(j, y) * lin1(k, z);
                     Hp[n * 3 + 1] = lin1(i, x) * dlin1(j) * lin1(k, z);
                     Hp[n * 3 + 2] = lin1(i, x) * lin1(j, y) * dlin1(k);
+                }
+        return 0;
+    }
+    if (type == 3) {
+        for (int k = 0; k < 3; ++k)
+            for (int j = 0; j < 3; ++j)
+                for (int i = 0; i < 3; ++i) {
+                    const int n = i + 3 * j + 9 * k;
+                    Hp[n * 3 + 0] = dquad1(i, x) * quad1(j, y) * quad1(k, z);
+                    Hp[n * 3 + 1] = quad1(i, x) * dquad1(j, y) * quad1(k, z);
+                    Hp[n * 3 + 2] = quad1(i, x) * quad1(j, y) * dquad1(k, z);
                 }
         return 0;
     }
@@ -231,6 +259,20 @@ int orc_quad_rule(int type, int nq, double *pts, double *w)
         }
         return -1;
     }
+    if (type == 3 && nq == 27) {
+        /* 3 x 3 x 3 Gauss-Legendre: nodes 0, +-sqrt(3/5), weights 8/9, 5/9 */
+        const double g = sqrt(0.6), x3[3] = {-g, 0.0, g}, w3[3] = {5.0 / 9.0, 8.0 / 9.0, 5.0 / 9.0};
+        for (int k = 0; k < 3; ++k)
+            for (int j = 0; j < 3; ++j)
+                for (int i = 0; i < 3; ++i) {
+                    const int q = i + 3 * j + 9 * k;
+                    pts[q * 3 + 0] = x3[i];
+                    pts[q * 3 + 1] = x3[j];
+                    pts[q * 3 + 2] = x3[k];
+                    w[q] = w3[i] * w3[j] * w3[k];
+                }
+        return 0;
+    }
     return -1;
 }
 
@@ -279,7 +321,7 @@ int orc_exact_rule(int type, int order, double *pts, double *w)
     for (int k = 0; k < order; ++k)
         for (int j = 0; j < order; ++j)
             for (int i = 0; i < order; ++i, ++q) {
-                if (type == 2) {
+                if (type == 2 || type == 3) {
                     pts[q * 3 + 0] = gx[i];
                     pts[q * 3 + 1] = gx[j];
                     pts[q * 3 + 2] = gx[k];
@@ -329,11 +371,11 @@ int orc_precompute(int type, int nq, int n_elem, const int32_t *conn, const doub
                    double *H, double *wJ, double *Jp_min)
 {
     const int n = orc_nodes_per_elem(type);
-    double pts[8 * 3], w[8];
-    if (n < 0 || orc_quad_rule(type, nq, pts, w)) return -1;
+    double pts[ORC_MAXQ * 3], w[ORC_MAXQ];
+    if (n < 0 || nq > ORC_MAXQ || orc_quad_rule(type, nq, pts, w)) return -1;
     int bad = 0;
     double jmin = INFINITY;
-    double Xe[30], Hp[30], Jp[9], Ji[9];
+    double Xe[3 * ORC_MAXN], Hp[3 * ORC_MAXN], Jp[9], Ji[9];
     for (int e = 0; e < n_elem; ++e) {
         gather(n, conn + (size_t)e * n, X, Xe);
         for (int q = 0; q < nq; ++q) {
@@ -539,8 +581,8 @@ static void rate_gradient(int n, const double *He, const double *vde, double Fd[
  * that the oracle never stores anything the CUDA side could share) */
 typedef struct {
     int n, nq;
-    double H[8 * 10 * 3];
-    double wJ[8];
+    double H[ORC_MAXQ * ORC_MAXN * 3];
+    double wJ[ORC_MAXQ];
     int bad;
 } elem_geom;
 
@@ -563,7 +605,7 @@ int orc_internal_force(int type, int nq, int n_elem, const int32_t *conn, int n_
     if (n < 0) return -1;
     (void)n_nodes;
     int bad = 0;
-    double Xe[30], ue[30], vde[30], F[9], Fd[9], P[9];
+    double Xe[3 * ORC_MAXN], ue[3 * ORC_MAXN], vde[3 * ORC_MAXN], F[9], Fd[9], P[9];
     elem_geom g;
     for (int e = 0; e < n_elem; ++e) {
         const int32_t *ce = conn + (size_t)e * n;
@@ -571,7 +613,7 @@ int orc_internal_force(int type, int nq, int n_elem, const int32_t *conn, int n_
         gather(n, ce, X, Xe);
         gather(n, ce, u, ue);
         if (udot) gather(n, ce, udot, vde);
-        double fe[30] = {0};
+        double fe[3 * ORC_MAXN] = {0};
         for (int q = 0; q < nq; ++q) {
             const double *He = g.H + q * n * 3;
             deformation_gradient(n, He, Xe, ue, kin_form, F);
@@ -737,7 +779,7 @@ static int element_mass(int type, const int32_t *ce, const double *X, double rho
 {
     const int n = orc_nodes_per_elem(type);
     const int order = 5;
-    double pts[125 * 3], w[125], Xe[30], Hp[30], Jp[9], s[10];
+    double pts[125 * 3], w[125], Xe[3 * ORC_MAXN], Hp[3 * ORC_MAXN], Jp[9], s[ORC_MAXN];
     if (orc_exact_rule(type, order, pts, w)) return -1;
     gather(n, ce, X, Xe);
     if (Me) memset(Me, 0, sizeof(double) * n * n);
@@ -766,7 +808,7 @@ static int element_matrices_sel(int type, int nq, const int32_t *ce, const doubl
     const int N = 3 * n;
     elem_geom g;
     if (element_geometry(type, nq, ce, X, &g) < 0) return -1;
-    double Xe[30], ue[30], vde[30], F[9], Fd[9];
+    double Xe[3 * ORC_MAXN], ue[3 * ORC_MAXN], vde[3 * ORC_MAXN], F[9], Fd[9];
     gather(n, ce, X, Xe);
     gather(n, ce, u, ue);
     const int visc = udot != NULL && (m->mu_v != 0.0 || m->lam_v != 0.0);
@@ -850,7 +892,7 @@ int orc_operator_apply(int type, int nq, int n_elem, const int32_t *conn, int n_
         return -2;
     }
     int bad = 0;
-    double ve[30];
+    double ve[3 * ORC_MAXN];
     for (int e = 0; e < n_elem; ++e) {
         const int32_t *ce = conn + (size_t)e * n;
         int st = element_matrices_sel(type, nq, ce, X, u, udot, mat + e, sym_only,
@@ -957,7 +999,7 @@ int orc_vjp(int type, int nq, int n_elem, const int32_t *conn, int n_nodes,
     }
     if (g_theta) {
         const int n = orc_nodes_per_elem(type);
-        double Xe[30], ue[30], re[30], F[9], dmu[9], dlam[9];
+        double Xe[3 * ORC_MAXN], ue[3 * ORC_MAXN], re[3 * ORC_MAXN], F[9], dmu[9], dlam[9];
         elem_geom g;
         for (int e = 0; e < n_elem; ++e) {
             const int32_t *ce = conn + (size_t)e * n;
@@ -1015,7 +1057,7 @@ int orc_gravity(int type, int n_elem, const int32_t *conn, int n_nodes, const do
     const int n = orc_nodes_per_elem(type);
     if (n < 0) return -1;
     (void)n_nodes;
-    double vs[10];
+    double vs[ORC_MAXN];
     for (int e = 0; e < n_elem; ++e) {
         const int32_t *ce = conn + (size_t)e * n;
         if (element_mass(type, ce, X, 1.0, NULL, vs)) return -1;
@@ -1037,7 +1079,7 @@ int orc_point_loads(int type, int n_loads, const int32_t *conn, const int32_t *e
 {
     const int n = orc_nodes_per_elem(type);
     if (n < 0) return -1;
-    double s[10];
+    double s[ORC_MAXN];
     for (int k = 0; k < n_loads; ++k) {
         if (orc_shape(type, xi + 3 * k, s)) return -1;
         const int32_t *ce = conn + (size_t)elem[k] * n;
@@ -1076,7 +1118,7 @@ static int face_map(int type, int face, double a, double b, double xi[3], double
         }
         return 0;
     }
-    if (type == 2) {
+    if (type == 2 || type == 3) {
         if (face < 0 || face > 5) return -1;
         const int d = face / 2, sgn = face % 2;
         const int d1 = d == 0 ? 1 : 0, d2 = d == 2 ? 1 : 2;
@@ -1092,8 +1134,9 @@ static int face_map(int type, int face, double a, double b, double xi[3], double
 }
 
 /* Face rule: tetrahedron faces 4 x 4 collapsed Gauss-Legendre on the unit
- * triangle ((a, b) = (u, (1 - u) v), weight (1 - u)); brick faces 3 x 3
- * Gauss-Legendre. Returns the number of points. */
+ * triangle ((a, b) = (u, (1 - u) v), weight (1 - u)); brick faces (H8, Q27)
+ * 3 x 3 Gauss-Legendre, exact for the biquadratic face shape functions of a
+ * flat face. Returns the number of points. */
 static int face_rule(int type, double *pa, double *pb, double *pw)
 {
     double gx[4], gw[4];
@@ -1130,7 +1173,7 @@ int orc_surface_traction(int type, int n_faces, const int32_t *conn, const doubl
 {
     const int n = orc_nodes_per_elem(type);
     if (n < 0) return -1;
-    double pa[16], pb[16], pw[16], s[10], Hp[30];
+    double pa[16], pb[16], pw[16], s[ORC_MAXN], Hp[3 * ORC_MAXN];
     const int nq = face_rule(type, pa, pb, pw);
     for (int k = 0; k < n_faces; ++k) {
         const int32_t *ce = conn + (size_t)elem[k] * n;
@@ -1173,7 +1216,7 @@ static void con_point(int type, const orc_constraint *k, int p, const int32_t *c
         return;
     }
     const int n = orc_nodes_per_elem(type);
-    double s[10];
+    double s[ORC_MAXN];
     orc_shape(type, k->xi[p], s);
     const int32_t *ce = conn + (size_t)k->elem[p] * n;
     for (int a = 0; a < 3; ++a) {
@@ -1244,7 +1287,7 @@ int orc_constraint_jt(int type, int n_cons, const orc_constraint *cons, const in
                       const double *u, const double *w, double *f)
 {
     const int n = orc_nodes_per_elem(type);
-    double gp[4][3], c, s[10];
+    double gp[4][3], c, s[ORC_MAXN];
     for (int k = 0; k < n_cons; ++k) {
         const orc_constraint *ck = cons + k;
         if (con_eval(type, ck, conn, X, u, &c, gp)) return -1;
@@ -1264,7 +1307,7 @@ int orc_constraint_j(int type, int n_cons, const orc_constraint *cons, const int
                      const double *u, const double *v, double *out)
 {
     const int n = orc_nodes_per_elem(type);
-    double gp[4][3], c, s[10];
+    double gp[4][3], c, s[ORC_MAXN];
     for (int k = 0; k < n_cons; ++k) {
         const orc_constraint *ck = cons + k;
         if (con_eval(type, ck, conn, X, u, &c, gp)) return -1;
@@ -1431,7 +1474,7 @@ static int newton_core(int type, int nq, int n_elem, const int32_t *conn, int n_
         }
         if (n_cons > 0) {
             /* diagonal of h^2 rho C_q^T C_q: sum over constraint points of (s_i dc/dr_p)^2 */
-            double gp[4][3], cv, sh[10];
+            double gp[4][3], cv, sh[ORC_MAXN];
             for (int k = 0; k < n_cons; ++k) {
                 con_eval(type, cons + k, conn, X, ut, &cv, gp);
                 for (int pp = 0; pp < con_npoints(cons[k].type); ++pp) {

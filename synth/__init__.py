@@ -8,7 +8,7 @@ consume what it produces, so it must stay free of the method itself.
 """
 
 from .mesh import (  # noqa: F401
-    T4, T10, H8, NODES_PER_ELEM, Mesh, box_mesh, concat_meshes, boundary_faces, face_corners,
+    T4, T10, H8, Q27, NODES_PER_ELEM, Mesh, box_mesh, concat_meshes, boundary_faces, face_corners,
 )
 from .workloads import (  # noqa: F401
     block_t10_svk, cantilever_beam, batch_bodies, diff_block, newton_beams,

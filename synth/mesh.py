@@ -8,6 +8,8 @@ Node ordering conventions follow the paper's element tables:
   coordinates (0,0,0), (1,0,0), (0,1,0), (0,0,1); nodes 5-10 sit on the edges
   (1,2), (2,3), (1,3), (1,4), (2,4), (3,4).
 * T4: the four corners in the same order.
+* Q27 (Appendix, 27-node hexahedron table): node i + 3 j + 9 k at parent
+  coordinates (i - 1, j - 1, k - 1), on the half-step grid.
 * H8: tensor-product ordering with the first index fastest, as in the Q27
   table of Appendix A.2, on the vertex grid {-1, 1}^3.
 
@@ -22,9 +24,9 @@ from itertools import permutations
 
 import numpy as np
 
-T4, T10, H8 = 0, 1, 2
-NODES_PER_ELEM = {T4: 4, T10: 10, H8: 8}
-TYPE_NAME = {T4: "T4", T10: "T10", H8: "H8"}
+T4, T10, H8, Q27 = 0, 1, 2, 3
+NODES_PER_ELEM = {T4: 4, T10: 10, H8: 8, Q27: 27}
+TYPE_NAME = {T4: "T4", T10: "T10", H8: "H8", Q27: "Q27"}
 
 
 @dataclass
@@ -89,7 +91,7 @@ def box_mesh(etype: int, cells, size, origin=(0.0, 0.0, 0.0)) -> Mesh:
     """
     nx, ny, nz = (int(c) for c in cells)
     lx, ly, lz = (float(s) for s in size)
-    step = 2 if etype == T10 else 1
+    step = 2 if etype in (T10, Q27) else 1
     gx, gy, gz = step * nx + 1, step * ny + 1, step * nz + 1
     xs = origin[0] + np.linspace(0.0, lx, gx)
     ys = origin[1] + np.linspace(0.0, ly, gy)
@@ -100,6 +102,16 @@ def box_mesh(etype: int, cells, size, origin=(0.0, 0.0, 0.0)) -> Mesh:
     # cells ordered with x fastest
     ck, cj, ci = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
     cell = np.stack([ci.ravel(), cj.ravel(), ck.ravel()], axis=1)  # (n_cells, 3)
+
+    if etype == Q27:
+        # half-step grid; node i + 3 j + 9 k of a cell sits at 2 cell + (i, j, k)
+        conn = np.empty((cell.shape[0], 27), dtype=np.int64)
+        for k in range(3):
+            for j in range(3):
+                for i in range(3):
+                    p = 2 * cell + np.array([i, j, k])
+                    conn[:, i + 3 * j + 9 * k] = _grid_index(p[:, 0], p[:, 1], p[:, 2], gx, gy)
+        return Mesh(X, conn.astype(np.int32), Q27)
 
     if etype == H8:
         conn = np.empty((cell.shape[0], 8), dtype=np.int64)
@@ -159,16 +171,24 @@ def concat_meshes(meshes):
 def face_corners(etype: int, face: int):
     """Local corner nodes of a parent face: tetrahedra, face k is opposite
     vertex k (the other three corners in increasing order); bricks, face
-    2 d + s holds the corners whose bit d equals s."""
+    2 d + s holds the corners whose bit d equals s (Q27: the corner nodes
+    with tensor index 0 or 2 along d)."""
     if etype in (T4, T10):
         return [j for j in range(4) if j != face]
     d, s = divmod(face, 2)
+    if etype == Q27:
+        out = []
+        for n in range(27):
+            idx = (n % 3, (n // 3) % 3, n // 9)
+            if all(t in (0, 2) for t in idx) and idx[d] == 2 * s:
+                out.append(n)
+        return out
     return [n for n in range(8) if ((n >> d) & 1) == s]
 
 
 def boundary_faces(etype: int, conn: np.ndarray):
     """(element, local face) of every face that belongs to exactly one element."""
-    nf = 4 if etype in (T4, T10) else 6
+    nf = 4 if etype in (T4, T10) else 6   # bricks (H8, Q27): 6 faces
     seen = {}
     for e in range(conn.shape[0]):
         for f in range(nf):

@@ -15,7 +15,7 @@ import pytest
 
 import oracle
 import synth
-from synth import T4, T10, H8
+from synth import T4, T10, H8, Q27
 
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
 ATOL = 1e-12
@@ -60,11 +60,11 @@ def test_t10_kronecker_at_printed_nodes():
         assert np.allclose(s, e, atol=1e-15), (j, s)
 
 
-@pytest.mark.parametrize("etype", [T4, T10, H8])
+@pytest.mark.parametrize("etype", [T4, T10, H8, Q27])
 def test_partition_of_unity_and_gradient_by_fd(etype):
     rng = np.random.default_rng(0)
     for _ in range(20):
-        if etype == H8:
+        if etype in (H8, Q27):
             xi = rng.uniform(-1, 1, 3)
         else:
             xi = rng.dirichlet(np.ones(4))[1:]
@@ -90,6 +90,46 @@ def test_t10_is_barycentric_quadratic_lagrange():
         s = oracle.shape(T10, L[1:])
         ref = [L[k] * (2 * L[k] - 1) for k in range(4)] + [4 * L[a] * L[b] for a, b in edges]
         assert np.allclose(s, ref, atol=1e-15)
+
+
+def test_q27_kronecker_at_printed_nodes():
+    tab = _load_golden("q27_parent_nodes.txt")
+    assert tab.shape == (27, 7)
+    for row in tab:
+        n = int(row[0]) - 1
+        assert n == int(row[1]) + 3 * int(row[2]) + 9 * int(row[3])
+        s = oracle.shape(Q27, row[4:7])
+        e = np.zeros(27)
+        e[n] = 1.0
+        assert np.allclose(s, e, atol=1e-15), (n, s)
+
+
+def test_q27_matches_printed_expanded_shape_functions():
+    # a few entries of the printed expanded vector s(xi, eta, zeta) (App., Q27)
+    rng = np.random.default_rng(13)
+    for _ in range(10):
+        x, y, z = rng.uniform(-1, 1, 3)
+        s = oracle.shape(Q27, np.array([x, y, z]))
+        s1 = (y**2 * x**2 * z**2 / 8 - y**2 * x**2 * z / 8 - y**2 * x * z**2 / 8 + y**2 * x * z / 8
+              - y * x**2 * z**2 / 8 + y * x**2 * z / 8 + y * x * z**2 / 8 - y * x * z / 8)
+        s14 = (-y**2 * x**2 * z**2 + y**2 * x**2 + y**2 * z**2 - y**2 + x**2 * z**2 - x**2 - z**2 + 1)
+        s27 = (y**2 * x**2 * z**2 / 8 + y**2 * x**2 * z / 8 + y**2 * x * z**2 / 8 + y**2 * x * z / 8
+               + y * x**2 * z**2 / 8 + y * x**2 * z / 8 + y * x * z**2 / 8 + y * x * z / 8)
+        s5 = (y**2 * x**2 * z**2 / 2 - y**2 * x**2 * z / 2 - y**2 * z**2 / 2 + y**2 * z / 2
+              - x**2 * z**2 / 2 + x**2 * z / 2 + z**2 / 2 - z / 2)
+        for got, ref in ((s[0], s1), (s[13], s14), (s[26], s27), (s[4], s5)):
+            assert abs(got - ref) < 1e-14
+
+
+def test_q27_gauss_rule_exact_to_degree_5():
+    pts, w = oracle.quad_rule(Q27, 27)
+    for a, b, c in product(range(7), repeat=3):
+        ex = np.prod([0.0 if k % 2 else 2.0 / (k + 1) for k in (a, b, c)])
+        val = np.sum(w * pts[:, 0] ** a * pts[:, 1] ** b * pts[:, 2] ** c)
+        if max(a, b, c) <= 5:
+            assert abs(val - ex) < 1e-14
+        elif (a, b, c) == (6, 0, 0):
+            assert abs(val - ex) > 1e-3      # and no further
 
 
 def test_h8_kronecker_q27_ordering():
@@ -150,7 +190,7 @@ def test_hex_gauss_and_exact_rules():
 # Section 6: H = Hp (U Hp)^{-1}, J_p
 # ------------------------------------------------------------------------
 
-@pytest.mark.parametrize("etype,nq", [(T4, 1), (T10, 4), (T10, 5), (H8, 8)])
+@pytest.mark.parametrize("etype,nq", [(T4, 1), (T10, 4), (T10, 5), (H8, 8), (Q27, 27)])
 def test_precompute_UH_identity_and_volume(etype, nq):
     m = synth.box_mesh(etype, (2, 2, 1), (0.8, 0.6, 0.3))
     rng = np.random.default_rng(2)
@@ -337,7 +377,7 @@ def _affine_state(wl, A, b=(0.1, -0.2, 0.3)):
     return wl.X @ (A - np.eye(3)).T + np.asarray(b)
 
 
-@pytest.mark.parametrize("etype,nq,model", [(T4, 1, 0), (T10, 4, 0), (T10, 5, 1), (H8, 8, 1)])
+@pytest.mark.parametrize("etype,nq,model", [(T4, 1, 0), (T10, 4, 0), (T10, 5, 1), (H8, 8, 1), (Q27, 27, 1)])
 def test_patch_test_uniform_F_zero_interior_force(etype, nq, model):
     cells = (3, 3, 3)
     m = synth.box_mesh(etype, cells, (1.0, 1.0, 1.0))
@@ -529,6 +569,31 @@ def test_t10_consistent_mass_by_barycentric_formula():
         assert abs(Me[0::3, 0::3].sum() - rho * V) < 1e-12 * rho * V
 
 
+def test_q27_box_mass_is_kronecker_of_1d_quadratic_masses():
+    # on a box the triquadratic shape functions factor, so m_ij = rho int s_i s_j dV
+    # is the Kronecker product of the 1D quadratic Lagrange mass matrices
+    # (L/30)[[4, 2, -1], [2, 16, 2], [-1, 2, 4]] (node n = i + 3 j + 9 k)
+    a, b, c = 0.7, 0.5, 0.9
+    m = synth.box_mesh(Q27, (1, 1, 1), (a, b, c))
+    rho = 1200.0
+    m1 = np.array([[4.0, 2.0, -1.0], [2.0, 16.0, 2.0], [-1.0, 2.0, 4.0]]) / 30.0
+    Mref = rho * np.kron(np.kron(c * m1, b * m1), a * m1)
+    _, _, Me = oracle.element_matrices(Q27, 27, m.conn[0], m.X, np.zeros_like(m.X), None,
+                                       oracle.material(1, MU, LAM, rho=rho))
+    V = a * b * c
+    assert np.abs(Me[0::3, 0::3] - Mref).max() < 1e-13 * rho * V
+    assert np.abs(Me[1::3, 1::3] - Mref).max() < 1e-13 * rho * V
+    assert np.abs(Me[0::3, 1::3]).max() == 0.0
+    # gravity weights int s_i dV: Kronecker of the 1D (1/6, 2/3, 1/6) L
+    w1 = np.array([1.0, 4.0, 1.0]) / 6.0
+    wl = synth.workloads.Workload("q27", m.X, [synth.workloads.Block(Q27, 27, m.conn, np.zeros(1, np.int32))],
+                                  np.array([1], np.int32), np.array([[MU, LAM, 0.0, 0.0, rho]]),
+                                  u=np.zeros_like(m.X))
+    f = oracle.gravity_load(wl, np.array([0.0, 0.0, -9.81]))
+    wref = np.kron(np.kron(c * w1, b * w1), a * w1)
+    assert np.abs(f[m.conn[0], 2] / (-9.81 * rho) - wref).max() < 1e-14
+
+
 def test_gravity_weights_t10_and_mass_totals():
     wl = synth.small_beam(cells=(2, 1, 1))
     g = np.array([0.0, 0.0, -9.81])
@@ -666,12 +731,12 @@ def _outward_normals(etype, X, conn, elem, face):
     for e, f in zip(elem, face):
         cs = synth.face_corners(etype, f)
         P = X[conn[e, cs]]
-        if etype == H8:          # corners in bit order: (0, 1, 3, 2) walks the quad
+        if etype in (H8, Q27):   # corners in tensor order: (0, 1, 3, 2) walks the quad
             P = P[[0, 1, 3, 2]]
             nv = 0.5 * np.cross(P[2] - P[0], P[3] - P[1])
         else:
             nv = 0.5 * np.cross(P[1] - P[0], P[2] - P[0])
-        inner = X[conn[e, [c for c in range(4 if etype != H8 else 8) if c not in cs]]].mean(axis=0)
+        inner = X[conn[e, [c for c in range(conn.shape[1]) if c not in cs]]].mean(axis=0)
         if np.dot(nv, inner - P[0]) > 0:
             nv = -nv
         a = np.linalg.norm(nv)
@@ -680,7 +745,7 @@ def _outward_normals(etype, X, conn, elem, face):
     return np.array(n_out), np.array(area)
 
 
-@pytest.mark.parametrize("etype,nq", [(T4, 1), (T10, 5), (H8, 8)])
+@pytest.mark.parametrize("etype,nq", [(T4, 1), (T10, 5), (H8, 8), (Q27, 27)])
 def test_traction_of_uniform_stress_balances_internal_force(etype, nq):
     """A homogeneous deformation F = A is in equilibrium under the boundary
     traction t0 = P(A) n0 (Sec. 4, the nominal traction induced by a stress):
@@ -706,7 +771,7 @@ def test_traction_of_uniform_stress_balances_internal_force(etype, nq):
         assert np.abs(one.sum(axis=0) - t0[k] * area[k]).max() < 1e-12 * np.abs(t0[k]).max() * area[k]
 
 
-@pytest.mark.parametrize("etype,nq", [(T4, 1), (T10, 5), (H8, 8)])
+@pytest.mark.parametrize("etype,nq", [(T4, 1), (T10, 5), (H8, 8), (Q27, 27)])
 def test_point_loads_partition_and_kronecker(etype, nq):
     m = synth.box_mesh(etype, (2, 1, 1), (1.0, 1.0, 1.0))
     from synth.workloads import Block, Workload
@@ -715,7 +780,7 @@ def test_point_loads_partition_and_kronecker(etype, nq):
     rng = np.random.default_rng(32)
     k = 7
     elem = rng.integers(0, m.n_elem, k).astype(np.int32)
-    if etype == H8:
+    if etype in (H8, Q27):
         xi = rng.uniform(-1, 1, (k, 3))
     else:
         L = rng.dirichlet(np.ones(4), k)
@@ -724,8 +789,8 @@ def test_point_loads_partition_and_kronecker(etype, nq):
     f = oracle.point_loads(wl, 0, elem, xi, force)
     assert np.abs(f.sum(axis=0) - force.sum(axis=0)).max() < 1e-12
     # a load at a node of the parent element goes to that node only
-    node_xi = {T4: [0, 0, 0], T10: [0.5, 0, 0], H8: [1, -1, -1]}[etype]
-    node_id = {T4: 0, T10: 4, H8: 1}[etype]
+    node_xi = {T4: [0, 0, 0], T10: [0.5, 0, 0], H8: [1, -1, -1], Q27: [0, 1, 0]}[etype]
+    node_id = {T4: 0, T10: 4, H8: 1, Q27: 16}[etype]
     f1 = oracle.point_loads(wl, 0, np.array([0], np.int32), np.array([node_xi], float), np.array([[1.0, 2.0, 3.0]]))
     g = m.conn[0, node_id]
     assert np.abs(f1[g] - [1.0, 2.0, 3.0]).max() < 1e-14
