@@ -62,13 +62,14 @@ typedef enum {
     TLFE_E_NONFINITE = 8      /* NaN / Inf met on the device */
 } tlfe_status;
 
-enum { TLFE_T4 = 0, TLFE_T10 = 1, TLFE_H8 = 2 };   /* element types (App. A; T4/H8 textbook) */
+enum { TLFE_T4 = 0, TLFE_T10 = 1, TLFE_H8 = 2, TLFE_Q27 = 3 };  /* element types (App. A; T4/H8 textbook) */
 enum { TLFE_SVK = 0, TLFE_NEOHOOKE = 1, TLFE_MOONEY_RIVLIN = 2 };  /* elastic laws (Sec. 3.2, App. C) */
 enum { TLFE_FP64 = 0, TLFE_FP32 = 1 };              /* element arithmetic */
 enum { TLFE_SCATTER_ATOMIC = 0, TLFE_SCATTER_COLOR = 1 };
 /* Where the element kernels take the reference gradients h_i from:
  *   TLFE_PATH_AUTO   : affine blocks (every T4; straight-edged T10;
- *                      parallelepiped H8) keep J^{-1} and det J per element and
+ *                      parallelepiped H8 and Q27 with evenly spaced nodes)
+ *                      keep J^{-1} and det J per element and
  *                      form h_i = J^{-T} dS_i/dxi(xi_q) at each point (Sec. 6,
  *                      affine case); other blocks stream the precomputed h_i
  *                      and w_q J_p of every point
@@ -79,8 +80,11 @@ enum { TLFE_PATH_AUTO = 0, TLFE_PATH_SLAB = 1, TLFE_PATH_AFFINE = 2 };
 
 /* One type-homogeneous element block.
  *   type  : TLFE_T4 (4 nodes), TLFE_T10 (10 nodes, App. A.1 node order),
- *           TLFE_H8 (8 nodes, tensor order i + 2j + 4k on {-1,1}^3)
- *   n_qp  : quadrature points per element: T4 1; T10 4 or 5; H8 8
+ *           TLFE_H8 (8 nodes, tensor order i + 2j + 4k on {-1,1}^3),
+ *           TLFE_Q27 (27 nodes, node i + 3j + 9k at (i-1, j-1, k-1), App. A
+ *           Q27 node table)
+ *   n_qp  : quadrature points per element: T4 1; T10 4 or 5; H8 8;
+ *           Q27 27 (3x3x3 Gauss-Legendre)
  *   conn  : host [n_elem][nodes] 0-based global node ids (copied)
  *   body  : host [n_elem] body id in [0, n_bodies), or NULL for body 0 */
 typedef struct {

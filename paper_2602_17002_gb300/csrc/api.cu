@@ -68,7 +68,8 @@ void *dalloc(tlfe_mesh *m, size_t bytes, cudaError_t *err)
 
 static bool valid_nq(int et, int nq)
 {
-    return (et == ET_T4 && nq == 1) || (et == ET_T10 && (nq == 4 || nq == 5)) || (et == ET_H8 && nq == 8);
+    return (et == ET_T4 && nq == 1) || (et == ET_T10 && (nq == 4 || nq == 5)) || (et == ET_H8 && nq == 8) ||
+           (et == ET_Q27 && nq == 27);
 }
 
 static tlfe_status validate(const tlfe_mesh_desc *d)
@@ -97,7 +98,7 @@ static tlfe_status validate(const tlfe_mesh_desc *d)
     int64_t ne = 0;
     for (int bi = 0; bi < d->n_blocks; ++bi) {
         const tlfe_block &b = d->blocks[bi];
-        if (b.type < 0 || b.type > 2) return fail(TLFE_E_INVALID, "bad element type");
+        if (b.type < 0 || b.type > 3) return fail(TLFE_E_INVALID, "bad element type");
         if (!valid_nq(b.type, b.n_qp)) return fail(TLFE_E_UNSUPPORTED, "unsupported quadrature size for the element type");
         if (b.n_elem < 0 || (b.n_elem > 0 && !b.conn)) return fail(TLFE_E_INVALID, "bad block element count / conn");
         const int npe = nodes_per_elem(b.type);

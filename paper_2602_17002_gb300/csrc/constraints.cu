@@ -38,7 +38,7 @@ __global__ void k_con_prepare(int n, const tlfe_constraint *__restrict__ cons, C
     for (int b = 0; b < bt.n; ++b) {
         if (e >= bt.base[b] && e < bt.base[b] + bt.ne[b]) {
             const double xi[3] = {c.xi[p][0], c.xi[p][1], c.xi[p][2]};
-            double v[10];
+            double v[27];
             shape_fn(bt.et[b], xi, v);
             const int npe = nodes_per_elem(bt.et[b]);
             for (int i = 0; i < npe; ++i) {

@@ -247,16 +247,18 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 // Resident CTAs (of 4 warps) per SM the register allocation aims at, by
 // measurement on the beam workload: the FP32 affine force kernel fits 16
 // warps per SM in 128 registers; the adjoint, with two element vectors live,
-// runs fastest unspilled at 8 warps; FP64 kernels take all 255 registers.
-template <typename R, int OP, bool AFF> constexpr int min_ctas()
+// runs fastest unspilled at 8 warps; FP64 kernels take all 255 registers, and
+// so do Q27 kernels (81-entry element vectors; their shared-memory footprint
+// limits the resident warps anyway).
+template <int ET, typename R, int OP, bool AFF> constexpr int min_ctas()
 {
-    if (sizeof(R) != 4) return 1;
+    if (sizeof(R) != 4 || ET == ET_Q27) return 1;
     if (OP == OP_VJP) return 2;
     return (OP == OP_FORCE && AFF) ? 4 : 3;
 }
 
 template <int ET, int NQ, typename R, int OP, bool AFF, int MAT>
-__global__ void __launch_bounds__(128, min_ctas<R, OP, AFF>()) k_elem(const KParams<R> p)
+__global__ void __launch_bounds__(128, min_ctas<ET, R, OP, AFF>()) k_elem(const KParams<R> p)
 {
     constexpr int NPE = Elem<ET>::NPE;
     constexpr int REC = Rec<OP, R>::REC;
@@ -736,6 +738,7 @@ template <int OP, typename R, bool AFF, int MAT> static void (*kernel_for_(int e
     if (et == ET_T10 && nq == 4) return k_elem<ET_T10, 4, R, OP, AFF, MAT>;
     if (et == ET_T10 && nq == 5) return k_elem<ET_T10, 5, R, OP, AFF, MAT>;
     if (et == ET_H8 && nq == 8) return k_elem<ET_H8, 8, R, OP, AFF, MAT>;
+    if (et == ET_Q27 && nq == 27) return k_elem<ET_Q27, 27, R, OP, AFF, MAT>;
     return nullptr;
 }
 // FP32 kernels are specialised on the material mode; FP64 kernels (the plain
@@ -763,6 +766,7 @@ template <int OP, typename R, bool AFF> size_t smem_for_(int et, int umax, int m
     if (et == ET_T4) return elem_smem_bytes<ET_T4, R, OP, AFF>(umax, meta_bytes, wpb);
     if (et == ET_T10) return elem_smem_bytes<ET_T10, R, OP, AFF>(umax, meta_bytes, wpb);
     if (et == ET_H8) return elem_smem_bytes<ET_H8, R, OP, AFF>(umax, meta_bytes, wpb);
+    if (et == ET_Q27) return elem_smem_bytes<ET_Q27, R, OP, AFF>(umax, meta_bytes, wpb);
     return 0;
 }
 template <int OP, typename R> size_t smem_for(int et, int umax, int meta_bytes, int wpb, bool aff)

@@ -7,9 +7,10 @@ namespace tlfe {
 
 // Affine element (Sec. 6, affine case): the map from the parent element is
 // u(xi) = A xi + b. Holds for every T4; for T10 when the mid-edge nodes sit at
-// their edge midpoints; for H8 when the brick is a parallelepiped. Tolerance
-// 1e-10 of the element extent.
-__device__ bool element_is_affine(int et, int npe, const double Xe[10][3])
+// their edge midpoints; for H8 when the brick is a parallelepiped; for Q27
+// when the nodes sit at X_0 + (i/2)(X_2 - X_0) + (j/2)(X_6 - X_0) + (k/2)(X_18 - X_0)
+// (node i + 3j + 9k). Tolerance 1e-10 of the element extent.
+__device__ bool element_is_affine(int et, int npe, const double Xe[27][3])
 {
     bool affine = true;
     double ext = 0.0;
@@ -30,6 +31,13 @@ __device__ bool element_is_affine(int et, int npe, const double Xe[10][3])
                                  ((n & 2) ? Xe[2][d] - Xe[0][d] : 0.0) + ((n & 4) ? Xe[4][d] - Xe[0][d] : 0.0);
                 if (fabs(Xe[n][d] - p) > tol) affine = false;
             }
+    } else if (et == ET_Q27) {
+        for (int n = 0; n < 27; ++n)
+            for (int d = 0; d < 3; ++d) {
+                const double p = Xe[0][d] + 0.5 * (n % 3) * (Xe[2][d] - Xe[0][d]) +
+                                 0.5 * ((n / 3) % 3) * (Xe[6][d] - Xe[0][d]) + 0.5 * (n / 9) * (Xe[18][d] - Xe[0][d]);
+                if (fabs(Xe[n][d] - p) > tol) affine = false;
+            }
     }
     return affine;
 }
@@ -37,7 +45,7 @@ __device__ bool element_is_affine(int et, int npe, const double Xe[10][3])
 // Jp = U Hp(xi) evaluated as sum_{i>0} (X_i - X_0) dS_i/dxi^T (the parent
 // gradients sum to zero); relative coordinates keep the digits that large
 // absolute coordinates would cancel away. Returns det Jp and Jp^{-1} = cof^T / det.
-__device__ double parent_jacobian_inv(int et, int npe, const double Xe[10][3], const double *g, double Ji[9])
+__device__ double parent_jacobian_inv(int et, int npe, const double Xe[27][3], const double *g, double Ji[9])
 {
     double J[9];
     for (int a = 0; a < 3; ++a)
@@ -90,7 +98,7 @@ __global__ void k_precompute(int et, int nq, int npe, int n_tiles, const int32_t
         return;
     }
     const int64_t el = (int64_t)e - elem_base;
-    double Xe[10][3];
+    double Xe[27][3];
     for (int i = 0; i < npe; ++i) {
         const int64_t n = conn[el * npe + i];
         for (int a = 0; a < 3; ++a) Xe[i][a] = X[n * 3 + a];
@@ -98,7 +106,7 @@ __global__ void k_precompute(int et, int nq, int npe, int n_tiles, const int32_t
     double vol = 0.0, jmin = 1e300, jmax = -1e300;
     int inverted = 0;
     for (int q = 0; q < nq; ++q) {
-        double xi[3], w, g[30];
+        double xi[3], w, g[81];
         quad_point(et, nq, q, xi, w);
         parent_grad(et, xi, g);
         double Ji[9];
@@ -166,13 +174,13 @@ __global__ void k_precompute_affine(int et, int npe, int n_tiles, const int32_t 
         return;
     }
     const int64_t el = (int64_t)e - elem_base;
-    double Xe[10][3];
+    double Xe[27][3];
     for (int i = 0; i < npe; ++i) {
         const int64_t n = conn[el * npe + i];
         for (int a = 0; a < 3; ++a) Xe[i][a] = X[n * 3 + a];
     }
-    double xi[3], g[30];
-    if (et == ET_H8) {
+    double xi[3], g[81];
+    if (et == ET_H8 || et == ET_Q27) {
         xi[0] = xi[1] = xi[2] = 0.0;
     } else {
         xi[0] = xi[1] = xi[2] = 0.25;
@@ -183,7 +191,7 @@ __global__ void k_precompute_affine(int et, int npe, int n_tiles, const int32_t 
     const bool ok = det > 0.0;
     for (int r = 0; r < 9; ++r) aff[(t * 10 + r) * 32 + lane] = ok ? R(Ji[r]) : R(0);
     aff[(t * 10 + 9) * 32 + lane] = ok ? R(det) : R(0);
-    evol[idx] = ok ? R(det * (et == ET_H8 ? 8.0 : 1.0 / 6.0)) : R(0);
+    evol[idx] = ok ? R(det * ((et == ET_H8 || et == ET_Q27) ? 8.0 : 1.0 / 6.0)) : R(0);
     if (!ok) atomicAdd(status + ST_INVERTED, 1);
     if (!element_is_affine(et, npe, Xe)) atomicAnd(affine_flag, 0);
 }

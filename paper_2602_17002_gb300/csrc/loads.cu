@@ -28,7 +28,7 @@ __global__ void k_point_loads(int et, int npe, int elem_base, int n_elem, const 
         atomicAdd(bad, 1);
         return;
     }
-    double sh[10];
+    double sh[27];
     shape_fn(et, x, sh);
     for (int i = 0; i < npe; ++i) {
         const int64_t nd = conn[(int64_t)e * npe + i];
@@ -38,8 +38,8 @@ __global__ void k_point_loads(int et, int npe, int elem_base, int n_elem, const 
 
 // Parent face `face` as (a, b) -> xi with tangents: tetrahedra, face k opposite
 // barycentric vertex k, L_p = 1 - a - b, L_q = a, L_r = b for the other
-// vertices p < q < r; bricks, face 2 d + s at xi_d = +-1 with (a, b) the other
-// coordinates in increasing order.
+// vertices p < q < r; bricks (H8, Q27), face 2 d + s at xi_d = +-1 with (a, b)
+// the other coordinates in increasing order.
 __device__ void face_point(int et, int face, double a, double b, double xi[3], double ta[3], double tb[3])
 {
     if (et == ET_T4 || et == ET_T10) {
@@ -91,7 +91,8 @@ __device__ void gauss4(int i, double &x, double &w)
 
 // One thread per (loaded face, face quadrature point): triangle faces take the
 // 4 x 4 collapsed Gauss rule (a, b) = (u, (1 - u) v) with weight (1 - u) on the
-// unit triangle, quadrilateral faces the 3 x 3 Gauss rule; dA0 = |X_a x X_b|.
+// unit triangle, quadrilateral faces the 3 x 3 Gauss rule (exact for the
+// biquadratic Q27 face functions on a flat face); dA0 = |X_a x X_b|.
 __global__ void k_surface_traction(int et, int npe, int elem_base, int n_elem, const int32_t *__restrict__ conn,
                                    const double *__restrict__ X, int n, const int32_t *__restrict__ elem,
                                    const int32_t *__restrict__ face, const double *__restrict__ t0, double *f,
@@ -124,7 +125,7 @@ __global__ void k_surface_traction(int et, int npe, int elem_base, int n_elem, c
         gauss3(q % 3, b, wb);
         w = wa * wb;
     }
-    double xi[3], ta[3], tb[3], sh[10], g[30];
+    double xi[3], ta[3], tb[3], sh[27], g[81];
     face_point(et, fc, a, b, xi, ta, tb);
     shape_fn(et, xi, sh);
     parent_grad(et, xi, g);
@@ -185,7 +186,7 @@ extern "C" tlfe_status tlfe_surface_traction(tlfe_mesh *m, int32_t n, const int3
     cudaStream_t s = (cudaStream_t)stream;
     for (const BlockStore &B : m->blocks) {
         if (B.n_elem == 0) continue;
-        const int nqf = (B.et == ET_H8) ? 9 : 16;
+        const int nqf = (B.et == ET_T4 || B.et == ET_T10) ? 16 : 9;
         const int64_t work = (int64_t)n * nqf;
         k_surface_traction<<<(unsigned)((work + 127) / 128), 128, 0, s>>>(B.et, B.npe, B.elem_base, B.n_elem,
                                                                           B.d_conn, m->d_X, n, elem, face, t0, f,

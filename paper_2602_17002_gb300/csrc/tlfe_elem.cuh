@@ -6,6 +6,10 @@
 //   T10: quadratic barycentric tetrahedron (App. A.1): corners L_k (2 L_k - 1),
 //        edge nodes 4 L_a L_b on edges (1,2) (2,3) (1,3) (1,4) (2,4) (3,4)
 //   H8 : trilinear brick on {-1,1}^3, node i + 2j + 4k (tensor order of App. A.2)
+//   Q27: triquadratic brick (App. A, Q27 element): node i + 3j + 9k at
+//        (xi, eta, zeta) = (i - 1, j - 1, k - 1), shape function
+//        l_i(xi) l_j(eta) l_k(zeta) with the 1D quadratic Lagrange polynomials
+//        l_0 = x (x - 1)/2, l_1 = 1 - x^2, l_2 = x (x + 1)/2 on the nodes -1, 0, 1
 #pragma once
 
 #include "tlfe_math.cuh"
@@ -21,9 +25,31 @@ __host__ __device__ inline void t10_edge(int e, int &a, int &b)
     b = B[e];
 }
 
+// 1D quadratic Lagrange polynomials on the nodes -1, 0, 1 and their derivatives
+__host__ __device__ inline void lagrange2(double x, double l[3], double dl[3])
+{
+    l[0] = 0.5 * x * (x - 1.0);
+    l[1] = (1.0 - x) * (1.0 + x);
+    l[2] = 0.5 * x * (x + 1.0);
+    dl[0] = x - 0.5;
+    dl[1] = -2.0 * x;
+    dl[2] = x + 0.5;
+}
+
 // d s_i / d xi_k in double, g[i*3 + k]
 __host__ __device__ inline void parent_grad(int et, const double xi[3], double *g)
 {
+    if (et == ET_Q27) {
+        double l[3][3], dl[3][3];
+        for (int d = 0; d < 3; ++d) lagrange2(xi[d], l[d], dl[d]);
+        for (int n = 0; n < 27; ++n) {
+            const int a = n % 3, b = (n / 3) % 3, c = n / 9;
+            g[n * 3 + 0] = dl[0][a] * l[1][b] * l[2][c];
+            g[n * 3 + 1] = l[0][a] * dl[1][b] * l[2][c];
+            g[n * 3 + 2] = l[0][a] * l[1][b] * dl[2][c];
+        }
+        return;
+    }
     if (et == ET_T4 || et == ET_T10) {
         const double L[4] = {1.0 - xi[0] - xi[1] - xi[2], xi[0], xi[1], xi[2]};
         // dL_k / dxi: L1 -> (-1,-1,-1), L2 -> e1, L3 -> e2, L4 -> e3
@@ -60,6 +86,12 @@ __host__ __device__ inline void parent_grad(int et, const double xi[3], double *
 // 4 L_a L_b; H8 trilinear tensor products
 __host__ __device__ inline void shape_fn(int et, const double xi[3], double *sh)
 {
+    if (et == ET_Q27) {
+        double l[3][3], dl[3][3];
+        for (int d = 0; d < 3; ++d) lagrange2(xi[d], l[d], dl[d]);
+        for (int n = 0; n < 27; ++n) sh[n] = l[0][n % 3] * l[1][(n / 3) % 3] * l[2][n / 9];
+        return;
+    }
     if (et == ET_T4 || et == ET_T10) {
         const double L[4] = {1.0 - xi[0] - xi[1] - xi[2], xi[0], xi[1], xi[2]};
         if (et == ET_T4) {
@@ -85,8 +117,9 @@ __host__ __device__ inline void shape_fn(int et, const double xi[3], double *sh)
 // Tetrahedra (parent volume 1/6): 1-point centroid; 4-point degree-2 rule with
 // barycentric (a, b, b, b), a = (5 + 3 sqrt5)/20, b = (5 - sqrt5)/20, w = 1/24;
 // 5-point degree-3 rule: centroid with w = -2/15, and (1/2, 1/6, 1/6, 1/6)
-// permutations with w = 3/40. Bricks: 2x2x2 Gauss-Legendre (+-1/sqrt3, w = 1),
-// or the 1-point centre rule (w = 8).
+// permutations with w = 3/40. H8: 2x2x2 Gauss-Legendre (+-1/sqrt3, w = 1), or
+// the 1-point centre rule (w = 8). Q27: 3x3x3 Gauss-Legendre (0, +-sqrt(3/5);
+// 8/9, 5/9 per direction), point q = i + 3j + 9k.
 __host__ __device__ inline bool quad_point(int et, int nq, int q, double xi[3], double &w)
 {
     if (et == ET_T4 || et == ET_T10) {
@@ -130,6 +163,16 @@ __host__ __device__ inline bool quad_point(int et, int nq, int q, double xi[3], 
             return true;
         }
     }
+    if (et == ET_Q27 && nq == 27) {
+        const int id[3] = {q % 3, (q / 3) % 3, q / 9};
+        const double r = sqrt(0.6);
+        w = 1.0;
+        for (int d = 0; d < 3; ++d) {
+            xi[d] = id[d] == 0 ? -r : (id[d] == 1 ? 0.0 : r);
+            w *= id[d] == 1 ? 8.0 / 9.0 : 5.0 / 9.0;
+        }
+        return true;
+    }
     return false;
 }
 
@@ -141,8 +184,14 @@ __host__ __device__ inline bool quad_point(int et, int nq, int q, double xi[3], 
 //        edge holds the corner, else -6; edge-edge 32 (same edge), 16 (one
 //        shared corner), 8 (disjoint)
 //   H8 (parallelepiped): prod_d (1/3 if the d-th tensor indices agree, else 1/6)
+//   Q27 (parallelepiped): prod_d m[i_d][j_d] with the normalised 1D quadratic
+//        mass m = [[4, 2, -1], [2, 16, 2], [-1, 2, 4]] / 30
 __host__ __device__ inline double mass_hat(int et, int i, int j)
 {
+    if (et == ET_Q27) {
+        const double m1[3][3] = {{4.0, 2.0, -1.0}, {2.0, 16.0, 2.0}, {-1.0, 2.0, 4.0}};
+        return m1[i % 3][j % 3] * m1[(i / 3) % 3][(j / 3) % 3] * m1[i / 9][j / 9] / 27000.0;
+    }
     if (et == ET_T4) return (i == j ? 2.0 : 1.0) / 20.0;
     if (et == ET_H8) {
         double m = 1.0;
@@ -258,9 +307,43 @@ template <int NQ, typename R> struct ParentGrad<ET_H8, NQ, R> {
     }
 };
 
+// Q27 (parallelepiped): dS_n/dxi_k = l'_{n_k}(xi_k) prod_{j != k} l_{n_j}(xi_j)
+// with the tensor indices (n_0, n_1, n_2) = (n % 3, (n / 3) % 3, n / 9); the
+// point of the 3x3x3 Gauss rule is held as the nine values l_a(xi_j) and the
+// nine derivatives l'_a(xi_j).
+template <int NQ, typename R> struct ParentGrad<ET_Q27, NQ, R> {
+    R l[3][3], dl[3][3];
+    __device__ __forceinline__ void at(int q)
+    {
+        const R r = R(0.77459666924148337704);  // sqrt(3/5)
+        const int id[3] = {q % 3, (q / 3) % 3, q / 9};
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const R x = id[j] == 0 ? -r : (id[j] == 1 ? R(0) : r);
+            l[j][0] = R(0.5) * x * (x - R(1));
+            l[j][1] = (R(1) - x) * (R(1) + x);
+            l[j][2] = R(0.5) * x * (x + R(1));
+            dl[j][0] = x - R(0.5);
+            dl[j][1] = R(-2) * x;
+            dl[j][2] = x + R(0.5);
+        }
+    }
+    __host__ __device__ static constexpr bool nz(int, int) { return true; }
+    __device__ __forceinline__ R g(int n, int k) const
+    {
+        const int a[3] = {n % 3, (n / 3) % 3, n / 9};
+        const int j1 = (k + 1) % 3, j2 = (k + 2) % 3;
+        return dl[k][a[k]] * (l[j1][a[j1]] * l[j2][a[j2]]);
+    }
+};
+
 // quadrature weight w_q of point q (parent measure), matching quad_point
 template <int ET, int NQ, typename R> __device__ __forceinline__ R quad_weight(int q)
 {
+    if constexpr (ET == ET_Q27) {
+        const R w1 = R(5.0 / 9.0), w0 = R(8.0 / 9.0);
+        return ((q % 3) == 1 ? w0 : w1) * (((q / 3) % 3) == 1 ? w0 : w1) * ((q / 9) == 1 ? w0 : w1);
+    }
     if constexpr (ET == ET_H8) return NQ == 8 ? R(1) : R(8);
     if constexpr (NQ == 5) return q == 0 ? R(-2.0 / 15.0) : R(3.0 / 40.0);
     if constexpr (NQ == 4) return R(1.0 / 24.0);

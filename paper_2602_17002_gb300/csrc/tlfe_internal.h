@@ -93,7 +93,7 @@ cudaError_t launch_color_round(int n_elem, int npe, const int32_t *conn, const i
                                int *overflow, cudaStream_t s);
 
 // ---- constraint primitives (constraints.cu) ----
-constexpr int CON_MAXN = 10;  // nodes of the largest element
+constexpr int CON_MAXN = 27;  // nodes of the largest element (Q27)
 constexpr int CON_MAXB = 16;  // element blocks a constraint set can refer to
 struct ConBlocks {            // block table passed to the kernels by value
     int n;

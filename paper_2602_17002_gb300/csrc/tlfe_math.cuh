@@ -23,17 +23,18 @@
 
 namespace tlfe {
 
-enum { ET_T4 = 0, ET_T10 = 1, ET_H8 = 2 };
+enum { ET_T4 = 0, ET_T10 = 1, ET_H8 = 2, ET_Q27 = 3 };
 enum { MODEL_SVK = 0, MODEL_NH = 1, MODEL_MR = 2 };
 
 template <int ET> struct Elem;
 template <> struct Elem<ET_T4> { static constexpr int NPE = 4; };
 template <> struct Elem<ET_T10> { static constexpr int NPE = 10; };
 template <> struct Elem<ET_H8> { static constexpr int NPE = 8; };
+template <> struct Elem<ET_Q27> { static constexpr int NPE = 27; };
 
 __host__ __device__ inline int nodes_per_elem(int et)
 {
-    return et == ET_T4 ? 4 : (et == ET_T10 ? 10 : (et == ET_H8 ? 8 : -1));
+    return et == ET_T4 ? 4 : (et == ET_T10 ? 10 : (et == ET_H8 ? 8 : (et == ET_Q27 ? 27 : -1)));
 }
 
 // Material record as the kernels see it (Lame constants, Kelvin-Voigt

@@ -17,7 +17,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libtlfe.so")
 
-T4, T10, H8 = 0, 1, 2
+T4, T10, H8, Q27 = 0, 1, 2, 3
 SVK, NEOHOOKE, MOONEY_RIVLIN = 0, 1, 2
 FP64, FP32 = 0, 1
 SCATTER_ATOMIC, SCATTER_COLOR = 0, 1

@@ -12,5 +12,5 @@ from .mesh import (  # noqa: F401
 )
 from .workloads import (  # noqa: F401
     block_t10_svk, cantilever_beam, batch_bodies, diff_block, newton_beams,
-    small_beam, lame_from_young, split_bodies,
+    small_beam, lame_from_young, split_bodies, q27_beam,
 )

@@ -18,10 +18,10 @@ from typing import List, Optional
 
 import numpy as np
 
-from .mesh import T4, T10, H8, NODES_PER_ELEM, box_mesh
+from .mesh import T4, T10, H8, Q27, NODES_PER_ELEM, box_mesh
 
 SVK, NEOHOOKE = 0, 1
-DEFAULT_NQ = {T4: 1, T10: 5, H8: 8}
+DEFAULT_NQ = {T4: 1, T10: 5, H8: 8, Q27: 27}
 
 
 def lame_from_young(E: float, nu: float):
@@ -130,6 +130,35 @@ def cantilever_beam(cells=(200, 20, 20), cell_edge: float = 0.05, seed: int = 2,
         blocks=[Block(T10, nq, m.conn, m.body)],
         model=np.array([NEOHOOKE], np.int32),
         params=np.array([[3.8e6, 5.8e6, damping, 0.0, 1000.0]]),
+        u=u, udot=udot, v=v)
+
+
+def q27_beam(cells=(8, 2, 2), cell_edge: float = 0.05, seed: int = 6, vseed: int = 16,
+             pseed: int = 26, model: int = 1, damping: float = 1e3, mu01: float = 0.0,
+             curve: float = 0.0) -> Workload:
+    """Cantilever of Q27 bricks (one brick per cell, 3x3x3 Gauss points):
+    neo-Hookean (model 1) or another law code, mu=3.8e6 lam=5.8e6, Kelvin-Voigt
+    mu_v = damping. The same bending field as cantilever_beam (tip deflection
+    5 % of the length) plus U(+-0.1 % of the cell edge) noise; velocities
+    N(0, 0.01^2) m/s; probe v ~ N(0, 1). curve > 0 moves every node of the
+    reference by U(+-curve * cell_edge), making the bricks non-affine."""
+    nx, ny, nz = cells
+    size = (nx * cell_edge, ny * cell_edge, nz * cell_edge)
+    m = box_mesh(Q27, cells, size)
+    rng = np.random.default_rng(seed)
+    X = m.X.copy()
+    if curve > 0:
+        X += _uniform_noise(rng, X.shape, curve * cell_edge)
+    u = _bending_field(X, size[0], 0.05 * size[0], rng, 0.001 * cell_edge)
+    udot = 0.01 * np.random.default_rng(vseed).standard_normal(X.shape)
+    v = np.random.default_rng(pseed).standard_normal(X.shape)
+    params = np.array([[3.8e6, 5.8e6, damping, 0.0, 1000.0]])
+    if mu01 != 0.0:
+        params = np.concatenate([params, [[mu01]]], axis=1)
+    return Workload(
+        name=f"beam{nx}x{ny}x{nz}_Q27", X=X,
+        blocks=[Block(Q27, 27, m.conn, m.body)],
+        model=np.array([model], np.int32), params=params,
         u=u, udot=udot, v=v)
 
 
