@@ -25,6 +25,9 @@ Other workloads (one JSON line each):
   --workload diff    1 M-element T10 block with per-element (mu, lambda):
                      loss 1/2 |f - f_target|^2, forward + adjoint through the
                      torch.autograd.Function.
+  --workload q27     the beam's 200 x 20 x 20 cells as 80,000 Q27 triquadratic
+                     bricks (the same 674,081 nodes), 3 x 3 x 3 Gauss points:
+                     the same step as the default workload.
 
 L2: inputs and streamed element data are larger than L2 (129 MB) in every
 workload, and a 512 MiB memset flushes L2 before every timed step, outside
@@ -60,11 +63,15 @@ WORKLOADS = {
              "E ~ logU[1e6, 1e9], FP32, graph-captured force + K v",
     "diff": "1 m^3 block 55^3 cells -> 998,250 T10, Q=5, neo-Hookean per-element (mu, lambda) + Kelvin-Voigt, "
             "loss 1/2 |f - f_target|^2, forward + VJP, FP32",
+    "q27": "cantilever beam 10x1x1 m, 200x20x20 cells -> 80k Q27 (674,081 nodes), Q=27 (3x3x3 Gauss), "
+           "neo-Hookean + Kelvin-Voigt, FP32",
 }
 GRAVITY = (0.0, 0.0, -9.81)
-# Algorithmic FP32 FLOPs per quadrature point of the T10 Q5 neo-Hookean +
-# Kelvin-Voigt kernels (2 FFMA + FADD + FMUL, counted by ncu on the affine path)
-FLOP_PER_QP = {"force": 852, "matvec": 1589, "vjp": 1786}
+# Algorithmic FP32 FLOPs per quadrature point of the neo-Hookean + Kelvin-Voigt
+# kernels on the affine path (2 FFMA + FADD + FMUL, counted by ncu): T10 Q5 for
+# the beam workload, Q27 for the q27 workload
+FLOP_PER_QP = {"beam": {"force": 852, "matvec": 1589, "vjp": 1786},
+               "q27": {"force": None, "matvec": None, "vjp": None}}
 # FP32 FMA roof: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz (maximum SM clock)
 ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
@@ -256,10 +263,12 @@ def cpu_sample(workload, wl, n_sample):
         val = 1.0 / (dt * wl.n_elem / b.n_elem)
         return val, dt, 1, (f"oracle Newton step of the smallest body ({b.n_elem} T10), extrapolated per element "
                             f"to {wl.n_elem}, {dt:.1f} s")
+    if workload == "q27":   # a Q27 brick costs the oracle about 40 T10 elements (27 points x 27 nodes)
+        n_sample = max(64, n_sample // 40)
     sub = _sub_first(wl, n_sample)
     blk = sub.blocks[0]
     t0 = time.perf_counter()
-    if workload == "beam":
+    if workload in ("beam", "q27"):
         oracle.internal_force(sub)
         oracle.operator_apply(sub, wl.v, a_K=1.0, a_C=1.0)
         oracle.vjp(sub, wl.v)
@@ -274,7 +283,7 @@ def cpu_sample(workload, wl, n_sample):
         what = "force + adjoint"
     dt = time.perf_counter() - t0
     return (blk.n_elem * blk.nq / dt, dt, 1,
-            f"first {blk.n_elem} of {wl.n_elem} elements ({'T4 T10 H8'.split()[blk.etype]} block), {what}, "
+            f"first {blk.n_elem} of {wl.n_elem} elements ({'T4 T10 H8 Q27'.split()[blk.etype]} block), {what}, "
             f"{dt:.1f} s")
 
 
@@ -282,6 +291,8 @@ def build_workload(workload):
     import synth
     if workload == "beam":
         return synth.cantilever_beam()
+    if workload == "q27":
+        return synth.q27_beam(cells=(200, 20, 20))
     if workload == "newton":
         return synth.newton_beams(64)
     if workload == "batch":
@@ -328,12 +339,15 @@ def run_reference(args):
 # workload: beam (default)
 # ---------------------------------------------------------------------------
 
-def run_beam(args, rank, world):
+def run_beam(args, rank, world, workload="beam"):
     import numpy as np
     import torch
 
     from paper_2602_17002_gb300 import tlfe
-    wl = build_workload("beam")
+    wl = build_workload(workload)
+    tag = workload
+    fpq = FLOP_PER_QP[workload]
+    pre = "" if workload == "beam" else workload + "_"   # traffic keys of the committed ncu summary
     L = tlfe.load()
     flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
@@ -385,7 +399,7 @@ def run_beam(args, rank, world):
     # the isoparametric (slab) path on the same mesh: per-point h_i streamed
     ms_, ud_, v_, outs_, gth_ = make(tlfe.FP32, tlfe.PATH_SLAB)
     info_s = ms_.info
-    per_s = time_step(ms_, ud_, v_, outs_, gth_, max(3, args.steps // 2), "beam_slab_timed")
+    per_s = time_step(ms_, ud_, v_, outs_, gth_, max(3, args.steps // 2), tag + "_slab_timed")
     ms_.close()
     ks = per_s.mean(axis=0)
     bytes_s = [info_s["stream_bytes_force"], info_s["stream_bytes_matvec"], info_s["stream_bytes_vjp"]]
@@ -394,7 +408,8 @@ def run_beam(args, rank, world):
     slab = {"kernels_ms": {n: float(t) for n, t in zip(names, ks)}, "ms_per_step": float(per_s.sum(axis=1).mean()),
             "kernels_gbs": {n: b / (t * 1e-3) / 1e9 for n, b, t in zip(names, bytes_s, ks)},
             "roofline": {"bound": "hbm", "achieved": ach_s, "peak": peak, "unit": "GB/s", "frac": ach_s / peak,
-                         "traffic": ncu_traffic("slab_" + names[js]), "kernel": names[js], "peak_source": peak_kind,
+                         "traffic": ncu_traffic(pre + "slab_" + names[js]), "kernel": names[js],
+                         "peak_source": peak_kind,
                          "algorithmic_bytes": bytes_s[js]}}
 
     # the default (affine) path: the timed step, launch schedules autotuned first
@@ -409,7 +424,7 @@ def run_beam(args, rank, world):
     barrier(world)
     torch.cuda.synchronize()
     with ClockSampler(torch.cuda.current_device()) as clk:
-        evs = timed_steps(step, args.steps, flush, stream, 4, "beam_affine_timed")
+        evs = timed_steps(step, args.steps, flush, stream, 4, tag + "_affine_timed")
     barrier(world)
     st = mesh.sync()
     per = np.array([[evs[k][j].elapsed_time(evs[k][j + 1]) for j in range(3)] for k in range(args.steps)])
@@ -421,13 +436,14 @@ def run_beam(args, rank, world):
     # roofline of the dominant kernel: FP32 FMA roof (bound), HBM fraction beside it
     bytes_alg = [info["stream_bytes_force"], info["stream_bytes_matvec"], info["stream_bytes_vjp"]]
     j = int(np.argmax(kern_ms))
-    flops = FLOP_PER_QP[names[j]] * units
-    achieved = flops / (kern_ms[j] * 1e-3) / 1e12
+    flops = fpq[names[j]] * units if fpq[names[j]] else None
+    achieved = flops / (kern_ms[j] * 1e-3) / 1e12 if flops else None
     hbm = bytes_alg[j] / (kern_ms[j] * 1e-3) / 1e9
     roof = {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / ALU_PEAK_TFLOPS, "traffic": ncu_traffic(names[j]), "kernel": names[j],
+            "frac": achieved / ALU_PEAK_TFLOPS if achieved else None,
+            "traffic": ncu_traffic(pre + names[j]), "kernel": names[j],
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz",
-            "algorithmic_flops": flops, "flop_per_qp": FLOP_PER_QP[names[j]],
+            "algorithmic_flops": flops, "flop_per_qp": fpq[names[j]],
             "algorithmic_bytes": bytes_alg[j], "hbm_achieved_gbs": hbm, "hbm_peak_gbs": peak,
             "hbm_frac": hbm / peak, "hbm_peak_source": peak_kind}
 
@@ -467,19 +483,20 @@ def run_beam(args, rank, world):
 
     # the same step with FP64 element arithmetic (the plain path)
     m64, ud64, v64, outs64, gth64 = make(tlfe.FP64)
-    per64 = time_step(m64, ud64, v64, outs64, gth64, max(3, args.steps // 4), "beam_fp64_timed")
+    per64 = time_step(m64, ud64, v64, outs64, gth64, max(3, args.steps // 4), tag + "_fp64_timed")
     ms64 = float(per64.sum(axis=1).mean())
     st64 = m64.sync()
     m64.close()
 
-    line = base_line(args, world, "beam", value, UNIT, step_ms, "f32",
+    line = base_line(args, world, workload, value, UNIT, step_ms, "f32",
                      step="internal force + K_t v + C v + VJP (u, udot, mu, lambda)", n_elem=wl.n_elem,
                      n_nodes=wl.n_nodes, n_qp=units, schedule="autotuned (tlfe_autotune) before the warm-up")
     line.update({
         "kernels_ms": {n: float(t) for n, t in zip(names, kern_ms)},
         "kernels_gbs": {n: b / (t * 1e-3) / 1e9 for n, b, t in zip(names, bytes_alg, kern_ms)},
         "force_qps": units / (kern_ms[0] * 1e-3),
-        "kernels_tflops": {n: FLOP_PER_QP[n] * units / (t * 1e-3) / 1e12 for n, t in zip(names, kern_ms)},
+        "kernels_tflops": {n: fpq[n] * units / (t * 1e-3) / 1e12 if fpq[n] else None
+                           for n, t in zip(names, kern_ms)},
         "roofline": roof,
         "element_path": "affine (Sec. 6 affine case: J^-1 and det J per element)",
         "slab_path": slab,
@@ -770,7 +787,8 @@ def main():
         return run_reference(args)
 
     rank, world, _ = dist_setup()
-    run = {"beam": run_beam, "newton": run_newton, "batch": run_batch, "diff": run_diff}[args.workload]
+    run = {"beam": run_beam, "newton": run_newton, "batch": run_batch, "diff": run_diff,
+           "q27": lambda a, r, w: run_beam(a, r, w, "q27")}[args.workload]
     line, wl = run(args, rank, world)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         if args.workload == "diff":

@@ -185,6 +185,129 @@ template <typename R> static Mat<R> to_mat(const tlfe_material &s)
     return m;
 }
 
+// 21 bits of x, y, z interleaved into one 63-bit Morton key
+static uint64_t morton3(uint32_t x, uint32_t y, uint32_t z)
+{
+    auto spread = [](uint64_t v) {
+        v &= 0x1FFFFF;
+        v = (v | v << 32) & 0x1F00000000FFFFull;
+        v = (v | v << 16) & 0x1F0000FF0000FFull;
+        v = (v | v << 8) & 0x100F00F00F00F00Full;
+        v = (v | v << 4) & 0x10C30C30C30C30C3ull;
+        v = (v | v << 2) & 0x1249249249249249ull;
+        return v;
+    };
+    return spread(x) | spread(y) << 1 | spread(z) << 2;
+}
+
+// unique nodes of the tiles of 32 consecutive elements of `order`: the sum
+// over the tiles plus the tile count times the largest (the gather work, and
+// the node patch that sets the shared memory of every warp)
+static int64_t tile_node_cost(const tlfe_mesh_desc *d, const tlfe_block &b, const std::vector<int32_t> &order)
+{
+    const int npe = nodes_per_elem(b.type);
+    std::vector<int32_t> stamp(d->n_nodes, -1);
+    int64_t total = 0, umax = 0, u = 0;
+    for (size_t k = 0; k < order.size(); ++k) {
+        const int tile = (int)(k / TILE);
+        if (k % TILE == 0) u = 0;
+        for (int i = 0; i < npe; ++i) {
+            const int32_t n = b.conn[(int64_t)order[k] * npe + i];
+            if (stamp[n] != tile) {
+                stamp[n] = tile;
+                ++total;
+                ++u;
+            }
+        }
+        umax = std::max(umax, u);
+    }
+    return total + (int64_t)((order.size() + TILE - 1) / TILE) * umax;
+}
+
+// Element order of the tiles. Candidates: the input order, and orders by
+// body, then along a Morton curve of the element centroids, then by element
+// index. The curve quantises each body's centroids on a cubic grid of step
+// f h, h = (bounding-box volume / elements)^(1/3), for f = 1 (one brick per
+// cell), 5^(1/3) and 6^(1/3) (five or six tetrahedra per cell) and 2, so that
+// on a structured mesh the grid cells are the mesh cells and 32 consecutive
+// elements form a compact block of cells; bodies that overlap in space are
+// not interleaved. A curve order replaces the input order only when it cuts
+// tile_node_cost by 15 % or more: on the beam of Kuhn tetrahedra numbered
+// cell by cell its 5 % saving measured slower than the input order, while on
+// bricks numbered row by row it saves about 30 % and measured 25 % faster.
+static std::vector<int32_t> locality_order(const tlfe_mesh_desc *d, const tlfe_block &b)
+{
+    const int npe = nodes_per_elem(b.type);
+    const int n = b.n_elem;
+    std::vector<int32_t> best(n);
+    std::iota(best.begin(), best.end(), 0);
+    if (n <= TILE) return best;
+    const int64_t ident_cost = tile_node_cost(d, b, best);
+    int64_t best_cost = ident_cost;
+    // per body: node bounding box and element count
+    auto body_of = [&](int e) { return b.body ? b.body[e] : 0; };
+    int nb = 0;
+    for (int e = 0; e < n; ++e) nb = std::max(nb, body_of(e) + 1);
+    std::vector<double> lo((size_t)nb * 3, INFINITY), hi((size_t)nb * 3, -INFINITY);
+    std::vector<int64_t> cnt(nb, 0);
+    std::vector<double> c((size_t)n * 3, 0.0);
+    for (int e = 0; e < n; ++e) {
+        const int bo = body_of(e);
+        ++cnt[bo];
+        for (int a = 0; a < 3; ++a) {
+            double sum = 0.0;
+            for (int i = 0; i < npe; ++i) {
+                const double x = d->X_ref[(size_t)b.conn[(int64_t)e * npe + i] * 3 + a];
+                sum += x;
+                lo[(size_t)bo * 3 + a] = std::min(lo[(size_t)bo * 3 + a], x);
+                hi[(size_t)bo * 3 + a] = std::max(hi[(size_t)bo * 3 + a], x);
+            }
+            c[(size_t)e * 3 + a] = sum / npe;
+        }
+    }
+    std::vector<double> h0(nb, 0.0);
+    for (int bo = 0; bo < nb; ++bo) {
+        if (cnt[bo] == 0) continue;
+        double vol = 1.0, ext = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            vol *= hi[(size_t)bo * 3 + a] - lo[(size_t)bo * 3 + a];
+            ext = std::max(ext, hi[(size_t)bo * 3 + a] - lo[(size_t)bo * 3 + a]);
+        }
+        h0[bo] = vol > 0.0 ? std::cbrt(vol / (double)cnt[bo]) : ext / std::cbrt((double)cnt[bo]);
+    }
+    struct Key {
+        int32_t body;
+        uint64_t code;
+        int32_t e;
+        bool operator<(const Key &o) const
+        {
+            return body != o.body ? body < o.body : (code != o.code ? code < o.code : e < o.e);
+        }
+    };
+    std::vector<Key> key(n);
+    std::vector<int32_t> order(n);
+    for (double f : {1.0, std::cbrt(5.0), std::cbrt(6.0), 2.0}) {
+        for (int e = 0; e < n; ++e) {
+            const int bo = body_of(e);
+            const double h = f * h0[bo];
+            uint32_t q[3] = {0, 0, 0};
+            for (int a = 0; a < 3; ++a) {
+                const double v = h > 0.0 ? std::floor((c[(size_t)e * 3 + a] - lo[(size_t)bo * 3 + a]) / h) : 0.0;
+                q[a] = (uint32_t)std::min(std::max(v, 0.0), (double)((1u << 21) - 1));
+            }
+            key[e] = {bo, morton3(q[0], q[1], q[2]), e};
+        }
+        std::sort(key.begin(), key.end());
+        for (int e = 0; e < n; ++e) order[e] = key[e].e;
+        const int64_t cost = tile_node_cost(d, b, order);
+        if (cost < best_cost && cost <= ident_cost - ident_cost * 15 / 100) {
+            best_cost = cost;
+            best = order;
+        }
+    }
+    return best;
+}
+
 static tlfe_status build_block(tlfe_mesh *m, const tlfe_mesh_desc *d, int bi, int elem_base, cudaStream_t s)
 {
     const tlfe_block &b = d->blocks[bi];
@@ -196,9 +319,9 @@ static tlfe_status build_block(tlfe_mesh *m, const tlfe_mesh_desc *d, int bi, in
     B.elem_base = elem_base;
     const int npe = B.npe;
 
-    // element order inside the layout: identity, or grouped by colour
-    std::vector<int32_t> order(b.n_elem);
-    std::iota(order.begin(), order.end(), 0);
+    // element order inside the layout: the locality order, then (colour
+    // mode) grouped by colour, keeping that order inside each colour
+    std::vector<int32_t> order = locality_order(d, b);
     std::vector<int> color_of;
     B.n_colors = 0;
     if (d->scatter == TLFE_SCATTER_COLOR && b.n_elem > 0) {

@@ -308,33 +308,48 @@ template <int NQ, typename R> struct ParentGrad<ET_H8, NQ, R> {
 };
 
 // Q27 (parallelepiped): dS_n/dxi_k = l'_{n_k}(xi_k) prod_{j != k} l_{n_j}(xi_j)
-// with the tensor indices (n_0, n_1, n_2) = (n % 3, (n / 3) % 3, n / 9); the
-// point of the 3x3x3 Gauss rule is held as the nine values l_a(xi_j) and the
-// nine derivatives l'_a(xi_j).
-template <int NQ, typename R> struct ParentGrad<ET_Q27, NQ, R> {
-    R l[3][3], dl[3][3];
-    __device__ __forceinline__ void at(int q)
-    {
-        const R r = R(0.77459666924148337704);  // sqrt(3/5)
-        const int id[3] = {q % 3, (q / 3) % 3, q / 9};
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            const R x = id[j] == 0 ? -r : (id[j] == 1 ? R(0) : r);
-            l[j][0] = R(0.5) * x * (x - R(1));
-            l[j][1] = (R(1) - x) * (R(1) + x);
-            l[j][2] = R(0.5) * x * (x + R(1));
-            dl[j][0] = x - R(0.5);
-            dl[j][1] = R(-2) * x;
-            dl[j][2] = x + R(0.5);
+// with the tensor indices (n_0, n_1, n_2) = (n % 3, (n / 3) % 3, n / 9). The 81
+// entries at each of the 27 Gauss points are tabulated once, at compile time,
+// in constant memory: every lane of a warp reads the same point's row, a
+// broadcast, in place of 108 multiplications per use.
+template <typename R> struct Q27Table {
+    R g[27][81];
+};
+__host__ __device__ constexpr double q27_l(int a, double x)
+{
+    return a == 0 ? 0.5 * x * (x - 1.0) : (a == 1 ? (1.0 - x) * (1.0 + x) : 0.5 * x * (x + 1.0));
+}
+__host__ __device__ constexpr double q27_dl(int a, double x) { return a == 0 ? x - 0.5 : (a == 1 ? -2.0 * x : x + 0.5); }
+template <typename R> constexpr Q27Table<R> make_q27_table()
+{
+    Q27Table<R> t{};
+    const double r = 0.77459666924148337704;  // sqrt(3/5)
+    for (int q = 0; q < 27; ++q) {
+        const int qi[3] = {q % 3, (q / 3) % 3, q / 9};
+        double x[3] = {0, 0, 0};
+        for (int j = 0; j < 3; ++j) x[j] = qi[j] == 0 ? -r : (qi[j] == 1 ? 0.0 : r);
+        for (int n = 0; n < 27; ++n) {
+            const int a[3] = {n % 3, (n / 3) % 3, n / 9};
+            for (int k = 0; k < 3; ++k) {
+                double v = 1.0;
+                for (int j = 0; j < 3; ++j) v *= j == k ? q27_dl(a[j], x[j]) : q27_l(a[j], x[j]);
+                t.g[q][n * 3 + k] = R(v);
+            }
         }
     }
-    __host__ __device__ static constexpr bool nz(int, int) { return true; }
-    __device__ __forceinline__ R g(int n, int k) const
+    return t;
+}
+static __constant__ Q27Table<float> kQ27F = make_q27_table<float>();
+static __constant__ Q27Table<double> kQ27D = make_q27_table<double>();
+template <int NQ, typename R> struct ParentGrad<ET_Q27, NQ, R> {
+    const R *row;
+    __device__ __forceinline__ void at(int q)
     {
-        const int a[3] = {n % 3, (n / 3) % 3, n / 9};
-        const int j1 = (k + 1) % 3, j2 = (k + 2) % 3;
-        return dl[k][a[k]] * (l[j1][a[j1]] * l[j2][a[j2]]);
+        if constexpr (sizeof(R) == 4) row = kQ27F.g[q];
+        else row = kQ27D.g[q];
     }
+    __host__ __device__ static constexpr bool nz(int, int) { return true; }
+    __device__ __forceinline__ R g(int n, int k) const { return row[n * 3 + k]; }
 };
 
 // quadrature weight w_q of point q (parent measure), matching quad_point
