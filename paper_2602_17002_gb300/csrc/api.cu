@@ -718,6 +718,8 @@ template <typename R> static void block_params(tlfe_mesh *m, const BlockStore &B
     p.meta_bytes = B.meta_bytes;
     p.umaxp = B.meta_umaxp;
     p.eid = B.d_eid;
+    p.conn = B.d_conn;
+    p.elem_base = B.elem_base;
     p.slab = (const R *)B.d_slab;
     p.aff = B.use_affine ? (const R *)B.d_aff : nullptr;
     p.emat = B.d_emat;
@@ -762,8 +764,10 @@ static tlfe_status launch_block(tlfe_mesh *m, const BlockStore &B, KParams<R> p,
         const int tiles = p.tile_end - p.tile_begin;
         if (tiles <= 0) continue;
         p.rmw_scatter = m->scatter == TLFE_SCATTER_COLOR ? 1 : 0;
-        // one warp per tile at a time, persistent over the resident warps
-        const int warps = std::min(tiles, std::max(1, ls.resident / ls.wpb) * ls.wpb * m->n_sm);
+        // one warp per tile (per element on the warp-per-element path) at a
+        // time, persistent over the resident warps
+        const int units = wpe_path(B.et, B.use_affine) ? tiles * TILE : tiles;
+        const int warps = std::min(units, std::max(1, ls.resident / ls.wpb) * ls.wpb * m->n_sm);
         const int grid = std::max(1, (warps + ls.wpb - 1) / ls.wpb);
         cudaError_t e = launch_op<OP, R>(B.et, B.nq, p, grid, ls.wpb, s);
         if (e != cudaSuccess) return cuda_fail(e, "element kernel launch");

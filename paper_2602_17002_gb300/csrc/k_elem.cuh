@@ -732,6 +732,12 @@ __global__ void __launch_bounds__(128, min_ctas<ET, R, OP, AFF>()) k_elem(const 
     }
 }
 
+}  // namespace tlfe
+
+#include "k_wpe.cuh"
+
+namespace tlfe {
+
 template <int OP, typename R, bool AFF, int MAT> static void (*kernel_for_(int et, int nq))(const KParams<R>)
 {
     if (et == ET_T4 && nq == 1) return k_elem<ET_T4, 1, R, OP, AFF, MAT>;
@@ -758,6 +764,7 @@ template <int OP, typename R, bool AFF> static void (*kernel_for_m(int et, int n
 }
 template <int OP, typename R> static void (*kernel_for(int et, int nq, bool aff, int mat))(const KParams<R>)
 {
+    if (wpe_path(et, aff)) return wpe_kernel_for<OP, R>(mat);
     return aff ? kernel_for_m<OP, R, true>(et, nq, mat) : kernel_for_m<OP, R, false>(et, nq, mat);
 }
 
@@ -771,6 +778,7 @@ template <int OP, typename R, bool AFF> size_t smem_for_(int et, int umax, int m
 }
 template <int OP, typename R> size_t smem_for(int et, int umax, int meta_bytes, int wpb, bool aff)
 {
+    if (wpe_path(et, aff)) return wpe_smem_bytes<R>(wpb);
     return aff ? smem_for_<OP, R, true>(et, umax, meta_bytes, wpb) : smem_for_<OP, R, false>(et, umax, meta_bytes, wpb);
 }
 

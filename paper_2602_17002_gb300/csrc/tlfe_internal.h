@@ -20,6 +20,9 @@ enum { MAT_ANY = 0, MAT_NH = 1, MAT_NH_KV = 2, MAT_SVK = 3, MAT_SVK_KV = 4 };
 
 constexpr int TILE = 32;     // elements per tile = lanes of one warp
 constexpr int AFF_ROWS = 10;  // affine record rows per tile: J^{-1} (9, row-major), det J
+// affine Q27 blocks run the warp-per-element kernels (one warp per element,
+// lanes over points then nodes); every other block runs one thread per element
+__host__ __device__ inline bool wpe_path(int et, bool aff) { return et == ET_Q27 && aff; }
 
 // values per node held in a warp's shared-memory patch: inputs (u, udot
 // [, v or cotangent]) then outputs (one array, two for the adjoint)
@@ -41,6 +44,8 @@ template <typename R> struct KParams {
     const unsigned char *meta;
     int meta_bytes, umaxp;
     const int32_t *eid;         // [n_tiles][32] global element id, -1 for padding lanes
+    const int32_t *conn;        // [n_elem][npe] global node ids, block element order (warp-per-element path)
+    int elem_base;              // global id of the block's first element
     const R *slab;              // [n_tiles][nq][3 npe + 1][32]: h_i components, then w_q J_p
     const R *aff;               // affine path: [n_tiles][10][32] J^{-1} (row-major) and det J; nullptr = slab path
     const int32_t *emat;        // [n_tiles][32] material index, or nullptr (uniform mat0)
