@@ -71,7 +71,7 @@ GRAVITY = (0.0, 0.0, -9.81)
 # kernels on the affine path (2 FFMA + FADD + FMUL, counted by ncu): T10 Q5 for
 # the beam workload, Q27 for the q27 workload
 FLOP_PER_QP = {"beam": {"force": 852, "matvec": 1589, "vjp": 1786},
-               "q27": {"force": None, "matvec": None, "vjp": None}}
+               "q27": {"force": 1932, "matvec": 3026, "vjp": 3567}}
 # FP32 FMA roof: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz (maximum SM clock)
 ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 

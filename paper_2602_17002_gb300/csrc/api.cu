@@ -649,7 +649,10 @@ extern "C" tlfe_status tlfe_get_mesh_info(const tlfe_mesh *m, tlfe_mesh_info *in
         } else {
             eb += (int64_t)B.n_elem * (B.nq * B.npe * 3 * rs + B.nq * rs);  // slab: h_i and w J_p
         }
-        eb += (int64_t)B.n_tiles * B.meta_bytes;                        // per-tile metadata records
+        if (wpe_path(B.et, B.use_affine))   // warp per element: connectivity and slot element ids
+            eb += (int64_t)B.n_elem * B.npe * 4 + (int64_t)B.n_tiles * TILE * 4;
+        else
+            eb += (int64_t)B.n_tiles * B.meta_bytes;                    // per-tile metadata records
         if (B.d_emat) eb += (int64_t)B.n_elem * 4;
         if (B.d_elam) eb += (int64_t)B.n_elem * 2 * rs;
     }
