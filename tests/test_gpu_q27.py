@@ -156,3 +156,52 @@ def test_q27_clamped_newton_step_matches_oracle(prec):
     assert rep_ref["status"] == 0
     assert np.abs(v - v_ref).max() <= 1e-6 * np.abs(v_ref).max()
     assert np.abs(v[fixed == 1]).max() == 0.0
+
+
+def _q27_variants(kind):
+    """The Q27 beam with per-element (mu, lambda) or with several bodies of
+    different laws in one block (per-element material index)."""
+    wl = synth.q27_beam(cells=(6, 2, 2))
+    rng = np.random.default_rng(17)
+    if kind == "elam":
+        theta = np.stack([3.8e6 * np.exp(0.3 * rng.standard_normal(wl.n_elem)),
+                          5.8e6 * np.exp(0.3 * rng.standard_normal(wl.n_elem))], axis=1)
+        return Workload("q27_elam", wl.X, wl.blocks, wl.model, wl.params, u=wl.u, udot=wl.udot, v=wl.v,
+                        elem_mu_lambda=theta)
+    blk = wl.blocks[0]
+    body = (np.arange(blk.n_elem) % 3).astype(np.int32)
+    params = np.array([[3.8e6, 5.8e6, 1e3, 0.0, 1000.0], [2.0e6, 4.0e6, 0.0, 0.0, 1200.0],
+                       [5.0e6, 7.0e6, 2e3, 1e3, 800.0]])
+    return Workload("q27_mats", wl.X, [Block(Q27, 27, blk.conn, body)], np.array([1, 0, 1], np.int32), params,
+                    u=wl.u, udot=wl.udot, v=wl.v)
+
+
+@pytest.mark.parametrize("kind", ["elam", "mats"])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_q27_per_element_parameters_and_materials(prec, kind):
+    """Warp-per-element kernels with per-element (mu, lambda), and with the
+    law and damping read per element (several bodies in one block)."""
+    wl = _q27_variants(kind)
+    h = 1e-3
+    _, out = run_all(wl, prec, aM=1.0 / h, aK=h, aC=1.0)
+    check_all(wl, out, prec, aM=1.0 / h, aK=h, aC=1.0)
+
+
+def test_q27_colour_scatter_and_mass_only():
+    """Colour passes (plain read-add-write scatter) on the warp-per-element
+    path, and the operator product with a_K = a_C = 0 (mass only)."""
+    wl = synth.q27_beam(cells=(6, 3, 2))
+    tl = T()
+    mesh = tl.Mesh.from_workload(wl, precision=tl.FP32, scatter=tl.SCATTER_COLOR, color_seed=7)
+    assert mesh.info["n_colors"] >= 8 and mesh.info["n_affine_blocks"] == 1
+    dt = mesh.torch_dtype
+    u, ud, v = _cuda(wl.u, torch.float64), _cuda(wl.udot, dt), _cuda(wl.v, dt)
+    f1 = mesh.internal_force(u, ud).cpu().numpy()
+    f2 = mesh.internal_force(u, ud).cpu().numpy()
+    assert np.array_equal(f1.view(np.uint32), f2.view(np.uint32))
+    f_ref, _ = oracle.internal_force(wl)
+    assert np.abs(f1 - f_ref).max() <= 2e-5 * np.abs(f_ref).max()
+    y = mesh.tangent_matvec(u, ud, v, 1.0, 0.0, 0.0).cpu().numpy()
+    y_ref = oracle.operator_apply(wl, wl.v, a_M=1.0, a_K=0.0, a_C=0.0)
+    assert np.abs(y - y_ref).max() <= 2e-5 * np.abs(y_ref).max()
+    mesh.sync()
