@@ -235,13 +235,97 @@ def timed_steps(step, steps, flush, stream, n_ev=2, label="timed"):
 # CPU oracle samples (the cpu_baseline and the reference arm)
 # ---------------------------------------------------------------------------
 
-def _sub_first(wl, n):
+def _compact_sample(wl, n):
+    """The first n elements of block 0 as a self-contained workload holding
+    only the nodes they use (renumbered), for shipping to worker processes."""
+    import numpy as np
     from synth.workloads import Block, Workload
     blk = wl.blocks[0]
     n = min(n, blk.n_elem)
-    return Workload("sample", wl.X, [Block(blk.etype, blk.nq, blk.conn[:n], blk.body[:n])], wl.model, wl.params,
-                    u=wl.u, udot=wl.udot, v=wl.v,
+    conn = blk.conn[:n]
+    nodes, inv = np.unique(conn, return_inverse=True)
+    pick = lambda a: None if a is None else np.ascontiguousarray(a[nodes])
+    return Workload("sample", pick(wl.X), [Block(blk.etype, blk.nq, inv.reshape(conn.shape).astype(conn.dtype),
+                                                blk.body[:n])], wl.model, wl.params,
+                    u=pick(wl.u), udot=pick(wl.udot), v=pick(wl.v),
                     elem_mu_lambda=None if wl.elem_mu_lambda is None else wl.elem_mu_lambda[:n])
+
+
+_WORKER_WL = None
+
+
+def _oracle_worker_init(sub):
+    global _WORKER_WL
+    _WORKER_WL = sub
+    import oracle
+    oracle.lib()
+
+
+def _oracle_ops(workload, sub):
+    import oracle
+    if workload in ("beam", "q27"):
+        oracle.internal_force(sub)
+        oracle.operator_apply(sub, sub.v, a_K=1.0, a_C=1.0)
+        oracle.vjp(sub, sub.v)
+        return "force + closed-form K_t v + C v + adjoint"
+    if workload == "batch":
+        oracle.internal_force(sub)
+        oracle.operator_apply(sub, sub.v, a_K=1.0)
+        return "force + closed-form K v"
+    oracle.internal_force(sub)
+    oracle.vjp(sub, sub.v)
+    return "force + adjoint"
+
+
+def _oracle_worker_chunk(workload, i0, i1):
+    """One worker's share of the sample: elements [i0, i1) of its block."""
+    from synth.workloads import Block, Workload
+    wl = _WORKER_WL
+    blk = wl.blocks[0]
+    sub = Workload("chunk", wl.X, [Block(blk.etype, blk.nq, blk.conn[i0:i1], blk.body[i0:i1])], wl.model, wl.params,
+                   u=wl.u, udot=wl.udot, v=wl.v,
+                   elem_mu_lambda=None if wl.elem_mu_lambda is None else wl.elem_mu_lambda[i0:i1])
+    t0 = time.perf_counter()
+    _oracle_ops(workload, sub)
+    return time.perf_counter() - t0
+
+
+def oracle_pool(workload, wl, n_sample):
+    """Spawned worker processes (one per host core, up to 64) holding the
+    compact sample, for the all-core oracle timing; None for the Newton
+    workload (one body, not split). Spawned, not forked: the parent has
+    touched the GPU by then."""
+    if workload == "newton":
+        return None
+    import multiprocessing as mp
+    procs = max(1, min(64, os.cpu_count() or 1))
+    sub = _compact_sample(wl, _sample_size(workload, n_sample))
+    return mp.get_context("spawn").Pool(procs, initializer=_oracle_worker_init, initargs=(sub,)), procs, sub
+
+
+def _sample_size(workload, n_sample):
+    if workload == "q27":   # a Q27 brick costs the oracle about 40 T10 elements (27 points x 27 nodes)
+        return max(64, n_sample // 40)
+    return n_sample
+
+
+def cpu_sample_parallel(workload, wl, pool_info):
+    """The oracle on the same bounded sample as cpu_sample, split in equal
+    element ranges over the pool's processes; wall time from the first
+    dispatch to the last result. Returns (value, seconds, processes, text)."""
+    pool, procs, sub = pool_info
+    ne = sub.blocks[0].n_elem
+    cuts = [ne * k // procs for k in range(procs + 1)]
+    chunks = [(workload, cuts[k], cuts[k + 1]) for k in range(procs) if cuts[k + 1] > cuts[k]]
+    t0 = time.perf_counter()
+    pool.starmap(_oracle_worker_chunk, chunks, chunksize=1)
+    dt = time.perf_counter() - t0
+    blk = sub.blocks[0]
+    what = {"beam": "force + closed-form K_t v + C v + adjoint", "q27": "force + closed-form K_t v + C v + adjoint",
+            "batch": "force + closed-form K v"}.get(workload, "force + adjoint")
+    return (blk.n_elem * blk.nq / dt, dt, procs,
+            f"first {blk.n_elem} of {wl.n_elem} elements ({'T4 T10 H8 Q27'.split()[blk.etype]} block), {what}, "
+            f"split over {len(chunks)} processes, {dt:.2f} s wall")
 
 
 def cpu_sample(workload, wl, n_sample):
@@ -263,24 +347,10 @@ def cpu_sample(workload, wl, n_sample):
         val = 1.0 / (dt * wl.n_elem / b.n_elem)
         return val, dt, 1, (f"oracle Newton step of the smallest body ({b.n_elem} T10), extrapolated per element "
                             f"to {wl.n_elem}, {dt:.1f} s")
-    if workload == "q27":   # a Q27 brick costs the oracle about 40 T10 elements (27 points x 27 nodes)
-        n_sample = max(64, n_sample // 40)
-    sub = _sub_first(wl, n_sample)
+    sub = _compact_sample(wl, _sample_size(workload, n_sample))
     blk = sub.blocks[0]
     t0 = time.perf_counter()
-    if workload in ("beam", "q27"):
-        oracle.internal_force(sub)
-        oracle.operator_apply(sub, wl.v, a_K=1.0, a_C=1.0)
-        oracle.vjp(sub, wl.v)
-        what = "force + closed-form K_t v + C v + adjoint"
-    elif workload == "batch":
-        oracle.internal_force(sub)
-        oracle.operator_apply(sub, wl.v, a_K=1.0)
-        what = "force + closed-form K v"
-    else:  # diff
-        oracle.internal_force(sub)
-        oracle.vjp(sub, wl.v)
-        what = "force + adjoint"
+    what = _oracle_ops(workload, sub)
     dt = time.perf_counter() - t0
     return (blk.n_elem * blk.nq / dt, dt, 1,
             f"first {blk.n_elem} of {wl.n_elem} elements ({'T4 T10 H8 Q27'.split()[blk.etype]} block), {what}, "
@@ -314,23 +384,32 @@ def run_reference(args):
     wl = build_workload(args.workload)
     if args.workload == "diff":
         wl.v = diff_cotangent(wl)
-    if args.workload != "newton":
-        for _ in range(max(0, args.warmup)):
-            cpu_sample(args.workload, wl, max(64, args.ref_sample // 16))
+    # all host cores (spawned processes over element ranges); the Newton
+    # sample, one body, on one core
+    pool_info = oracle_pool(args.workload, wl, args.ref_sample)
+    step = ((lambda: cpu_sample_parallel(args.workload, wl, pool_info)) if pool_info
+            else (lambda: cpu_sample(args.workload, wl, args.ref_sample)))
     ts, vals = [], []
-    steps = 1 if args.workload == "newton" else args.steps
-    what = ""
-    for _ in range(steps):
-        v, dt, thr, what = cpu_sample(args.workload, wl, args.ref_sample)
-        ts.append(dt)
-        vals.append(v)
+    what, thr = "", 1
+    try:
+        if pool_info:
+            for _ in range(max(0, args.warmup)):
+                step()
+        for _ in range(1 if args.workload == "newton" else args.steps):
+            v, dt, thr, what = step()
+            ts.append(dt)
+            vals.append(v)
+    finally:
+        if pool_info:
+            pool_info[0].close()
+            pool_info[0].join()
     value = float(np.mean(vals))
     unit = "steps/s" if args.workload == "newton" else UNIT
     line = base_line(args, 1, args.workload, value, unit, float(np.mean(ts)) * 1e3, "f64")
     line.update({"impl": "reference", "n_gpus": args.gpus,
-                 "cpu_baseline": {"value": value, "unit": unit, "cores": 1, "kind": "oracle", "sample": what},
+                 "cpu_baseline": {"value": value, "unit": unit, "cores": thr, "kind": "oracle", "sample": what},
                  "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}})
-    line["config"]["parallelism"] = "host, 1 core"
+    line["config"]["parallelism"] = f"host, {thr} core{'s' if thr > 1 else ''}"
     print(json.dumps(line), flush=True)
     return 0
 
@@ -794,7 +873,19 @@ def main():
         if args.workload == "diff":
             wl.v = diff_cotangent(wl)
         val, secs, thr, what = cpu_sample(args.workload, wl, args.cpu_sample)
-        line["cpu_baseline"] = {"value": val, "unit": line["unit"], "cores": thr, "kind": "oracle", "sample": what}
+        base = {"value": val, "unit": line["unit"], "cores": thr, "kind": "oracle", "sample": what}
+        pool_info = oracle_pool(args.workload, wl, args.cpu_sample)
+        if pool_info:   # the same sample on all host cores; the one-core run beside it
+            try:
+                cpu_sample_parallel(args.workload, wl, pool_info)   # warm-up
+                pv, ps, procs, pwhat = cpu_sample_parallel(args.workload, wl, pool_info)
+            finally:
+                pool_info[0].close()
+                pool_info[0].join()
+            line["cpu_baseline"] = {"value": pv, "unit": line["unit"], "cores": procs, "kind": "oracle",
+                                    "sample": pwhat, "single_core": base}
+        else:
+            line["cpu_baseline"] = base
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

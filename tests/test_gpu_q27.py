@@ -205,3 +205,32 @@ def test_q27_colour_scatter_and_mass_only():
     y_ref = oracle.operator_apply(wl, wl.v, a_M=1.0, a_K=0.0, a_C=0.0)
     assert np.abs(y - y_ref).max() <= 2e-5 * np.abs(y_ref).max()
     mesh.sync()
+
+
+def test_q27_full_size_bench_configuration():
+    """The 80k-brick Q27 beam the benchmark times, with its schedules
+    autotuned as the benchmark does: force, K v + C v and the adjoint at
+    sampled nodes (a node's value depends only on the bricks holding it),
+    on the warp-per-element path (FP32, FP64) and the slab path (FP32)."""
+    from test_gpu_parity import _subset, relerr
+    wl = synth.q27_beam(cells=(200, 20, 20))
+    rng = np.random.default_rng(9)
+    ks = rng.choice(wl.n_nodes, 120, replace=False)
+    sub = _subset(wl, np.isin(wl.blocks[0].conn, ks).any(axis=1))
+    f_ref, bad = oracle.internal_force(sub)
+    assert bad == 0
+    y_ref = oracle.operator_apply(sub, wl.v, a_K=1.0, a_C=1.0)
+    g_ref, gd_ref, _ = oracle.vjp(sub, wl.v)
+    tl = T()
+    for prec, tol, path in ((1, 2e-5, 0), (1, 2e-5, 1), (0, 1e-12, 0)):
+        mesh = tl.Mesh.from_workload(wl, precision=prec, element_path=path)
+        dt = mesh.torch_dtype
+        u, ud, v = _cuda(wl.u, torch.float64), _cuda(wl.udot, dt), _cuda(wl.v, dt)
+        mesh.autotune(u, ud, v)
+        f = mesh.internal_force(u, ud)
+        y = mesh.tangent_matvec(u, ud, v, 0.0, 1.0, 1.0)
+        gu, gud, _ = mesh.vjp(u, ud, v)
+        mesh.sync()
+        for got, ref in ((f, f_ref), (y, y_ref), (gu, g_ref), (gud, gd_ref)):
+            assert relerr(got.double().cpu().numpy()[ks], ref[ks]) <= tol
+        mesh.close()
