@@ -86,7 +86,8 @@ def lib():
                 "orc_constraint_jt": [i32, i32, P, P, P, P, P, P],
                 "orc_constraint_j": [i32, i32, P, P, P, P, P, P],
                 "orc_newton_step_alm": [i32, i32, i32, P, i32, P, P, P, P, f64, P, P, f64, f64, i32, i32,
-                                        i32, P, f64, f64, i32, P, P, P, P, P],
+                                        i32, P, f64, f64, i32, i32, P, P, P, P, P],
+                "orc_constraint_row_weights": [i32, i32, P, P, P, P],
             }.items():
                 fn = getattr(L, name)
                 fn.argtypes = args
@@ -397,9 +398,21 @@ def constraint_j(wl, cons, v, u=None):
     return out
 
 
+def constraint_row_weights(wl, cons):
+    """Row weights of Eq. row_weights (DP1 rows 1/sqrt(|a0|^2 + |b0|^2) at the
+    reference configuration, all other rows 1)."""
+    blk = wl.blocks[0]
+    w = np.zeros(len(cons))
+    _check(lib().orc_constraint_row_weights(blk.etype, len(cons), _p(cons), _p(blk.conn), _p(_f64(wl.X)), _p(w)),
+           "constraint_row_weights")
+    return w
+
+
 def newton_step_alm(wl, u_n, v_n, h, gravity, cons, rho, lam=None, fixed=None, newton_rtol=1e-8, cg_rtol=1e-4,
-                    max_newton=20, max_cg=2000, alm_tol=1e-10, max_outer=50):
-    """Augmented-Lagrangian backward-Euler step (Sec. 7): returns (v, lam, report)."""
+                    max_newton=20, max_cg=2000, alm_tol=1e-10, max_outer=50, row_norm=True):
+    """Augmented-Lagrangian backward-Euler step (Sec. 7) on the row-normalised
+    constraints (Eqs. row_weights, rev_normalized; row_norm=False: raw rows):
+    returns (v, lam, report), lam the multipliers of the rows used."""
     assert len(wl.blocks) == 1
     blk = wl.blocks[0]
     m = block_materials(wl, 0)
@@ -413,6 +426,7 @@ def newton_step_alm(wl, u_n, v_n, h, gravity, cons, rho, lam=None, fixed=None, n
                                      _p(m), _p(_f64(u_n)), _p(_f64(v_n)), C.c_double(h), _p(_f64(gravity)), _p(fx),
                                      C.c_double(newton_rtol), C.c_double(cg_rtol), int(max_newton), int(max_cg),
                                      len(cons), _p(cons), C.c_double(rho), C.c_double(alm_tol), int(max_outer),
-                                     _p(lam), _p(v), C.byref(rep), C.byref(outer), C.byref(cn)), "newton_step_alm")
+                                     int(bool(row_norm)), _p(lam), _p(v), C.byref(rep), C.byref(outer), C.byref(cn)),
+           "newton_step_alm")
     return v, lam, {"newton_iters": rep.newton_iters, "cg_iters": rep.cg_iters, "status": rep.status,
                     "rel_residual": rep.rel_residual, "outer_iters": outer.value, "c_norm": cn.value}

@@ -1302,6 +1302,29 @@ int orc_constraint_jt(int type, int n_cons, const orc_constraint *cons, const in
     return 0;
 }
 
+/* Row weights of the constraint set (Eq. row_weights), constant, from the
+ * reference configuration q = X: a DP1 row gets w = 1 / sqrt(|a0|^2 + |b0|^2)
+ * with its directions a0 = r_Q - r_P and b0 = r_T - r_R there; CD rows (and
+ * the DIST and DP2 rows, which the equation does not scale) get 1. A DP1 row
+ * whose reference directions both vanish keeps 1. */
+int orc_constraint_row_weights(int type, int n_cons, const orc_constraint *cons, const int32_t *conn,
+                               const double *X, double *w)
+{
+    for (int k = 0; k < n_cons; ++k) {
+        w[k] = 1.0;
+        if (cons[k].type != 2) continue;
+        double r[4][3], a0[3], b0[3];
+        for (int p = 0; p < 4; ++p) con_point(type, cons + k, p, conn, X, NULL, r[p]);
+        for (int q = 0; q < 3; ++q) {
+            a0[q] = r[1][q] - r[0][q];
+            b0[q] = r[3][q] - r[2][q];
+        }
+        const double s2 = dot3(a0, a0) + dot3(b0, b0);
+        if (s2 > 0.0) w[k] = 1.0 / sqrt(s2);
+    }
+    return 0;
+}
+
 /* out = C_q v */
 int orc_constraint_j(int type, int n_cons, const orc_constraint *cons, const int32_t *conn, const double *X,
                      const double *u, const double *v, double *out)
@@ -1339,10 +1362,13 @@ typedef struct {
     int n_cons;
     const orc_constraint *cons;
     const double *lam;
+    const double *wrow; /* [n_cons] row weights w_k (Eq. row_weights), or NULL for all ones */
     double rho, h;
     const double *uq;  /* q(v) - X at which C_q is evaluated */
     double *cw;        /* [n_cons] scratch */
 } step_ctx;
+
+static double row_w(const step_ctx *c, int k) { return c->wrow ? c->wrow[k] : 1.0; }
 
 static void project(const step_ctx *c, double *x)
 {
@@ -1358,8 +1384,9 @@ static double norm2(const double *x, size_t N)
     return sqrt(s);
 }
 
-/* g(v) = 1/h M (v - v_n) + f_int(q(v), v) - f_ff + h C_q^T (lam + rho c)
- * with q(v) = q_n + h v (Eqs. step_map_velocity_level and residual, f_ext = 0);
+/* g(v) = 1/h M (v - v_n) + f_int(q(v), v) - f_ff + h C^_q^T (lam + rho c^)
+ * with q(v) = q_n + h v (Eqs. step_map_velocity_level and residual, f_ext = 0)
+ * and the row-normalised constraints c^ = W c, C^_q = W C_q (Eq. rev_normalized);
  * clamped DOFs are projected out. */
 static int residual(const step_ctx *c, const double *u_n, const double *v_n, const double *v,
                     double h, const double *f_ff, double *u_tmp, double *dv, double *g)
@@ -1378,7 +1405,7 @@ static int residual(const step_ctx *c, const double *u_n, const double *v_n, con
     if (st2 < 0) return st2;
     if (c->n_cons > 0) {
         if (orc_constraint_eval(c->type, c->n_cons, c->cons, c->conn, c->X, u_tmp, c->cw)) return -1;
-        for (int k = 0; k < c->n_cons; ++k) c->cw[k] = h * (c->lam[k] + c->rho * c->cw[k]);
+        for (int k = 0; k < c->n_cons; ++k) c->cw[k] = h * row_w(c, k) * (c->lam[k] + c->rho * row_w(c, k) * c->cw[k]);
         if (orc_constraint_jt(c->type, c->n_cons, c->cons, c->conn, c->X, u_tmp, c->cw, g)) return -1;
     }
     project(c, g);
@@ -1399,10 +1426,10 @@ static void apply_A(const step_ctx *c, const double *x, double *y)
         }
     }
     if (c->n_cons > 0) {
-        /* Gauss-Newton constraint term h^2 rho C_q^T C_q (the curvature terms
+        /* Gauss-Newton constraint term h^2 rho C^_q^T C^_q (the curvature terms
          * h^2 sum eta_k grad^2 c_k are left out, App. B.2) */
         orc_constraint_j(c->type, c->n_cons, c->cons, c->conn, c->X, c->uq, x, c->cw);
-        for (int k = 0; k < c->n_cons; ++k) c->cw[k] *= c->h * c->h * c->rho;
+        for (int k = 0; k < c->n_cons; ++k) c->cw[k] *= c->h * c->h * c->rho * row_w(c, k) * row_w(c, k);
         orc_constraint_jt(c->type, c->n_cons, c->cons, c->conn, c->X, c->uq, c->cw, y);
     }
     project(c, y);
@@ -1417,13 +1444,13 @@ static int newton_core(int type, int nq, int n_elem, const int32_t *conn, int n_
                        const orc_material *mat, const double *u_n, const double *v_n, double h,
                        const double gravity[3], const uint8_t *fixed, double newton_rtol, double cg_rtol,
                        int max_newton, int max_cg, int n_cons, const orc_constraint *cons, const double *lam,
-                       double rho, double *g_ref_io, double *v_out, orc_report *rep)
+                       const double *wrow, double rho, double *g_ref_io, double *v_out, orc_report *rep)
 {
     const int n = orc_nodes_per_elem(type);
     if (n < 0 || h <= 0.0) return -1;
     const int NE = 3 * n;
     const size_t N = (size_t)n_nodes * 3;
-    step_ctx c = {type, nq, n_elem, n, n_nodes, conn, X, mat, fixed, NULL, n_cons, cons, lam, rho, h, NULL, NULL};
+    step_ctx c = {type, nq, n_elem, n, n_nodes, conn, X, mat, fixed, NULL, n_cons, cons, lam, wrow, rho, h, NULL, NULL};
     double *cw = malloc(sizeof(double) * (n_cons > 0 ? n_cons : 1));
     c.cw = cw;
     c.A = malloc(sizeof(double) * (size_t)n_elem * NE * NE);
@@ -1473,17 +1500,18 @@ static int newton_core(int type, int nq, int n_elem, const int32_t *conn, int n_
             for (int q = 0; q < NE; ++q) D[(size_t)ce[q / 3] * 3 + q % 3] += Ae[(size_t)q * NE + q];
         }
         if (n_cons > 0) {
-            /* diagonal of h^2 rho C_q^T C_q: sum over constraint points of (s_i dc/dr_p)^2 */
+            /* diagonal of h^2 rho C^_q^T C^_q: sum over constraint points of (w_k s_i dc/dr_p)^2 */
             double gp[4][3], cv, sh[ORC_MAXN];
             for (int k = 0; k < n_cons; ++k) {
                 con_eval(type, cons + k, conn, X, ut, &cv, gp);
+                const double wk2 = row_w(&c, k) * row_w(&c, k);
                 for (int pp = 0; pp < con_npoints(cons[k].type); ++pp) {
                     if (cons[k].elem[pp] < 0) continue;
                     orc_shape(type, cons[k].xi[pp], sh);
                     const int32_t *ce = conn + (size_t)cons[k].elem[pp] * n;
                     for (int i = 0; i < n; ++i)
                         for (int a = 0; a < 3; ++a)
-                            D[(size_t)ce[i] * 3 + a] += h * h * rho * sh[i] * sh[i] * gp[pp][a] * gp[pp][a];
+                            D[(size_t)ce[i] * 3 + a] += h * h * rho * wk2 * sh[i] * sh[i] * gp[pp][a] * gp[pp][a];
                 }
             }
         }
@@ -1558,27 +1586,33 @@ int orc_newton_step(int type, int nq, int n_elem, const int32_t *conn, int n_nod
 {
     memcpy(v_out, v_n, (size_t)n_nodes * 3 * sizeof(double));
     return newton_core(type, nq, n_elem, conn, n_nodes, X, mat, u_n, v_n, h, gravity, fixed, newton_rtol, cg_rtol,
-                       max_newton, max_cg, 0, NULL, NULL, 0.0, NULL, v_out, rep);
+                       max_newton, max_cg, 0, NULL, NULL, NULL, 0.0, NULL, v_out, rep);
 }
 
 /* Augmented-Lagrangian step (Sec. 7, Eq. alm_multiplier_update): alternate the
- * inner Newton solve of g(v, lam) = 0 with lam += rho c(q(v)) until
- * ||c(q(v))||_2 <= alm_tol or max_outer updates; lam is updated in place.
- * Reports the outer iterations and ||c||. */
+ * inner Newton solve of g(v, lam) = 0 with lam += rho c^(q(v)) until
+ * ||c^(q(v))||_2 <= alm_tol or max_outer updates; lam is updated in place.
+ * With row_norm, c^ = W c holds the row-normalised constraints of Eqs.
+ * row_weights and rev_normalized (lam are their multipliers); without it,
+ * W = I. Reports the outer iterations and ||c^||. */
 int orc_newton_step_alm(int type, int nq, int n_elem, const int32_t *conn, int n_nodes, const double *X,
                         const orc_material *mat, const double *u_n, const double *v_n, double h,
                         const double gravity[3], const uint8_t *fixed, double newton_rtol, double cg_rtol,
                         int max_newton, int max_cg, int n_cons, const orc_constraint *cons, double rho,
-                        double alm_tol, int max_outer, double *lam, double *v_out, orc_report *rep,
+                        double alm_tol, int max_outer, int row_norm, double *lam, double *v_out, orc_report *rep,
                         int *outer_iters, double *c_norm)
 {
     const size_t N = (size_t)n_nodes * 3;
-    double *uq = malloc(N * sizeof(double)), *cv = malloc(sizeof(double) * (n_cons > 0 ? n_cons : 1));
-    if (!uq || !cv) {
+    double *uq = malloc(N * sizeof(double)), *cv = malloc(sizeof(double) * (n_cons > 0 ? n_cons : 1)),
+           *wr = malloc(sizeof(double) * (n_cons > 0 ? n_cons : 1));
+    if (!uq || !cv || !wr) {
         free(uq);
         free(cv);
+        free(wr);
         return -2;
     }
+    for (int j = 0; j < n_cons; ++j) wr[j] = 1.0;
+    if (row_norm) orc_constraint_row_weights(type, n_cons, cons, conn, X, wr);
     memcpy(v_out, v_n, N * sizeof(double));
     int ret = 0, k = 0;
     double g_ref = 0.0; /* inner solves stop relative to the first residual of the step */
@@ -1586,7 +1620,7 @@ int orc_newton_step_alm(int type, int nq, int n_elem, const int32_t *conn, int n
     rep->newton_iters = rep->cg_iters = 0;
     for (;;) {
         ret = newton_core(type, nq, n_elem, conn, n_nodes, X, mat, u_n, v_n, h, gravity, fixed, newton_rtol,
-                          cg_rtol, max_newton, max_cg, n_cons, cons, lam, rho, &g_ref, v_out, &r1);
+                          cg_rtol, max_newton, max_cg, n_cons, cons, lam, wr, rho, &g_ref, v_out, &r1);
         if (ret < 0) break;
         rep->newton_iters += r1.newton_iters;
         rep->cg_iters += r1.cg_iters;
@@ -1594,6 +1628,7 @@ int orc_newton_step_alm(int type, int nq, int n_elem, const int32_t *conn, int n
         rep->rel_residual = r1.rel_residual;
         for (size_t q = 0; q < N; ++q) uq[q] = u_n[q] + h * v_out[q];
         orc_constraint_eval(type, n_cons, cons, conn, X, uq, cv);
+        for (int j = 0; j < n_cons; ++j) cv[j] *= wr[j];
         *c_norm = norm2(cv, (size_t)n_cons);
         if (*c_norm <= alm_tol || k >= max_outer) break;
         for (int j = 0; j < n_cons; ++j) lam[j] += rho * cv[j];
@@ -1603,6 +1638,7 @@ int orc_newton_step_alm(int type, int nq, int n_elem, const int32_t *conn, int n
     if (ret >= 0 && *c_norm > alm_tol) rep->status = 5;
     free(uq);
     free(cv);
+    free(wr);
     return ret;
 }
 

@@ -125,8 +125,11 @@ int orc_newton_step_alm(int type, int nq, int n_elem, const int32_t *conn, int n
                         const orc_material *mat, const double *u_n, const double *v_n, double h,
                         const double gravity[3], const uint8_t *fixed, double newton_rtol, double cg_rtol,
                         int max_newton, int max_cg, int n_cons, const orc_constraint *cons, double rho,
-                        double alm_tol, int max_outer, double *lam, double *v_out, orc_report *rep,
-                        int *outer_iters, double *c_norm);
+                        double alm_tol, int max_outer, int row_norm, double *lam, double *v_out,
+                        orc_report *rep, int *outer_iters, double *c_norm);
+/* row weights of Eq. row_weights at the reference configuration */
+int orc_constraint_row_weights(int type, int n_cons, const orc_constraint *cons, const int32_t *conn,
+                               const double *X, double *w);
 
 int orc_newton_step(int type, int nq, int n_elem, const int32_t *conn, int n_nodes,
                     const double *X, const orc_material *mat, const double *u_n,

@@ -903,3 +903,92 @@ def test_alm_clamp_by_coordinate_differences_reproduces_the_projected_clamp():
     assert np.abs(v - v_proj).max() <= 1e-7 * np.abs(v_proj).max()
     # the multipliers carry the support reactions: C_q^T lam h balances the load at the clamp
     assert np.abs(lam).max() > 0
+
+
+def test_row_weights_closed_form():
+    """Eq. row_weights at nodes (point evaluation returns the node): a DP1
+    row gets 1 / sqrt(|a0|^2 + |b0|^2), every other row 1."""
+    from synth.workloads import Block, Workload
+    m = synth.box_mesh(T4, (1, 1, 1), (0.3, 0.7, 1.1))
+    wl = Workload("w", m.X, [Block(T4, 1, m.conn, np.zeros(m.n_elem, np.int32))], np.array([1], np.int32),
+                  np.array([[MU, LAM, 0.0, 0.0, 1000.0]]), u=np.zeros_like(m.X))
+    c0, X = m.conn[0], m.X
+    node_xi = [[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]]
+    cons = oracle.constraints([
+        {"type": oracle.CD, "elem": [0, 0], "xi": [node_xi[0], node_xi[1]], "d": (1, 0, 0), "f": 0.0},
+        {"type": oracle.DIST, "elem": [0, 0], "xi": [node_xi[0], node_xi[2]], "f": 0.5},
+        {"type": oracle.DP1, "elem": [0, 0, 0, 0], "xi": node_xi, "f": 0.0},
+        {"type": oracle.DP2, "elem": [0, 0, 0, 0], "xi": node_xi, "f": 0.0},
+    ])
+    w = oracle.constraint_row_weights(wl, cons)
+    a0, b0 = X[c0[1]] - X[c0[0]], X[c0[3]] - X[c0[2]]
+    assert w[0] == 1.0 and w[1] == 1.0 and w[3] == 1.0
+    assert abs(w[2] - 1.0 / np.sqrt(a0 @ a0 + b0 @ b0)) < 1e-15
+
+
+def _revolute_problem(delta):
+    """Two T10 beams along x: body 0 clamped at x = 0, body 1 beside it (y
+    offset) and free; a revolute-type joint at their far ends: three CD rows
+    between coincident-in-x/z points, and two DP1 rows keeping body 1's
+    x-fibre perpendicular to body 0's y- and z-fibres (fibres of length
+    delta)."""
+    from synth.workloads import Block, Workload
+    m1 = synth.box_mesh(T10, (4, 1, 1), (0.2, 0.05, 0.05))
+    m2 = synth.box_mesh(T10, (4, 1, 1), (0.2, 0.05, 0.05), origin=(0.2, 0.0, 0.0))
+    m = synth.concat_meshes([m1, m2])
+    wl = Workload("rev", m.X, [Block(T10, 5, m.conn, m.body)], np.array([1, 1], np.int32),
+                  np.array([[MU, LAM, 0.0, 0.0, 1000.0]] * 2), u=np.zeros_like(m.X))
+    fixed = (np.abs(m.X[:, 0]) < 1e-12).astype(np.uint8)
+    conn = m.conn
+
+    def locate(body, p):
+        """(element, parent xi) of physical point p inside a body's elements."""
+        for e in np.nonzero(m.body == body)[0]:
+            Xc = m.X[conn[e, :4]]
+            J = np.stack([Xc[1] - Xc[0], Xc[2] - Xc[0], Xc[3] - Xc[0]], axis=1)
+            xi = np.linalg.solve(J, p - Xc[0])
+            if xi.min() >= -1e-12 and xi.sum() <= 1 + 1e-12:
+                return int(e), xi
+        raise AssertionError("point outside the body")
+    j = np.array([0.2, 0.025, 0.025])      # the joint: the shared end face centre
+    p0, p1 = locate(0, j - [0.01, 0, 0]), locate(1, j + [0.01, 0, 0])
+    items = []
+    for d in np.eye(3):
+        items.append({"type": oracle.CD, "elem": [p0[0], p1[0]], "xi": [p0[1], p1[1]], "d": tuple(d),
+                      "f": float(d @ np.array([0.02, 0.0, 0.0]))})
+    c0 = j - [0.01, 0, 0]
+    for fib in (np.array([0, 1.0, 0]), np.array([0, 0, 1.0])):
+        P, Q = locate(0, c0 - 0.5 * delta * fib), locate(0, c0 + 0.5 * delta * fib)
+        R, T = locate(1, j + [0.01 - 0.5 * delta, 0, 0]), locate(1, j + [0.01 + 0.5 * delta, 0, 0])
+        items.append({"type": oracle.DP1, "elem": [P[0], Q[0], R[0], T[0]], "xi": [P[1], Q[1], R[1], T[1]],
+                      "f": 0.0})
+    return wl, fixed, oracle.constraints(items)
+
+
+def test_row_normalised_alm_converges_to_a_penalty_independent_solution():
+    """A revolute-type joint with 2 cm DP1 fibres (Eqs. row_weights,
+    rev_normalized). With the row weights (about 1 / (sqrt(2) delta) on the
+    DP1 rows) the augmented-Lagrangian step converges for two penalties rho
+    and reaches the same velocities and multipliers: the constrained solution
+    does not depend on rho. With raw rows, the same settings stall above the
+    tolerance: the scale mismatch the weights remove."""
+    delta = 0.02
+    wl, fixed, cons = _revolute_problem(delta)
+    w = oracle.constraint_row_weights(wl, cons)
+    assert np.allclose(w[:3], 1.0) and np.allclose(w[3:], 1.0 / (np.sqrt(2.0) * delta), rtol=1e-12)
+    g = np.array([0.0, 0.0, -9.81])
+    z = np.zeros_like(wl.X)
+    kw = dict(fixed=fixed, newton_rtol=1e-10, cg_rtol=1e-10, max_newton=30, max_cg=5000, max_outer=40, alm_tol=1e-10)
+    runs = [oracle.newton_step_alm(wl, z, z, 1e-3, g, cons, rho=rho, row_norm=True, **kw) for rho in (1e8, 1e9)]
+    for v, lam, r in runs:
+        assert r["status"] == 0 and r["c_norm"] <= 1e-10
+        assert np.abs(oracle.constraint_eval(wl, cons, 1e-3 * v)).max() <= 1e-10
+    # each run stops at ||c^|| <= alm_tol: a position residual of alm_tol over
+    # one step of h bounds the velocity difference by alm_tol / h; the
+    # multipliers agree to the inner Newton tolerance
+    (v1, lam1, _), (v2, lam2, _) = runs
+    assert np.abs(v1 - v2).max() <= kw["alm_tol"] / 1e-3
+    assert np.abs(lam1 - lam2).max() <= 1e-4 * np.abs(lam1).max()
+    _, _, r_raw = oracle.newton_step_alm(wl, z, z, 1e-3, g, cons, rho=1e8, row_norm=False,
+                                         **dict(kw, alm_tol=1e-10 / w.max()))
+    assert r_raw["status"] != 0 and r_raw["outer_iters"] == 40
