@@ -303,6 +303,11 @@ tlfe_status tlfe_vjp(tlfe_mesh *mesh, const void *u_dev, const void *udot_dev, c
  * out), alternate with lambda += rho c(q(v)) (Eq. alm_multiplier_update) until
  * ||c|| <= alm_tol or max_outer updates; the Newton solves after the first
  * start from the previous v and stop relative to the step's first residual.
+ * The step works on row-normalised constraints c^_k = w_k c_k (Eqs. row_weights,
+ * rev_normalized): w_k = 1 / sqrt(|a_0|^2 + |b_0|^2) for a DP1 row, with a_0 and
+ * b_0 its two directions in the reference configuration, and w_k = 1 for CD,
+ * DIST and DP2 rows. lambda_dev holds the multipliers of the normalised rows
+ * and c_norm is ||c^||; tlfe_constraint_eval / _j / _jt return raw rows.
  * Constraints may couple bodies: the whole mesh is then solved as one system
  * (one convergence test). */
 typedef struct {
@@ -320,9 +325,9 @@ typedef struct {
     int32_t n_cons;
     const tlfe_constraint *cons_dev;  /* device [n_cons] */
     double rho;                /* penalty rho > 0 */
-    double alm_tol;            /* stop when ||c(q(v))||_2 <= alm_tol */
+    double alm_tol;            /* stop when ||c^(q(v))||_2 <= alm_tol (normalised rows) */
     int32_t max_outer;         /* multiplier updates at most */
-    double *lambda_dev;        /* device double [n_cons], multipliers in/out */
+    double *lambda_dev;        /* device double [n_cons], multipliers of the normalised rows, in/out */
 } tlfe_step_params;
 
 typedef struct {
@@ -332,7 +337,7 @@ typedef struct {
     int32_t n_bodies_converged;
     double rel_residual;       /* max over bodies of ||g_b|| / ||g_b(v_n)|| */
     int32_t outer_iters;       /* multiplier updates (constraints) */
-    double c_norm;             /* ||c(q(v))||_2 at return (constraints) */
+    double c_norm;             /* ||c^(q(v))||_2 at return (normalised rows) */
 } tlfe_step_report;
 
 /* u_n_dev, v_n_dev, v_out_dev: device double [n_nodes][3]. report_host is

@@ -51,19 +51,13 @@ __global__ void k_con_prepare(int n, const tlfe_constraint *__restrict__ cons, C
     atomicAdd(bad, 1);  // element id outside every block
 }
 
-// c_k and dc_k/dr_p at q = X + u:
-//   CD  : c = d.(r_Q - r_P) - f,        dc/dr_P = -d, dc/dr_Q = d
-//   DIST: c = (a.a - f^2)/2, a = r_Q - r_P; dc/dr_P = -a, dc/dr_Q = a
-//   DP1 / DP2: c = a.b - f, b = r_T - r_R;  dc/dr_P = -b, dc/dr_Q = b, dc/dr_R = -a, dc/dr_T = a
-__global__ void k_con_eval(int n, const tlfe_constraint *__restrict__ cons, const double *__restrict__ sh,
-                           const int32_t *__restrict__ nd, const double *__restrict__ X, const double *__restrict__ u,
-                           double *cval, double *gp)
+// positions r_p = sum_i s_i (X_i + u_i) of the points of constraint k (u may
+// be NULL: the reference configuration); ground points at their coordinates
+__device__ void con_positions(int k, const tlfe_constraint &c, const double *__restrict__ sh,
+                              const int32_t *__restrict__ nd, const double *__restrict__ X,
+                              const double *__restrict__ u, double r[4][3])
 {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    const tlfe_constraint &c = cons[k];
     const int np = con_npoints(c.type);
-    double r[4][3];
     for (int p = 0; p < 4; ++p) {
         for (int a = 0; a < 3; ++a) r[p][a] = 0.0;
         if (p >= np) continue;
@@ -78,6 +72,23 @@ __global__ void k_con_eval(int n, const tlfe_constraint *__restrict__ cons, cons
             for (int a = 0; a < 3; ++a) r[p][a] += s[i] * (X[3 * (int64_t)d[i] + a] + (u ? u[3 * (int64_t)d[i] + a] : 0.0));
         }
     }
+}
+
+// c_k and dc_k/dr_p at q = X + u:
+//   CD  : c = d.(r_Q - r_P) - f,        dc/dr_P = -d, dc/dr_Q = d
+//   DIST: c = (a.a - f^2)/2, a = r_Q - r_P; dc/dr_P = -a, dc/dr_Q = a
+//   DP1 / DP2: c = a.b - f, b = r_T - r_R;  dc/dr_P = -b, dc/dr_Q = b, dc/dr_R = -a, dc/dr_T = a
+// times the row weight wrow[k] when wrow is given (the normalised rows of the
+// step, Eq. rev_normalized)
+__global__ void k_con_eval(int n, const tlfe_constraint *__restrict__ cons, const double *__restrict__ sh,
+                           const int32_t *__restrict__ nd, const double *__restrict__ X, const double *__restrict__ u,
+                           const double *__restrict__ wrow, double *cval, double *gp)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const tlfe_constraint &c = cons[k];
+    double r[4][3];
+    con_positions(k, c, sh, nd, X, u, r);
     double A[3], B[3], g[4][3];
     for (int a = 0; a < 3; ++a) {
         A[a] = r[1][a] - r[0][a];
@@ -106,9 +117,34 @@ __global__ void k_con_eval(int n, const tlfe_constraint *__restrict__ cons, cons
             g[3][a] = A[a];
         }
     }
-    cval[k] = val;
+    const double w = wrow ? wrow[k] : 1.0;
+    cval[k] = w * val;
     for (int p = 0; p < 4; ++p)
-        for (int a = 0; a < 3; ++a) gp[((size_t)k * 4 + p) * 3 + a] = g[p][a];
+        for (int a = 0; a < 3; ++a) gp[((size_t)k * 4 + p) * 3 + a] = w * g[p][a];
+}
+
+// Row weights of Eq. row_weights, from the reference configuration: a DP1 row
+// (c = a.b - f) gets 1 / sqrt(|a_0|^2 + |b_0|^2), with a_0 = r_Q - r_P and
+// b_0 = r_T - r_R at q = X; every other row (CD, DIST, DP2) gets 1, as does a
+// DP1 row whose reference directions both vanish.
+__global__ void k_con_row_weights(int n, const tlfe_constraint *__restrict__ cons, const double *__restrict__ sh,
+                                  const int32_t *__restrict__ nd, const double *__restrict__ X, double *wrow)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const tlfe_constraint &c = cons[k];
+    double w = 1.0;
+    if (c.type == TLFE_CON_DP1) {
+        double r[4][3];
+        con_positions(k, c, sh, nd, X, nullptr, r);
+        double s2 = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            const double A = r[1][a] - r[0][a], B = r[3][a] - r[2][a];
+            s2 += A * A + B * B;
+        }
+        if (s2 > 0.0) w = 1.0 / sqrt(s2);
+    }
+    wrow[k] = w;
 }
 
 // f += scale * C_q^T w, one thread per (constraint, point)
@@ -206,9 +242,15 @@ cudaError_t con_prepare(const ConBlocks &bt, int n, const tlfe_constraint *cons,
     return cudaGetLastError();
 }
 cudaError_t con_eval(int n, const tlfe_constraint *cons, const double *sh, const int32_t *nd, const double *X,
-                     const double *u, double *c, double *gp, cudaStream_t s)
+                     const double *u, const double *wrow, double *c, double *gp, cudaStream_t s)
 {
-    if (n > 0) k_con_eval<<<grid_of(n), 128, 0, s>>>(n, cons, sh, nd, X, u, c, gp);
+    if (n > 0) k_con_eval<<<grid_of(n), 128, 0, s>>>(n, cons, sh, nd, X, u, wrow, c, gp);
+    return cudaGetLastError();
+}
+cudaError_t con_row_weights(int n, const tlfe_constraint *cons, const double *sh, const int32_t *nd, const double *X,
+                            double *wrow, cudaStream_t s)
+{
+    if (n > 0) k_con_row_weights<<<grid_of(n), 128, 0, s>>>(n, cons, sh, nd, X, wrow);
     return cudaGetLastError();
 }
 template <typename R>
@@ -281,7 +323,7 @@ static tlfe_status con_setup(tlfe_mesh *m, int n, const tlfe_constraint *cons, c
         return fail(TLFE_E_OOM, "constraint scratch");
     cudaError_t e = cudaMemsetAsync(cs.bad, 0, sizeof(int), s);
     if (e == cudaSuccess) e = con_prepare(bt, n, cons, cs.sh, cs.nd, cs.bad, s);
-    if (e == cudaSuccess) e = con_eval(n, cons, cs.sh, cs.nd, m->d_X, u, cs.c, cs.gp, s);
+    if (e == cudaSuccess) e = con_eval(n, cons, cs.sh, cs.nd, m->d_X, u, nullptr, cs.c, cs.gp, s);
     int bad = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, cs.bad, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

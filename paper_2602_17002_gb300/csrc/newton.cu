@@ -85,6 +85,7 @@ struct NewtonState {
     double *con_sh = nullptr, *con_gp = nullptr;   // [cap][4][CON_MAXN], [cap][4][3]
     int32_t *con_nd = nullptr;                     // [cap][4][CON_MAXN]
     double *con_c = nullptr, *con_w = nullptr, *lam = nullptr;  // [cap]
+    double *con_wrow = nullptr;                    // [cap] row weights (Eq. row_weights)
     int *con_bad = nullptr;
     int *alm = nullptr;          // [2]: keep the first residual norm as reference; start from the current v
     double *g0keep = nullptr;    // [nb] residual norms of the first Newton solve of the step
@@ -556,7 +557,8 @@ static tlfe_status enq_residual(const StepCtx &x, cudaStream_t s)
     if (st != TLFE_OK) return st;
     if (ns->n_cons > 0) {
         // + h C_q^T (lambda + rho c) at q(v) (Eq. residual)
-        NCK(con_eval(ns->n_cons, ns->cons, ns->con_sh, ns->con_nd, x.m->d_X, ns->u_cur, ns->con_c, ns->con_gp, s));
+        NCK(con_eval(ns->n_cons, ns->cons, ns->con_sh, ns->con_nd, x.m->d_X, ns->u_cur, ns->con_wrow, ns->con_c,
+                     ns->con_gp, s));
         NCK(con_weights(ns->n_cons, ns->lam, ns->con_c, ns->rho, ns->h, ns->con_w, s));
         NCK(con_jt<double>(ns->n_cons, ns->con_sh, ns->con_nd, ns->con_gp, ns->con_w, 1.0, ns->y2, s));
     }
@@ -850,6 +852,7 @@ static tlfe_status ensure_constraints(NewtonState *ns, int n)
     if ((st = nalloc(ns, &ns->con_gp, (size_t)n * 12)) != TLFE_OK) return st;
     if ((st = nalloc(ns, &ns->con_c, (size_t)n)) != TLFE_OK) return st;
     if ((st = nalloc(ns, &ns->con_w, (size_t)n)) != TLFE_OK) return st;
+    if ((st = nalloc(ns, &ns->con_wrow, (size_t)n)) != TLFE_OK) return st;
     if ((st = nalloc(ns, &ns->lam, (size_t)n)) != TLFE_OK) return st;
     ns->cap_cons = n;
     ns->use_graph = -1;  // buffers moved: the graph is rebuilt
@@ -895,6 +898,9 @@ extern "C" tlfe_status tlfe_newton_step(tlfe_mesh *m, const double *u_n, const d
                             cudaMemcpyDeviceToDevice, s));
         NCK(cudaMemsetAsync(ns->con_bad, 0, sizeof(int), s));
         NCK(con_prepare(bt, n_cons, ns->cons, ns->con_sh, ns->con_nd, ns->con_bad, s));
+        // constant row weights from the reference configuration (Eq. row_weights):
+        // the step works on the normalised rows w_k c_k (Eq. rev_normalized)
+        NCK(con_row_weights(n_cons, ns->cons, ns->con_sh, ns->con_nd, m->d_X, ns->con_wrow, s));
         NCK(cudaMemcpyAsync(&bad, ns->con_bad, sizeof(int), cudaMemcpyDeviceToHost, s));
         NCK(cudaStreamSynchronize(s));
         if (bad) return fail(TLFE_E_INVALID, "constraint with a bad type or an element outside the mesh");

@@ -108,7 +108,9 @@ struct ConBlocks {            // block table passed to the kernels by value
 cudaError_t con_prepare(const ConBlocks &bt, int n, const tlfe_constraint *cons, double *sh, int32_t *nd, int *bad,
                         cudaStream_t s);
 cudaError_t con_eval(int n, const tlfe_constraint *cons, const double *sh, const int32_t *nd, const double *X,
-                     const double *u, double *c, double *gp, cudaStream_t s);
+                     const double *u, const double *wrow, double *c, double *gp, cudaStream_t s);
+cudaError_t con_row_weights(int n, const tlfe_constraint *cons, const double *sh, const int32_t *nd, const double *X,
+                            double *wrow, cudaStream_t s);
 template <typename R>
 cudaError_t con_jt(int n, const double *sh, const int32_t *nd, const double *gp, const double *w, double scale, R *f,
                    cudaStream_t s);

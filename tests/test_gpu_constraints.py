@@ -135,3 +135,36 @@ def test_alm_step_matches_oracle_and_the_projected_clamp(prec, use_graph):
     assert np.abs(v - v_proj).max() <= 1e-6 * np.abs(v_proj).max()
     lam = rep["lam"].cpu().numpy()
     assert np.abs(lam - lam_ref).max() <= 1e-4 * np.abs(lam_ref).max()
+
+
+@pytest.mark.parametrize("prec,use_graph", [(0, True), (1, True), (1, False)])
+def test_alm_revolute_joint_with_row_normalisation_matches_oracle(prec, use_graph):
+    """A revolute-type joint (three CD rows, two DP1 rows on 2 cm fibres)
+    between a clamped and a hanging beam: the step works on the row-normalised
+    constraints (Eqs. row_weights, rev_normalized) and agrees with the
+    oracle's normalised step in velocities and multipliers."""
+    import sys
+    sys.path.insert(0, os.path.dirname(__file__))
+    from test_oracle_pins import _revolute_problem
+    tl = T()
+    wl, fixed, cons = _revolute_problem(0.02)
+    g = np.array([0.0, 0.0, -9.81])
+    z = np.zeros_like(wl.X)
+    kw = dict(newton_rtol=1e-10, cg_rtol=1e-10)
+    v_ref, lam_ref, r_ref = oracle.newton_step_alm(wl, z, z, 1e-3, g, cons, rho=1e9, fixed=fixed, alm_tol=1e-10,
+                                                   max_outer=40, max_newton=30, max_cg=5000, **kw)
+    assert r_ref["status"] == 0
+    gc = np.zeros(len(cons), tl.CON_DTYPE)
+    for name in tl.CON_DTYPE.names:
+        gc[name] = cons[name]
+    mesh = tl.Mesh.from_workload(wl, precision=prec)
+    zt = torch.zeros(wl.X.shape, dtype=torch.float64, device="cuda")
+    v, rep = mesh.newton_step(zt, zt, 1e-3, gravity=g, fixed=torch.from_numpy(fixed).cuda(), max_newton=30,
+                              max_cg=5000, use_graph=use_graph, constraints=gc, rho=1e9, alm_tol=1e-10, max_outer=40,
+                              **kw)
+    assert rep["status"] == 0 and rep["c_norm"] <= 1e-10, rep
+    v = v.cpu().numpy()
+    # both stop at ||c^|| <= 1e-10: velocities agree to about alm_tol / h
+    assert np.abs(v - v_ref).max() <= 2e-10 / 1e-3
+    lam = rep["lam"].cpu().numpy()
+    assert np.abs(lam - lam_ref).max() <= 1e-4 * np.abs(lam_ref).max()
