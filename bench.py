@@ -243,19 +243,35 @@ def timed_steps(step, steps, flush, stream, n_ev=2, label="timed"):
 # ---------------------------------------------------------------------------
 
 def _compact_sample(wl, n):
-    """The first n elements of block 0 as a self-contained workload holding
-    only the nodes they use (renumbered), for shipping to worker processes."""
+    """The first n / n_blocks elements of every block as a self-contained
+    workload holding only the nodes they use (renumbered), for shipping to
+    worker processes."""
     import numpy as np
     from synth.workloads import Block, Workload
-    blk = wl.blocks[0]
-    n = min(n, blk.n_elem)
-    conn = blk.conn[:n]
-    nodes, inv = np.unique(conn, return_inverse=True)
+    nb = -(-n // len(wl.blocks))
+    parts, ml, off = [], [], 0
+    for blk in wl.blocks:
+        k = min(nb, blk.n_elem)
+        parts.append((blk, k))
+        if wl.elem_mu_lambda is not None:
+            ml.append(wl.elem_mu_lambda[off:off + k])
+        off += blk.n_elem
+    nodes = np.unique(np.concatenate([blk.conn[:k].ravel() for blk, k in parts]))
+    remap = lambda c: np.searchsorted(nodes, c).astype(c.dtype)
     pick = lambda a: None if a is None else np.ascontiguousarray(a[nodes])
-    return Workload("sample", pick(wl.X), [Block(blk.etype, blk.nq, inv.reshape(conn.shape).astype(conn.dtype),
-                                                blk.body[:n])], wl.model, wl.params,
+    return Workload("sample", pick(wl.X), [Block(blk.etype, blk.nq, remap(blk.conn[:k]), blk.body[:k])
+                                          for blk, k in parts], wl.model, wl.params,
                     u=pick(wl.u), udot=pick(wl.udot), v=pick(wl.v),
-                    elem_mu_lambda=None if wl.elem_mu_lambda is None else wl.elem_mu_lambda[:n])
+                    elem_mu_lambda=np.concatenate(ml) if ml else None)
+
+
+def _sample_text(wl, sub):
+    names = 'T4 T10 H8 Q27'.split()
+    if len(sub.blocks) == 1:
+        b = sub.blocks[0]
+        return f"first {b.n_elem} of {wl.n_elem} elements ({names[b.etype]} block)"
+    return "first " + ", ".join(f"{b.n_elem} {names[b.etype]}" for b in sub.blocks) + \
+        f" of the {len(sub.blocks)} blocks ({wl.n_elem} elements)"
 
 
 _WORKER_WL = None
@@ -284,14 +300,24 @@ def _oracle_ops(workload, sub):
     return "force + adjoint"
 
 
-def _oracle_worker_chunk(workload, i0, i1):
-    """One worker's share of the sample: elements [i0, i1) of its block."""
+def _oracle_worker_chunk(workload, k, procs):
+    """One worker's share of the sample: the k-th of procs equal element
+    ranges of every block."""
+    import numpy as np
     from synth.workloads import Block, Workload
     wl = _WORKER_WL
-    blk = wl.blocks[0]
-    sub = Workload("chunk", wl.X, [Block(blk.etype, blk.nq, blk.conn[i0:i1], blk.body[i0:i1])], wl.model, wl.params,
-                   u=wl.u, udot=wl.udot, v=wl.v,
-                   elem_mu_lambda=None if wl.elem_mu_lambda is None else wl.elem_mu_lambda[i0:i1])
+    blocks, ml, off = [], [], 0
+    for blk in wl.blocks:
+        i0, i1 = blk.n_elem * k // procs, blk.n_elem * (k + 1) // procs
+        if i1 > i0:
+            blocks.append(Block(blk.etype, blk.nq, blk.conn[i0:i1], blk.body[i0:i1]))
+            if wl.elem_mu_lambda is not None:
+                ml.append(wl.elem_mu_lambda[off + i0:off + i1])
+        off += blk.n_elem
+    if not blocks:
+        return 0.0
+    sub = Workload("chunk", wl.X, blocks, wl.model, wl.params, u=wl.u, udot=wl.udot, v=wl.v,
+                   elem_mu_lambda=np.concatenate(ml) if ml else None)
     t0 = time.perf_counter()
     _oracle_ops(workload, sub)
     return time.perf_counter() - t0
@@ -321,18 +347,14 @@ def cpu_sample_parallel(workload, wl, pool_info):
     element ranges over the pool's processes; wall time from the first
     dispatch to the last result. Returns (value, seconds, processes, text)."""
     pool, procs, sub = pool_info
-    ne = sub.blocks[0].n_elem
-    cuts = [ne * k // procs for k in range(procs + 1)]
-    chunks = [(workload, cuts[k], cuts[k + 1]) for k in range(procs) if cuts[k + 1] > cuts[k]]
+    chunks = [(workload, k, procs) for k in range(procs)]
     t0 = time.perf_counter()
     pool.starmap(_oracle_worker_chunk, chunks, chunksize=1)
     dt = time.perf_counter() - t0
-    blk = sub.blocks[0]
     what = {"beam": "force + closed-form K_t v + C v + adjoint", "q27": "force + closed-form K_t v + C v + adjoint",
             "batch": "force + closed-form K v"}.get(workload, "force + adjoint")
-    return (blk.n_elem * blk.nq / dt, dt, procs,
-            f"first {blk.n_elem} of {wl.n_elem} elements ({'T4 T10 H8 Q27'.split()[blk.etype]} block), {what}, "
-            f"split over {len(chunks)} processes, {dt:.2f} s wall")
+    nqp = sum(b.n_elem * b.nq for b in sub.blocks)
+    return (nqp / dt, dt, procs, f"{_sample_text(wl, sub)}, {what}, split over {procs} processes, {dt:.2f} s wall")
 
 
 def cpu_sample(workload, wl, n_sample):
@@ -355,13 +377,11 @@ def cpu_sample(workload, wl, n_sample):
         return val, dt, 1, (f"oracle Newton step of the smallest body ({b.n_elem} T10), extrapolated per element "
                             f"to {wl.n_elem}, {dt:.1f} s")
     sub = _compact_sample(wl, _sample_size(workload, n_sample))
-    blk = sub.blocks[0]
     t0 = time.perf_counter()
     what = _oracle_ops(workload, sub)
     dt = time.perf_counter() - t0
-    return (blk.n_elem * blk.nq / dt, dt, 1,
-            f"first {blk.n_elem} of {wl.n_elem} elements ({'T4 T10 H8 Q27'.split()[blk.etype]} block), {what}, "
-            f"{dt:.1f} s")
+    nqp = sum(b.n_elem * b.nq for b in sub.blocks)
+    return nqp / dt, dt, 1, f"{_sample_text(wl, sub)}, {what}, {dt:.1f} s"
 
 
 def build_workload(workload):
