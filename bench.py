@@ -672,6 +672,13 @@ def run_newton(args, rank, world):
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = allmax(e0.elapsed_time(e1) / args.steps, world)
+    # one more, untimed step through the host-driven loop (the same kernels,
+    # launched one by one) in its own NVTX range: kernel-level profilers do
+    # not see inside a graph with conditional nodes
+    torch.cuda.nvtx.range_push("newton_host_step")
+    mesh.newton_step(z, z, h, fixed=fx, use_graph=False, v_out=v_out, **kw)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     mesh.close()
 
     # plain path: the FP64 library, one body at a time, host-driven Newton/CG loop

@@ -64,7 +64,7 @@ struct NewtonState {
     // FP64 vectors [3N]
     double *u_n = nullptr, *v_n = nullptr, *v = nullptr, *u_cur = nullptr, *dv = nullptr, *g = nullptr,
            *fff = nullptr, *fgrav = nullptr, *y1 = nullptr, *y2 = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr,
-           *Ap = nullptr, *Dinv = nullptr, *gv = nullptr, *Dd = nullptr;
+           *Dinv = nullptr, *gv = nullptr, *Dd = nullptr;
     // mesh-precision vectors [3N]
     float *ud32 = nullptr, *p32 = nullptr, *Ap32 = nullptr, *D32 = nullptr;
     uint8_t *fixed = nullptr;  // [N], 1 = clamped (nodes outside every element included)
@@ -199,9 +199,11 @@ __global__ void k_dinv(ChunkArgs c, const R *D, const uint8_t *fixed, const doub
     }
 }
 
-// x = 0, r = -g (active bodies), z = Dinv r, p = z; partials of r.z and r.r
+// x = 0, r = -g (active bodies), z = Dinv r, p = z (and its mesh-precision
+// copy p_lo, when given); partials of r.z and r.r
+template <typename R>
 __global__ void k_cg_init(ChunkArgs c, const double *g, const double *Dinv, const double *sc, int nb, double *x,
-                          double *r, double *z, double *p, double *partials)
+                          double *r, double *z, double *p, R *p_lo, double *partials)
 {
     __shared__ double sh[32];
     const int ch = blockIdx.x;
@@ -215,6 +217,7 @@ __global__ void k_cg_init(ChunkArgs c, const double *g, const double *Dinv, cons
         r[i] = ri;
         z[i] = zi;
         p[i] = zi;
+        if (p_lo) p_lo[i] = R(zi);
         rz += ri * zi;
         rr += ri * ri;
     }
@@ -250,24 +253,16 @@ __global__ void k_cg_init_finish(int nb, const int32_t *boff, const double *part
     }
 }
 
-// mesh-precision copy of the search direction
-template <typename R> __global__ void k_to_lo(ChunkArgs c, const double *a, R *b)
-{
-    const int ch = blockIdx.x;
-    for (int i = c.start[ch] + threadIdx.x; i < c.end[ch]; i += blockDim.x) b[i] = R(a[i]);
-}
-
-// Ap (FP64, clamped DOFs zero); partial of p.Ap
+// partial of p.Ap, Ap the operator product in the mesh precision with the
+// clamped DOFs zero (k_cg_xr forms the same values again)
 template <typename R>
-__global__ void k_cg_pap(ChunkArgs c, const R *Ap_lo, const uint8_t *fixed, const double *p, double *Ap,
-                         double *partials)
+__global__ void k_cg_pap(ChunkArgs c, const R *Ap_lo, const uint8_t *fixed, const double *p, double *partials)
 {
     __shared__ double sh[32];
     const int ch = blockIdx.x;
     double acc = 0.0;
     for (int i = c.start[ch] + threadIdx.x; i < c.end[ch]; i += blockDim.x) {
         const double a = fixed[i / 3] ? 0.0 : double(Ap_lo[i]);
-        Ap[i] = a;
         acc += p[i] * a;
     }
     const double s = block_sum(acc, sh);
@@ -285,9 +280,11 @@ __global__ void k_cg_alpha(int nb, const int32_t *boff, const double *partials, 
     }
 }
 
-// x += alpha p, r -= alpha Ap, z = Dinv r; partials of r.r and r.z
-__global__ void k_cg_xr(ChunkArgs c, const double *sc, int nb, const double *p, const double *Ap,
-                        const double *Dinv, double *x, double *r, double *z, double *partials)
+// x += alpha p, r -= alpha Ap, z = Dinv r; partials of r.r and r.z. Ap is
+// read in the mesh precision with the clamped DOFs zeroed, as in k_cg_pap.
+template <typename R>
+__global__ void k_cg_xr(ChunkArgs c, const double *sc, int nb, const double *p, const R *Ap_lo,
+                        const uint8_t *fixed, const double *Dinv, double *x, double *r, double *z, double *partials)
 {
     __shared__ double sh[32];
     const int ch = blockIdx.x;
@@ -295,8 +292,9 @@ __global__ void k_cg_xr(ChunkArgs c, const double *sc, int nb, const double *p, 
     const double alpha = sc[S_ALPHA * nb + b];
     double rr = 0.0, rz = 0.0;
     for (int i = c.start[ch] + threadIdx.x; i < c.end[ch]; i += blockDim.x) {
+        const double api = fixed[i / 3] ? 0.0 : double(Ap_lo[i]);
         const double xi = x[i] + alpha * p[i];
-        const double ri = r[i] - alpha * Ap[i];
+        const double ri = r[i] - alpha * api;
         const double zi = Dinv[i] * ri;
         x[i] = xi;
         r[i] = ri;
@@ -342,14 +340,20 @@ __global__ void k_cg_beta(int nb, const int32_t *boff, const double *partials, i
     }
 }
 
-// p = z + beta p on CG-active bodies
-__global__ void k_cg_p(ChunkArgs c, const double *sc, int nb, const double *z, double *p)
+// p = z + beta p on CG-active bodies, and its mesh-precision copy p_lo when
+// given (the operator's input; unchanged bodies keep theirs)
+template <typename R>
+__global__ void k_cg_p(ChunkArgs c, const double *sc, int nb, const double *z, double *p, R *p_lo)
 {
     const int ch = blockIdx.x;
     const int b = c.body[ch];
     if (sc[S_CACT * nb + b] == 0.0) return;
     const double beta = sc[S_BETA * nb + b];
-    for (int i = c.start[ch] + threadIdx.x; i < c.end[ch]; i += blockDim.x) p[i] = z[i] + beta * p[i];
+    for (int i = c.start[ch] + threadIdx.x; i < c.end[ch]; i += blockDim.x) {
+        const double pi = z[i] + beta * p[i];
+        p[i] = pi;
+        if (p_lo) p_lo[i] = R(pi);
+    }
 }
 
 // v += x on Newton-active bodies (x is zero elsewhere); count the iteration
@@ -486,7 +490,7 @@ static tlfe_status setup_newton(tlfe_mesh *m, cudaStream_t s, int coupled)
     NA(ns->chunk_body, ns->n_chunks);
     NA(ns->body_chunk_off, ns->nb + 1);
     for (double **q : {&ns->u_n, &ns->v_n, &ns->v, &ns->u_cur, &ns->dv, &ns->g, &ns->fff, &ns->fgrav, &ns->y1, &ns->y2, &ns->x,
-                       &ns->r, &ns->z, &ns->p, &ns->Ap, &ns->Dinv, &ns->gv, &ns->Dd})
+                       &ns->r, &ns->z, &ns->p, &ns->Dinv, &ns->gv, &ns->Dd})
         NA(*q, N3);
     for (float **q : {&ns->ud32, &ns->p32, &ns->Ap32, &ns->D32}) NA(*q, N3);
     NA(ns->fixed, (size_t)N);
@@ -588,7 +592,12 @@ static tlfe_status enq_cg_init(const StepCtx &x, cudaStream_t s)
             NCK(con_diag<double>(ns->n_cons, ns->con_sh, ns->con_nd, ns->con_gp, h * h * ns->rho, ns->Dd, s));
         k_dinv<double><<<nc, RT, 0, s>>>(x.c, ns->Dd, ns->fixed, ns->sc, ns->nb, ns->Dinv);
     }
-    k_cg_init<<<nc, RT, 0, s>>>(x.c, ns->g, ns->Dinv, ns->sc, ns->nb, ns->x, ns->r, ns->z, ns->p, ns->partials);
+    if (x.m->precision == TLFE_FP32)
+        k_cg_init<float><<<nc, RT, 0, s>>>(x.c, ns->g, ns->Dinv, ns->sc, ns->nb, ns->x, ns->r, ns->z, ns->p, ns->p32,
+                                           ns->partials);
+    else
+        k_cg_init<double><<<nc, RT, 0, s>>>(x.c, ns->g, ns->Dinv, ns->sc, ns->nb, ns->x, ns->r, ns->z, ns->p, nullptr,
+                                            ns->partials);
     k_cg_init_finish<<<1, 1024, 0, s>>>(ns->nb, ns->body_chunk_off, ns->partials, nc, ns->sc, ns->it, ns->max_cg,
                                          ns->hC, x.use_handle);
     NCK(cudaGetLastError());
@@ -601,8 +610,7 @@ static tlfe_status enq_cg_iter(const StepCtx &x, cudaStream_t s)
     const int nc = ns->n_chunks;
     const double h = ns->h;
     tlfe_status st;
-    if (x.m->precision == TLFE_FP32) {
-        k_to_lo<float><<<nc, RT, 0, s>>>(x.c, ns->p, ns->p32);
+    if (x.m->precision == TLFE_FP32) {  // p32 = p in FP32, kept by k_cg_init / k_cg_p
         st = run_op<OP_MATVEC, float>(x.m, ns->u_cur, ns->ud32, ns->p32, ns->Ap32, nullptr, nullptr, 1.0 / h, h, 1.0,
                                       1, s);
         if (st != TLFE_OK) return st;
@@ -610,7 +618,7 @@ static tlfe_status enq_cg_iter(const StepCtx &x, cudaStream_t s)
             NCK(con_j(ns->n_cons, ns->con_sh, ns->con_nd, ns->con_gp, ns->p, ns->con_w, s));
             NCK(con_jt<float>(ns->n_cons, ns->con_sh, ns->con_nd, ns->con_gp, ns->con_w, h * h * ns->rho, ns->Ap32, s));
         }
-        k_cg_pap<float><<<nc, RT, 0, s>>>(x.c, ns->Ap32, ns->fixed, ns->p, ns->Ap, ns->partials);
+        k_cg_pap<float><<<nc, RT, 0, s>>>(x.c, ns->Ap32, ns->fixed, ns->p, ns->partials);
     } else {
         st = run_op<OP_MATVEC, double>(x.m, ns->u_cur, ns->v, ns->p, ns->y1, nullptr, nullptr, 1.0 / h, h, 1.0, 1, s);
         if (st != TLFE_OK) return st;
@@ -618,13 +626,21 @@ static tlfe_status enq_cg_iter(const StepCtx &x, cudaStream_t s)
             NCK(con_j(ns->n_cons, ns->con_sh, ns->con_nd, ns->con_gp, ns->p, ns->con_w, s));
             NCK(con_jt<double>(ns->n_cons, ns->con_sh, ns->con_nd, ns->con_gp, ns->con_w, h * h * ns->rho, ns->y1, s));
         }
-        k_cg_pap<double><<<nc, RT, 0, s>>>(x.c, ns->y1, ns->fixed, ns->p, ns->Ap, ns->partials);
+        k_cg_pap<double><<<nc, RT, 0, s>>>(x.c, ns->y1, ns->fixed, ns->p, ns->partials);
     }
     k_cg_alpha<<<1, 1024, 0, s>>>(ns->nb, ns->body_chunk_off, ns->partials, ns->sc);
-    k_cg_xr<<<nc, RT, 0, s>>>(x.c, ns->sc, ns->nb, ns->p, ns->Ap, ns->Dinv, ns->x, ns->r, ns->z, ns->partials);
+    if (x.m->precision == TLFE_FP32)
+        k_cg_xr<float><<<nc, RT, 0, s>>>(x.c, ns->sc, ns->nb, ns->p, ns->Ap32, ns->fixed, ns->Dinv, ns->x, ns->r, ns->z,
+                                         ns->partials);
+    else
+        k_cg_xr<double><<<nc, RT, 0, s>>>(x.c, ns->sc, ns->nb, ns->p, ns->y1, ns->fixed, ns->Dinv, ns->x, ns->r, ns->z,
+                                          ns->partials);
     k_cg_beta<<<1, 1024, 0, s>>>(ns->nb, ns->body_chunk_off, ns->partials, nc, ns->sc, ns->it, ns->crtol, ns->max_cg,
                                   ns->hC, x.use_handle);
-    k_cg_p<<<nc, RT, 0, s>>>(x.c, ns->sc, ns->nb, ns->z, ns->p);
+    if (x.m->precision == TLFE_FP32)
+        k_cg_p<float><<<nc, RT, 0, s>>>(x.c, ns->sc, ns->nb, ns->z, ns->p, ns->p32);
+    else
+        k_cg_p<double><<<nc, RT, 0, s>>>(x.c, ns->sc, ns->nb, ns->z, ns->p, nullptr);
     NCK(cudaGetLastError());
     return TLFE_OK;
 }
