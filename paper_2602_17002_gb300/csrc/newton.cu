@@ -118,27 +118,29 @@ struct ChunkArgs {
 // u_cur = u_n + h v, dv = v - v_n, and the mesh-precision copies
 template <typename R>
 __global__ void k_prep(ChunkArgs c, double h, const double *u_n, const double *v, const double *v_n, double *u_cur,
-                       double *dv, R *u_lo, R *ud_lo)
+                       double *dv, R *dv_lo, R *ud_lo)
 {
     const int ch = blockIdx.x;
     for (int i = c.start[ch] + threadIdx.x; i < c.end[ch]; i += blockDim.x) {
         const double uc = u_n[i] + h * v[i];
         u_cur[i] = uc;
         dv[i] = v[i] - v_n[i];
-        if (u_lo) u_lo[i] = R(uc);
+        if (dv_lo) dv_lo[i] = R(dv[i]);
         if (ud_lo) ud_lo[i] = R(v[i]);
     }
 }
 
-// g = y1 + y2 - f_ff on free DOFs, 0 on clamped ones; partial of g.g
-__global__ void k_residual(ChunkArgs c, const double *y1, const double *y2, const double *fff, const uint8_t *fixed,
+// g = y1 + y2 - f_ff on free DOFs, 0 on clamped ones (in FP64, y1 and y2 in
+// either precision); partial of g.g
+template <typename T>
+__global__ void k_residual(ChunkArgs c, const T *y1, const T *y2, const double *fff, const uint8_t *fixed,
                            double *g, double *partials)
 {
     __shared__ double sh[32];
     const int ch = blockIdx.x;
     double acc = 0.0;
     for (int i = c.start[ch] + threadIdx.x; i < c.end[ch]; i += blockDim.x) {
-        const double gi = fixed[i / 3] ? 0.0 : y1[i] + y2[i] - fff[i];
+        const double gi = fixed[i / 3] ? 0.0 : double(y1[i]) + double(y2[i]) - fff[i];
         g[i] = gi;
         acc += gi * gi;
     }
@@ -155,10 +157,13 @@ __global__ void k_add(int64_t n, const double *a, const double *b, double *c)
 
 // Newton convergence test per body; sets the Newton WHILE condition
 // (alm[0]: later solves of an augmented-Lagrangian step keep the first
-// solve's reference norm g0keep)
+// solve's reference norm g0keep). With low_first, the first residual of the
+// solve was evaluated in FP32: it sets the reference norm and the first
+// Newton right-hand side but cannot certify convergence, so every body with
+// g0 > 0 takes at least one Newton iteration and an FP64 residual decides.
 __global__ void k_newton_check(int nb, const int32_t *boff, const double *partials, double *sc, int *it, double rtol,
                                int max_newton, cudaGraphConditionalHandle hN, int use_handle, const int *alm,
-                               double *g0keep)
+                               double *g0keep, int low_first)
 {
     int any = 0;
     for (int b = threadIdx.x; b < nb; b += blockDim.x) {
@@ -175,7 +180,8 @@ __global__ void k_newton_check(int nb, const int32_t *boff, const double *partia
         }
         sc[S_GN * nb + b] = gn;
         const double g0 = sc[S_G0 * nb + b];
-        const int act = (g0 > 0.0 && gn > rtol * g0 && it[I_NEWTON] < max_newton) ? 1 : 0;
+        const bool uncertified = low_first && it[I_NEWTON] == 0;
+        const int act = (g0 > 0.0 && (gn > rtol * g0 || uncertified) && it[I_NEWTON] < max_newton) ? 1 : 0;
         sc[S_NACT * nb + b] = act;
         any |= act;
     }
@@ -544,31 +550,51 @@ struct StepCtx {
 
 // --- building blocks, all stream-ordered on s --------------------------------
 
-static tlfe_status enq_residual(const StepCtx &x, cudaStream_t s)
+// Residual g(v) of Eq. residual at the current v, its per-body norms and the
+// Newton test. Evaluated with the FP64 twin mesh (FP64 element arithmetic), so
+// that it can certify relative residuals near 1e-8; with `first` on an FP32
+// mesh without constraints, the step's first residual is evaluated with the
+// FP32 kernels instead (it only sets g0 and the first right-hand side, which
+// CG solves to cg_rtol anyway; k_newton_check then does not accept it as
+// converged). Scratch for that FP32 evaluation: p32 (v - v_n), Ap32 (mass
+// product), D32 (force), all set later by the CG set-up.
+static tlfe_status enq_residual(const StepCtx &x, cudaStream_t s, bool first)
 {
     NewtonState *ns = x.ns;
     tlfe_mesh *m64 = ns->twin ? ns->twin : x.m;
     const int nc = ns->n_chunks;
+    const bool low = first && x.m->precision == TLFE_FP32 && ns->n_cons == 0;
     if (x.m->precision == TLFE_FP32)
-        k_prep<float><<<nc, RT, 0, s>>>(x.c, ns->h, ns->u_n, ns->v, ns->v_n, ns->u_cur, ns->dv, nullptr, ns->ud32);
+        k_prep<float><<<nc, RT, 0, s>>>(x.c, ns->h, ns->u_n, ns->v, ns->v_n, ns->u_cur, ns->dv, low ? ns->p32 : nullptr,
+                                        ns->ud32);
     else
         k_prep<double><<<nc, RT, 0, s>>>(x.c, ns->h, ns->u_n, ns->v, ns->v_n, ns->u_cur, ns->dv, nullptr, nullptr);
     NCK(cudaGetLastError());
-    tlfe_status st = run_op<OP_MATVEC, double>(m64, ns->u_cur, ns->v, ns->dv, ns->y1, nullptr, nullptr, 1.0 / ns->h,
-                                               0.0, 0.0, 0, s);
-    if (st != TLFE_OK) return st;
-    st = run_op<OP_FORCE, double>(m64, ns->u_cur, ns->v, nullptr, ns->y2, nullptr, nullptr, 0.0, 1.0, 0.0, 0, s);
-    if (st != TLFE_OK) return st;
-    if (ns->n_cons > 0) {
-        // + h C_q^T (lambda + rho c) at q(v) (Eq. residual)
-        NCK(con_eval(ns->n_cons, ns->cons, ns->con_sh, ns->con_nd, x.m->d_X, ns->u_cur, ns->con_wrow, ns->con_c,
-                     ns->con_gp, s));
-        NCK(con_weights(ns->n_cons, ns->lam, ns->con_c, ns->rho, ns->h, ns->con_w, s));
-        NCK(con_jt<double>(ns->n_cons, ns->con_sh, ns->con_nd, ns->con_gp, ns->con_w, 1.0, ns->y2, s));
+    tlfe_status st;
+    if (low) {
+        st = run_op<OP_MATVEC, float>(x.m, ns->u_cur, ns->ud32, ns->p32, ns->Ap32, nullptr, nullptr, 1.0 / ns->h, 0.0,
+                                      0.0, 0, s);
+        if (st != TLFE_OK) return st;
+        st = run_op<OP_FORCE, float>(x.m, ns->u_cur, ns->ud32, nullptr, ns->D32, nullptr, nullptr, 0.0, 1.0, 0.0, 0, s);
+        if (st != TLFE_OK) return st;
+        k_residual<float><<<nc, RT, 0, s>>>(x.c, ns->Ap32, ns->D32, ns->fff, ns->fixed, ns->g, ns->partials);
+    } else {
+        st = run_op<OP_MATVEC, double>(m64, ns->u_cur, ns->v, ns->dv, ns->y1, nullptr, nullptr, 1.0 / ns->h, 0.0, 0.0, 0,
+                                       s);
+        if (st != TLFE_OK) return st;
+        st = run_op<OP_FORCE, double>(m64, ns->u_cur, ns->v, nullptr, ns->y2, nullptr, nullptr, 0.0, 1.0, 0.0, 0, s);
+        if (st != TLFE_OK) return st;
+        if (ns->n_cons > 0) {
+            // + h C_q^T (lambda + rho c) at q(v) (Eq. residual)
+            NCK(con_eval(ns->n_cons, ns->cons, ns->con_sh, ns->con_nd, x.m->d_X, ns->u_cur, ns->con_wrow, ns->con_c,
+                         ns->con_gp, s));
+            NCK(con_weights(ns->n_cons, ns->lam, ns->con_c, ns->rho, ns->h, ns->con_w, s));
+            NCK(con_jt<double>(ns->n_cons, ns->con_sh, ns->con_nd, ns->con_gp, ns->con_w, 1.0, ns->y2, s));
+        }
+        k_residual<double><<<nc, RT, 0, s>>>(x.c, ns->y1, ns->y2, ns->fff, ns->fixed, ns->g, ns->partials);
     }
-    k_residual<<<nc, RT, 0, s>>>(x.c, ns->y1, ns->y2, ns->fff, ns->fixed, ns->g, ns->partials);
     k_newton_check<<<1, 1024, 0, s>>>(ns->nb, ns->body_chunk_off, ns->partials, ns->sc, ns->it, ns->nrtol,
-                                       ns->max_newton, ns->hN, x.use_handle, ns->alm, ns->g0keep);
+                                       ns->max_newton, ns->hN, x.use_handle, ns->alm, ns->g0keep, low ? 1 : 0);
     NCK(cudaGetLastError());
     return TLFE_OK;
 }
@@ -651,7 +677,7 @@ static tlfe_status enq_newton_tail(const StepCtx &x, cudaStream_t s)
     k_v_update<<<ns->n_chunks, RT, 0, s>>>(x.c, ns->sc, ns->nb, ns->x, ns->v);
     k_newton_count<<<1, 1024, 0, s>>>(ns->nb, ns->sc, ns->it);
     NCK(cudaGetLastError());
-    return enq_residual(x, s);
+    return enq_residual(x, s, false);
 }
 
 static tlfe_status enq_prologue(const StepCtx &x, cudaStream_t s)
@@ -660,7 +686,7 @@ static tlfe_status enq_prologue(const StepCtx &x, cudaStream_t s)
     k_reset<<<1, 1024, 0, s>>>(ns->nb, ns->sc, ns->it);
     k_start<<<ns->n_chunks, RT, 0, s>>>(x.c, ns->fixed, ns->v_n, ns->v, ns->alm);
     NCK(cudaGetLastError());
-    return enq_residual(x, s);
+    return enq_residual(x, s, true);
 }
 
 // add a conditional WHILE node to the graph being captured on `s`; returns its body graph
