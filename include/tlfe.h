@@ -375,6 +375,17 @@ tlfe_status tlfe_body_norms(tlfe_mesh *mesh, const double *x_dev, double *out_de
  * sharing nothing but this library) race; order them on one stream. */
 tlfe_status tlfe_norm_noalloc(const double *x_dev, int64_t n, double *out_dev, void *stream);
 
+/* Diagnostic of the timeout path of device-side waits (no counterpart in the
+ * paper). The element kernels wait for their bulk copies with a bounded number
+ * of mbarrier try_wait rounds and, when a copy never lands, record the fact in
+ * the mesh's status word and return instead of hanging. This call runs that
+ * wait on an mbarrier that expects 16 bytes no copy will deliver, for
+ * spin_limit rounds (1 .. 2^20; each round may pause the thread for a
+ * hardware-chosen time slice), then records the timeout the same way: the next
+ * tlfe_sync returns TLFE_E_TIMEOUT and clears the status, and the mesh and
+ * the CUDA context stay usable. Stream-ordered; no fault, no trap. */
+tlfe_status tlfe_selftest_wait_timeout(tlfe_mesh *mesh, int64_t spin_limit, void *stream);
+
 /* Thread-local text of the last error (never NULL). */
 const char *tlfe_last_error(void);
 

@@ -83,7 +83,8 @@ _lib = None
 EXPORTS = ["tlfe_create_mesh", "tlfe_destroy_mesh", "tlfe_get_mesh_info", "tlfe_get_colors", "tlfe_sync",
            "tlfe_internal_force", "tlfe_internal_force_host", "tlfe_tangent_matvec", "tlfe_jacobi_diag",
            "tlfe_vjp", "tlfe_set_elem_mu_lambda", "tlfe_autotune", "tlfe_point_loads", "tlfe_surface_traction",
-           "tlfe_constraint_eval", "tlfe_constraint_jt", "tlfe_constraint_j", "tlfe_newton_step", "tlfe_body_norms", "tlfe_norm_noalloc", "tlfe_last_error", "tlfe_version"]
+           "tlfe_constraint_eval", "tlfe_constraint_jt", "tlfe_constraint_j", "tlfe_newton_step", "tlfe_body_norms", "tlfe_norm_noalloc", "tlfe_selftest_wait_timeout", "tlfe_last_error",
+           "tlfe_version"]
 
 
 def load(path: str = LIB_PATH) -> C.CDLL:
@@ -117,6 +118,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "tlfe_constraint_jt": [P, I, P, P, P, P, P],
         "tlfe_constraint_j": [P, I, P, P, P, P, P],
         "tlfe_norm_noalloc": [P, C.c_int64, P, P],
+        "tlfe_selftest_wait_timeout": [P, C.c_int64, P],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -250,6 +252,12 @@ class Mesh:
         n = C.c_int64(0)
         _check(load().tlfe_sync(self._h, _stream(stream), C.byref(n)))
         return n.value
+
+    def selftest_wait_timeout(self, spin_limit=4096, stream=None):
+        """Run a bounded device wait that cannot complete
+        (tlfe_selftest_wait_timeout); the next sync() raises TLFEError with
+        TLFE_E_TIMEOUT (6) and the mesh stays usable."""
+        _check(load().tlfe_selftest_wait_timeout(self._h, int(spin_limit), _stream(stream)))
 
     def internal_force(self, u, udot=None, out=None, stream=None):
         """u: (n_nodes, 3) float64 displacement (FP64 in both precisions); udot

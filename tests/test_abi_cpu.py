@@ -80,3 +80,9 @@ def test_null_handles_and_oversized_noalloc_are_rejected(lib):
     assert lib.tlfe_norm_noalloc(C.byref(one), C.c_int64(4096 * 4096 + 1), C.byref(one), None) == 1
     assert "exceeds the maximum" in lib.tlfe_last_error().decode()
     assert lib.tlfe_norm_noalloc(None, C.c_int64(-1), C.byref(one), None) == 1
+
+
+def test_wait_timeout_selftest_validates_its_arguments(lib):
+    """The timeout diagnostic rejects a NULL mesh before touching the device."""
+    assert lib.tlfe_selftest_wait_timeout(None, C.c_int64(16), None) == 1
+    assert "mesh is NULL" in lib.tlfe_last_error().decode()

@@ -289,3 +289,26 @@ def test_mooney_rivlin_per_element_parameters(prec):
     wl = _mooney_rivlin(synth.diff_block(cells=3), 0.2)
     _, out = run_all(wl, prec)
     check_all(wl, out, prec)
+
+
+def test_bounded_wait_times_out_and_the_context_stays_usable():
+    """A device-side wait that nothing completes (tlfe_selftest_wait_timeout:
+    the element kernels' bounded mbarrier wait on 16 bytes no copy delivers)
+    gives TLFE_E_TIMEOUT at the next sync, without a fault; the status is then
+    clear and the same mesh evaluates correctly."""
+    tl = T()
+    wl = synth.small_beam(cells=(4, 2, 2))
+    mesh = tl.Mesh.from_workload(wl, precision=tl.FP32)
+    with pytest.raises(tl.TLFEError):
+        mesh.selftest_wait_timeout(0)
+    mesh.selftest_wait_timeout(4096)
+    with pytest.raises(tl.TLFEError) as ei:
+        mesh.sync()
+    assert ei.value.code == 6
+    dt = mesh.torch_dtype
+    u, ud = dev(wl.u, torch.float64), dev(wl.udot, dt)
+    f = mesh.internal_force(u, ud)
+    assert mesh.sync() == 0
+    f_ref, _ = oracle.internal_force(wl)
+    assert relerr(f, f_ref) <= TOL[1]
+    mesh.close()
