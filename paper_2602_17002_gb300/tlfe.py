@@ -519,3 +519,36 @@ def tlfe_sync(mesh: Mesh, stream=None):
 
 def tlfe_version() -> str:
     return load().tlfe_version().decode()
+
+
+# ---------------------------------------------------------------------------
+# checkpoint / resume of a time-stepping run
+# ---------------------------------------------------------------------------
+
+def save_checkpoint(path, u, v, step, lam=None, **meta):
+    """Write the state of a backward-Euler run to an .npz file: displacement
+    u and velocity v (float64 (n_nodes, 3)), the step index, the constraint
+    multipliers lam when the run has constraints, and any scalar metadata
+    (step size, seeds, ...). The arrays are copied bit for bit, so a run
+    resumed with load_checkpoint on a mesh built the same way repeats the
+    original steps exactly where the step itself is deterministic (colour
+    scatter: no atomic accumulation)."""
+    import numpy as np
+    arrs = {"u": u.detach().cpu().numpy(), "v": v.detach().cpu().numpy(), "step": np.int64(step)}
+    if lam is not None:
+        arrs["lam"] = lam.detach().cpu().numpy()
+    for k, x in meta.items():
+        arrs["meta_" + k] = np.asarray(x)
+    np.savez(path, **arrs)
+
+
+def load_checkpoint(path, device="cuda"):
+    """Read a save_checkpoint file: returns a dict with u, v (float64 tensors
+    on `device`), step (int), lam (tensor or None) and meta (dict)."""
+    import numpy as np
+    import torch
+    with np.load(path) as z:
+        out = {"u": torch.from_numpy(z["u"].copy()).to(device), "v": torch.from_numpy(z["v"].copy()).to(device),
+               "step": int(z["step"]), "lam": torch.from_numpy(z["lam"].copy()).to(device) if "lam" in z else None,
+               "meta": {k[5:]: z[k].item() if z[k].ndim == 0 else z[k] for k in z.files if k.startswith("meta_")}}
+    return out
