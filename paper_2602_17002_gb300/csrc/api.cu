@@ -537,6 +537,7 @@ static tlfe_status build_block(tlfe_mesh *m, const tlfe_mesh_desc *d, int bi, in
 
 extern "C" tlfe_status tlfe_create_mesh(const tlfe_mesh_desc *desc, void *stream, tlfe_mesh **out)
 {
+    TLFE_TRACE("tlfe_create_mesh");
     if (!out) return fail(TLFE_E_INVALID, "out is NULL");
     *out = nullptr;
     tlfe_status st = validate(desc);
@@ -619,6 +620,7 @@ extern "C" tlfe_status tlfe_create_mesh(const tlfe_mesh_desc *desc, void *stream
 
 extern "C" tlfe_status tlfe_destroy_mesh(tlfe_mesh *m)
 {
+    TLFE_TRACE("tlfe_destroy_mesh");
     if (!m) return TLFE_OK;
     cudaDeviceSynchronize();
     destroy_newton(m);
@@ -629,6 +631,7 @@ extern "C" tlfe_status tlfe_destroy_mesh(tlfe_mesh *m)
 
 extern "C" tlfe_status tlfe_get_mesh_info(const tlfe_mesh *m, tlfe_mesh_info *info)
 {
+    TLFE_TRACE("tlfe_get_mesh_info");
     if (!m || !info) return fail(TLFE_E_INVALID, "NULL argument");
     info->n_nodes = m->n_nodes;
     info->n_elem = m->n_elem;
@@ -670,6 +673,7 @@ extern "C" tlfe_status tlfe_get_mesh_info(const tlfe_mesh *m, tlfe_mesh_info *in
 
 extern "C" tlfe_status tlfe_get_colors(const tlfe_mesh *m, int32_t *colors)
 {
+    TLFE_TRACE("tlfe_get_colors");
     if (!m || !colors) return fail(TLFE_E_INVALID, "NULL argument");
     for (auto &B : m->blocks)
         for (int k = 0; k < B.n_elem; ++k) colors[B.elem_base + k] = B.colors.empty() ? -1 : B.colors[k];
@@ -678,6 +682,7 @@ extern "C" tlfe_status tlfe_get_colors(const tlfe_mesh *m, int32_t *colors)
 
 extern "C" tlfe_status tlfe_sync(tlfe_mesh *m, void *stream, int64_t *n_inverted)
 {
+    TLFE_TRACE("tlfe_sync");
     if (!m) return fail(TLFE_E_INVALID, "mesh is NULL");
     cudaStream_t s = (cudaStream_t)stream;
     int h[ST_COUNT];
@@ -932,6 +937,7 @@ static bool all_affine(const tlfe_mesh *m)
 
 extern "C" tlfe_status tlfe_internal_force(tlfe_mesh *m, const void *u, const void *ud, void *f, void *stream)
 {
+    TLFE_TRACE("tlfe_internal_force");
     tlfe_status st = check_mesh_args(m, {u, f});
     if (st != TLFE_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
@@ -943,6 +949,7 @@ extern "C" tlfe_status tlfe_internal_force(tlfe_mesh *m, const void *u, const vo
 extern "C" tlfe_status tlfe_internal_force_host(tlfe_mesh *m, const void *u_h, const void *ud_h, void *f_h,
                                                 void *stream)
 {
+    TLFE_TRACE("tlfe_internal_force_host");
     tlfe_status st = check_mesh_args(m, {u_h, f_h});
     if (st != TLFE_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
@@ -962,6 +969,7 @@ extern "C" tlfe_status tlfe_internal_force_host(tlfe_mesh *m, const void *u_h, c
 extern "C" tlfe_status tlfe_tangent_matvec(tlfe_mesh *m, const void *u, const void *ud, const void *v, double aM,
                                            double aK, double aC, void *y, void *stream)
 {
+    TLFE_TRACE("tlfe_tangent_matvec");
     tlfe_status st = check_mesh_args(m, {u, v, y});
     if (st != TLFE_OK) return st;
     if (!std::isfinite(aM) || !std::isfinite(aK) || !std::isfinite(aC)) return fail(TLFE_E_INVALID, "non-finite coefficient");
@@ -975,6 +983,7 @@ extern "C" tlfe_status tlfe_tangent_matvec(tlfe_mesh *m, const void *u, const vo
 extern "C" tlfe_status tlfe_jacobi_diag(tlfe_mesh *m, const void *u, const void *ud, double aM, double aK, double aC,
                                         void *d, void *stream)
 {
+    TLFE_TRACE("tlfe_jacobi_diag");
     tlfe_status st = check_mesh_args(m, {u, d});
     if (st != TLFE_OK) return st;
     if (aM != 0.0 && !all_affine(m)) return fail(TLFE_E_UNSUPPORTED, "consistent mass needs affine elements");
@@ -987,6 +996,7 @@ extern "C" tlfe_status tlfe_jacobi_diag(tlfe_mesh *m, const void *u, const void 
 extern "C" tlfe_status tlfe_vjp(tlfe_mesh *m, const void *u, const void *ud, const void *cot, void *g_u, void *g_ud,
                                 double *g_th, void *stream)
 {
+    TLFE_TRACE("tlfe_vjp");
     tlfe_status st = check_mesh_args(m, {u, cot});
     if (st != TLFE_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
@@ -1001,6 +1011,7 @@ extern "C" tlfe_status tlfe_vjp(tlfe_mesh *m, const void *u, const void *ud, con
 
 extern "C" tlfe_status tlfe_autotune(tlfe_mesh *m, const double *u, const void *ud, const void *v, void *stream)
 {
+    TLFE_TRACE("tlfe_autotune");
     tlfe_status st = check_mesh_args(m, {u});
     if (st != TLFE_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
@@ -1009,6 +1020,7 @@ extern "C" tlfe_status tlfe_autotune(tlfe_mesh *m, const double *u, const void *
 
 extern "C" tlfe_status tlfe_set_elem_mu_lambda(tlfe_mesh *m, const double *mu_lambda_dev, void *stream)
 {
+    TLFE_TRACE("tlfe_set_elem_mu_lambda");
     tlfe_status st = check_mesh_args(m, {mu_lambda_dev});
     if (st != TLFE_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;

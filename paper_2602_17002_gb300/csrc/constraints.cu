@@ -335,6 +335,7 @@ static tlfe_status con_setup(tlfe_mesh *m, int n, const tlfe_constraint *cons, c
 extern "C" tlfe_status tlfe_constraint_eval(tlfe_mesh *m, int32_t n, const tlfe_constraint *cons, const double *u,
                                             double *c, void *stream)
 {
+    TLFE_TRACE("tlfe_constraint_eval");
     if (!m || n < 0 || (n > 0 && (!cons || !u || !c))) return fail(TLFE_E_INVALID, "bad constraint arguments");
     if (n == 0) return TLFE_OK;
     cudaStream_t s = (cudaStream_t)stream;
@@ -349,6 +350,7 @@ extern "C" tlfe_status tlfe_constraint_eval(tlfe_mesh *m, int32_t n, const tlfe_
 extern "C" tlfe_status tlfe_constraint_jt(tlfe_mesh *m, int32_t n, const tlfe_constraint *cons, const double *u,
                                           const double *w, double *f, void *stream)
 {
+    TLFE_TRACE("tlfe_constraint_jt");
     if (!m || n < 0 || (n > 0 && (!cons || !u || !w || !f))) return fail(TLFE_E_INVALID, "bad constraint arguments");
     if (n == 0) return TLFE_OK;
     cudaStream_t s = (cudaStream_t)stream;
@@ -363,6 +365,7 @@ extern "C" tlfe_status tlfe_constraint_jt(tlfe_mesh *m, int32_t n, const tlfe_co
 extern "C" tlfe_status tlfe_constraint_j(tlfe_mesh *m, int32_t n, const tlfe_constraint *cons, const double *u,
                                          const double *v, double *out, void *stream)
 {
+    TLFE_TRACE("tlfe_constraint_j");
     if (!m || n < 0 || (n > 0 && (!cons || !u || !v || !out))) return fail(TLFE_E_INVALID, "bad constraint arguments");
     if (n == 0) return TLFE_OK;
     cudaStream_t s = (cudaStream_t)stream;

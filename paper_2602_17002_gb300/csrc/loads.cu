@@ -165,6 +165,7 @@ static tlfe_status loads_check(tlfe_mesh *m, int n, std::initializer_list<const 
 extern "C" tlfe_status tlfe_point_loads(tlfe_mesh *m, int32_t n, const int32_t *elem, const double *xi,
                                         const double *force, double *f, void *stream)
 {
+    TLFE_TRACE("tlfe_point_loads");
     tlfe_status st = loads_check(m, n, {elem, xi, force, f});
     if (st != TLFE_OK || n == 0) return st;
     cudaStream_t s = (cudaStream_t)stream;
@@ -181,6 +182,7 @@ extern "C" tlfe_status tlfe_point_loads(tlfe_mesh *m, int32_t n, const int32_t *
 extern "C" tlfe_status tlfe_surface_traction(tlfe_mesh *m, int32_t n, const int32_t *elem, const int32_t *face,
                                              const double *t0, double *f, void *stream)
 {
+    TLFE_TRACE("tlfe_surface_traction");
     tlfe_status st = loads_check(m, n, {elem, face, t0, f});
     if (st != TLFE_OK || n == 0) return st;
     cudaStream_t s = (cudaStream_t)stream;

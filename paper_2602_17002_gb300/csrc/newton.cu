@@ -802,6 +802,7 @@ tlfe_mesh *newton_twin(tlfe_mesh *m) { return m->newton ? m->newton->twin : null
 
 extern "C" tlfe_status tlfe_body_norms(tlfe_mesh *m, const double *x, double *out, void *stream)
 {
+    TLFE_TRACE("tlfe_body_norms");
     if (!m || !x || !out) return fail(TLFE_E_INVALID, "NULL argument");
     cudaStream_t s = (cudaStream_t)stream;
     // per-body tables (a workspace built for a coupled, constrained step has one group)
@@ -905,6 +906,7 @@ extern "C" tlfe_status tlfe_newton_step(tlfe_mesh *m, const double *u_n, const d
                                         const tlfe_step_params *prm, double *v_out, tlfe_step_report *rep,
                                         void *stream)
 {
+    TLFE_TRACE("tlfe_newton_step");
     if (!m || !u_n || !v_n || !prm || !v_out || !rep) return fail(TLFE_E_INVALID, "NULL argument");
     memset(rep, 0, sizeof(*rep));
     if (!(prm->h > 0.0) || !std::isfinite(prm->h) || !(prm->newton_rtol >= 0.0) || !(prm->cg_rtol >= 0.0) ||

@@ -35,6 +35,7 @@ using namespace tlfe;
 
 extern "C" tlfe_status tlfe_selftest_wait_timeout(tlfe_mesh *m, int64_t spin_limit, void *stream)
 {
+    TLFE_TRACE("tlfe_selftest_wait_timeout");
     if (!m) return fail(TLFE_E_INVALID, "mesh is NULL");
     if (spin_limit < 1 || spin_limit > (int64_t)MBAR_SPIN_LIMIT)
         return fail(TLFE_E_INVALID, "spin_limit must be in [1, " + std::to_string(MBAR_SPIN_LIMIT) + "]");

@@ -9,6 +9,8 @@
 #include <tuple>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "tlfe_internal.h"
 
 namespace tlfe {
@@ -77,6 +79,17 @@ struct tlfe_mesh {
 };
 
 namespace tlfe {
+
+// NVTX range named after the C entry point for the duration of the call, so
+// that profilers and timelines attribute the kernels a call launches to it
+// (free when no tool is attached)
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
+#define TLFE_TRACE(name) tlfe::TraceRange tlfe_trace_range_(name)
 
 tlfe_status fail(tlfe_status st, const std::string &msg);
 tlfe_status cuda_fail(cudaError_t e, const char *where);
