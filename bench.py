@@ -852,9 +852,11 @@ def run_diff(args, rank, world):
             t.grad = None
         f = autograd.internal_force(mesh, u, ud, theta)
         loss = 0.5 * ((f.double() - f_t) ** 2).sum()
-        loss.backward()
         if ev:
             ev[1].record(stream)
+        loss.backward()
+        if ev:
+            ev[2].record(stream)
         losses.append(loss.detach())
 
     for _ in range(args.warmup):
@@ -862,23 +864,69 @@ def run_diff(args, rank, world):
     torch.cuda.synchronize()
     barrier(world)
     with ClockSampler(torch.cuda.current_device()) as clk:
-        evs = timed_steps(step, args.steps, flush, stream)
+        evs = timed_steps(step, args.steps, flush, stream, 3)
     barrier(world)
     st = mesh.sync()
-    ms = allmax(float(np.mean([e[0].elapsed_time(e[1]) for e in evs])), world)
+    ms = allmax(float(np.mean([e[0].elapsed_time(e[2]) for e in evs])), world)
+    ms_fwd = float(np.mean([e[0].elapsed_time(e[1]) for e in evs]))
+    ms_bwd = float(np.mean([e[1].elapsed_time(e[2]) for e in evs]))
     units = wl.n_qp
     peak, peak_kind = peaks()
-    b_alg = info["stream_bytes_force"] + info["stream_bytes_vjp"]
-    achieved = b_alg / (ms * 1e-3) / 1e9
+    # roofline of the longer half, the backward (the adjoint kernel plus the
+    # loss gradient, a few elementwise torch kernels): FP32 FMA roof, HBM beside
+    fpq = FLOP_PER_QP["beam"]    # T10 Q5 neo-Hookean + Kelvin-Voigt, as the beam
+    flops = fpq["vjp"] * units
+    achieved = flops / (ms_bwd * 1e-3) / 1e12
+    b_bwd = info["stream_bytes_vjp"]
+    hbm = b_bwd / (ms_bwd * 1e-3) / 1e9
+
+    # end to end: u, udot and the parameters from pinned host memory, the
+    # loss and the three gradients back to the host, every step
+    hu, hud, hth = (t.detach().cpu().pin_memory() for t in (u, ud, theta))
+    hgu, hgud, hgth = (torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in (u, ud, theta))
+    hloss = torch.empty((), dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        with torch.no_grad():
+            u.copy_(hu, non_blocking=True)
+            ud.copy_(hud, non_blocking=True)
+            theta.copy_(hth, non_blocking=True)
+        step()
+        hgu.copy_(u.grad, non_blocking=True)
+        hgud.copy_(ud.grad, non_blocking=True)
+        hgth.copy_(theta.grad, non_blocking=True)
+        hloss.copy_(losses[-1], non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    barrier(world)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = allmax(e0.elapsed_time(e1) / args.steps, world)
+    h2d = sum(t.numel() * t.element_size() for t in (hu, hud, hth))
+    d2h = sum(t.numel() * t.element_size() for t in (hgu, hgud, hgth)) + 8
+
     line = base_line(args, world, "diff", world * units / (ms * 1e-3), UNIT, ms, "f32",
                      n_elem=wl.n_elem, n_nodes=wl.n_nodes, n_qp=units,
                      step="autograd forward (tlfe_internal_force) + loss in torch + backward (tlfe_vjp)")
     line.update({
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "kernel": "force + vjp (+ torch loss)", "peak_source": peak_kind,
-                     "algorithmic_bytes": b_alg},
+        "phases_ms": {"forward_and_loss": ms_fwd, "backward": ms_bwd},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / ALU_PEAK_TFLOPS, "traffic": None,
+                     "kernel": "backward: tlfe_vjp (+ the loss gradient)",
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz",
+                     "algorithmic_flops": flops, "flop_per_qp": fpq["vjp"], "algorithmic_bytes": b_bwd,
+                     "hbm_achieved_gbs": hbm, "hbm_peak_gbs": peak, "hbm_frac": hbm / peak,
+                     "hbm_peak_source": peak_kind},
         "loss": float(losses[-1].item()),
-        "e2e": None, "gpu_launches": 2 * args.steps, "clocks": clk.summary(), "device_status": st})
+        "e2e": {"value": world * units / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+        "gpu_launches": 2 * args.steps, "clocks": clk.summary(), "device_status": st})
     mesh.close()
     return line, wl
 
