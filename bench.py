@@ -97,12 +97,21 @@ KERNEL_SOURCES = ("k_elem.cuh", "k_wpe.cuh", "tlfe_elem.cuh", "tlfe_math.cuh", "
                   "api.cu", "k_setup.cu", "k_force.cu", "k_matvec.cu", "k_vjp.cu", "k_diag.cu")
 
 
+def _strip_comments(src):
+    """C/C++ source without comments and blank-line runs, so that the hash
+    follows the code, not its prose (string and character literals kept)."""
+    import re
+    pat = re.compile(r'//[^\n]*|/\*.*?\*/|"(?:\\.|[^"\\])*"|\'(?:\\.|[^\'\\])*\'', re.S)
+    out = pat.sub(lambda m: m.group(0) if m.group(0)[0] in "\"'" else " ", src)
+    return "\n".join(ln.rstrip() for ln in out.splitlines() if ln.strip())
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2602_17002_gb300", "csrc")
     for name in KERNEL_SOURCES:
-        with open(os.path.join(csrc, name), "rb") as fh:
-            h.update(name.encode() + fh.read())
+        with open(os.path.join(csrc, name), encoding="utf-8") as fh:
+            h.update(name.encode() + _strip_comments(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -5,11 +5,18 @@
 // Work decomposition: one thread per element, one warp per tile of 32
 // elements, warps independent of each other (persistent, grid-striding over
 // tiles). Per warp:
-//   - the reference data of one quadrature point of one tile (h_i rows and
-//     w_q J_p, a contiguous "slice" of the slab [tile][q][3 npe + 1][32]) is
-//     streamed by cp.async.bulk into a ring of NSLICE shared-memory slots,
-//     issued NSLICE slices ahead by lane 0 and completed on one mbarrier per
-//     slot;
+//   - the tile's metadata (unique-node list, local indices, node-to-slot
+//     lists) comes by cp.async.bulk one tile ahead into a double buffer, with
+//     the per-element J^{-1} and det J record on the affine path;
+//   - slab path only: the reference data of one quadrature point of one tile
+//     (h_i rows and w_q J_p, a contiguous "slice" of the slab
+//     [tile][q][3 npe + 1][32]) is streamed by cp.async.bulk into a ring of
+//     NSLICE shared-memory slots, issued NSLICE slices ahead by lane 0 and
+//     completed on one mbarrier per slot; the affine path instead forms
+//     h_i = J^{-T} g_i from the parent gradients g_i at each point;
+//   - the nodes of the next tile are prefetched into L2, after the first
+//     quadrature point in the affine force, operator and diagonal kernels and
+//     after the last one otherwise;
 //   - the nodal values of the tile's unique nodes (a sorted list built at mesh
 //     creation) are gathered into a shared-memory patch with consecutive lanes
 //     on consecutive node ids; each lane then reads its element's nodes from
@@ -24,6 +31,8 @@
 //     elements of a launch share a node).
 // Every mbarrier wait is bounded; on timeout the kernel latches ST_TIMEOUT in
 // the status word, drains its own copies (again bounded) and returns.
+// Affine Q27 blocks do not come here: they run the warp-per-element kernels
+// of k_wpe.cuh (kernel_for / smem_for below dispatch on wpe_path).
 #pragma once
 
 #include <string>
