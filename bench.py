@@ -72,6 +72,13 @@ GRAVITY = (0.0, 0.0, -9.81)
 # the beam workload, Q27 for the q27 workload
 FLOP_PER_QP = {"beam": {"force": 852, "matvec": 1589, "vjp": 1786},
                "q27": {"force": 1932, "matvec": 3026, "vjp": 3567}}
+# batch workload (generic-material kernels, affine path, no damping): FP32 FLOP
+# per point by (element type, law, op), law 0 = SVK, 1 = neo-Hookean; ncu
+# counts of two captures of the timed step (16 and 512 bodies, whose SVK /
+# neo-Hookean mixes differ), solved per law
+FLOP_PER_QP_BATCH = {(0, 0): {"force": 288.5, "matvec": 504.5}, (0, 1): {"force": 361.2, "matvec": 692.2},
+                     (1, 0): {"force": 484.6, "matvec": 874.4}, (1, 1): {"force": 554.7, "matvec": 1056.5},
+                     (2, 0): {"force": 547.0, "matvec": 1035.5}, (2, 1): {"force": 616.3, "matvec": 1216.0}}
 # FP32 FMA roof: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz (maximum SM clock)
 ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
@@ -393,7 +400,7 @@ def cpu_sample(workload, wl, n_sample):
     return nqp / dt, dt, 1, f"{_sample_text(wl, sub)}, {what}, {dt:.1f} s"
 
 
-def build_workload(workload):
+def build_workload(workload, bodies=512):
     import synth
     if workload == "beam":
         return synth.cantilever_beam()
@@ -402,7 +409,7 @@ def build_workload(workload):
     if workload == "newton":
         return synth.newton_beams(64)
     if workload == "batch":
-        return synth.batch_bodies(512)
+        return synth.batch_bodies(bodies)
     return synth.diff_block()
 
 
@@ -417,7 +424,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     import numpy as np
-    wl = build_workload(args.workload)
+    wl = build_workload(args.workload, args.bodies)
     if args.workload == "diff":
         wl.v = diff_cotangent(wl)
     # all host cores (spawned processes over element ranges); the Newton
@@ -754,7 +761,7 @@ def run_batch(args, rank, world):
     import torch
 
     from paper_2602_17002_gb300 import tlfe
-    wl = build_workload("batch")
+    wl = build_workload("batch", args.bodies)
     mesh = tlfe.Mesh.from_workload(wl, precision=tlfe.FP32)
     info = mesh.info
     u = torch.from_numpy(wl.u).to("cuda", torch.float64)
@@ -792,14 +799,23 @@ def run_batch(args, rank, world):
     torch.cuda.synchronize()
     barrier(world)
     with ClockSampler(torch.cuda.current_device()) as clk:
-        evs = timed_steps(step, args.steps, flush, stream)
+        evs = timed_steps(step, args.steps, flush, stream, label="batch_timed")
     barrier(world)
     st = mesh.sync()
     ms = allmax(float(np.mean([e[0].elapsed_time(e[1]) for e in evs])), world)
     units = wl.n_qp
     peak, peak_kind = peaks()
     b_alg = info["stream_bytes_force"] + info["stream_bytes_matvec"]
-    achieved = b_alg / (ms * 1e-3) / 1e9
+    hbm = b_alg / (ms * 1e-3) / 1e9
+    # every block is affine and ALU-bound (about 26 FLOP per streamed byte,
+    # above the FP32 ridge): FP32 FMA roof, HBM beside it
+    flops = 0.0
+    for b in wl.blocks:
+        laws = np.asarray(wl.model)[b.body]
+        for law in (0, 1):
+            f_qp = FLOP_PER_QP_BATCH[(b.etype, law)]
+            flops += int((laws == law).sum()) * b.nq * (f_qp["force"] + f_qp["matvec"])
+    achieved = flops / (ms * 1e-3) / 1e12
     # e2e: u and v from pinned host memory, f and K v back
     hu, hv = u.cpu().pin_memory(), v.cpu().pin_memory()
     hf, hy = torch.empty_like(hv).pin_memory(), torch.empty_like(hv).pin_memory()
@@ -819,13 +835,19 @@ def run_batch(args, rank, world):
                      n_bodies=wl.n_bodies, n_elem=wl.n_elem, n_nodes=wl.n_nodes, n_qp=units,
                      elements_by_type={types[b.etype]: b.n_elem for b in wl.blocks},
                      step="internal force + K v over all bodies, one CUDA graph replay")
+    if wl.n_bodies != 512:
+        line["config"]["workload"] = WORKLOADS["batch"].replace("512 bodies", f"{wl.n_bodies} bodies")
     line.update({
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "kernel": "force + matvec, all element blocks", "peak_source": peak_kind,
-                     "algorithmic_bytes": b_alg},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / ALU_PEAK_TFLOPS,
+                     "traffic": ncu_traffic("batch512_step") if wl.n_bodies == 512 else None,
+                     "kernel": "force + matvec, all element blocks (one step)",
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz",
+                     "algorithmic_flops": flops, "algorithmic_bytes": b_alg, "hbm_achieved_gbs": hbm,
+                     "hbm_peak_gbs": peak, "hbm_frac": hbm / peak, "hbm_peak_source": peak_kind},
         "e2e": {"value": world * units / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": u.numel() * 8 + v.numel() * 4, "d2h_bytes_per_step": 2 * v.numel() * 4},
-        "gpu_launches": 2 * len([b for b in wl.blocks if b.n_elem]) * args.steps,
+        "gpu_launches": 2 * info["n_passes"] * args.steps,
         "clocks": clk.summary(), "device_status": st})
     mesh.close()
     return line, wl
@@ -950,6 +972,7 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=10000, help="elements per reference-arm step")
     ap.add_argument("--cpu-sample", type=int, default=40000, help="elements in the cpu_baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--bodies", type=int, default=512, help="bodies in the batch workload (512 = the benchmark)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

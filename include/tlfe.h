@@ -147,6 +147,8 @@ typedef struct {
     int64_t stream_bytes_vjp;     /* algorithmic bytes of one tlfe_vjp (all outputs) */
     int64_t device_bytes;         /* device memory held by the handle */
     int32_t n_affine_blocks;      /* blocks whose kernels run on the affine path */
+    int32_t n_passes;             /* element-kernel launches of one operation: one per elastic law of each
+                                     block (per colour and law in colour mode), each its own tile range */
 } tlfe_mesh_info;
 
 tlfe_status tlfe_get_mesh_info(const tlfe_mesh *mesh, tlfe_mesh_info *info);

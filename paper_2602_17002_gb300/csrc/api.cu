@@ -319,35 +319,42 @@ static tlfe_status build_block(tlfe_mesh *m, const tlfe_mesh_desc *d, int bi, in
     B.elem_base = elem_base;
     const int npe = B.npe;
 
-    // element order inside the layout: the locality order, then (colour
-    // mode) grouped by colour, keeping that order inside each colour
+    // the material of block element k: its body's
+    const bool have_body = b.body != nullptr && b.n_elem > 0;
+    auto mat_of = [&](int k) -> const tlfe_material & { return d->body_mat[have_body ? b.body[k] : 0]; };
+
+    // element order inside the layout: the locality order, then grouped by
+    // colour (colour mode) and by elastic law, keeping that order inside each
+    // group. Every group starts a new tile and is launched as its own pass,
+    // so that a pass has one law and runs that law's specialised kernel.
     std::vector<int32_t> order = locality_order(d, b);
-    std::vector<int> color_of;
     B.n_colors = 0;
-    if (d->scatter == TLFE_SCATTER_COLOR && b.n_elem > 0) {
+    const bool colour_mode = d->scatter == TLFE_SCATTER_COLOR;
+    if (colour_mode && b.n_elem > 0) {
         std::vector<int32_t> col;
         tlfe_status st = color_block(m, b, d->color_seed, col, s);
         if (st != TLFE_OK) return st;
         B.colors = col;
         B.n_colors = *std::max_element(col.begin(), col.end()) + 1;
-        std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return col[a] < col[c]; });
     }
-    // tiles: in colour mode every colour starts a new tile
+    auto group = [&](int k) -> int64_t { return (int64_t)(colour_mode ? B.colors[k] : 0) * 4 + mat_of(k).model; };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return group(a) < group(c); });
     std::vector<int32_t> eid;
     B.color_tile_off.assign(1, 0);
-    if (d->scatter == TLFE_SCATTER_COLOR) {
-        size_t k = 0;
-        for (int c = 0; c < B.n_colors; ++c) {
-            size_t k0 = k;
-            while (k < order.size() && B.colors[order[k]] == c) ++k;
-            for (size_t j = k0; j < k; ++j) eid.push_back(elem_base + order[j]);
-            while (eid.size() % TILE) eid.push_back(-1);
-            B.color_tile_off.push_back((int)(eid.size() / TILE));
+    B.pass_model.clear();
+    B.pass_visc.clear();
+    for (size_t k = 0; k < order.size();) {
+        const int64_t g = group(order[k]);
+        B.pass_model.push_back(mat_of(order[k]).model);
+        bool damped = false;
+        for (; k < order.size() && group(order[k]) == g; ++k) {
+            const tlfe_material &mm = mat_of(order[k]);
+            damped = damped || mm.mu_v != 0.0 || mm.lambda_v != 0.0;
+            eid.push_back(elem_base + order[k]);
         }
-    } else {
-        for (size_t j = 0; j < order.size(); ++j) eid.push_back(elem_base + order[j]);
         while (eid.size() % TILE) eid.push_back(-1);
         B.color_tile_off.push_back((int)(eid.size() / TILE));
+        B.pass_visc.push_back(damped);
     }
     B.n_tiles = (int)(eid.size() / TILE);
 
@@ -424,7 +431,6 @@ static tlfe_status build_block(tlfe_mesh *m, const tlfe_mesh_desc *d, int bi, in
     }
 
     // materials: uniform when all elements of the block share one body
-    const bool have_body = b.body != nullptr && b.n_elem > 0;
     const int body0 = have_body ? b.body[0] : 0;
     bool uniform = true;
     if (have_body)
@@ -668,6 +674,9 @@ extern "C" tlfe_status tlfe_get_mesh_info(const tlfe_mesh *m, tlfe_mesh_info *in
     info->stream_bytes_vjp = eb + nu + nb * (visc ? 4 : 2) + (int64_t)m->n_elem * 16;  // u, udot, r; g_u, g_udot; g_theta
     info->device_bytes = m->device_bytes;
     info->n_affine_blocks = naff;
+    info->n_passes = 0;
+    for (auto &B : m->blocks)
+        if (B.n_elem > 0) info->n_passes += (int)B.color_tile_off.size() - 1;
     return TLFE_OK;
 }
 
@@ -706,12 +715,13 @@ template <typename R> static const Mat<R> *mats_of(const tlfe_mesh *m);
 template <> const Mat<float> *mats_of<float>(const tlfe_mesh *m) { return m->d_mats_f; }
 template <> const Mat<double> *mats_of<double>(const tlfe_mesh *m) { return m->d_mats_d; }
 
-// material mode of a launch: the block's law when all its elements share
-// one, with the viscous term when a velocity is given and the block is damped
-static int mat_mode_of(const BlockStore &B, bool visc)
+// material mode of pass c of block B: the pass's law, with the viscous term
+// when a velocity is given and an element of the pass is damped
+static int pass_mat_mode(const BlockStore &B, int c, bool have_ud)
 {
-    if (B.model == MODEL_NH) return visc ? MAT_NH_KV : MAT_NH;
-    if (B.model == MODEL_SVK) return visc ? MAT_SVK_KV : MAT_SVK;
+    const bool visc = have_ud && B.pass_visc[c];
+    if (B.pass_model[c] == MODEL_NH) return visc ? MAT_NH_KV : MAT_NH;
+    if (B.pass_model[c] == MODEL_SVK) return visc ? MAT_SVK_KV : MAT_SVK;
     return MAT_ANY;
 }
 
@@ -735,8 +745,6 @@ template <typename R> static void block_params(tlfe_mesh *m, const BlockStore &B
     p.evol = (const R *)B.d_evol;
     p.mats = B.d_emat ? mats_of<R>(m) : nullptr;
     p.mat0 = to_mat<R>(m->h_mats[B.uniform_body >= 0 ? B.uniform_body : 0]);
-    p.visc = (B.visc && p.ud) ? 1 : 0;
-    p.mat_mode = mat_mode_of(B, p.visc != 0);
     p.status = m->d_status;
 }
 
@@ -759,18 +767,30 @@ static tlfe_status block_sched(tlfe_mesh *m, int bi, int mat, LaunchSched *out)
     return TLFE_OK;
 }
 
-// launch one element kernel per colour pass of block B with schedule ls
+// launch one element kernel per pass of block bi, each with its material
+// mode's schedule (or with `fixed`, for the passes of mode only_mat alone)
 template <int OP, typename R>
-static tlfe_status launch_block(tlfe_mesh *m, const BlockStore &B, KParams<R> p, const LaunchSched &ls,
-                                cudaStream_t s)
+static tlfe_status launch_block(tlfe_mesh *m, int bi, KParams<R> p, cudaStream_t s,
+                                const LaunchSched *fixed = nullptr, int only_mat = -1)
 {
-    p.tile_chunk = ls.chunk;
+    const BlockStore &B = m->blocks[bi];
     const int n_passes = (int)B.color_tile_off.size() - 1;
     for (int c = 0; c < n_passes; ++c) {
         p.tile_begin = B.color_tile_off[c];
         p.tile_end = B.color_tile_off[c + 1];
         const int tiles = p.tile_end - p.tile_begin;
         if (tiles <= 0) continue;
+        p.visc = (B.pass_visc[c] && p.ud) ? 1 : 0;
+        p.mat_mode = pass_mat_mode(B, c, p.ud != nullptr);
+        if (only_mat >= 0 && p.mat_mode != only_mat) continue;
+        LaunchSched ls;
+        if (fixed) {
+            ls = *fixed;
+        } else {
+            tlfe_status st = block_sched<OP, R>(m, bi, p.mat_mode, &ls);
+            if (st != TLFE_OK) return st;
+        }
+        p.tile_chunk = ls.chunk;
         p.rmw_scatter = m->scatter == TLFE_SCATTER_COLOR ? 1 : 0;
         // one warp per tile (per element on the warp-per-element path) at a
         // time, persistent over the resident warps
@@ -786,12 +806,8 @@ static tlfe_status launch_block(tlfe_mesh *m, const BlockStore &B, KParams<R> p,
 template <int OP, typename R>
 static tlfe_status run_block_op(tlfe_mesh *m, int bi, KParams<R> p, cudaStream_t s)
 {
-    const BlockStore &B = m->blocks[bi];
-    block_params<R>(m, B, p);
-    LaunchSched ls;
-    tlfe_status st = block_sched<OP, R>(m, bi, p.mat_mode, &ls);
-    if (st != TLFE_OK) return st;
-    return launch_block<OP, R>(m, B, p, ls, s);
+    block_params<R>(m, m->blocks[bi], p);
+    return launch_block<OP, R>(m, bi, p, s);
 }
 
 template <int OP, typename R>
@@ -835,38 +851,45 @@ static tlfe_status tune_block(tlfe_mesh *m, int bi, KParams<R> p, cudaStream_t s
 {
     const BlockStore &B = m->blocks[bi];
     block_params<R>(m, B, p);
-    const int mat = p.mat_mode;
-    LaunchSched best;
-    float best_ms = 1e30f;
-    for (int wpb : {4, 2, 1}) {
-        std::string why;
-        LaunchSched ls;
-        ls.wpb = wpb;
-        ls.resident = occupancy_op<OP, R>(B.et, B.nq, B.use_affine, mat, B.umax, B.meta_bytes, &ls.wpb, &why);
-        if (ls.resident <= 0) continue;
-        for (int chunk : {0, 1}) {
-            ls.chunk = chunk;
-            tlfe_status st = launch_block<OP, R>(m, B, p, ls, s);  // warm-up
-            if (st != TLFE_OK) return st;
-            float ms[3];
-            for (int r = 0; r < 3; ++r) {
-                CK(cudaEventRecord(e0, s));
-                st = launch_block<OP, R>(m, B, p, ls, s);
+    std::vector<int> modes;  // the material modes of the block's passes
+    for (int c = 0; c + 1 < (int)B.color_tile_off.size(); ++c) {
+        const int mat = pass_mat_mode(B, c, p.ud != nullptr);
+        if (std::find(modes.begin(), modes.end(), mat) == modes.end()) modes.push_back(mat);
+    }
+    for (int mat : modes) {
+        LaunchSched best;
+        float best_ms = 1e30f;
+        for (int wpb : {4, 2, 1}) {
+            std::string why;
+            LaunchSched ls;
+            ls.wpb = wpb;
+            ls.resident = occupancy_op<OP, R>(B.et, B.nq, B.use_affine, mat, B.umax, B.meta_bytes, &ls.wpb, &why);
+            if (ls.resident <= 0) continue;
+            for (int chunk : {0, 1}) {
+                ls.chunk = chunk;
+                tlfe_status st = launch_block<OP, R>(m, bi, p, s, &ls, mat);  // warm-up
                 if (st != TLFE_OK) return st;
-                CK(cudaEventRecord(e1, s));
-                CK(cudaEventSynchronize(e1));
-                CK(cudaEventElapsedTime(&ms[r], e0, e1));
-            }
-            std::sort(ms, ms + 3);
-            if (ms[1] < best_ms) {
-                best_ms = ms[1];
-                best = ls;
+                float ms[3];
+                for (int r = 0; r < 3; ++r) {
+                    CK(cudaEventRecord(e0, s));
+                    st = launch_block<OP, R>(m, bi, p, s, &ls, mat);
+                    if (st != TLFE_OK) return st;
+                    CK(cudaEventRecord(e1, s));
+                    CK(cudaEventSynchronize(e1));
+                    CK(cudaEventElapsedTime(&ms[r], e0, e1));
+                }
+                std::sort(ms, ms + 3);
+                if (ms[1] < best_ms) {
+                    best_ms = ms[1];
+                    best = ls;
+                }
             }
         }
+        if (best.resident <= 0)
+            return fail(TLFE_E_UNSUPPORTED, "no resident configuration for block " + std::to_string(bi));
+        best.tuned = true;
+        m->sched[std::make_tuple(OP, bi, mat, (int)sizeof(R))] = best;
     }
-    if (best.resident <= 0) return fail(TLFE_E_UNSUPPORTED, "no resident configuration for block " + std::to_string(bi));
-    best.tuned = true;
-    m->sched[std::make_tuple(OP, bi, mat, (int)sizeof(R))] = best;
     return TLFE_OK;
 }
 

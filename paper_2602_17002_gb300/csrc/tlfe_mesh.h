@@ -34,7 +34,12 @@ struct BlockStore {
     bool visc = false;
     int uniform_body = 0;            // body id when every element shares it, else -1
     int64_t n_unique = 0;            // sum over tiles of the unique node count
-    std::vector<int> color_tile_off; // tile range of each pass ([0, n_tiles] in atomic mode)
+    // passes: tile range [color_tile_off[c], color_tile_off[c + 1]) of pass c,
+    // one per (colour in colour mode,) elastic law; the law and whether any
+    // element of the pass is damped
+    std::vector<int> color_tile_off;
+    std::vector<int> pass_model;
+    std::vector<bool> pass_visc;
     std::vector<int32_t> colors;     // colour of each block element (colour mode)
     int32_t *d_eid = nullptr, *d_toff = nullptr, *d_tnodes = nullptr, *d_emat = nullptr;
     uint16_t *d_lidx = nullptr;

@@ -55,7 +55,7 @@ class tlfe_mesh_info(C.Structure):
                 ("n_colors", C.c_int32), ("precision", C.c_int32), ("scatter", C.c_int32),
                 ("n_qp", C.c_int64), ("stream_bytes_force", C.c_int64),
                 ("stream_bytes_matvec", C.c_int64), ("stream_bytes_vjp", C.c_int64),
-                ("device_bytes", C.c_int64), ("n_affine_blocks", C.c_int32)]
+                ("device_bytes", C.c_int64), ("n_affine_blocks", C.c_int32), ("n_passes", C.c_int32)]
 
 
 class tlfe_step_params(C.Structure):

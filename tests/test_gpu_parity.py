@@ -91,6 +91,55 @@ def test_mixed_batch_t4_t10_h8(prec, path):
     check_all(wl, out, prec)
 
 
+def _mixed_law_batch():
+    """A batch whose blocks mix SVK, neo-Hookean and Mooney-Rivlin bodies,
+    some of them damped (with a velocity field)."""
+    wl = synth.batch_bodies(n_bodies=12, seed=11, ne_range=(40, 300))
+    model = np.asarray(wl.model).copy()
+    model[::4] = 2                                        # Mooney-Rivlin, mu01 = 0.3 mu / 2
+    params = np.concatenate([wl.params, 0.15 * wl.params[:, :1]], axis=1)
+    params[1::3, 2] = 1e3                                 # Kelvin-Voigt mu_v on every third body
+    wl.model, wl.params = model, params
+    wl.udot = 0.01 * np.random.default_rng(31).standard_normal(wl.X.shape)
+    return wl
+
+
+@pytest.mark.parametrize("scatter", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_mixed_law_blocks_run_one_pass_per_law(prec, scatter):
+    """Each block is laid out as one tile range per elastic law (per colour
+    and law in colour mode) and each range is launched with its law's kernel:
+    the pass count is the number of such groups, every output matches the
+    oracle, and colour mode repeats bit for bit."""
+    wl = _mixed_law_batch()
+    mesh, out = run_all(wl, prec, scatter=scatter, aK=1.0, aC=1.0)
+    check_all(wl, out, prec, aK=1.0, aC=1.0)
+    law = np.asarray(wl.model)
+    if scatter == 0:
+        groups = sum(len(np.unique(law[b.body])) for b in wl.blocks if len(b.body))
+    else:
+        col, k0, groups = mesh.colors(), 0, 0
+        for b in wl.blocks:
+            n = len(b.body)
+            groups += len({(int(c), int(m)) for c, m in zip(col[k0:k0 + n], law[b.body])})
+            k0 += n
+    assert groups > len(wl.blocks)            # the mix really splits blocks
+    assert mesh.info["n_passes"] == groups
+    if scatter == 1:
+        dt = mesh.torch_dtype
+        u, ud, v = dev(wl.u, torch.float64), dev(wl.udot, dt), dev(wl.v, dt)
+        y1 = mesh.tangent_matvec(u, ud, v, 0.0, 1.0, 1.0).cpu().numpy()
+        y2 = mesh.tangent_matvec(u, ud, v, 0.0, 1.0, 1.0).cpu().numpy()
+        assert np.array_equal(y1, y2)
+        assert np.array_equal(y1, out["y"].cpu().numpy())
+
+
+def test_single_law_block_is_one_pass():
+    wl = synth.small_beam(cells=(6, 2, 2))
+    tl = T()
+    assert tl.Mesh.from_workload(wl, precision=tl.FP32).info["n_passes"] == 1
+
+
 @pytest.mark.parametrize("path", PATHS)
 @pytest.mark.parametrize("prec", [0, 1])
 def test_per_element_parameters_and_damping(prec, path):
