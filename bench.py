@@ -72,13 +72,12 @@ GRAVITY = (0.0, 0.0, -9.81)
 # the beam workload, Q27 for the q27 workload
 FLOP_PER_QP = {"beam": {"force": 852, "matvec": 1589, "vjp": 1786},
                "q27": {"force": 1932, "matvec": 3026, "vjp": 3567}}
-# batch workload (generic-material kernels, affine path, no damping): FP32 FLOP
-# per point by (element type, law, op), law 0 = SVK, 1 = neo-Hookean; ncu
-# counts of two captures of the timed step (16 and 512 bodies, whose SVK /
-# neo-Hookean mixes differ), solved per law
-FLOP_PER_QP_BATCH = {(0, 0): {"force": 288.5, "matvec": 504.5}, (0, 1): {"force": 361.2, "matvec": 692.2},
-                     (1, 0): {"force": 484.6, "matvec": 874.4}, (1, 1): {"force": 554.7, "matvec": 1056.5},
-                     (2, 0): {"force": 547.0, "matvec": 1035.5}, (2, 1): {"force": 616.3, "matvec": 1216.0}}
+# batch workload (affine path, no damping): FP32 FLOP per point by (element
+# type, law, op), law 0 = SVK, 1 = neo-Hookean; ncu counts (2 FFMA + FADD +
+# FMUL) of the per-law kernels of one timed step of the 512-body batch
+FLOP_PER_QP_BATCH = {(0, 0): {"force": 288.3, "matvec": 503.3}, (0, 1): {"force": 359.3, "matvec": 690.3},
+                     (1, 0): {"force": 483.7, "matvec": 865.7}, (1, 1): {"force": 552.3, "matvec": 1048.3},
+                     (2, 0): {"force": 540.0, "matvec": 942.3}, (2, 1): {"force": 611.4, "matvec": 1124.7}}
 # FP32 FMA roof: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz (maximum SM clock)
 ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
