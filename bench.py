@@ -568,36 +568,78 @@ def run_beam(args, rank, world, workload="beam"):
             "algorithmic_bytes": bytes_alg[j], "hbm_achieved_gbs": hbm, "hbm_peak_gbs": peak,
             "hbm_frac": hbm / peak, "hbm_peak_source": peak_kind}
 
-    # end to end through the public API with host buffers (pinned), copies timed
-    f, y, gu, gud = outs
+    # end to end through the public API with host buffers (pinned), copies
+    # timed: every step copies u, udot and v in and f, K v, g_u, g_udot and
+    # g_theta out. Three streams: host-to-device copies, the compute stream
+    # and device-to-host copies; the next step's inputs come in while this
+    # step computes (two device input sets), and each output goes back as soon
+    # as its operation has finished (two device output sets)
     hu, hud, hv = u.cpu().pin_memory(), ud.cpu().pin_memory(), v.cpu().pin_memory()
     hf, hy, hgu, hgud = (torch.empty(ud.shape, dtype=ud.dtype).pin_memory() for _ in range(4))
     hgth = torch.empty(gth.shape, dtype=torch.float64).pin_memory()
-    du, dud, dv = torch.empty_like(u), torch.empty_like(ud), torch.empty_like(ud)
-    e2e_inner = make_step(mesh, du, dud, dv, outs, gth)
+    ins = [(torch.empty_like(u), torch.empty_like(ud), torch.empty_like(ud)) for _ in range(2)]
+    outs2 = [outs, [torch.empty_like(ud) for _ in range(4)]]
+    gths = [gth, torch.empty_like(gth)]
+    inner = [make_step(mesh, *ins[i], outs2[i], gths[i]) for i in range(2)]
+    h2d_s, d2h_s = torch.cuda.Stream(), torch.cuda.Stream()
+    ev = lambda: torch.cuda.Event()
 
-    def e2e_step():
-        du.copy_(hu, non_blocking=True)
-        dud.copy_(hud, non_blocking=True)
-        dv.copy_(hv, non_blocking=True)
-        e2e_inner()
-        hf.copy_(f, non_blocking=True)
-        hy.copy_(y, non_blocking=True)
-        hgu.copy_(gu, non_blocking=True)
-        hgud.copy_(gud, non_blocking=True)
-        hgth.copy_(gth, non_blocking=True)
+    def e2e_run(n):
+        in_ready, comp_done, out_done = [ev(), ev()], [None, None], [None, None]
 
-    for _ in range(2):
-        e2e_step()
+        def h2d(b):
+            if comp_done[b] is not None:
+                h2d_s.wait_event(comp_done[b])          # the last step that read this input set has ended
+            with torch.cuda.stream(h2d_s):
+                for d, h in zip(ins[b], (hu, hud, hv)):
+                    d.copy_(h, non_blocking=True)
+            in_ready[b].record(h2d_s)
+
+        h2d(0)
+        for k in range(n):
+            b = k & 1
+            stream.wait_event(in_ready[b])
+            if out_done[b] is not None:
+                stream.wait_event(out_done[b])          # the step two back has copied this output set out
+            e = [ev() for _ in range(4)]
+            inner[b](e)
+            comp_done[b] = e[3]
+            if k + 1 < n:
+                h2d(b ^ 1)
+            f_, y_, gu_, gud_ = outs2[b]
+            with torch.cuda.stream(d2h_s):
+                d2h_s.wait_event(e[1])
+                hf.copy_(f_, non_blocking=True)
+                d2h_s.wait_event(e[2])
+                hy.copy_(y_, non_blocking=True)
+                d2h_s.wait_event(e[3])
+                hgu.copy_(gu_, non_blocking=True)
+                hgud.copy_(gud_, non_blocking=True)
+                hgth.copy_(gths[b], non_blocking=True)
+            out_done[b] = ev()
+            out_done[b].record(d2h_s)
+        for o in out_done:
+            if o is not None:
+                stream.wait_event(o)
+
+    e2e_run(2)
     torch.cuda.synchronize()
     barrier(world)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
-        e2e_step()
+    h2d_s.wait_event(e0)
+    e2e_run(args.steps)
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = allmax(e0.elapsed_time(e1) / args.steps, world)
+    st_e2e = mesh.sync()
+    # the host copies against one device-only step on the same inputs (the
+    # atomic scatter's order varies, so within the FP32 bar, not bit for bit)
+    chk = [x.clone().double() for x in (hf, hy, hgu, hgud, hgth)]
+    step()
+    torch.cuda.synchronize()
+    e2e_err = max(float((c - o.cpu().double()).abs().max() / o.cpu().double().abs().max().clamp_min(1e-300))
+                  for c, o in zip(chk, outs + [gth]))
     h2d = u.numel() * 8 + 2 * ud.numel() * 4
     d2h = 4 * ud.numel() * 4 + gth.numel() * 8
     mesh.close()
@@ -624,7 +666,10 @@ def run_beam(args, rank, world, workload="beam"):
         "fp64_plain": {"ms_per_step": ms64, "kernels_ms": {n: float(t) for n, t in zip(names, per64.mean(axis=0))},
                        "speedup_fp32_over_fp64": ms64 / step_ms, "device_status": st64},
         "e2e": {"value": world * units / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
+                "overlap": "copies on their own streams: the next step's inputs are copied in while a step "
+                           "computes, each output is copied out when its operation ends",
+                "max_rel_diff_vs_device_step": e2e_err, "device_status": st_e2e},
         "gpu_launches": 3 * args.steps,
         "clocks": clk.summary(),
         "device_status": st})
