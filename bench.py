@@ -78,6 +78,9 @@ FLOP_PER_QP = {"beam": {"force": 852, "matvec": 1589, "vjp": 1786},
 FLOP_PER_QP_BATCH = {(0, 0): {"force": 288.3, "matvec": 503.3}, (0, 1): {"force": 359.3, "matvec": 690.3},
                      (1, 0): {"force": 483.7, "matvec": 865.7}, (1, 1): {"force": 552.3, "matvec": 1048.3},
                      (2, 0): {"force": 540.0, "matvec": 942.3}, (2, 1): {"force": 611.4, "matvec": 1124.7}}
+# how the end-to-end measurements move data
+OVERLAP = ("copies on their own streams: the next step's inputs are copied in while a step computes (two device "
+           "input sets), outputs are copied out as their operations end (two device output sets)")
 # FP32 FMA roof: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz (maximum SM clock)
 ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
@@ -667,8 +670,7 @@ def run_beam(args, rank, world, workload="beam"):
                        "speedup_fp32_over_fp64": ms64 / step_ms, "device_status": st64},
         "e2e": {"value": world * units / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
-                "overlap": "copies on their own streams: the next step's inputs are copied in while a step "
-                           "computes, each output is copied out when its operation ends",
+                "overlap": OVERLAP,
                 "max_rel_diff_vs_device_step": e2e_err, "device_status": st_e2e},
         "gpu_launches": 3 * args.steps,
         "clocks": clk.summary(),
@@ -814,21 +816,26 @@ def run_batch(args, rank, world):
     flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device="cuda")
     side = torch.cuda.Stream()
     L = tlfe.load()
+    # two buffer sets (u, v, f, y), one graph each: the timed step replays the
+    # first; the end-to-end run alternates them
+    bufs = [(u, v, f, y), (torch.empty_like(u), torch.empty_like(v), torch.empty_like(v), torch.empty_like(v))]
 
-    def calls(s):
+    def calls(s, u_, v_, f_, y_):
         sp = tlfe._stream(s)
-        tlfe._check(L.tlfe_internal_force(mesh.handle, tlfe._ptr(u), None, tlfe._ptr(f), sp))
-        tlfe._check(L.tlfe_tangent_matvec(mesh.handle, tlfe._ptr(u), None, tlfe._ptr(v), 0.0, 1.0, 0.0,
-                                          tlfe._ptr(y), sp))
+        tlfe._check(L.tlfe_internal_force(mesh.handle, tlfe._ptr(u_), None, tlfe._ptr(f_), sp))
+        tlfe._check(L.tlfe_tangent_matvec(mesh.handle, tlfe._ptr(u_), None, tlfe._ptr(v_), 0.0, 1.0, 0.0,
+                                          tlfe._ptr(y_), sp))
 
     mesh.autotune(u, None, v)
     with torch.cuda.stream(side):
         for _ in range(2):
-            calls(side)                      # occupancy and schedule caches filled before capture
+            calls(side, *bufs[0])            # occupancy and schedule caches filled before capture
     torch.cuda.synchronize()
-    g = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g, stream=side):
-        calls(side)
+    graphs = [torch.cuda.CUDAGraph() for _ in range(2)]
+    for gr, bf in zip(graphs, bufs):
+        with torch.cuda.graph(gr, stream=side):
+            calls(side, *bf)
+    g = graphs[0]
     stream = torch.cuda.current_stream()
 
     def step(ev=None):
@@ -860,17 +867,51 @@ def run_batch(args, rank, world):
             f_qp = FLOP_PER_QP_BATCH[(b.etype, law)]
             flops += int((laws == law).sum()) * b.nq * (f_qp["force"] + f_qp["matvec"])
     achieved = flops / (ms * 1e-3) / 1e12
-    # e2e: u and v from pinned host memory, f and K v back
+    # e2e: u and v from pinned host memory, f and K v back, every step; the
+    # copies run on their own streams, overlapped with the other buffer set's
+    # graph replay
     hu, hv = u.cpu().pin_memory(), v.cpu().pin_memory()
     hf, hy = torch.empty_like(hv).pin_memory(), torch.empty_like(hv).pin_memory()
+    h2d_s, d2h_s = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def e2e_run(n):
+        in_ready, comp_done, out_done = [torch.cuda.Event(), torch.cuda.Event()], [None, None], [None, None]
+
+        def h2d(b):
+            if comp_done[b] is not None:
+                h2d_s.wait_event(comp_done[b])          # the last replay that read this set has ended
+            with torch.cuda.stream(h2d_s):
+                bufs[b][0].copy_(hu, non_blocking=True)
+                bufs[b][1].copy_(hv, non_blocking=True)
+            in_ready[b].record(h2d_s)
+
+        h2d(0)
+        for k in range(n):
+            b = k & 1
+            stream.wait_event(in_ready[b])
+            if out_done[b] is not None:
+                stream.wait_event(out_done[b])          # this set's outputs of two steps back are out
+            graphs[b].replay()
+            comp_done[b] = torch.cuda.Event()
+            comp_done[b].record(stream)
+            if k + 1 < n:
+                h2d(b ^ 1)
+            with torch.cuda.stream(d2h_s):
+                d2h_s.wait_event(comp_done[b])
+                hf.copy_(bufs[b][2], non_blocking=True)
+                hy.copy_(bufs[b][3], non_blocking=True)
+            out_done[b] = torch.cuda.Event()
+            out_done[b].record(d2h_s)
+        for o in out_done:
+            if o is not None:
+                stream.wait_event(o)
+
+    e2e_run(2)
+    torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
-        u.copy_(hu, non_blocking=True)
-        v.copy_(hv, non_blocking=True)
-        g.replay()
-        hf.copy_(f, non_blocking=True)
-        hy.copy_(y, non_blocking=True)
+    h2d_s.wait_event(e0)
+    e2e_run(args.steps)
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = allmax(e0.elapsed_time(e1) / args.steps, world)
@@ -890,7 +931,8 @@ def run_batch(args, rank, world):
                      "algorithmic_flops": flops, "algorithmic_bytes": b_alg, "hbm_achieved_gbs": hbm,
                      "hbm_peak_gbs": peak, "hbm_frac": hbm / peak, "hbm_peak_source": peak_kind},
         "e2e": {"value": world * units / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
-                "h2d_bytes_per_step": u.numel() * 8 + v.numel() * 4, "d2h_bytes_per_step": 2 * v.numel() * 4},
+                "h2d_bytes_per_step": u.numel() * 8 + v.numel() * 4, "d2h_bytes_per_step": 2 * v.numel() * 4,
+                "overlap": OVERLAP},
         "gpu_launches": 2 * info["n_passes"] * args.steps,
         "clocks": clk.summary(), "device_status": st})
     mesh.close()
@@ -956,30 +998,61 @@ def run_diff(args, rank, world):
     hbm = b_bwd / (ms_bwd * 1e-3) / 1e9
 
     # end to end: u, udot and the parameters from pinned host memory, the
-    # loss and the three gradients back to the host, every step
+    # loss and the three gradients back to the host, every step. Copies run on
+    # their own streams: the next step's inputs come in while a step computes
+    # (two sets of leaf tensors), the gradients go out when its backward ends
     hu, hud, hth = (t.detach().cpu().pin_memory() for t in (u, ud, theta))
     hgu, hgud, hgth = (torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in (u, ud, theta))
     hloss = torch.empty((), dtype=torch.float64).pin_memory()
+    leaves = [tuple(t.detach().clone().requires_grad_(True) for t in (u, ud, theta)) for _ in range(2)]
+    h2d_s, d2h_s = torch.cuda.Stream(), torch.cuda.Stream()
 
-    def e2e_step():
-        with torch.no_grad():
-            u.copy_(hu, non_blocking=True)
-            ud.copy_(hud, non_blocking=True)
-            theta.copy_(hth, non_blocking=True)
-        step()
-        hgu.copy_(u.grad, non_blocking=True)
-        hgud.copy_(ud.grad, non_blocking=True)
-        hgth.copy_(theta.grad, non_blocking=True)
-        hloss.copy_(losses[-1], non_blocking=True)
+    def e2e_run(n):
+        in_ready, comp_done, out_done = [torch.cuda.Event(), torch.cuda.Event()], [None, None], [None, None]
 
-    for _ in range(2):
-        e2e_step()
+        def h2d(b):
+            if comp_done[b] is not None:
+                h2d_s.wait_event(comp_done[b])          # the last step that read these leaves has ended
+            with torch.cuda.stream(h2d_s), torch.no_grad():
+                for d, h in zip(leaves[b], (hu, hud, hth)):
+                    d.copy_(h, non_blocking=True)
+            in_ready[b].record(h2d_s)
+
+        h2d(0)
+        for k in range(n):
+            b = k & 1
+            stream.wait_event(in_ready[b])
+            if out_done[b] is not None:
+                stream.wait_event(out_done[b])
+            lu, lud, lth = leaves[b]
+            for t in leaves[b]:
+                t.grad = None
+            f = autograd.internal_force(mesh, lu, lud, lth)
+            loss = 0.5 * ((f.double() - f_t) ** 2).sum()
+            loss.backward()
+            comp_done[b] = torch.cuda.Event()
+            comp_done[b].record(stream)
+            if k + 1 < n:
+                h2d(b ^ 1)
+            res = [t.grad for t in leaves[b]] + [loss.detach()]
+            with torch.cuda.stream(d2h_s):
+                d2h_s.wait_event(comp_done[b])
+                for h, g in zip((hgu, hgud, hgth, hloss), res):
+                    h.copy_(g, non_blocking=True)
+                    g.record_stream(d2h_s)                # kept alive until the copy has run
+            out_done[b] = torch.cuda.Event()
+            out_done[b].record(d2h_s)
+        for o in out_done:
+            if o is not None:
+                stream.wait_event(o)
+
+    e2e_run(2)
     torch.cuda.synchronize()
     barrier(world)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
-        e2e_step()
+    h2d_s.wait_event(e0)
+    e2e_run(args.steps)
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = allmax(e0.elapsed_time(e1) / args.steps, world)
@@ -1000,7 +1073,7 @@ def run_diff(args, rank, world):
                      "hbm_peak_source": peak_kind},
         "loss": float(losses[-1].item()),
         "e2e": {"value": world * units / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "overlap": OVERLAP},
         "gpu_launches": 2 * args.steps, "clocks": clk.summary(), "device_status": st})
     mesh.close()
     return line, wl
