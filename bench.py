@@ -402,6 +402,11 @@ def cpu_sample(workload, wl, n_sample):
     return nqp / dt, dt, 1, f"{_sample_text(wl, sub)}, {what}, {dt:.1f} s"
 
 
+def scatter_mode(args):
+    from paper_2602_17002_gb300 import tlfe
+    return tlfe.SCATTER_COLOR if args.scatter == "colour" else tlfe.SCATTER_ATOMIC
+
+
 def build_workload(workload, bodies=512):
     import synth
     if workload == "beam":
@@ -479,7 +484,7 @@ def run_beam(args, rank, world, workload="beam"):
     u = torch.from_numpy(wl.u).to("cuda", torch.float64)   # displacement state: FP64 in both precisions
 
     def make(prec, path=0):
-        mesh = tlfe.Mesh.from_workload(wl, precision=prec, element_path=path)
+        mesh = tlfe.Mesh.from_workload(wl, precision=prec, element_path=path, scatter=scatter_mode(args))
         dt = mesh.torch_dtype
         ud = torch.from_numpy(wl.udot).to("cuda", dt)
         v = torch.from_numpy(wl.v).to("cuda", dt)
@@ -808,7 +813,7 @@ def run_batch(args, rank, world):
 
     from paper_2602_17002_gb300 import tlfe
     wl = build_workload("batch", args.bodies)
-    mesh = tlfe.Mesh.from_workload(wl, precision=tlfe.FP32)
+    mesh = tlfe.Mesh.from_workload(wl, precision=tlfe.FP32, scatter=scatter_mode(args))
     info = mesh.info
     u = torch.from_numpy(wl.u).to("cuda", torch.float64)
     v = torch.from_numpy(wl.v).to("cuda", torch.float32)
@@ -949,7 +954,7 @@ def run_diff(args, rank, world):
 
     from paper_2602_17002_gb300 import autograd, tlfe
     wl = build_workload("diff")
-    mesh = tlfe.Mesh.from_workload(wl, precision=tlfe.FP32)
+    mesh = tlfe.Mesh.from_workload(wl, precision=tlfe.FP32, scatter=scatter_mode(args))
     info = mesh.info
     u = torch.from_numpy(wl.u).to("cuda", torch.float64).requires_grad_(True)
     ud = torch.from_numpy(wl.udot).to("cuda", torch.float32).requires_grad_(True)
@@ -1090,6 +1095,10 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=40000, help="elements in the cpu_baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--bodies", type=int, default=512, help="bodies in the batch workload (512 = the benchmark)")
+    ap.add_argument("--scatter", default="atomic", choices=["atomic", "colour"],
+                    help="element scatter of the beam, q27, batch and diff meshes: atomic adds, or deterministic "
+                         "colour passes")
+    ap.add_argument("--log", default=None, help="also append the JSON line to this file (JSON lines)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -1117,8 +1126,13 @@ def main():
                                     "sample": pwhat, "single_core": base}
         else:
             line["cpu_baseline"] = base
+    if args.scatter != "atomic" and args.workload != "newton":
+        line["config"]["scatter"] = args.scatter
     if rank == 0:
         print(json.dumps(line), flush=True)
+        if args.log:
+            with open(args.log, "a") as fh:
+                fh.write(json.dumps(dict(line, argv=sys.argv[1:], time=time.strftime("%Y-%m-%dT%H:%M:%S"))) + "\n")
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
