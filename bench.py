@@ -404,7 +404,7 @@ def cpu_sample(workload, wl, n_sample):
 
 def scatter_mode(args):
     from paper_2602_17002_gb300 import tlfe
-    return tlfe.SCATTER_COLOR if args.scatter == "colour" else tlfe.SCATTER_ATOMIC
+    return {"atomic": tlfe.SCATTER_ATOMIC, "colour": tlfe.SCATTER_COLOR, "sorted": tlfe.SCATTER_SORTED}[args.scatter]
 
 
 def build_workload(workload, bodies=512):
@@ -1095,9 +1095,9 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=40000, help="elements in the cpu_baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--bodies", type=int, default=512, help="bodies in the batch workload (512 = the benchmark)")
-    ap.add_argument("--scatter", default="atomic", choices=["atomic", "colour"],
-                    help="element scatter of the beam, q27, batch and diff meshes: atomic adds, or deterministic "
-                         "colour passes")
+    ap.add_argument("--scatter", default="atomic", choices=["atomic", "colour", "sorted"],
+                    help="element scatter of the beam, q27, batch and diff meshes: atomic adds, deterministic "
+                         "colour passes, or deterministic node-ordered partial sums")
     ap.add_argument("--log", default=None, help="also append the JSON line to this file (JSON lines)")
     args = ap.parse_args()
     if args.warmup < 3:

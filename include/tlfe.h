@@ -38,7 +38,10 @@
  *     the next tlfe_sync (or by calls documented as synchronising).
  *   - No call aborts, traps or exits; errors are returned as tlfe_status and a
  *     thread-local message is available from tlfe_last_error().
- *   - A mesh handle may be used from one host thread at a time.
+ *   - A mesh handle may be used from one host thread at a time. Operations on
+ *     one handle share its workspaces (staging buffers, the Newton state, the
+ *     partial sums of TLFE_SCATTER_SORTED): issue them in one stream, or order
+ *     streams with events, so that they do not run concurrently.
  */
 #ifndef TLFE_H
 #define TLFE_H
@@ -65,7 +68,16 @@ typedef enum {
 enum { TLFE_T4 = 0, TLFE_T10 = 1, TLFE_H8 = 2, TLFE_Q27 = 3 };  /* element types (App. A; T4/H8 textbook) */
 enum { TLFE_SVK = 0, TLFE_NEOHOOKE = 1, TLFE_MOONEY_RIVLIN = 2 };  /* elastic laws (Sec. 3.2, App. C) */
 enum { TLFE_FP64 = 0, TLFE_FP32 = 1 };              /* element arithmetic */
-enum { TLFE_SCATTER_ATOMIC = 0, TLFE_SCATTER_COLOR = 1 };
+/* How element contributions are summed into the node arrays:
+ *   TLFE_SCATTER_ATOMIC : per tile, one atomic add per unique node and
+ *                         component (fastest; summation order not fixed)
+ *   TLFE_SCATTER_COLOR  : colour passes (no two elements of a pass share a
+ *                         node) with plain read-add-write; deterministic
+ *   TLFE_SCATTER_SORTED : every tile stores its per-node sums to a partial
+ *                         buffer, then one thread per node adds that node's
+ *                         partials in a fixed order; deterministic, and
+ *                         close to the atomic mode in speed */
+enum { TLFE_SCATTER_ATOMIC = 0, TLFE_SCATTER_COLOR = 1, TLFE_SCATTER_SORTED = 2 };
 /* Where the element kernels take the reference gradients h_i from:
  *   TLFE_PATH_AUTO   : affine blocks (every T4; straight-edged T10;
  *                      parallelepiped H8 and Q27 with evenly spaced nodes)
@@ -118,8 +130,9 @@ typedef struct {
     const tlfe_material *body_mat;  /* host [n_bodies] */
     const double *elem_mu_lambda;   /* host [n_elem_total][2] per-element (mu, lambda), or NULL */
     int32_t precision;              /* TLFE_FP32 or TLFE_FP64 */
-    int32_t scatter;                /* TLFE_SCATTER_ATOMIC (fast, order not fixed) or
-                                       TLFE_SCATTER_COLOR (deterministic colour passes) */
+    int32_t scatter;                /* TLFE_SCATTER_ATOMIC (fast, order not fixed),
+                                       TLFE_SCATTER_COLOR (deterministic colour passes) or
+                                       TLFE_SCATTER_SORTED (deterministic node-ordered partial sums) */
     uint64_t color_seed;            /* priority seed of the conflict colouring */
     int32_t element_path;           /* TLFE_PATH_AUTO, TLFE_PATH_SLAB or TLFE_PATH_AFFINE */
 } tlfe_mesh_desc;

@@ -79,7 +79,7 @@ static tlfe_status validate(const tlfe_mesh_desc *d)
     if (d->n_blocks <= 0 || !d->blocks) return fail(TLFE_E_INVALID, "n_blocks must be > 0 and blocks non-NULL");
     if (d->n_bodies <= 0 || !d->body_mat) return fail(TLFE_E_INVALID, "n_bodies must be > 0 and body_mat non-NULL");
     if (d->precision != TLFE_FP32 && d->precision != TLFE_FP64) return fail(TLFE_E_INVALID, "bad precision");
-    if (d->scatter != TLFE_SCATTER_ATOMIC && d->scatter != TLFE_SCATTER_COLOR)
+    if (d->scatter != TLFE_SCATTER_ATOMIC && d->scatter != TLFE_SCATTER_COLOR && d->scatter != TLFE_SCATTER_SORTED)
         return fail(TLFE_E_INVALID, "bad scatter mode");
     if (d->element_path != TLFE_PATH_AUTO && d->element_path != TLFE_PATH_SLAB && d->element_path != TLFE_PATH_AFFINE)
         return fail(TLFE_E_INVALID, "bad element path");
@@ -407,7 +407,9 @@ static tlfe_status build_block(tlfe_mesh *m, const tlfe_mesh_desc *d, int bi, in
     B.n_unique = (int64_t)tnodes.size();
 
     // one fixed-size metadata record per tile, fetched by one bulk copy:
-    //   [U, 0, 0, 0 | eid[32] | node ids[umaxp] | lidx[npe][32] | position[npe*32] | soff[soffp]]
+    //   [U, P, 0, 0 | eid[32] | node ids[umaxp] | lidx[npe][32] | position[npe*32] | soff[soffp]]
+    // with P the tile's first partial-sum position (sorted scatter)
+    const int64_t part_base = (int64_t)m->h_part_node.size();
     const int umaxp = (B.umax + 3) / 4 * 4;
     const int soffp = (B.umax + 1 + 7) / 8 * 8;
     B.meta_bytes = 16 + 4 * TILE + 4 * umaxp + 2 * 2 * npe * TILE + 2 * soffp;
@@ -420,6 +422,7 @@ static tlfe_status build_block(tlfe_mesh *m, const tlfe_mesh_desc *d, int bi, in
             const int U = toff[t + 1] - toff[t];
             int32_t *hdr = (int32_t *)r;
             hdr[0] = U;
+            hdr[1] = (int32_t)std::min<int64_t>(INT32_MAX, part_base + toff[t]);
             memcpy(r + 16, eid.data() + (size_t)t * TILE, 4 * TILE);
             memcpy(r + 16 + 4 * TILE, tnodes.data() + toff[t], 4 * (size_t)U);
             unsigned char *q = r + 16 + 4 * TILE + 4 * umaxp;
@@ -538,6 +541,23 @@ static tlfe_status build_block(tlfe_mesh *m, const tlfe_mesh_desc *d, int bi, in
     }
     cudaFree(d_aflag);
     if (e != cudaSuccess) return cuda_fail(e, "reference precompute");
+
+    // sorted scatter: the node of each of this block's partial-sum positions,
+    // in the order the kernels store them (tile node lists, or 27 per slot on
+    // the warp-per-element path)
+    if (d->scatter == TLFE_SCATTER_SORTED) {
+        std::vector<int32_t> &pn = m->h_part_node;
+        B.part_base = part_base;
+        if (wpe_path(B.et, B.use_affine)) {
+            for (size_t k = 0; k < eid.size(); ++k)
+                for (int i = 0; i < npe; ++i)
+                    pn.push_back(eid[k] < 0 ? -1 : b.conn[(int64_t)(eid[k] - elem_base) * npe + i]);
+        } else {
+            pn.insert(pn.end(), tnodes.begin(), tnodes.end());
+        }
+        if (pn.size() > (size_t)INT32_MAX)
+            return fail(TLFE_E_UNSUPPORTED, "sorted scatter: more than 2^31 partial sums");
+    }
     return TLFE_OK;
 }
 
@@ -612,6 +632,29 @@ extern "C" tlfe_status tlfe_create_mesh(const tlfe_mesh_desc *desc, void *stream
         m->n_qp += (int64_t)desc->blocks[bi].n_elem * desc->blocks[bi].n_qp;
     }
     m->n_elem = base;
+    if (m->scatter == TLFE_SCATTER_SORTED) {
+        // transpose of the position -> node map: for each node its positions in
+        // ascending order, which fixes the order of its sum
+        const std::vector<int32_t> &pn = m->h_part_node;
+        m->n_part = (int64_t)pn.size();
+        std::vector<int64_t> ptr((size_t)m->n_nodes + 1, 0);
+        for (int32_t n : pn)
+            if (n >= 0) ptr[(size_t)n + 1]++;
+        for (int n = 0; n < m->n_nodes; ++n) ptr[n + 1] += ptr[n];
+        std::vector<int32_t> pos((size_t)std::max<int64_t>(1, ptr[m->n_nodes]));
+        std::vector<int64_t> fill(ptr.begin(), ptr.end() - 1);
+        for (int64_t k = 0; k < m->n_part; ++k)
+            if (pn[k] >= 0) pos[fill[pn[k]]++] = (int32_t)k;
+        const size_t rs = m->precision == TLFE_FP32 ? 4 : 8;
+        m->d_part_ptr = (int64_t *)dalloc(m, sizeof(int64_t) * ptr.size(), &ae);
+        m->d_part_pos = (int32_t *)dalloc(m, sizeof(int32_t) * pos.size(), &ae);
+        m->d_part = dalloc(m, rs * 2 * 3 * (size_t)std::max<int64_t>(1, m->n_part), &ae);
+        if (ae != cudaSuccess) return bail(cuda_fail(ae, "cudaMalloc (sorted scatter)"));
+        CKM(cudaMemcpy(m->d_part_ptr, ptr.data(), sizeof(int64_t) * ptr.size(), cudaMemcpyHostToDevice));
+        CKM(cudaMemcpy(m->d_part_pos, pos.data(), sizeof(int32_t) * pos.size(), cudaMemcpyHostToDevice));
+        m->h_part_node.clear();
+        m->h_part_node.shrink_to_fit();
+    }
     int h_status[ST_COUNT];
     CKM(cudaMemcpy(h_status, m->d_status, sizeof(h_status), cudaMemcpyDeviceToHost));
     if (h_status[ST_INVERTED] > 0)
@@ -746,6 +789,7 @@ template <typename R> static void block_params(tlfe_mesh *m, const BlockStore &B
     p.mats = B.d_emat ? mats_of<R>(m) : nullptr;
     p.mat0 = to_mat<R>(m->h_mats[B.uniform_body >= 0 ? B.uniform_body : 0]);
     p.status = m->d_status;
+    p.part_base = B.part_base;
 }
 
 // the launch schedule of (OP, block bi): from the cache, else from the occupancy API
@@ -810,6 +854,22 @@ static tlfe_status run_block_op(tlfe_mesh *m, int bi, KParams<R> p, cudaStream_t
     return launch_block<OP, R>(m, bi, p, s);
 }
 
+// sorted scatter, second half: out[n] = sum of node n's partials in ascending
+// position order (one thread per node and component: a fixed order, so the
+// result repeats bit for bit); nodes in no element get 0
+template <typename R>
+__global__ void k_node_sum(int64_t n3, const int64_t *__restrict__ ptr, const int32_t *__restrict__ pos,
+                           const R *__restrict__ part, R *__restrict__ out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t n = i / 3;
+        const int c = (int)(i - 3 * n);
+        R a = R(0);
+        for (int64_t k = ptr[n]; k < ptr[n + 1]; ++k) a += part[(int64_t)pos[k] * 3 + c];
+        out[i] = a;
+    }
+}
+
 template <int OP, typename R>
 tlfe_status run_op(tlfe_mesh *m, const void *u, const void *ud, const void *v, void *out0, void *out1,
                    double *gth, double aM, double aK, double aC, int sym_only, cudaStream_t s)
@@ -828,12 +888,32 @@ tlfe_status run_op(tlfe_mesh *m, const void *u, const void *ud, const void *v, v
     p.sym_only = sym_only;
     p.mass_only = (OP == OP_MATVEC && aK == 0.0 && aC == 0.0) ? 1 : 0;
     const size_t nb = sizeof(R) * 3 * (size_t)m->n_nodes;
-    if (out0) CK(cudaMemsetAsync(out0, 0, nb, s));
-    if (out1) CK(cudaMemsetAsync(out1, 0, nb, s));
+    const bool sorted = m->scatter == TLFE_SCATTER_SORTED;
+    if (sorted) {
+        if (sizeof(R) != (m->precision == TLFE_FP32 ? 4u : 8u))
+            return fail(TLFE_E_UNSUPPORTED, "sorted scatter: operation precision differs from the mesh's");
+        p.part0 = (R *)m->d_part;
+        p.part1 = p.part0 + 3 * std::max<int64_t>(1, m->n_part);
+    } else {
+        if (out0) CK(cudaMemsetAsync(out0, 0, nb, s));
+        if (out1) CK(cudaMemsetAsync(out1, 0, nb, s));
+    }
     for (int bi = 0; bi < (int)m->blocks.size(); ++bi) {
         if (m->blocks[bi].n_elem == 0) continue;
         tlfe_status st = run_block_op<OP, R>(m, bi, p, s);
         if (st != TLFE_OK) return st;
+    }
+    if (sorted) {
+        const int64_t n3 = 3 * (int64_t)m->n_nodes;
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n3 + 255) / 256, (int64_t)m->n_sm * 16));
+        R *outs[2] = {(R *)out0, (R *)out1};
+        for (int fo = 0; fo < 2; ++fo) {
+            if (!outs[fo] || n3 == 0) continue;
+            k_node_sum<R><<<grid, 256, 0, s>>>(n3, m->d_part_ptr, m->d_part_pos, fo == 0 ? p.part0 : p.part1,
+                                                outs[fo]);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return cuda_fail(e, "k_node_sum launch");
+        }
     }
     return TLFE_OK;
 }
@@ -914,6 +994,10 @@ static tlfe_status tune_all(tlfe_mesh *m, const double *u, const void *ud, const
     p.v = (const R *)v;
     p.out0 = (R *)o0;
     p.out1 = (R *)o1;
+    if (m->scatter == TLFE_SCATTER_SORTED && sizeof(R) == (m->precision == TLFE_FP32 ? 4u : 8u)) {
+        p.part0 = (R *)m->d_part;   // time the kernels as they run: storing tile partials
+        p.part1 = p.part0 + 3 * std::max<int64_t>(1, m->n_part);
+    }
     p.gth = gth;
     p.aK = R(1);
     p.aC = R(1);

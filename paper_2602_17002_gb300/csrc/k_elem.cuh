@@ -702,10 +702,11 @@ __global__ void __launch_bounds__(128, min_ctas<ET, R, OP, AFF>()) k_elem(const 
         // ---- per output field: each lane writes its element vector into the
         // node-sorted position array (the patch is dead now), then one lane per
         // unique node sums that node's contiguous positions and adds the sum
-        // to the global array
+        // to the global array (sorted scatter: stores it as the tile's partial)
 #pragma unroll
         for (int fo = 0; fo < NFO; ++fo) {
             R *out = fo == 0 ? p.out0 : p.out1;
+            R *part = fo == 0 ? p.part0 : p.part1;
             __syncwarp();
             if (valid) {
 #pragma unroll
@@ -729,7 +730,12 @@ __global__ void __launch_bounds__(128, min_ctas<ET, R, OP, AFF>()) k_elem(const 
                             a2 += work[(sb + j) * 3 + 2];
                         }
                 }
-                if (p.rmw_scatter) {
+                if (part) {  // word 1 of the record: the tile's first partial position
+                    R *dst = part + ((int64_t)reinterpret_cast<const int32_t *>(M)[1] + kk) * 3;
+                    dst[0] = a0;
+                    dst[1] = a1;
+                    dst[2] = a2;
+                } else if (p.rmw_scatter) {
                     out[3 * n] += a0;
                     out[3 * n + 1] += a1;
                     out[3 * n + 2] += a2;

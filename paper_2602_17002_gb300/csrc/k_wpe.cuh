@@ -302,8 +302,14 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 2) k_wpe_q27(const K
 #pragma unroll
             for (int fo = 0; fo < OpFields<OP>::NFO; ++fo) {
                 R *out = fo == 0 ? p.out0 : p.out1;
+                R *part = fo == 0 ? p.part0 : p.part1;
                 const R *a3 = fo == 0 ? acc0 : acc1;
-                if (p.rmw_scatter) {
+                if (part) {  // sorted scatter: this element's partial for node n
+                    R *dst = part + (int64_t)((int)p.part_base + s * 27 + n) * 3;  // positions < 2^31
+                    dst[0] = a3[0];
+                    dst[1] = a3[1];
+                    dst[2] = a3[2];
+                } else if (p.rmw_scatter) {
                     out[3 * node] += a3[0];
                     out[3 * node + 1] += a3[1];
                     out[3 * node + 2] += a3[2];

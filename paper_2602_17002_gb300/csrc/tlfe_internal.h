@@ -38,7 +38,8 @@ template <typename R> struct KParams {
     const int32_t *tnodes;      // sorted unique global node ids of each tile
     const uint16_t *lidx;       // [n_tiles][npe][32] index of (elem, node) into the tile's list
     // per-tile metadata records of meta_bytes each (16-byte multiple):
-    //   int32 U, 3 x pad | int32 eid[32] | int32 node id[umaxp] | u16 lidx[npe][32] |
+    //   int32 U, int32 first partial position (sorted scatter), 2 x pad |
+    //   int32 eid[32] | int32 node id[umaxp] | u16 lidx[npe][32] |
     //   u16 position[npe * 32] (slot i * 32 + lane -> its place in the node-sorted order) |
     //   u16 node offsets[U + 1] into that order (padded)
     const unsigned char *meta;
@@ -63,6 +64,13 @@ template <typename R> struct KParams {
     int sym_only;
     int mass_only;              // operator product with a_K = a_C = 0: no quadrature loop, no slab stream
     int rmw_scatter;            // 1: plain read-add-write (colour passes), 0: atomics
+    // sorted scatter (part0 != nullptr): per-node tile sums are stored to
+    // part{0,1}[position * 3 + c] instead of being added, with position
+    // part_base + toff[t] + k for unique node k of tile t (tile kernels: the
+    // record header holds part_base + toff[t]) or part_base + slot * 27 + n
+    // (warp-per-element kernels)
+    R *part0, *part1;
+    int64_t part_base;
     int visc;                   // udot given and material damped somewhere in the block
     int mat_mode;               // MAT_* (compile-time material of the launched kernel)
     int tile_chunk;             // 1: each warp takes a contiguous run of tiles; 0: interleaved

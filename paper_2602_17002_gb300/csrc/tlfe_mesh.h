@@ -48,6 +48,7 @@ struct BlockStore {
     void *d_slab = nullptr, *d_evol = nullptr, *d_elam = nullptr;
     void *d_aff = nullptr;           // [n_tiles][10][32] J^{-1}, det J (affine path)
     int32_t *d_conn = nullptr;       // [n_elem][npe] global node ids (block element order)
+    int64_t part_base = 0;           // sorted scatter: first partial-sum position of the block
 };
 
 }  // namespace tlfe
@@ -81,6 +82,15 @@ struct tlfe_mesh {
     // warps per SM at `wpb` warps per CTA, and the tile assignment; filled from
     // the occupancy API on first use, replaced by measurement in tlfe_autotune
     std::map<std::tuple<int, int, int, int>, tlfe::LaunchSched> sched;
+    // sorted scatter: the node of every partial-sum position (-1: unused),
+    // filled block by block at creation; its transpose (positions of node n
+    // in ascending order: part_pos[part_ptr[n] .. part_ptr[n + 1])) and the
+    // two partial buffers [2][n_part][3] in the mesh precision
+    std::vector<int32_t> h_part_node;
+    int64_t n_part = 0;
+    int64_t *d_part_ptr = nullptr;
+    int32_t *d_part_pos = nullptr;
+    void *d_part = nullptr;
 };
 
 namespace tlfe {

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libtlfe.so")
 T4, T10, H8, Q27 = 0, 1, 2, 3
 SVK, NEOHOOKE, MOONEY_RIVLIN = 0, 1, 2
 FP64, FP32 = 0, 1
-SCATTER_ATOMIC, SCATTER_COLOR = 0, 1
+SCATTER_ATOMIC, SCATTER_COLOR, SCATTER_SORTED = 0, 1, 2
 PATH_AUTO, PATH_SLAB, PATH_AFFINE = 0, 1, 2
 
 STATUS = {0: "TLFE_OK", 1: "TLFE_E_INVALID", 2: "TLFE_E_OOM", 3: "TLFE_E_CUDA", 4: "TLFE_E_INVERTED",

@@ -162,14 +162,17 @@ def _run(mesh, wl, u, v, steps):
     return u, v
 
 
-def test_checkpoint_restart_is_bit_exact_in_colour_mode(tmp_path):
+@pytest.mark.parametrize("mode", ["colour", "sorted"])
+def test_checkpoint_restart_is_bit_exact_in_colour_mode(tmp_path, mode):
     """Run 4 steps, checkpointing after 2 (save_checkpoint); a fresh mesh that
     resumes from the file (load_checkpoint) reproduces steps 3 and 4 bit for
-    bit: colour passes scatter without atomics and the CG reductions are
-    fixed-order."""
+    bit in both deterministic scatter modes: colour passes scatter without
+    atomics, the sorted mode sums each node's tile partials in a fixed order,
+    and the CG reductions are fixed-order."""
     tl = T()
+    scatter = tl.SCATTER_COLOR if mode == "colour" else tl.SCATTER_SORTED
     wl = beams(2, [4, 6], clamp=True, damping=1e3)
-    mesh = tl.Mesh.from_workload(wl, precision=tl.FP32, scatter=tl.SCATTER_COLOR)
+    mesh = tl.Mesh.from_workload(wl, precision=tl.FP32, scatter=scatter)
     z = torch.zeros((wl.n_nodes, 3), dtype=torch.float64, device="cuda")
     u2, v2 = _run(mesh, wl, z, z.clone(), 2)
     path = str(tmp_path / "state.npz")
@@ -179,7 +182,7 @@ def test_checkpoint_restart_is_bit_exact_in_colour_mode(tmp_path):
     ck = tl.load_checkpoint(path)
     assert ck["step"] == 2 and ck["meta"]["h"] == H and ck["meta"]["seed"] == 5 and ck["lam"] is None
     assert torch.equal(ck["u"], u2) and torch.equal(ck["v"], v2)
-    fresh = tl.Mesh.from_workload(wl, precision=tl.FP32, scatter=tl.SCATTER_COLOR)
+    fresh = tl.Mesh.from_workload(wl, precision=tl.FP32, scatter=scatter)
     u4b, v4b = _run(fresh, wl, ck["u"], ck["v"], 2)
     assert torch.equal(u4b, u4) and torch.equal(v4b, v4)
     assert float(v4.abs().max()) > 0.0

@@ -187,6 +187,21 @@ def test_q27_per_element_parameters_and_materials(prec, kind):
     check_all(wl, out, prec, aM=1.0 / h, aK=h, aC=1.0)
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_q27_sorted_scatter(prec):
+    """Sorted scatter on the warp-per-element path (27 partials per element)
+    beside tile-kernel blocks: parity with the oracle and bit-exact repeats."""
+    wl = _q27_variants("mats")
+    tl = T()
+    h = 1e-3
+    mesh, out = run_all(wl, prec, scatter=tl.SCATTER_SORTED, aM=1.0 / h, aK=h, aC=1.0)
+    check_all(wl, out, prec, aM=1.0 / h, aK=h, aC=1.0)
+    dt = mesh.torch_dtype
+    u, ud, v = _cuda(wl.u, torch.float64), _cuda(wl.udot, dt), _cuda(wl.v, dt)
+    assert torch.equal(mesh.internal_force(u, ud), out["f"])
+    assert torch.equal(mesh.tangent_matvec(u, ud, v, 1.0 / h, h, 1.0), out["y"])
+
+
 def test_q27_colour_scatter_and_mass_only():
     """Colour passes (plain read-add-write scatter) on the warp-per-element
     path, and the operator product with a_K = a_C = 0 (mass only)."""
