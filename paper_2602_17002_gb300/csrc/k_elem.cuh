@@ -702,11 +702,11 @@ __global__ void __launch_bounds__(128, min_ctas<ET, R, OP, AFF>()) k_elem(const 
         // ---- per output field: each lane writes its element vector into the
         // node-sorted position array (the patch is dead now), then one lane per
         // unique node sums that node's contiguous positions and adds the sum
-        // to the global array (sorted scatter: stores it as the tile's partial)
-#pragma unroll
-        for (int fo = 0; fo < NFO; ++fo) {
-            R *out = fo == 0 ? p.out0 : p.out1;
-            R *part = fo == 0 ? p.part0 : p.part1;
+        // to the global array. The sorted scatter stores the sum as the tile's
+        // partial instead (word 1 of the record: the tile's first partial
+        // position); it runs as its own copy of the loop, so that the adding
+        // path compiles as it does without it.
+        auto slots_in = [&](int fo) {
             __syncwarp();
             if (valid) {
 #pragma unroll
@@ -717,32 +717,51 @@ __global__ void __launch_bounds__(128, min_ctas<ET, R, OP, AFF>()) k_elem(const 
                 }
             }
             __syncwarp();
-            for (int kk = lane; kk < U; kk += 32) {
-                const int64_t n = nodes[kk];
-                const int s0 = soff[kk], s1e = soff[kk + 1];
-                R a0 = R(0), a1 = R(0), a2 = R(0);
-                for (int sb = s0; sb < s1e; sb += 4) {
+        };
+        auto node_sum = [&](int kk, R &a0, R &a1, R &a2) {
+            const int s0 = soff[kk], s1e = soff[kk + 1];
+            a0 = a1 = a2 = R(0);
+            for (int sb = s0; sb < s1e; sb += 4) {
 #pragma unroll
-                    for (int j = 0; j < 4; ++j)
-                        if (sb + j < s1e) {
-                            a0 += work[(sb + j) * 3 + 0];
-                            a1 += work[(sb + j) * 3 + 1];
-                            a2 += work[(sb + j) * 3 + 2];
-                        }
+                for (int j = 0; j < 4; ++j)
+                    if (sb + j < s1e) {
+                        a0 += work[(sb + j) * 3 + 0];
+                        a1 += work[(sb + j) * 3 + 1];
+                        a2 += work[(sb + j) * 3 + 2];
+                    }
+            }
+        };
+        if (p.part0) {
+#pragma unroll
+            for (int fo = 0; fo < NFO; ++fo) {
+                slots_in(fo);
+                R *dst = (fo == 0 ? p.part0 : p.part1) + (int64_t)reinterpret_cast<const int32_t *>(M)[1] * 3;
+                for (int kk = lane; kk < U; kk += 32) {
+                    R a0, a1, a2;
+                    node_sum(kk, a0, a1, a2);
+                    dst[kk * 3] = a0;
+                    dst[kk * 3 + 1] = a1;
+                    dst[kk * 3 + 2] = a2;
                 }
-                if (part) {  // word 1 of the record: the tile's first partial position
-                    R *dst = part + ((int64_t)reinterpret_cast<const int32_t *>(M)[1] + kk) * 3;
-                    dst[0] = a0;
-                    dst[1] = a1;
-                    dst[2] = a2;
-                } else if (p.rmw_scatter) {
-                    out[3 * n] += a0;
-                    out[3 * n + 1] += a1;
-                    out[3 * n + 2] += a2;
-                } else {
-                    atomicAdd(out + 3 * n, a0);
-                    atomicAdd(out + 3 * n + 1, a1);
-                    atomicAdd(out + 3 * n + 2, a2);
+            }
+        } else {
+#pragma unroll
+            for (int fo = 0; fo < NFO; ++fo) {
+                R *out = fo == 0 ? p.out0 : p.out1;
+                slots_in(fo);
+                for (int kk = lane; kk < U; kk += 32) {
+                    const int64_t n = nodes[kk];
+                    R a0, a1, a2;
+                    node_sum(kk, a0, a1, a2);
+                    if (p.rmw_scatter) {
+                        out[3 * n] += a0;
+                        out[3 * n + 1] += a1;
+                        out[3 * n + 2] += a2;
+                    } else {
+                        atomicAdd(out + 3 * n, a0);
+                        atomicAdd(out + 3 * n + 1, a1);
+                        atomicAdd(out + 3 * n + 2, a2);
+                    }
                 }
             }
         }
