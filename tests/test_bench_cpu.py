@@ -1,0 +1,63 @@
+"""Host-side logic of bench.py (no GPU): the kernel-source hash that keys the
+committed ncu traffic figures, the per-law FLOP table of the batch workload,
+and the command line."""
+
+import os
+import subprocess
+import sys
+
+import numpy as np
+
+import bench
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_comment_stripping_keeps_code_and_literals():
+    src = ('int a = 1; // trailing note\n'
+           '/* block\n   comment */ float b = 2.0f;\n'
+           'const char *s = "a // not a comment /* nor this */";\n'
+           "char c = '/';\n\n\n"
+           'return a; /* one */ /* two */\n')
+    out = bench._strip_comments(src)
+    assert "trailing note" not in out and "block" not in out and "one" not in out
+    assert 'int a = 1;' in out and 'float b = 2.0f;' in out and 'return a;' in out
+    assert '"a // not a comment /* nor this */"' in out
+    assert "'/'" in out
+    assert "\n\n" not in out                      # blank lines dropped
+
+
+def test_comment_only_edits_keep_the_stripped_text():
+    a = "x = y + z; // sum\n/* about it */\nw = 2 * x;\n"
+    b = "x = y + z;   // the sum, reworded\n\n// a new comment line\nw = 2 * x;  /* more */\n"
+    c = "x = y - z; // sum\nw = 2 * x;\n"
+    assert bench._strip_comments(a) == bench._strip_comments(b)
+    assert bench._strip_comments(a) != bench._strip_comments(c)
+
+
+def test_kernel_source_hash_is_stable_and_covers_existing_files():
+    csrc = os.path.join(ROOT, "paper_2602_17002_gb300", "csrc")
+    for name in bench.KERNEL_SOURCES:
+        assert os.path.exists(os.path.join(csrc, name)), name
+    h1, h2 = bench.kernel_source_hash(), bench.kernel_source_hash()
+    assert h1 == h2 and len(h1) == 16
+
+
+def test_batch_flop_table_covers_every_type_and_law():
+    wl = synth.batch_bodies(n_bodies=24, seed=3)
+    law = np.asarray(wl.model)
+    for b in wl.blocks:
+        for lw in np.unique(law[b.body]):
+            ent = bench.FLOP_PER_QP_BATCH[(b.etype, int(lw))]
+            assert 0 < ent["force"] < ent["matvec"]
+
+
+def test_command_line_lists_the_workloads_and_modes():
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--help"], capture_output=True,
+                         text=True, timeout=120)
+    assert out.returncode == 0
+    for flag in ("--workload", "--scatter", "--bodies", "--log", "--impl", "--steps", "--warmup", "--gpus"):
+        assert flag in out.stdout
+    for mode in ("atomic", "colour", "sorted"):
+        assert mode in out.stdout
