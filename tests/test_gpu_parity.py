@@ -173,6 +173,22 @@ def test_sorted_scatter_leaves_nodes_outside_elements_at_zero():
             assert not out[k].cpu().numpy()[unused].any(), k
 
 
+@pytest.mark.parametrize("scatter", [0, 1, 2])
+def test_blocks_sharing_nodes(scatter):
+    """One body split into two blocks that share the nodes of their interface:
+    every scatter mode (atomic, colour, sorted) sums both blocks there."""
+    base = synth.small_beam(cells=(6, 2, 2))
+    blk = base.blocks[0]
+    h = blk.n_elem // 2
+    wl = Workload("split", base.X, [Block(blk.etype, blk.nq, blk.conn[:h], blk.body[:h]),
+                                    Block(blk.etype, blk.nq, blk.conn[h:], blk.body[h:])],
+                  base.model, base.params, u=base.u, udot=base.udot, v=base.v)
+    assert np.intersect1d(blk.conn[:h], blk.conn[h:]).size > 0
+    for prec in (0, 1):
+        _, out = run_all(wl, prec, scatter=scatter, aK=1.0, aC=1.0)
+        check_all(wl, out, prec, aK=1.0, aC=1.0)
+
+
 def test_single_law_block_is_one_pass():
     wl = synth.small_beam(cells=(6, 2, 2))
     tl = T()
