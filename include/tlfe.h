@@ -170,6 +170,20 @@ tlfe_status tlfe_get_mesh_info(const tlfe_mesh *mesh, tlfe_mesh_info *info);
  * the mesh was not coloured. Synchronises. */
 tlfe_status tlfe_get_colors(const tlfe_mesh *mesh, int32_t *colors_host);
 
+/* Gather and scatter indices of the element kernels (the assembly of Sec.
+ * 4.3: f_i of element e is added into the node conn[e][i]), read back from the
+ * device tables the kernels use: the per-tile metadata records (unique-node
+ * list, local indices, node-sorted positions), the partial-sum transpose of
+ * TLFE_SCATTER_SORTED, and the connectivity of warp-per-element blocks.
+ * gather_host[k] receives the node whose values the kernels load for local
+ * node i of element e, scatter_host[k] the node whose entries
+ * 3 node + d (d = 0, 1, 2) receive that local node's contribution, with
+ * k = (offset of e's block) + (e's index in the block) * nodes + i and blocks
+ * in creation order (host int32 arrays of sum over blocks of n_elem * nodes;
+ * either may be NULL). A correct mesh gives conn[e][i] in both. Allocates
+ * and frees scratch; synchronises the device. */
+tlfe_status tlfe_get_scatter_targets(const tlfe_mesh *mesh, int32_t *gather_host, int32_t *scatter_host);
+
 /* Wait for `stream`, read and clear the device status word.
  * n_inverted (nullable) receives the number of quadrature points that met
  * J <= 0 since the last sync. Returns TLFE_E_INVERTED / TLFE_E_NONFINITE when
@@ -384,10 +398,15 @@ tlfe_status tlfe_body_norms(tlfe_mesh *mesh, const double *x_dev, double *out_de
  * limit): the partial sums live in a fixed 32 KiB array in device memory that
  * every GPU loading the library holds until the process exits.
  * Allocates nothing (no cudaMalloc, cudaFree or allocating library routine).
- * The first call on a device looks up that array's device address, once per
- * device, so make that first call before any stream capture. All calls share
- * the array: calls that overlap on the GPU (different streams, or devices
- * sharing nothing but this library) race; order them on one stream. */
+ * Each device that loads the library has its own copy of the array. The first
+ * call on a device looks up that copy's device address, once per device and
+ * with that device current, so make that first call before any stream
+ * capture. Every call on one device uses that device's copy and leaves its
+ * partial sums there: calls that overlap on the same device (different
+ * streams) race, so order them on one stream; calls on different devices do
+ * not interfere. The looked-up address lasts as long as the device's context:
+ * after cudaDeviceReset on that device, restart the process before calling
+ * this entry point again. */
 tlfe_status tlfe_norm_noalloc(const double *x_dev, int64_t n, double *out_dev, void *stream);
 
 /* Diagnostic of the timeout path of device-side waits (no counterpart in the

@@ -30,7 +30,9 @@
 //     per component (a plain read-add-write in colour passes, where no two
 //     elements of a launch share a node).
 // Every mbarrier wait is bounded; on timeout the kernel latches ST_TIMEOUT in
-// the status word, drains its own copies (again bounded) and returns.
+// the status word, waits (again bounded) for the copies it still has in
+// flight, each by the parity of its barrier's one outstanding phase, and
+// returns.
 // Affine Q27 blocks do not come here: they run the warp-per-element kernels
 // of k_wpe.cuh (kernel_for / smem_for below dispatch on wpe_path).
 #pragma once
@@ -334,6 +336,16 @@ __global__ void __launch_bounds__(128, min_ctas<ET, R, OP, AFF>()) k_elem(const 
         if (n_my > 0) issue_meta(0);
         for (int j = 0; j < NSLICE && j < n_slices; ++j) issue(j);
     }
+    // copies issued and waited for, counted alike in every lane (the issue
+    // decisions are warp-uniform): slices j < sl_issued and metadata records
+    // k < mt_issued were requested, those below sl_done / mt_done have landed.
+    // A barrier never holds more than one outstanding phase (slot b is
+    // re-armed only after its previous slice was consumed; record k + 1 is
+    // requested only after record k - 1, the previous user of its barrier,
+    // was waited for), so the timeout drain below can wait on each
+    // outstanding phase by its parity without ambiguity.
+    int sl_issued = n_slices < NSLICE ? n_slices : NSLICE, sl_done = 0;
+    int mt_issued = n_my > 0 ? 1 : 0, mt_done = 0;
 
     bool timed_out = false;
     for (int k = 0; k < n_my; ++k) {
@@ -344,7 +356,11 @@ __global__ void __launch_bounds__(128, min_ctas<ET, R, OP, AFF>()) k_elem(const 
             timed_out = true;
             break;
         }
-        if (lane == 0 && k + 1 < n_my) issue_meta(k + 1);
+        mt_done = k + 1;
+        if (k + 1 < n_my) {
+            if (lane == 0) issue_meta(k + 1);
+            mt_issued = k + 2;
+        }
         const unsigned char *M = mbuf + (size_t)(k & 1) * MRB;
         const int U = *reinterpret_cast<const int32_t *>(M);
         const int e = reinterpret_cast<const int32_t *>(M + 16)[lane];
@@ -480,6 +496,7 @@ __global__ void __launch_bounds__(128, min_ctas<ET, R, OP, AFF>()) k_elem(const 
                     timed_out = true;
                     break;
                 }
+                sl_done = j + 1;
                 sl = reinterpret_cast<const R *>(ring + (size_t)b * SL::BYTES) + lane;
                 w = sl[NPE * 3 * 32];
             }
@@ -653,9 +670,12 @@ __global__ void __launch_bounds__(128, min_ctas<ET, R, OP, AFF>()) k_elem(const 
                 // slot b is no longer read: hand it to the slice NSLICE ahead
                 const int j = k * NQ + q;
                 __syncwarp();
-                if (lane == 0 && j + NSLICE < n_slices) {
-                    fence_proxy_async();
-                    issue(j + NSLICE);
+                if (j + NSLICE < n_slices) {
+                    if (lane == 0) {
+                        fence_proxy_async();
+                        issue(j + NSLICE);
+                    }
+                    sl_issued = j + NSLICE + 1;
                 }
             }
         }
@@ -768,14 +788,13 @@ __global__ void __launch_bounds__(128, min_ctas<ET, R, OP, AFF>()) k_elem(const 
         __syncwarp();
     }
     if (timed_out) {
-        // a copy never landed: record it and wait (bounded) for this warp's
-        // outstanding copies before leaving
+        // a copy never landed: record it, then wait (bounded) for every copy
+        // this warp still has in flight, by the parity of the one phase its
+        // barrier has outstanding, so that no bulk copy is still writing into
+        // shared memory when the CTA exits
         if (lane == 0) atomicAdd(p.status + ST_TIMEOUT, 1);
-        for (int b = 0; b < NSLICE + 2; ++b) {
-            long long spins = 0;
-            while (!mbar_try_wait(bar + b, 0) && !mbar_try_wait(bar + b, 1) && ++spins < MBAR_SPIN_LIMIT) {
-            }
-        }
+        for (int j = sl_done; j < sl_issued; ++j) mbar_wait_bounded(bar + j % NSLICE, (uint32_t)((j / NSLICE) & 1));
+        for (int k = mt_done; k < mt_issued; ++k) mbar_wait_bounded(mbar + (k & 1), (uint32_t)((k >> 1) & 1));
     }
 }
 

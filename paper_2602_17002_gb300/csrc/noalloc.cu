@@ -17,13 +17,16 @@ constexpr int NA_MAX_PARTIALS = 4096;       // size of the scratch array (32 KiB
 constexpr int NA_THREADS = 256;
 constexpr int NA_MAX_DEVICES = 64;
 
-// Scratch of every call on a device: one partial sum per chunk. Shared by all
-// calls (each call overwrites the partials it reads), so calls that overlap
-// on the GPU race.
+// Scratch of every call on a device: one partial sum per chunk. Each device
+// holds its own copy; all calls on one device share it (each call overwrites
+// the partials it reads), so calls that overlap on the same device race.
 static __device__ __align__(256) double g_norm_scratch[NA_MAX_PARTIALS];
 
 // Device addresses of g_norm_scratch, looked up once per device. In host code
 // the symbol itself is only a host-side stand-in and must not reach a kernel.
+// An address stays valid for the life of the device's context; a
+// cudaDeviceReset would reload the module elsewhere, so the header asks for a
+// process restart after one.
 static double *g_scratch_addr[NA_MAX_DEVICES] = {};
 static std::mutex g_scratch_mutex;
 

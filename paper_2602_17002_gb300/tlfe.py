@@ -22,6 +22,7 @@ SVK, NEOHOOKE, MOONEY_RIVLIN = 0, 1, 2
 FP64, FP32 = 0, 1
 SCATTER_ATOMIC, SCATTER_COLOR, SCATTER_SORTED = 0, 1, 2
 PATH_AUTO, PATH_SLAB, PATH_AFFINE = 0, 1, 2
+NPE = {T4: 4, T10: 10, H8: 8, Q27: 27}
 
 STATUS = {0: "TLFE_OK", 1: "TLFE_E_INVALID", 2: "TLFE_E_OOM", 3: "TLFE_E_CUDA", 4: "TLFE_E_INVERTED",
           5: "TLFE_E_NOT_CONVERGED", 6: "TLFE_E_TIMEOUT", 7: "TLFE_E_UNSUPPORTED", 8: "TLFE_E_NONFINITE"}
@@ -80,7 +81,8 @@ CON_DTYPE = np.dtype([("type", np.int32), ("elem", np.int32, (4,)), ("xi", np.fl
 
 _lib = None
 
-EXPORTS = ["tlfe_create_mesh", "tlfe_destroy_mesh", "tlfe_get_mesh_info", "tlfe_get_colors", "tlfe_sync",
+EXPORTS = ["tlfe_create_mesh", "tlfe_destroy_mesh", "tlfe_get_mesh_info", "tlfe_get_colors",
+           "tlfe_get_scatter_targets", "tlfe_sync",
            "tlfe_internal_force", "tlfe_internal_force_host", "tlfe_tangent_matvec", "tlfe_jacobi_diag",
            "tlfe_vjp", "tlfe_set_elem_mu_lambda", "tlfe_autotune", "tlfe_point_loads", "tlfe_surface_traction",
            "tlfe_constraint_eval", "tlfe_constraint_jt", "tlfe_constraint_j", "tlfe_newton_step", "tlfe_body_norms", "tlfe_norm_noalloc", "tlfe_selftest_wait_timeout", "tlfe_last_error",
@@ -102,6 +104,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "tlfe_destroy_mesh": [P],
         "tlfe_get_mesh_info": [P, C.POINTER(tlfe_mesh_info)],
         "tlfe_get_colors": [P, P],
+        "tlfe_get_scatter_targets": [P, P, P],
         "tlfe_sync": [P, P, C.POINTER(C.c_int64)],
         "tlfe_internal_force": [P, P, P, P, P],
         "tlfe_internal_force_host": [P, P, P, P, P],
@@ -192,6 +195,7 @@ class Mesh:
         self.precision = precision
         self.n_nodes = X.shape[0]
         self._n_bodies = len(materials)
+        self.block_sizes = [tuple(int(x) for x in np.asarray(b[2]).reshape(-1, NPE[int(b[0])]).shape) for b in blocks]
         self.info = self.get_info()
         self._keep = None
 
@@ -220,6 +224,22 @@ class Mesh:
         out = np.zeros(self.info["n_elem"], np.int32)
         _check(load().tlfe_get_colors(self._h, out.ctypes.data))
         return out
+
+    def scatter_targets(self):
+        """(gather, scatter): per block, (n_elem, nodes) int32 arrays of the
+        node each (element, local node) is gathered from and scattered to by
+        the element kernels' device tables (tlfe_get_scatter_targets)."""
+        sizes = self.block_sizes
+        total = sum(n * npe for n, npe in sizes)
+        g = np.full(total, -2, np.int32)
+        s = np.full(total, -2, np.int32)
+        _check(load().tlfe_get_scatter_targets(self._h, g.ctypes.data, s.ctypes.data))
+        out_g, out_s, off = [], [], 0
+        for n, npe in sizes:
+            out_g.append(g[off:off + n * npe].reshape(n, npe))
+            out_s.append(s[off:off + n * npe].reshape(n, npe))
+            off += n * npe
+        return out_g, out_s
 
     def close(self):
         if getattr(self, "_h", None):

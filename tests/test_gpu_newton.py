@@ -52,15 +52,26 @@ def test_free_fall_is_exact(prec, use_graph):
     assert np.abs(v - H * G).max() < 1e-9 * 9.81 * H
 
 
+# (Newton tolerance, CG tolerance, velocity bar) per mesh precision. One FP64
+# step equals the oracle's step to 1e-10: with CG solved to 1e-8 the last
+# Newton iteration lands on the FP64 rounding floor of the residual (about
+# 1e-11 relative on these beams), and two such solves agree in velocity to
+# about 1e-12 (at h = 1e-3 the Newton matrix is close to M / h, so the
+# velocity error is of the order of the residual). The FP32 operator's
+# rounding (about 1e-7 of |f|) bounds the FP32 step at 1e-6.
+NEWTON_BAR = {0: (1e-10, 1e-8, 1e-10), 1: (1e-10, 1e-6, 1e-6)}
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 def test_clamped_beam_matches_oracle(prec):
+    rtol, cg_rtol, bar = NEWTON_BAR[prec]
     wl = beams(1, [6], clamp=True)
-    v, rep, _ = step(wl, prec, True, rtol=1e-10, cg_rtol=1e-6)
-    assert rep["status"] == 0 and rep["rel_residual"] <= 1e-10
+    v, rep, _ = step(wl, prec, True, rtol=rtol, cg_rtol=cg_rtol)
+    assert rep["status"] == 0 and rep["rel_residual"] <= rtol
     v_ref, rep_ref = oracle.newton_step(wl, np.zeros_like(wl.X), np.zeros_like(wl.X), H, G, fixed=wl.fixed,
-                                        newton_rtol=1e-10, cg_rtol=1e-6)
-    assert rep_ref["status"] == 0
-    assert np.abs(v - v_ref).max() <= 1e-6 * np.abs(v_ref).max()
+                                        newton_rtol=1e-10, cg_rtol=1e-8)
+    assert rep_ref["status"] == 0 and rep_ref["rel_residual"] <= 1e-10
+    assert np.abs(v - v_ref).max() <= bar * np.abs(v_ref).max()
     assert np.abs(v[wl.fixed == 1]).max() == 0.0
 
 

@@ -277,6 +277,63 @@ def test_colour_scatter_matches_oracle_greedy_and_is_deterministic():
     assert relerr(f1, f_ref) <= 2e-5
 
 
+def _typed_meshes():
+    """One workload per element type (T4, T10, H8 and Q27 on the warp-per-element
+    path, Q27 curved on the tile path) and one multi-block batch."""
+    out = {}
+    for name, et in (("T4", synth.T4), ("H8", synth.H8)):
+        m = synth.box_mesh(et, (7, 3, 2), (0.35, 0.15, 0.1))
+        rng = np.random.default_rng(41 + et)
+        out[name] = Workload(name, m.X, [Block(et, synth.workloads.DEFAULT_NQ[et], m.conn, m.body)],
+                             np.array([1], np.int32), np.array([[3.8e6, 5.8e6, 0.0, 0.0, 1000.0]]),
+                             u=1e-3 * rng.standard_normal(m.X.shape), udot=None, v=rng.standard_normal(m.X.shape))
+    out["T10"] = synth.small_beam(cells=(6, 3, 2))
+    out["Q27"] = synth.q27_beam(cells=(5, 3, 2))
+    out["Q27_curved"] = synth.q27_beam(cells=(5, 3, 2), curve=0.05)
+    out["batch"] = synth.batch_bodies(n_bodies=7, seed=13, ne_range=(30, 500))
+    return out
+
+
+@pytest.mark.parametrize("name", ["T4", "T10", "H8", "Q27", "Q27_curved", "batch"])
+def test_colours_bit_exact_every_element_type(name):
+    """Colouring (two elements conflict iff they share a node; colour = the
+    smallest not used by a higher-priority conflicting element of the block,
+    priority splitmix64(e xor seed)) equals the oracle's sequential greedy run
+    on every block, for every element type and a multi-block batch."""
+    wl = _typed_meshes()[name]
+    seed = 0x5EED + len(name)
+    tl = T()
+    mesh = tl.Mesh.from_workload(wl, precision=tl.FP32, scatter=tl.SCATTER_COLOR, color_seed=seed)
+    col = mesh.colors()
+    k0, nc_max = 0, 0
+    for blk in wl.blocks:
+        ref, nc = oracle.color_greedy(blk.conn, wl.n_nodes, seed)
+        assert np.array_equal(col[k0:k0 + blk.n_elem], ref)
+        nc_max = max(nc_max, nc)
+        k0 += blk.n_elem
+    assert mesh.info["n_colors"] == nc_max
+    mesh.close()
+
+
+@pytest.mark.parametrize("scatter", [0, 1, 2])
+@pytest.mark.parametrize("name", ["T4", "T10", "H8", "Q27", "Q27_curved", "batch"])
+def test_gather_and_scatter_indices_bit_exact(name, scatter):
+    """The node every (element, local node) is gathered from and scattered to,
+    read back from the kernels' device tables (metadata records, node-sorted
+    positions, the sorted-scatter transpose, the warp-per-element
+    connectivity), equals conn[e][i] bit for bit: the scatter target of
+    component d is 3 conn[e][i] + d."""
+    wl = _typed_meshes()[name]
+    tl = T()
+    for prec in (0, 1):
+        mesh = tl.Mesh.from_workload(wl, precision=prec, scatter=scatter)
+        g, s = mesh.scatter_targets()
+        for blk, gb, sb in zip(wl.blocks, g, s):
+            assert np.array_equal(gb, blk.conn)
+            assert np.array_equal(sb, blk.conn)
+        mesh.close()
+
+
 def test_inverted_points_are_counted():
     wl = synth.small_beam(cells=(4, 1, 1), damping=0.0)
     # squash the beam through itself along x: J < 0 everywhere

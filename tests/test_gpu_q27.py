@@ -146,15 +146,19 @@ def test_q27_clamped_newton_step_matches_oracle(prec):
     z = torch.zeros((wl.n_nodes, 3), dtype=torch.float64, device="cuda")
     G = np.array([0.0, 0.0, -9.81])
     h = 1e-3
-    v, rep = mesh.newton_step(z, z.clone(), h, gravity=G, fixed=torch.from_numpy(fixed).cuda(), newton_rtol=1e-10,
-                              cg_rtol=1e-6, max_newton=20, max_cg=2000, use_graph=True)
+    # FP64: both steps solved with CG to 1e-8, which lands the last Newton
+    # iteration on the rounding floor of the residual: equal to 1e-10. FP32:
+    # the operator's rounding bounds the step at 1e-6
+    rtol, cg_rtol, bar = (1e-10, 1e-8, 1e-10) if prec == 0 else (1e-10, 1e-6, 1e-6)
+    v, rep = mesh.newton_step(z, z.clone(), h, gravity=G, fixed=torch.from_numpy(fixed).cuda(), newton_rtol=rtol,
+                              cg_rtol=cg_rtol, max_newton=20, max_cg=2000, use_graph=True)
     torch.cuda.synchronize()
     v = v.cpu().numpy()
-    assert rep["status"] == 0 and rep["rel_residual"] <= 1e-10
+    assert rep["status"] == 0 and rep["rel_residual"] <= rtol
     v_ref, rep_ref = oracle.newton_step(wl, np.zeros_like(wl.X), np.zeros_like(wl.X), h, G, fixed=fixed,
-                                        newton_rtol=1e-10, cg_rtol=1e-6)
-    assert rep_ref["status"] == 0
-    assert np.abs(v - v_ref).max() <= 1e-6 * np.abs(v_ref).max()
+                                        newton_rtol=1e-10, cg_rtol=1e-8)
+    assert rep_ref["status"] == 0 and rep_ref["rel_residual"] <= 1e-10
+    assert np.abs(v - v_ref).max() <= bar * np.abs(v_ref).max()
     assert np.abs(v[fixed == 1]).max() == 0.0
 
 

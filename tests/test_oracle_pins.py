@@ -16,6 +16,7 @@ import pytest
 import oracle
 import synth
 from synth import T4, T10, H8, Q27
+from synth.workloads import DEFAULT_NQ, Block, Workload
 
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
 ATOL = 1e-12
@@ -503,6 +504,75 @@ def test_tangent_matches_fd_and_symmetry(builder):
         Cw = oracle.operator_apply(wl, w, a_K=0.0, a_C=1.0)
         assert abs(np.sum(w * Cv) - np.sum(v * Cw)) < 1e-10 * abs(np.sum(w * Cv))
         assert np.sum(v * Cv) > 0
+
+
+def _damped_block(etype, cells, model=1, seed=31):
+    """A small damped body of one element type with a random state: bending
+    displacement + noise, random velocities (Kelvin-Voigt mu_v, lam_v > 0 so
+    that every viscous block is non-zero)."""
+    m = synth.box_mesh(etype, cells, tuple(0.05 * c for c in cells))
+    rng = np.random.default_rng(seed)
+    u = 2e-3 * rng.standard_normal(m.X.shape)
+    udot = 0.05 * rng.standard_normal(m.X.shape)
+    return Workload(name=f"damped_{etype}", X=m.X, blocks=[Block(etype, DEFAULT_NQ[etype],
+                                                                            m.conn, m.body)],
+                          model=np.array([model], np.int32),
+                          params=np.array([[MU, LAM, 2e3, 7e2, 1000.0]]), u=u, udot=udot,
+                          v=rng.standard_normal(m.X.shape))
+
+
+@pytest.mark.parametrize("etype,cells", [(T10, (2, 1, 1)), (H8, (2, 2, 1))])
+def test_jacobi_diag_is_the_diagonal_of_the_symmetric_operator(etype, cells):
+    """Sec. 2.2 Newton matrix, Jacobi preconditioner: jacobi_diag[k] equals
+    e_k . (a_M M + a_K K^e + a_C C) e_k, the operator applied to every unit
+    vector (a wrong DOF in the diagonal's scatter, or a term dropped from it
+    but not from the operator, fails here)."""
+    wl = _damped_block(etype, cells)
+    n3 = 3 * wl.n_nodes
+    for aM, aK, aC in ((0.0, 1.0, 0.0), (0.0, 0.0, 1.0), (1e3, 0.7, 1.9)):
+        d = oracle.jacobi_diag(wl, a_M=aM, a_K=aK, a_C=aC).ravel()
+        ref = np.zeros(n3)
+        for k in range(n3):
+            e = np.zeros(n3)
+            e[k] = 1.0
+            y = oracle.operator_apply(wl, e.reshape(-1, 3), a_M=aM, a_K=aK, a_C=aC, sym_only=True)
+            ref[k] = y.ravel()[k]
+        assert np.abs(d - ref).max() <= 1e-13 * np.abs(ref).max()
+        assert np.all(ref > 0)          # the diagonal of an SPD operator
+
+
+@pytest.mark.parametrize("etype,cells", [(T10, (2, 1, 1)), (H8, (2, 2, 1)), (T4, (2, 2, 2))])
+def test_symmetric_operator_is_the_elastic_stiffness(etype, cells):
+    """The CG operator's stiffness K^e (Sec. 7 reading: the viscous stiffness
+    K^v left out) against central differences of the force with the velocity
+    switched off, which is the elastic force alone (P^v = 0 when Fdot = 0):
+    K^e v = d/de f(u + e v, udot = 0). It must not depend on the velocity,
+    and with mu_v = lam_v = 0 it equals the full K_t."""
+    wl = _damped_block(etype, cells)
+    rng = np.random.default_rng(5)
+    v = rng.standard_normal(wl.X.shape)
+    Ke_v = oracle.operator_apply(wl, v, sym_only=True)
+    h = 1e-7
+    z = np.zeros_like(wl.X)
+    fp, _ = oracle.internal_force(wl, u=wl.u + h * v, udot=z)
+    fm, _ = oracle.internal_force(wl, u=wl.u - h * v, udot=z)
+    assert np.abs((fp - fm) / (2 * h) - Ke_v).max() < 1e-7 * np.abs(Ke_v).max()
+    # independent of the velocity at which it is evaluated
+    Ke_v0 = oracle.operator_apply(wl, v, sym_only=True, udot=z)
+    assert np.abs(Ke_v0 - Ke_v).max() <= 1e-12 * np.abs(Ke_v).max()
+    # the full K_t differs by the viscous stiffness, which is not zero here
+    Kt_v = oracle.operator_apply(wl, v)
+    assert np.abs(Kt_v - Ke_v).max() > 1e-6 * np.abs(Ke_v).max()
+    # undamped: the symmetric operator is the full one
+    wl.params[:, 2:4] = 0.0
+    assert np.abs(oracle.operator_apply(wl, v, sym_only=True) - oracle.operator_apply(wl, v)).max() <= \
+        1e-13 * np.abs(Ke_v).max()
+    # the damping product C is the same in both (C v = d/de f(u, udot + e v))
+    wl.params[:, 2:4] = (2e3, 7e2)
+    Cv = oracle.operator_apply(wl, v, a_K=0.0, a_C=1.0, sym_only=True)
+    fp, _ = oracle.internal_force(wl, udot=wl.udot + h * v)
+    fm, _ = oracle.internal_force(wl, udot=wl.udot - h * v)
+    assert np.abs((fp - fm) / (2 * h) - Cv).max() < 1e-7 * np.abs(Cv).max()
 
 
 def test_vjp_parameter_gradient_by_fd():
