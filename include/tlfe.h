@@ -89,6 +89,16 @@ enum { TLFE_SCATTER_ATOMIC = 0, TLFE_SCATTER_COLOR = 1, TLFE_SCATTER_SORTED = 2 
  *   TLFE_PATH_AFFINE : every block on the affine path; TLFE_E_UNSUPPORTED at
  *                      creation when a block is not affine */
 enum { TLFE_PATH_AUTO = 0, TLFE_PATH_SLAB = 1, TLFE_PATH_AFFINE = 2 };
+/* How the element passes of one operation are launched (a property of this
+ * GPU implementation; the paper has no counterpart):
+ *   TLFE_LAUNCH_AUTO     : one persistent launch per operation over every pass
+ *                          it covers (FP32 meshes, atomic or sorted scatter,
+ *                          T4 / T10 / H8 blocks on the affine path) when there
+ *                          are two or more such passes, else one launch per
+ *                          pass; tlfe_autotune keeps whichever measures faster
+ *   TLFE_LAUNCH_PER_PASS : one launch per pass (element block and law)
+ *   TLFE_LAUNCH_FUSED    : the persistent launch wherever it covers a pass */
+enum { TLFE_LAUNCH_AUTO = 0, TLFE_LAUNCH_PER_PASS = 1, TLFE_LAUNCH_FUSED = 2 };
 
 /* One type-homogeneous element block.
  *   type  : TLFE_T4 (4 nodes), TLFE_T10 (10 nodes, App. A.1 node order),
@@ -160,11 +170,23 @@ typedef struct {
     int64_t stream_bytes_vjp;     /* algorithmic bytes of one tlfe_vjp (all outputs) */
     int64_t device_bytes;         /* device memory held by the handle */
     int32_t n_affine_blocks;      /* blocks whose kernels run on the affine path */
-    int32_t n_passes;             /* element-kernel launches of one operation: one per elastic law of each
-                                     block (per colour and law in colour mode), each its own tile range */
+    int32_t n_passes;             /* tile ranges of one operation: one per elastic law of each block (per
+                                     colour and law in colour mode) */
+    int32_t n_fused_passes;       /* passes the fused persistent launch covers (0: no fused launch) */
+    int32_t n_fused_items;        /* work items (tile runs) of the fused launch */
+    int32_t launches_force;       /* kernel launches of one tlfe_internal_force in the current launch mode */
+    int32_t launches_matvec;      /* kernel launches of one tlfe_tangent_matvec in the current launch mode */
 } tlfe_mesh_info;
 
 tlfe_status tlfe_get_mesh_info(const tlfe_mesh *mesh, tlfe_mesh_info *info);
+
+/* Launch mode of the element passes (TLFE_LAUNCH_AUTO, TLFE_LAUNCH_PER_PASS
+ * or TLFE_LAUNCH_FUSED; see their definition). Results do not depend on it
+ * beyond the order of floating-point additions in the atomic scatter (the
+ * sorted scatter's results are the same bit for bit). Takes effect at the
+ * next call; a graph captured by tlfe_force_matvec keeps the mode it was
+ * captured with until its arguments change. */
+tlfe_status tlfe_set_launch_mode(tlfe_mesh *mesh, int32_t mode);
 
 /* Colour of every element in global element order (host [n_elem]); -1 when
  * the mesh was not coloured. Synchronises. */
@@ -217,6 +239,23 @@ tlfe_status tlfe_internal_force_host(tlfe_mesh *mesh, const void *u_host, const 
 tlfe_status tlfe_tangent_matvec(tlfe_mesh *mesh, const void *u_dev, const void *udot_dev,
                                 const void *v_dev, double a_M, double a_K, double a_C,
                                 void *y_dev, void *stream);
+
+/* Internal force and operator product of one state in one call (the force +
+ * K v step of a batch of bodies: Sec. 4.3, Eq. internal_force_universal, and
+ * the product above):
+ *   f = f_int(u, udot),  y = a_M M v + a_K K_t(u, udot) v + a_C C(u) v
+ * with the arguments and layouts of tlfe_internal_force and
+ * tlfe_tangent_matvec (f and y distinct). The handle keeps a CUDA graph of
+ * the call: the first call with a given set of pointers and coefficients (or
+ * the first after tlfe_autotune, tlfe_set_launch_mode or the first
+ * tlfe_set_elem_mu_lambda) evaluates directly and captures the same launches
+ * on a stream of its own; later calls with the same arguments replay that
+ * graph on `stream`. In TLFE_LAUNCH_AUTO and TLFE_LAUNCH_FUSED modes a mesh
+ * with a fused plan runs each operation as one persistent launch. The first
+ * call with new arguments must not itself be made during a stream capture.
+ * Stream-ordered; the graph is released with the handle. */
+tlfe_status tlfe_force_matvec(tlfe_mesh *mesh, const void *u_dev, const void *udot_dev, const void *v_dev,
+                              double a_M, double a_K, double a_C, void *f_dev, void *y_dev, void *stream);
 
 /* Diagonal of a_M M + a_K K^e + a_C C (the Jacobi preconditioner of the
  * Newton/CG step; K^e is the elastic, symmetric part of K_t).

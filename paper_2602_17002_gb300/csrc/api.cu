@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "tlfe_elem.cuh"
+#include "tlfe_fused.h"
 #include "tlfe_internal.h"
 #include "tlfe_mesh.h"
 
@@ -561,6 +562,68 @@ static tlfe_status build_block(tlfe_mesh *m, const tlfe_mesh_desc *d, int bi, in
     return TLFE_OK;
 }
 
+// Work items of the fused launch: the passes the fused kernels cover (FP32,
+// atomic or sorted scatter, affine T4 / T10 / H8 tile blocks), when there are
+// at least two. Each pass is cut into runs of tiles of about equal work
+// (quadrature points x nodes of FUSED_ITEM_COST per run); the items are
+// listed longest first: the passes in decreasing work per tile, each in tile
+// order (neighbouring runs share nodes through L2), then the shorter
+// remainder runs in decreasing length, so that light items fill the tail.
+constexpr int FUSED_ITEM_COST = 400;
+
+static tlfe_status build_fused_plan(tlfe_mesh *m)
+{
+    if (m->precision != TLFE_FP32 || m->scatter == TLFE_SCATTER_COLOR) return TLFE_OK;
+    std::vector<std::pair<int, int>> passes;
+    std::vector<bool> covered(m->blocks.size(), false);
+    for (int bi = 0; bi < (int)m->blocks.size(); ++bi) {
+        const BlockStore &B = m->blocks[bi];
+        if (B.n_elem == 0 || !B.use_affine || wpe_path(B.et, true) || fused_code(B.et, B.nq) < 0) continue;
+        covered[bi] = true;
+        for (int c = 0; c + 1 < (int)B.color_tile_off.size(); ++c)
+            if (B.color_tile_off[c + 1] > B.color_tile_off[c]) passes.emplace_back(bi, c);
+    }
+    if (passes.size() < 2 || passes.size() > (size_t)FUSED_MAXP) return TLFE_OK;
+    auto tile_cost = [&](int bi) { return m->blocks[bi].nq * m->blocks[bi].npe; };
+    std::vector<int> order(passes.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return tile_cost(passes[a].first) > tile_cost(passes[b].first); });
+    std::vector<int4> full, rest;
+    for (int k : order) {
+        const BlockStore &B = m->blocks[passes[k].first];
+        const int c = passes[k].second;
+        const int per = std::max(1, std::min(1024, FUSED_ITEM_COST / tile_cost(passes[k].first)));
+        for (int t = B.color_tile_off[c]; t < B.color_tile_off[c + 1]; t += per) {
+            const int te = std::min(t + per, B.color_tile_off[c + 1]);
+            (te - t == per ? full : rest).push_back(make_int4(k, t, te, 0));
+        }
+    }
+    std::stable_sort(rest.begin(), rest.end(), [&](const int4 &a, const int4 &b) {
+        return (int64_t)(a.z - a.y) * tile_cost(passes[a.x].first) > (int64_t)(b.z - b.y) * tile_cost(passes[b.x].first);
+    });
+    full.insert(full.end(), rest.begin(), rest.end());
+    FusedPlan *fp = new FusedPlan();
+    m->fused = fp;
+    fp->passes = passes;
+    fp->covered = covered;
+    fp->n_items = (int)full.size();
+    CKA(fp->d_items, sizeof(int4) * full.size(), m);
+    CKA(fp->d_counter, sizeof(int) * 4, m);
+    CK(cudaMemcpy(fp->d_items, full.data(), sizeof(int4) * full.size(), cudaMemcpyHostToDevice));
+    for (int o = 0; o < 2; ++o) {
+        size_t w = 0;
+        for (auto &pc : passes) {
+            const BlockStore &B = m->blocks[pc.first];
+            const int code = fused_code(B.et, B.nq);
+            w = std::max(w, o == 0 ? fused_warp_region<float, OP_FORCE>(code, B.umax, B.meta_bytes)
+                                   : fused_warp_region<float, OP_MATVEC>(code, B.umax, B.meta_bytes));
+        }
+        fp->wreg[o] = w;
+    }
+    return TLFE_OK;
+}
+
 extern "C" tlfe_status tlfe_create_mesh(const tlfe_mesh_desc *desc, void *stream, tlfe_mesh **out)
 {
     TLFE_TRACE("tlfe_create_mesh");
@@ -632,6 +695,8 @@ extern "C" tlfe_status tlfe_create_mesh(const tlfe_mesh_desc *desc, void *stream
         m->n_qp += (int64_t)desc->blocks[bi].n_elem * desc->blocks[bi].n_qp;
     }
     m->n_elem = base;
+    st = build_fused_plan(m);
+    if (st != TLFE_OK) return bail(st);
     if (m->scatter == TLFE_SCATTER_SORTED) {
         // transpose of the position -> node map: for each node its positions in
         // ascending order, which fixes the order of its sum
@@ -673,7 +738,9 @@ extern "C" tlfe_status tlfe_destroy_mesh(tlfe_mesh *m)
     if (!m) return TLFE_OK;
     cudaDeviceSynchronize();
     destroy_newton(m);
+    destroy_graphs(m);
     for (void *p : m->allocs) cudaFree(p);
+    delete m->fused;
     delete m;
     return TLFE_OK;
 }
@@ -720,6 +787,23 @@ extern "C" tlfe_status tlfe_get_mesh_info(const tlfe_mesh *m, tlfe_mesh_info *in
     info->n_passes = 0;
     for (auto &B : m->blocks)
         if (B.n_elem > 0) info->n_passes += (int)B.color_tile_off.size() - 1;
+    info->n_fused_passes = m->fused ? (int)m->fused->passes.size() : 0;
+    info->n_fused_items = m->fused ? m->fused->n_items : 0;
+    // element-kernel launches of one force / operator-product call in the
+    // current launch mode (the sorted scatter adds one node-sum kernel)
+    for (int o = 0; o < 2; ++o) {
+        const bool fused = m->fused && m->launch_mode != TLFE_LAUNCH_PER_PASS &&
+                           (m->launch_mode == TLFE_LAUNCH_FUSED || m->fused->on[o]);
+        int n = fused ? 1 : 0;
+        for (size_t bi = 0; bi < m->blocks.size(); ++bi) {
+            const BlockStore &B = m->blocks[bi];
+            if (B.n_elem == 0 || (fused && m->fused->covered[bi])) continue;
+            for (int c = 0; c + 1 < (int)B.color_tile_off.size(); ++c)
+                if (B.color_tile_off[c + 1] > B.color_tile_off[c]) ++n;
+        }
+        if (m->scatter == TLFE_SCATTER_SORTED) ++n;
+        (o == 0 ? info->launches_force : info->launches_matvec) = n;
+    }
     return TLFE_OK;
 }
 
@@ -870,6 +954,63 @@ __global__ void k_node_sum(int64_t n3, const int64_t *__restrict__ ptr, const in
     }
 }
 
+// whether OP runs as the fused persistent launch on this mesh (launch mode,
+// and the autotuner's choice in TLFE_LAUNCH_AUTO)
+template <int OP, typename R> static bool use_fused(const tlfe_mesh *m)
+{
+    if constexpr (sizeof(R) != 4 || (OP != OP_FORCE && OP != OP_MATVEC)) {
+        return false;
+    } else {
+        if (!m->fused || m->launch_mode == TLFE_LAUNCH_PER_PASS) return false;
+        return m->launch_mode == TLFE_LAUNCH_FUSED || m->fused->on[OP == OP_FORCE ? 0 : 1];
+    }
+}
+
+// the fused launch of OP over every covered pass: one parameter-table entry
+// per pass (the call's fields of `base`, the block's layout, the pass's tile
+// range and material mode), the item counter zeroed, all resident CTAs of the
+// schedule (`fixed`, or the plan's: tuned, else from the occupancy API)
+template <int OP>
+static tlfe_status run_fused(tlfe_mesh *m, const KParams<float> &base, cudaStream_t s,
+                             const LaunchSched *fixed = nullptr)
+{
+    FusedPlan &fp = *m->fused;
+    const int o = OP == OP_FORCE ? 0 : 1;
+    static thread_local FusedArgs<float> a;  // 17 KB: kept off the stack
+    memset(&a, 0, sizeof(a));
+    a.n_items = fp.n_items;
+    a.items = fp.d_items;
+    a.counter = fp.d_counter + o;
+    a.wreg = (int)fp.wreg[o];
+    for (size_t k = 0; k < fp.passes.size(); ++k) {
+        const BlockStore &B = m->blocks[fp.passes[k].first];
+        const int c = fp.passes[k].second;
+        KParams<float> p = base;
+        block_params<float>(m, B, p);
+        p.tile_begin = B.color_tile_off[c];
+        p.tile_end = B.color_tile_off[c + 1];
+        p.visc = (B.pass_visc[c] && p.ud) ? 1 : 0;
+        p.mat_mode = pass_mat_mode(B, c, p.ud != nullptr);
+        p.tile_chunk = 0;
+        p.rmw_scatter = 0;
+        a.pass[k] = p;
+        a.kind[k] = fused_code(B.et, B.nq) * MAT_N + p.mat_mode;
+    }
+    LaunchSched ls = fixed ? *fixed : fp.sched[o];
+    if (ls.resident <= 0) {
+        ls.wpb = 0;
+        ls.resident = occupancy_fused<OP, float>(fp.wreg[o], &ls.wpb);
+        if (ls.resident <= 0) return fail(TLFE_E_UNSUPPORTED, "fused element kernel cannot be made resident");
+        if (!fixed) fp.sched[o] = ls;
+    }
+    const int warps = std::min(fp.n_items, std::max(1, ls.resident / ls.wpb) * ls.wpb * m->n_sm);
+    const int grid = std::max(1, (warps + ls.wpb - 1) / ls.wpb);
+    CK(cudaMemsetAsync(a.counter, 0, sizeof(int), s));
+    cudaError_t e = launch_fused<OP, float>(a, grid, ls.wpb, s);
+    if (e != cudaSuccess) return cuda_fail(e, "fused element kernel launch");
+    return TLFE_OK;
+}
+
 template <int OP, typename R>
 tlfe_status run_op(tlfe_mesh *m, const void *u, const void *ud, const void *v, void *out0, void *out1,
                    double *gth, double aM, double aK, double aC, int sym_only, cudaStream_t s)
@@ -898,8 +1039,15 @@ tlfe_status run_op(tlfe_mesh *m, const void *u, const void *ud, const void *v, v
         if (out0) CK(cudaMemsetAsync(out0, 0, nb, s));
         if (out1) CK(cudaMemsetAsync(out1, 0, nb, s));
     }
+    const bool fused = use_fused<OP, R>(m);
+    if constexpr (sizeof(R) == 4 && (OP == OP_FORCE || OP == OP_MATVEC)) {
+        if (fused) {
+            tlfe_status st = run_fused<OP>(m, p, s);
+            if (st != TLFE_OK) return st;
+        }
+    }
     for (int bi = 0; bi < (int)m->blocks.size(); ++bi) {
-        if (m->blocks[bi].n_elem == 0) continue;
+        if (m->blocks[bi].n_elem == 0 || (fused && m->fused->covered[bi])) continue;
         tlfe_status st = run_block_op<OP, R>(m, bi, p, s);
         if (st != TLFE_OK) return st;
     }
@@ -973,6 +1121,68 @@ static tlfe_status tune_block(tlfe_mesh *m, int bi, KParams<R> p, cudaStream_t s
     return TLFE_OK;
 }
 
+// median of three timed runs of `launch` (after one untimed run), in ms
+template <typename F>
+static tlfe_status time_median3(F launch, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, float *out)
+{
+    tlfe_status st = launch();
+    if (st != TLFE_OK) return st;
+    float ms[3];
+    for (int r = 0; r < 3; ++r) {
+        CK(cudaEventRecord(e0, s));
+        st = launch();
+        if (st != TLFE_OK) return st;
+        CK(cudaEventRecord(e1, s));
+        CK(cudaEventSynchronize(e1));
+        CK(cudaEventElapsedTime(&ms[r], e0, e1));
+    }
+    std::sort(ms, ms + 3);
+    *out = ms[1];
+    return TLFE_OK;
+}
+
+// The fused launch of OP at every resident CTA size (4, 2, 1 warps) against
+// the per-pass launches (with their tuned schedules) of the passes it covers;
+// keeps the fastest schedule and, in TLFE_LAUNCH_AUTO, the faster mode.
+template <int OP>
+static tlfe_status tune_fused(tlfe_mesh *m, KParams<float> p, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1)
+{
+    FusedPlan &fp = *m->fused;
+    const int o = OP == OP_FORCE ? 0 : 1;
+    float per_pass = 0.f;
+    tlfe_status st = time_median3(
+        [&]() -> tlfe_status {
+            for (int bi = 0; bi < (int)m->blocks.size(); ++bi) {
+                if (!fp.covered[bi]) continue;
+                tlfe_status s2 = run_block_op<OP, float>(m, bi, p, s);
+                if (s2 != TLFE_OK) return s2;
+            }
+            return TLFE_OK;
+        },
+        s, e0, e1, &per_pass);
+    if (st != TLFE_OK) return st;
+    LaunchSched best;
+    float best_ms = 1e30f;
+    for (int wpb : {4, 2, 1}) {
+        LaunchSched ls;
+        ls.wpb = wpb;
+        ls.resident = occupancy_fused<OP, float>(fp.wreg[o], &ls.wpb);
+        if (ls.resident <= 0) continue;
+        float ms = 0.f;
+        st = time_median3([&]() { return run_fused<OP>(m, p, s, &ls); }, s, e0, e1, &ms);
+        if (st != TLFE_OK) return st;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = ls;
+        }
+    }
+    if (best.resident <= 0) return TLFE_OK;  // keep the per-pass launches
+    best.tuned = true;
+    fp.sched[o] = best;
+    fp.on[o] = best_ms <= per_pass;
+    return TLFE_OK;
+}
+
 template <typename R>
 static tlfe_status tune_all(tlfe_mesh *m, const double *u, const void *ud, const void *v, cudaStream_t s)
 {
@@ -1006,6 +1216,12 @@ static tlfe_status tune_all(tlfe_mesh *m, const double *u, const void *ud, const
         st = tune_block<OP_FORCE, R>(m, bi, p, s, e0, e1);
         if (st == TLFE_OK && v) st = tune_block<OP_MATVEC, R>(m, bi, p, s, e0, e1);
         if (st == TLFE_OK && v) st = tune_block<OP_VJP, R>(m, bi, p, s, e0, e1);
+    }
+    if constexpr (sizeof(R) == 4) {
+        if (st == TLFE_OK && m->fused) {
+            st = tune_fused<OP_FORCE>(m, p, s, e0, e1);
+            if (st == TLFE_OK && v) st = tune_fused<OP_MATVEC>(m, p, s, e0, e1);
+        }
     }
     cudaStreamSynchronize(s);
     if (e0) cudaEventDestroy(e0);
@@ -1122,7 +1338,19 @@ extern "C" tlfe_status tlfe_autotune(tlfe_mesh *m, const double *u, const void *
     tlfe_status st = check_mesh_args(m, {u});
     if (st != TLFE_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
+    ++m->sched_gen;
     return m->precision == TLFE_FP32 ? tune_all<float>(m, u, ud, v, s) : tune_all<double>(m, u, ud, v, s);
+}
+
+extern "C" tlfe_status tlfe_set_launch_mode(tlfe_mesh *m, int32_t mode)
+{
+    TLFE_TRACE("tlfe_set_launch_mode");
+    if (!m) return fail(TLFE_E_INVALID, "mesh is NULL");
+    if (mode != TLFE_LAUNCH_AUTO && mode != TLFE_LAUNCH_PER_PASS && mode != TLFE_LAUNCH_FUSED)
+        return fail(TLFE_E_INVALID, "bad launch mode");
+    m->launch_mode = mode;
+    ++m->sched_gen;
+    return TLFE_OK;
 }
 
 extern "C" tlfe_status tlfe_set_elem_mu_lambda(tlfe_mesh *m, const double *mu_lambda_dev, void *stream)
@@ -1134,7 +1362,10 @@ extern "C" tlfe_status tlfe_set_elem_mu_lambda(tlfe_mesh *m, const double *mu_la
     const size_t rs = m->precision == TLFE_FP32 ? 4 : 8;
     for (auto &B : m->blocks) {
         if (B.n_tiles == 0) continue;
-        if (!B.d_elam) CKA(B.d_elam, rs * (size_t)B.n_tiles * TILE * 2, m);
+        if (!B.d_elam) {
+            CKA(B.d_elam, rs * (size_t)B.n_tiles * TILE * 2, m);
+            ++m->sched_gen;  // the blocks' launch parameters now carry the per-element array
+        }
         cudaError_t e = launch_set_elam(m->precision, B.n_tiles, B.d_eid, mu_lambda_dev, B.d_elam, s);
         if (e != cudaSuccess) return cuda_fail(e, "tlfe_set_elem_mu_lambda");
     }

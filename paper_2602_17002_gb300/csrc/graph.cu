@@ -1,0 +1,102 @@
+// tlfe_force_matvec: the internal force and the operator product of one
+// state in one call, replayed from a CUDA graph the mesh handle owns (the
+// batched force + K v step: one persistent launch per operation where the
+// mesh has a fused plan, the sorted scatter's node sums, the output clears).
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "tlfe_mesh.h"
+
+namespace tlfe {
+
+struct OpGraph {
+    // the arguments and launch settings the graph was captured with
+    const void *u = nullptr, *ud = nullptr, *v = nullptr;
+    void *f = nullptr, *y = nullptr;
+    double aM = 0, aK = 0, aC = 0;
+    int sched_gen = -1;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cap = nullptr;  // capture stream (the caller's may be the legacy stream)
+};
+
+void destroy_graphs(tlfe_mesh *m)
+{
+    if (!m->fm_graph) return;
+    if (m->fm_graph->exec) cudaGraphExecDestroy(m->fm_graph->exec);
+    if (m->fm_graph->cap) cudaStreamDestroy(m->fm_graph->cap);
+    delete m->fm_graph;
+    m->fm_graph = nullptr;
+}
+
+template <typename R>
+static tlfe_status record_ops(tlfe_mesh *m, const void *u, const void *ud, const void *v, double aM, double aK,
+                              double aC, void *f, void *y, cudaStream_t s)
+{
+    tlfe_status st = run_op<OP_FORCE, R>(m, u, ud, nullptr, f, nullptr, nullptr, 0, 1, 0, 0, s);
+    if (st != TLFE_OK) return st;
+    return run_op<OP_MATVEC, R>(m, u, ud, v, y, nullptr, nullptr, aM, aK, aC, 0, s);
+}
+
+}  // namespace tlfe
+
+using namespace tlfe;
+
+extern "C" tlfe_status tlfe_force_matvec(tlfe_mesh *m, const void *u, const void *ud, const void *v, double aM,
+                                         double aK, double aC, void *f, void *y, void *stream)
+{
+    TLFE_TRACE("tlfe_force_matvec");
+    if (!m) return fail(TLFE_E_INVALID, "mesh is NULL");
+    if (!u || !v || !f || !y) return fail(TLFE_E_INVALID, "required array pointer is NULL");
+    if (f == y) return fail(TLFE_E_INVALID, "f and y must be different arrays");
+    cudaStream_t s = (cudaStream_t)stream;
+    OpGraph *g = m->fm_graph;
+    if (g && g->exec && g->u == u && g->ud == ud && g->v == v && g->f == f && g->y == y && g->aM == aM &&
+        g->aK == aK && g->aC == aC && g->sched_gen == m->sched_gen) {
+        cudaError_t e = cudaGraphLaunch(g->exec, s);
+        if (e != cudaSuccess) return cuda_fail(e, "tlfe_force_matvec: graph launch");
+        return TLFE_OK;
+    }
+    // new arguments: evaluate directly (validates them, fills the launch
+    // caches), then capture the same calls on the handle's capture stream
+    tlfe_status st = tlfe_internal_force(m, u, ud, f, stream);
+    if (st != TLFE_OK) return st;
+    st = tlfe_tangent_matvec(m, u, ud, v, aM, aK, aC, y, stream);
+    if (st != TLFE_OK) return st;
+    if (!g) g = m->fm_graph = new OpGraph();
+    if (g->exec) {
+        cudaGraphExecDestroy(g->exec);
+        g->exec = nullptr;
+    }
+    if (!g->cap) {
+        cudaError_t e = cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_fail(e, "tlfe_force_matvec: capture stream");
+    }
+    cudaError_t e = cudaStreamBeginCapture(g->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "tlfe_force_matvec: begin capture");
+    st = m->precision == TLFE_FP32 ? record_ops<float>(m, u, ud, v, aM, aK, aC, f, y, g->cap)
+                                   : record_ops<double>(m, u, ud, v, aM, aK, aC, f, y, g->cap);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(g->cap, &graph);
+    if (st != TLFE_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "tlfe_force_matvec: end capture");
+    e = cudaGraphInstantiate(&g->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        g->exec = nullptr;
+        return cuda_fail(e, "tlfe_force_matvec: graph instantiation");
+    }
+    g->u = u;
+    g->ud = ud;
+    g->v = v;
+    g->f = f;
+    g->y = y;
+    g->aM = aM;
+    g->aK = aK;
+    g->aC = aC;
+    g->sched_gen = m->sched_gen;
+    return TLFE_OK;
+}

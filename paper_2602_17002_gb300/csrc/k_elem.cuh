@@ -268,8 +268,20 @@ template <int ET, typename R, int OP, bool AFF> constexpr int min_ctas()
     return (OP == OP_FORCE && AFF) ? 4 : 3;
 }
 
+__device__ __forceinline__ void mbar_inval(uint64_t *bar)
+{
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// The work of one warp on the tiles t0, t0 + tstep, ... (n_my of them) of
+// the pass described by p: wbase is the warp's shared-memory region (laid out
+// by warp_region_bytes) and bar its NSLICE + 2 mbarriers, freshly initialised
+// by the caller (every phase count starts at 0). Returns false when a bounded
+// wait ran out (the status word has the timeout, and every copy the warp had
+// in flight has been waited for).
 template <int ET, int NQ, typename R, int OP, bool AFF, int MAT>
-__global__ void __launch_bounds__(128, min_ctas<ET, R, OP, AFF>()) k_elem(const KParams<R> p)
+__device__ __forceinline__ bool elem_tiles(const KParams<R> &p, unsigned char *wbase, uint64_t *bar, int t0,
+                                           int tstep, int n_my)
 {
     constexpr int NPE = Elem<ET>::NPE;
     constexpr int REC = Rec<OP, R>::REC;
@@ -284,39 +296,17 @@ __global__ void __launch_bounds__(128, min_ctas<ET, R, OP, AFF>()) k_elem(const 
     constexpr uint32_t AB = AFF ? AffRec<R>::BYTES : 0;
     constexpr bool PF_EARLY = AFF && OP != OP_VJP;  // where the next tile's L2 prefetch goes (see prefetch_next)
 
-    extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    const int wpb = blockDim.x >> 5;
-    const int umax = p.umax;
     const int MB = p.meta_bytes;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem) + wib * (NSLICE + 2);  // [wpb][NSLICE + 2] (<= 128 B)
     uint64_t *mbar = bar + NSLICE;
     const size_t MRB = (size_t)MB + AB;                        // metadata (+ affine) record bytes
-    unsigned char *wbase = smem + 128 + (size_t)wib * warp_region_bytes<ET, R, OP, AFF>(umax, MB);
     unsigned char *ring = wbase;
     unsigned char *mbuf = wbase + (AFF ? 0 : NSLICE * SL::BYTES);  // [2][MB + AB]
     R *work = reinterpret_cast<R *>(mbuf + 2 * MRB);           // patch [umax][REC], later slots
 
-    const int gw = blockIdx.x * wpb + wib;
-    const int W = gridDim.x * wpb;
-    // tiles of this warp: interleaved (t0 + k W) or, with tile_chunk, one
-    // contiguous run of neighbouring tiles (which share nodes through L2)
-    const int n_tiles = p.tile_end - p.tile_begin;
-    const int per = (n_tiles + W - 1) / W;
-    const int t0 = p.tile_chunk ? p.tile_begin + gw * per : p.tile_begin + gw;
-    const int tstep = p.tile_chunk ? 1 : W;
-    const int n_my = p.tile_chunk ? max(0, min(per, n_tiles - gw * per))
-                                  : (t0 < p.tile_end ? (p.tile_end - t0 + W - 1) / W : 0);
     const bool mass_only = OP == OP_MATVEC && p.mass_only != 0;
     const int n_slices = (mass_only || AFF) ? 0 : n_my * NQ;
     const bool need_ud = p.visc != 0;
-
-    if (lane == 0) {
-        for (int b = 0; b < NSLICE + 2; ++b) mbar_init(bar + b, 1);
-        fence_mbar_init();
-    }
-    __syncwarp();
 
     auto issue = [&](int j) {  // slab slice j of this warp into ring slot j % NSLICE
         const int t = t0 + (j / NQ) * tstep;
@@ -795,7 +785,39 @@ __global__ void __launch_bounds__(128, min_ctas<ET, R, OP, AFF>()) k_elem(const 
         if (lane == 0) atomicAdd(p.status + ST_TIMEOUT, 1);
         for (int j = sl_done; j < sl_issued; ++j) mbar_wait_bounded(bar + j % NSLICE, (uint32_t)((j / NSLICE) & 1));
         for (int k = mt_done; k < mt_issued; ++k) mbar_wait_bounded(mbar + (k & 1), (uint32_t)((k >> 1) & 1));
+        return false;
     }
+    return true;
+}
+
+// One element kernel per (type, quadrature, precision, op, path, material
+// mode): one launch per pass, warps persistent over the pass's tiles.
+template <int ET, int NQ, typename R, int OP, bool AFF, int MAT>
+__global__ void __launch_bounds__(128, min_ctas<ET, R, OP, AFF>()) k_elem(const KParams<R> p)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem) + wib * (NSLICE + 2);  // [wpb][NSLICE + 2] (<= 128 B)
+    unsigned char *wbase = smem + 128 + (size_t)wib * warp_region_bytes<ET, R, OP, AFF>(p.umax, p.meta_bytes);
+
+    const int gw = blockIdx.x * wpb + wib;
+    const int W = gridDim.x * wpb;
+    // tiles of this warp: interleaved (t0 + k W) or, with tile_chunk, one
+    // contiguous run of neighbouring tiles (which share nodes through L2)
+    const int n_tiles = p.tile_end - p.tile_begin;
+    const int per = (n_tiles + W - 1) / W;
+    const int t0 = p.tile_chunk ? p.tile_begin + gw * per : p.tile_begin + gw;
+    const int tstep = p.tile_chunk ? 1 : W;
+    const int n_my = p.tile_chunk ? max(0, min(per, n_tiles - gw * per))
+                                  : (t0 < p.tile_end ? (p.tile_end - t0 + W - 1) / W : 0);
+    if (lane == 0) {
+        for (int b = 0; b < NSLICE + 2; ++b) mbar_init(bar + b, 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    elem_tiles<ET, NQ, R, OP, AFF, MAT>(p, wbase, bar, t0, tstep, n_my);
 }
 
 }  // namespace tlfe

@@ -51,6 +51,23 @@ struct BlockStore {
     int64_t part_base = 0;           // sorted scatter: first partial-sum position of the block
 };
 
+// One persistent launch per operation over the passes of an FP32 mesh (atomic
+// or sorted scatter) whose blocks run the affine tile kernels: the work items
+// (pass, first tile, end tile) in the order warps take them, and per fused op
+// (force, operator product) its launch schedule and warp-region size.
+struct FusedPlan {
+    std::vector<std::pair<int, int>> passes;  // (block, pass) covered, in table order
+    std::vector<bool> covered;                // per block: its passes run in the fused launch
+    int n_items = 0;
+    int4 *d_items = nullptr;
+    int *d_counter = nullptr;                 // one counter per fused op
+    LaunchSched sched[2];                     // [0] force, [1] operator product
+    size_t wreg[2] = {0, 0};
+    bool on[2] = {true, true};                // fused (true) or per-pass launches, per op
+};
+
+struct OpGraph;  // graph.cu: the captured force + operator-product call
+
 }  // namespace tlfe
 
 struct tlfe_mesh {
@@ -91,6 +108,12 @@ struct tlfe_mesh {
     int64_t *d_part_ptr = nullptr;
     int32_t *d_part_pos = nullptr;
     void *d_part = nullptr;
+    // fused launch plan (nullptr when the mesh has fewer than two passes the
+    // fused kernels cover, or is FP64 or coloured) and the launch mode
+    tlfe::FusedPlan *fused = nullptr;
+    int launch_mode = TLFE_LAUNCH_AUTO;
+    tlfe::OpGraph *fm_graph = nullptr;
+    int sched_gen = 0;  // bumped whenever launch schedules, mode or block parameters change
 };
 
 namespace tlfe {
@@ -107,6 +130,7 @@ struct TraceRange {
 #define TLFE_TRACE(name) tlfe::TraceRange tlfe_trace_range_(name)
 
 tlfe_status fail(tlfe_status st, const std::string &msg);
+void destroy_graphs(tlfe_mesh *m);  // graph.cu
 tlfe_status cuda_fail(cudaError_t e, const char *where);
 void *dalloc(tlfe_mesh *m, size_t bytes, cudaError_t *err);
 void destroy_newton(tlfe_mesh *m);

@@ -22,6 +22,7 @@ SVK, NEOHOOKE, MOONEY_RIVLIN = 0, 1, 2
 FP64, FP32 = 0, 1
 SCATTER_ATOMIC, SCATTER_COLOR, SCATTER_SORTED = 0, 1, 2
 PATH_AUTO, PATH_SLAB, PATH_AFFINE = 0, 1, 2
+LAUNCH_AUTO, LAUNCH_PER_PASS, LAUNCH_FUSED = 0, 1, 2
 NPE = {T4: 4, T10: 10, H8: 8, Q27: 27}
 
 STATUS = {0: "TLFE_OK", 1: "TLFE_E_INVALID", 2: "TLFE_E_OOM", 3: "TLFE_E_CUDA", 4: "TLFE_E_INVERTED",
@@ -56,7 +57,9 @@ class tlfe_mesh_info(C.Structure):
                 ("n_colors", C.c_int32), ("precision", C.c_int32), ("scatter", C.c_int32),
                 ("n_qp", C.c_int64), ("stream_bytes_force", C.c_int64),
                 ("stream_bytes_matvec", C.c_int64), ("stream_bytes_vjp", C.c_int64),
-                ("device_bytes", C.c_int64), ("n_affine_blocks", C.c_int32), ("n_passes", C.c_int32)]
+                ("device_bytes", C.c_int64), ("n_affine_blocks", C.c_int32), ("n_passes", C.c_int32),
+                ("n_fused_passes", C.c_int32), ("n_fused_items", C.c_int32), ("launches_force", C.c_int32),
+                ("launches_matvec", C.c_int32)]
 
 
 class tlfe_step_params(C.Structure):
@@ -82,7 +85,7 @@ CON_DTYPE = np.dtype([("type", np.int32), ("elem", np.int32, (4,)), ("xi", np.fl
 _lib = None
 
 EXPORTS = ["tlfe_create_mesh", "tlfe_destroy_mesh", "tlfe_get_mesh_info", "tlfe_get_colors",
-           "tlfe_get_scatter_targets", "tlfe_sync",
+           "tlfe_get_scatter_targets", "tlfe_set_launch_mode", "tlfe_force_matvec", "tlfe_sync",
            "tlfe_internal_force", "tlfe_internal_force_host", "tlfe_tangent_matvec", "tlfe_jacobi_diag",
            "tlfe_vjp", "tlfe_set_elem_mu_lambda", "tlfe_autotune", "tlfe_point_loads", "tlfe_surface_traction",
            "tlfe_constraint_eval", "tlfe_constraint_jt", "tlfe_constraint_j", "tlfe_newton_step", "tlfe_body_norms", "tlfe_norm_noalloc", "tlfe_selftest_wait_timeout", "tlfe_last_error",
@@ -105,6 +108,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "tlfe_get_mesh_info": [P, C.POINTER(tlfe_mesh_info)],
         "tlfe_get_colors": [P, P],
         "tlfe_get_scatter_targets": [P, P, P],
+        "tlfe_set_launch_mode": [P, I],
+        "tlfe_force_matvec": [P, P, P, P, D, D, D, P, P, P],
         "tlfe_sync": [P, P, C.POINTER(C.c_int64)],
         "tlfe_internal_force": [P, P, P, P, P],
         "tlfe_internal_force_host": [P, P, P, P, P],
@@ -240,6 +245,24 @@ class Mesh:
             out_s.append(s[off:off + n * npe].reshape(n, npe))
             off += n * npe
         return out_g, out_s
+
+    def set_launch_mode(self, mode):
+        """LAUNCH_AUTO, LAUNCH_PER_PASS or LAUNCH_FUSED (tlfe_set_launch_mode)."""
+        _check(load().tlfe_set_launch_mode(self._h, int(mode)))
+        self.info = self.get_info()
+
+    def force_matvec(self, u, udot, v, a_M=0.0, a_K=1.0, a_C=0.0, f=None, y=None, stream=None):
+        """f = f_int(u, udot) and y = a_M M v + a_K K_t v + a_C C v in one call,
+        replayed from a CUDA graph the mesh keeps (tlfe_force_matvec)."""
+        import torch
+        self._node_array(u, "u", torch.float64)
+        self._node_array(udot, "udot")
+        self._node_array(v, "v")
+        f = self._new() if f is None else self._node_array(f, "f")
+        y = self._new() if y is None else self._node_array(y, "y")
+        _check(load().tlfe_force_matvec(self._h, _ptr(u), _ptr(udot), _ptr(v), float(a_M), float(a_K), float(a_C),
+                                        _ptr(f), _ptr(y), _stream(stream)))
+        return f, y
 
     def close(self):
         if getattr(self, "_h", None):
