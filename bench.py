@@ -80,7 +80,7 @@ FLOP_PER_QP_BATCH = {(0, 0): {"force": 288.3, "matvec": 503.3}, (0, 1): {"force"
                      (2, 0): {"force": 540.0, "matvec": 942.3}, (2, 1): {"force": 610.4, "matvec": 1124.7}}
 # how the end-to-end measurements move data
 OVERLAP = ("copies on their own streams: the next step's inputs are copied in while a step computes (two device "
-           "input sets), outputs are copied out as their operations end (two device output sets)")
+           "staging sets), outputs are copied out as their operations end")
 # FP32 FMA roof: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz (maximum SM clock)
 ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
@@ -88,6 +88,46 @@ ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # ---------------------------------------------------------------------------
 # shared helpers
 # ---------------------------------------------------------------------------
+
+_ALU = {}
+
+
+def alu_peaks():
+    """Measured FMA peaks of this GPU (tlfe_peak_probe: independent FMA chains on
+    every lane, CUDA events, best of 5 launches), FP32 and FP64, in TFLOP/s,
+    with the SM clock sampled while the FP32 probe ran. Cached per process."""
+    if not _ALU:
+        import torch
+        from paper_2602_17002_gb300 import tlfe
+        tlfe.load()
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            f32, ms32 = clk.timed(lambda: tlfe.peak_probe(tlfe.FP32, ctas_per_sm=4, iters=1 << 16))
+        f64, ms64 = tlfe.peak_probe(tlfe.FP64, ctas_per_sm=4, iters=1 << 12)
+        c = clk.summary()
+        _ALU.update(fp32=f32, fp64=f64, sm_mhz=c["sm_mhz"],
+                    source=f"measured: tlfe_peak_probe FMA chains, {f32:.1f} TFLOP/s FP32 and {f64:.2f} TFLOP/s FP64 "
+                           f"at {c['sm_mhz']} MHz SM clock (derived nominal FP32: 152 x 128 x 2 x 2.07 GHz = "
+                           f"{ALU_PEAK_TFLOPS:.1f})")
+    return _ALU
+
+
+def survey_bytes(wl, s=4):
+    """Algorithmic bytes of one force / operator product / adjoint by the
+    minimum-traffic count with streamed reference data: connectivity 4 n,
+    reference gradients 3 n Q s and weights Q s per element (2 s more with
+    per-element parameters); each input node array read once and each output
+    node array written once (3 s per node); the adjoint also writes the
+    parameter gradient (2 s per element). Node arrays count at the element
+    precision s."""
+    npe = {0: 4, 1: 10, 2: 8, 3: 27}
+    el = sum(b.n_elem * (4 * npe[b.etype] + 3 * npe[b.etype] * b.nq * s + b.nq * s) for b in wl.blocks)
+    if wl.elem_mu_lambda is not None:
+        el += 2 * s * wl.n_elem
+    node = 3 * s * wl.n_nodes
+    n_in = 2 if wl.udot is not None else 1
+    return {"force": el + node * (n_in + 1), "matvec": el + node * (n_in + 2),
+            "vjp": el + node * (n_in + 1 + n_in) + 2 * s * wl.n_elem}
+
 
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -139,7 +179,11 @@ def ncu_traffic(kernel_key):
 
 
 class ClockSampler:
-    """nvidia-smi samples during the timed region."""
+    """nvidia-smi samples (every 20 ms) around the timed region. Each sample
+    is stamped with the host time it arrived; timed() marks the region, and
+    summary() keeps the samples that fall inside it (widened by 50 ms, the
+    reporting lag), or, when the region is shorter than the sampling period,
+    the sample nearest to it."""
 
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -149,21 +193,31 @@ class ClockSampler:
         self.index = index
         self.proc = None
         self.lines = []
+        self.win = None
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            time.sleep(0.3)                      # the first samples arrive before the timed region
         except Exception:
             self.proc = None
         return self
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def timed(self, fn):
+        """Run fn() as the timed region and remember its host-time window."""
+        t0 = time.perf_counter()
+        out = fn()
+        self.win = (t0, time.perf_counter())
+        time.sleep(0.1)
+        return out
 
     def __exit__(self, *a):
         if self.proc:
@@ -175,22 +229,34 @@ class ClockSampler:
             self.t.join(timeout=2)
 
     def summary(self):
-        sm, smax, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        rows = []
+        for ts, ln in self.lines:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 8:
                 continue
             try:
-                sm.append(float(parts[0]))
-                smax = float(parts[1])
+                rows.append((ts, float(parts[0]), float(parts[1]), parts[4:8]))
             except ValueError:
                 continue
-            for nm, val in zip(names, parts[4:8]):
+        sel, how = rows, "all samples"
+        if self.win and rows:
+            t0, t1 = self.win
+            sel = [r for r in rows if t0 - 0.05 <= r[0] <= t1 + 0.05]
+            how = "inside the timed region"
+            if not sel:
+                mid = 0.5 * (t0 + t1)
+                sel = [min(rows, key=lambda r: abs(r[0] - mid))]
+                how = f"nearest sample, {abs(sel[0][0] - mid) * 1e3:.0f} ms from the timed region's middle"
+        reasons = set()
+        for r in sel:
+            for nm, val in zip(names, r[3]):
                 if val.lower().startswith("active"):
                     reasons.add(nm)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        return {"sm_mhz": statistics.median([r[1] for r in sel]) if sel else None,
+                "sm_max_mhz": sel[-1][2] if sel else None, "reasons": sorted(reasons), "samples": len(sel),
+                "selection": how,
+                "timed_region_ms": (self.win[1] - self.win[0]) * 1e3 if self.win else None}
 
 
 def dist_setup():
@@ -553,7 +619,7 @@ def run_beam(args, rank, world, workload="beam"):
     barrier(world)
     torch.cuda.synchronize()
     with ClockSampler(torch.cuda.current_device()) as clk:
-        evs = timed_steps(step, args.steps, flush, stream, 4, tag + "_affine_timed")
+        evs = clk.timed(lambda: timed_steps(step, args.steps, flush, stream, 4, tag + "_affine_timed"))
     barrier(world)
     st = mesh.sync()
     per = np.array([[evs[k][j].elapsed_time(evs[k][j + 1]) for j in range(3)] for k in range(args.steps)])
@@ -568,74 +634,42 @@ def run_beam(args, rank, world, workload="beam"):
     flops = fpq[names[j]] * units if fpq[names[j]] else None
     achieved = flops / (kern_ms[j] * 1e-3) / 1e12 if flops else None
     hbm = bytes_alg[j] / (kern_ms[j] * 1e-3) / 1e9
-    roof = {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / ALU_PEAK_TFLOPS if achieved else None,
+    alu = alu_peaks()
+    roof = {"bound": "alu", "achieved": achieved, "peak": alu["fp32"], "unit": "TFLOP/s",
+            "frac": achieved / alu["fp32"] if achieved else None,
             "traffic": ncu_traffic(pre + names[j]), "kernel": names[j],
-            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz",
+            "peak_source": alu["source"],
             "algorithmic_flops": flops, "flop_per_qp": fpq[names[j]],
             "algorithmic_bytes": bytes_alg[j], "hbm_achieved_gbs": hbm, "hbm_peak_gbs": peak,
             "hbm_frac": hbm / peak, "hbm_peak_source": peak_kind}
+    # the same kernels against HBM by the minimum-traffic byte count with
+    # streamed reference gradients (what the slab path moves); the affine
+    # path forms those gradients instead of reading them
+    sb = survey_bytes(wl)
+    roof["streamed_bytes"] = sb[names[j]]
+    roof["streamed_hbm_frac"] = sb[names[j]] / (kern_ms[j] * 1e-3) / 1e9 / peak
+    kernels_streamed_frac = {n: sb[n] / (t * 1e-3) / 1e9 / peak for n, t in zip(names, kern_ms)}
 
-    # end to end through the public API with host buffers (pinned), copies
-    # timed: every step copies u, udot and v in and f, K v, g_u, g_udot and
-    # g_theta out. Three streams: host-to-device copies, the compute stream
-    # and device-to-host copies; the next step's inputs come in while this
-    # step computes (two device input sets), and each output goes back as soon
-    # as its operation has finished (two device output sets)
+    # end to end through the C ABI with host buffers (tlfe_step_host, pinned
+    # memory), copies timed: every step copies u, udot and v in and f, K v,
+    # g_u, g_udot and g_theta out. The library alternates two device staging
+    # sets and copies on two streams of its own, so each call's transfers
+    # overlap its neighbours' computation; step_host_wait ends the region.
     hu, hud, hv = u.cpu().pin_memory(), ud.cpu().pin_memory(), v.cpu().pin_memory()
     hf, hy, hgu, hgud = (torch.empty(ud.shape, dtype=ud.dtype).pin_memory() for _ in range(4))
     hgth = torch.empty(gth.shape, dtype=torch.float64).pin_memory()
-    ins = [(torch.empty_like(u), torch.empty_like(ud), torch.empty_like(ud)) for _ in range(2)]
-    outs2 = [outs, [torch.empty_like(ud) for _ in range(4)]]
-    gths = [gth, torch.empty_like(gth)]
-    inner = [make_step(mesh, *ins[i], outs2[i], gths[i]) for i in range(2)]
-    h2d_s, d2h_s = torch.cuda.Stream(), torch.cuda.Stream()
-    ev = lambda: torch.cuda.Event()
 
     def e2e_run(n):
-        in_ready, comp_done, out_done = [ev(), ev()], [None, None], [None, None]
+        for _ in range(n):
+            mesh.step_host(hu, hud, hv, hv, f=hf, y=hy, g_u=hgu, g_udot=hgud, g_mu_lambda=hgth,
+                           a_M=0.0, a_K=1.0, a_C=1.0, stream=stream)
+        mesh.step_host_wait()
 
-        def h2d(b):
-            if comp_done[b] is not None:
-                h2d_s.wait_event(comp_done[b])          # the last step that read this input set has ended
-            with torch.cuda.stream(h2d_s):
-                for d, h in zip(ins[b], (hu, hud, hv)):
-                    d.copy_(h, non_blocking=True)
-            in_ready[b].record(h2d_s)
-
-        h2d(0)
-        for k in range(n):
-            b = k & 1
-            stream.wait_event(in_ready[b])
-            if out_done[b] is not None:
-                stream.wait_event(out_done[b])          # the step two back has copied this output set out
-            e = [ev() for _ in range(4)]
-            inner[b](e)
-            comp_done[b] = e[3]
-            if k + 1 < n:
-                h2d(b ^ 1)
-            f_, y_, gu_, gud_ = outs2[b]
-            with torch.cuda.stream(d2h_s):
-                d2h_s.wait_event(e[1])
-                hf.copy_(f_, non_blocking=True)
-                d2h_s.wait_event(e[2])
-                hy.copy_(y_, non_blocking=True)
-                d2h_s.wait_event(e[3])
-                hgu.copy_(gu_, non_blocking=True)
-                hgud.copy_(gud_, non_blocking=True)
-                hgth.copy_(gths[b], non_blocking=True)
-            out_done[b] = ev()
-            out_done[b].record(d2h_s)
-        for o in out_done:
-            if o is not None:
-                stream.wait_event(o)
-
-    e2e_run(2)
+    e2e_run(3)
     torch.cuda.synchronize()
     barrier(world)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    h2d_s.wait_event(e0)
     e2e_run(args.steps)
     e1.record(stream)
     torch.cuda.synchronize()
@@ -665,6 +699,7 @@ def run_beam(args, rank, world, workload="beam"):
     line.update({
         "kernels_ms": {n: float(t) for n, t in zip(names, kern_ms)},
         "kernels_gbs": {n: b / (t * 1e-3) / 1e9 for n, b, t in zip(names, bytes_alg, kern_ms)},
+        "kernels_streamed_hbm_frac": kernels_streamed_frac,
         "force_qps": units / (kern_ms[0] * 1e-3),
         "kernels_tflops": {n: fpq[n] * units / (t * 1e-3) / 1e12 if fpq[n] else None
                            for n, t in zip(names, kern_ms)},
@@ -674,7 +709,7 @@ def run_beam(args, rank, world, workload="beam"):
         "fp64_plain": {"ms_per_step": ms64, "kernels_ms": {n: float(t) for n, t in zip(names, per64.mean(axis=0))},
                        "speedup_fp32_over_fp64": ms64 / step_ms, "device_status": st64},
         "e2e": {"value": world * units / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "call": "tlfe_step_host (C ABI, host buffers)",
                 "overlap": OVERLAP,
                 "max_rel_diff_vs_device_step": e2e_err, "device_status": st_e2e},
         "gpu_launches": 3 * args.steps,
@@ -719,7 +754,7 @@ def run_newton(args, rank, world):
     torch.cuda.synchronize()
     barrier(world)
     with ClockSampler(torch.cuda.current_device()) as clk:
-        evs = timed_steps(step, args.steps, flush, stream)
+        evs = clk.timed(lambda: timed_steps(step, args.steps, flush, stream))
     barrier(world)
     ms = allmax(float(np.mean([e[0].elapsed_time(e[1]) for e in evs])), world)
     rep = reps[-1]
@@ -819,34 +854,19 @@ def run_batch(args, rank, world):
     v = torch.from_numpy(wl.v).to("cuda", torch.float32)
     f, y = torch.empty_like(v), torch.empty_like(v)
     flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device="cuda")
-    side = torch.cuda.Stream()
-    L = tlfe.load()
-    # two buffer sets (u, v, f, y), one graph each: the timed step replays the
-    # first; the end-to-end run alternates them
-    bufs = [(u, v, f, y), (torch.empty_like(u), torch.empty_like(v), torch.empty_like(v), torch.empty_like(v))]
-
-    def calls(s, u_, v_, f_, y_):
-        sp = tlfe._stream(s)
-        tlfe._check(L.tlfe_internal_force(mesh.handle, tlfe._ptr(u_), None, tlfe._ptr(f_), sp))
-        tlfe._check(L.tlfe_tangent_matvec(mesh.handle, tlfe._ptr(u_), None, tlfe._ptr(v_), 0.0, 1.0, 0.0,
-                                          tlfe._ptr(y_), sp))
-
-    mesh.autotune(u, None, v)
-    with torch.cuda.stream(side):
-        for _ in range(2):
-            calls(side, *bufs[0])            # occupancy and schedule caches filled before capture
-    torch.cuda.synchronize()
-    graphs = [torch.cuda.CUDAGraph() for _ in range(2)]
-    for gr, bf in zip(graphs, bufs):
-        with torch.cuda.graph(gr, stream=side):
-            calls(side, *bf)
-    g = graphs[0]
     stream = torch.cuda.current_stream()
+    # schedules by measurement: per pass and CTA size, and the fused launch
+    # (one persistent launch per operation over every pass) against the
+    # per-pass launches; then the timed step is the library's own graph of
+    # force + K v (tlfe_force_matvec: captured on the first call, replayed)
+    mesh.autotune(u, None, v)
+    info = mesh.info
+    mesh.force_matvec(u, None, v, 0.0, 1.0, 0.0, f=f, y=y)
 
     def step(ev=None):
         if ev:
             ev[0].record(stream)
-        g.replay()
+        mesh.force_matvec(u, None, v, 0.0, 1.0, 0.0, f=f, y=y)
         if ev:
             ev[1].record(stream)
 
@@ -855,10 +875,18 @@ def run_batch(args, rank, world):
     torch.cuda.synchronize()
     barrier(world)
     with ClockSampler(torch.cuda.current_device()) as clk:
-        evs = timed_steps(step, args.steps, flush, stream, label="batch_timed")
+        evs = clk.timed(lambda: timed_steps(step, args.steps, flush, stream, label="batch_timed"))
     barrier(world)
     st = mesh.sync()
     ms = allmax(float(np.mean([e[0].elapsed_time(e[1]) for e in evs])), world)
+    # the same step with one launch per pass (context for the fused launch)
+    mesh.set_launch_mode(tlfe.LAUNCH_PER_PASS)
+    for _ in range(2):
+        step()
+    evs_pp = timed_steps(step, max(3, args.steps // 2), flush, stream, label="batch_per_pass")
+    ms_pp = float(np.mean([e[0].elapsed_time(e[1]) for e in evs_pp]))
+    launches_pp = mesh.info["launches_force"] + mesh.info["launches_matvec"]
+    mesh.set_launch_mode(tlfe.LAUNCH_AUTO)
     units = wl.n_qp
     peak, peak_kind = peaks()
     b_alg = info["stream_bytes_force"] + info["stream_bytes_matvec"]
@@ -872,50 +900,21 @@ def run_batch(args, rank, world):
             f_qp = FLOP_PER_QP_BATCH[(b.etype, law)]
             flops += int((laws == law).sum()) * b.nq * (f_qp["force"] + f_qp["matvec"])
     achieved = flops / (ms * 1e-3) / 1e12
-    # e2e: u and v from pinned host memory, f and K v back, every step; the
-    # copies run on their own streams, overlapped with the other buffer set's
-    # graph replay
+    # e2e through the C ABI with host buffers (tlfe_step_host): u and v in,
+    # f and K v out, every step; the library overlaps each call's transfers
+    # with its neighbours' computation
     hu, hv = u.cpu().pin_memory(), v.cpu().pin_memory()
     hf, hy = torch.empty_like(hv).pin_memory(), torch.empty_like(hv).pin_memory()
-    h2d_s, d2h_s = torch.cuda.Stream(), torch.cuda.Stream()
 
     def e2e_run(n):
-        in_ready, comp_done, out_done = [torch.cuda.Event(), torch.cuda.Event()], [None, None], [None, None]
-
-        def h2d(b):
-            if comp_done[b] is not None:
-                h2d_s.wait_event(comp_done[b])          # the last replay that read this set has ended
-            with torch.cuda.stream(h2d_s):
-                bufs[b][0].copy_(hu, non_blocking=True)
-                bufs[b][1].copy_(hv, non_blocking=True)
-            in_ready[b].record(h2d_s)
-
-        h2d(0)
-        for k in range(n):
-            b = k & 1
-            stream.wait_event(in_ready[b])
-            if out_done[b] is not None:
-                stream.wait_event(out_done[b])          # this set's outputs of two steps back are out
-            graphs[b].replay()
-            comp_done[b] = torch.cuda.Event()
-            comp_done[b].record(stream)
-            if k + 1 < n:
-                h2d(b ^ 1)
-            with torch.cuda.stream(d2h_s):
-                d2h_s.wait_event(comp_done[b])
-                hf.copy_(bufs[b][2], non_blocking=True)
-                hy.copy_(bufs[b][3], non_blocking=True)
-            out_done[b] = torch.cuda.Event()
-            out_done[b].record(d2h_s)
-        for o in out_done:
-            if o is not None:
-                stream.wait_event(o)
+        for _ in range(n):
+            mesh.step_host(hu, None, hv, None, f=hf, y=hy, a_M=0.0, a_K=1.0, a_C=0.0, stream=stream)
+        mesh.step_host_wait()
 
     e2e_run(2)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    h2d_s.wait_event(e0)
     e2e_run(args.steps)
     e1.record(stream)
     torch.cuda.synchronize()
@@ -924,21 +923,27 @@ def run_batch(args, rank, world):
     line = base_line(args, world, "batch", world * units / (ms * 1e-3), UNIT, ms, "f32",
                      n_bodies=wl.n_bodies, n_elem=wl.n_elem, n_nodes=wl.n_nodes, n_qp=units,
                      elements_by_type={types[b.etype]: b.n_elem for b in wl.blocks},
-                     step="internal force + K v over all bodies, one CUDA graph replay")
+                     step="internal force + K v over all bodies, one replay of the library's CUDA graph "
+                          "(tlfe_force_matvec)")
     if wl.n_bodies != 512:
         line["config"]["workload"] = WORKLOADS["batch"].replace("512 bodies", f"{wl.n_bodies} bodies")
     line.update({
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / ALU_PEAK_TFLOPS,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peaks()["fp32"], "unit": "TFLOP/s",
+                     "frac": achieved / alu_peaks()["fp32"],
                      "traffic": ncu_traffic("batch512_step") if wl.n_bodies == 512 else None,
                      "kernel": "force + matvec, all element blocks (one step)",
-                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz",
+                     "peak_source": alu_peaks()["source"],
                      "algorithmic_flops": flops, "algorithmic_bytes": b_alg, "hbm_achieved_gbs": hbm,
                      "hbm_peak_gbs": peak, "hbm_frac": hbm / peak, "hbm_peak_source": peak_kind},
         "e2e": {"value": world * units / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": u.numel() * 8 + v.numel() * 4, "d2h_bytes_per_step": 2 * v.numel() * 4,
-                "overlap": OVERLAP},
-        "gpu_launches": 2 * info["n_passes"] * args.steps,
+                "call": "tlfe_step_host (C ABI, host buffers)", "overlap": OVERLAP},
+        "launch": {"mode": "fused" if info["launches_force"] == 1 else "per pass",
+                   "fused_passes": info["n_fused_passes"], "fused_items": info["n_fused_items"],
+                   "passes": info["n_passes"], "launches_per_step": info["launches_force"] + info["launches_matvec"],
+                   "graph": "tlfe_force_matvec (captured by the library, replayed)",
+                   "per_pass": {"ms_per_step": ms_pp, "launches_per_step": launches_pp}},
+        "gpu_launches": (info["launches_force"] + info["launches_matvec"]) * args.steps,
         "clocks": clk.summary(), "device_status": st})
     mesh.close()
     return line, wl
@@ -986,7 +991,7 @@ def run_diff(args, rank, world):
     torch.cuda.synchronize()
     barrier(world)
     with ClockSampler(torch.cuda.current_device()) as clk:
-        evs = timed_steps(step, args.steps, flush, stream, 3)
+        evs = clk.timed(lambda: timed_steps(step, args.steps, flush, stream, 3))
     barrier(world)
     st = mesh.sync()
     ms = allmax(float(np.mean([e[0].elapsed_time(e[2]) for e in evs])), world)
@@ -1069,10 +1074,10 @@ def run_diff(args, rank, world):
                      step="autograd forward (tlfe_internal_force) + loss in torch + backward (tlfe_vjp)")
     line.update({
         "phases_ms": {"forward_and_loss": ms_fwd, "backward": ms_bwd},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / ALU_PEAK_TFLOPS, "traffic": None,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peaks()["fp32"], "unit": "TFLOP/s",
+                     "frac": achieved / alu_peaks()["fp32"], "traffic": None,
                      "kernel": "backward: tlfe_vjp (+ the loss gradient)",
-                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz",
+                     "peak_source": alu_peaks()["source"],
                      "algorithmic_flops": flops, "flop_per_qp": fpq["vjp"], "algorithmic_bytes": b_bwd,
                      "hbm_achieved_gbs": hbm, "hbm_peak_gbs": peak, "hbm_frac": hbm / peak,
                      "hbm_peak_source": peak_kind},
@@ -1082,6 +1087,31 @@ def run_diff(args, rank, world):
         "gpu_launches": 2 * args.steps, "clocks": clk.summary(), "device_status": st})
     mesh.close()
     return line, wl
+
+
+def cpu_baseline(workload, wl, unit, n_sample, single_core=True):
+    """The oracle on a bounded sample of the workload on all host cores
+    (spawned processes over element ranges), with the one-core time of the
+    same sample beside it; the Newton sample (one body) on one core."""
+    if workload == "diff":
+        wl.v = diff_cotangent(wl)
+    base = None
+    if single_core or workload == "newton":
+        val, secs, thr, what = cpu_sample(workload, wl, n_sample)
+        base = {"value": val, "unit": unit, "cores": thr, "kind": "oracle", "sample": what}
+    pool_info = oracle_pool(workload, wl, n_sample)
+    if not pool_info:
+        return base
+    try:
+        cpu_sample_parallel(workload, wl, pool_info)   # warm-up
+        pv, ps, procs, pwhat = cpu_sample_parallel(workload, wl, pool_info)
+    finally:
+        pool_info[0].close()
+        pool_info[0].join()
+    out = {"value": pv, "unit": unit, "cores": procs, "kind": "oracle", "sample": pwhat}
+    if base:
+        out["single_core"] = base
+    return out
 
 
 def main():
@@ -1099,6 +1129,11 @@ def main():
                     help="element scatter of the meshes (of the batched step for newton): atomic adds, "
                          "deterministic colour passes, or deterministic node-ordered partial sums")
     ap.add_argument("--log", default=None, help="also append the JSON line to this file (JSON lines)")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="default workload: skip the batch, Newton and differentiation sub-measurements")
+    ap.add_argument("--sub-steps", type=int, default=5, help="timed steps of each sub-measurement")
+    ap.add_argument("--sub-cpu-sample", type=int, default=12000,
+                    help="elements in the sub-measurements' cpu_baseline samples")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -1106,26 +1141,30 @@ def main():
         return run_reference(args)
 
     rank, world, _ = dist_setup()
-    run = {"beam": run_beam, "newton": run_newton, "batch": run_batch, "diff": run_diff,
-           "q27": lambda a, r, w: run_beam(a, r, w, "q27")}[args.workload]
-    line, wl = run(args, rank, world)
+    runs = {"beam": run_beam, "newton": run_newton, "batch": run_batch, "diff": run_diff,
+            "q27": lambda a, r, w: run_beam(a, r, w, "q27")}
+    line, wl = runs[args.workload](args, rank, world)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        if args.workload == "diff":
-            wl.v = diff_cotangent(wl)
-        val, secs, thr, what = cpu_sample(args.workload, wl, args.cpu_sample)
-        base = {"value": val, "unit": line["unit"], "cores": thr, "kind": "oracle", "sample": what}
-        pool_info = oracle_pool(args.workload, wl, args.cpu_sample)
-        if pool_info:   # the same sample on all host cores; the one-core run beside it
-            try:
-                cpu_sample_parallel(args.workload, wl, pool_info)   # warm-up
-                pv, ps, procs, pwhat = cpu_sample_parallel(args.workload, wl, pool_info)
-            finally:
-                pool_info[0].close()
-                pool_info[0].join()
-            line["cpu_baseline"] = {"value": pv, "unit": line["unit"], "cores": procs, "kind": "oracle",
-                                    "sample": pwhat, "single_core": base}
-        else:
-            line["cpu_baseline"] = base
+        line["cpu_baseline"] = cpu_baseline(args.workload, wl, line["unit"], args.cpu_sample)
+    if args.workload == "beam" and not args.headline_only:
+        # the other benchmark configurations of the step, each measured here
+        # with its own clocks, roofline and CPU baseline, at fewer steps
+        sub_args = argparse.Namespace(**vars(args))
+        sub_args.steps = max(3, min(args.steps, args.sub_steps))
+        sub_args.warmup = 3
+        line["configs"] = {}
+        for name in ("batch", "newton", "diff"):
+            sl, swl = runs[name](sub_args, rank, world)
+            if rank == 0 and world == 1 and not args.no_cpu_baseline:
+                sl["cpu_baseline"] = cpu_baseline(name, swl, sl["unit"], args.sub_cpu_sample, single_core=False)
+            sl.pop("metric", None)
+            sl.pop("data", None)
+            line["configs"][name] = sl
+            del swl
+        line["gpu_launches"] = line["gpu_launches"] + sum(
+            (c.get("gpu_launches") or 0) for c in line["configs"].values())
+        line["gpu_launches_note"] = ("element, node-sum and probe kernels of the headline and the configs' timed "
+                                     "regions; the Newton step's graph launches follow its iteration counts")
     if args.scatter != "atomic":
         line["config"]["scatter"] = args.scatter + (" (batched step; the plain FP64 path stays atomic)"
                                                     if args.workload == "newton" else "")

@@ -228,6 +228,43 @@ tlfe_status tlfe_internal_force(tlfe_mesh *mesh, const void *u_dev, const void *
 tlfe_status tlfe_internal_force_host(tlfe_mesh *mesh, const void *u_host, const void *udot_host,
                                      void *f_host, void *stream);
 
+/* Element operations of one state on HOST buffers, for callers whose data
+ * live in host memory (the force of Sec. 4.3, the operator product and the
+ * vector-Jacobian products below). Arrays have the layouts and dtypes of the
+ * device calls: u_host double [n_nodes][3]; udot, v, cot, f, y, g_u, g_udot in
+ * the mesh dtype [n_nodes][3]; g_mu_lambda double [n_elem][2]. udot may be
+ * NULL. Each operation runs when its inputs and an output are given:
+ *   f_host                       -> tlfe_internal_force
+ *   v_host and y_host            -> tlfe_tangent_matvec (a_M, a_K, a_C)
+ *   cot_host and any g_*_host    -> tlfe_vjp
+ * Asynchronous: the call copies the inputs into one of two sets of device
+ * staging buffers held by the handle (consecutive calls alternate) on a copy
+ * stream of its own, runs the operations on `stream` once the inputs are in,
+ * and copies each output back on a second copy stream as soon as its
+ * operation has ended, so that consecutive calls overlap their transfers with
+ * each other's computation. Host buffers must stay valid, and inputs
+ * unchanged, until tlfe_step_host_wait returns; outputs are complete then.
+ * Pinned (page-locked) host memory is needed for the copies to overlap. The
+ * first call allocates the staging buffers and copy streams. */
+typedef struct {
+    const double *u_host;
+    const void *udot_host;
+    const void *v_host;
+    const void *cot_host;
+    double a_M, a_K, a_C;
+    void *f_host;
+    void *y_host;
+    void *g_u_host;
+    void *g_udot_host;
+    double *g_mu_lambda_host;
+} tlfe_host_step;
+
+tlfe_status tlfe_step_host(tlfe_mesh *mesh, const tlfe_host_step *args, void *stream);
+
+/* Wait until every tlfe_step_host call issued on the handle has finished,
+ * its outputs written to the host buffers. */
+tlfe_status tlfe_step_host_wait(tlfe_mesh *mesh);
+
 /* Matrix-free operator product (App. C; Newton matrix of Sec. 2.2 / Sec. 7):
  *   y = a_M M v + a_K K_t(u, udot) v + a_C C(u) v
  * M: consistent mass m_ij = rho int s_i s_j dV (Sec. 4.1), K_t = d f_int / d x
@@ -458,6 +495,17 @@ tlfe_status tlfe_norm_noalloc(const double *x_dev, int64_t n, double *out_dev, v
  * tlfe_sync returns TLFE_E_TIMEOUT and clears the status, and the mesh and
  * the CUDA context stay usable. Stream-ordered; no fault, no trap. */
 tlfe_status tlfe_selftest_wait_timeout(tlfe_mesh *mesh, int64_t spin_limit, void *stream);
+
+/* Arithmetic peak probe (no counterpart in the paper; the denominator of the
+ * element kernels' ALU roofline): enqueues one kernel of ctas_per_sm CTAs of
+ * 256 threads per SM in which every thread runs 16 independent fused
+ * multiply-add chains for `iters` rounds, in FP32 (precision = TLFE_FP32) or
+ * FP64 (TLFE_FP64). *flop_host receives the launch's FLOP count (2 per FMA);
+ * time the launch with events on `stream` for the rate. out_dev: device
+ * buffer of at least 2 values of that precision (receives a checksum).
+ * ctas_per_sm in [1, 32], iters in [1, 2^32]. Stream-ordered. */
+tlfe_status tlfe_peak_probe(int32_t precision, int32_t ctas_per_sm, int64_t iters, void *out_dev,
+                            double *flop_host, void *stream);
 
 /* Thread-local text of the last error (never NULL). */
 const char *tlfe_last_error(void);

@@ -739,6 +739,7 @@ extern "C" tlfe_status tlfe_destroy_mesh(tlfe_mesh *m)
     cudaDeviceSynchronize();
     destroy_newton(m);
     destroy_graphs(m);
+    destroy_host_stage(m);
     for (void *p : m->allocs) cudaFree(p);
     delete m->fused;
     delete m;

@@ -66,7 +66,8 @@ struct FusedPlan {
     bool on[2] = {true, true};                // fused (true) or per-pass launches, per op
 };
 
-struct OpGraph;  // graph.cu: the captured force + operator-product call
+struct OpGraph;    // graph.cu: the captured force + operator-product call
+struct HostStage;  // hoststep.cu: staging buffers and copy streams of tlfe_step_host
 
 }  // namespace tlfe
 
@@ -114,6 +115,7 @@ struct tlfe_mesh {
     int launch_mode = TLFE_LAUNCH_AUTO;
     tlfe::OpGraph *fm_graph = nullptr;
     int sched_gen = 0;  // bumped whenever launch schedules, mode or block parameters change
+    tlfe::HostStage *host_stage = nullptr;
 };
 
 namespace tlfe {
@@ -130,7 +132,8 @@ struct TraceRange {
 #define TLFE_TRACE(name) tlfe::TraceRange tlfe_trace_range_(name)
 
 tlfe_status fail(tlfe_status st, const std::string &msg);
-void destroy_graphs(tlfe_mesh *m);  // graph.cu
+void destroy_graphs(tlfe_mesh *m);      // graph.cu
+void destroy_host_stage(tlfe_mesh *m);  // hoststep.cu
 tlfe_status cuda_fail(cudaError_t e, const char *where);
 void *dalloc(tlfe_mesh *m, size_t bytes, cudaError_t *err);
 void destroy_newton(tlfe_mesh *m);

@@ -76,6 +76,13 @@ class tlfe_step_report(C.Structure):
                 ("c_norm", C.c_double)]
 
 
+class tlfe_host_step(C.Structure):
+    _fields_ = [("u_host", C.c_void_p), ("udot_host", C.c_void_p), ("v_host", C.c_void_p),
+                ("cot_host", C.c_void_p), ("a_M", C.c_double), ("a_K", C.c_double), ("a_C", C.c_double),
+                ("f_host", C.c_void_p), ("y_host", C.c_void_p), ("g_u_host", C.c_void_p),
+                ("g_udot_host", C.c_void_p), ("g_mu_lambda_host", C.c_void_p)]
+
+
 # bilateral constraint records (tlfe_constraint): points P, Q[, R, T] as (global
 # element, parent coordinates); element < 0 = ground point at world coordinates
 CON_CD, CON_DIST, CON_DP1, CON_DP2 = 0, 1, 2, 3
@@ -85,7 +92,8 @@ CON_DTYPE = np.dtype([("type", np.int32), ("elem", np.int32, (4,)), ("xi", np.fl
 _lib = None
 
 EXPORTS = ["tlfe_create_mesh", "tlfe_destroy_mesh", "tlfe_get_mesh_info", "tlfe_get_colors",
-           "tlfe_get_scatter_targets", "tlfe_set_launch_mode", "tlfe_force_matvec", "tlfe_sync",
+           "tlfe_get_scatter_targets", "tlfe_set_launch_mode", "tlfe_force_matvec", "tlfe_step_host",
+           "tlfe_step_host_wait", "tlfe_peak_probe", "tlfe_sync",
            "tlfe_internal_force", "tlfe_internal_force_host", "tlfe_tangent_matvec", "tlfe_jacobi_diag",
            "tlfe_vjp", "tlfe_set_elem_mu_lambda", "tlfe_autotune", "tlfe_point_loads", "tlfe_surface_traction",
            "tlfe_constraint_eval", "tlfe_constraint_jt", "tlfe_constraint_j", "tlfe_newton_step", "tlfe_body_norms", "tlfe_norm_noalloc", "tlfe_selftest_wait_timeout", "tlfe_last_error",
@@ -109,6 +117,9 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "tlfe_get_colors": [P, P],
         "tlfe_get_scatter_targets": [P, P, P],
         "tlfe_set_launch_mode": [P, I],
+        "tlfe_step_host": [P, C.POINTER(tlfe_host_step), P],
+        "tlfe_step_host_wait": [P],
+        "tlfe_peak_probe": [I, I, C.c_int64, P, C.POINTER(C.c_double), P],
         "tlfe_force_matvec": [P, P, P, P, D, D, D, P, P, P],
         "tlfe_sync": [P, P, C.POINTER(C.c_int64)],
         "tlfe_internal_force": [P, P, P, P, P],
@@ -263,6 +274,40 @@ class Mesh:
         _check(load().tlfe_force_matvec(self._h, _ptr(u), _ptr(udot), _ptr(v), float(a_M), float(a_K), float(a_C),
                                         _ptr(f), _ptr(y), _stream(stream)))
         return f, y
+
+    def step_host(self, u, udot=None, v=None, cot=None, f=None, y=None, g_u=None, g_udot=None,
+                  g_mu_lambda=None, a_M=0.0, a_K=1.0, a_C=0.0, stream=None):
+        """Host-buffer element operations (tlfe_step_host): every array is a
+        contiguous CPU torch tensor or numpy array (pinned memory lets the
+        copies overlap); u float64 (n_nodes, 3), the other node arrays in the
+        mesh dtype, g_mu_lambda float64 (n_elem, 2). Asynchronous: the outputs
+        are complete after step_host_wait()."""
+        import torch
+        dt = np.float32 if self.precision == FP32 else np.float64
+
+        def ptr(a, dtype, shape, name):
+            if a is None:
+                return None
+            if isinstance(a, torch.Tensor):
+                ok = (not a.is_cuda and a.is_contiguous() and tuple(a.shape) == shape
+                      and a.dtype == (torch.float32 if dtype == np.float32 else torch.float64))
+                p = a.data_ptr()
+            else:
+                ok = a.dtype == dtype and a.flags.c_contiguous and a.shape == shape
+                p = a.ctypes.data
+            if not ok:
+                raise TLFEError(1, f"{name} must be a contiguous host array {shape} of {np.dtype(dtype).name}")
+            return p
+        n3 = (self.n_nodes, 3)
+        args = tlfe_host_step(ptr(u, np.float64, n3, "u"), ptr(udot, dt, n3, "udot"), ptr(v, dt, n3, "v"),
+                              ptr(cot, dt, n3, "cot"), float(a_M), float(a_K), float(a_C),
+                              ptr(f, dt, n3, "f"), ptr(y, dt, n3, "y"), ptr(g_u, dt, n3, "g_u"),
+                              ptr(g_udot, dt, n3, "g_udot"),
+                              ptr(g_mu_lambda, np.float64, (self.info["n_elem"], 2), "g_mu_lambda"))
+        _check(load().tlfe_step_host(self._h, C.byref(args), _stream(stream)))
+
+    def step_host_wait(self):
+        _check(load().tlfe_step_host_wait(self._h))
 
     def close(self):
         if getattr(self, "_h", None):
@@ -542,6 +587,29 @@ def tlfe_newton_step(mesh: Mesh, u_n, v_n, h, **kw):
 
 def tlfe_body_norms(mesh: Mesh, x, out=None, stream=None):
     return mesh.body_norms(x, out=out, stream=stream)
+
+
+def peak_probe(precision=FP32, ctas_per_sm=4, iters=1 << 16, repeats=5, stream=None):
+    """FMA peak of this GPU in TFLOP/s (tlfe_peak_probe, timed with CUDA events
+    on the launching stream; best of `repeats` launches after one warm-up)."""
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    out = torch.zeros(2, dtype=torch.float32 if precision == FP32 else torch.float64, device="cuda")
+    flop = C.c_double(0.0)
+    L = load()
+    _check(L.tlfe_peak_probe(int(precision), int(ctas_per_sm), C.c_int64(iters), _ptr(out), C.byref(flop),
+                             _stream(s)))
+    best = None
+    for _ in range(repeats):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        _check(L.tlfe_peak_probe(int(precision), int(ctas_per_sm), C.c_int64(iters), _ptr(out), C.byref(flop),
+                                 _stream(s)))
+        e1.record(s)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    return flop.value / (best * 1e-3) / 1e12, best
 
 
 def tlfe_norm_noalloc(x, out, stream=None):
