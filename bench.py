@@ -292,19 +292,65 @@ def allmax(x, world):
     return float(t.item())
 
 
+def allsum(x, world):
+    """Sum of a host scalar over all ranks."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def job_value(units_per_rank, world, step_ms_max):
-    """Whole-job throughput of weak-scaled replicas: every rank processes
-    units_per_rank per step; the job takes the slowest rank's time."""
+    """Whole-job throughput when every rank processes units_per_rank per step
+    and the job takes the slowest rank's time."""
     return world * units_per_rank / (step_ms_max * 1e-3)
+
+
+SPLIT = {"beam": "slab", "q27": "slab", "diff": "slab", "batch": "bodies", "newton": "bodies"}
+
+
+def parallelism(workload, world):
+    if world == 1:
+        return "1 GPU"
+    if SPLIT[workload] == "slab":
+        return (f"slab split x{world}: the body's elements in {world} equal slabs along x, one per GPU; the "
+                f"duplicated interface nodes' partial results summed by one NCCL all-reduce of a compact buffer "
+                f"per operation")
+    return f"bodies bin-packed x{world} by cost (largest first onto the least-loaded GPU); no exchange"
 
 
 def base_line(args, world, workload, value, unit, step_ms, dtype, higher=True, **config):
     return {"metric": METRIC, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": higher, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": higher, "scaling": "strong",
             "vs_baseline": None, "dtype": dtype, "data": "synthetic (seeded)",
             "config": dict({"workload": WORKLOADS[workload],
                             "l2": "inputs > L2; 512 MiB memset flush before every timed step, outside its events",
-                            "parallelism": f"replicas x{world} (one independent problem per GPU)"}, **config)}
+                            "parallelism": parallelism(workload, world)}, **config)}
+
+
+def shard_one_body(wl, rank, world):
+    """This rank's slab of a one-body workload: (share, interface, element mask)."""
+    from paper_2602_17002_gb300 import shard
+    blocks = [(b.etype, b.nq, b.conn, b.body) for b in wl.blocks]
+    masks = shard.slab_partition(wl.X, blocks, world)
+    nodes_all = [shard.local_blocks(blocks, m)[0] for m in masks]
+    itf = shard.interfaces(nodes_all)[rank]
+    share, _ = shard.sub_workload(wl, masks[rank])
+    return share, itf, masks[rank]
+
+
+def shard_bodies(wl, rank, world):
+    """This rank's bodies of a many-body workload (cost-based bin packing):
+    (share with its bodies renumbered, their global ids)."""
+    from paper_2602_17002_gb300 import shard
+    blocks = [(b.etype, b.nq, b.conn, b.body) for b in wl.blocks]
+    parts = shard.pack_bodies(shard.body_costs(blocks, wl.n_bodies), world)
+    share, _ = shard.sub_workload(wl, shard.body_masks(blocks, parts[rank]), bodies=parts[rank])
+    return share, parts[rank]
 
 
 def timed_steps(step, steps, flush, stream, n_ev=2, label="timed"):
@@ -539,7 +585,20 @@ def run_beam(args, rank, world, workload="beam"):
     import torch
 
     from paper_2602_17002_gb300 import tlfe
-    wl = build_workload(workload)
+    full = build_workload(workload)
+    wl, itf = full, None
+    if world > 1:   # this GPU's slab; interface rows summed over the GPUs after every operation
+        wl, itf, _ = shard_one_body(full, rank, world)
+    xs_cache = {}
+
+    def xsum(t):
+        if itf is None:
+            return
+        if t.dtype not in xs_cache:
+            from paper_2602_17002_gb300 import shard
+            xs_cache[t.dtype] = shard.InterfaceSum(itf, t.dtype, "cuda")
+        xs_cache[t.dtype](t)
+
     tag = workload
     fpq = FLOP_PER_QP[workload]
     pre = "" if workload == "beam" else workload + "_"   # traffic keys of the committed ncu summary
@@ -566,14 +625,18 @@ def run_beam(args, rank, world, workload="beam"):
             if ev:
                 ev[0].record(stream)
             tlfe._check(L.tlfe_internal_force(h, tlfe._ptr(u_), tlfe._ptr(ud), tlfe._ptr(f), sp))
+            xsum(f)
             if ev:
                 ev[1].record(stream)
             tlfe._check(L.tlfe_tangent_matvec(h, tlfe._ptr(u_), tlfe._ptr(ud), tlfe._ptr(v), 0.0, 1.0, 1.0,
                                               tlfe._ptr(y), sp))
+            xsum(y)
             if ev:
                 ev[2].record(stream)
             tlfe._check(L.tlfe_vjp(h, tlfe._ptr(u_), tlfe._ptr(ud), tlfe._ptr(v), tlfe._ptr(gu), tlfe._ptr(gud),
                                    tlfe._ptr(gth), sp))
+            xsum(gu)
+            xsum(gud)
             if ev:
                 ev[3].record(stream)
         return step
@@ -625,8 +688,8 @@ def run_beam(args, rank, world, workload="beam"):
     per = np.array([[evs[k][j].elapsed_time(evs[k][j + 1]) for j in range(3)] for k in range(args.steps)])
     step_ms = allmax(float(per.sum(axis=1).mean()), world)
     kern_ms = per.mean(axis=0)
-    units = wl.n_qp
-    value = job_value(units, world, step_ms)
+    units = wl.n_qp                     # this GPU's points (all of them on one GPU)
+    value = full.n_qp / (step_ms * 1e-3)  # the whole body per step, at the slowest GPU's time
 
     # roofline of the dominant kernel: FP32 FMA roof (bound), HBM fraction beside it
     bytes_alg = [info["stream_bytes_force"], info["stream_bytes_matvec"], info["stream_bytes_vjp"]]
@@ -660,10 +723,22 @@ def run_beam(args, rank, world, workload="beam"):
     hgth = torch.empty(gth.shape, dtype=torch.float64).pin_memory()
 
     def e2e_run(n):
+        if itf is None:
+            for _ in range(n):
+                mesh.step_host(hu, hud, hv, hv, f=hf, y=hy, g_u=hgu, g_udot=hgud, g_mu_lambda=hgth,
+                               a_M=0.0, a_K=1.0, a_C=1.0, stream=stream)
+            mesh.step_host_wait()
+            return
+        # split body: the interface sums act on device arrays, so the inputs
+        # are copied in, the step (with its sums) runs, and the outputs are
+        # copied out, on the compute stream
         for _ in range(n):
-            mesh.step_host(hu, hud, hv, hv, f=hf, y=hy, g_u=hgu, g_udot=hgud, g_mu_lambda=hgth,
-                           a_M=0.0, a_K=1.0, a_C=1.0, stream=stream)
-        mesh.step_host_wait()
+            for d, hsrc in zip((u, ud, v), (hu, hud, hv)):
+                d.copy_(hsrc, non_blocking=True)
+            step()
+            for hdst, d in zip((hf, hy, hgu, hgud, hgth), outs + [gth]):
+                hdst.copy_(d, non_blocking=True)
+        torch.cuda.synchronize()
 
     e2e_run(3)
     torch.cuda.synchronize()
@@ -694,13 +769,15 @@ def run_beam(args, rank, world, workload="beam"):
     m64.close()
 
     line = base_line(args, world, workload, value, UNIT, step_ms, "f32",
-                     step="internal force + K_t v + C v + VJP (u, udot, mu, lambda)", n_elem=wl.n_elem,
-                     n_nodes=wl.n_nodes, n_qp=units, schedule="autotuned (tlfe_autotune) before the warm-up")
+                     step="internal force + K_t v + C v + VJP (u, udot, mu, lambda)", n_elem=full.n_elem,
+                     n_nodes=full.n_nodes, n_qp=full.n_qp, schedule="autotuned (tlfe_autotune) before the warm-up")
+    if itf is not None:
+        line["config"]["per_gpu"] = {"n_elem": wl.n_elem, "n_nodes": wl.n_nodes, "interface_nodes": itf.n}
     line.update({
         "kernels_ms": {n: float(t) for n, t in zip(names, kern_ms)},
         "kernels_gbs": {n: b / (t * 1e-3) / 1e9 for n, b, t in zip(names, bytes_alg, kern_ms)},
         "kernels_streamed_hbm_frac": kernels_streamed_frac,
-        "force_qps": units / (kern_ms[0] * 1e-3),
+        "force_qps": full.n_qp / (kern_ms[0] * 1e-3),
         "kernels_tflops": {n: fpq[n] * units / (t * 1e-3) / 1e12 if fpq[n] else None
                            for n, t in zip(names, kern_ms)},
         "roofline": roof,
@@ -708,8 +785,10 @@ def run_beam(args, rank, world, workload="beam"):
         "slab_path": slab,
         "fp64_plain": {"ms_per_step": ms64, "kernels_ms": {n: float(t) for n, t in zip(names, per64.mean(axis=0))},
                        "speedup_fp32_over_fp64": ms64 / step_ms, "device_status": st64},
-        "e2e": {"value": world * units / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "call": "tlfe_step_host (C ABI, host buffers)",
+        "e2e": {"value": full.n_qp / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
+                "call": ("tlfe_step_host (C ABI, host buffers)" if itf is None else
+                         "pinned-host copies around the device calls and interface sums"),
                 "overlap": OVERLAP,
                 "max_rel_diff_vs_device_step": e2e_err, "device_status": st_e2e},
         "gpu_launches": 3 * args.steps,
@@ -728,7 +807,10 @@ def run_newton(args, rank, world):
 
     import synth
     from paper_2602_17002_gb300 import tlfe
-    wl = build_workload("newton")
+    full = build_workload("newton")
+    wl = full
+    if world > 1:   # this GPU's bodies (cost-based bin packing); the bodies do not interact
+        wl, _ = shard_bodies(full, rank, world)
     h = 1e-3
     kw = dict(gravity=GRAVITY, newton_rtol=1e-8, cg_rtol=1e-4, max_newton=20, max_cg=4000)
     flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device="cuda")
@@ -807,15 +889,15 @@ def run_newton(args, rank, world):
     preps = plain_step()
     p1.record(stream)
     torch.cuda.synchronize()
-    ms_plain = p0.elapsed_time(p1)
+    ms_plain = allmax(p0.elapsed_time(p1), world)
     wall_plain = (time.perf_counter() - t0) * 1e3
     v_p = np.concatenate([vb.cpu().numpy() for _, _, _, vb in plain])
     for mb, *_ in plain:
         mb.close()
     dv_rel = float(np.abs(v_b - v_p).max() / max(np.abs(v_p).max(), 1e-300))
 
-    line = base_line(args, world, "newton", world * 1e3 / ms, "steps/s", ms, "f32",
-                     n_bodies=wl.n_bodies, n_elem=wl.n_elem, n_nodes=wl.n_nodes,
+    line = base_line(args, world, "newton", 1e3 / ms, "steps/s", ms, "f32",
+                     n_bodies=full.n_bodies, n_elem=full.n_elem, n_nodes=full.n_nodes,
                      step="one backward-Euler step of all bodies from rest (h = 1e-3 s, gravity, x = 0 clamped)")
     line.update({
         "batched": {"ms_per_step": ms, "newton_iters": rep["newton_iters"], "cg_iters": rep["cg_iters"],
@@ -830,7 +912,7 @@ def run_newton(args, rank, world):
                        "precision": "FP64 everywhere", "graph": False, "schedule": "one body at a time"},
         "speedup_batched_over_plain": ms_plain / ms,
         "max_rel_diff_v": dv_rel,
-        "e2e": {"value": world * 1e3 / e2e_ms, "unit": "steps/s", "h2d_bytes_per_step": 2 * z.numel() * 8,
+        "e2e": {"value": 1e3 / e2e_ms, "unit": "steps/s", "h2d_bytes_per_step": 2 * z.numel() * 8,
                 "d2h_bytes_per_step": z.numel() * 8, "ms_per_step": e2e_ms},
         "gpu_launches": None,
         "gpu_launches_note": "graph replays; the kernel count follows the Newton/CG iteration counts",
@@ -847,7 +929,10 @@ def run_batch(args, rank, world):
     import torch
 
     from paper_2602_17002_gb300 import tlfe
-    wl = build_workload("batch", args.bodies)
+    full = build_workload("batch", args.bodies)
+    wl = full
+    if world > 1:   # this GPU's bodies (cost-based bin packing); no exchange
+        wl, _ = shard_bodies(full, rank, world)
     mesh = tlfe.Mesh.from_workload(wl, precision=tlfe.FP32, scatter=scatter_mode(args))
     info = mesh.info
     u = torch.from_numpy(wl.u).to("cuda", torch.float64)
@@ -920,22 +1005,24 @@ def run_batch(args, rank, world):
     torch.cuda.synchronize()
     e2e_ms = allmax(e0.elapsed_time(e1) / args.steps, world)
     types = {0: "T4", 1: "T10", 2: "H8"}
-    line = base_line(args, world, "batch", world * units / (ms * 1e-3), UNIT, ms, "f32",
-                     n_bodies=wl.n_bodies, n_elem=wl.n_elem, n_nodes=wl.n_nodes, n_qp=units,
-                     elements_by_type={types[b.etype]: b.n_elem for b in wl.blocks},
+    line = base_line(args, world, "batch", full.n_qp / (ms * 1e-3), UNIT, ms, "f32",
+                     n_bodies=full.n_bodies, n_elem=full.n_elem, n_nodes=full.n_nodes, n_qp=full.n_qp,
+                     elements_by_type={types[b.etype]: b.n_elem for b in full.blocks},
                      step="internal force + K v over all bodies, one replay of the library's CUDA graph "
                           "(tlfe_force_matvec)")
-    if wl.n_bodies != 512:
-        line["config"]["workload"] = WORKLOADS["batch"].replace("512 bodies", f"{wl.n_bodies} bodies")
+    if full.n_bodies != 512:
+        line["config"]["workload"] = WORKLOADS["batch"].replace("512 bodies", f"{full.n_bodies} bodies")
+    if world > 1:
+        line["config"]["per_gpu"] = {"n_bodies": wl.n_bodies, "n_elem": wl.n_elem, "n_qp": wl.n_qp}
     line.update({
         "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peaks()["fp32"], "unit": "TFLOP/s",
                      "frac": achieved / alu_peaks()["fp32"],
-                     "traffic": ncu_traffic("batch512_step") if wl.n_bodies == 512 else None,
+                     "traffic": ncu_traffic("batch512_step") if wl.n_bodies == 512 and world == 1 else None,
                      "kernel": "force + matvec, all element blocks (one step)",
                      "peak_source": alu_peaks()["source"],
                      "algorithmic_flops": flops, "algorithmic_bytes": b_alg, "hbm_achieved_gbs": hbm,
                      "hbm_peak_gbs": peak, "hbm_frac": hbm / peak, "hbm_peak_source": peak_kind},
-        "e2e": {"value": world * units / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
+        "e2e": {"value": full.n_qp / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": u.numel() * 8 + v.numel() * 4, "d2h_bytes_per_step": 2 * v.numel() * 4,
                 "call": "tlfe_step_host (C ABI, host buffers)", "overlap": OVERLAP},
         "launch": {"mode": "fused" if info["launches_force"] == 1 else "per pass",
@@ -958,16 +1045,44 @@ def run_diff(args, rank, world):
     import torch
 
     from paper_2602_17002_gb300 import autograd, tlfe
-    wl = build_workload("diff")
+    full = build_workload("diff")
+    wl, itf, theta_t = full, None, full.extra["theta_target"]
+    xs32 = xs64 = None
+    owned = None
+    if world > 1:
+        # this GPU's slab: the forward force is summed over the GPUs at the
+        # interface nodes (and, by the adjoint of that sum, so is the loss
+        # gradient); the loss counts every node once; the position and
+        # velocity gradients are summed at the interface after the backward
+        from paper_2602_17002_gb300 import shard
+        wl, itf, emask = shard_one_body(full, rank, world)
+        theta_t = full.extra["theta_target"][emask[0]]
+        xs32 = shard.InterfaceSum(itf, torch.float32, "cuda")
+        xs64 = shard.InterfaceSum(itf, torch.float64, "cuda")
+        owned = torch.from_numpy(shard.owned_rows(wl.n_nodes, itf)).cuda()
     mesh = tlfe.Mesh.from_workload(wl, precision=tlfe.FP32, scatter=scatter_mode(args))
     info = mesh.info
     u = torch.from_numpy(wl.u).to("cuda", torch.float64).requires_grad_(True)
     ud = torch.from_numpy(wl.udot).to("cuda", torch.float32).requires_grad_(True)
     theta = torch.from_numpy(wl.elem_mu_lambda).to("cuda", torch.float64).requires_grad_(True)
     mesh.autotune(u.detach(), ud.detach(), ud.detach())
+
+    def force(uu, vv, th):
+        f = autograd.internal_force(mesh, uu, vv, th)
+        return f if xs32 is None else autograd.interface_sum(f, xs32)
+
+    def loss_of(f):
+        r2 = (f.double() - f_t) ** 2
+        return 0.5 * (r2.sum() if owned is None else r2[owned].sum())
+
+    def finish_grads(uu, vv):
+        if xs64 is not None:
+            xs64(uu.grad)
+            xs32(vv.grad)
+
     # f_target from the perturbed parameter field, computed once by the library
     with torch.no_grad():
-        f_t = autograd.internal_force(mesh, u, ud, torch.from_numpy(wl.extra["theta_target"]).cuda()).double()
+        f_t = force(u, ud, torch.from_numpy(theta_t).cuda()).double()
     flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
     losses = []
@@ -977,11 +1092,12 @@ def run_diff(args, rank, world):
             ev[0].record(stream)
         for t in (u, ud, theta):
             t.grad = None
-        f = autograd.internal_force(mesh, u, ud, theta)
-        loss = 0.5 * ((f.double() - f_t) ** 2).sum()
+        f = force(u, ud, theta)
+        loss = loss_of(f)
         if ev:
             ev[1].record(stream)
         loss.backward()
+        finish_grads(u, ud)
         if ev:
             ev[2].record(stream)
         losses.append(loss.detach())
@@ -997,7 +1113,7 @@ def run_diff(args, rank, world):
     ms = allmax(float(np.mean([e[0].elapsed_time(e[2]) for e in evs])), world)
     ms_fwd = float(np.mean([e[0].elapsed_time(e[1]) for e in evs]))
     ms_bwd = float(np.mean([e[1].elapsed_time(e[2]) for e in evs]))
-    units = wl.n_qp
+    units = wl.n_qp                     # this GPU's points
     peak, peak_kind = peaks()
     # roofline of the longer half, the backward (the adjoint kernel plus the
     # loss gradient, a few elementwise torch kernels): FP32 FMA roof, HBM beside
@@ -1037,9 +1153,10 @@ def run_diff(args, rank, world):
             lu, lud, lth = leaves[b]
             for t in leaves[b]:
                 t.grad = None
-            f = autograd.internal_force(mesh, lu, lud, lth)
-            loss = 0.5 * ((f.double() - f_t) ** 2).sum()
+            f = force(lu, lud, lth)
+            loss = loss_of(f)
             loss.backward()
+            finish_grads(lu, lud)
             comp_done[b] = torch.cuda.Event()
             comp_done[b].record(stream)
             if k + 1 < n:
@@ -1069,8 +1186,8 @@ def run_diff(args, rank, world):
     h2d = sum(t.numel() * t.element_size() for t in (hu, hud, hth))
     d2h = sum(t.numel() * t.element_size() for t in (hgu, hgud, hgth)) + 8
 
-    line = base_line(args, world, "diff", world * units / (ms * 1e-3), UNIT, ms, "f32",
-                     n_elem=wl.n_elem, n_nodes=wl.n_nodes, n_qp=units,
+    line = base_line(args, world, "diff", full.n_qp / (ms * 1e-3), UNIT, ms, "f32",
+                     n_elem=full.n_elem, n_nodes=full.n_nodes, n_qp=full.n_qp,
                      step="autograd forward (tlfe_internal_force) + loss in torch + backward (tlfe_vjp)")
     line.update({
         "phases_ms": {"forward_and_loss": ms_fwd, "backward": ms_bwd},
@@ -1081,8 +1198,8 @@ def run_diff(args, rank, world):
                      "algorithmic_flops": flops, "flop_per_qp": fpq["vjp"], "algorithmic_bytes": b_bwd,
                      "hbm_achieved_gbs": hbm, "hbm_peak_gbs": peak, "hbm_frac": hbm / peak,
                      "hbm_peak_source": peak_kind},
-        "loss": float(losses[-1].item()),
-        "e2e": {"value": world * units / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+        "loss": allsum(float(losses[-1].item()), world),
+        "e2e": {"value": full.n_qp / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "overlap": OVERLAP},
         "gpu_launches": 2 * args.steps, "clocks": clk.summary(), "device_status": st})
     mesh.close()

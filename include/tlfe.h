@@ -496,6 +496,23 @@ tlfe_status tlfe_norm_noalloc(const double *x_dev, int64_t n, double *out_dev, v
  * the CUDA context stay usable. Stream-ordered; no fault, no trap. */
 tlfe_status tlfe_selftest_wait_timeout(tlfe_mesh *mesh, int64_t spin_limit, void *stream);
 
+/* Node rows of a [n_nodes][3] array to and from a compact buffer, for the
+ * interface exchange of one body split across GPUs (its elements in slabs,
+ * the nodes of the slab interfaces duplicated): after each operator
+ * application the ranks sum their partial rows of the interface nodes through
+ * one compact buffer (Sec. 4.3 assembly across the split).
+ *   tlfe_gather_nodes : out[o(k)][c] = x[idx[k]][c], o(k) = out_idx[k], or k
+ *                       when out_idx is NULL; rows 0 .. n_out_clear - 1 of
+ *                       out are zeroed first (0: none)
+ *   tlfe_scatter_nodes: x[idx[k]][c] = in[i(k)][c], i(k) = in_idx[k], or k
+ * k < n, c < 3; float (TLFE_FP32) or double (TLFE_FP64) arrays; index arrays
+ * device int32 [n] (a destination row listed twice gets one of the values).
+ * Device pointers; stream-ordered; no mesh handle. */
+tlfe_status tlfe_gather_nodes(int32_t precision, const void *x_dev, const int32_t *idx_dev, int32_t n,
+                              void *out_dev, const int32_t *out_idx_dev, int32_t n_out_clear, void *stream);
+tlfe_status tlfe_scatter_nodes(int32_t precision, const void *in_dev, const int32_t *in_idx_dev,
+                               const int32_t *idx_dev, int32_t n, void *x_dev, void *stream);
+
 /* Arithmetic peak probe (no counterpart in the paper; the denominator of the
  * element kernels' ALU roofline): enqueues one kernel of ctas_per_sm CTAs of
  * 256 threads per SM in which every thread runs 16 independent fused

@@ -46,3 +46,28 @@ def internal_force(mesh: Mesh, u, udot=None, theta=None):
     """Differentiable f_int(u, udot, theta): u (n_nodes, 3) displacement (used in
     FP64), udot in the mesh dtype, theta (n_elem, 2) float64 (mu_e, lambda_e)."""
     return InternalForce.apply(mesh, u, udot, theta)
+
+
+class InterfaceSumFn(torch.autograd.Function):
+    """y = x with the rows of the interface nodes summed over the GPUs sharing
+    them (shard.InterfaceSum). The sum is linear and symmetric in the ranks,
+    so its adjoint is the same sum applied to the cotangent: every rank
+    holding an interface node gets the full cotangent there."""
+
+    @staticmethod
+    def forward(ctx, x, xs):
+        ctx.xs = xs
+        y = x.detach().clone().contiguous()
+        xs(y)
+        return y
+
+    @staticmethod
+    def backward(ctx, g):
+        g2 = g.detach().clone().contiguous()
+        ctx.xs(g2)
+        return g2, None
+
+
+def interface_sum(x, xs):
+    """Differentiable interface sum of a split body (see InterfaceSumFn)."""
+    return InterfaceSumFn.apply(x, xs)

@@ -93,7 +93,8 @@ _lib = None
 
 EXPORTS = ["tlfe_create_mesh", "tlfe_destroy_mesh", "tlfe_get_mesh_info", "tlfe_get_colors",
            "tlfe_get_scatter_targets", "tlfe_set_launch_mode", "tlfe_force_matvec", "tlfe_step_host",
-           "tlfe_step_host_wait", "tlfe_peak_probe", "tlfe_sync",
+           "tlfe_step_host_wait", "tlfe_peak_probe", "tlfe_gather_nodes",
+           "tlfe_scatter_nodes", "tlfe_sync",
            "tlfe_internal_force", "tlfe_internal_force_host", "tlfe_tangent_matvec", "tlfe_jacobi_diag",
            "tlfe_vjp", "tlfe_set_elem_mu_lambda", "tlfe_autotune", "tlfe_point_loads", "tlfe_surface_traction",
            "tlfe_constraint_eval", "tlfe_constraint_jt", "tlfe_constraint_j", "tlfe_newton_step", "tlfe_body_norms", "tlfe_norm_noalloc", "tlfe_selftest_wait_timeout", "tlfe_last_error",
@@ -120,6 +121,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "tlfe_step_host": [P, C.POINTER(tlfe_host_step), P],
         "tlfe_step_host_wait": [P],
         "tlfe_peak_probe": [I, I, C.c_int64, P, C.POINTER(C.c_double), P],
+        "tlfe_gather_nodes": [I, P, P, I, P, P, I, P],
+        "tlfe_scatter_nodes": [I, P, P, P, I, P, P],
         "tlfe_force_matvec": [P, P, P, P, D, D, D, P, P, P],
         "tlfe_sync": [P, P, C.POINTER(C.c_int64)],
         "tlfe_internal_force": [P, P, P, P, P],
@@ -610,6 +613,43 @@ def peak_probe(precision=FP32, ctas_per_sm=4, iters=1 << 16, repeats=5, stream=N
         ms = e0.elapsed_time(e1)
         best = ms if best is None else min(best, ms)
     return flop.value / (best * 1e-3) / 1e12, best
+
+
+def _rows_prec(*ts):
+    import torch
+    prec = {torch.float32: FP32, torch.float64: FP64}.get(ts[0].dtype)
+    if prec is None or not all(t.is_cuda and t.dtype == ts[0].dtype and t.is_contiguous() and t.dim() == 2
+                               and t.shape[1] == 3 for t in ts):
+        raise TLFEError(1, "node rows: contiguous CUDA (n, 3) float32 / float64 arrays of one dtype")
+    return prec
+
+
+def _idx(i, n):
+    import torch
+    if i is None:
+        return None
+    if not (i.is_cuda and i.dtype == torch.int32 and i.is_contiguous() and i.numel() == n):
+        raise TLFEError(1, "node rows: index arrays are contiguous CUDA int32 of one length")
+    return i
+
+
+def gather_nodes(x, idx, out, out_idx=None, clear=False, stream=None):
+    """out[out_idx[k]] = x[idx[k]] (out[k] without out_idx), after zeroing out
+    when clear (tlfe_gather_nodes)."""
+    prec = _rows_prec(x, out)
+    n = int(idx.numel())
+    _check(load().tlfe_gather_nodes(prec, _ptr(x), _ptr(_idx(idx, n)), n, _ptr(out), _ptr(_idx(out_idx, n)),
+                                    int(out.shape[0]) if clear else 0, _stream(stream)))
+    return out
+
+
+def scatter_nodes(buf, idx, x, buf_idx=None, stream=None):
+    """x[idx[k]] = buf[buf_idx[k]] (buf[k] without buf_idx) (tlfe_scatter_nodes)."""
+    prec = _rows_prec(x, buf)
+    n = int(idx.numel())
+    _check(load().tlfe_scatter_nodes(prec, _ptr(buf), _ptr(_idx(buf_idx, n)), _ptr(_idx(idx, n)), n, _ptr(x),
+                                     _stream(stream)))
+    return x
 
 
 def tlfe_norm_noalloc(x, out, stream=None):

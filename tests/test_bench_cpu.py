@@ -61,3 +61,22 @@ def test_command_line_lists_the_workloads_and_modes():
         assert flag in out.stdout
     for mode in ("atomic", "colour", "sorted"):
         assert mode in out.stdout
+
+
+def test_bench_shards_cover_the_workloads():
+    """bench.py's split for N GPUs: one body in slabs (elements once each,
+    interface nodes shared) and bodies bin-packed (each body on one GPU)."""
+    import numpy as np
+
+    import bench
+    import synth
+    wl = synth.small_beam(cells=(10, 2, 2))
+    shares = [bench.shard_one_body(wl, r, 3) for r in range(3)]
+    assert sum(sh.n_elem for sh, _, _ in shares) == wl.n_elem
+    assert all(itf.n == shares[0][1].n > 0 for _, itf, _ in shares)
+    bw = synth.batch_bodies(n_bodies=11, seed=2, ne_range=(30, 200))
+    parts = [bench.shard_bodies(bw, r, 4) for r in range(4)]
+    assert np.array_equal(np.sort(np.concatenate([p for _, p in parts])), np.arange(11))
+    assert sum(sh.n_elem for sh, _ in parts) == bw.n_elem
+    assert sum(sh.n_nodes for sh, _ in parts) == bw.n_nodes
+    assert bench.parallelism("beam", 1) == "1 GPU" and "slab" in bench.parallelism("beam", 2)

@@ -1,8 +1,6 @@
-"""Host logic of the multi-rank benchmark path, run as two gloo ranks on CPU.
-
-The element path shards as independent problems (one replica per GPU, weak
-scaling), so the only cross-rank steps are the barriers that bracket the
-timed region and the max-over-ranks reduction of the step time.
+"""Host logic of the multi-rank benchmark path, run as two gloo ranks on CPU:
+the barriers that bracket the timed region and the max-over-ranks reduction
+of the step time (the work split itself is tested in test_shard_cpu.py).
 """
 
 import os
