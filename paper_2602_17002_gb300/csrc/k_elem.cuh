@@ -107,21 +107,33 @@ template <int OP> struct OpFields {
     static constexpr int NFO = OUT / 3;           // output vector fields per node
 };
 
-// Patch record of one node: packed 3-vectors in a record padded to 16 bytes.
-//   FP32: [u_hi(3) u_lo(3) | udot(3) | v(3)]  -> 12 floats (48 B)
-//   FP64: [u(3) | udot(3) | v(3)]             -> 6 or 10 doubles
+// Patch record of one node.
+//   FP32 (12 floats, 48 B), laid out for paired arithmetic (FFMA2 on the x
+//   and y components of a 3-vector, the z component alone):
+//     [h0 h1 l0 l1 | h2 l2 ud2 v2 | ud0 ud1 v0 v1]
+//   FP64: [u(3) | udot(3) | v(3)]  (6 or 10 doubles)
 // The displacement arrives in FP64; FP32 kernels keep it as an unevaluated
-// pair (hi, lo) with u = hi + lo to about 2^-46 |u|, so that element-relative
+// pair (h, l) with u = h + l to about 2^-46 |u|, so that element-relative
 // differences u_i - u_0 are formed without the rounding of |u| (large rigid
-// motions).
+// motions). The FP64 displacement is first copied into the record's bytes
+// 0..23 (the h, l slots and the unused h2, l2 of slot 2's first half) and
+// split there in place.
 template <int OP, typename R> struct Rec {
-    static constexpr int NU = sizeof(R) == 4 ? 2 : 1;          // 3-vectors holding u
-    static constexpr int OFF_UD = 3 * NU;                       // udot
-    static constexpr int OFF_V = 3 * NU + 3;                    // direction / cotangent
-    static constexpr int RAW = 3 * (NU + OpFields<OP>::NFI - 1);
-    static constexpr int ALIGN = 16 / (int)sizeof(R);
-    static constexpr int REC = (RAW + ALIGN - 1) / ALIGN * ALIGN;
+    static constexpr bool PK = sizeof(R) == 4;
+    // FP32 slots (float offsets)
+    static constexpr int H01 = 0, L01 = 2, H2 = 4, L2 = 5, UD2 = 6, V2 = 7, UD01 = 8, V01 = 10;
+    // FP64 offsets
+    static constexpr int OFF_UD = 3;                            // udot
+    static constexpr int OFF_V = 6;                             // direction / cotangent
+    static constexpr int REC = PK ? 12 : (3 * OpFields<OP>::NFI + 1) / 2 * 2;
 };
+
+// packed FP32 pairs (sm_100 and later: one instruction for two lanes of work)
+__device__ __forceinline__ float2 bc2(float x) { return make_float2(x, x); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float4 lds4(const float *r) { return *reinterpret_cast<const float4 *>(r); }
 
 constexpr int NSLICE = 2;  // ring depth per warp (quadrature-point slices)
 
@@ -206,13 +218,8 @@ template <int OFF> __device__ __forceinline__ void st3c(double *r, double x, dou
         *reinterpret_cast<double2 *>(r + OFF + 1) = make_double2(y, z);
     }
 }
-// FP32 u pair of a record: hi at 0..2, lo at 3..5 (one 16-byte and one 8-byte load)
-__device__ __forceinline__ void ld_u(const float *r, float h[3], float l[3])
-{
-    const float4 a = *reinterpret_cast<const float4 *>(r);
-    const float2 b = *reinterpret_cast<const float2 *>(r + 4);
-    h[0] = a.x, h[1] = a.y, h[2] = a.z, l[0] = a.w, l[1] = b.x, l[2] = b.y;
-}
+// FP64 displacement of a record (the FP32 kernels read their (h, l) pairs
+// from the paired slots directly)
 __device__ __forceinline__ void ld_u(const double *r, double h[3], double l[3])
 {
     ld3c<0>(r, h[0], h[1], h[2]);
@@ -284,9 +291,12 @@ __device__ __forceinline__ bool elem_tiles(const KParams<R> &p, unsigned char *w
                                            int tstep, int n_my)
 {
     constexpr int NPE = Elem<ET>::NPE;
-    constexpr int REC = Rec<OP, R>::REC;
-    constexpr int OFF_UD = Rec<OP, R>::OFF_UD;
-    constexpr int OFF_V = Rec<OP, R>::OFF_V;
+    using RC = Rec<OP, R>;
+    constexpr int REC = RC::REC;
+    constexpr int OFF_UD = RC::OFF_UD;
+    constexpr int OFF_V = RC::OFF_V;
+    constexpr bool PK = RC::PK;                        // FP32: paired (x, y) arithmetic
+    constexpr bool PKA = PK && OP != OP_DIAG;          // ... and paired element-vector accumulators
     constexpr int NFO = OpFields<OP>::NFO;
     constexpr bool HAS_V = OpFields<OP>::NFI == 3;
     constexpr bool DD_REG = OP == OP_FORCE || OP == OP_DIAG;
@@ -370,16 +380,29 @@ __device__ __forceinline__ bool elem_tiles(const KParams<R> &p, unsigned char *w
             R *rec = work + (size_t)kk * REC;
 #pragma unroll
             for (int a = 0; a < 3; ++a) cp_async<8>(reinterpret_cast<double *>(rec) + a, p.u + 3 * n + a);
-            if (need_ud)
+            if constexpr (PK) {
+                if (need_ud) {
+                    cp_async<4>(rec + RC::UD01, p.ud + 3 * n);
+                    cp_async<4>(rec + RC::UD01 + 1, p.ud + 3 * n + 1);
+                    cp_async<4>(rec + RC::UD2, p.ud + 3 * n + 2);
+                }
+                if (HAS_V) {
+                    cp_async<4>(rec + RC::V01, p.v + 3 * n);
+                    cp_async<4>(rec + RC::V01 + 1, p.v + 3 * n + 1);
+                    cp_async<4>(rec + RC::V2, p.v + 3 * n + 2);
+                }
+            } else {
+                if (need_ud)
 #pragma unroll
-                for (int a = 0; a < 3; ++a) cp_async<sizeof(R)>(rec + OFF_UD + a, p.ud + 3 * n + a);
-            if (HAS_V)
+                    for (int a = 0; a < 3; ++a) cp_async<sizeof(R)>(rec + OFF_UD + a, p.ud + 3 * n + a);
+                if (HAS_V)
 #pragma unroll
-                for (int a = 0; a < 3; ++a) cp_async<sizeof(R)>(rec + OFF_V + a, p.v + 3 * n + a);
+                    for (int a = 0; a < 3; ++a) cp_async<sizeof(R)>(rec + OFF_V + a, p.v + 3 * n + a);
+            }
         }
         cp_async_commit();
         cp_async_wait<0>();
-        if constexpr (sizeof(R) == 4) {
+        if constexpr (PK) {
             for (int kk = lane; kk < U; kk += 32) {
                 R *rec = work + (size_t)kk * REC;
                 const double2 u01 = *reinterpret_cast<const double2 *>(rec);
@@ -388,8 +411,8 @@ __device__ __forceinline__ bool elem_tiles(const KParams<R> &p, unsigned char *w
                 split_f64(u01.x, h[0], l[0]);
                 split_f64(u01.y, h[1], l[1]);
                 split_f64(u2, h[2], l[2]);
-                *reinterpret_cast<float4 *>(rec) = make_float4(h[0], h[1], h[2], l[0]);
-                *reinterpret_cast<float2 *>(rec + 4) = make_float2(l[1], l[2]);
+                *reinterpret_cast<float4 *>(rec) = make_float4(h[0], h[1], l[0], l[1]);
+                *reinterpret_cast<float2 *>(rec + RC::H2) = make_float2(h[2], l[2]);
             }
         }
         int li[NPE];
@@ -424,25 +447,55 @@ __device__ __forceinline__ bool elem_tiles(const KParams<R> &p, unsigned char *w
         // kernels; the operator and adjoint kernels, which hold more
         // accumulators, re-form them from the patch at every point.
         R h0v[3], l0v[3];
-        ld_u(work + li[0] * REC, h0v, l0v);
         R dd[NPE][3];
+        // FP32: node 0's pair, negated, with x and y paired; d_i = (h_i - h_0)
+        // + (l_i - l_0) as (h_i + (-h_0)) + (l_i + (-l_0)), the same roundings
+        float2 nh01 = make_float2(0.f, 0.f), nl01 = make_float2(0.f, 0.f), dp[NPE];
+        float nh2 = 0.f, nl2 = 0.f;
+        if constexpr (PK) {
+            const float4 A = lds4(work + li[0] * REC), B = lds4(work + li[0] * REC + 4);
+            nh01 = make_float2(-A.x, -A.y);
+            nl01 = make_float2(-A.z, -A.w);
+            nh2 = -B.x;
+            nl2 = -B.y;
+        } else {
+            ld_u(work + li[0] * REC, h0v, l0v);
+        }
         if constexpr (DD_REG) {
 #pragma unroll
             for (int i = 1; i < NPE; ++i) {
-                R hv[3], lv[3];
-                ld_u(work + li[i] * REC, hv, lv);
+                if constexpr (PK) {
+                    const float4 A = lds4(work + li[i] * REC), B = lds4(work + li[i] * REC + 4);
+                    dp[i] = add2(add2(make_float2(A.x, A.y), nh01), add2(make_float2(A.z, A.w), nl01));
+                    dd[i][2] = (B.x + nh2) + (B.y + nl2);
+                } else {
+                    R hv[3], lv[3];
+                    ld_u(work + li[i] * REC, hv, lv);
 #pragma unroll
-                for (int a = 0; a < 3; ++a) dd[i][a] = (hv[a] - h0v[a]) + (lv[a] - l0v[a]);
+                    for (int a = 0; a < 3; ++a) dd[i][a] = (hv[a] - h0v[a]) + (lv[a] - l0v[a]);
+                }
             }
         }
+        // element vectors: FP32 keeps (x, y) of each node as a pair and z alone
         R acc0[NPE][3], acc1[NPE][3];
+        float2 ap0[NPE], ap1[NPE];
 #pragma unroll
-        for (int i = 0; i < NPE; ++i)
+        for (int i = 0; i < NPE; ++i) {
+            if constexpr (PKA) {
+                ap0[i] = make_float2(0.f, 0.f);
+                acc0[i][2] = R(0);
+                if (OP == OP_VJP) {
+                    ap1[i] = make_float2(0.f, 0.f);
+                    acc1[i][2] = R(0);
+                }
+            } else {
 #pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                acc0[i][d] = R(0);
-                if (OP == OP_VJP) acc1[i][d] = R(0);
+                for (int d = 0; d < 3; ++d) {
+                    acc0[i][d] = R(0);
+                    if (OP == OP_VJP) acc1[i][d] = R(0);
+                }
             }
+        }
         R gmu_acc = R(0), glam_acc = R(0);
         int bad = 0;
 
@@ -498,6 +551,87 @@ __device__ __forceinline__ bool elem_tiles(const KParams<R> &p, unsigned char *w
             // (affine path: the same sums against g_i, then times J^{-1})
             QP<R> s1;
             R D[9];
+            if constexpr (PK) {
+                // rows 0 and 1 of G', Fd', D' paired per column k, row 2 alone
+                float2 Gp[3], Fp[3], Dp[3];
+                float Gs[3], Fs[3], Ds[3];
+#pragma unroll
+                for (int k2 = 0; k2 < 3; ++k2) {
+                    Gp[k2] = Fp[k2] = Dp[k2] = make_float2(0.f, 0.f);
+                    Gs[k2] = Fs[k2] = Ds[k2] = 0.f;
+                }
+#pragma unroll
+                for (int i = 0; i < NPE; ++i) {
+                    R hk[3];
+#pragma unroll
+                    for (int k2 = 0; k2 < 3; ++k2) hk[k2] = nz(i, k2) ? grad(i, k2) : R(0);
+                    const float *rec = work + li[i] * REC;
+                    float4 B = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if ((i > 0 && !DD_REG) || visc || HAS_V) B = lds4(rec + 4);
+                    if (i > 0) {
+                        float2 d01;
+                        float d2;
+                        if constexpr (DD_REG) {
+                            d01 = dp[i];
+                            d2 = dd[i][2];
+                        } else {
+                            const float4 A = lds4(rec);
+                            d01 = add2(add2(make_float2(A.x, A.y), nh01), add2(make_float2(A.z, A.w), nl01));
+                            d2 = (B.x + nh2) + (B.y + nl2);
+                        }
+#pragma unroll
+                        for (int k2 = 0; k2 < 3; ++k2)
+                            if (nz(i, k2)) {
+                                Gp[k2] = fma2(d01, bc2(hk[k2]), Gp[k2]);
+                                Gs[k2] = fmaf(d2, hk[k2], Gs[k2]);
+                            }
+                    }
+                    if (visc || HAS_V) {
+                        const float4 C4 = lds4(rec + 8);
+                        if (visc)
+#pragma unroll
+                            for (int k2 = 0; k2 < 3; ++k2)
+                                if (nz(i, k2)) {
+                                    Fp[k2] = fma2(make_float2(C4.x, C4.y), bc2(hk[k2]), Fp[k2]);
+                                    Fs[k2] = fmaf(B.z, hk[k2], Fs[k2]);
+                                }
+                        if (HAS_V)
+#pragma unroll
+                            for (int k2 = 0; k2 < 3; ++k2)
+                                if (nz(i, k2)) {
+                                    Dp[k2] = fma2(make_float2(C4.z, C4.w), bc2(hk[k2]), Dp[k2]);
+                                    Ds[k2] = fmaf(B.w, hk[k2], Ds[k2]);
+                                }
+                    }
+                }
+                // affine path: X = X' J^{-1}, rows 0 and 1 paired
+                auto finish = [&](const float2 Xp[3], const float Xs[3], float *X) {
+#pragma unroll
+                    for (int b2 = 0; b2 < 3; ++b2) {
+                        if constexpr (AFF) {
+                            float2 q2 = mul2(Xp[0], bc2(Ji[b2]));
+                            q2 = fma2(Xp[1], bc2(Ji[3 + b2]), q2);
+                            q2 = fma2(Xp[2], bc2(Ji[6 + b2]), q2);
+                            X[b2] = q2.x;
+                            X[3 + b2] = q2.y;
+                            X[6 + b2] = fmaf(Xs[2], Ji[6 + b2], fmaf(Xs[1], Ji[3 + b2], Xs[0] * Ji[b2]));
+                        } else {
+                            X[b2] = Xp[b2].x;
+                            X[3 + b2] = Xp[b2].y;
+                            X[6 + b2] = Xs[b2];
+                        }
+                    }
+                };
+                finish(Gp, Gs, s1.G);
+                if (visc) finish(Fp, Fs, s1.Fd);
+                else
+#pragma unroll
+                    for (int k2 = 0; k2 < 9; ++k2) s1.Fd[k2] = 0.f;
+                if (HAS_V) finish(Dp, Ds, D);
+                else
+#pragma unroll
+                    for (int k2 = 0; k2 < 9; ++k2) D[k2] = 0.f;
+            } else {
 #pragma unroll
             for (int k2 = 0; k2 < 9; ++k2) {
                 s1.G[k2] = R(0);
@@ -557,6 +691,7 @@ __device__ __forceinline__ bool elem_tiles(const KParams<R> &p, unsigned char *w
                     for (int k2 = 0; k2 < 9; ++k2) D[k2] = T[k2];
                 }
             }
+            }
             R P[9];
             stress<R>(m, s1, visc, P);
             bad += (valid && !s1.ok) ? 1 : 0;
@@ -596,24 +731,60 @@ __device__ __forceinline__ bool elem_tiles(const KParams<R> &p, unsigned char *w
                     }
                 }
             } else {
-                R T0[9], T1[9];  // element-vector operators of this point, scaled by w
+                R T0[9], T1[9];  // element-vector operators of this point (scaled by w below)
                 if (OP == OP_FORCE) {
 #pragma unroll
-                    for (int k2 = 0; k2 < 9; ++k2) T0[k2] = w * P[k2];
+                    for (int k2 = 0; k2 < 9; ++k2) T0[k2] = P[k2];
                 } else if (OP == OP_MATVEC) {
                     dstress<R>(m, s1, visc, D, p.aK, p.aC, p.sym_only != 0, T0);
-#pragma unroll
-                    for (int k2 = 0; k2 < 9; ++k2) T0[k2] *= w;
                 } else {
                     R gmu, glam;
                     astress<R>(m, s1, visc, D, T0, T1, gmu, glam);
                     gmu_acc += w * gmu;
                     glam_acc += w * glam;
+                }
+                if constexpr (PKA) {
+                    // w T h_i = w (T J^{-T}) g_i: rows 0 and 1 of the point's
+                    // operator paired per column, then accumulated into the
+                    // paired element vectors
+                    auto pack = [&](const float *T, float2 Tp[3], float Ts[3]) {
 #pragma unroll
-                    for (int k2 = 0; k2 < 9; ++k2) {
-                        T0[k2] *= w;
-                        T1[k2] *= w;
+                        for (int k2 = 0; k2 < 3; ++k2) {
+                            if constexpr (AFF) {
+                                float2 q2 = mul2(make_float2(T[0], T[3]), bc2(Ji[k2 * 3]));
+                                q2 = fma2(make_float2(T[1], T[4]), bc2(Ji[k2 * 3 + 1]), q2);
+                                q2 = fma2(make_float2(T[2], T[5]), bc2(Ji[k2 * 3 + 2]), q2);
+                                Tp[k2] = mul2(q2, bc2(w));
+                                Ts[k2] = w * fmaf(T[8], Ji[k2 * 3 + 2], fmaf(T[7], Ji[k2 * 3 + 1], T[6] * Ji[k2 * 3]));
+                            } else {
+                                Tp[k2] = mul2(make_float2(T[k2], T[3 + k2]), bc2(w));
+                                Ts[k2] = w * T[6 + k2];
+                            }
+                        }
+                    };
+                    float2 Tp0[3], Tp1[3];
+                    float Ts0[3], Ts1[3];
+                    pack(T0, Tp0, Ts0);
+                    if (OP == OP_VJP) pack(T1, Tp1, Ts1);
+#pragma unroll
+                    for (int i = 0; i < NPE; ++i) {
+#pragma unroll
+                        for (int k2 = 0; k2 < 3; ++k2)
+                            if (nz(i, k2)) {
+                                const float hk = grad(i, k2);
+                                ap0[i] = fma2(Tp0[k2], bc2(hk), ap0[i]);
+                                acc0[i][2] = fmaf(Ts0[k2], hk, acc0[i][2]);
+                                if (OP == OP_VJP) {
+                                    ap1[i] = fma2(Tp1[k2], bc2(hk), ap1[i]);
+                                    acc1[i][2] = fmaf(Ts1[k2], hk, acc1[i][2]);
+                                }
+                            }
                     }
+                } else {
+#pragma unroll
+                for (int k2 = 0; k2 < 9; ++k2) {
+                    T0[k2] *= w;
+                    if (OP == OP_VJP) T1[k2] *= w;
                 }
                 if constexpr (AFF) {
                     // T h_i = (T J^{-T}) g_i
@@ -651,6 +822,7 @@ __device__ __forceinline__ bool elem_tiles(const KParams<R> &p, unsigned char *w
                                 if (OP == OP_VJP) acc1[i][a] += T1[a * 3 + k2] * hk[k2];
                             }
                 }
+                }
             }
             if (PF_EARLY && q == 0 && !prefetch_next()) {
                 timed_out = true;
@@ -682,14 +854,26 @@ __device__ __forceinline__ bool elem_tiles(const KParams<R> &p, unsigned char *w
             if (OP == OP_MATVEC) {
 #pragma unroll
                 for (int jn = 0; jn < NPE; ++jn) {
-                    R x[3];
-                    ld3c<OFF_V>(work + li[jn] * REC, x[0], x[1], x[2]);
+                    if constexpr (PKA) {
+                        const float *rec = work + li[jn] * REC;
+                        const float2 v01 = *reinterpret_cast<const float2 *>(rec + RC::V01);
+                        const float v2 = rec[RC::V2];
 #pragma unroll
-                    for (int i = 0; i < NPE; ++i) {
-                        const R mh = c * R(mass_hat(ET, i, jn));
-                        acc0[i][0] += mh * x[0];
-                        acc0[i][1] += mh * x[1];
-                        acc0[i][2] += mh * x[2];
+                        for (int i = 0; i < NPE; ++i) {
+                            const float mh = c * float(mass_hat(ET, i, jn));
+                            ap0[i] = fma2(v01, bc2(mh), ap0[i]);
+                            acc0[i][2] += mh * v2;
+                        }
+                    } else {
+                        R x[3];
+                        ld3c<OFF_V>(work + li[jn] * REC, x[0], x[1], x[2]);
+#pragma unroll
+                        for (int i = 0; i < NPE; ++i) {
+                            const R mh = c * R(mass_hat(ET, i, jn));
+                            acc0[i][0] += mh * x[0];
+                            acc0[i][1] += mh * x[1];
+                            acc0[i][2] += mh * x[2];
+                        }
                     }
                 }
             } else {
@@ -722,8 +906,15 @@ __device__ __forceinline__ bool elem_tiles(const KParams<R> &p, unsigned char *w
 #pragma unroll
                 for (int i = 0; i < NPE; ++i) {
                     const int ps = spos[i * 32 + lane];
+                    if constexpr (PKA) {
+                        const float2 a01 = fo == 0 ? ap0[i] : ap1[i];
+                        work[ps * 3] = a01.x;
+                        work[ps * 3 + 1] = a01.y;
+                        work[ps * 3 + 2] = fo == 0 ? acc0[i][2] : acc1[i][2];
+                    } else {
 #pragma unroll
-                    for (int d = 0; d < 3; ++d) work[ps * 3 + d] = fo == 0 ? acc0[i][d] : acc1[i][d];
+                        for (int d = 0; d < 3; ++d) work[ps * 3 + d] = fo == 0 ? acc0[i][d] : acc1[i][d];
+                    }
                 }
             }
             __syncwarp();
