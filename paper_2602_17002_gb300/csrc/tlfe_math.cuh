@@ -99,6 +99,37 @@ template <typename R> __device__ __forceinline__ void mm3_acc(const R A[9], cons
             C[a * 3 + b] += A[a * 3] * B[b] + A[a * 3 + 1] * B[3 + b] + A[a * 3 + 2] * B[6 + b];
 }
 
+// FP32 products with rows 0 and 1 paired in packed FP32x2 operations (one
+// instruction for two lanes of work; the same operations in the same order
+// as the scalar form)
+__device__ __forceinline__ void mm3(const float A[9], const float B[9], float C[9])
+{
+    const float2 a0 = make_float2(A[0], A[3]), a1 = make_float2(A[1], A[4]), a2 = make_float2(A[2], A[5]);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        float2 q = __fmul2_rn(a0, make_float2(B[b], B[b]));
+        q = __ffma2_rn(a1, make_float2(B[3 + b], B[3 + b]), q);
+        q = __ffma2_rn(a2, make_float2(B[6 + b], B[6 + b]), q);
+        C[b] = q.x;
+        C[3 + b] = q.y;
+        C[6 + b] = fmaf(A[8], B[6 + b], fmaf(A[7], B[3 + b], A[6] * B[b]));
+    }
+}
+__device__ __forceinline__ void mm3_acc(const float A[9], const float B[9], float C[9])
+{
+    const float2 a0 = make_float2(A[0], A[3]), a1 = make_float2(A[1], A[4]), a2 = make_float2(A[2], A[5]);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        float2 q = __fmul2_rn(a0, make_float2(B[b], B[b]));
+        q = __ffma2_rn(a1, make_float2(B[3 + b], B[3 + b]), q);
+        q = __ffma2_rn(a2, make_float2(B[6 + b], B[6 + b]), q);
+        const float2 c = __fadd2_rn(make_float2(C[b], C[3 + b]), q);
+        C[b] = c.x;
+        C[3 + b] = c.y;
+        C[6 + b] += fmaf(A[8], B[6 + b], fmaf(A[7], B[3 + b], A[6] * B[b]));
+    }
+}
+
 // sym(A^T B) = (A^T B + B^T A) / 2
 template <typename R> __device__ __forceinline__ void symAtB(const R A[9], const R B[9], R S[9])
 {
