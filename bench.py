@@ -142,8 +142,9 @@ def peaks():
 # the mesh layout they read and their launch schedules (not the Newton,
 # constraint or load code): the committed ncu traffic is valid while these
 # are unchanged
-KERNEL_SOURCES = ("k_elem.cuh", "k_wpe.cuh", "tlfe_elem.cuh", "tlfe_math.cuh", "tlfe_internal.h", "tlfe_mesh.h",
-                  "api.cu", "k_setup.cu", "k_force.cu", "k_matvec.cu", "k_vjp.cu", "k_diag.cu")
+KERNEL_SOURCES = ("k_elem.cuh", "k_wpe.cuh", "k_fused.cuh", "tlfe_fused.h", "tlfe_elem.cuh", "tlfe_math.cuh",
+                  "tlfe_internal.h", "tlfe_mesh.h", "api.cu", "k_setup.cu", "k_force.cu", "k_matvec.cu", "k_vjp.cu",
+                  "k_diag.cu", "k_fused_force.cu", "k_fused_matvec.cu")
 
 
 def _strip_comments(src):
@@ -964,13 +965,16 @@ def run_batch(args, rank, world):
     barrier(world)
     st = mesh.sync()
     ms = allmax(float(np.mean([e[0].elapsed_time(e[1]) for e in evs])), world)
-    # the same step with one launch per pass (context for the fused launch)
-    mesh.set_launch_mode(tlfe.LAUNCH_PER_PASS)
-    for _ in range(2):
-        step()
-    evs_pp = timed_steps(step, max(3, args.steps // 2), flush, stream, label="batch_per_pass")
-    ms_pp = float(np.mean([e[0].elapsed_time(e[1]) for e in evs_pp]))
-    launches_pp = mesh.info["launches_force"] + mesh.info["launches_matvec"]
+    # the same step in each launch mode (the tuner keeps the faster one per
+    # operation in the timed step above)
+    modes = {}
+    for name, mode in (("fused", tlfe.LAUNCH_FUSED), ("per_pass", tlfe.LAUNCH_PER_PASS)):
+        mesh.set_launch_mode(mode)
+        for _ in range(2):
+            step()
+        evs_m = timed_steps(step, max(3, args.steps // 2), flush, stream, label="batch_" + name)
+        modes[name] = {"ms_per_step": float(np.mean([e[0].elapsed_time(e[1]) for e in evs_m])),
+                       "launches_per_step": mesh.info["launches_force"] + mesh.info["launches_matvec"]}
     mesh.set_launch_mode(tlfe.LAUNCH_AUTO)
     units = wl.n_qp
     peak, peak_kind = peaks()
@@ -1025,11 +1029,12 @@ def run_batch(args, rank, world):
         "e2e": {"value": full.n_qp / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": u.numel() * 8 + v.numel() * 4, "d2h_bytes_per_step": 2 * v.numel() * 4,
                 "call": "tlfe_step_host (C ABI, host buffers)", "overlap": OVERLAP},
-        "launch": {"mode": "fused" if info["launches_force"] == 1 else "per pass",
+        "launch": {"force": "fused" if info["launches_force"] == 1 else "per pass",
+                   "matvec": "fused" if info["launches_matvec"] == 1 else "per pass",
+                   "chosen_by": "tlfe_autotune (the faster mode per operation)",
                    "fused_passes": info["n_fused_passes"], "fused_items": info["n_fused_items"],
                    "passes": info["n_passes"], "launches_per_step": info["launches_force"] + info["launches_matvec"],
-                   "graph": "tlfe_force_matvec (captured by the library, replayed)",
-                   "per_pass": {"ms_per_step": ms_pp, "launches_per_step": launches_pp}},
+                   "graph": "tlfe_force_matvec (captured by the library, replayed)", "modes": modes},
         "gpu_launches": (info["launches_force"] + info["launches_matvec"]) * args.steps,
         "clocks": clk.summary(), "device_status": st})
     mesh.close()

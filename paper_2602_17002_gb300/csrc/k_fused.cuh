@@ -26,8 +26,11 @@ template <int OP> constexpr int fused_min_ctas() { return OP == OP_FORCE ? 4 : (
 // into one switch, the bodies spilled heavily and compiled several times
 // slower)
 template <typename R, int OP, int CODE, int MAT>
-__device__ __noinline__ bool fused_run(const KParams<R> &p, unsigned char *wbase, uint64_t *bar, int t0, int n)
+__device__ __noinline__ bool fused_run(const KParams<R> *__restrict__ pp, unsigned char *wbase, uint64_t *bar, int t0,
+                                       int n)
 {
+    // the parameters are read through a pointer no store of the body aliases
+    const KParams<R> &p = *pp;
     if constexpr (CODE == FK_T4Q1) return elem_tiles<ET_T4, 1, R, OP, true, MAT>(p, wbase, bar, t0, 1, n);
     if constexpr (CODE == FK_T10Q4) return elem_tiles<ET_T10, 4, R, OP, true, MAT>(p, wbase, bar, t0, 1, n);
     if constexpr (CODE == FK_T10Q5) return elem_tiles<ET_T10, 5, R, OP, true, MAT>(p, wbase, bar, t0, 1, n);
@@ -36,7 +39,7 @@ __device__ __noinline__ bool fused_run(const KParams<R> &p, unsigned char *wbase
 }
 
 template <typename R, int OP, int CODE>
-__device__ __forceinline__ bool fused_mat(int mat, const KParams<R> &p, unsigned char *wbase, uint64_t *bar, int t0,
+__device__ __forceinline__ bool fused_mat(int mat, const KParams<R> *p, unsigned char *wbase, uint64_t *bar, int t0,
                                           int n)
 {
     switch (mat) {
@@ -48,15 +51,27 @@ __device__ __forceinline__ bool fused_mat(int mat, const KParams<R> &p, unsigned
     }
 }
 
+// bytes of the per-warp copy of the current pass's parameters, ahead of the
+// warp's region: the out-of-line bodies read the parameters through a
+// pointer, which into shared memory is a short-latency load
+template <typename R> __host__ __device__ constexpr size_t fused_param_bytes()
+{
+    return (sizeof(KParams<R>) + 127) / 128 * 128;
+}
+
 template <typename R, int OP>
 __global__ void __launch_bounds__(128, fused_min_ctas<OP>()) k_fused(const __grid_constant__ FusedArgs<R> a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
+    constexpr size_t PB = fused_param_bytes<R>();
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem) + wib * (NSLICE + 2);
-    unsigned char *wbase = smem + 128 + (size_t)wib * a.wreg;
+    unsigned char *pbase = smem + 128 + (size_t)wib * (a.wreg + PB);
+    unsigned char *wbase = pbase + PB;
+    KParams<R> *ps = reinterpret_cast<KParams<R> *>(pbase);
     bool first = true;
+    int cur = -1;  // pass whose parameters the copy holds
     for (;;) {
         int it = 0;
         if (lane == 0) it = atomicAdd(a.counter, 1);
@@ -74,7 +89,14 @@ __global__ void __launch_bounds__(128, fused_min_ctas<OP>()) k_fused(const __gri
         }
         first = false;
         __syncwarp();
-        const KParams<R> &p = a.pass[w.x];
+        if (w.x != cur) {  // warp-uniform
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(&a.pass[w.x]);
+            uint32_t *dst = reinterpret_cast<uint32_t *>(ps);
+            for (int k = lane; k < (int)(sizeof(KParams<R>) / 4); k += 32) dst[k] = src[k];
+            cur = w.x;
+            __syncwarp();
+        }
+        const KParams<R> *p = ps;
         const int kind = a.kind[w.x];
         const int mat = kind % MAT_N;
         const int n = w.z - w.y;
@@ -112,7 +134,7 @@ template <int OP, typename R> int occupancy_fused(size_t wreg, int *wpb_io)
     int best = 0;
     for (int wpb : {4, 2, 1}) {
         if (only > 0 && wpb != only) continue;
-        const size_t smem = 128 + (size_t)wpb * wreg;
+        const size_t smem = 128 + (size_t)wpb * (wreg + fused_param_bytes<R>());
         if (smem > 227 * 1024) continue;
         int nb = 0;
         cudaError_t e = cudaFuncSetAttribute(k_fused<R, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -129,7 +151,7 @@ template <int OP, typename R> int occupancy_fused(size_t wreg, int *wpb_io)
 template <int OP, typename R>
 cudaError_t launch_fused(const FusedArgs<R> &a, int grid, int wpb, cudaStream_t s)
 {
-    const size_t smem = 128 + (size_t)wpb * a.wreg;
+    const size_t smem = 128 + (size_t)wpb * (a.wreg + fused_param_bytes<R>());
     cudaError_t e = cudaFuncSetAttribute(k_fused<R, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_fused<R, OP><<<grid, 32 * wpb, smem, s>>>(a);

@@ -407,6 +407,7 @@ class Mesh:
         if v is not None:
             self._node_array(v, "v")
         _check(load().tlfe_autotune(self._h, _ptr(u), _ptr(udot), _ptr(v), _stream(stream)))
+        self.info = self.get_info()   # the tuner may switch between fused and per-pass launches
 
     def set_elem_mu_lambda(self, theta, stream=None):
         """theta: contiguous CUDA float64 tensor (n_elem, 2) of per-element (mu, lambda)."""
