@@ -3,6 +3,12 @@
 Each translation unit under csrc/ is compiled by its own nvcc process (in
 parallel), then linked into ``_build/libtlfe.so``. Re-running only recompiles
 units whose source or any header is newer than their object file.
+
+``build(checked=True)`` also links ``_build/libtlfe_checked.so``, the
+bounds-checked build: the element-kernel units compiled with
+TLFE_BOUNDS_CHECK (every index read from a device table range-checked into
+the status word, see tlfe_internal.h), the other units shared with the
+normal build. ``tlfe.load()`` takes it when TLFE_LIB names it.
 """
 
 from __future__ import annotations
@@ -18,6 +24,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libtlfe.so")
+LIB_CHECKED = os.path.join(OUT, "libtlfe_checked.so")
+# units holding the element kernels: compiled a second time with the bounds checks
+CHECKED_UNITS = ("k_force.cu", "k_matvec.cu", "k_vjp.cu", "k_diag.cu", "k_fused_force.cu", "k_fused_matvec.cu")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -38,11 +47,13 @@ def _deps_mtime() -> float:
     return max(os.path.getmtime(h) for h in hdrs)
 
 
-def _compile(src: str, verbose_ptxas: bool) -> str:
-    obj = os.path.join(OUT, os.path.basename(src).replace(".cu", ".o"))
+def _compile(src: str, verbose_ptxas: bool, checked: bool = False) -> str:
+    obj = os.path.join(OUT, os.path.basename(src).replace(".cu", ".checked.o" if checked else ".o"))
     if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(src), _deps_mtime()):
         return obj
-    cmd = [nvcc()] + ARCH + FLAGS + (["-Xptxas", "-v"] if verbose_ptxas else []) + ["-c", src, "-o", obj + ".tmp"]
+    extra = ["-DTLFE_BOUNDS_CHECK"] if checked else []
+    cmd = [nvcc()] + ARCH + FLAGS + extra + (["-Xptxas", "-v"] if verbose_ptxas else []) + \
+        ["-c", src, "-o", obj + ".tmp"]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{res.stderr[-4000:]}")
@@ -53,21 +64,33 @@ def _compile(src: str, verbose_ptxas: bool) -> str:
     return obj
 
 
-def build(verbose_ptxas: bool = False, jobs: int | None = None) -> str:
+def _link(lib: str, objs) -> None:
+    if os.path.exists(lib) and os.path.getmtime(lib) >= max(os.path.getmtime(o) for o in objs):
+        return
+    tmp = lib + f".tmp{os.getpid()}"
+    cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + list(objs) + ["-lcudart_static", "-lrt", "-ldl", "-lpthread"]
+    res = subprocess.run(cmd, capture_output=True, text=True)
+    if res.returncode != 0:
+        raise RuntimeError(f"link failed:\n{res.stderr[-4000:]}")
+    os.replace(tmp, lib)
+
+
+def build(verbose_ptxas: bool = False, jobs: int | None = None, checked: bool = False) -> str:
     os.makedirs(OUT, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
-    jobs = jobs or min(len(srcs), os.cpu_count() or 4)
+    tasks = [(s, False) for s in srcs]
+    if checked:
+        tasks += [(s, True) for s in srcs if os.path.basename(s) in CHECKED_UNITS]
+    # the heaviest units first, so that the parallel build ends sooner
+    tasks.sort(key=lambda t: os.path.basename(t[0]) not in CHECKED_UNITS)
+    jobs = jobs or min(len(tasks), os.cpu_count() or 4)
     with cf.ThreadPoolExecutor(max_workers=jobs) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose_ptxas), srcs))
-    if not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
-        tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart_static", "-lrt", "-ldl", "-lpthread"]
-        res = subprocess.run(cmd, capture_output=True, text=True)
-        if res.returncode != 0:
-            raise RuntimeError(f"link failed:\n{res.stderr[-4000:]}")
-        os.replace(tmp, LIB)
+        objs = dict(zip(tasks, ex.map(lambda t: _compile(t[0], verbose_ptxas, t[1]), tasks)))
+    _link(LIB, [objs[(s, False)] for s in srcs])
+    if checked:
+        _link(LIB_CHECKED, [objs[(s, os.path.basename(s) in CHECKED_UNITS)] for s in srcs])
     return LIB
 
 
 if __name__ == "__main__":
-    print(build(verbose_ptxas="-v" in sys.argv))
+    print(build(verbose_ptxas="-v" in sys.argv, checked="--checked" in sys.argv))

@@ -828,6 +828,9 @@ extern "C" tlfe_status tlfe_sync(tlfe_mesh *m, void *stream, int64_t *n_inverted
     CK(cudaStreamSynchronize(s));
     if (n_inverted) *n_inverted = h[ST_INVERTED];
     if (h[ST_TIMEOUT]) return fail(TLFE_E_TIMEOUT, "a bounded device wait ran out");
+    if (h[ST_BOUNDS])
+        return fail(TLFE_E_INVALID, std::to_string(h[ST_BOUNDS]) +
+                                        " table index(es) out of range in the element kernels (bounds-checked build)");
     if (h[ST_NONFINITE]) return fail(TLFE_E_NONFINITE, "non-finite value met on the device");
     if (h[ST_INVERTED]) return fail(TLFE_E_INVERTED, std::to_string(h[ST_INVERTED]) + " quadrature point(s) with J <= 0");
     return TLFE_OK;
@@ -875,6 +878,11 @@ template <typename R> static void block_params(tlfe_mesh *m, const BlockStore &B
     p.mat0 = to_mat<R>(m->h_mats[B.uniform_body >= 0 ? B.uniform_body : 0]);
     p.status = m->d_status;
     p.part_base = B.part_base;
+    p.n_nodes = m->n_nodes;
+    p.n_elem_total = m->n_elem;
+    p.n_mats = m->n_bodies;
+    p.n_part = m->n_part;
+    p.n_elem_block = B.n_elem;
 }
 
 // the launch schedule of (OP, block bi): from the cache, else from the occupancy API

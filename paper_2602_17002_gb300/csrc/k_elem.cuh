@@ -362,7 +362,7 @@ __device__ __forceinline__ bool elem_tiles(const KParams<R> &p, unsigned char *w
             mt_issued = k + 2;
         }
         const unsigned char *M = mbuf + (size_t)(k & 1) * MRB;
-        const int U = *reinterpret_cast<const int32_t *>(M);
+        const int U = (int)bounds_clamp(*reinterpret_cast<const int32_t *>(M), (int64_t)p.umax + 1, p.status);
         const int e = reinterpret_cast<const int32_t *>(M + 16)[lane];
         const int32_t *nodes = reinterpret_cast<const int32_t *>(M + 16 + 128);
         const uint16_t *mlidx = reinterpret_cast<const uint16_t *>(M + 16 + 128 + 4 * p.umaxp);
@@ -376,7 +376,7 @@ __device__ __forceinline__ bool elem_tiles(const KParams<R> &p, unsigned char *w
         // split the FP64 displacement in place into its (hi, lo) pair (both
         // take the same 24 bytes of the record)
         for (int kk = lane; kk < U; kk += 32) {
-            const int64_t n = nodes[kk];
+            const int64_t n = bounds_clamp(nodes[kk], p.n_nodes, p.status);
             R *rec = work + (size_t)kk * REC;
 #pragma unroll
             for (int a = 0; a < 3; ++a) cp_async<8>(reinterpret_cast<double *>(rec) + a, p.u + 3 * n + a);
@@ -417,10 +417,10 @@ __device__ __forceinline__ bool elem_tiles(const KParams<R> &p, unsigned char *w
         }
         int li[NPE];
 #pragma unroll
-        for (int i = 0; i < NPE; ++i) li[i] = mlidx[i * 32 + lane];
+        for (int i = 0; i < NPE; ++i) li[i] = (int)bounds_clamp(mlidx[i * 32 + lane], U, p.status);
         const bool valid = e >= 0;
         Mat<R> m = p.mat0;
-        if (p.mats) m = p.mats[p.emat[(size_t)t * 32 + lane]];
+        if (p.mats) m = p.mats[bounds_clamp(p.emat[(size_t)t * 32 + lane], p.n_mats, p.status)];
         if (p.elam) {
             m.mu = p.elam[((size_t)t * 2 + 0) * 32 + lane];
             m.lam = p.elam[((size_t)t * 2 + 1) * 32 + lane];
@@ -886,7 +886,7 @@ __device__ __forceinline__ bool elem_tiles(const KParams<R> &p, unsigned char *w
                 }
             }
         }
-        if (OP == OP_VJP && valid && p.gth) {
+        if (OP == OP_VJP && valid && p.gth && bounds_ok(e, p.n_elem_total, p.status)) {
             p.gth[(size_t)e * 2 + 0] = double(gmu_acc);
             p.gth[(size_t)e * 2 + 1] = double(glam_acc);
         }
@@ -905,7 +905,7 @@ __device__ __forceinline__ bool elem_tiles(const KParams<R> &p, unsigned char *w
             if (valid) {
 #pragma unroll
                 for (int i = 0; i < NPE; ++i) {
-                    const int ps = spos[i * 32 + lane];
+                    const int ps = (int)bounds_clamp(spos[i * 32 + lane], NPE * 32, p.status);
                     if constexpr (PKA) {
                         const float2 a01 = fo == 0 ? ap0[i] : ap1[i];
                         work[ps * 3] = a01.x;
@@ -920,7 +920,8 @@ __device__ __forceinline__ bool elem_tiles(const KParams<R> &p, unsigned char *w
             __syncwarp();
         };
         auto node_sum = [&](int kk, R &a0, R &a1, R &a2) {
-            const int s0 = soff[kk], s1e = soff[kk + 1];
+            const int s0 = (int)bounds_clamp(soff[kk], NPE * 32 + 1, p.status);
+            const int s1e = (int)bounds_clamp(soff[kk + 1], NPE * 32 + 1, p.status);
             a0 = a1 = a2 = R(0);
             for (int sb = s0; sb < s1e; sb += 4) {
 #pragma unroll
@@ -936,8 +937,10 @@ __device__ __forceinline__ bool elem_tiles(const KParams<R> &p, unsigned char *w
 #pragma unroll
             for (int fo = 0; fo < NFO; ++fo) {
                 slots_in(fo);
-                R *dst = (fo == 0 ? p.part0 : p.part1) + (int64_t)reinterpret_cast<const int32_t *>(M)[1] * 3;
+                const int64_t P0 = reinterpret_cast<const int32_t *>(M)[1];
+                R *dst = (fo == 0 ? p.part0 : p.part1) + P0 * 3;
                 for (int kk = lane; kk < U; kk += 32) {
+                    if (!bounds_ok(P0 + kk, p.n_part, p.status)) continue;
                     R a0, a1, a2;
                     node_sum(kk, a0, a1, a2);
                     dst[kk * 3] = a0;
@@ -951,7 +954,7 @@ __device__ __forceinline__ bool elem_tiles(const KParams<R> &p, unsigned char *w
                 R *out = fo == 0 ? p.out0 : p.out1;
                 slots_in(fo);
                 for (int kk = lane; kk < U; kk += 32) {
-                    const int64_t n = nodes[kk];
+                    const int64_t n = bounds_clamp(nodes[kk], p.n_nodes, p.status);
                     R a0, a1, a2;
                     node_sum(kk, a0, a1, a2);
                     if (p.rmw_scatter) {

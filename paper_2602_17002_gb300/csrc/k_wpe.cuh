@@ -96,7 +96,8 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 2) k_wpe_q27(const K
 
         // ---- nodal values of the element: lane n loads node n
         const int nl = q_lane ? lane : 0;
-        const int64_t node = p.conn[((int64_t)e - p.elem_base) * 27 + nl];
+        const int64_t node = bounds_clamp(p.conn[bounds_clamp((int64_t)e - p.elem_base, p.n_elem_block, p.status) * 27 + nl],
+                                          p.n_nodes, p.status);
         {
             double u3[3];
             R d[3];
@@ -305,7 +306,8 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 2) k_wpe_q27(const K
                 R *part = fo == 0 ? p.part0 : p.part1;
                 const R *a3 = fo == 0 ? acc0 : acc1;
                 if (part) {  // sorted scatter: this element's partial for node n
-                    R *dst = part + (int64_t)((int)p.part_base + s * 27 + n) * 3;  // positions < 2^31
+                    const int64_t pos = (int64_t)((int)p.part_base + s * 27 + n);  // positions < 2^31
+                    R *dst = part + bounds_clamp(pos, p.n_part, p.status) * 3;
                     dst[0] = a3[0];
                     dst[1] = a3[1];
                     dst[2] = a3[2];
@@ -320,7 +322,7 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 2) k_wpe_q27(const K
                 }
             }
         }
-        if (OP == OP_VJP && p.gth) {
+        if (OP == OP_VJP && p.gth && bounds_ok(e, p.n_elem_total, p.status)) {
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 gmu += __shfl_xor_sync(0xffffffffu, gmu, o);

@@ -13,7 +13,9 @@
 namespace tlfe {
 
 enum { OP_FORCE = 0, OP_MATVEC = 1, OP_VJP = 2, OP_DIAG = 3 };
-enum { ST_INVERTED = 0, ST_NONFINITE = 1, ST_TIMEOUT = 2, ST_COUNT = 4 };
+// status word: counts of device-side events, read and cleared by tlfe_sync;
+// ST_BOUNDS counts table indices found out of range (bounds-checked build)
+enum { ST_INVERTED = 0, ST_NONFINITE = 1, ST_TIMEOUT = 2, ST_BOUNDS = 3, ST_COUNT = 4 };
 // material modes of an element launch: the law and the viscous term fixed at
 // compile time, or both read per element (MAT_ANY)
 enum { MAT_ANY = 0, MAT_NH = 1, MAT_NH_KV = 2, MAT_SVK = 3, MAT_SVK_KV = 4 };
@@ -75,7 +77,38 @@ template <typename R> struct KParams {
     int mat_mode;               // MAT_* (compile-time material of the launched kernel)
     int tile_chunk;             // 1: each warp takes a contiguous run of tiles; 0: interleaved
     int *status;                // [ST_COUNT]
+    // extents of the arrays the tables index, for the bounds-checked build
+    // (TLFE_BOUNDS_CHECK): node arrays, parameter gradient, partial sums, materials
+    int n_nodes, n_elem_total, n_mats, n_elem_block;
+    int64_t n_part;
 };
+
+// Bounds-checked build (compiled with TLFE_BOUNDS_CHECK): an index read from a
+// device table is checked against the extent of the array it addresses; an
+// index out of range is counted in the status word (ST_BOUNDS, reported by
+// tlfe_sync) and clamped into the array, so that the access stays in bounds.
+// The normal build compiles the checks away.
+__device__ __forceinline__ int64_t bounds_clamp(int64_t x, int64_t lim, int *status)
+{
+#ifdef TLFE_BOUNDS_CHECK
+    if (x < 0 || x >= lim) {
+        atomicAdd(status + ST_BOUNDS, 1);
+        return x < 0 ? 0 : (lim > 0 ? lim - 1 : 0);
+    }
+#endif
+    return x;
+}
+// whether an index is in range (always true in the normal build); counts misses
+__device__ __forceinline__ bool bounds_ok(int64_t x, int64_t lim, int *status)
+{
+#ifdef TLFE_BOUNDS_CHECK
+    if (x < 0 || x >= lim) {
+        atomicAdd(status + ST_BOUNDS, 1);
+        return false;
+    }
+#endif
+    return true;
+}
 
 // element-kernel launcher for one op and precision, dispatching on (element
 // type, nq) and on the path (affine when p.aff is set, else the slab);

@@ -15,7 +15,9 @@ from typing import Optional, Sequence
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build", "libtlfe.so")
+# TLFE_LIB may name another build of the library, e.g. the bounds-checked
+# _build/libtlfe_checked.so (build_lib.build(checked=True))
+LIB_PATH = os.environ.get("TLFE_LIB") or os.path.join(HERE, "_build", "libtlfe.so")
 
 T4, T10, H8, Q27 = 0, 1, 2, 3
 SVK, NEOHOOKE, MOONEY_RIVLIN = 0, 1, 2
