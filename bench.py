@@ -573,6 +573,8 @@ def run_reference(args):
                  "cpu_baseline": {"value": value, "unit": unit, "cores": thr, "kind": "oracle", "sample": what},
                  "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}})
     line["config"]["parallelism"] = f"host, {thr} core{'s' if thr > 1 else ''}"
+    line["config"]["workload"] = WORKLOADS[args.workload].replace(", FP32", "") + \
+        " (the FP64 CPU oracle on a bounded sample of it)"
     print(json.dumps(line), flush=True)
     return 0
 
