@@ -785,6 +785,8 @@ def run_beam(args, rank, world, workload="beam"):
                            for n, t in zip(names, kern_ms)},
         "roofline": roof,
         "element_path": "affine (Sec. 6 affine case: J^-1 and det J per element)",
+        "patch": {"layout": "banked" if info["patch_layout"] == tlfe.PATCH_BANKED else "sorted",
+                  "passes_per_quarter_warp_load": info["patch_passes"]},
         "slab_path": slab,
         "fp64_plain": {"ms_per_step": ms64, "kernels_ms": {n: float(t) for n, t in zip(names, per64.mean(axis=0))},
                        "speedup_fp32_over_fp64": ms64 / step_ms, "device_status": st64},

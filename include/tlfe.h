@@ -89,6 +89,18 @@ enum { TLFE_SCATTER_ATOMIC = 0, TLFE_SCATTER_COLOR = 1, TLFE_SCATTER_SORTED = 2 
  *   TLFE_PATH_AFFINE : every block on the affine path; TLFE_E_UNSUPPORTED at
  *                      creation when a block is not affine */
 enum { TLFE_PATH_AUTO = 0, TLFE_PATH_SLAB = 1, TLFE_PATH_AFFINE = 2 };
+/* Order of a tile's nodes in the shared-memory node patch of the element
+ * kernels (32 elements per tile; results do not depend on it):
+ *   TLFE_PATCH_BANKED : nodes placed so that the 8 lanes of a quarter warp,
+ *                       which read the same element-local node of their
+ *                       elements in one 16-byte load, hit distinct bank
+ *                       groups; nodes move only inside runs of 32 in
+ *                       ascending id, so that the gather and scatter touch
+ *                       the same memory sectors per warp instruction (default)
+ *   TLFE_PATCH_SORTED : nodes in ascending id
+ * On the T10 beam a quarter-warp patch load takes 1.03 shared-memory passes
+ * banked and 1.88 sorted (tlfe_mesh_info.patch_passes). */
+enum { TLFE_PATCH_BANKED = 0, TLFE_PATCH_SORTED = 1 };
 /* How the element passes of one operation are launched (a property of this
  * GPU implementation; the paper has no counterpart):
  *   TLFE_LAUNCH_AUTO     : one persistent launch per operation over every pass
@@ -145,6 +157,7 @@ typedef struct {
                                        TLFE_SCATTER_SORTED (deterministic node-ordered partial sums) */
     uint64_t color_seed;            /* priority seed of the conflict colouring */
     int32_t element_path;           /* TLFE_PATH_AUTO, TLFE_PATH_SLAB or TLFE_PATH_AFFINE */
+    int32_t patch_layout;           /* TLFE_PATCH_BANKED (0) or TLFE_PATCH_SORTED */
 } tlfe_mesh_desc;
 
 typedef struct tlfe_mesh tlfe_mesh;
@@ -176,6 +189,10 @@ typedef struct {
     int32_t n_fused_items;        /* work items (tile runs) of the fused launch */
     int32_t launches_force;       /* kernel launches of one tlfe_internal_force in the current launch mode */
     int32_t launches_matvec;      /* kernel launches of one tlfe_tangent_matvec in the current launch mode */
+    int32_t patch_layout;         /* the desc's patch_layout */
+    double patch_passes;          /* shared-memory passes of one 16-byte node-patch load of a quarter warp
+                                     (8 lanes reading one element-local node of their elements), averaged
+                                     over the tile kernels' loads; 1 = free of bank conflicts */
 } tlfe_mesh_info;
 
 tlfe_status tlfe_get_mesh_info(const tlfe_mesh *mesh, tlfe_mesh_info *info);

@@ -9,6 +9,7 @@
 #include <cstring>
 #include <numeric>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "tlfe_elem.cuh"
@@ -84,6 +85,8 @@ static tlfe_status validate(const tlfe_mesh_desc *d)
         return fail(TLFE_E_INVALID, "bad scatter mode");
     if (d->element_path != TLFE_PATH_AUTO && d->element_path != TLFE_PATH_SLAB && d->element_path != TLFE_PATH_AFFINE)
         return fail(TLFE_E_INVALID, "bad element path");
+    if (d->patch_layout != TLFE_PATCH_BANKED && d->patch_layout != TLFE_PATCH_SORTED)
+        return fail(TLFE_E_INVALID, "bad patch layout");
     for (int k = 0; k < 3 * d->n_nodes; ++k)
         if (!std::isfinite(d->X_ref[k])) return fail(TLFE_E_INVALID, "X_ref holds a non-finite value");
     for (int b = 0; b < d->n_bodies; ++b) {
@@ -309,6 +312,162 @@ static std::vector<int32_t> locality_order(const tlfe_mesh_desc *d, const tlfe_b
     return best;
 }
 
+// Shared-memory passes of the node-patch loads of one tile. The FP32 element
+// kernels read a node's 48-byte patch record in 16-byte loads, and the 8
+// lanes of a quarter warp (one pass of a 16-byte load) all read the record of
+// the same element-local node i of their elements: record s starts in 16-byte
+// bank group 3 s mod 8, so distinct records whose slots agree mod 8 are read
+// in separate passes (equal records are one broadcast). `li` holds [npe][32]
+// slots, `valid` the lanes that hold an element; returns the passes summed
+// over (i, quarter) and adds the loads to *loads.
+static int64_t patch_tile_passes(int npe, const uint16_t *li, const bool *valid, int64_t *loads)
+{
+    int64_t passes = 0;
+    for (int i = 0; i < npe; ++i)
+        for (int q = 0; q < TILE / 8; ++q) {
+            int seen[8], ns = 0, mult[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            for (int l = q * 8; l < q * 8 + 8; ++l) {
+                if (!valid[l]) continue;
+                const int sl = li[i * TILE + l];
+                bool dup = false;
+                for (int k = 0; k < ns; ++k) dup = dup || seen[k] == sl;
+                if (dup) continue;
+                seen[ns++] = sl;
+                ++mult[sl & 7];
+            }
+            if (ns == 0) continue;
+            ++*loads;
+            passes += *std::max_element(mult, mult + 8);
+        }
+    return passes;
+}
+
+// Patch slots of a tile's U unique nodes (TLFE_PATCH_BANKED): nodes read
+// together by a quarter warp (see patch_tile_passes) get distinct slots mod 8.
+// The gather and the scatter walk the list 32 entries per warp instruction,
+// so each run of 32 consecutive nodes in ascending id keeps its 32 entries
+// (its nodes only change places inside the run): the warp's global accesses
+// touch the same sectors as in ascending order. Inside that limit this
+// colours the conflict graph with the 8 residues: nodes by decreasing
+// conflict count, each onto the residue its already placed neighbours use
+// least among those its run still has room for (ceil(n / 8) per residue for
+// a run of n nodes; ties: the least used, then the lowest residue); then,
+// while some node gains, a move to a residue with room or a swap with a
+// node of another residue in its run. Node k of run j gets slot 32 j + 8 r +
+// c, c its residue and r its rank among the run's nodes of that residue; the
+// last run may leave holes. `pos` holds [npe][32] indices into the sorted
+// list; returns the slot count S.
+static int patch_slots(int U, int npe, const uint16_t *pos, const bool *valid, std::vector<uint16_t> &slot)
+{
+    // the loads: distinct nodes of each (i, quarter)
+    static thread_local std::vector<int> gk, deg, adj, fill, col, order, cnt, cap;
+    const int n_loads = npe * (TILE / 8);
+    gk.assign((size_t)n_loads * 9, 0);
+    for (int g = 0; g < n_loads; ++g) {
+        const int i = g / (TILE / 8), q = g % (TILE / 8);
+        int *G = gk.data() + (size_t)g * 9, ng = 0;
+        for (int l = q * 8; l < q * 8 + 8; ++l) {
+            if (!valid[l]) continue;
+            const int k = pos[i * TILE + l];
+            bool dup = false;
+            for (int j = 0; j < ng; ++j) dup = dup || G[1 + j] == k;
+            if (!dup) G[1 + ng++] = k;
+        }
+        G[0] = ng;
+    }
+    // conflict lists (a pair sharing several loads appears once per load)
+    deg.assign(U + 1, 0);
+    for (int g = 0; g < n_loads; ++g) {
+        const int *G = gk.data() + (size_t)g * 9;
+        for (int a = 0; a < G[0]; ++a) deg[G[1 + a] + 1] += G[0] - 1;
+    }
+    for (int k = 0; k < U; ++k) deg[k + 1] += deg[k];
+    adj.resize(deg[U]);
+    fill.assign(deg.begin(), deg.end() - 1);
+    for (int g = 0; g < n_loads; ++g) {
+        const int *G = gk.data() + (size_t)g * 9;
+        for (int a = 0; a < G[0]; ++a)
+            for (int b = 0; b < G[0]; ++b)
+                if (a != b) adj[fill[G[1 + a]]++] = G[1 + b];
+    }
+    // runs of 32 and their room per residue
+    const int n_runs = (U + 31) / 32;
+    cnt.assign((size_t)n_runs * 8, 0);
+    cap.resize(n_runs);
+    for (int j = 0; j < n_runs; ++j) cap[j] = (std::min(32, U - 32 * j) + 7) / 8;
+    col.assign(U, -1);
+    order.resize(U);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return deg[a + 1] - deg[a] > deg[b + 1] - deg[b]; });
+    auto conflicts = [&](int a, int *c8) {
+        for (int c = 0; c < 8; ++c) c8[c] = 0;
+        for (int j = deg[a]; j < deg[a + 1]; ++j)
+            if (col[adj[j]] >= 0) ++c8[col[adj[j]]];
+    };
+    for (int a : order) {
+        int c8[8], best = -1;
+        const int *n8 = cnt.data() + (size_t)(a / 32) * 8;
+        conflicts(a, c8);
+        for (int c = 0; c < 8; ++c) {
+            if (n8[c] >= cap[a / 32]) continue;
+            if (best < 0 || c8[c] < c8[best] || (c8[c] == c8[best] && n8[c] < n8[best])) best = c;
+        }
+        col[a] = best;
+        ++cnt[(size_t)(a / 32) * 8 + best];
+    }
+    for (int pass = 0; pass < 8; ++pass) {
+        bool changed = false;
+        for (int a = 0; a < U; ++a) {
+            int c8[8];
+            conflicts(a, c8);
+            const int ca = col[a], j = a / 32;
+            if (c8[ca] == 0) continue;
+            int *n8 = cnt.data() + (size_t)j * 8;
+            int best = ca;
+            for (int c = 0; c < 8; ++c)
+                if (c != ca && n8[c] < cap[j] && c8[c] < c8[best]) best = c;
+            if (best != ca) {
+                --n8[ca];
+                ++n8[best];
+                col[a] = best;
+                changed = true;
+                continue;
+            }
+            // swap with the node b of the run that lowers the conflicts of
+            // a and b the most (entries of a and b on each other drop out)
+            int gain = 0, swap_with = -1;
+            for (int b = 32 * j; b < std::min(U, 32 * j + 32); ++b) {
+                const int cb = col[b];
+                if (cb == ca) continue;
+                int d8[8], ab = 0;
+                conflicts(b, d8);
+                for (int e = deg[a]; e < deg[a + 1]; ++e) ab += adj[e] == b;
+                const int g = (c8[ca] + d8[cb]) - ((c8[cb] - ab) + (d8[ca] - ab));
+                if (g > gain) {
+                    gain = g;
+                    swap_with = b;
+                }
+            }
+            if (swap_with >= 0) {
+                std::swap(col[a], col[swap_with]);
+                changed = true;
+            }
+        }
+        if (!changed) break;
+    }
+    slot.assign(U, 0);
+    int S = 0;
+    for (int j = 0; j < n_runs; ++j) {
+        int rank[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int a = 32 * j; a < std::min(U, 32 * j + 32); ++a) {
+            slot[a] = (uint16_t)(32 * j + 8 * rank[col[a]]++ + col[a]);
+            S = std::max(S, slot[a] + 1);
+        }
+    }
+    return S;
+}
+
 static tlfe_status build_block(tlfe_mesh *m, const tlfe_mesh_desc *d, int bi, int elem_base, cudaStream_t s)
 {
     const tlfe_block &b = d->blocks[bi];
@@ -359,51 +518,105 @@ static tlfe_status build_block(tlfe_mesh *m, const tlfe_mesh_desc *d, int bi, in
     }
     B.n_tiles = (int)(eid.size() / TILE);
 
-    // per tile: sorted unique node list, (element, node) -> list index, and
-    // for each slot i*32 + lane its position in the node-sorted order (the
-    // positions of unique node k are [soff[k], soff[k + 1]))
+    // per tile: its node list (the unique nodes, in ascending id or, in the
+    // banked patch layout, at their patch slots with holes of -1 between),
+    // (element, node) -> list index, and for each slot i*32 + lane its
+    // position in the node-grouped order (the positions of list entry kk are
+    // [soff[kk], soff[kk + 1]), empty for a hole). Tiles are independent:
+    // batches of them are built on the host's cores, then appended in order.
     std::vector<int32_t> toff(B.n_tiles + 1, 0), tnodes;
     std::vector<uint16_t> lidx((size_t)B.n_tiles * npe * TILE, 0);
     std::vector<uint16_t> nsl((size_t)B.n_tiles * npe * TILE, 0xFFFF), soff;
     soff.reserve((size_t)B.n_tiles * (npe * 12 + 1));
-    std::vector<int> cnt;
     tnodes.reserve((size_t)B.n_tiles * npe * 12);
-    std::vector<int32_t> tmp;
     B.umax = 1;
-    for (int t = 0; t < B.n_tiles; ++t) {
+    B.patch_loads = B.patch_passes = 0;
+    struct TileList {
+        std::vector<int32_t> nodes;
+        std::vector<uint16_t> soff;
+        int64_t loads = 0, passes = 0;
+    };
+    const bool banked = d->patch_layout == TLFE_PATCH_BANKED;
+    auto build_tile = [&](int t, TileList &o) {
+        static thread_local std::vector<int32_t> ulist;
+        static thread_local std::vector<uint16_t> slot;
+        static thread_local std::vector<int> cnt;
+        std::vector<int32_t> &tmp = o.nodes;
         tmp.clear();
+        bool valid[TILE];
         for (int l = 0; l < TILE; ++l) {
             const int e = eid[(size_t)t * TILE + l];
+            valid[l] = e >= 0;
             if (e < 0) continue;
             for (int i = 0; i < npe; ++i) tmp.push_back(b.conn[(int64_t)(e - elem_base) * npe + i]);
         }
         std::sort(tmp.begin(), tmp.end());
         tmp.erase(std::unique(tmp.begin(), tmp.end()), tmp.end());
+        uint16_t *lt = lidx.data() + (size_t)t * npe * TILE;
         for (int l = 0; l < TILE; ++l) {
+            if (!valid[l]) continue;
             const int e = eid[(size_t)t * TILE + l];
-            if (e < 0) continue;
             for (int i = 0; i < npe; ++i) {
                 const int nd = b.conn[(int64_t)(e - elem_base) * npe + i];
-                const int pos = (int)(std::lower_bound(tmp.begin(), tmp.end(), nd) - tmp.begin());
-                lidx[((size_t)t * npe + i) * TILE + l] = (uint16_t)pos;
+                lt[i * TILE + l] = (uint16_t)(std::lower_bound(tmp.begin(), tmp.end(), nd) - tmp.begin());
             }
         }
+        // the banked layout moves node k of the sorted list to slot[k]
+        if (banked && !tmp.empty()) {
+            const int S = patch_slots((int)tmp.size(), npe, lt, valid, slot);
+            for (int k = 0; k < npe * TILE; ++k) lt[k] = valid[k % TILE] ? slot[lt[k]] : slot[0];
+            ulist.assign(S, -1);
+            for (size_t k = 0; k < tmp.size(); ++k) ulist[slot[k]] = tmp[k];
+            tmp.swap(ulist);
+        }
+        o.loads = 0;
+        o.passes = patch_tile_passes(npe, lt, valid, &o.loads);
         const int U = (int)tmp.size();
         cnt.assign(U + 1, 0);
         for (int l = 0; l < TILE; ++l)
-            if (eid[(size_t)t * TILE + l] >= 0)
-                for (int i = 0; i < npe; ++i) cnt[lidx[((size_t)t * npe + i) * TILE + l] + 1]++;
+            if (valid[l])
+                for (int i = 0; i < npe; ++i) cnt[lt[i * TILE + l] + 1]++;
         for (int k = 0; k < U; ++k) cnt[k + 1] += cnt[k];
-        for (int k = 0; k <= U; ++k) soff.push_back((uint16_t)cnt[k]);
+        o.soff.assign(cnt.begin(), cnt.end());
+        uint16_t *nt = nsl.data() + (size_t)t * npe * TILE;
         for (int i = 0; i < npe; ++i)
             for (int l = 0; l < TILE; ++l)
-                if (eid[(size_t)t * TILE + l] >= 0) {
-                    const int k = lidx[((size_t)t * npe + i) * TILE + l];
-                    nsl[(size_t)t * npe * TILE + i * TILE + l] = (uint16_t)(cnt[k]++);
+                if (valid[l]) nt[i * TILE + l] = (uint16_t)(cnt[lt[i * TILE + l]]++);
+    };
+    {
+        constexpr int BATCH = 8192;
+        const int nthr = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+        std::vector<TileList> out((size_t)std::min(B.n_tiles, BATCH));
+        for (int t0 = 0; t0 < B.n_tiles; t0 += BATCH) {
+            const int t1 = std::min(B.n_tiles, t0 + BATCH);
+            auto worker = [&](int w, int nw) {
+                for (int t = t0 + w; t < t1; t += nw) build_tile(t, out[t - t0]);
+            };
+            if (nthr == 1 || t1 - t0 < 256) {
+                worker(0, 1);
+            } else {
+                std::vector<std::thread> pool;
+                std::vector<int> here;  // shares whose thread could not be started run on this one
+                for (int w = 0; w < nthr; ++w) {
+                    try {
+                        pool.emplace_back(worker, w, nthr);
+                    } catch (...) {
+                        here.push_back(w);
+                    }
                 }
-        tnodes.insert(tnodes.end(), tmp.begin(), tmp.end());
-        toff[t + 1] = (int32_t)tnodes.size();
-        B.umax = std::max(B.umax, U);
+                for (int w : here) worker(w, nthr);
+                for (auto &th : pool) th.join();
+            }
+            for (int t = t0; t < t1; ++t) {
+                const TileList &o = out[t - t0];
+                tnodes.insert(tnodes.end(), o.nodes.begin(), o.nodes.end());
+                soff.insert(soff.end(), o.soff.begin(), o.soff.end());
+                toff[t + 1] = (int32_t)tnodes.size();
+                B.umax = std::max(B.umax, (int)o.nodes.size());
+                B.patch_loads += o.loads;
+                B.patch_passes += o.passes;
+            }
+        }
     }
     B.n_unique = (int64_t)tnodes.size();
 
@@ -643,6 +856,7 @@ extern "C" tlfe_status tlfe_create_mesh(const tlfe_mesh_desc *desc, void *stream
     m->blocks.resize(desc->n_blocks);
     m->color_seed = desc->color_seed;
     m->element_path = desc->element_path;
+    m->patch_layout = desc->patch_layout;
     m->h_X.assign(desc->X_ref, desc->X_ref + 3 * (size_t)desc->n_nodes);
     m->node_body.assign(desc->n_nodes, -1);
     {
@@ -788,6 +1002,14 @@ extern "C" tlfe_status tlfe_get_mesh_info(const tlfe_mesh *m, tlfe_mesh_info *in
     info->n_passes = 0;
     for (auto &B : m->blocks)
         if (B.n_elem > 0) info->n_passes += (int)B.color_tile_off.size() - 1;
+    info->patch_layout = m->patch_layout;
+    int64_t pl = 0, pp = 0;
+    for (auto &B : m->blocks)
+        if (!wpe_path(B.et, B.use_affine)) {
+            pl += B.patch_loads;
+            pp += B.patch_passes;
+        }
+    info->patch_passes = pl > 0 ? (double)pp / (double)pl : 1.0;
     info->n_fused_passes = m->fused ? (int)m->fused->passes.size() : 0;
     info->n_fused_items = m->fused ? m->fused->n_items : 0;
     // element-kernel launches of one force / operator-product call in the

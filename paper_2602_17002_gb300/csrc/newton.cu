@@ -535,6 +535,7 @@ static tlfe_status setup_newton(tlfe_mesh *m, cudaStream_t s, int coupled)
         d.scatter = m->scatter;
         d.color_seed = m->color_seed;
         d.element_path = m->element_path;
+        d.patch_layout = m->patch_layout;
         st = tlfe_create_mesh(&d, s, &ns->twin);
         if (st != TLFE_OK) return st;
     }

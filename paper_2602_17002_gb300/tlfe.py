@@ -25,6 +25,7 @@ FP64, FP32 = 0, 1
 SCATTER_ATOMIC, SCATTER_COLOR, SCATTER_SORTED = 0, 1, 2
 PATH_AUTO, PATH_SLAB, PATH_AFFINE = 0, 1, 2
 LAUNCH_AUTO, LAUNCH_PER_PASS, LAUNCH_FUSED = 0, 1, 2
+PATCH_BANKED, PATCH_SORTED = 0, 1
 NPE = {T4: 4, T10: 10, H8: 8, Q27: 27}
 
 STATUS = {0: "TLFE_OK", 1: "TLFE_E_INVALID", 2: "TLFE_E_OOM", 3: "TLFE_E_CUDA", 4: "TLFE_E_INVERTED",
@@ -51,7 +52,7 @@ class tlfe_mesh_desc(C.Structure):
     _fields_ = [("n_nodes", C.c_int32), ("X_ref", C.c_void_p), ("n_blocks", C.c_int32),
                 ("blocks", C.c_void_p), ("n_bodies", C.c_int32), ("body_mat", C.c_void_p),
                 ("elem_mu_lambda", C.c_void_p), ("precision", C.c_int32), ("scatter", C.c_int32),
-                ("color_seed", C.c_uint64), ("element_path", C.c_int32)]
+                ("color_seed", C.c_uint64), ("element_path", C.c_int32), ("patch_layout", C.c_int32)]
 
 
 class tlfe_mesh_info(C.Structure):
@@ -61,7 +62,7 @@ class tlfe_mesh_info(C.Structure):
                 ("stream_bytes_matvec", C.c_int64), ("stream_bytes_vjp", C.c_int64),
                 ("device_bytes", C.c_int64), ("n_affine_blocks", C.c_int32), ("n_passes", C.c_int32),
                 ("n_fused_passes", C.c_int32), ("n_fused_items", C.c_int32), ("launches_force", C.c_int32),
-                ("launches_matvec", C.c_int32)]
+                ("launches_matvec", C.c_int32), ("patch_layout", C.c_int32), ("patch_passes", C.c_double)]
 
 
 class tlfe_step_params(C.Structure):
@@ -183,11 +184,13 @@ class Mesh:
 
     def __init__(self, X: np.ndarray, blocks: Sequence[tuple], materials: Sequence[tuple],
                  elem_mu_lambda: Optional[np.ndarray] = None, precision: int = FP32,
-                 scatter: int = SCATTER_ATOMIC, color_seed: int = 0, stream=None, element_path: int = PATH_AUTO):
+                 scatter: int = SCATTER_ATOMIC, color_seed: int = 0, stream=None, element_path: int = PATH_AUTO,
+                 patch_layout: int = PATCH_BANKED):
         """X: (n_nodes, 3) float64 reference coordinates.
         blocks: (etype, n_qp, conn (n_elem, npe) int32, body (n_elem,) int32 or None).
         materials: per body (model, mu, lam, mu_v, lam_v, rho[, mu01]).
-        element_path: PATH_AUTO, PATH_SLAB or PATH_AFFINE (see include/tlfe.h)."""
+        element_path: PATH_AUTO, PATH_SLAB or PATH_AFFINE; patch_layout: PATCH_BANKED or
+        PATCH_SORTED (see include/tlfe.h)."""
         L = load()
         self._keep = []
         X = np.ascontiguousarray(X, dtype=np.float64)
@@ -209,7 +212,8 @@ class Mesh:
             self._keep.append(eml)
         desc = tlfe_mesh_desc(X.shape[0], X.ctypes.data, len(blocks), C.addressof(cb), len(materials),
                               C.addressof(cm), None if eml is None else eml.ctypes.data,
-                              int(precision), int(scatter), C.c_uint64(color_seed), int(element_path))
+                              int(precision), int(scatter), C.c_uint64(color_seed), int(element_path),
+                              int(patch_layout))
         h = C.c_void_p()
         _check(L.tlfe_create_mesh(C.byref(desc), _stream(stream), C.byref(h)))
         self._h = h
@@ -222,10 +226,11 @@ class Mesh:
 
     @classmethod
     def from_workload(cls, wl, precision=FP32, scatter=SCATTER_ATOMIC, color_seed=0, stream=None,
-                      element_path=PATH_AUTO):
+                      element_path=PATH_AUTO, patch_layout=PATCH_BANKED):
         blocks = [(b.etype, b.nq, b.conn, b.body) for b in wl.blocks]
         mats = [(int(wl.model[k]), *wl.params[k]) for k in range(wl.n_bodies)]
-        return cls(wl.X, blocks, mats, wl.elem_mu_lambda, precision, scatter, color_seed, stream, element_path)
+        return cls(wl.X, blocks, mats, wl.elem_mu_lambda, precision, scatter, color_seed, stream, element_path,
+                   patch_layout)
 
     @property
     def handle(self):
