@@ -414,9 +414,11 @@ tlfe_status tlfe_vjp(tlfe_mesh *mesh, const void *u_dev, const void *udot_dev, c
  * optional applied load (f_ext_dev; dead load over the step), by inexact
  * Newton: each iteration solves (M/h + h K^e + C) dv = -g by Jacobi-PCG with
  * per-body scalars (all bodies advance together, each stops on its own), and
- * stops when ||g_b|| <= newton_rtol ||g_b(v_n)|| for every body b. The residual,
- * the CG vectors, dots and updates are FP64; the operator products run in the
- * mesh precision. Nodes with fixed_dev[k] = 1 are clamped (v = 0).
+ * stops when ||g_b|| <= newton_rtol ||g_b(v_n)|| for every body b. The residual
+ * and the update of v are FP64; the operator products and the CG vectors run
+ * in the mesh precision, and the CG dots are summed per chunk in FP64 (an
+ * FP32 mesh forms each thread's share in double-float arithmetic, about 44
+ * significant bits). Nodes with fixed_dev[k] = 1 are clamped (v = 0).
  * The whole step is one CUDA graph with conditional WHILE nodes (built on the
  * first call, replayed afterwards).
  * With constraints (n_cons > 0) the step is the augmented-Lagrangian iteration

@@ -165,9 +165,10 @@ __global__ void k_con_jt(int n, const double *__restrict__ sh, const int32_t *__
     }
 }
 
-// out_k = (C_q v)_k
+// out_k = (C_q v)_k (v in FP64, or the FP32 search direction of an FP32 mesh)
+template <typename V>
 __global__ void k_con_j(int n, const double *__restrict__ sh, const int32_t *__restrict__ nd,
-                        const double *__restrict__ gp, const double *__restrict__ v, double *out)
+                        const double *__restrict__ gp, const V *__restrict__ v, double *out)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
@@ -264,12 +265,17 @@ template cudaError_t con_jt<float>(int, const double *, const int32_t *, const d
                                    cudaStream_t);
 template cudaError_t con_jt<double>(int, const double *, const int32_t *, const double *, const double *, double,
                                     double *, cudaStream_t);
-cudaError_t con_j(int n, const double *sh, const int32_t *nd, const double *gp, const double *v, double *out,
+template <typename V>
+cudaError_t con_j(int n, const double *sh, const int32_t *nd, const double *gp, const V *v, double *out,
                   cudaStream_t s)
 {
-    if (n > 0) k_con_j<<<grid_of(n), 128, 0, s>>>(n, sh, nd, gp, v, out);
+    if (n > 0) k_con_j<V><<<grid_of(n), 128, 0, s>>>(n, sh, nd, gp, v, out);
     return cudaGetLastError();
 }
+template cudaError_t con_j<float>(int, const double *, const int32_t *, const double *, const float *, double *,
+                                  cudaStream_t);
+template cudaError_t con_j<double>(int, const double *, const int32_t *, const double *, const double *, double *,
+                                   cudaStream_t);
 template <typename R>
 cudaError_t con_diag(int n, const double *sh, const int32_t *nd, const double *gp, double alpha, R *D, cudaStream_t s)
 {

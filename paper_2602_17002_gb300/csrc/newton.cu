@@ -36,6 +36,7 @@ namespace tlfe {
 
 constexpr int CHUNK = 4096;  // DOFs per reduction chunk
 constexpr int RT = 256;      // threads per chunk CTA
+constexpr int UNR = 4;       // DOFs a thread of the CG vector kernels loads before it uses them
 
 enum {
     S_G0 = 0,   // ||g_b(v_n)||
@@ -61,12 +62,13 @@ struct NewtonState {
     // body / chunk tables
     int nb = 0, n_chunks = 0;
     int32_t *chunk_start = nullptr, *chunk_end = nullptr, *chunk_body = nullptr, *body_chunk_off = nullptr;
-    // FP64 vectors [3N]
+    // FP64 vectors [3N] (x, r, p, Dinv: the CG state of an FP64 mesh)
     double *u_n = nullptr, *v_n = nullptr, *v = nullptr, *u_cur = nullptr, *dv = nullptr, *g = nullptr,
-           *fff = nullptr, *fgrav = nullptr, *y1 = nullptr, *y2 = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr,
+           *fff = nullptr, *fgrav = nullptr, *y1 = nullptr, *y2 = nullptr, *x = nullptr, *r = nullptr, *p = nullptr,
            *Dinv = nullptr, *gv = nullptr, *Dd = nullptr;
     // mesh-precision vectors [3N]
     float *ud32 = nullptr, *p32 = nullptr, *Ap32 = nullptr, *D32 = nullptr;
+    float *x32 = nullptr, *r32 = nullptr, *Dinv32 = nullptr;  // CG state of an FP32 mesh (p32: its direction)
     uint8_t *fixed = nullptr;  // [N], 1 = clamped (nodes outside every element included)
     double *partials = nullptr;  // [2][n_chunks]
     double *sc = nullptr;        // [S_COUNT][nb]
@@ -192,44 +194,76 @@ __global__ void k_newton_check(int nb, const int32_t *boff, const double *partia
     }
 }
 
-// Jacobi inverse on free DOFs of Newton-active bodies
+// Sum of products for the CG dots, per thread, in the vector type V of the CG
+// state. FP64 state: a plain FP64 sum. FP32 state: an unevaluated FP32 pair
+// (hi, lo), each product split exactly into its rounded value and error by
+// one FMA and added with Knuth's two-sum (error-free transformations; the
+// sum carries about 44 significant bits), so that the dots keep FP64-class
+// accuracy while running on the FP32 pipes (GB300's FP64 rate is about 1/64
+// of its FP32 rate, and these kernels would be bound by it). The intrinsics
+// keep the compiler from fusing the products into the sums.
+template <typename V> struct DotAcc;
+template <> struct DotAcc<double> {
+    double s = 0.0;
+    __device__ void add(double a, double b) { s += a * b; }
+    __device__ double value() const { return s; }
+};
+template <> struct DotAcc<float> {
+    float hi = 0.f, lo = 0.f;
+    __device__ void add(float a, float b)
+    {
+        const float p = __fmul_rn(a, b);
+        const float e = fmaf(a, b, -p);            // a b = p + e exactly
+        const float t = __fadd_rn(hi, p);          // two-sum: hi + p = t + err exactly
+        const float bv = __fsub_rn(t, hi);
+        const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bv)), __fsub_rn(p, bv));
+        hi = t;
+        lo = __fadd_rn(lo, __fadd_rn(err, e));
+    }
+    __device__ double value() const { return double(hi) + double(lo); }
+};
+
+// Jacobi inverse on free DOFs of Newton-active bodies, in the type of the CG state
 template <typename R>
-__global__ void k_dinv(ChunkArgs c, const R *D, const uint8_t *fixed, const double *sc, int nb, double *Dinv)
+__global__ void k_dinv(ChunkArgs c, const R *D, const uint8_t *fixed, const double *sc, int nb, R *Dinv)
 {
     const int ch = blockIdx.x;
     const int b = c.body[ch];
     const bool act = sc[S_NACT * nb + b] != 0.0;
     for (int i = c.start[ch] + threadIdx.x; i < c.end[ch]; i += blockDim.x) {
-        const double d = double(D[i]);
-        Dinv[i] = (act && !fixed[i / 3] && d != 0.0) ? 1.0 / d : 0.0;
+        const R d = D[i];
+        Dinv[i] = (act && !fixed[i / 3] && d != R(0)) ? R(1) / d : R(0);
     }
 }
 
-// x = 0, r = -g (active bodies), z = Dinv r, p = z (and its mesh-precision
-// copy p_lo, when given); partials of r.z and r.r
+// The CG state (x, r, p, Dinv) is held in the mesh precision R: FP64 for an
+// FP64 mesh; FP32 for an FP32 mesh, whose operator runs in FP32 anyway. The
+// Newton residual g, the step's update v += x and the chunk / body sums of
+// the dots stay in FP64; each CG solve only needs the relative tolerance
+// cg_rtol, and the Newton iteration corrects the rounding of its solution.
+
+// x = 0, r = -g (active bodies), z = Dinv r, p = z; partials of r.z and r.r
 template <typename R>
-__global__ void k_cg_init(ChunkArgs c, const double *g, const double *Dinv, const double *sc, int nb, double *x,
-                          double *r, double *z, double *p, R *p_lo, double *partials)
+__global__ void k_cg_init(ChunkArgs c, const double *g, const R *Dinv, const double *sc, int nb, R *x, R *r, R *p,
+                          double *partials)
 {
     __shared__ double sh[32];
     const int ch = blockIdx.x;
     const int b = c.body[ch];
     const bool act = sc[S_NACT * nb + b] != 0.0;
-    double rz = 0.0, rr = 0.0;
+    DotAcc<R> rz, rr;
     for (int i = c.start[ch] + threadIdx.x; i < c.end[ch]; i += blockDim.x) {
-        const double ri = act ? -g[i] : 0.0;
-        const double zi = Dinv[i] * ri;
-        x[i] = 0.0;
+        const R ri = act ? R(-g[i]) : R(0);
+        const R zi = Dinv[i] * ri;
+        x[i] = R(0);
         r[i] = ri;
-        z[i] = zi;
         p[i] = zi;
-        if (p_lo) p_lo[i] = R(zi);
-        rz += ri * zi;
-        rr += ri * ri;
+        rz.add(ri, zi);
+        rr.add(ri, ri);
     }
-    const double s1 = block_sum(rz, sh);
+    const double s1 = block_sum(rz.value(), sh);
     if (threadIdx.x == 0) partials[ch] = s1;
-    const double s2 = block_sum(rr, sh);
+    const double s2 = block_sum(rr.value(), sh);
     if (threadIdx.x == 0) partials[c.n_chunks + ch] = s2;
 }
 
@@ -259,19 +293,30 @@ __global__ void k_cg_init_finish(int nb, const int32_t *boff, const double *part
     }
 }
 
-// partial of p.Ap, Ap the operator product in the mesh precision with the
-// clamped DOFs zero (k_cg_xr forms the same values again)
+// partial of p.Ap, Ap the operator product with the clamped DOFs zero
+// (k_cg_xr forms the same values again). Each thread loads UNR DOFs before
+// it uses them; its sum runs over its DOFs in plain strided order.
 template <typename R>
-__global__ void k_cg_pap(ChunkArgs c, const R *Ap_lo, const uint8_t *fixed, const double *p, double *partials)
+__global__ void k_cg_pap(ChunkArgs c, const R *__restrict__ Ap, const uint8_t *__restrict__ fixed,
+                         const R *__restrict__ p, double *partials)
 {
     __shared__ double sh[32];
     const int ch = blockIdx.x;
-    double acc = 0.0;
-    for (int i = c.start[ch] + threadIdx.x; i < c.end[ch]; i += blockDim.x) {
-        const double a = fixed[i / 3] ? 0.0 : double(Ap_lo[i]);
-        acc += p[i] * a;
+    const int i1 = c.end[ch];
+    DotAcc<R> acc;
+    for (int i0 = c.start[ch] + threadIdx.x; i0 < i1; i0 += UNR * RT) {
+        R a[UNR], q[UNR];
+#pragma unroll
+        for (int k = 0; k < UNR; ++k) {
+            const int i = i0 + k * RT;
+            const bool in = i < i1;
+            a[k] = in && !fixed[i / 3] ? Ap[i] : R(0);
+            q[k] = in ? p[i] : R(0);
+        }
+#pragma unroll
+        for (int k = 0; k < UNR; ++k) acc.add(q[k], a[k]);
     }
-    const double s = block_sum(acc, sh);
+    const double s = block_sum(acc.value(), sh);
     if (threadIdx.x == 0) partials[ch] = s;
 }
 
@@ -286,31 +331,49 @@ __global__ void k_cg_alpha(int nb, const int32_t *boff, const double *partials, 
     }
 }
 
-// x += alpha p, r -= alpha Ap, z = Dinv r; partials of r.r and r.z. Ap is
-// read in the mesh precision with the clamped DOFs zeroed, as in k_cg_pap.
+// x += alpha p, r -= alpha Ap; partials of r.r and r.z with z = Dinv r (z is
+// not stored: k_cg_p forms it again). Ap with the clamped DOFs zeroed, as in
+// k_cg_pap.
 template <typename R>
-__global__ void k_cg_xr(ChunkArgs c, const double *sc, int nb, const double *p, const R *Ap_lo,
-                        const uint8_t *fixed, const double *Dinv, double *x, double *r, double *z, double *partials)
+__global__ void k_cg_xr(ChunkArgs c, const double *sc, int nb, const R *__restrict__ p, const R *__restrict__ Ap,
+                        const uint8_t *__restrict__ fixed, const R *__restrict__ Dinv, R *__restrict__ x,
+                        R *__restrict__ r, double *partials)
 {
     __shared__ double sh[32];
     const int ch = blockIdx.x;
     const int b = c.body[ch];
-    const double alpha = sc[S_ALPHA * nb + b];
-    double rr = 0.0, rz = 0.0;
-    for (int i = c.start[ch] + threadIdx.x; i < c.end[ch]; i += blockDim.x) {
-        const double api = fixed[i / 3] ? 0.0 : double(Ap_lo[i]);
-        const double xi = x[i] + alpha * p[i];
-        const double ri = r[i] - alpha * api;
-        const double zi = Dinv[i] * ri;
-        x[i] = xi;
-        r[i] = ri;
-        z[i] = zi;
-        rr += ri * ri;
-        rz += ri * zi;
+    const int i1 = c.end[ch];
+    const R alpha = R(sc[S_ALPHA * nb + b]);
+    DotAcc<R> rr, rz;
+    for (int i0 = c.start[ch] + threadIdx.x; i0 < i1; i0 += UNR * RT) {
+        R api[UNR], pi[UNR], xi[UNR], ri[UNR], di[UNR];
+#pragma unroll
+        for (int k = 0; k < UNR; ++k) {
+            const int i = i0 + k * RT;
+            const bool in = i < i1;
+            api[k] = in && !fixed[i / 3] ? Ap[i] : R(0);
+            pi[k] = in ? p[i] : R(0);
+            xi[k] = in ? x[i] : R(0);
+            ri[k] = in ? r[i] : R(0);
+            di[k] = in ? Dinv[i] : R(0);
+        }
+#pragma unroll
+        for (int k = 0; k < UNR; ++k) {
+            const int i = i0 + k * RT;
+            const R xn = xi[k] + alpha * pi[k];
+            const R rn = ri[k] - alpha * api[k];
+            const R zn = di[k] * rn;
+            if (i < i1) {
+                x[i] = xn;
+                r[i] = rn;
+            }
+            rr.add(rn, rn);
+            rz.add(rn, zn);
+        }
     }
-    const double s1 = block_sum(rr, sh);
+    const double s1 = block_sum(rr.value(), sh);
     if (threadIdx.x == 0) partials[ch] = s1;
-    const double s2 = block_sum(rz, sh);
+    const double s2 = block_sum(rz.value(), sh);
     if (threadIdx.x == 0) partials[c.n_chunks + ch] = s2;
 }
 
@@ -346,29 +409,42 @@ __global__ void k_cg_beta(int nb, const int32_t *boff, const double *partials, i
     }
 }
 
-// p = z + beta p on CG-active bodies, and its mesh-precision copy p_lo when
-// given (the operator's input; unchanged bodies keep theirs)
+// p = z + beta p with z = Dinv r, on CG-active bodies (unchanged bodies keep
+// theirs); p is the operator's next input
 template <typename R>
-__global__ void k_cg_p(ChunkArgs c, const double *sc, int nb, const double *z, double *p, R *p_lo)
+__global__ void k_cg_p(ChunkArgs c, const double *sc, int nb, const R *__restrict__ r, const R *__restrict__ Dinv,
+                       R *__restrict__ p)
 {
     const int ch = blockIdx.x;
     const int b = c.body[ch];
     if (sc[S_CACT * nb + b] == 0.0) return;
-    const double beta = sc[S_BETA * nb + b];
-    for (int i = c.start[ch] + threadIdx.x; i < c.end[ch]; i += blockDim.x) {
-        const double pi = z[i] + beta * p[i];
-        p[i] = pi;
-        if (p_lo) p_lo[i] = R(pi);
+    const R beta = R(sc[S_BETA * nb + b]);
+    const int i1 = c.end[ch];
+    for (int i0 = c.start[ch] + threadIdx.x; i0 < i1; i0 += UNR * RT) {
+        R zi[UNR], pi[UNR];
+#pragma unroll
+        for (int k = 0; k < UNR; ++k) {
+            const int i = i0 + k * RT;
+            const bool in = i < i1;
+            zi[k] = in ? Dinv[i] * r[i] : R(0);
+            pi[k] = in ? p[i] : R(0);
+        }
+#pragma unroll
+        for (int k = 0; k < UNR; ++k) {
+            const int i = i0 + k * RT;
+            if (i < i1) p[i] = zi[k] + beta * pi[k];
+        }
     }
 }
 
-// v += x on Newton-active bodies (x is zero elsewhere); count the iteration
-__global__ void k_v_update(ChunkArgs c, const double *sc, int nb, const double *x, double *v)
+// v += x on Newton-active bodies (x is zero elsewhere)
+template <typename R>
+__global__ void k_v_update(ChunkArgs c, const double *sc, int nb, const R *x, double *v)
 {
     const int ch = blockIdx.x;
     const int b = c.body[ch];
     if (sc[S_NACT * nb + b] == 0.0) return;
-    for (int i = c.start[ch] + threadIdx.x; i < c.end[ch]; i += blockDim.x) v[i] += x[i];
+    for (int i = c.start[ch] + threadIdx.x; i < c.end[ch]; i += blockDim.x) v[i] += double(x[i]);
 }
 
 __global__ void k_newton_count(int nb, double *sc, int *it)
@@ -495,10 +571,16 @@ static tlfe_status setup_newton(tlfe_mesh *m, cudaStream_t s, int coupled)
     NA(ns->chunk_end, ns->n_chunks);
     NA(ns->chunk_body, ns->n_chunks);
     NA(ns->body_chunk_off, ns->nb + 1);
-    for (double **q : {&ns->u_n, &ns->v_n, &ns->v, &ns->u_cur, &ns->dv, &ns->g, &ns->fff, &ns->fgrav, &ns->y1, &ns->y2, &ns->x,
-                       &ns->r, &ns->z, &ns->p, &ns->Dinv, &ns->gv, &ns->Dd})
+    for (double **q : {&ns->u_n, &ns->v_n, &ns->v, &ns->u_cur, &ns->dv, &ns->g, &ns->fff, &ns->fgrav, &ns->y1, &ns->y2,
+                       &ns->gv, &ns->Dd})
         NA(*q, N3);
     for (float **q : {&ns->ud32, &ns->p32, &ns->Ap32, &ns->D32}) NA(*q, N3);
+    // the CG state in the mesh precision
+    if (m->precision == TLFE_FP32) {
+        for (float **q : {&ns->x32, &ns->r32, &ns->Dinv32}) NA(*q, N3);
+    } else {
+        for (double **q : {&ns->x, &ns->r, &ns->p, &ns->Dinv}) NA(*q, N3);
+    }
     NA(ns->fixed, (size_t)N);
     NA(ns->partials, 2 * (size_t)ns->n_chunks);
     NA(ns->sc, (size_t)S_COUNT * ns->nb);
@@ -611,7 +693,7 @@ static tlfe_status enq_cg_init(const StepCtx &x, cudaStream_t s)
         if (st != TLFE_OK) return st;
         if (ns->n_cons > 0)
             NCK(con_diag<float>(ns->n_cons, ns->con_sh, ns->con_nd, ns->con_gp, h * h * ns->rho, ns->D32, s));
-        k_dinv<float><<<nc, RT, 0, s>>>(x.c, ns->D32, ns->fixed, ns->sc, ns->nb, ns->Dinv);
+        k_dinv<float><<<nc, RT, 0, s>>>(x.c, ns->D32, ns->fixed, ns->sc, ns->nb, ns->Dinv32);
     } else {
         st = run_op<OP_DIAG, double>(x.m, ns->u_cur, ns->v, nullptr, ns->Dd, nullptr, nullptr, 1.0 / h, h, 1.0, 1, s);
         if (st != TLFE_OK) return st;
@@ -620,11 +702,10 @@ static tlfe_status enq_cg_init(const StepCtx &x, cudaStream_t s)
         k_dinv<double><<<nc, RT, 0, s>>>(x.c, ns->Dd, ns->fixed, ns->sc, ns->nb, ns->Dinv);
     }
     if (x.m->precision == TLFE_FP32)
-        k_cg_init<float><<<nc, RT, 0, s>>>(x.c, ns->g, ns->Dinv, ns->sc, ns->nb, ns->x, ns->r, ns->z, ns->p, ns->p32,
+        k_cg_init<float><<<nc, RT, 0, s>>>(x.c, ns->g, ns->Dinv32, ns->sc, ns->nb, ns->x32, ns->r32, ns->p32,
                                            ns->partials);
     else
-        k_cg_init<double><<<nc, RT, 0, s>>>(x.c, ns->g, ns->Dinv, ns->sc, ns->nb, ns->x, ns->r, ns->z, ns->p, nullptr,
-                                            ns->partials);
+        k_cg_init<double><<<nc, RT, 0, s>>>(x.c, ns->g, ns->Dinv, ns->sc, ns->nb, ns->x, ns->r, ns->p, ns->partials);
     k_cg_init_finish<<<1, 1024, 0, s>>>(ns->nb, ns->body_chunk_off, ns->partials, nc, ns->sc, ns->it, ns->max_cg,
                                          ns->hC, x.use_handle);
     NCK(cudaGetLastError());
@@ -637,37 +718,37 @@ static tlfe_status enq_cg_iter(const StepCtx &x, cudaStream_t s)
     const int nc = ns->n_chunks;
     const double h = ns->h;
     tlfe_status st;
-    if (x.m->precision == TLFE_FP32) {  // p32 = p in FP32, kept by k_cg_init / k_cg_p
+    if (x.m->precision == TLFE_FP32) {  // p32: the FP32 search direction, kept by k_cg_init / k_cg_p
         st = run_op<OP_MATVEC, float>(x.m, ns->u_cur, ns->ud32, ns->p32, ns->Ap32, nullptr, nullptr, 1.0 / h, h, 1.0,
                                       1, s);
         if (st != TLFE_OK) return st;
         if (ns->n_cons > 0) {  // + h^2 rho C_q^T C_q p (Gauss-Newton)
-            NCK(con_j(ns->n_cons, ns->con_sh, ns->con_nd, ns->con_gp, ns->p, ns->con_w, s));
+            NCK(con_j<float>(ns->n_cons, ns->con_sh, ns->con_nd, ns->con_gp, ns->p32, ns->con_w, s));
             NCK(con_jt<float>(ns->n_cons, ns->con_sh, ns->con_nd, ns->con_gp, ns->con_w, h * h * ns->rho, ns->Ap32, s));
         }
-        k_cg_pap<float><<<nc, RT, 0, s>>>(x.c, ns->Ap32, ns->fixed, ns->p, ns->partials);
+        k_cg_pap<float><<<nc, RT, 0, s>>>(x.c, ns->Ap32, ns->fixed, ns->p32, ns->partials);
     } else {
         st = run_op<OP_MATVEC, double>(x.m, ns->u_cur, ns->v, ns->p, ns->y1, nullptr, nullptr, 1.0 / h, h, 1.0, 1, s);
         if (st != TLFE_OK) return st;
         if (ns->n_cons > 0) {
-            NCK(con_j(ns->n_cons, ns->con_sh, ns->con_nd, ns->con_gp, ns->p, ns->con_w, s));
+            NCK(con_j<double>(ns->n_cons, ns->con_sh, ns->con_nd, ns->con_gp, ns->p, ns->con_w, s));
             NCK(con_jt<double>(ns->n_cons, ns->con_sh, ns->con_nd, ns->con_gp, ns->con_w, h * h * ns->rho, ns->y1, s));
         }
         k_cg_pap<double><<<nc, RT, 0, s>>>(x.c, ns->y1, ns->fixed, ns->p, ns->partials);
     }
     k_cg_alpha<<<1, 1024, 0, s>>>(ns->nb, ns->body_chunk_off, ns->partials, ns->sc);
     if (x.m->precision == TLFE_FP32)
-        k_cg_xr<float><<<nc, RT, 0, s>>>(x.c, ns->sc, ns->nb, ns->p, ns->Ap32, ns->fixed, ns->Dinv, ns->x, ns->r, ns->z,
-                                         ns->partials);
+        k_cg_xr<float><<<nc, RT, 0, s>>>(x.c, ns->sc, ns->nb, ns->p32, ns->Ap32, ns->fixed, ns->Dinv32, ns->x32,
+                                         ns->r32, ns->partials);
     else
-        k_cg_xr<double><<<nc, RT, 0, s>>>(x.c, ns->sc, ns->nb, ns->p, ns->y1, ns->fixed, ns->Dinv, ns->x, ns->r, ns->z,
+        k_cg_xr<double><<<nc, RT, 0, s>>>(x.c, ns->sc, ns->nb, ns->p, ns->y1, ns->fixed, ns->Dinv, ns->x, ns->r,
                                           ns->partials);
     k_cg_beta<<<1, 1024, 0, s>>>(ns->nb, ns->body_chunk_off, ns->partials, nc, ns->sc, ns->it, ns->crtol, ns->max_cg,
                                   ns->hC, x.use_handle);
     if (x.m->precision == TLFE_FP32)
-        k_cg_p<float><<<nc, RT, 0, s>>>(x.c, ns->sc, ns->nb, ns->z, ns->p, ns->p32);
+        k_cg_p<float><<<nc, RT, 0, s>>>(x.c, ns->sc, ns->nb, ns->r32, ns->Dinv32, ns->p32);
     else
-        k_cg_p<double><<<nc, RT, 0, s>>>(x.c, ns->sc, ns->nb, ns->z, ns->p, nullptr);
+        k_cg_p<double><<<nc, RT, 0, s>>>(x.c, ns->sc, ns->nb, ns->r, ns->Dinv, ns->p);
     NCK(cudaGetLastError());
     return TLFE_OK;
 }
@@ -675,7 +756,10 @@ static tlfe_status enq_cg_iter(const StepCtx &x, cudaStream_t s)
 static tlfe_status enq_newton_tail(const StepCtx &x, cudaStream_t s)
 {
     NewtonState *ns = x.ns;
-    k_v_update<<<ns->n_chunks, RT, 0, s>>>(x.c, ns->sc, ns->nb, ns->x, ns->v);
+    if (x.m->precision == TLFE_FP32)
+        k_v_update<float><<<ns->n_chunks, RT, 0, s>>>(x.c, ns->sc, ns->nb, ns->x32, ns->v);
+    else
+        k_v_update<double><<<ns->n_chunks, RT, 0, s>>>(x.c, ns->sc, ns->nb, ns->x, ns->v);
     k_newton_count<<<1, 1024, 0, s>>>(ns->nb, ns->sc, ns->it);
     NCK(cudaGetLastError());
     return enq_residual(x, s, false);

@@ -155,7 +155,8 @@ cudaError_t con_row_weights(int n, const tlfe_constraint *cons, const double *sh
 template <typename R>
 cudaError_t con_jt(int n, const double *sh, const int32_t *nd, const double *gp, const double *w, double scale, R *f,
                    cudaStream_t s);
-cudaError_t con_j(int n, const double *sh, const int32_t *nd, const double *gp, const double *v, double *out,
+template <typename V>
+cudaError_t con_j(int n, const double *sh, const int32_t *nd, const double *gp, const V *v, double *out,
                   cudaStream_t s);
 template <typename R>
 cudaError_t con_diag(int n, const double *sh, const int32_t *nd, const double *gp, double alpha, R *D, cudaStream_t s);
