@@ -112,6 +112,20 @@ __device__ __forceinline__ double block_sum(double v, double *sh)
     return s;  // valid in thread 0
 }
 
+// Sum of the chunk partials k0 <= k < k1 of one body by one warp: lane l adds
+// partials k0 + l, k0 + l + 32, ... in that order, then a fixed butterfly
+// combines the lanes; every lane returns the same value, and the order does
+// not depend on anything but k0 and k1 (deterministic).
+__device__ __forceinline__ double warp_body_sum(const double *partials, int k0, int k1)
+{
+    const int l = threadIdx.x & 31;
+    double s = 0.0;
+    for (int k = k0 + l; k < k1; k += 32) s += partials[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
 struct ChunkArgs {
     const int32_t *start, *end, *body;
     int n_chunks;
@@ -168,10 +182,10 @@ __global__ void k_newton_check(int nb, const int32_t *boff, const double *partia
                                double *g0keep, int low_first)
 {
     int any = 0;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-        double s = 0.0;
-        for (int k = boff[b]; k < boff[b + 1]; ++k) s += partials[k];
-        const double gn = sqrt(s);
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int b = threadIdx.x >> 5; b < nb; b += nw) {  // one warp per body
+        const double gn = sqrt(warp_body_sum(partials, boff[b], boff[b + 1]));
+        if (lane != 0) continue;
         if (it[I_NEWTON] == 0) {
             if (alm[0]) {
                 sc[S_G0 * nb + b] = g0keep[b];
@@ -271,12 +285,11 @@ __global__ void k_cg_init_finish(int nb, const int32_t *boff, const double *part
                                  int *it, int max_cg, cudaGraphConditionalHandle hC, int use_handle)
 {
     int any = 0;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-        double rz = 0.0, rr = 0.0;
-        for (int k = boff[b]; k < boff[b + 1]; ++k) {
-            rz += partials[k];
-            rr += partials[n_chunks + k];
-        }
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int b = threadIdx.x >> 5; b < nb; b += nw) {  // one warp per body
+        const double rz = warp_body_sum(partials, boff[b], boff[b + 1]);
+        const double rr = warp_body_sum(partials + n_chunks, boff[b], boff[b + 1]);
+        if (lane != 0) continue;
         const double r0 = sqrt(rr);
         sc[S_RZ * nb + b] = rz;
         sc[S_R0 * nb + b] = r0;
@@ -322,9 +335,10 @@ __global__ void k_cg_pap(ChunkArgs c, const R *__restrict__ Ap, const uint8_t *_
 
 __global__ void k_cg_alpha(int nb, const int32_t *boff, const double *partials, double *sc)
 {
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-        double pap = 0.0;
-        for (int k = boff[b]; k < boff[b + 1]; ++k) pap += partials[k];
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int b = threadIdx.x >> 5; b < nb; b += nw) {  // one warp per body
+        const double pap = warp_body_sum(partials, boff[b], boff[b + 1]);
+        if (lane != 0) continue;
         const bool act = sc[S_CACT * nb + b] != 0.0 && pap > 0.0;
         if (sc[S_CACT * nb + b] != 0.0 && !(pap > 0.0)) sc[S_CACT * nb + b] = 0.0;  // not SPD here: stop this body
         sc[S_ALPHA * nb + b] = act ? sc[S_RZ * nb + b] / pap : 0.0;
@@ -382,12 +396,11 @@ __global__ void k_cg_beta(int nb, const int32_t *boff, const double *partials, i
 {
     int any = 0;
     const int itn = it[I_CG] + 1;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-        double rr = 0.0, rz = 0.0;
-        for (int k = boff[b]; k < boff[b + 1]; ++k) {
-            rr += partials[k];
-            rz += partials[n_chunks + k];
-        }
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int b = threadIdx.x >> 5; b < nb; b += nw) {  // one warp per body
+        const double rr = warp_body_sum(partials, boff[b], boff[b + 1]);
+        const double rz = warp_body_sum(partials + n_chunks, boff[b], boff[b + 1]);
+        if (lane != 0) continue;
         const double rn = sqrt(rr);
         int act = sc[S_CACT * nb + b] != 0.0 ? 1 : 0;
         if (act) {
@@ -870,10 +883,9 @@ __global__ void k_sq_partials(ChunkArgs c, const double *x, double *partials)
 
 __global__ void k_body_norms(int nb, const int32_t *boff, const double *partials, double *out)
 {
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-        double s = 0.0;
-        for (int k = boff[b]; k < boff[b + 1]; ++k) s += partials[k];
-        out[b] = sqrt(s);
+    for (int b = threadIdx.x >> 5; b < nb; b += blockDim.x >> 5) {  // one warp per body
+        const double s = warp_body_sum(partials, boff[b], boff[b + 1]);
+        if ((threadIdx.x & 31) == 0) out[b] = sqrt(s);
     }
 }
 
