@@ -907,7 +907,9 @@ def run_newton(args, rank, world):
     line.update({
         "batched": {"ms_per_step": ms, "newton_iters": rep["newton_iters"], "cg_iters": rep["cg_iters"],
                     "rel_residual": rep["rel_residual"], "bodies_converged": rep["n_bodies_converged"],
-                    "status": rep["status"], "precision": "FP32 element kernels, FP64 residual/dots/update",
+                    "status": rep["status"],
+                    "precision": "FP32 element kernels and CG vectors (dots: double-float per thread, FP64 per "
+                                 "chunk and body), FP64 residual and update",
                     "graph": True},
         "plain_fp64": {"ms_per_step": ms_plain, "host_wall_ms": wall_plain,
                        "newton_iters_max": max(r["newton_iters"] for r in preps),
