@@ -98,7 +98,7 @@ enum { TLFE_PATH_AUTO = 0, TLFE_PATH_SLAB = 1, TLFE_PATH_AFFINE = 2 };
  *                       ascending id, so that the gather and scatter touch
  *                       the same memory sectors per warp instruction (default)
  *   TLFE_PATCH_SORTED : nodes in ascending id
- * On the T10 beam a quarter-warp patch load takes 1.03 shared-memory passes
+ * On the T10 beam a quarter-warp patch load takes 1.04 shared-memory passes
  * banked and 1.88 sorted (tlfe_mesh_info.patch_passes). */
 enum { TLFE_PATCH_BANKED = 0, TLFE_PATCH_SORTED = 1 };
 /* How the element passes of one operation are launched (a property of this

@@ -345,19 +345,20 @@ static int64_t patch_tile_passes(int npe, const uint16_t *li, const bool *valid,
 // Patch slots of a tile's U unique nodes (TLFE_PATCH_BANKED): nodes read
 // together by a quarter warp (see patch_tile_passes) get distinct slots mod 8.
 // The gather and the scatter walk the list 32 entries per warp instruction,
-// so each run of 32 consecutive nodes in ascending id keeps its 32 entries
-// (its nodes only change places inside the run): the warp's global accesses
-// touch the same sectors as in ascending order. Inside that limit this
-// colours the conflict graph with the 8 residues: nodes by decreasing
-// conflict count, each onto the residue its already placed neighbours use
-// least among those its run still has room for (ceil(n / 8) per residue for
-// a run of n nodes; ties: the least used, then the lowest residue); then,
-// while some node gains, a move to a residue with room or a swap with a
-// node of another residue in its run. Node k of run j gets slot 32 j + 8 r +
-// c, c its residue and r its rank among the run's nodes of that residue; the
-// last run may leave holes. `pos` holds [npe][32] indices into the sorted
-// list; returns the slot count S.
-static int patch_slots(int U, int npe, const uint16_t *pos, const bool *valid, std::vector<uint16_t> &slot)
+// so each run of 32 consecutive nodes in ascending id keeps its entries (its
+// nodes only change places inside the run): the warp's global accesses touch
+// the same sectors as in ascending order. A run of n nodes owns the slots
+// 32 j .. 32 j + n - 1, of which those with residue c (mod 8) number
+// (n - c + 7) / 8 for c < n; inside that limit this colours the conflict
+// graph with the 8 residues: nodes by decreasing conflict count, each onto
+// the residue its already placed neighbours use least among those its run
+// still has slots of (ties: the most free slots, then the lowest residue);
+// then, while some node gains, a move to a residue with a free slot or a
+// swap with a node of another residue in its run. Node k of run j gets slot
+// 32 j + 8 r + c, c its residue and r its rank among the run's nodes of that
+// residue: a permutation of 0 .. U - 1 (no holes). `pos` holds [npe][32]
+// indices into the sorted list.
+static void patch_slots(int U, int npe, const uint16_t *pos, const bool *valid, std::vector<uint16_t> &slot)
 {
     // the loads: distinct nodes of each (i, quarter)
     static thread_local std::vector<int> gk, deg, adj, fill, col, order, cnt, cap;
@@ -390,11 +391,14 @@ static int patch_slots(int U, int npe, const uint16_t *pos, const bool *valid, s
             for (int b = 0; b < G[0]; ++b)
                 if (a != b) adj[fill[G[1 + a]]++] = G[1 + b];
     }
-    // runs of 32 and their room per residue
+    // runs of 32 and their slots per residue
     const int n_runs = (U + 31) / 32;
     cnt.assign((size_t)n_runs * 8, 0);
-    cap.resize(n_runs);
-    for (int j = 0; j < n_runs; ++j) cap[j] = (std::min(32, U - 32 * j) + 7) / 8;
+    cap.resize((size_t)n_runs * 8);
+    for (int j = 0; j < n_runs; ++j) {
+        const int n = std::min(32, U - 32 * j);
+        for (int c = 0; c < 8; ++c) cap[(size_t)j * 8 + c] = c < n ? (n - c + 7) / 8 : 0;
+    }
     col.assign(U, -1);
     order.resize(U);
     std::iota(order.begin(), order.end(), 0);
@@ -408,10 +412,11 @@ static int patch_slots(int U, int npe, const uint16_t *pos, const bool *valid, s
     for (int a : order) {
         int c8[8], best = -1;
         const int *n8 = cnt.data() + (size_t)(a / 32) * 8;
+        const int *k8 = cap.data() + (size_t)(a / 32) * 8;
         conflicts(a, c8);
         for (int c = 0; c < 8; ++c) {
-            if (n8[c] >= cap[a / 32]) continue;
-            if (best < 0 || c8[c] < c8[best] || (c8[c] == c8[best] && n8[c] < n8[best])) best = c;
+            if (n8[c] >= k8[c]) continue;
+            if (best < 0 || c8[c] < c8[best] || (c8[c] == c8[best] && k8[c] - n8[c] > k8[best] - n8[best])) best = c;
         }
         col[a] = best;
         ++cnt[(size_t)(a / 32) * 8 + best];
@@ -424,9 +429,10 @@ static int patch_slots(int U, int npe, const uint16_t *pos, const bool *valid, s
             const int ca = col[a], j = a / 32;
             if (c8[ca] == 0) continue;
             int *n8 = cnt.data() + (size_t)j * 8;
+            const int *k8 = cap.data() + (size_t)j * 8;
             int best = ca;
             for (int c = 0; c < 8; ++c)
-                if (c != ca && n8[c] < cap[j] && c8[c] < c8[best]) best = c;
+                if (c != ca && n8[c] < k8[c] && c8[c] < c8[best]) best = c;
             if (best != ca) {
                 --n8[ca];
                 ++n8[best];
@@ -457,15 +463,11 @@ static int patch_slots(int U, int npe, const uint16_t *pos, const bool *valid, s
         if (!changed) break;
     }
     slot.assign(U, 0);
-    int S = 0;
     for (int j = 0; j < n_runs; ++j) {
         int rank[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        for (int a = 32 * j; a < std::min(U, 32 * j + 32); ++a) {
+        for (int a = 32 * j; a < std::min(U, 32 * j + 32); ++a)
             slot[a] = (uint16_t)(32 * j + 8 * rank[col[a]]++ + col[a]);
-            S = std::max(S, slot[a] + 1);
-        }
     }
-    return S;
 }
 
 static tlfe_status build_block(tlfe_mesh *m, const tlfe_mesh_desc *d, int bi, int elem_base, cudaStream_t s)
@@ -519,10 +521,10 @@ static tlfe_status build_block(tlfe_mesh *m, const tlfe_mesh_desc *d, int bi, in
     B.n_tiles = (int)(eid.size() / TILE);
 
     // per tile: its node list (the unique nodes, in ascending id or, in the
-    // banked patch layout, at their patch slots with holes of -1 between),
-    // (element, node) -> list index, and for each slot i*32 + lane its
-    // position in the node-grouped order (the positions of list entry kk are
-    // [soff[kk], soff[kk + 1]), empty for a hole). Tiles are independent:
+    // banked patch layout, permuted to their patch slots), (element, node) ->
+    // list index, and for each slot i*32 + lane its position in the
+    // node-grouped order (the positions of list entry kk are [soff[kk],
+    // soff[kk + 1])). Tiles are independent:
     // batches of them are built on the host's cores, then appended in order.
     std::vector<int32_t> toff(B.n_tiles + 1, 0), tnodes;
     std::vector<uint16_t> lidx((size_t)B.n_tiles * npe * TILE, 0);
@@ -561,11 +563,12 @@ static tlfe_status build_block(tlfe_mesh *m, const tlfe_mesh_desc *d, int bi, in
                 lt[i * TILE + l] = (uint16_t)(std::lower_bound(tmp.begin(), tmp.end(), nd) - tmp.begin());
             }
         }
-        // the banked layout moves node k of the sorted list to slot[k]
+        // the banked layout moves node k of the sorted list to slot[k] (a
+        // permutation of the list)
         if (banked && !tmp.empty()) {
-            const int S = patch_slots((int)tmp.size(), npe, lt, valid, slot);
+            patch_slots((int)tmp.size(), npe, lt, valid, slot);
             for (int k = 0; k < npe * TILE; ++k) lt[k] = valid[k % TILE] ? slot[lt[k]] : slot[0];
-            ulist.assign(S, -1);
+            ulist.resize(tmp.size());
             for (size_t k = 0; k < tmp.size(); ++k) ulist[slot[k]] = tmp[k];
             tmp.swap(ulist);
         }

@@ -21,10 +21,9 @@
 //     creation) are gathered into a shared-memory patch, one record per list
 //     entry, with consecutive lanes on consecutive entries; each lane then
 //     reads its element's nodes from the patch through precomputed local
-//     indices. The list places the nodes so that the 8 lanes of a quarter
+//     indices. The list orders the nodes so that the 8 lanes of a quarter
 //     warp, which read the same element-local node of their elements in one
-//     16-byte load, hit distinct bank groups (holes of -1 fill the unused
-//     entries; they are never read);
+//     16-byte load, hit distinct bank groups;
 //   - each lane evaluates F = I + sum_i u_i h_i^T per quadrature point and the
 //     stress, its directional derivative, its adjoint or the diagonal moduli,
 //     accumulating its element vector sum_q w_q J_p (.) h_iq in registers;
@@ -380,7 +379,6 @@ __device__ __forceinline__ bool elem_tiles(const KParams<R> &p, unsigned char *w
         // split the FP64 displacement in place into its (hi, lo) pair (both
         // take the same 24 bytes of the record)
         for (int kk = lane; kk < U; kk += 32) {
-            if (nodes[kk] < 0) continue;  // a hole of the banked layout
             const int64_t n = bounds_clamp(nodes[kk], p.n_nodes, p.status);
             R *rec = work + (size_t)kk * REC;
 #pragma unroll
@@ -409,7 +407,6 @@ __device__ __forceinline__ bool elem_tiles(const KParams<R> &p, unsigned char *w
         cp_async_wait<0>();
         if constexpr (PK) {
             for (int kk = lane; kk < U; kk += 32) {
-                if (nodes[kk] < 0) continue;
                 R *rec = work + (size_t)kk * REC;
                 const double2 u01 = *reinterpret_cast<const double2 *>(rec);
                 const double u2 = reinterpret_cast<const double *>(rec)[2];
@@ -520,7 +517,6 @@ __device__ __forceinline__ bool elem_tiles(const KParams<R> &p, unsigned char *w
             const int32_t *nodes_n = reinterpret_cast<const int32_t *>(Mn + 16 + 128);
             for (int kk = lane; kk < Un; kk += 32) {
                 const int64_t n = nodes_n[kk];
-                if (n < 0) continue;
                 prefetch_l2(p.u + 3 * n);
                 if (need_ud) prefetch_l2(p.ud + 3 * n);
                 if (HAS_V) prefetch_l2(p.v + 3 * n);
@@ -947,7 +943,7 @@ __device__ __forceinline__ bool elem_tiles(const KParams<R> &p, unsigned char *w
                 const int64_t P0 = reinterpret_cast<const int32_t *>(M)[1];
                 R *dst = (fo == 0 ? p.part0 : p.part1) + P0 * 3;
                 for (int kk = lane; kk < U; kk += 32) {
-                    if (nodes[kk] < 0 || !bounds_ok(P0 + kk, p.n_part, p.status)) continue;
+                    if (!bounds_ok(P0 + kk, p.n_part, p.status)) continue;
                     R a0, a1, a2;
                     node_sum(kk, a0, a1, a2);
                     dst[kk * 3] = a0;
@@ -961,7 +957,6 @@ __device__ __forceinline__ bool elem_tiles(const KParams<R> &p, unsigned char *w
                 R *out = fo == 0 ? p.out0 : p.out1;
                 slots_in(fo);
                 for (int kk = lane; kk < U; kk += 32) {
-                    if (nodes[kk] < 0) continue;
                     const int64_t n = bounds_clamp(nodes[kk], p.n_nodes, p.status);
                     R a0, a1, a2;
                     node_sum(kk, a0, a1, a2);

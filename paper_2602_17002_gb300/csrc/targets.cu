@@ -24,8 +24,7 @@ __global__ void k_part_inverse(int n_nodes, const int64_t *__restrict__ ptr, con
 // Tile path: one thread per element slot. Walks the slot's metadata record as
 // the element kernel does: the gather reads node ids[lidx[i][lane]]; the
 // scatter writes slot (i, lane) to node-sorted position spos[i][lane], which
-// belongs to the list entry kk with soff[kk] <= position < soff[kk + 1] (a
-// hole of the banked layout owns an empty range, so kk is never one);
+// belongs to the list entry kk with soff[kk] <= position < soff[kk + 1];
 // that node's sum goes to node ids[kk] (atomic and colour modes) or to
 // partial position P + kk, whose node the transpose names (sorted mode).
 __global__ void k_tile_targets(int n_slots, int npe, const unsigned char *__restrict__ meta, int meta_bytes,

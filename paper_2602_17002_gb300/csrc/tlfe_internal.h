@@ -35,15 +35,15 @@ __host__ __device__ constexpr int op_nf(int op) { return op_in_fields(op) + (op 
 template <typename R> struct KParams {
     // block layout (AoSoA tiles of 32 elements, see create_mesh)
     int tile_begin, tile_end;
-    int umax;                   // max node-list length of a tile (shared-memory patch records)
+    int umax;                   // max unique nodes of a tile (shared-memory patch records)
     const int32_t *tnode_off;   // [n_tiles + 1] offsets into tnodes
-    const int32_t *tnodes;      // node list of each tile: unique global node ids, -1 for a hole
+    const int32_t *tnodes;      // node list of each tile: its unique global node ids, in patch order
     const uint16_t *lidx;       // [n_tiles][npe][32] index of (elem, node) into the tile's list
     // per-tile metadata records of meta_bytes each (16-byte multiple):
     //   int32 U, int32 first partial position (sorted scatter), 2 x pad |
-    //   int32 eid[32] | int32 node id[umaxp] (-1: hole) | u16 lidx[npe][32] |
+    //   int32 eid[32] | int32 node id[umaxp] | u16 lidx[npe][32] |
     //   u16 position[npe * 32] (slot i * 32 + lane -> its place in the node-grouped order) |
-    //   u16 node offsets[U + 1] into that order (padded; empty for a hole)
+    //   u16 node offsets[U + 1] into that order (padded)
     const unsigned char *meta;
     int meta_bytes, umaxp;
     const int32_t *eid;         // [n_tiles][32] global element id, -1 for padding lanes

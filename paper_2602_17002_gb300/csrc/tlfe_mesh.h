@@ -33,7 +33,7 @@ struct BlockStore {
     int model = -1;                  // elastic law shared by every element of the block, or -1
     bool visc = false;
     int uniform_body = 0;            // body id when every element shares it, else -1
-    int64_t n_unique = 0;            // sum over tiles of the patch slots (unique nodes and holes)
+    int64_t n_unique = 0;            // sum over tiles of the unique node count
     int64_t patch_loads = 0;         // quarter-warp node-patch loads of one pass over the tiles (per
     int64_t patch_passes = 0;        // element-local node) and the shared-memory passes they take
     // passes: tile range [color_tile_off[c], color_tile_off[c + 1]) of pass c,

@@ -1,8 +1,8 @@
-"""Node-patch layouts of the tile kernels: the banked layout (nodes placed so
-that a quarter warp's 16-byte patch loads hit distinct bank groups, holes
-between them) and the plain ascending layout give bit-identical results in
-the deterministic (sorted) scatter mode, on every element type and path, and
-the banked layout's patch loads take about one shared-memory pass each."""
+"""Node-patch layouts of the tile kernels: the banked layout (each tile's node
+list permuted so that a quarter warp's 16-byte patch loads hit distinct bank
+groups) and the plain ascending layout give bit-identical results in the
+deterministic (sorted) scatter mode, on every element type and path, and the
+banked layout's patch loads take about one shared-memory pass each."""
 
 import numpy as np
 import pytest
@@ -68,7 +68,7 @@ def test_banked_and_sorted_layouts_agree_bit_for_bit(name, prec, path):
 
 
 def test_banked_layout_is_conflict_free_on_the_full_beam():
-    """480k-element beam: a quarter-warp patch load takes at most 1.03
+    """480k-element beam: a quarter-warp patch load takes at most 1.05
     passes, against about 1.9 in ascending node order."""
     tl = T()
     wl = synth.cantilever_beam()
@@ -77,10 +77,10 @@ def test_banked_layout_is_conflict_free_on_the_full_beam():
         m = tl.Mesh.from_workload(wl, precision=tl.FP32, patch_layout=layout)
         info[layout] = m.info
         m.close()
-    assert info[tl.PATCH_BANKED]["patch_passes"] <= 1.03
+    assert info[tl.PATCH_BANKED]["patch_passes"] <= 1.05
     assert 1.7 < info[tl.PATCH_SORTED]["patch_passes"] < 2.1
-    # the banked lists are barely longer than the ascending ones (holes in a tile's last run only)
-    assert info[tl.PATCH_BANKED]["device_bytes"] <= info[tl.PATCH_SORTED]["device_bytes"] * 1.01
+    # the banked lists are permutations of the ascending ones: the same memory
+    assert info[tl.PATCH_BANKED]["device_bytes"] == info[tl.PATCH_SORTED]["device_bytes"]
 
 
 def test_bad_patch_layout_is_rejected():
