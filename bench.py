@@ -111,7 +111,7 @@ def alu_peaks():
     return _ALU
 
 
-def survey_bytes(wl, s=4):
+def streamed_bytes(wl, s=4):
     """Algorithmic bytes of one force / operator product / adjoint by the
     minimum-traffic count with streamed reference data: connectivity 4 n,
     reference gradients 3 n Q s and weights Q s per element (2 s more with
@@ -711,7 +711,7 @@ def run_beam(args, rank, world, workload="beam"):
     # the same kernels against HBM by the minimum-traffic byte count with
     # streamed reference gradients (what the slab path moves); the affine
     # path forms those gradients instead of reading them
-    sb = survey_bytes(wl)
+    sb = streamed_bytes(wl)
     roof["streamed_bytes"] = sb[names[j]]
     roof["streamed_hbm_frac"] = sb[names[j]] / (kern_ms[j] * 1e-3) / 1e9 / peak
     kernels_streamed_frac = {n: sb[n] / (t * 1e-3) / 1e9 / peak for n, t in zip(names, kern_ms)}
