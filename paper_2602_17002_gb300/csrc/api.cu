@@ -1173,18 +1173,46 @@ static tlfe_status run_block_op(tlfe_mesh *m, int bi, KParams<R> p, cudaStream_t
 }
 
 // sorted scatter, second half: out[n] = sum of node n's partials in ascending
-// position order (one thread per node and component: a fixed order, so the
-// result repeats bit for bit); nodes in no element get 0
+// position order, for one or two output fields at once (part1 / out1 may be
+// null). One thread per node: it reads the node's position range and
+// positions once for both fields, loads up to four partial rows before it
+// adds them, and adds in ascending position order, so the result repeats bit
+// for bit; nodes in no element get 0.
 template <typename R>
-__global__ void k_node_sum(int64_t n3, const int64_t *__restrict__ ptr, const int32_t *__restrict__ pos,
-                           const R *__restrict__ part, R *__restrict__ out)
+__global__ void k_node_sum(int64_t n_nodes, const int64_t *__restrict__ ptr, const int32_t *__restrict__ pos,
+                           const R *__restrict__ part0, R *__restrict__ out0, const R *__restrict__ part1,
+                           R *__restrict__ out1)
 {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t n = i / 3;
-        const int c = (int)(i - 3 * n);
-        R a = R(0);
-        for (int64_t k = ptr[n]; k < ptr[n + 1]; ++k) a += part[(int64_t)pos[k] * 3 + c];
-        out[i] = a;
+    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < n_nodes;
+         n += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k0 = ptr[n], k1 = ptr[n + 1];
+        R a[3] = {R(0), R(0), R(0)}, b[3] = {R(0), R(0), R(0)};
+        for (int64_t k = k0; k < k1; k += 4) {
+            int64_t q[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) q[j] = k + j < k1 ? (int64_t)pos[k + j] * 3 : -1;
+            R v[4][3], w[4][3];
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    v[j][c] = q[j] >= 0 ? part0[q[j] + c] : R(0);
+                    w[j][c] = (part1 && q[j] >= 0) ? part1[q[j] + c] : R(0);
+                }
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (q[j] >= 0)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        a[c] += v[j][c];
+                        b[c] += w[j][c];
+                    }
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) out0[3 * n + c] = a[c];
+        if (out1)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) out1[3 * n + c] = b[c];
     }
 }
 
@@ -1286,13 +1314,16 @@ tlfe_status run_op(tlfe_mesh *m, const void *u, const void *ud, const void *v, v
         if (st != TLFE_OK) return st;
     }
     if (sorted) {
-        const int64_t n3 = 3 * (int64_t)m->n_nodes;
-        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n3 + 255) / 256, (int64_t)m->n_sm * 16));
-        R *outs[2] = {(R *)out0, (R *)out1};
-        for (int fo = 0; fo < 2; ++fo) {
-            if (!outs[fo] || n3 == 0) continue;
-            k_node_sum<R><<<grid, 256, 0, s>>>(n3, m->d_part_ptr, m->d_part_pos, fo == 0 ? p.part0 : p.part1,
-                                                outs[fo]);
+        const int64_t nn = m->n_nodes;
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((nn + 255) / 256, (int64_t)m->n_sm * 16));
+        R *o0 = (R *)out0, *o1 = (R *)out1;
+        if (!o0) {  // a single field given as the second one
+            o0 = o1;
+            o1 = nullptr;
+        }
+        if (o0 && nn > 0) {
+            const R *q0 = o0 == (R *)out0 ? p.part0 : p.part1;
+            k_node_sum<R><<<grid, 256, 0, s>>>(nn, m->d_part_ptr, m->d_part_pos, q0, o0, o1 ? p.part1 : nullptr, o1);
             cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) return cuda_fail(e, "k_node_sum launch");
         }
