@@ -56,7 +56,7 @@ extern "C" {
 typedef enum {
     TLFE_OK = 0,
     TLFE_E_INVALID = 1,       /* bad argument, out-of-range connectivity, bad sizes */
-    TLFE_E_OOM = 2,           /* device allocation failed */
+    TLFE_E_OOM = 2,           /* device allocation failed (or host memory, while building a mesh) */
     TLFE_E_CUDA = 3,          /* a CUDA runtime call failed */
     TLFE_E_INVERTED = 4,      /* J_p <= 0 at creation, or J <= 0 (neo-Hookean) on the device */
     TLFE_E_NOT_CONVERGED = 5, /* Newton did not reach the tolerance within max_newton */

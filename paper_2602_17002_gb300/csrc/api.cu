@@ -9,6 +9,8 @@
 #include <cstring>
 #include <numeric>
 #include <string>
+#include <atomic>
+#include <new>
 #include <thread>
 #include <vector>
 
@@ -592,8 +594,14 @@ static tlfe_status build_block(tlfe_mesh *m, const tlfe_mesh_desc *d, int bi, in
         std::vector<TileList> out((size_t)std::min(B.n_tiles, BATCH));
         for (int t0 = 0; t0 < B.n_tiles; t0 += BATCH) {
             const int t1 = std::min(B.n_tiles, t0 + BATCH);
+            // a host allocation failing in a worker is passed on after the join
+            std::atomic<bool> failed(false);
             auto worker = [&](int w, int nw) {
-                for (int t = t0 + w; t < t1; t += nw) build_tile(t, out[t - t0]);
+                try {
+                    for (int t = t0 + w; t < t1 && !failed.load(); t += nw) build_tile(t, out[t - t0]);
+                } catch (...) {
+                    failed.store(true);
+                }
             };
             if (nthr == 1 || t1 - t0 < 256) {
                 worker(0, 1);
@@ -610,6 +618,7 @@ static tlfe_status build_block(tlfe_mesh *m, const tlfe_mesh_desc *d, int bi, in
                 for (int w : here) worker(w, nthr);
                 for (auto &th : pool) th.join();
             }
+            if (failed.load()) throw std::bad_alloc();
             for (int t = t0; t < t1; ++t) {
                 const TileList &o = out[t - t0];
                 tnodes.insert(tnodes.end(), o.nodes.begin(), o.nodes.end());
@@ -840,15 +849,36 @@ static tlfe_status build_fused_plan(tlfe_mesh *m)
     return TLFE_OK;
 }
 
+static tlfe_status create_mesh(const tlfe_mesh_desc *desc, cudaStream_t s, tlfe_mesh **out, tlfe_mesh **held);
+
+// Host allocations (the mesh's host tables, the tile lists of a large batch)
+// can fail; the exception does not cross the C ABI: the handle under
+// construction is released and TLFE_E_OOM returned.
 extern "C" tlfe_status tlfe_create_mesh(const tlfe_mesh_desc *desc, void *stream, tlfe_mesh **out)
 {
     TLFE_TRACE("tlfe_create_mesh");
     if (!out) return fail(TLFE_E_INVALID, "out is NULL");
     *out = nullptr;
+    tlfe_mesh *held = nullptr;  // the handle under construction, until create_mesh releases it itself
+    tlfe_status st;
+    try {
+        st = create_mesh(desc, (cudaStream_t)stream, out, &held);
+    } catch (const std::exception &ex) {
+        st = fail(TLFE_E_OOM, std::string("host allocation failed while building the mesh (") + ex.what() + ")");
+    }
+    if (st != TLFE_OK) {
+        if (held) tlfe_destroy_mesh(held);
+        *out = nullptr;
+    }
+    return st;
+}
+
+static tlfe_status create_mesh(const tlfe_mesh_desc *desc, cudaStream_t s, tlfe_mesh **out, tlfe_mesh **held)
+{
     tlfe_status st = validate(desc);
     if (st != TLFE_OK) return st;
-    cudaStream_t s = (cudaStream_t)stream;
     tlfe_mesh *m = new tlfe_mesh();
+    *held = m;
     CK(cudaGetDevice(&m->device));
     CK(cudaDeviceGetAttribute(&m->n_sm, cudaDevAttrMultiProcessorCount, m->device));
     m->precision = desc->precision;
@@ -878,6 +908,7 @@ extern "C" tlfe_status tlfe_create_mesh(const tlfe_mesh_desc *desc, void *stream
         if (desc->elem_mu_lambda) m->h_elam.assign(desc->elem_mu_lambda, desc->elem_mu_lambda + 2 * ne);
     }
     auto bail = [&](tlfe_status e) {
+        *held = nullptr;
         tlfe_destroy_mesh(m);
         return e;
     };
