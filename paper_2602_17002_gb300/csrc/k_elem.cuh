@@ -15,8 +15,9 @@
 //     completed on one mbarrier per slot; the affine path instead forms
 //     h_i = J^{-T} g_i from the parent gradients g_i at each point;
 //   - the nodes of the next tile are prefetched into L2, after the first
-//     quadrature point in the affine force, operator and diagonal kernels and
-//     after the last one otherwise;
+//     quadrature point in the affine force, operator and diagonal kernels,
+//     after the last one on the slab path (the affine adjoint runs faster
+//     without);
 //   - the nodal values of the tile's unique nodes (a list built at mesh
 //     creation) are gathered into a shared-memory patch, one record per list
 //     entry, with consecutive lanes on consecutive entries; each lane then
@@ -308,6 +309,7 @@ __device__ __forceinline__ bool elem_tiles(const KParams<R> &p, unsigned char *w
     using PG = ParentGrad<ET, NQ, R>;
     constexpr uint32_t AB = AFF ? AffRec<R>::BYTES : 0;
     constexpr bool PF_EARLY = AFF && OP != OP_VJP;  // where the next tile's L2 prefetch goes (see prefetch_next)
+    constexpr bool PF_NONE = AFF && OP == OP_VJP;
 
     const int lane = threadIdx.x & 31;
     const int MB = p.meta_bytes;
@@ -505,9 +507,13 @@ __device__ __forceinline__ bool elem_tiles(const KParams<R> &p, unsigned char *w
         // ---- the next tile's nodal inputs towards L2 (its metadata was
         // requested at the start of this tile); false when that metadata never
         // landed. Issued after this tile's first point on the affine path
-        // (force, operator, diagonal), else after the last: measured on the
-        // beam, the early prefetch cut the affine K v kernel by 18 % and the
-        // force by 12 %, and slowed the 255-register adjoint and the slab path.
+        // (force, operator, diagonal), after the last on the slab path, and
+        // not at all by the affine adjoint: measured on the beam, the early
+        // prefetch cut the affine K v kernel by 18 % and the force by 12 %,
+        // and slowed the slab path; the 255-register affine adjoint ran 1.2 %
+        // slower with it early, and 1.3 % faster without it than with it late,
+        // also with the L2 flushed before the launch. (The tile-start wait on
+        // the metadata barrier stands without it.)
         auto prefetch_next = [&]() -> bool {
             if (k + 1 >= n_my) return true;
             const bool ok = mbar_wait_bounded(mbar + ((k + 1) & 1), (uint32_t)(((k + 1) >> 1) & 1));
@@ -846,7 +852,7 @@ __device__ __forceinline__ bool elem_tiles(const KParams<R> &p, unsigned char *w
         }
         if (timed_out) break;
 
-        if (!(PF_EARLY && !mass_only) && !prefetch_next()) {
+        if (!PF_NONE && !(PF_EARLY && !mass_only) && !prefetch_next()) {
             timed_out = true;
             break;
         }
