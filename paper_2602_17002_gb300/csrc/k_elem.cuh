@@ -138,6 +138,16 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float4 lds4(const float *r) { return *reinterpret_cast<const float4 *>(r); }
+// a shared-memory u16 the compiler may not keep in a register across uses
+// (volatile): the force and adjoint kernels re-read each element's local
+// node indices at every point instead of holding them, which frees the
+// registers for the point's arithmetic
+__device__ __forceinline__ int lds_u16_volatile(const uint16_t *p)
+{
+    unsigned short v;
+    asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(smem_u32(p)));
+    return (int)v;
+}
 
 constexpr int NSLICE = 2;  // ring depth per warp (quadrature-point slices)
 
@@ -269,13 +279,21 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 // Resident CTAs (of 4 warps) per SM the register allocation aims at, by
 // measurement on the beam workload: the FP32 affine force kernel fits 16
 // warps per SM in 128 registers; the adjoint, with two element vectors live,
-// runs fastest unspilled at 8 warps; FP64 kernels take all 255 registers, and
-// so do Q27 kernels (81-entry element vectors; their shared-memory footprint
-// limits the resident warps anyway).
-template <int ET, typename R, int OP, bool AFF> constexpr int min_ctas()
+// fits 12 warps in 168 registers (its local indices re-read from shared
+// memory at every point) with a spill of at most a few bytes for the laws
+// listed below, and runs 6.5 % faster there than at 8 warps and 214
+// registers; with the generic law or the undamped neo-Hookean one it would
+// spill 70-200 bytes and keeps 8 warps. FP64 kernels take all 255 registers,
+// and so do Q27 kernels (81-entry element vectors; their shared-memory
+// footprint limits the resident warps anyway).
+template <int ET, typename R, int OP, bool AFF, int MAT> constexpr int min_ctas()
 {
     if (sizeof(R) != 4 || ET == ET_Q27) return 1;
-    if (OP == OP_VJP) return 2;
+    if (OP == OP_VJP) {
+        const bool fits = ET == ET_T4 || MAT == MAT_NH_KV || MAT == MAT_SVK || (MAT == MAT_SVK_KV && AFF) ||
+                          (ET == ET_H8 && MAT != MAT_ANY);
+        return fits ? 3 : 2;
+    }
     return (OP == OP_FORCE && AFF) ? 4 : 3;
 }
 
@@ -310,6 +328,7 @@ __device__ __forceinline__ bool elem_tiles(const KParams<R> &p, unsigned char *w
     constexpr uint32_t AB = AFF ? AffRec<R>::BYTES : 0;
     constexpr bool PF_EARLY = AFF && OP != OP_VJP;  // where the next tile's L2 prefetch goes (see prefetch_next)
     constexpr bool PF_NONE = AFF && OP == OP_VJP;
+    constexpr bool LI_REREAD = OP == OP_FORCE || OP == OP_VJP;  // local indices read again at every point
 
     const int lane = threadIdx.x & 31;
     const int MB = p.meta_bytes;
@@ -574,7 +593,9 @@ __device__ __forceinline__ bool elem_tiles(const KParams<R> &p, unsigned char *w
                     R hk[3];
 #pragma unroll
                     for (int k2 = 0; k2 < 3; ++k2) hk[k2] = nz(i, k2) ? grad(i, k2) : R(0);
-                    const float *rec = work + li[i] * REC;
+                    const int lii = LI_REREAD ? (int)bounds_clamp(lds_u16_volatile(mlidx + i * 32 + lane), U, p.status)
+                                              : li[i];
+                    const float *rec = work + lii * REC;
                     float4 B = make_float4(0.f, 0.f, 0.f, 0.f);
                     if ((i > 0 && !DD_REG) || visc || HAS_V) B = lds4(rec + 4);
                     if (i > 0) {
@@ -996,7 +1017,7 @@ __device__ __forceinline__ bool elem_tiles(const KParams<R> &p, unsigned char *w
 // One element kernel per (type, quadrature, precision, op, path, material
 // mode): one launch per pass, warps persistent over the pass's tiles.
 template <int ET, int NQ, typename R, int OP, bool AFF, int MAT>
-__global__ void __launch_bounds__(128, min_ctas<ET, R, OP, AFF>()) k_elem(const KParams<R> p)
+__global__ void __launch_bounds__(128, min_ctas<ET, R, OP, AFF, MAT>()) k_elem(const KParams<R> p)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31;
