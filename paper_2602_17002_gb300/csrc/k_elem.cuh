@@ -138,10 +138,23 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float4 lds4(const float *r) { return *reinterpret_cast<const float4 *>(r); }
-// a shared-memory u16 the compiler may not keep in a register across uses
-// (volatile): the force and adjoint kernels re-read each element's local
-// node indices at every point instead of holding them, which frees the
-// registers for the point's arithmetic
+// shared-memory loads the compiler may not hoist out of the point loop and
+// keep in registers (volatile): the force and adjoint kernels re-read each
+// element's local node indices at every point, and the adjoint also its
+// J^{-1} and node 0's displacement pair, instead of holding them across the
+// loop, which frees registers for the point's arithmetic
+__device__ __forceinline__ float lds_f32_volatile(const float *p)
+{
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(smem_u32(p)));
+    return v;
+}
+__device__ __forceinline__ float4 lds4_volatile(const float *p)
+{
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(smem_u32(p)));
+    return v;
+}
 __device__ __forceinline__ int lds_u16_volatile(const uint16_t *p)
 {
     unsigned short v;
@@ -279,11 +292,11 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 // Resident CTAs (of 4 warps) per SM the register allocation aims at, by
 // measurement on the beam workload: the FP32 affine force kernel fits 16
 // warps per SM in 128 registers; the adjoint, with two element vectors live,
-// fits 12 warps in 168 registers (its local indices re-read from shared
-// memory at every point) with a spill of at most a few bytes for the laws
-// listed below, and runs 6.5 % faster there than at 8 warps and 214
-// registers; with the generic law or the undamped neo-Hookean one it would
-// spill 70-200 bytes and keeps 8 warps. FP64 kernels take all 255 registers,
+// fits 12 warps in 168 registers (its local indices, J^{-1} and node 0's
+// pair re-read from shared memory at every point) without spill or with a
+// few bytes for the laws listed below, and runs 7 % faster there than at 8
+// warps and 214 registers; with the generic law or the undamped
+// neo-Hookean one it would spill 70-200 bytes and keeps 8 warps. FP64 kernels take all 255 registers,
 // and so do Q27 kernels (81-entry element vectors; their shared-memory
 // footprint limits the resident warps anyway).
 template <int ET, typename R, int OP, bool AFF, int MAT> constexpr int min_ctas()
@@ -328,7 +341,10 @@ __device__ __forceinline__ bool elem_tiles(const KParams<R> &p, unsigned char *w
     constexpr uint32_t AB = AFF ? AffRec<R>::BYTES : 0;
     constexpr bool PF_EARLY = AFF && OP != OP_VJP;  // where the next tile's L2 prefetch goes (see prefetch_next)
     constexpr bool PF_NONE = AFF && OP == OP_VJP;
-    constexpr bool LI_REREAD = OP == OP_FORCE || OP == OP_VJP;  // local indices read again at every point
+    constexpr bool LI_REREAD = OP == OP_FORCE || OP == OP_VJP;
+    // the adjoint also re-reads J^{-1} (affine record) and node 0's pair at
+    // every point: 168 registers without spill (12 warps per SM)
+    constexpr bool DIET = OP == OP_VJP;
 
     const int lane = threadIdx.x & 31;
     const int MB = p.meta_bytes;
@@ -581,6 +597,14 @@ __device__ __forceinline__ bool elem_tiles(const KParams<R> &p, unsigned char *w
             R D[9];
             if constexpr (PK) {
                 // rows 0 and 1 of G', Fd', D' paired per column k, row 2 alone
+                if constexpr (DIET && !DD_REG) {  // node 0's negated pair, read again for this point
+                    const int l0 = (int)bounds_clamp(lds_u16_volatile(mlidx + lane), U, p.status);
+                    const float4 A0 = lds4_volatile(work + l0 * REC), B0 = lds4_volatile(work + l0 * REC + 4);
+                    nh01 = make_float2(-A0.x, -A0.y);
+                    nl01 = make_float2(-A0.z, -A0.w);
+                    nh2 = -B0.x;
+                    nl2 = -B0.y;
+                }
                 float2 Gp[3], Fp[3], Dp[3];
                 float Gs[3], Fs[3], Ds[3];
 #pragma unroll
@@ -639,12 +663,16 @@ __device__ __forceinline__ bool elem_tiles(const KParams<R> &p, unsigned char *w
 #pragma unroll
                     for (int b2 = 0; b2 < 3; ++b2) {
                         if constexpr (AFF) {
-                            float2 q2 = mul2(Xp[0], bc2(Ji[b2]));
-                            q2 = fma2(Xp[1], bc2(Ji[3 + b2]), q2);
-                            q2 = fma2(Xp[2], bc2(Ji[6 + b2]), q2);
+                            const float *Ajl = reinterpret_cast<const float *>(M + MB) + lane;
+                            const float j0 = DIET ? lds_f32_volatile(Ajl + b2 * 32) : Ji[b2];
+                            const float j3 = DIET ? lds_f32_volatile(Ajl + (3 + b2) * 32) : Ji[3 + b2];
+                            const float j6 = DIET ? lds_f32_volatile(Ajl + (6 + b2) * 32) : Ji[6 + b2];
+                            float2 q2 = mul2(Xp[0], bc2(j0));
+                            q2 = fma2(Xp[1], bc2(j3), q2);
+                            q2 = fma2(Xp[2], bc2(j6), q2);
                             X[b2] = q2.x;
                             X[3 + b2] = q2.y;
-                            X[6 + b2] = fmaf(Xs[2], Ji[6 + b2], fmaf(Xs[1], Ji[3 + b2], Xs[0] * Ji[b2]));
+                            X[6 + b2] = fmaf(Xs[2], j6, fmaf(Xs[1], j3, Xs[0] * j0));
                         } else {
                             X[b2] = Xp[b2].x;
                             X[3 + b2] = Xp[b2].y;
@@ -781,11 +809,15 @@ __device__ __forceinline__ bool elem_tiles(const KParams<R> &p, unsigned char *w
 #pragma unroll
                         for (int k2 = 0; k2 < 3; ++k2) {
                             if constexpr (AFF) {
-                                float2 q2 = mul2(make_float2(T[0], T[3]), bc2(Ji[k2 * 3]));
-                                q2 = fma2(make_float2(T[1], T[4]), bc2(Ji[k2 * 3 + 1]), q2);
-                                q2 = fma2(make_float2(T[2], T[5]), bc2(Ji[k2 * 3 + 2]), q2);
+                                const float *Ajl = reinterpret_cast<const float *>(M + MB) + lane;
+                                const float j0 = DIET ? lds_f32_volatile(Ajl + (k2 * 3) * 32) : Ji[k2 * 3];
+                                const float j1 = DIET ? lds_f32_volatile(Ajl + (k2 * 3 + 1) * 32) : Ji[k2 * 3 + 1];
+                                const float j2 = DIET ? lds_f32_volatile(Ajl + (k2 * 3 + 2) * 32) : Ji[k2 * 3 + 2];
+                                float2 q2 = mul2(make_float2(T[0], T[3]), bc2(j0));
+                                q2 = fma2(make_float2(T[1], T[4]), bc2(j1), q2);
+                                q2 = fma2(make_float2(T[2], T[5]), bc2(j2), q2);
                                 Tp[k2] = mul2(q2, bc2(w));
-                                Ts[k2] = w * fmaf(T[8], Ji[k2 * 3 + 2], fmaf(T[7], Ji[k2 * 3 + 1], T[6] * Ji[k2 * 3]));
+                                Ts[k2] = w * fmaf(T[8], j2, fmaf(T[7], j1, T[6] * j0));
                             } else {
                                 Tp[k2] = mul2(make_float2(T[k2], T[3 + k2]), bc2(w));
                                 Ts[k2] = w * T[6 + k2];
