@@ -545,10 +545,10 @@ __device__ __forceinline__ bool elem_tiles(const KParams<R> &p, unsigned char *w
         // (force, operator, diagonal), after the last on the slab path, and
         // not at all by the affine adjoint: measured on the beam, the early
         // prefetch cut the affine K v kernel by 18 % and the force by 12 %,
-        // and slowed the slab path; the 255-register affine adjoint ran 1.2 %
-        // slower with it early, and 1.3 % faster without it than with it late,
-        // also with the L2 flushed before the launch. (The tile-start wait on
-        // the metadata barrier stands without it.)
+        // and slowed the slab path; the affine adjoint runs 4-5 % faster
+        // without it than with it early or late, also with the L2 flushed
+        // before the launch. (The tile-start wait on the metadata barrier
+        // stands without it.)
         auto prefetch_next = [&]() -> bool {
             if (k + 1 >= n_my) return true;
             const bool ok = mbar_wait_bounded(mbar + ((k + 1) & 1), (uint32_t)(((k + 1) >> 1) & 1));
