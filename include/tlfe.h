@@ -532,6 +532,78 @@ tlfe_status tlfe_gather_nodes(int32_t precision, const void *x_dev, const int32_
 tlfe_status tlfe_scatter_nodes(int32_t precision, const void *in_dev, const int32_t *in_idx_dev,
                                const int32_t *idx_dev, int32_t n, void *x_dev, void *stream);
 
+/* The CG operator of the Newton step (Sec. 2.2 Newton matrix, Sec. 7; App. C
+ * tangent blocks): y = a_M M v + a_K K^e(u) v + a_C C(u) v, the symmetric
+ * part of the operator of tlfe_tangent_matvec (the viscous stiffness K^v of
+ * the Kelvin-Voigt law left out), whose diagonal tlfe_jacobi_diag returns.
+ * Arguments, layouts and errors as tlfe_tangent_matvec. */
+tlfe_status tlfe_newton_operator(tlfe_mesh *mesh, const void *u_dev, const void *udot_dev,
+                                 const void *v_dev, double a_M, double a_K, double a_C,
+                                 void *y_dev, void *stream);
+
+/* Backward-Euler step of one body split across GPUs (Sec. 7, Eqs.
+ * step_map_velocity_level and residual; the inexact Newton / Jacobi-PCG
+ * iteration of tlfe_newton_step). Each rank holds a mesh of its slab of
+ * elements and every node they touch, so interface nodes sit on two ranks.
+ * The caller drives the iteration on the host:
+ *   residual  tlfe_split_prep, then f = tlfe_internal_force(u, v) and
+ *             y = tlfe_tangent_matvec(a_M = 1/h, a_K = a_C = 0) on w, then
+ *             tlfe_split_residual; the interface rows of g summed over the
+ *             ranks; ||g||^2 = tlfe_split_dot(g, g), all-reduced
+ *   CG        D = tlfe_jacobi_diag(1/h, h, 1), interface-summed, then
+ *             tlfe_split_cg_dinv and tlfe_split_cg_start (r.z, r.r, all-reduced);
+ *             per iteration q = tlfe_newton_operator(1/h, h, 1) on p,
+ *             interface-summed, tlfe_split_cg_pq (p.q, all-reduced),
+ *             alpha = r.z / p.q, tlfe_split_cg_update (the new r.z and r.r,
+ *             all-reduced), beta = r.z(new) / r.z, tlfe_split_cg_direction
+ *   update    tlfe_split_velocity(v, add_x = 1)
+ * so that per CG iteration the ranks exchange one compact interface buffer
+ * and all-reduce three FP64 scalars. Every sum over rows counts only the rows
+ * with own[k] = 1 (each interface node is owned by exactly one rank), in FP64
+ * and in a fixed order: a chunk partial of 4096 values per CTA into work_dev,
+ * then the partials in order into dots_dev (deterministic). The caller
+ * all-reduces dots_dev and reads the sums on the host.
+ * Clamped rows (fixed[k] = 1) are projected out of g, r, z, p, q and v.
+ * x, r, p, q, dinv: device [n_rows][3] in `precision` (the operator mesh's);
+ * every other vector is device double [n_rows][3]. All pointers are
+ * caller-owned device memory; no call allocates. Stream-ordered. */
+typedef struct {
+    int32_t precision;       /* TLFE_FP32 / TLFE_FP64: dtype of x, r, p, q, dinv */
+    int32_t n_rows;          /* node rows of this rank's share (>= 0) */
+    const uint8_t *fixed;    /* device [n_rows], 1 = clamped node, or NULL (none) */
+    const uint8_t *own;      /* device [n_rows], 1 = row counted in sums, or NULL (all) */
+    void *x, *r, *p, *q, *dinv;
+    double *work;            /* device, tlfe_split_work_doubles(n_rows) doubles */
+    double *dots;            /* device double [2]: partial sums of the last call */
+} tlfe_split_cg;
+
+/* Doubles of work_dev for a share of n_rows node rows. */
+int64_t tlfe_split_work_doubles(int64_t n_rows);
+/* u_out = u_n + h v; w_out = v - v_n - h b0, b0 = gravity_host[3] (so that
+ * M/h w = M/h (v - v_n) - f_ff with f_ff = M b0, Sec. 4.2); v_op_out, when not
+ * NULL, receives v in `precision` (the operator mesh's udot). */
+tlfe_status tlfe_split_prep(const tlfe_split_cg *c, double h, const double *gravity_host,
+                            const double *u_n, const double *v_n, const double *v, double *u_out,
+                            double *w_out, void *v_op_out, void *stream);
+/* g = f + y with the clamped rows zeroed (this rank's partial residual). */
+tlfe_status tlfe_split_residual(const tlfe_split_cg *c, const double *f, const double *y, double *g,
+                                void *stream);
+/* v_out = v_base (+ x when add_x), clamped rows zeroed; v_out may be v_base. */
+tlfe_status tlfe_split_velocity(const tlfe_split_cg *c, const double *v_base, int32_t add_x,
+                                double *v_out, void *stream);
+/* dots[0] = sum over owned rows of a . b (double arrays). */
+tlfe_status tlfe_split_dot(const tlfe_split_cg *c, const double *a, const double *b, void *stream);
+/* dinv = 1 / D on free rows with D != 0, else 0 (D in `precision`). */
+tlfe_status tlfe_split_cg_dinv(const tlfe_split_cg *c, const void *D, void *stream);
+/* x = 0, r = -g (clamped rows 0), p = dinv r; dots = (r . dinv r, r . r). */
+tlfe_status tlfe_split_cg_start(const tlfe_split_cg *c, const double *g, void *stream);
+/* q: clamped rows zeroed; dots[0] = p . q. */
+tlfe_status tlfe_split_cg_pq(const tlfe_split_cg *c, void *stream);
+/* x += alpha p, r -= alpha q; dots = (r . dinv r, r . r). */
+tlfe_status tlfe_split_cg_update(const tlfe_split_cg *c, double alpha, void *stream);
+/* p = dinv r + beta p. */
+tlfe_status tlfe_split_cg_direction(const tlfe_split_cg *c, double beta, void *stream);
+
 /* Arithmetic peak probe (no counterpart in the paper; the denominator of the
  * element kernels' ALU roofline): enqueues one kernel of ctas_per_sm CTAs of
  * 256 threads per SM in which every thread runs 16 independent fused

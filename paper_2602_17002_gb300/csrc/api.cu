@@ -1599,6 +1599,20 @@ extern "C" tlfe_status tlfe_tangent_matvec(tlfe_mesh *m, const void *u, const vo
                : run_op<OP_MATVEC, double>(m, u, ud, v, y, nullptr, nullptr, aM, aK, aC, 0, s);
 }
 
+extern "C" tlfe_status tlfe_newton_operator(tlfe_mesh *m, const void *u, const void *ud, const void *v, double aM,
+                                            double aK, double aC, void *y, void *stream)
+{
+    TLFE_TRACE("tlfe_newton_operator");
+    tlfe_status st = check_mesh_args(m, {u, v, y});
+    if (st != TLFE_OK) return st;
+    if (!std::isfinite(aM) || !std::isfinite(aK) || !std::isfinite(aC)) return fail(TLFE_E_INVALID, "non-finite coefficient");
+    if (aM != 0.0 && !all_affine(m)) return fail(TLFE_E_UNSUPPORTED, "consistent mass needs affine elements");
+    cudaStream_t s = (cudaStream_t)stream;
+    return m->precision == TLFE_FP32
+               ? run_op<OP_MATVEC, float>(m, u, ud, v, y, nullptr, nullptr, aM, aK, aC, 1, s)
+               : run_op<OP_MATVEC, double>(m, u, ud, v, y, nullptr, nullptr, aM, aK, aC, 1, s);
+}
+
 extern "C" tlfe_status tlfe_jacobi_diag(tlfe_mesh *m, const void *u, const void *ud, double aM, double aK, double aC,
                                         void *d, void *stream)
 {

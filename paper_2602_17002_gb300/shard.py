@@ -19,6 +19,14 @@ Two splits, both host logic on index arrays (no element arithmetic):
   all-reduce of torch.distributed; peers' data is copied into local memory
   by the collective, never read in place).
 
+* The backward-Euler step of one split body (Sec. 7): ``split_newton_step``
+  runs the inexact Newton / Jacobi-PCG iteration of tlfe_newton_step from
+  the host over the rank's shares, with the interface sum after every
+  operator application and an FP64 all-reduce of the CG scalars (p.q, then
+  r.z and r.r) per iteration; ``SplitShare`` does a share's work in the
+  library, ``DistGroup`` / ``LocalGroup`` make the exchanges across
+  processes or within one.
+
 ``local_blocks`` renumbers a rank's share into a self-contained mesh.
 """
 
@@ -202,3 +210,160 @@ class InterfaceSum:
         dist.all_reduce(self.buf, op=dist.ReduceOp.SUM, group=self.group)
         self.unpack(self.buf, self.pos, x, self.idx)
         return x
+
+
+# ---------------------------------------------------------------------------
+# Backward-Euler step of one body split across ranks (Sec. 7)
+# ---------------------------------------------------------------------------
+
+class DistGroup:
+    """The exchanges of a split step when every rank is its own process (one
+    share per process): interface rows by an InterfaceSum, scalars by an
+    FP64 all-reduce of torch.distributed."""
+
+    def __init__(self, iface_sum: "InterfaceSum", group=None):
+        self.iface_sum = iface_sum
+        self.group = group
+
+    def sum_rows(self, xs):
+        (x,) = xs
+        self.iface_sum(x)
+
+    def sum_scalars(self, ds) -> np.ndarray:
+        import torch.distributed as dist
+        (d,) = ds
+        dist.all_reduce(d, op=dist.ReduceOp.SUM, group=self.group)
+        return d.cpu().numpy().astype(np.float64)
+
+
+class LocalGroup:
+    """The same exchanges when one process holds every share of the body (the
+    shares run one after another on one device): the interface rows of all
+    shares are added in share order through one compact buffer per share,
+    and the scalars are added in share order on the host. `pack` / `unpack`
+    are those of InterfaceSum (the library's row kernels by default)."""
+
+    def __init__(self, ifaces: Sequence[Interface], dtype, device, pack=None, unpack=None):
+        import torch
+        self.sums = [InterfaceSum(itf, dtype, device, pack=pack, unpack=unpack) for itf in ifaces]
+        self.total = torch.zeros_like(self.sums[0].buf)
+
+    def sum_rows(self, xs):
+        self.total.zero_()
+        for s, x in zip(self.sums, xs):
+            s.pack(x, s.idx, s.buf, s.pos)
+            self.total += s.buf          # stands in for the all-reduce of the buffers
+        for s, x in zip(self.sums, xs):
+            s.unpack(self.total, s.pos, x, s.idx)
+
+    def sum_scalars(self, ds) -> np.ndarray:
+        tot = None
+        for d in ds:
+            a = d.cpu().numpy().astype(np.float64)
+            tot = a if tot is None else tot + a
+        return tot
+
+
+def split_newton_step(parts, group, h, newton_rtol=1e-8, cg_rtol=1e-4, max_newton=20, max_cg=2000):
+    """Inexact Newton / Jacobi-PCG step of Sec. 7 on one body split into the
+    shares `parts` (this process's shares; the group adds the other ranks'):
+    g(v) = M/h (v - v_n) + f_int(q_n + h v, v) - f_ff (Eq. residual), each
+    Newton iteration solving (M/h + h K^e + C) dv = -g (the symmetric part of
+    dg/dv, as tlfe_newton_step) by Jacobi-PCG, then v += dv, until
+    ||g|| <= newton_rtol ||g(v_n)||. Per operator application the ranks sum
+    the interface rows (group.sum_rows); per CG iteration they all-reduce
+    p.q, then r.z and r.r (group.sum_scalars: three FP64 scalars). Each share
+    (SplitShare below, or a stand-in with the same methods) does its own
+    vector and element work. Returns a report; every share holds its v."""
+    for s in parts:
+        s.start()
+    def residual_norm():
+        group.sum_rows([s.residual(h) for s in parts])
+        return float(np.sqrt(max(group.sum_scalars([s.dot_g() for s in parts])[0], 0.0)))
+    g0 = residual_norm()
+    gn, it, cg_total = g0, 0, 0
+    while g0 > 0.0 and gn > newton_rtol * g0 and it < max_newton:
+        group.sum_rows([s.diag(h) for s in parts])
+        rz, rr = group.sum_scalars([s.cg_start() for s in parts])[:2]
+        r0 = np.sqrt(max(rr, 0.0))
+        k = 0
+        while np.sqrt(max(rr, 0.0)) > cg_rtol * r0 and k < max_cg:
+            group.sum_rows([s.apply(h) for s in parts])
+            pq = group.sum_scalars([s.cg_pq() for s in parts])[0]
+            alpha = rz / pq
+            rz1, rr = group.sum_scalars([s.cg_update(alpha) for s in parts])[:2]
+            beta = rz1 / rz
+            rz = rz1
+            for s in parts:
+                s.cg_direction(beta)
+            k += 1
+        cg_total += k
+        for s in parts:
+            s.newton_update()
+        gn = residual_norm()
+        it += 1
+    conv = not (g0 > 0.0 and gn > newton_rtol * g0)
+    return {"newton_iters": it, "cg_iters": cg_total, "status": 0 if conv else 5,
+            "rel_residual": gn / g0 if g0 > 0.0 else 0.0}
+
+
+class SplitShare:
+    """One share of a split body on the GPU for split_newton_step: its FP64
+    mesh for the residual, its operator mesh (FP64 or FP32) for the CG
+    products and the Jacobi diagonal, and the library's split-step vector
+    kernels (tlfe.SplitCG); every computation runs in libtlfe. u_n, v_n:
+    float64 CUDA (n_rows, 3) of the share's nodes; fixed: uint8 CUDA [n_rows]
+    or None; own: uint8 CUDA [n_rows] (owned_rows) or None; gravity: b0."""
+
+    def __init__(self, res_mesh, op_mesh, u_n, v_n, gravity, fixed=None, own=None):
+        import torch
+        from . import tlfe
+        self.res, self.op = res_mesh, op_mesh
+        n = res_mesh.n_nodes
+        self.u_n, self.v_n = u_n, v_n
+        self.grav = [float(g) for g in gravity]
+        self.cg = tlfe.SplitCG(n, op_mesh.precision, fixed=fixed, own=own)
+        z = lambda: torch.zeros((n, 3), dtype=torch.float64, device=u_n.device)  # noqa: E731
+        self.v, self.u, self.w, self.f, self.y, self.g = z(), z(), z(), z(), z(), z()
+        self.v_op = None if op_mesh.precision == tlfe.FP64 else \
+            torch.zeros((n, 3), dtype=op_mesh.torch_dtype, device=u_n.device)
+        self.D = torch.zeros((n, 3), dtype=op_mesh.torch_dtype, device=u_n.device)
+
+    def _ud(self):
+        return self.v if self.v_op is None else self.v_op
+
+    def start(self):
+        self.cg.velocity(self.v_n, False, self.v)
+
+    def residual(self, h):
+        self.cg.prep(h, self.grav, self.u_n, self.v_n, self.v, self.u, self.w,
+                     None if self.v_op is None else self.v_op)
+        self.res.internal_force(self.u, self.v, out=self.f)
+        self.res.tangent_matvec(self.u, None, self.w, 1.0 / h, 0.0, 0.0, out=self.y)
+        self.cg.residual(self.f, self.y, self.g)
+        return self.g
+
+    def dot_g(self):
+        return self.cg.dot(self.g, self.g)
+
+    def diag(self, h):
+        return self.op.jacobi_diag(self.u, self._ud(), 1.0 / h, h, 1.0, out=self.D)
+
+    def cg_start(self):
+        self.cg.cg_dinv(self.D)
+        return self.cg.cg_start(self.g)
+
+    def apply(self, h):
+        return self.op.newton_operator(self.u, self._ud(), self.cg.p, 1.0 / h, h, 1.0, out=self.cg.q)
+
+    def cg_pq(self):
+        return self.cg.cg_pq()
+
+    def cg_update(self, alpha):
+        return self.cg.cg_update(alpha)
+
+    def cg_direction(self, beta):
+        self.cg.cg_direction(beta)
+
+    def newton_update(self):
+        self.cg.velocity(self.v, True, self.v)

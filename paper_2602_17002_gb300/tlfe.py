@@ -92,6 +92,14 @@ CON_CD, CON_DIST, CON_DP1, CON_DP2 = 0, 1, 2, 3
 CON_DTYPE = np.dtype([("type", np.int32), ("elem", np.int32, (4,)), ("xi", np.float64, (4, 3)),
                       ("d", np.float64, (3,)), ("f", np.float64)], align=True)
 
+
+
+class tlfe_split_cg(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("n_rows", C.c_int32), ("fixed", C.c_void_p), ("own", C.c_void_p),
+                ("x", C.c_void_p), ("r", C.c_void_p), ("p", C.c_void_p), ("q", C.c_void_p),
+                ("dinv", C.c_void_p), ("work", C.c_void_p), ("dots", C.c_void_p)]
+
+
 _lib = None
 
 EXPORTS = ["tlfe_create_mesh", "tlfe_destroy_mesh", "tlfe_get_mesh_info", "tlfe_get_colors",
@@ -101,7 +109,9 @@ EXPORTS = ["tlfe_create_mesh", "tlfe_destroy_mesh", "tlfe_get_mesh_info", "tlfe_
            "tlfe_internal_force", "tlfe_internal_force_host", "tlfe_tangent_matvec", "tlfe_jacobi_diag",
            "tlfe_vjp", "tlfe_set_elem_mu_lambda", "tlfe_autotune", "tlfe_point_loads", "tlfe_surface_traction",
            "tlfe_constraint_eval", "tlfe_constraint_jt", "tlfe_constraint_j", "tlfe_newton_step", "tlfe_body_norms", "tlfe_norm_noalloc", "tlfe_selftest_wait_timeout", "tlfe_last_error",
-           "tlfe_version"]
+           "tlfe_version", "tlfe_newton_operator", "tlfe_split_work_doubles", "tlfe_split_prep",
+           "tlfe_split_residual", "tlfe_split_velocity", "tlfe_split_dot", "tlfe_split_cg_dinv",
+           "tlfe_split_cg_start", "tlfe_split_cg_pq", "tlfe_split_cg_update", "tlfe_split_cg_direction"]
 
 
 def load(path: str = LIB_PATH) -> C.CDLL:
@@ -144,6 +154,16 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "tlfe_constraint_j": [P, I, P, P, P, P, P],
         "tlfe_norm_noalloc": [P, C.c_int64, P, P],
         "tlfe_selftest_wait_timeout": [P, C.c_int64, P],
+        "tlfe_newton_operator": [P, P, P, P, D, D, D, P, P],
+        "tlfe_split_prep": [C.POINTER(tlfe_split_cg), D, P, P, P, P, P, P, P, P],
+        "tlfe_split_residual": [C.POINTER(tlfe_split_cg), P, P, P, P],
+        "tlfe_split_velocity": [C.POINTER(tlfe_split_cg), P, I, P, P],
+        "tlfe_split_dot": [C.POINTER(tlfe_split_cg), P, P, P],
+        "tlfe_split_cg_dinv": [C.POINTER(tlfe_split_cg), P, P],
+        "tlfe_split_cg_start": [C.POINTER(tlfe_split_cg), P, P],
+        "tlfe_split_cg_pq": [C.POINTER(tlfe_split_cg), P],
+        "tlfe_split_cg_update": [C.POINTER(tlfe_split_cg), D, P],
+        "tlfe_split_cg_direction": [C.POINTER(tlfe_split_cg), D, P],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -153,6 +173,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     L.tlfe_last_error.argtypes = []
     L.tlfe_version.restype = C.c_char_p
     L.tlfe_version.argtypes = []
+    L.tlfe_split_work_doubles.restype = C.c_int64
+    L.tlfe_split_work_doubles.argtypes = [C.c_int64]
     _lib = L
     return L
 
@@ -393,6 +415,18 @@ class Mesh:
         out = self._new() if out is None else self._node_array(out, "out")
         _check(load().tlfe_tangent_matvec(self._h, _ptr(u), _ptr(udot), _ptr(v), float(a_M), float(a_K),
                                           float(a_C), _ptr(out), _stream(stream)))
+        return out
+
+    def newton_operator(self, u, udot, v, a_M=0.0, a_K=1.0, a_C=0.0, out=None, stream=None):
+        """y = a_M M v + a_K K^e v + a_C C v, the symmetric CG operator of the
+        Newton step (tlfe_newton_operator)."""
+        import torch
+        self._node_array(u, "u", torch.float64)
+        self._node_array(udot, "udot")
+        self._node_array(v, "v")
+        out = self._new() if out is None else self._node_array(out, "out")
+        _check(load().tlfe_newton_operator(self._h, _ptr(u), _ptr(udot), _ptr(v), float(a_M), float(a_K),
+                                           float(a_C), _ptr(out), _stream(stream)))
         return out
 
     def jacobi_diag(self, u, udot=None, a_M=0.0, a_K=1.0, a_C=0.0, out=None, stream=None):
@@ -658,6 +692,89 @@ def scatter_nodes(buf, idx, x, buf_idx=None, stream=None):
     _check(load().tlfe_scatter_nodes(prec, _ptr(buf), _ptr(_idx(buf_idx, n)), _ptr(_idx(idx, n)), n, _ptr(x),
                                      _stream(stream)))
     return x
+
+
+class SplitCG:
+    """Device vectors of one share of a body split across GPUs and the
+    marshalling of the tlfe_split_* calls on them (the per-rank vector work of
+    the split backward-Euler step). x, r, p, q, dinv are (n_rows, 3) CUDA
+    tensors in the operator mesh's precision; dots is the float64 CUDA [2]
+    tensor that receives each call's partial sums over the owned rows (the
+    calls that sum return it; the caller all-reduces it before the next call
+    overwrites it). fixed / own: uint8 CUDA [n_rows] or None."""
+
+    def __init__(self, n_rows, precision, fixed=None, own=None, device="cuda"):
+        import torch
+        dt = torch.float32 if precision == FP32 else torch.float64
+        for m, name in ((fixed, "fixed"), (own, "own")):
+            if m is not None and not (m.is_cuda and m.dtype == torch.uint8 and m.is_contiguous()
+                                      and m.numel() == n_rows):
+                raise TLFEError(1, f"{name} must be a contiguous CUDA uint8 tensor of {n_rows} rows")
+        self.n_rows, self.precision, self.dtype = int(n_rows), precision, dt
+        self.fixed, self.own = fixed, own
+        self.x, self.r, self.p, self.q, self.dinv = (torch.zeros((n_rows, 3), dtype=dt, device=device)
+                                                     for _ in range(5))
+        self.work = torch.zeros(int(load().tlfe_split_work_doubles(C.c_int64(n_rows))), dtype=torch.float64,
+                                device=device)
+        self.dots = torch.zeros(2, dtype=torch.float64, device=device)
+        self.c = tlfe_split_cg(int(precision), self.n_rows, _ptr(fixed), _ptr(own), _ptr(self.x), _ptr(self.r),
+                               _ptr(self.p), _ptr(self.q), _ptr(self.dinv), _ptr(self.work), _ptr(self.dots))
+
+    def _rows(self, t, name, dtype=None):
+        import torch
+        dt = dtype or torch.float64
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dt and t.is_contiguous()
+                and tuple(t.shape) == (self.n_rows, 3)):
+            raise TLFEError(1, f"{name} must be a contiguous CUDA {dt} tensor of shape ({self.n_rows}, 3)")
+        return t
+
+    def prep(self, h, gravity, u_n, v_n, v, u_out, w_out, v_op_out=None, stream=None):
+        for t, n in ((u_n, "u_n"), (v_n, "v_n"), (v, "v"), (u_out, "u_out"), (w_out, "w_out")):
+            self._rows(t, n)
+        if v_op_out is not None:
+            self._rows(v_op_out, "v_op_out", self.dtype)
+        g = (C.c_double * 3)(*[float(x) for x in gravity])
+        _check(load().tlfe_split_prep(C.byref(self.c), float(h), g, _ptr(u_n), _ptr(v_n), _ptr(v), _ptr(u_out),
+                                      _ptr(w_out), _ptr(v_op_out), _stream(stream)))
+
+    def residual(self, f, y, g, stream=None):
+        for t, n in ((f, "f"), (y, "y"), (g, "g")):
+            self._rows(t, n)
+        _check(load().tlfe_split_residual(C.byref(self.c), _ptr(f), _ptr(y), _ptr(g), _stream(stream)))
+        return g
+
+    def velocity(self, v_base, add_x, v_out, stream=None):
+        self._rows(v_base, "v_base")
+        self._rows(v_out, "v_out")
+        _check(load().tlfe_split_velocity(C.byref(self.c), _ptr(v_base), int(bool(add_x)), _ptr(v_out),
+                                          _stream(stream)))
+        return v_out
+
+    def dot(self, a, b, stream=None):
+        self._rows(a, "a")
+        self._rows(b, "b")
+        _check(load().tlfe_split_dot(C.byref(self.c), _ptr(a), _ptr(b), _stream(stream)))
+        return self.dots[:1]
+
+    def cg_dinv(self, D, stream=None):
+        self._rows(D, "D", self.dtype)
+        _check(load().tlfe_split_cg_dinv(C.byref(self.c), _ptr(D), _stream(stream)))
+
+    def cg_start(self, g, stream=None):
+        self._rows(g, "g")
+        _check(load().tlfe_split_cg_start(C.byref(self.c), _ptr(g), _stream(stream)))
+        return self.dots
+
+    def cg_pq(self, stream=None):
+        _check(load().tlfe_split_cg_pq(C.byref(self.c), _stream(stream)))
+        return self.dots[:1]
+
+    def cg_update(self, alpha, stream=None):
+        _check(load().tlfe_split_cg_update(C.byref(self.c), float(alpha), _stream(stream)))
+        return self.dots
+
+    def cg_direction(self, beta, stream=None):
+        _check(load().tlfe_split_cg_direction(C.byref(self.c), float(beta), _stream(stream)))
 
 
 def tlfe_norm_noalloc(x, out, stream=None):
