@@ -339,7 +339,7 @@ class SplitShare:
         self.cg.prep(h, self.grav, self.u_n, self.v_n, self.v, self.u, self.w,
                      None if self.v_op is None else self.v_op)
         self.res.internal_force(self.u, self.v, out=self.f)
-        self.res.tangent_matvec(self.u, None, self.w, 1.0 / h, 0.0, 0.0, out=self.y)
+        self.res.tangent_matvec(self.u, self.v, self.w, 1.0 / h, 0.0, 0.0, out=self.y)
         self.cg.residual(self.f, self.y, self.g)
         return self.g
 
