@@ -1242,7 +1242,36 @@ def cpu_baseline(workload, wl, unit, n_sample, single_core=True):
     return out
 
 
-def main():
+def parse_args(ap, argv=None):
+    """Parse the command line; with --case FILE the file's JSON object gives
+    option defaults first (unknown keys and values of the wrong kind are
+    errors), so that flags on the command line take precedence."""
+    pre = argparse.ArgumentParser(add_help=False)
+    pre.add_argument("--case", default=None)
+    known, _ = pre.parse_known_args(argv)
+    if known.case:
+        with open(known.case) as fh:
+            case = json.load(fh)
+        if not isinstance(case, dict):
+            ap.error(f"--case {known.case}: expected a JSON object")
+        acts = {a.dest: a for a in ap._actions if a.dest not in ("help", "case")}
+        for k, v in case.items():
+            key = k.replace("-", "_")
+            if key not in acts:
+                ap.error(f"--case {known.case}: unknown option {k!r}")
+            a = acts[key]
+            if a.choices is not None and v not in a.choices:
+                ap.error(f"--case {known.case}: {k} = {v!r} is not one of {sorted(a.choices)}")
+            if a.type is not None and v is not None and not isinstance(v, bool):
+                try:
+                    v = a.type(v)
+                except (TypeError, ValueError):
+                    ap.error(f"--case {known.case}: {k} = {v!r} is not a valid {a.type.__name__}")
+            ap.set_defaults(**{key: v})
+    return ap.parse_args(argv)
+
+
+def make_parser():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
@@ -1262,7 +1291,15 @@ def main():
     ap.add_argument("--sub-steps", type=int, default=5, help="timed steps of each sub-measurement")
     ap.add_argument("--sub-cpu-sample", type=int, default=12000,
                     help="elements in the sub-measurements' cpu_baseline samples")
-    args = ap.parse_args()
+    ap.add_argument("--case", default=None,
+                    help="JSON file of option values (keys: the long option names without the leading dashes, e.g. "
+                         '{"workload": "batch", "scatter": "sorted", "steps": 10}); options given on the '
+                         "command line override it")
+    return ap
+
+
+def main():
+    args = parse_args(make_parser())
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

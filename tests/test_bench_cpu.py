@@ -80,3 +80,22 @@ def test_bench_shards_cover_the_workloads():
     assert sum(sh.n_elem for sh, _ in parts) == bw.n_elem
     assert sum(sh.n_nodes for sh, _ in parts) == bw.n_nodes
     assert bench.parallelism("beam", 1) == "1 GPU" and "slab" in bench.parallelism("beam", 2)
+
+
+def test_case_file_sets_option_defaults_and_flags_override_it(tmp_path):
+    import json
+
+    import pytest
+    case = tmp_path / "case.json"
+    case.write_text(json.dumps({"workload": "batch", "scatter": "sorted", "steps": 7, "sub-steps": 4,
+                                "headline_only": True}))
+    a = bench.parse_args(bench.make_parser(), ["--case", str(case)])
+    assert (a.workload, a.scatter, a.steps, a.sub_steps, a.headline_only) == ("batch", "sorted", 7, 4, True)
+    assert a.warmup == 3 and a.gpus == 1                     # untouched defaults
+    a = bench.parse_args(bench.make_parser(), ["--case", str(case), "--steps", "9", "--scatter", "colour"])
+    assert (a.steps, a.scatter, a.workload) == (9, "colour", "batch")
+    assert bench.parse_args(bench.make_parser(), []).workload == "beam"
+    for bad in ({"workloads": "beam"}, {"scatter": "smem"}, {"steps": "many"}, ["beam"]):
+        case.write_text(json.dumps(bad))
+        with pytest.raises(SystemExit):
+            bench.parse_args(bench.make_parser(), ["--case", str(case)])
