@@ -218,16 +218,22 @@ class InterfaceSum:
 
 class DistGroup:
     """The exchanges of a split step when every rank is its own process (one
-    share per process): interface rows by an InterfaceSum, scalars by an
-    FP64 all-reduce of torch.distributed."""
+    share per process): interface rows by an InterfaceSum (one compact buffer
+    per dtype of the rows summed: the FP64 residual, the operator mesh's
+    diagonal and CG products), scalars by an FP64 all-reduce of
+    torch.distributed. `pack` / `unpack` as for InterfaceSum."""
 
-    def __init__(self, iface_sum: "InterfaceSum", group=None):
-        self.iface_sum = iface_sum
-        self.group = group
+    def __init__(self, iface: Interface, device, group=None, pack=None, unpack=None):
+        self.iface, self.device, self.group = iface, device, group
+        self.pack, self.unpack = pack, unpack
+        self.sums = {}
 
     def sum_rows(self, xs):
         (x,) = xs
-        self.iface_sum(x)
+        if x.dtype not in self.sums:
+            self.sums[x.dtype] = InterfaceSum(self.iface, x.dtype, self.device, group=self.group,
+                                              pack=self.pack, unpack=self.unpack)
+        self.sums[x.dtype](x)
 
     def sum_scalars(self, ds) -> np.ndarray:
         import torch.distributed as dist
@@ -239,22 +245,28 @@ class DistGroup:
 class LocalGroup:
     """The same exchanges when one process holds every share of the body (the
     shares run one after another on one device): the interface rows of all
-    shares are added in share order through one compact buffer per share,
-    and the scalars are added in share order on the host. `pack` / `unpack`
-    are those of InterfaceSum (the library's row kernels by default)."""
+    shares are added in share order through one compact buffer per share and
+    dtype, and the scalars are added in share order on the host. `pack` /
+    `unpack` are those of InterfaceSum (the library's row kernels by default)."""
 
-    def __init__(self, ifaces: Sequence[Interface], dtype, device, pack=None, unpack=None):
-        import torch
-        self.sums = [InterfaceSum(itf, dtype, device, pack=pack, unpack=unpack) for itf in ifaces]
-        self.total = torch.zeros_like(self.sums[0].buf)
+    def __init__(self, ifaces: Sequence[Interface], device, pack=None, unpack=None):
+        self.ifaces, self.device = list(ifaces), device
+        self.pack, self.unpack = pack, unpack
+        self.sums = {}
 
     def sum_rows(self, xs):
-        self.total.zero_()
-        for s, x in zip(self.sums, xs):
+        import torch
+        dt = xs[0].dtype
+        if dt not in self.sums:
+            sums = [InterfaceSum(itf, dt, self.device, pack=self.pack, unpack=self.unpack) for itf in self.ifaces]
+            self.sums[dt] = (sums, torch.zeros_like(sums[0].buf))
+        sums, total = self.sums[dt]
+        total.zero_()
+        for s, x in zip(sums, xs):
             s.pack(x, s.idx, s.buf, s.pos)
-            self.total += s.buf          # stands in for the all-reduce of the buffers
-        for s, x in zip(self.sums, xs):
-            s.unpack(self.total, s.pos, x, s.idx)
+            total += s.buf          # stands in for the all-reduce of the buffers
+        for s, x in zip(sums, xs):
+            s.unpack(total, s.pos, x, s.idx)
 
     def sum_scalars(self, ds) -> np.ndarray:
         tot = None

@@ -48,7 +48,7 @@ BARS = [(0, 1e-10, 1e-8, 1e-10), (1, 1e-10, 1e-6, 1e-6)]
 def test_split_step_matches_the_unsplit_oracle(prec, rtol, cg_rtol, bar, n_shares, damping):
     wl = clamped_beam(cells=9, damping=damping)
     parts, nodes, ifs = _shares(wl, n_shares, prec)
-    group = shard.LocalGroup(ifs, torch.float64, "cuda")
+    group = shard.LocalGroup(ifs, "cuda")
     rep = shard.split_newton_step(parts, group, H, newton_rtol=rtol, cg_rtol=cg_rtol)
     torch.cuda.synchronize()
     assert rep["status"] == 0 and rep["rel_residual"] <= rtol and rep["newton_iters"] >= 1
@@ -80,7 +80,7 @@ def test_split_step_repeats_bit_for_bit_in_sorted_scatter_mode():
             own = torch.from_numpy(shard.owned_rows(nd.size, itf).astype(np.uint8)).cuda()
             parts.append(shard.SplitShare(mesh, mesh, z, z.clone(), G, fixed=torch.from_numpy(sw.fixed).cuda(),
                                           own=own))
-        rep = shard.split_newton_step(parts, shard.LocalGroup(ifs, torch.float64, "cuda"), H)
+        rep = shard.split_newton_step(parts, shard.LocalGroup(ifs, "cuda"), H)
         outs.append(([s.v.cpu().numpy() for s in parts], rep))
     assert outs[0][1] == outs[1][1]
     for a, b in zip(outs[0][0], outs[1][0]):
