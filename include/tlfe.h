@@ -362,8 +362,10 @@ typedef struct {
 } tlfe_constraint;
 
 /* c_dev[k] = c_k(X + u) for the n constraints cons_dev (device arrays; u_dev
- * device double [n_nodes][3], c_dev device double [n]). Allocates and frees
- * scratch; synchronises `stream`. Invalid elements or types: TLFE_E_INVALID. */
+ * device double [n_nodes][3], c_dev device double [n]). The first call with
+ * more constraints than any call before on the handle allocates its constraint
+ * scratch (kept until tlfe_destroy_mesh); later calls reuse it. All three calls
+ * synchronise `stream`. Invalid elements or types: TLFE_E_INVALID. */
 tlfe_status tlfe_constraint_eval(tlfe_mesh *mesh, int32_t n, const tlfe_constraint *cons_dev, const double *u_dev,
                                  double *c_dev, void *stream);
 /* f_dev += C_q^T w (C_q = dc/dq at X + u, applied through the element blocks

@@ -989,6 +989,11 @@ extern "C" tlfe_status tlfe_destroy_mesh(tlfe_mesh *m)
     destroy_graphs(m);
     destroy_host_stage(m);
     for (void *p : m->allocs) cudaFree(p);
+    cudaFree(m->d_con_sh);
+    cudaFree(m->d_con_gp);
+    cudaFree(m->d_con_c);
+    cudaFree(m->d_con_nd);
+    cudaFree(m->d_con_bad);
     delete m->fused;
     delete m;
     return TLFE_OK;

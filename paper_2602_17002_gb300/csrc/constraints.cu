@@ -5,6 +5,7 @@
 // augmented-Lagrangian Newton step.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include "tlfe_elem.cuh"
@@ -300,21 +301,41 @@ cudaError_t con_lam_update(int n, double *lam, const double *c, double rho, cuda
 
 using namespace tlfe;
 
-// scratch of one standalone call: point data, coefficients and values
+// scratch of a standalone call: point data, coefficients and values of the
+// mesh handle's constraint scratch (grown by con_setup, freed with the handle;
+// every standalone call synchronises its stream before returning, so the next
+// call reuses it only after the previous one's kernels have ended)
 namespace {
 struct ConScratch {
     double *sh = nullptr, *gp = nullptr, *c = nullptr;
     int32_t *nd = nullptr;
     int *bad = nullptr;
-    ~ConScratch()
-    {
-        cudaFree(sh);
-        cudaFree(gp);
-        cudaFree(c);
-        cudaFree(nd);
-        cudaFree(bad);
-    }
 };
+
+tlfe_status con_reserve(tlfe_mesh *m, int n)
+{
+    if (n <= m->con_cap) return TLFE_OK;
+    cudaFree(m->d_con_sh);
+    cudaFree(m->d_con_nd);
+    cudaFree(m->d_con_gp);
+    cudaFree(m->d_con_c);
+    cudaFree(m->d_con_bad);
+    m->d_con_sh = m->d_con_gp = m->d_con_c = nullptr;
+    m->d_con_nd = nullptr;
+    m->d_con_bad = nullptr;
+    m->con_cap = 0;
+    const size_t cap = std::max<size_t>((size_t)n, 64);
+    if (cudaMalloc(&m->d_con_sh, sizeof(double) * 4 * CON_MAXN * cap) != cudaSuccess ||
+        cudaMalloc(&m->d_con_nd, sizeof(int32_t) * 4 * CON_MAXN * cap) != cudaSuccess ||
+        cudaMalloc(&m->d_con_gp, sizeof(double) * 12 * cap) != cudaSuccess ||
+        cudaMalloc(&m->d_con_c, sizeof(double) * cap) != cudaSuccess ||
+        cudaMalloc(&m->d_con_bad, sizeof(int)) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(TLFE_E_OOM, "constraint scratch");
+    }
+    m->con_cap = (int)cap;
+    return TLFE_OK;
+}
 }  // namespace
 
 static tlfe_status con_setup(tlfe_mesh *m, int n, const tlfe_constraint *cons, const double *u, ConScratch &cs,
@@ -322,11 +343,13 @@ static tlfe_status con_setup(tlfe_mesh *m, int n, const tlfe_constraint *cons, c
 {
     const ConBlocks bt = con_blocks(m);
     if (bt.n < 0) return fail(TLFE_E_UNSUPPORTED, "constraints support at most 16 element blocks");
-    if (cudaMalloc(&cs.sh, sizeof(double) * 4 * CON_MAXN * (size_t)n) != cudaSuccess ||
-        cudaMalloc(&cs.nd, sizeof(int32_t) * 4 * CON_MAXN * (size_t)n) != cudaSuccess ||
-        cudaMalloc(&cs.gp, sizeof(double) * 12 * (size_t)n) != cudaSuccess ||
-        cudaMalloc(&cs.c, sizeof(double) * (size_t)n) != cudaSuccess || cudaMalloc(&cs.bad, sizeof(int)) != cudaSuccess)
-        return fail(TLFE_E_OOM, "constraint scratch");
+    tlfe_status st = con_reserve(m, n);
+    if (st != TLFE_OK) return st;
+    cs.sh = m->d_con_sh;
+    cs.nd = m->d_con_nd;
+    cs.gp = m->d_con_gp;
+    cs.c = m->d_con_c;
+    cs.bad = m->d_con_bad;
     cudaError_t e = cudaMemsetAsync(cs.bad, 0, sizeof(int), s);
     if (e == cudaSuccess) e = con_prepare(bt, n, cons, cs.sh, cs.nd, cs.bad, s);
     if (e == cudaSuccess) e = con_eval(n, cons, cs.sh, cs.nd, m->d_X, u, nullptr, cs.c, cs.gp, s);

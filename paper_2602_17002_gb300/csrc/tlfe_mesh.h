@@ -119,6 +119,13 @@ struct tlfe_mesh {
     tlfe::OpGraph *fm_graph = nullptr;
     int sched_gen = 0;  // bumped whenever launch schedules, mode or block parameters change
     tlfe::HostStage *host_stage = nullptr;
+    // scratch of the standalone constraint calls (tlfe_constraint_eval / _j /
+    // _jt): point data for con_cap constraints, grown on demand and kept
+    // until the handle is destroyed
+    int con_cap = 0;
+    double *d_con_sh = nullptr, *d_con_gp = nullptr, *d_con_c = nullptr;
+    int32_t *d_con_nd = nullptr;
+    int *d_con_bad = nullptr;
 };
 
 namespace tlfe {
