@@ -68,16 +68,25 @@ WORKLOADS = {
 }
 GRAVITY = (0.0, 0.0, -9.81)
 # Algorithmic FP32 FLOPs per quadrature point of the neo-Hookean + Kelvin-Voigt
-# kernels on the affine path (2 FFMA + FADD + FMUL, counted by ncu): T10 Q5 for
-# the beam workload, Q27 for the q27 workload
-FLOP_PER_QP = {"beam": {"force": 852, "matvec": 1589, "vjp": 1786},
+# kernels on the affine path: T10 Q5 for the beam workload, Q27 for the q27
+# workload. force, matvec, vjp: 2 FFMA + FADD + FMUL thread instructions counted
+# by ncu on the scalar build of these kernels; force_matvec (the one-pass force +
+# operator product): 2 FFMA + FADD + FMUL + 4 FFMA2 + 2 FADD2 + 2 FMUL2 counted
+# by ncu on the packed build (the same count gives the adjoint 1820, against
+# 1786 on the scalar build)
+FLOP_PER_QP = {"beam": {"force": 852, "matvec": 1589, "vjp": 1786, "force_matvec": 1934},
                "q27": {"force": 1932, "matvec": 3026, "vjp": 3567}}
 # batch workload (affine path, no damping): FP32 FLOP per point by (element
-# type, law, op), law 0 = SVK, 1 = neo-Hookean; ncu counts (2 FFMA + FADD +
-# FMUL) of the per-law kernels of one timed step of the 512-body batch
-FLOP_PER_QP_BATCH = {(0, 0): {"force": 288.3, "matvec": 503.3}, (0, 1): {"force": 359.3, "matvec": 690.3},
-                     (1, 0): {"force": 483.7, "matvec": 865.7}, (1, 1): {"force": 552.3, "matvec": 1048.3},
-                     (2, 0): {"force": 540.0, "matvec": 942.3}, (2, 1): {"force": 610.4, "matvec": 1124.7}}
+# type, law, op), law 0 = SVK, 1 = neo-Hookean; ncu counts of the per-law
+# kernels of one timed step (force, matvec: 2 FFMA + FADD + FMUL on the scalar
+# build, 512-body batch; force_matvec: with the packed instructions as above,
+# 64-body batch)
+FLOP_PER_QP_BATCH = {(0, 0): {"force": 288.3, "matvec": 503.3, "force_matvec": 652.3},
+                     (0, 1): {"force": 359.3, "matvec": 690.3, "force_matvec": 839.4},
+                     (1, 0): {"force": 483.7, "matvec": 865.7, "force_matvec": 1096.7},
+                     (1, 1): {"force": 552.3, "matvec": 1048.3, "force_matvec": 1279.3},
+                     (2, 0): {"force": 540.0, "matvec": 942.3, "force_matvec": 1188.5},
+                     (2, 1): {"force": 610.4, "matvec": 1124.7, "force_matvec": 1370.7}}
 # how the end-to-end measurements move data
 OVERLAP = ("copies on their own streams: the next step's inputs are copied in while a step computes (two device "
            "staging sets), outputs are copied out as their operations end")
@@ -126,7 +135,16 @@ def streamed_bytes(wl, s=4):
     node = 3 * s * wl.n_nodes
     n_in = 2 if wl.udot is not None else 1
     return {"force": el + node * (n_in + 1), "matvec": el + node * (n_in + 2),
+            "force_matvec": el + node * (n_in + 3),   # one pass: u (+udot) and v read, f and y written
             "vjp": el + node * (n_in + 1 + n_in) + 2 * s * wl.n_elem}
+
+
+def step_launches(info):
+    """Element-kernel launches of one force + K v call (tlfe_force_matvec):
+    one per pass of the one-pass kernel, else those of both operations."""
+    if info["force_matvec_fused"]:
+        return info["launches_matvec"]
+    return info["launches_force"] + info["launches_matvec"]
 
 
 def peaks():
@@ -144,7 +162,7 @@ def peaks():
 # are unchanged
 KERNEL_SOURCES = ("k_elem.cuh", "k_wpe.cuh", "k_fused.cuh", "tlfe_fused.h", "tlfe_elem.cuh", "tlfe_math.cuh",
                   "tlfe_internal.h", "tlfe_mesh.h", "api.cu", "k_setup.cu", "k_force.cu", "k_matvec.cu", "k_vjp.cu",
-                  "k_diag.cu", "k_fused_force.cu", "k_fused_matvec.cu")
+                  "k_diag.cu", "k_fm.cu", "k_fused_force.cu", "k_fused_matvec.cu")
 
 
 def _strip_comments(src):
@@ -621,63 +639,76 @@ def run_beam(args, rank, world, workload="beam"):
         return mesh, ud, v, outs, gth
 
     def make_step(mesh, u_, ud, v, outs, gth):
+        """The step's calls and the names of its timed phases: force and
+        operator product in one pass (tlfe_force_matvec, graph-replayed) where
+        the mesh takes it after autotuning, else in two; then the adjoint."""
         h = mesh.handle
         f, y, gu, gud = outs
+        one_pass = bool(mesh.info["force_matvec_fused"])
+        names = ["force_matvec", "vjp"] if one_pass else ["force", "matvec", "vjp"]
 
         def step(ev=None):
             if ev:
                 ev[0].record(stream)
-            tlfe._check(L.tlfe_internal_force(h, tlfe._ptr(u_), tlfe._ptr(ud), tlfe._ptr(f), sp))
-            xsum(f)
+            if one_pass:
+                tlfe._check(L.tlfe_force_matvec(h, tlfe._ptr(u_), tlfe._ptr(ud), tlfe._ptr(v), 0.0, 1.0, 1.0,
+                                                tlfe._ptr(f), tlfe._ptr(y), sp))
+                xsum(f)
+                xsum(y)
+            else:
+                tlfe._check(L.tlfe_internal_force(h, tlfe._ptr(u_), tlfe._ptr(ud), tlfe._ptr(f), sp))
+                xsum(f)
+                if ev:
+                    ev[1].record(stream)
+                tlfe._check(L.tlfe_tangent_matvec(h, tlfe._ptr(u_), tlfe._ptr(ud), tlfe._ptr(v), 0.0, 1.0, 1.0,
+                                                  tlfe._ptr(y), sp))
+                xsum(y)
             if ev:
-                ev[1].record(stream)
-            tlfe._check(L.tlfe_tangent_matvec(h, tlfe._ptr(u_), tlfe._ptr(ud), tlfe._ptr(v), 0.0, 1.0, 1.0,
-                                              tlfe._ptr(y), sp))
-            xsum(y)
-            if ev:
-                ev[2].record(stream)
+                ev[len(names) - 1].record(stream)
             tlfe._check(L.tlfe_vjp(h, tlfe._ptr(u_), tlfe._ptr(ud), tlfe._ptr(v), tlfe._ptr(gu), tlfe._ptr(gud),
                                    tlfe._ptr(gth), sp))
             xsum(gu)
             xsum(gud)
             if ev:
-                ev[3].record(stream)
-        return step
+                ev[len(names)].record(stream)
+        return step, names
 
     def time_step(mesh, ud, v, outs, gth, steps, label):
         mesh.autotune(u, ud, v)
-        step = make_step(mesh, u, ud, v, outs, gth)
+        step, nm = make_step(mesh, u, ud, v, outs, gth)
         for _ in range(args.warmup):
             step()
         mesh.sync()
         torch.cuda.synchronize()
-        evs = timed_steps(step, steps, flush, stream, 4, label)
-        return np.array([[e[j].elapsed_time(e[j + 1]) for j in range(3)] for e in evs])
+        evs = timed_steps(step, steps, flush, stream, len(nm) + 1, label)
+        return np.array([[e[j].elapsed_time(e[j + 1]) for j in range(len(nm))] for e in evs]), nm
 
-    names = ["force", "matvec", "vjp"]
+    def phase_bytes(info_, nm):
+        return [info_["stream_bytes_" + n] for n in nm]
+
     peak, peak_kind = peaks()
 
     # the isoparametric (slab) path on the same mesh: per-point h_i streamed
     ms_, ud_, v_, outs_, gth_ = make(tlfe.FP32, tlfe.PATH_SLAB)
+    per_s, names_s = time_step(ms_, ud_, v_, outs_, gth_, max(3, args.steps // 2), tag + "_slab_timed")
     info_s = ms_.info
-    per_s = time_step(ms_, ud_, v_, outs_, gth_, max(3, args.steps // 2), tag + "_slab_timed")
     ms_.close()
     ks = per_s.mean(axis=0)
-    bytes_s = [info_s["stream_bytes_force"], info_s["stream_bytes_matvec"], info_s["stream_bytes_vjp"]]
+    bytes_s = phase_bytes(info_s, names_s)
     js = int(np.argmax(ks))
     ach_s = bytes_s[js] / (ks[js] * 1e-3) / 1e9
-    slab = {"kernels_ms": {n: float(t) for n, t in zip(names, ks)}, "ms_per_step": float(per_s.sum(axis=1).mean()),
-            "kernels_gbs": {n: b / (t * 1e-3) / 1e9 for n, b, t in zip(names, bytes_s, ks)},
+    slab = {"kernels_ms": {n: float(t) for n, t in zip(names_s, ks)}, "ms_per_step": float(per_s.sum(axis=1).mean()),
+            "kernels_gbs": {n: b / (t * 1e-3) / 1e9 for n, b, t in zip(names_s, bytes_s, ks)},
             "roofline": {"bound": "hbm", "achieved": ach_s, "peak": peak, "unit": "GB/s", "frac": ach_s / peak,
-                         "traffic": ncu_traffic(pre + "slab_" + names[js]), "kernel": names[js],
+                         "traffic": ncu_traffic(pre + "slab_" + names_s[js]), "kernel": names_s[js],
                          "peak_source": peak_kind,
                          "algorithmic_bytes": bytes_s[js]}}
 
     # the default (affine) path: the timed step, launch schedules autotuned first
     mesh, ud, v, outs, gth = make(tlfe.FP32)
-    info = mesh.info
     mesh.autotune(u, ud, v)
-    step = make_step(mesh, u, ud, v, outs, gth)
+    info = mesh.info
+    step, names = make_step(mesh, u, ud, v, outs, gth)
     for _ in range(args.warmup):
         step()
     mesh.sync()
@@ -685,17 +716,19 @@ def run_beam(args, rank, world, workload="beam"):
     barrier(world)
     torch.cuda.synchronize()
     with ClockSampler(torch.cuda.current_device()) as clk:
-        evs = clk.timed(lambda: timed_steps(step, args.steps, flush, stream, 4, tag + "_affine_timed"))
+        evs = clk.timed(lambda: timed_steps(step, args.steps, flush, stream, len(names) + 1,
+                                            tag + "_affine_timed"))
     barrier(world)
     st = mesh.sync()
-    per = np.array([[evs[k][j].elapsed_time(evs[k][j + 1]) for j in range(3)] for k in range(args.steps)])
+    per = np.array([[evs[k][j].elapsed_time(evs[k][j + 1]) for j in range(len(names))]
+                    for k in range(args.steps)])
     step_ms = allmax(float(per.sum(axis=1).mean()), world)
     kern_ms = per.mean(axis=0)
     units = wl.n_qp                     # this GPU's points (all of them on one GPU)
     value = full.n_qp / (step_ms * 1e-3)  # the whole body per step, at the slowest GPU's time
 
     # roofline of the dominant kernel: FP32 FMA roof (bound), HBM fraction beside it
-    bytes_alg = [info["stream_bytes_force"], info["stream_bytes_matvec"], info["stream_bytes_vjp"]]
+    bytes_alg = phase_bytes(info, names)
     j = int(np.argmax(kern_ms))
     flops = fpq[names[j]] * units if fpq[names[j]] else None
     achieved = flops / (kern_ms[j] * 1e-3) / 1e12 if flops else None
@@ -766,7 +799,7 @@ def run_beam(args, rank, world, workload="beam"):
 
     # the same step with FP64 element arithmetic (the plain path)
     m64, ud64, v64, outs64, gth64 = make(tlfe.FP64)
-    per64 = time_step(m64, ud64, v64, outs64, gth64, max(3, args.steps // 4), tag + "_fp64_timed")
+    per64, names64 = time_step(m64, ud64, v64, outs64, gth64, max(3, args.steps // 4), tag + "_fp64_timed")
     ms64 = float(per64.sum(axis=1).mean())
     st64 = m64.sync()
     m64.close()
@@ -780,7 +813,8 @@ def run_beam(args, rank, world, workload="beam"):
         "kernels_ms": {n: float(t) for n, t in zip(names, kern_ms)},
         "kernels_gbs": {n: b / (t * 1e-3) / 1e9 for n, b, t in zip(names, bytes_alg, kern_ms)},
         "kernels_streamed_hbm_frac": kernels_streamed_frac,
-        "force_qps": full.n_qp / (kern_ms[0] * 1e-3),
+        "phases": names,
+        ("force_qps" if names[0] == "force" else "force_matvec_qps"): full.n_qp / (kern_ms[0] * 1e-3),
         "kernels_tflops": {n: fpq[n] * units / (t * 1e-3) / 1e12 if fpq[n] else None
                            for n, t in zip(names, kern_ms)},
         "roofline": roof,
@@ -788,7 +822,7 @@ def run_beam(args, rank, world, workload="beam"):
         "patch": {"layout": "banked" if info["patch_layout"] == tlfe.PATCH_BANKED else "sorted",
                   "passes_per_quarter_warp_load": info["patch_passes"]},
         "slab_path": slab,
-        "fp64_plain": {"ms_per_step": ms64, "kernels_ms": {n: float(t) for n, t in zip(names, per64.mean(axis=0))},
+        "fp64_plain": {"ms_per_step": ms64, "kernels_ms": {n: float(t) for n, t in zip(names64, per64.mean(axis=0))},
                        "speedup_fp32_over_fp64": ms64 / step_ms, "device_status": st64},
         "e2e": {"value": full.n_qp / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
@@ -796,7 +830,7 @@ def run_beam(args, rank, world, workload="beam"):
                          "pinned-host copies around the device calls and interface sums"),
                 "overlap": OVERLAP,
                 "max_rel_diff_vs_device_step": e2e_err, "device_status": st_e2e},
-        "gpu_launches": 3 * args.steps,
+        "gpu_launches": len(names) * args.steps,
         "clocks": clk.summary(),
         "device_status": st})
     return line, wl
@@ -980,7 +1014,7 @@ def run_batch(args, rank, world):
             step()
         evs_m = timed_steps(step, max(3, args.steps // 2), flush, stream, label="batch_" + name)
         modes[name] = {"ms_per_step": float(np.mean([e[0].elapsed_time(e[1]) for e in evs_m])),
-                       "launches_per_step": mesh.info["launches_force"] + mesh.info["launches_matvec"]}
+                       "launches_per_step": step_launches(mesh.info)}
     mesh.set_launch_mode(tlfe.LAUNCH_AUTO)
     units = wl.n_qp
     peak, peak_kind = peaks()
@@ -988,13 +1022,18 @@ def run_batch(args, rank, world):
     hbm = b_alg / (ms * 1e-3) / 1e9
     # every block is affine and ALU-bound (about 26 FLOP per streamed byte,
     # above the FP32 ridge): FP32 FMA roof, HBM beside it
+    one_pass = bool(info["force_matvec_fused"])   # force and K v in one pass per block and law
+    if one_pass:
+        b_alg = info["stream_bytes_force_matvec"]
+        hbm = b_alg / (ms * 1e-3) / 1e9
     flops = 0.0
     for b in wl.blocks:
         laws = np.asarray(wl.model)[b.body]
         for law in (0, 1):
             f_qp = FLOP_PER_QP_BATCH[(b.etype, law)]
-            flops += int((laws == law).sum()) * b.nq * (f_qp["force"] + f_qp["matvec"])
-    achieved = flops / (ms * 1e-3) / 1e12
+            per = f_qp.get("force_matvec") if one_pass else f_qp["force"] + f_qp["matvec"]
+            flops = None if (flops is None or per is None) else flops + int((laws == law).sum()) * b.nq * per
+    achieved = flops / (ms * 1e-3) / 1e12 if flops else None
     # e2e through the C ABI with host buffers (tlfe_step_host): u and v in,
     # f and K v out, every step; the library overlaps each call's transfers
     # with its neighbours' computation
@@ -1026,9 +1065,10 @@ def run_batch(args, rank, world):
         line["config"]["per_gpu"] = {"n_bodies": wl.n_bodies, "n_elem": wl.n_elem, "n_qp": wl.n_qp}
     line.update({
         "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peaks()["fp32"], "unit": "TFLOP/s",
-                     "frac": achieved / alu_peaks()["fp32"],
+                     "frac": achieved / alu_peaks()["fp32"] if achieved else None,
                      "traffic": ncu_traffic("batch512_step") if wl.n_bodies == 512 and world == 1 else None,
-                     "kernel": "force + matvec, all element blocks (one step)",
+                     "kernel": ("force + matvec in one pass per block and law (one step)" if one_pass else
+                                "force + matvec, all element blocks (one step)"),
                      "peak_source": alu_peaks()["source"],
                      "algorithmic_flops": flops, "algorithmic_bytes": b_alg, "hbm_achieved_gbs": hbm,
                      "hbm_peak_gbs": peak, "hbm_frac": hbm / peak, "hbm_peak_source": peak_kind},
@@ -1037,11 +1077,12 @@ def run_batch(args, rank, world):
                 "call": "tlfe_step_host (C ABI, host buffers)", "overlap": OVERLAP},
         "launch": {"force": "fused" if info["launches_force"] == 1 else "per pass",
                    "matvec": "fused" if info["launches_matvec"] == 1 else "per pass",
+                   "force_matvec_one_pass": one_pass,
                    "chosen_by": "tlfe_autotune (the faster mode per operation)",
                    "fused_passes": info["n_fused_passes"], "fused_items": info["n_fused_items"],
-                   "passes": info["n_passes"], "launches_per_step": info["launches_force"] + info["launches_matvec"],
+                   "passes": info["n_passes"], "launches_per_step": step_launches(info),
                    "graph": "tlfe_force_matvec (captured by the library, replayed)", "modes": modes},
-        "gpu_launches": (info["launches_force"] + info["launches_matvec"]) * args.steps,
+        "gpu_launches": step_launches(info) * args.steps,
         "clocks": clk.summary(), "device_status": st})
     mesh.close()
     return line, wl

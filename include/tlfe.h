@@ -193,6 +193,12 @@ typedef struct {
     double patch_passes;          /* shared-memory passes of one 16-byte node-patch load of a quarter warp
                                      (8 lanes reading one element-local node of their elements), averaged
                                      over the tile kernels' loads; 1 = free of bank conflicts */
+    int32_t force_matvec_fused;   /* 1: tlfe_force_matvec and tlfe_step_host (with f and y requested)
+                                     evaluate the force and the operator product in one pass per element
+                                     block and law (FP32 meshes of T4, T10 and H8 blocks, neither
+                                     operation on the persistent launch; tlfe_autotune keeps the faster
+                                     of one fused pass and two passes); 0: two passes */
+    int64_t stream_bytes_force_matvec;  /* algorithmic bytes of that fused pass (u, udot, v read once; f, y) */
 } tlfe_mesh_info;
 
 tlfe_status tlfe_get_mesh_info(const tlfe_mesh *mesh, tlfe_mesh_info *info);
@@ -254,6 +260,8 @@ tlfe_status tlfe_internal_force_host(tlfe_mesh *mesh, const void *u_host, const 
  *   f_host                       -> tlfe_internal_force
  *   v_host and y_host            -> tlfe_tangent_matvec (a_M, a_K, a_C)
  *   cot_host and any g_*_host    -> tlfe_vjp
+ * (with f and y both requested, as one pass where tlfe_force_matvec would take
+ * it, tlfe_mesh_info.force_matvec_fused)
  * Asynchronous: the call copies the inputs into one of two sets of device
  * staging buffers held by the handle (consecutive calls alternate) on a copy
  * stream of its own, runs the operations on `stream` once the inputs are in,
@@ -304,10 +312,15 @@ tlfe_status tlfe_tangent_matvec(tlfe_mesh *mesh, const void *u_dev, const void *
  * the first after tlfe_autotune, tlfe_set_launch_mode or the first
  * tlfe_set_elem_mu_lambda) evaluates directly and captures the same launches
  * on a stream of its own; later calls with the same arguments replay that
- * graph on `stream`. In TLFE_LAUNCH_AUTO and TLFE_LAUNCH_FUSED modes a mesh
- * with a fused plan runs each operation as one persistent launch. The first
- * call with new arguments must not itself be made during a stream capture.
- * Stream-ordered; the graph is released with the handle. */
+ * graph on `stream`. On an FP32 mesh of T4, T10 and H8 blocks the two
+ * operations run as one pass per element block and law, which gathers the
+ * nodal inputs and forms F, Fdot and the stress once for both outputs
+ * (tlfe_mesh_info.force_matvec_fused says whether it does; tlfe_autotune keeps
+ * the faster of that pass and two passes). Otherwise, in TLFE_LAUNCH_AUTO and
+ * TLFE_LAUNCH_FUSED modes a mesh with a fused plan runs each operation as one
+ * persistent launch. The first call with new arguments must not itself be
+ * made during a stream capture. Stream-ordered; the graph is released with
+ * the handle. */
 tlfe_status tlfe_force_matvec(tlfe_mesh *mesh, const void *u_dev, const void *udot_dev, const void *v_dev,
                               double a_M, double a_K, double a_C, void *f_dev, void *y_dev, void *stream);
 
@@ -383,8 +396,11 @@ tlfe_status tlfe_constraint_j(tlfe_mesh *mesh, int32_t n, const tlfe_constraint 
  * caller's state over the resident CTA sizes (4, 2, 1 warps) and both tile
  * assignments (interleaved; contiguous runs per warp), writing into scratch
  * arrays, and keeps the fastest schedule for later calls with the same
- * material mode (velocity given or not). Results of later calls are unchanged
- * up to the order of floating-point additions in the scatter.
+ * material mode (velocity given or not); with v_dev on an FP32 mesh it also
+ * tunes the one-pass force + operator product of tlfe_force_matvec and keeps
+ * that pass only if it measures faster than the two passes. Results of later
+ * calls are unchanged up to the order of floating-point additions in the
+ * scatter.
  * u_dev: device double [n_nodes][3]; udot_dev, v_dev: device [n_nodes][3] in
  * the mesh dtype, or NULL. Allocates and frees scratch; synchronises `stream`.
  * Optional: without it, the schedule comes from the occupancy API. */

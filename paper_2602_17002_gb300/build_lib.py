@@ -26,7 +26,8 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libtlfe.so")
 LIB_CHECKED = os.path.join(OUT, "libtlfe_checked.so")
 # units holding the element kernels: compiled a second time with the bounds checks
-CHECKED_UNITS = ("k_force.cu", "k_matvec.cu", "k_vjp.cu", "k_diag.cu", "k_fused_force.cu", "k_fused_matvec.cu")
+CHECKED_UNITS = ("k_force.cu", "k_matvec.cu", "k_vjp.cu", "k_diag.cu", "k_fm.cu", "k_fused_force.cu",
+                 "k_fused_matvec.cu")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -1066,6 +1066,8 @@ extern "C" tlfe_status tlfe_get_mesh_info(const tlfe_mesh *m, tlfe_mesh_info *in
         if (m->scatter == TLFE_SCATTER_SORTED) ++n;
         (o == 0 ? info->launches_force : info->launches_matvec) = n;
     }
+    info->force_matvec_fused = fm_eligible(m) ? 1 : 0;
+    info->stream_bytes_force_matvec = eb + nu + nb * (visc ? 4 : 3);  // u (+udot), v read; f, y written
     return TLFE_OK;
 }
 
@@ -1368,6 +1370,36 @@ tlfe_status run_op(tlfe_mesh *m, const void *u, const void *ud, const void *v, v
 }
 
 
+// The fused force + operator-product pass (OP_FM) exists for the tile
+// kernels of FP32 T4, T10 and H8 blocks (not for Q27, whose affine blocks run
+// the warp-per-element kernels); it replaces the two per-pass launches where
+// neither operation runs as the persistent launch.
+static bool fm_kernels(const tlfe_mesh *m)
+{
+    if (m->precision != TLFE_FP32) return false;
+    for (const BlockStore &B : m->blocks)
+        if (B.n_elem > 0 && B.et == ET_Q27) return false;
+    return true;
+}
+
+bool fm_eligible(const tlfe_mesh *m)
+{
+    return m->fm_on && fm_kernels(m) && !use_fused<OP_FORCE, float>(m) && !use_fused<OP_MATVEC, float>(m);
+}
+
+tlfe_status force_matvec_op(tlfe_mesh *m, const void *u, const void *ud, const void *v, double aM, double aK,
+                            double aC, void *f, void *y, cudaStream_t s)
+{
+    if (fm_eligible(m)) return run_op<OP_FM, float>(m, u, ud, v, f, y, nullptr, aM, aK, aC, 0, s);
+    tlfe_status st;
+    if (m->precision == TLFE_FP32) {
+        st = run_op<OP_FORCE, float>(m, u, ud, nullptr, f, nullptr, nullptr, 0, 1, 0, 0, s);
+        return st != TLFE_OK ? st : run_op<OP_MATVEC, float>(m, u, ud, v, y, nullptr, nullptr, aM, aK, aC, 0, s);
+    }
+    st = run_op<OP_FORCE, double>(m, u, ud, nullptr, f, nullptr, nullptr, 0, 1, 0, 0, s);
+    return st != TLFE_OK ? st : run_op<OP_MATVEC, double>(m, u, ud, v, y, nullptr, nullptr, aM, aK, aC, 0, s);
+}
+
 // ---------------------------------------------------------------------------
 // Autotuner: time every resident CTA size (4, 2, 1 warps) and both tile
 // assignments (interleaved, contiguous runs) of each block's force, operator
@@ -1523,6 +1555,28 @@ static tlfe_status tune_all(tlfe_mesh *m, const double *u, const void *ud, const
             st = tune_fused<OP_FORCE>(m, p, s, e0, e1);
             if (st == TLFE_OK && v) st = tune_fused<OP_MATVEC>(m, p, s, e0, e1);
         }
+        // the fused force + operator-product pass: its own schedules, then one
+        // fused pass against the two passes (with their tuned schedules) on
+        // the caller's inputs; the faster is kept
+        if (st == TLFE_OK && v && fm_kernels(m)) {
+            m->fm_on = 1;
+            for (int bi = 0; bi < (int)m->blocks.size() && st == TLFE_OK; ++bi)
+                if (m->blocks[bi].n_elem > 0) st = tune_block<OP_FM, R>(m, bi, p, s, e0, e1);
+            if (st == TLFE_OK && fm_eligible(m)) {
+                float t_fm = 0.f, t_two = 0.f;
+                st = time_median3([&]() { return run_op<OP_FM, float>(m, u, ud, v, o0, o1, nullptr, 0, 1, 1, 0, s); },
+                                  s, e0, e1, &t_fm);
+                if (st == TLFE_OK)
+                    st = time_median3(
+                        [&]() {
+                            tlfe_status s2 = run_op<OP_FORCE, float>(m, u, ud, nullptr, o0, nullptr, nullptr, 0, 1, 0, 0, s);
+                            return s2 != TLFE_OK ? s2
+                                                 : run_op<OP_MATVEC, float>(m, u, ud, v, o1, nullptr, nullptr, 0, 1, 1, 0, s);
+                        },
+                        s, e0, e1, &t_two);
+                if (st == TLFE_OK) m->fm_on = t_fm <= t_two ? 1 : 0;
+            }
+        }
     }
     cudaStreamSynchronize(s);
     if (e0) cudaEventDestroy(e0);
@@ -1541,6 +1595,7 @@ template tlfe_status run_op<OP_DIAG, float>(tlfe_mesh *, const void *, const voi
 template tlfe_status run_op<OP_DIAG, double>(tlfe_mesh *, const void *, const void *, const void *, void *, void *, double *, double, double, double, int, cudaStream_t);
 template tlfe_status run_op<OP_VJP, float>(tlfe_mesh *, const void *, const void *, const void *, void *, void *, double *, double, double, double, int, cudaStream_t);
 template tlfe_status run_op<OP_VJP, double>(tlfe_mesh *, const void *, const void *, const void *, void *, void *, double *, double, double, double, int, cudaStream_t);
+template tlfe_status run_op<OP_FM, float>(tlfe_mesh *, const void *, const void *, const void *, void *, void *, double *, double, double, double, int, cudaStream_t);
 
 }  // namespace tlfe
 
@@ -1557,6 +1612,17 @@ static bool all_affine(const tlfe_mesh *m)
     for (auto &B : m->blocks)
         if (B.n_elem > 0 && !B.affine) return false;
     return true;
+}
+
+tlfe_status tlfe::check_force_matvec(tlfe_mesh *m, const void *u, const void *v, const void *f, const void *y,
+                                     double aM, double aK, double aC)
+{
+    tlfe_status st = check_mesh_args(m, {u, v, f, y});
+    if (st != TLFE_OK) return st;
+    if (f == y) return fail(TLFE_E_INVALID, "f and y must be different arrays");
+    if (!std::isfinite(aM) || !std::isfinite(aK) || !std::isfinite(aC)) return fail(TLFE_E_INVALID, "non-finite coefficient");
+    if (aM != 0.0 && !all_affine(m)) return fail(TLFE_E_UNSUPPORTED, "consistent mass needs affine elements");
+    return TLFE_OK;
 }
 
 extern "C" tlfe_status tlfe_internal_force(tlfe_mesh *m, const void *u, const void *ud, void *f, void *stream)

@@ -1,7 +1,9 @@
 // tlfe_force_matvec: the internal force and the operator product of one
 // state in one call, replayed from a CUDA graph the mesh handle owns (the
-// batched force + K v step: one persistent launch per operation where the
-// mesh has a fused plan, the sorted scatter's node sums, the output clears).
+// batched force + K v step: one fused pass per element block and law where
+// the mesh allows it, else one persistent launch per operation where the mesh
+// has a fused plan, or one launch per pass and operation; the sorted
+// scatter's node sums; the output clears).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -29,14 +31,6 @@ void destroy_graphs(tlfe_mesh *m)
     m->fm_graph = nullptr;
 }
 
-template <typename R>
-static tlfe_status record_ops(tlfe_mesh *m, const void *u, const void *ud, const void *v, double aM, double aK,
-                              double aC, void *f, void *y, cudaStream_t s)
-{
-    tlfe_status st = run_op<OP_FORCE, R>(m, u, ud, nullptr, f, nullptr, nullptr, 0, 1, 0, 0, s);
-    if (st != TLFE_OK) return st;
-    return run_op<OP_MATVEC, R>(m, u, ud, v, y, nullptr, nullptr, aM, aK, aC, 0, s);
-}
 
 }  // namespace tlfe
 
@@ -46,9 +40,8 @@ extern "C" tlfe_status tlfe_force_matvec(tlfe_mesh *m, const void *u, const void
                                          double aK, double aC, void *f, void *y, void *stream)
 {
     TLFE_TRACE("tlfe_force_matvec");
-    if (!m) return fail(TLFE_E_INVALID, "mesh is NULL");
-    if (!u || !v || !f || !y) return fail(TLFE_E_INVALID, "required array pointer is NULL");
-    if (f == y) return fail(TLFE_E_INVALID, "f and y must be different arrays");
+    tlfe_status st = check_force_matvec(m, u, v, f, y, aM, aK, aC);
+    if (st != TLFE_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     OpGraph *g = m->fm_graph;
     if (g && g->exec && g->u == u && g->ud == ud && g->v == v && g->f == f && g->y == y && g->aM == aM &&
@@ -57,11 +50,9 @@ extern "C" tlfe_status tlfe_force_matvec(tlfe_mesh *m, const void *u, const void
         if (e != cudaSuccess) return cuda_fail(e, "tlfe_force_matvec: graph launch");
         return TLFE_OK;
     }
-    // new arguments: evaluate directly (validates them, fills the launch
-    // caches), then capture the same calls on the handle's capture stream
-    tlfe_status st = tlfe_internal_force(m, u, ud, f, stream);
-    if (st != TLFE_OK) return st;
-    st = tlfe_tangent_matvec(m, u, ud, v, aM, aK, aC, y, stream);
+    // new arguments: evaluate directly (fills the launch caches), then
+    // capture the same launches on the handle's capture stream
+    st = force_matvec_op(m, u, ud, v, aM, aK, aC, f, y, s);
     if (st != TLFE_OK) return st;
     if (!g) g = m->fm_graph = new OpGraph();
     if (g->exec) {
@@ -74,8 +65,7 @@ extern "C" tlfe_status tlfe_force_matvec(tlfe_mesh *m, const void *u, const void
     }
     cudaError_t e = cudaStreamBeginCapture(g->cap, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "tlfe_force_matvec: begin capture");
-    st = m->precision == TLFE_FP32 ? record_ops<float>(m, u, ud, v, aM, aK, aC, f, y, g->cap)
-                                   : record_ops<double>(m, u, ud, v, aM, aK, aC, f, y, g->cap);
+    st = force_matvec_op(m, u, ud, v, aM, aK, aC, f, y, g->cap);
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(g->cap, &graph);
     if (st != TLFE_OK) {

@@ -111,6 +111,13 @@ extern "C" tlfe_status tlfe_step_host(tlfe_mesh *m, const tlfe_host_step *a, voi
     if (h.used[b]) CKH(cudaStreamWaitEvent(s, h.out_done[b], 0));
     const void *ud = a->udot_host ? dud : nullptr;
     tlfe_status st = TLFE_OK;
+    if (do_f && do_y && fm_eligible(m)) {  // one fused pass for both
+        st = check_force_matvec(m, du, dv, df, dy, a->a_M, a->a_K, a->a_C);
+        if (st == TLFE_OK) st = force_matvec_op(m, du, ud, dv, a->a_M, a->a_K, a->a_C, df, dy, s);
+        if (st != TLFE_OK) return st;
+        CKH(cudaEventRecord(h.op_done[b][0], s));
+        CKH(cudaEventRecord(h.op_done[b][1], s));
+    } else {
     if (do_f) {
         st = tlfe_internal_force(m, du, ud, df, stream);
         if (st != TLFE_OK) return st;
@@ -120,6 +127,7 @@ extern "C" tlfe_status tlfe_step_host(tlfe_mesh *m, const tlfe_host_step *a, voi
         st = tlfe_tangent_matvec(m, du, ud, dv, a->a_M, a->a_K, a->a_C, dy, stream);
         if (st != TLFE_OK) return st;
         CKH(cudaEventRecord(h.op_done[b][1], s));
+    }
     }
     if (do_g) {
         st = tlfe_vjp(m, du, ud, dcot, a->g_u_host ? dgu : nullptr, a->g_udot_host ? dgud : nullptr,

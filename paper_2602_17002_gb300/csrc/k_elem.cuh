@@ -302,7 +302,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 template <int ET, typename R, int OP, bool AFF, int MAT> constexpr int min_ctas()
 {
     if (sizeof(R) != 4 || ET == ET_Q27) return 1;
-    if (OP == OP_VJP) {
+    if (OP == OP_VJP || OP == OP_FM) {
         const bool fits = ET == ET_T4 || MAT == MAT_NH_KV || MAT == MAT_SVK || (MAT == MAT_SVK_KV && AFF) ||
                           (ET == ET_H8 && MAT != MAT_ANY);
         return fits ? 3 : 2;
@@ -341,10 +341,14 @@ __device__ __forceinline__ bool elem_tiles(const KParams<R> &p, unsigned char *w
     constexpr uint32_t AB = AFF ? AffRec<R>::BYTES : 0;
     constexpr bool PF_EARLY = AFF && OP != OP_VJP;  // where the next tile's L2 prefetch goes (see prefetch_next)
     constexpr bool PF_NONE = AFF && OP == OP_VJP;
-    constexpr bool LI_REREAD = OP == OP_FORCE || OP == OP_VJP;
-    // the adjoint also re-reads J^{-1} (affine record) and node 0's pair at
-    // every point: 168 registers without spill (12 warps per SM)
-    constexpr bool DIET = OP == OP_VJP;
+    constexpr bool LI_REREAD = OP == OP_FORCE || OP == OP_VJP || OP == OP_FM;
+    // two element vectors per element: the adjoint's (g_u, g_udot) and the
+    // fused force + operator product's (f, y)
+    constexpr bool TWO = OP == OP_VJP || OP == OP_FM;
+    // the adjoint (and the fused force + operator product, which holds as
+    // many accumulators) also re-reads J^{-1} (affine record) and node 0's
+    // pair at every point: 168 registers without spill (12 warps per SM)
+    constexpr bool DIET = OP == OP_VJP || OP == OP_FM;
 
     const int lane = threadIdx.x & 31;
     const int MB = p.meta_bytes;
@@ -524,7 +528,7 @@ __device__ __forceinline__ bool elem_tiles(const KParams<R> &p, unsigned char *w
             if constexpr (PKA) {
                 ap0[i] = make_float2(0.f, 0.f);
                 acc0[i][2] = R(0);
-                if (OP == OP_VJP) {
+                if (TWO) {
                     ap1[i] = make_float2(0.f, 0.f);
                     acc1[i][2] = R(0);
                 }
@@ -532,7 +536,7 @@ __device__ __forceinline__ bool elem_tiles(const KParams<R> &p, unsigned char *w
 #pragma unroll
                 for (int d = 0; d < 3; ++d) {
                     acc0[i][d] = R(0);
-                    if (OP == OP_VJP) acc1[i][d] = R(0);
+                    if (TWO) acc1[i][d] = R(0);
                 }
             }
         }
@@ -795,6 +799,9 @@ __device__ __forceinline__ bool elem_tiles(const KParams<R> &p, unsigned char *w
                     for (int k2 = 0; k2 < 9; ++k2) T0[k2] = P[k2];
                 } else if (OP == OP_MATVEC) {
                     dstress<R>(m, s1, visc, D, p.aK, p.aC, p.sym_only != 0, T0);
+                } else if (OP == OP_FM) {
+                    // FP32 only: the force's and the operator product's
+                    // element vectors are accumulated one after the other below
                 } else {
                     R gmu, glam;
                     astress<R>(m, s1, visc, D, T0, T1, gmu, glam);
@@ -824,10 +831,38 @@ __device__ __forceinline__ bool elem_tiles(const KParams<R> &p, unsigned char *w
                             }
                         }
                     };
+                    if constexpr (OP == OP_FM) {
+                        // force first (P packed and accumulated, then dead),
+                        // then the stress derivative along the direction, so
+                        // that the two point operators are never live together
+                        float2 Tp[3];
+                        float Ts[3];
+                        pack(P, Tp, Ts);
+#pragma unroll
+                        for (int i = 0; i < NPE; ++i)
+#pragma unroll
+                            for (int k2 = 0; k2 < 3; ++k2)
+                                if (nz(i, k2)) {
+                                    const float hk = grad(i, k2);
+                                    ap0[i] = fma2(Tp[k2], bc2(hk), ap0[i]);
+                                    acc0[i][2] = fmaf(Ts[k2], hk, acc0[i][2]);
+                                }
+                        dstress<R>(m, s1, visc, D, p.aK, p.aC, p.sym_only != 0, T1);
+                        pack(T1, Tp, Ts);
+#pragma unroll
+                        for (int i = 0; i < NPE; ++i)
+#pragma unroll
+                            for (int k2 = 0; k2 < 3; ++k2)
+                                if (nz(i, k2)) {
+                                    const float hk = grad(i, k2);
+                                    ap1[i] = fma2(Tp[k2], bc2(hk), ap1[i]);
+                                    acc1[i][2] = fmaf(Ts[k2], hk, acc1[i][2]);
+                                }
+                    } else {
                     float2 Tp0[3], Tp1[3];
                     float Ts0[3], Ts1[3];
                     pack(T0, Tp0, Ts0);
-                    if (OP == OP_VJP) pack(T1, Tp1, Ts1);
+                    if (TWO) pack(T1, Tp1, Ts1);
 #pragma unroll
                     for (int i = 0; i < NPE; ++i) {
 #pragma unroll
@@ -836,17 +871,18 @@ __device__ __forceinline__ bool elem_tiles(const KParams<R> &p, unsigned char *w
                                 const float hk = grad(i, k2);
                                 ap0[i] = fma2(Tp0[k2], bc2(hk), ap0[i]);
                                 acc0[i][2] = fmaf(Ts0[k2], hk, acc0[i][2]);
-                                if (OP == OP_VJP) {
+                                if (TWO) {
                                     ap1[i] = fma2(Tp1[k2], bc2(hk), ap1[i]);
                                     acc1[i][2] = fmaf(Ts1[k2], hk, acc1[i][2]);
                                 }
                             }
                     }
+                    }
                 } else {
 #pragma unroll
                 for (int k2 = 0; k2 < 9; ++k2) {
                     T0[k2] *= w;
-                    if (OP == OP_VJP) T1[k2] *= w;
+                    if (TWO) T1[k2] *= w;
                 }
                 if constexpr (AFF) {
                     // T h_i = (T J^{-T}) g_i
@@ -859,7 +895,7 @@ __device__ __forceinline__ bool elem_tiles(const KParams<R> &p, unsigned char *w
                                             T0[a * 3 + 2] * Ji[k2 * 3 + 2];
 #pragma unroll
                     for (int k2 = 0; k2 < 9; ++k2) T0[k2] = T[k2];
-                    if (OP == OP_VJP) {
+                    if (TWO) {
 #pragma unroll
                         for (int a = 0; a < 3; ++a)
 #pragma unroll
@@ -881,7 +917,7 @@ __device__ __forceinline__ bool elem_tiles(const KParams<R> &p, unsigned char *w
                         for (int k2 = 0; k2 < 3; ++k2)
                             if (nz(i, k2)) {
                                 acc0[i][a] += T0[a * 3 + k2] * hk[k2];
-                                if (OP == OP_VJP) acc1[i][a] += T1[a * 3 + k2] * hk[k2];
+                                if (TWO) acc1[i][a] += T1[a * 3 + k2] * hk[k2];
                             }
                 }
                 }
@@ -910,31 +946,36 @@ __device__ __forceinline__ bool elem_tiles(const KParams<R> &p, unsigned char *w
             break;
         }
 
-        // consistent mass of affine elements: m_ij = rho V Mhat_ij (Sec. 4.1)
-        if ((OP == OP_MATVEC || OP == OP_DIAG) && p.aM != R(0)) {
+        // consistent mass of affine elements: m_ij = rho V Mhat_ij (Sec. 4.1),
+        // into the operator product (the second element vector of OP_FM)
+        if ((OP == OP_MATVEC || OP == OP_DIAG || OP == OP_FM) && p.aM != R(0)) {
             const R c = p.aM * m.rho * p.evol[(size_t)t * 32 + lane];
-            if (OP == OP_MATVEC) {
+            if (OP == OP_MATVEC || OP == OP_FM) {
+                float2 *apy = OP == OP_FM ? ap1 : ap0;
+                R(*accy)[3] = OP == OP_FM ? acc1 : acc0;
 #pragma unroll
                 for (int jn = 0; jn < NPE; ++jn) {
+                    const int lj = LI_REREAD ? (int)bounds_clamp(lds_u16_volatile(mlidx + jn * 32 + lane), U, p.status)
+                                             : li[jn];
                     if constexpr (PKA) {
-                        const float *rec = work + li[jn] * REC;
+                        const float *rec = work + lj * REC;
                         const float2 v01 = *reinterpret_cast<const float2 *>(rec + RC::V01);
                         const float v2 = rec[RC::V2];
 #pragma unroll
                         for (int i = 0; i < NPE; ++i) {
                             const float mh = c * float(mass_hat(ET, i, jn));
-                            ap0[i] = fma2(v01, bc2(mh), ap0[i]);
-                            acc0[i][2] += mh * v2;
+                            apy[i] = fma2(v01, bc2(mh), apy[i]);
+                            accy[i][2] += mh * v2;
                         }
                     } else {
                         R x[3];
-                        ld3c<OFF_V>(work + li[jn] * REC, x[0], x[1], x[2]);
+                        ld3c<OFF_V>(work + lj * REC, x[0], x[1], x[2]);
 #pragma unroll
                         for (int i = 0; i < NPE; ++i) {
                             const R mh = c * R(mass_hat(ET, i, jn));
-                            acc0[i][0] += mh * x[0];
-                            acc0[i][1] += mh * x[1];
-                            acc0[i][2] += mh * x[2];
+                            accy[i][0] += mh * x[0];
+                            accy[i][1] += mh * x[1];
+                            accy[i][2] += mh * x[2];
                         }
                     }
                 }
@@ -1084,11 +1125,15 @@ namespace tlfe {
 
 template <int OP, typename R, bool AFF, int MAT> static void (*kernel_for_(int et, int nq))(const KParams<R>)
 {
+    if constexpr (OP == OP_FM) {  // the fused force + operator product: FP32 T4, T10 and H8 blocks
+        if (sizeof(R) != 4 || et == ET_Q27) return nullptr;
+    }
     if (et == ET_T4 && nq == 1) return k_elem<ET_T4, 1, R, OP, AFF, MAT>;
     if (et == ET_T10 && nq == 4) return k_elem<ET_T10, 4, R, OP, AFF, MAT>;
     if (et == ET_T10 && nq == 5) return k_elem<ET_T10, 5, R, OP, AFF, MAT>;
     if (et == ET_H8 && nq == 8) return k_elem<ET_H8, 8, R, OP, AFF, MAT>;
-    if (et == ET_Q27 && nq == 27) return k_elem<ET_Q27, 27, R, OP, AFF, MAT>;
+    if constexpr (OP != OP_FM)
+        if (et == ET_Q27 && nq == 27) return k_elem<ET_Q27, 27, R, OP, AFF, MAT>;
     return nullptr;
 }
 // FP32 kernels are specialised on the material mode; FP64 kernels (the plain
@@ -1108,7 +1153,11 @@ template <int OP, typename R, bool AFF> static void (*kernel_for_m(int et, int n
 }
 template <int OP, typename R> static void (*kernel_for(int et, int nq, bool aff, int mat))(const KParams<R>)
 {
-    if (wpe_path(et, aff)) return wpe_kernel_for<OP, R>(mat);
+    if constexpr (OP == OP_FM) {
+        if (wpe_path(et, aff)) return nullptr;
+    } else {
+        if (wpe_path(et, aff)) return wpe_kernel_for<OP, R>(mat);
+    }
     return aff ? kernel_for_m<OP, R, true>(et, nq, mat) : kernel_for_m<OP, R, false>(et, nq, mat);
 }
 
@@ -1117,12 +1166,12 @@ template <int OP, typename R, bool AFF> size_t smem_for_(int et, int umax, int m
     if (et == ET_T4) return elem_smem_bytes<ET_T4, R, OP, AFF>(umax, meta_bytes, wpb);
     if (et == ET_T10) return elem_smem_bytes<ET_T10, R, OP, AFF>(umax, meta_bytes, wpb);
     if (et == ET_H8) return elem_smem_bytes<ET_H8, R, OP, AFF>(umax, meta_bytes, wpb);
-    if (et == ET_Q27) return elem_smem_bytes<ET_Q27, R, OP, AFF>(umax, meta_bytes, wpb);
+    if (et == ET_Q27 && OP != OP_FM) return elem_smem_bytes<ET_Q27, R, OP, AFF>(umax, meta_bytes, wpb);
     return 0;
 }
 template <int OP, typename R> size_t smem_for(int et, int umax, int meta_bytes, int wpb, bool aff)
 {
-    if (wpe_path(et, aff)) return wpe_smem_bytes<R>(wpb);
+    if (wpe_path(et, aff)) return OP == OP_FM ? 0 : wpe_smem_bytes<R>(wpb);
     return aff ? smem_for_<OP, R, true>(et, umax, meta_bytes, wpb) : smem_for_<OP, R, false>(et, umax, meta_bytes, wpb);
 }
 

@@ -12,7 +12,9 @@
 
 namespace tlfe {
 
-enum { OP_FORCE = 0, OP_MATVEC = 1, OP_VJP = 2, OP_DIAG = 3 };
+// OP_FM: internal force and operator product of one state in one pass
+// (outputs f and y; the gather, kinematics and stress state shared)
+enum { OP_FORCE = 0, OP_MATVEC = 1, OP_VJP = 2, OP_DIAG = 3, OP_FM = 4 };
 // status word: counts of device-side events, read and cleared by tlfe_sync;
 // ST_BOUNDS counts table indices found out of range (bounds-checked build)
 enum { ST_INVERTED = 0, ST_NONFINITE = 1, ST_TIMEOUT = 2, ST_BOUNDS = 3, ST_COUNT = 4 };
@@ -28,8 +30,8 @@ __host__ __device__ inline bool wpe_path(int et, bool aff) { return et == ET_Q27
 
 // values per node held in a warp's shared-memory patch: inputs (u, udot
 // [, v or cotangent]) then outputs (one array, two for the adjoint)
-__host__ __device__ constexpr int op_in_fields(int op) { return (op == OP_MATVEC || op == OP_VJP) ? 9 : 6; }
-__host__ __device__ constexpr int op_nf(int op) { return op_in_fields(op) + (op == OP_VJP ? 6 : 3); }
+__host__ __device__ constexpr int op_in_fields(int op) { return (op == OP_MATVEC || op == OP_VJP || op == OP_FM) ? 9 : 6; }
+__host__ __device__ constexpr int op_nf(int op) { return op_in_fields(op) + ((op == OP_VJP || op == OP_FM) ? 6 : 3); }
 
 // Everything an element kernel needs about one block and one call.
 template <typename R> struct KParams {

@@ -119,6 +119,9 @@ struct tlfe_mesh {
     tlfe::OpGraph *fm_graph = nullptr;
     int sched_gen = 0;  // bumped whenever launch schedules, mode or block parameters change
     tlfe::HostStage *host_stage = nullptr;
+    // the force and the operator product of one state as one fused pass
+    // (OP_FM) where the mesh allows it; tlfe_autotune sets it by measurement
+    int fm_on = 1;
     // scratch of the standalone constraint calls (tlfe_constraint_eval / _j /
     // _jt): point data for con_cap constraints, grown on demand and kept
     // until the handle is destroyed
@@ -142,6 +145,14 @@ struct TraceRange {
 #define TLFE_TRACE(name) tlfe::TraceRange tlfe_trace_range_(name)
 
 tlfe_status fail(tlfe_status st, const std::string &msg);
+// force and operator product of one state (tlfe_force_matvec, tlfe_step_host):
+// one fused pass where fm_eligible, else the two passes; the argument checks
+// of tlfe_internal_force and tlfe_tangent_matvec together
+bool fm_eligible(const tlfe_mesh *m);
+tlfe_status force_matvec_op(tlfe_mesh *m, const void *u, const void *ud, const void *v, double aM, double aK,
+                            double aC, void *f, void *y, cudaStream_t s);
+tlfe_status check_force_matvec(tlfe_mesh *m, const void *u, const void *v, const void *f, const void *y, double aM,
+                               double aK, double aC);
 void destroy_graphs(tlfe_mesh *m);      // graph.cu
 void destroy_host_stage(tlfe_mesh *m);  // hoststep.cu
 tlfe_status cuda_fail(cudaError_t e, const char *where);

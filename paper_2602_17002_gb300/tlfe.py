@@ -62,7 +62,8 @@ class tlfe_mesh_info(C.Structure):
                 ("stream_bytes_matvec", C.c_int64), ("stream_bytes_vjp", C.c_int64),
                 ("device_bytes", C.c_int64), ("n_affine_blocks", C.c_int32), ("n_passes", C.c_int32),
                 ("n_fused_passes", C.c_int32), ("n_fused_items", C.c_int32), ("launches_force", C.c_int32),
-                ("launches_matvec", C.c_int32), ("patch_layout", C.c_int32), ("patch_passes", C.c_double)]
+                ("launches_matvec", C.c_int32), ("patch_layout", C.c_int32), ("patch_passes", C.c_double),
+                ("force_matvec_fused", C.c_int32), ("stream_bytes_force_matvec", C.c_int64)]
 
 
 class tlfe_step_params(C.Structure):
