@@ -1,6 +1,7 @@
 // Element kernels of the TL-FEA hot path (internal force, operator product,
-// adjoint, Jacobi diagonal), templated on element type, quadrature size,
-// arithmetic type and operation.
+// adjoint, Jacobi diagonal, and the force and operator product of one state
+// in one pass), templated on element type, quadrature size, arithmetic type
+// and operation.
 //
 // Work decomposition: one thread per element, one warp per tile of 32
 // elements, warps independent of each other (persistent, grid-striding over
