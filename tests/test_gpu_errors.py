@@ -72,6 +72,9 @@ def _operators(wl, prec, ks=None):
     cv = mesh.tangent_matvec(u, ud, v, 0.0, 0.0, 1.0).double().cpu().numpy() if wl.udot is not None else None
     gu, gud, gth = (None if x is None else x.double().cpu().numpy() for x in mesh.vjp(u, ud, v))
     dg = mesh.jacobi_diag(u, ud, 0.0, 1.0, 1.0).double().cpu().numpy()
+    one_pass = bool(mesh.info["force_matvec_fused"])
+    if one_pass:   # the same results from the one-pass force + operator product (tlfe_force_matvec)
+        f1, y1 = (x.double().cpu().numpy() for x in mesh.force_matvec(u, ud, v, 0.0, 1.0, 1.0))
     mesh.sync()
     mesh.close()
     sub, emask = (wl, np.ones(wl.n_elem, bool)) if ks is None else _subset(wl, ks)
@@ -82,10 +85,15 @@ def _operators(wl, prec, ks=None):
     gu_ref, gud_ref, gth_ref = oracle.vjp(sub, wl.v)
     dg_ref = oracle.jacobi_diag(sub, a_K=1.0, a_C=1.0)
     damped = wl.udot is not None and np.abs(wl.params[:, 2:4]).max() > 0
-    return {"f": rel(f[sel], f_ref[sel]), "Kv": rel(kv[sel], kv_ref[sel]),
-            "Cv": rel(cv[sel], cv_ref[sel]) if damped else None,
-            "g_u": rel(gu[sel], gu_ref[sel]), "g_udot": rel(gud[sel], gud_ref[sel]) if damped else None,
-            "g_theta": rel(gth[emask], gth_ref), "diag": rel(dg[sel], dg_ref[sel])}
+    out = {"f": rel(f[sel], f_ref[sel]), "Kv": rel(kv[sel], kv_ref[sel]),
+           "Cv": rel(cv[sel], cv_ref[sel]) if damped else None,
+           "g_u": rel(gu[sel], gu_ref[sel]), "g_udot": rel(gud[sel], gud_ref[sel]) if damped else None,
+           "g_theta": rel(gth[emask], gth_ref), "diag": rel(dg[sel], dg_ref[sel])}
+    if one_pass:
+        y_ref = kv_ref + cv_ref if cv_ref is not None else kv_ref
+        out["f_one_pass"] = rel(f1[sel], f_ref[sel])
+        out["Kv+Cv_one_pass"] = rel(y1[sel], y_ref[sel])
+    return out
 
 
 @pytest.mark.parametrize("prec", [0, 1])
@@ -118,6 +126,12 @@ def test_errors_batch():
     u, v = dev(wl.u, torch.float64), dev(wl.v, torch.float32)
     f, y = mesh.force_matvec(u, None, v, 0.0, 1.0, 0.0)
     mesh.sync()
+    f, y = f.clone(), y.clone()
+    # the same step as the benchmark runs it after autotuning: one pass per block and law
+    mesh.set_launch_mode(tl.LAUNCH_PER_PASS)
+    assert mesh.info["force_matvec_fused"] == 1
+    f1, y1 = mesh.force_matvec(u, None, v, 0.0, 1.0, 0.0)
+    mesh.sync()
     lo = np.full(wl.n_bodies, np.iinfo(np.int64).max)
     hi = np.full(wl.n_bodies, -1)
     for blk in wl.blocks:
@@ -134,7 +148,7 @@ def test_errors_batch():
     f_ref, _ = oracle.internal_force(sub)
     y_ref = oracle.operator_apply(sub, wl.v, a_K=1.0)
     errs = {}
-    for name, got, ref in (("f", f, f_ref), ("Kv", y, y_ref)):
+    for name, got, ref in (("f", f, f_ref), ("Kv", y, y_ref), ("f_one_pass", f1, f_ref), ("Kv_one_pass", y1, y_ref)):
         g = got.double().cpu().numpy()[ks]
         r = ref[ks]
         den = np.zeros(wl.n_bodies)
