@@ -51,6 +51,19 @@ def test_batch_flop_table_covers_every_type_and_law():
         for lw in np.unique(law[b.body]):
             ent = bench.FLOP_PER_QP_BATCH[(b.etype, int(lw))]
             assert 0 < ent["force"] < ent["matvec"]
+            # one pass does the operator product's work and less than both passes
+            assert ent["matvec"] < ent["force_matvec"] < ent["force"] + ent["matvec"]
+    beam = bench.FLOP_PER_QP["beam"]
+    assert beam["matvec"] < beam["force_matvec"] < beam["force"] + beam["matvec"]
+
+
+def test_streamed_bytes_of_the_one_pass_kernel():
+    """The one pass reads the element data and the inputs once and writes f
+    and y: the operator product's bytes plus one written node array."""
+    wl = synth.small_beam(cells=(6, 2, 2))
+    sb = bench.streamed_bytes(wl)
+    assert sb["force_matvec"] == sb["matvec"] + 3 * 4 * wl.n_nodes
+    assert sb["force_matvec"] < sb["force"] + sb["matvec"]
 
 
 def test_command_line_lists_the_workloads_and_modes():
