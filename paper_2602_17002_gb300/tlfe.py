@@ -297,7 +297,8 @@ class Mesh:
 
     def force_matvec(self, u, udot, v, a_M=0.0, a_K=1.0, a_C=0.0, f=None, y=None, stream=None):
         """f = f_int(u, udot) and y = a_M M v + a_K K_t v + a_C C v in one call,
-        replayed from a CUDA graph the mesh keeps (tlfe_force_matvec)."""
+        replayed from a CUDA graph the mesh keeps (tlfe_force_matvec); one pass
+        per element block and law where info["force_matvec_fused"] is 1."""
         import torch
         self._node_array(u, "u", torch.float64)
         self._node_array(udot, "udot")
