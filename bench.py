@@ -34,7 +34,7 @@ workload, and a 512 MiB memset flushes L2 before every timed step, outside
 the step's CUDA-event pair.
 
 --impl reference times the CPU FP64 oracle on a bounded sample of the same
-workload on the host cores (the reference arm of this build).
+workload on the host cores (the benchmark's reference arm).
 """
 
 from __future__ import annotations

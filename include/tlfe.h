@@ -61,7 +61,7 @@ typedef enum {
     TLFE_E_INVERTED = 4,      /* J_p <= 0 at creation, or J <= 0 (neo-Hookean) on the device */
     TLFE_E_NOT_CONVERGED = 5, /* Newton did not reach the tolerance within max_newton */
     TLFE_E_TIMEOUT = 6,       /* a bounded device-side wait ran out */
-    TLFE_E_UNSUPPORTED = 7,   /* valid request this build does not implement */
+    TLFE_E_UNSUPPORTED = 7,   /* valid request the library does not implement */
     TLFE_E_NONFINITE = 8      /* NaN / Inf met on the device */
 } tlfe_status;
 
