@@ -215,3 +215,20 @@ def test_two_gloo_ranks_step_one_split_body_like_the_unsplit_oracle():
         nodes, v, _ = got[r]
         assert np.abs(v - v_ref[nodes]).max() <= 1e-10 * np.abs(v_ref).max()
         assert np.abs(v[wl.fixed[nodes] == 1]).max(initial=0.0) == 0.0
+
+
+def test_edge_cases_one_share_and_a_body_already_at_rest_in_equilibrium():
+    """One share (no interface nodes) is the unsplit step; a body at rest
+    with no load has g(v_n) = 0 and takes no Newton iteration."""
+    wl = clamped_beam(cells=6)
+    masks, nodes, ifs = _split(wl, 1)
+    assert ifs[0].n == 0 and nodes[0].size == wl.n_nodes
+    part = OracleShare(shard.sub_workload(wl, masks[0])[0], shard.owned_rows(nodes[0].size, ifs[0]), G)
+    rep = shard.split_newton_step([part], shard.LocalGroup(ifs, "cpu", pack=_np_pack, unpack=_np_unpack), H,
+                                  newton_rtol=1e-10, cg_rtol=1e-8)
+    v_ref, _ = _reference(wl)
+    assert rep["status"] == 0 and np.abs(part.v - v_ref[nodes[0]]).max() <= 1e-10 * np.abs(v_ref).max()
+    rest = OracleShare(shard.sub_workload(wl, masks[0])[0], np.ones(wl.n_nodes, bool), np.zeros(3))
+    rep0 = shard.split_newton_step([rest], shard.LocalGroup(ifs, "cpu", pack=_np_pack, unpack=_np_unpack), H)
+    assert rep0 == {"newton_iters": 0, "cg_iters": 0, "status": 0, "rel_residual": 0.0}
+    assert np.array_equal(rest.v, np.zeros_like(rest.v))
